@@ -1,0 +1,137 @@
+"""AlSub oracle -- TEST INFRASTRUCTURE ONLY.
+
+A ctypes wrapper around ``alsub_oracle.c``: a plain, serial FP64 half-edge subdivider written
+from the paper's classical rules (Catmull-Clark Sec. 3.1, creases Sec. 3.3, sqrt(3) Appendix A,
+Loop Appendix B). Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
+may import this package. It shares no code with the CUDA path and never calls it.
+
+Every function follows its passage as cited in the C source. One part is "parity unpinned": the
+crease vertex/edge rule reading (the paper delegates the rules to DeRose et al. 1998 and prints no
+example); it is pinned only by its limit cases.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "alsub_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+SCHEMES = {"cc": 0, "loop": 1, "sqrt3": 2}
+ERRORS = {1: "invalid argument", 2: "non-manifold", 3: "boundary (open mesh)", 4: "out of memory",
+          5: "invalid crease"}
+
+
+class OracleError(RuntimeError):
+    def __init__(self, code):
+        super().__init__(f"oracle error {code}: {ERRORS.get(code, '?')}")
+        self.code = code
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction, so FP32 crease arithmetic is exact)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off",
+                               "-fno-fast-math", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
+            f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
+            f64p = np.ctypeslib.ndpointer(np.float64, flags="C")
+            lib.or_run.argtypes = [ctypes.c_int] * 4 + [ctypes.c_int, ctypes.c_int, i32p, i32p, f64p,
+                                                        ctypes.c_int, i32p, f32p,
+                                                        ctypes.POINTER(ctypes.c_void_p)]
+            lib.or_counts.argtypes = [ctypes.c_void_p, ctypes.c_int, np.ctypeslib.ndpointer(np.int64)]
+            lib.or_faces.argtypes = [ctypes.c_void_p, ctypes.c_int, i32p, i32p]
+            lib.or_positions.argtypes = [ctypes.c_void_p, ctypes.c_int, f64p]
+            lib.or_creases.argtypes = [ctypes.c_void_p, ctypes.c_int, i32p, f32p]
+            lib.or_operator.argtypes = [ctypes.c_void_p, ctypes.c_int, i32p, i32p, f64p]
+            lib.or_free.argtypes = [ctypes.c_void_p]
+            for f in ("or_run", "or_counts", "or_faces", "or_positions", "or_creases", "or_operator"):
+                getattr(lib, f).restype = ctypes.c_int
+            lib.or_free.restype = None
+            _lib = lib
+    return _lib
+
+
+def subdivide(mesh: dict, levels: int, scheme: str | None = None, keep_all: bool = True,
+              operator: bool = False, P0=None) -> list[dict | None]:
+    """Refine ``mesh`` ``levels`` times; returns one dict per level (None for levels not kept).
+
+    Each dict holds V, F, nnz, E, K, off, fv, P (float64[V,3]), crease_verts, crease_sharp and,
+    when ``operator`` is set and the level is below ``levels``, the operator R_l as COO
+    (R_rows, R_cols, R_w) mapping level l to level l+1.
+    """
+    lib = _load()
+    scheme = scheme or mesh.get("scheme", "cc")
+    off = np.ascontiguousarray(mesh["off"], dtype=np.int32)
+    fv = np.ascontiguousarray(mesh["fv"], dtype=np.int32)
+    P = np.ascontiguousarray(mesh["P"] if P0 is None else P0, dtype=np.float64).reshape(-1)
+    cv = np.ascontiguousarray(mesh["crease_verts"], dtype=np.int32).reshape(-1)
+    cs = np.ascontiguousarray(mesh["crease_sharp"], dtype=np.float32).reshape(-1)
+    if cv.size == 0:
+        cv = np.zeros(2, np.int32)
+        cs_n = 0
+        cs = np.zeros(1, np.float32)
+    else:
+        cs_n = cs.size
+    h = ctypes.c_void_p()
+    st = lib.or_run(SCHEMES[scheme], int(levels), int(keep_all), int(operator), int(mesh["V"]),
+                    int(mesh["F"]), off, fv, P, cs_n, cv, cs, ctypes.byref(h))
+    if st:
+        raise OracleError(st)
+    try:
+        out = []
+        for l in range(levels + 1):
+            cnt = np.zeros(6, np.int64)
+            if lib.or_counts(h, l, cnt):
+                out.append(None)
+                continue
+            V, F, nnz, E, K, rnnz = (int(x) for x in cnt)
+            d = dict(V=V, F=F, nnz=nnz, E=E, K=K)
+            d["off"] = np.zeros(F + 1, np.int32)
+            d["fv"] = np.zeros(max(nnz, 1), np.int32)
+            lib.or_faces(h, l, d["off"], d["fv"])
+            d["fv"] = d["fv"][:nnz]
+            Pl = np.zeros(3 * V, np.float64)
+            lib.or_positions(h, l, Pl)
+            d["P"] = Pl.reshape(V, 3)
+            cvl = np.zeros(2 * K + 2, np.int32)
+            csl = np.zeros(K + 1, np.float32)
+            lib.or_creases(h, l, cvl, csl)
+            d["crease_verts"] = cvl[:2 * K].reshape(K, 2)
+            d["crease_sharp"] = csl[:K]
+            if operator and l < levels and rnnz > 0:
+                rr = np.zeros(rnnz, np.int32)
+                rc = np.zeros(rnnz, np.int32)
+                rw = np.zeros(rnnz, np.float64)
+                lib.or_operator(h, l, rr, rc, rw)
+                d["R_rows"], d["R_cols"], d["R_w"] = rr, rc, rw
+            out.append(d)
+        return out
+    finally:
+        lib.or_free(h)
+
+
+def operator_matrix(level: dict, n_cols: int):
+    """The level's operator as a scipy.sparse CSR matrix (rows = next level's vertices)."""
+    import scipy.sparse as sp
+    n_rows = int(level["R_rows"].max()) + 1 if level["R_rows"].size else 0
+    return sp.csr_matrix((level["R_w"], (level["R_rows"], level["R_cols"])), shape=(n_rows, n_cols))

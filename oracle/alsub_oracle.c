@@ -1,0 +1,717 @@
+/*
+ * AlSub oracle -- TEST INFRASTRUCTURE ONLY.
+ *
+ * A plain, serial, FP64 half-edge subdivider that the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg use to check and time the CUDA path. Nothing in the product
+ * library links, loads or calls it, and it shares no code, header or table with the CUDA path.
+ *
+ * It applies one level at a time with the CLASSICAL local rules (not the sparse-matrix form the
+ * GPU uses), so that agreement between the two checks the paper's equivalence of both forms:
+ *   Catmull-Clark  Sec. 3.1: face point (Eq. 1), edge point (Eq. 2), vertex update
+ *                  (Eq. pos_update), topology refinement (step 4; the refined matrix layout of
+ *                  Sec. 3.2 "Topology refinement": old vertices, then face point |v|+r, then edge
+ *                  point |v|+|f|+e).
+ *   Loop           Appendix B: edge point, smoothing Eq. loop_smooth with beta_n, 1-to-4 split.
+ *   sqrt(3)        Appendix A: face point, smoothing Eq. sqrt2 with alpha_n (Eq. alpha),
+ *                  one child triangle per corner (p_k, f_{F(l,k)}, f_i).
+ *   Creases        Sec. 3.3: crease valency k (Eq. CC_crease_valency), vertex sharpness s
+ *                  (Eq. CC_crease_vsharpness), Chaikin-style inheritance (Eqs. after Sec. 3.3's
+ *                  two-step description). The vertex/edge crease rules themselves are delegated
+ *                  by the paper to DeRose et al. 1998; the reading used here is:
+ *                    edge point: sigma >= 1 -> midpoint; 0 < sigma < 1 -> (1-sigma) smooth +
+ *                    sigma midpoint; vertex: k < 2 smooth; k == 2 sharp = (p_a + 6 p + p_b)/8;
+ *                    k >= 3 sharp = p; result w sharp + (1-w) smooth, w = min(s, 1).
+ *                  Chaikin neighbour of a crease end v: the other crease's sharpness when k(v)
+ *                  == 2 and it is finite, else the crease's own sharpness. The inherited value
+ *                  is evaluated in FP32, in the fixed order t = 3*s; u = s_o + t; w = u * 0.25;
+ *                  y = w - 1; max(y, 0) (compile with -ffp-contract=off).
+ *                  sqrt(3) ignores sharpness (the paper gives it no crease treatment).
+ * Edge numbering follows Sec. 3.2: edges are numbered in the order of the non-zeros of the upper
+ * triangle of E, i.e. lexicographically by (min vertex, max vertex).
+ * Child faces: face r with corners j = 0..c-1 is replaced by its children in corner order; the
+ * child of corner j starts at the parent vertex v_j.
+ *
+ * Parity of the crease rule reading has no printed example in the paper: it is pinned only by its
+ * limit cases (sigma = 0 smooth, sigma = inf cubic B-spline curve, sigma = 1 one sharp step).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+enum { OR_OK = 0, OR_ERR_ARG = 1, OR_ERR_NONMANIFOLD = 2, OR_ERR_BOUNDARY = 3, OR_ERR_OOM = 4,
+       OR_ERR_CREASE = 5 };
+enum { OR_CC = 0, OR_LOOP = 1, OR_SQRT3 = 2 };
+
+typedef struct {
+    int V, F, nnz, E, K;
+    int *off;          /* F+1 */
+    int *fv;           /* nnz */
+    double *P;         /* 3V */
+    int *cv;           /* 2K crease endpoints */
+    float *cs;         /* K crease sharpness */
+    /* operator R_l mapping this level to the next (COO), if requested */
+    long long rnnz;
+    int *rr, *rc;
+    double *rw;
+} olevel;
+
+typedef struct {
+    int levels;
+    olevel *L;         /* levels + 1 entries; entries not kept are left empty */
+} oresult;
+
+/* ---------------------------------------------------------------- half-edge view of a level */
+
+typedef struct {
+    int V, F, nnz;
+    const int *off, *fv;
+    int *cf;           /* corner -> face */
+    int *nx, *pv;      /* next / previous corner in the face */
+    int *tw;           /* twin corner (the corner running the other way along the edge) */
+    int *vo, *vb;      /* outgoing corners bucketed by start vertex: vb[vo[v] .. vo[v+1]) */
+    int *eid;          /* edge id per corner (lexicographic numbering) */
+    int E;
+    int *ea, *eb;      /* edge endpoints, ea < eb */
+    int *eo;           /* a corner of each edge */
+} hedge;
+
+static void hedge_free(hedge *h) {
+    free(h->cf); free(h->nx); free(h->pv); free(h->tw); free(h->vo); free(h->vb);
+    free(h->eid); free(h->ea); free(h->eb); free(h->eo);
+    memset(h, 0, sizeof(*h));
+}
+
+typedef struct { int a, b, c; } ekey;
+
+static int ekey_cmp(const void *x, const void *y) {
+    const ekey *p = (const ekey *)x, *q = (const ekey *)y;
+    if (p->a != q->a) return p->a < q->a ? -1 : 1;
+    if (p->b != q->b) return p->b < q->b ? -1 : 1;
+    return 0;
+}
+
+/* Build corners, twins and the lexicographic edge numbering. Closed 2-manifolds only. */
+static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv) {
+    memset(h, 0, sizeof(*h));
+    h->V = V; h->F = F; h->nnz = off[F]; h->off = off; h->fv = fv;
+    int n = h->nnz;
+    h->cf = malloc(sizeof(int) * (size_t)n); h->nx = malloc(sizeof(int) * (size_t)n);
+    h->pv = malloc(sizeof(int) * (size_t)n); h->tw = malloc(sizeof(int) * (size_t)n);
+    h->vo = calloc((size_t)V + 1, sizeof(int)); h->vb = malloc(sizeof(int) * (size_t)n);
+    h->eid = malloc(sizeof(int) * (size_t)n);
+    if (!h->cf || !h->nx || !h->pv || !h->tw || !h->vo || !h->vb || !h->eid) return OR_ERR_OOM;
+    for (int r = 0; r < F; r++) {
+        int s = off[r], c = off[r + 1] - off[r];
+        if (c < 3) return OR_ERR_ARG;
+        for (int j = 0; j < c; j++) {
+            h->cf[s + j] = r;
+            h->nx[s + j] = s + (j + 1) % c;
+            h->pv[s + j] = s + (j + c - 1) % c;
+        }
+    }
+    for (int i = 0; i < n; i++) {
+        if (fv[i] < 0 || fv[i] >= V) return OR_ERR_ARG;
+        h->vo[fv[i] + 1]++;
+    }
+    for (int v = 0; v < V; v++) {
+        if (h->vo[v + 1] == 0) return OR_ERR_ARG;    /* isolated vertex */
+        h->vo[v + 1] += h->vo[v];
+    }
+    int *fill = calloc((size_t)V, sizeof(int));
+    if (!fill) return OR_ERR_OOM;
+    for (int i = 0; i < n; i++) h->vb[h->vo[fv[i]] + fill[fv[i]]++] = i;  /* ascending corners */
+    free(fill);
+    /* twin of a->b: the unique corner b->a */
+    for (int i = 0; i < n; i++) {
+        int a = fv[i], b = fv[h->nx[i]];
+        if (a == b) return OR_ERR_ARG;
+        int found = -1, cnt = 0;
+        for (int q = h->vo[b]; q < h->vo[b + 1]; q++) {
+            int d = h->vb[q];
+            if (fv[h->nx[d]] == a) { found = d; cnt++; }
+        }
+        if (cnt == 0) return OR_ERR_BOUNDARY;
+        if (cnt > 1) return OR_ERR_NONMANIFOLD;
+        h->tw[i] = found;
+        for (int q = h->vo[a]; q < h->vo[a + 1]; q++) {   /* duplicate directed edge */
+            int d = h->vb[q];
+            if (d != i && fv[h->nx[d]] == b) return OR_ERR_NONMANIFOLD;
+        }
+    }
+    /* every vertex: its outgoing corners form a single fan (one cycle under tw(pv(.))) */
+    for (int v = 0; v < V; v++) {
+        int start = h->vb[h->vo[v]], x = start, steps = 0, deg = h->vo[v + 1] - h->vo[v];
+        do { x = h->tw[h->pv[x]]; steps++; } while (x != start && steps <= deg);
+        if (steps != deg) return OR_ERR_NONMANIFOLD;
+    }
+    /* edges: one per corner pair; number them lexicographically by (min, max) */
+    if (n % 2) return OR_ERR_BOUNDARY;
+    int E = n / 2;
+    ekey *keys = malloc(sizeof(ekey) * (size_t)E);
+    if (!keys) return OR_ERR_OOM;
+    int k = 0;
+    for (int i = 0; i < n; i++) {
+        int a = fv[i], b = fv[h->nx[i]];
+        if (a < b) { keys[k].a = a; keys[k].b = b; keys[k].c = i; k++; }
+    }
+    if (k != E) { free(keys); return OR_ERR_NONMANIFOLD; }
+    qsort(keys, (size_t)E, sizeof(ekey), ekey_cmp);
+    h->E = E;
+    h->ea = malloc(sizeof(int) * (size_t)E); h->eb = malloc(sizeof(int) * (size_t)E);
+    h->eo = malloc(sizeof(int) * (size_t)E);
+    if (!h->ea || !h->eb || !h->eo) { free(keys); return OR_ERR_OOM; }
+    for (int e = 0; e < E; e++) {
+        h->ea[e] = keys[e].a; h->eb[e] = keys[e].b; h->eo[e] = keys[e].c;
+        h->eid[keys[e].c] = e;
+        h->eid[h->tw[keys[e].c]] = e;
+    }
+    free(keys);
+    return OR_OK;
+}
+
+/* edge id of (a, b) or -1 */
+static int hedge_find_edge(const hedge *h, int a, int b) {
+    if (a < 0 || b < 0 || a >= h->V || b >= h->V) return -1;
+    for (int q = h->vo[a]; q < h->vo[a + 1]; q++) {
+        int d = h->vb[q];
+        if (h->fv[h->nx[d]] == b) return h->eid[d];
+    }
+    return -1;
+}
+
+/* ---------------------------------------------------------------- crease bookkeeping */
+
+typedef struct {
+    float *es;         /* sharpness per edge (0 = smooth) */
+    int *k;            /* crease valency per vertex: incident edges with sigma > 0 */
+    double *S;         /* sum of incident crease sharpness */
+    int *n1, *n2;      /* the first two crease neighbours (for k == 2) */
+    float *s1, *s2;    /* their crease sharpness */
+} creases;
+
+static void creases_free(creases *c) {
+    free(c->es); free(c->k); free(c->S); free(c->n1); free(c->n2); free(c->s1); free(c->s2);
+    memset(c, 0, sizeof(*c));
+}
+
+static int creases_build(creases *c, const hedge *h, int K, const int *cv, const float *cs) {
+    memset(c, 0, sizeof(*c));
+    c->es = calloc((size_t)h->E, sizeof(float));
+    c->k = calloc((size_t)h->V, sizeof(int));
+    c->S = calloc((size_t)h->V, sizeof(double));
+    c->n1 = malloc(sizeof(int) * (size_t)h->V); c->n2 = malloc(sizeof(int) * (size_t)h->V);
+    c->s1 = calloc((size_t)h->V, sizeof(float)); c->s2 = calloc((size_t)h->V, sizeof(float));
+    if (!c->es || !c->k || !c->S || !c->n1 || !c->n2 || !c->s1 || !c->s2) return OR_ERR_OOM;
+    for (int i = 0; i < K; i++) {
+        float s = cs[i];
+        if (!(s >= 0.0f)) return OR_ERR_CREASE;        /* negative or NaN */
+        int e = hedge_find_edge(h, cv[2 * i], cv[2 * i + 1]);
+        if (e < 0) return OR_ERR_CREASE;
+        if (c->es[e] != 0.0f) return OR_ERR_CREASE;    /* tagged twice */
+        c->es[e] = s;
+    }
+    for (int v = 0; v < h->V; v++) { c->n1[v] = -1; c->n2[v] = -1; }
+    for (int e = 0; e < h->E; e++) {
+        float s = c->es[e];
+        if (s > 0.0f) {
+            int ends[2] = {h->ea[e], h->eb[e]};
+            for (int t = 0; t < 2; t++) {
+                int v = ends[t], o = ends[1 - t];
+                if (c->k[v] == 0) { c->n1[v] = o; c->s1[v] = s; }
+                else if (c->k[v] == 1) { c->n2[v] = o; c->s2[v] = s; }
+                c->k[v]++;
+                c->S[v] += (double)s;
+            }
+        }
+    }
+    return OR_OK;
+}
+
+/* Chaikin-style sharpness of the child half of crease (v, o) at end v, FP32 in a fixed order. */
+static float chaikin_child(const creases *c, int v, int o, float s) {
+    float so = s;
+    if (c->k[v] == 2) {
+        float other = (c->n1[v] == o) ? c->s2[v] : c->s1[v];
+        if (isfinite(other)) so = other;
+    }
+    volatile float t = 3.0f * s;
+    volatile float u = so + t;
+    volatile float w = u * 0.25f;
+    volatile float y = w - 1.0f;
+    return y > 0.0f ? y : 0.0f;
+}
+
+/* crease-rule vertex: w sharp + (1-w) smooth for k >= 2 */
+static void crease_vertex(const creases *c, const double *P, int v, double *out /* smooth in */) {
+    int k = c->k[v];
+    if (k < 2) return;
+    double s = c->S[v] / (double)k;
+    double w = s < 1.0 ? s : 1.0;
+    double sharp[3];
+    for (int d = 0; d < 3; d++) {
+        if (k == 2) sharp[d] = (P[3 * c->n1[v] + d] + 6.0 * P[3 * v + d] + P[3 * c->n2[v] + d]) / 8.0;
+        else sharp[d] = P[3 * v + d];
+        out[d] = w * sharp[d] + (1.0 - w) * out[d];
+    }
+}
+
+static void crease_edge(double sigma, const double *pa, const double *pb, double *out) {
+    if (!(sigma > 0.0)) return;
+    for (int d = 0; d < 3; d++) {
+        double mid = 0.5 * (pa[d] + pb[d]);
+        out[d] = sigma >= 1.0 ? mid : (1.0 - sigma) * out[d] + sigma * mid;
+    }
+}
+
+/* ---------------------------------------------------------------- sparse row accumulator */
+
+typedef struct { int n, cap; int *c; double *w; } row;
+
+static int row_add(row *r, int col, double w) {
+    for (int i = 0; i < r->n; i++) if (r->c[i] == col) { r->w[i] += w; return OR_OK; }
+    if (r->n == r->cap) {
+        int cap = r->cap ? 2 * r->cap : 64;
+        int *c = realloc(r->c, sizeof(int) * (size_t)cap);
+        if (!c) return OR_ERR_OOM;
+        r->c = c;
+        double *w2 = realloc(r->w, sizeof(double) * (size_t)cap);
+        if (!w2) return OR_ERR_OOM;
+        r->w = w2;
+        r->cap = cap;
+    }
+    r->c[r->n] = col; r->w[r->n] = w; r->n++;
+    return OR_OK;
+}
+
+typedef struct { long long n, cap; int *r, *c; double *w; } coo;
+
+static int coo_push_row(coo *m, int rowi, row *r) {
+    /* rows are emitted with columns ascending; exact zeros are dropped */
+    for (int i = 1; i < r->n; i++) {
+        int c = r->c[i]; double w = r->w[i]; int j = i - 1;
+        while (j >= 0 && r->c[j] > c) { r->c[j + 1] = r->c[j]; r->w[j + 1] = r->w[j]; j--; }
+        r->c[j + 1] = c; r->w[j + 1] = w;
+    }
+    for (int i = 0; i < r->n; i++) {
+        if (r->w[i] == 0.0) continue;
+        if (m->n == m->cap) {
+            long long cap = m->cap ? 2 * m->cap : 1024;
+            int *a = realloc(m->r, sizeof(int) * (size_t)cap); if (!a) return OR_ERR_OOM; m->r = a;
+            int *b = realloc(m->c, sizeof(int) * (size_t)cap); if (!b) return OR_ERR_OOM; m->c = b;
+            double *w = realloc(m->w, sizeof(double) * (size_t)cap); if (!w) return OR_ERR_OOM; m->w = w;
+            m->cap = cap;
+        }
+        m->r[m->n] = rowi; m->c[m->n] = r->c[i]; m->w[m->n] = r->w[i]; m->n++;
+    }
+    r->n = 0;
+    return OR_OK;
+}
+
+/* row += w * (crease-rule vertex row of v), applied as w_s * sharp + (1 - w_s) * smooth */
+static int crease_vertex_row(const creases *c, int v, row *smooth) {
+    int k = c->k[v];
+    if (k < 2) return OR_OK;
+    double s = c->S[v] / (double)k;
+    double w = s < 1.0 ? s : 1.0;
+    for (int i = 0; i < smooth->n; i++) smooth->w[i] *= (1.0 - w);
+    int st;
+    if (k == 2) {
+        if ((st = row_add(smooth, c->n1[v], w / 8.0))) return st;
+        if ((st = row_add(smooth, v, w * 6.0 / 8.0))) return st;
+        if ((st = row_add(smooth, c->n2[v], w / 8.0))) return st;
+    } else if ((st = row_add(smooth, v, w))) return st;
+    return OR_OK;
+}
+
+static int crease_edge_row(double sigma, int a, int b, row *smooth) {
+    if (!(sigma > 0.0)) return OR_OK;
+    double w = sigma >= 1.0 ? 1.0 : sigma;
+    for (int i = 0; i < smooth->n; i++) smooth->w[i] *= (1.0 - w);
+    int st;
+    if ((st = row_add(smooth, a, 0.5 * w))) return st;
+    return row_add(smooth, b, 0.5 * w);
+}
+
+/* ---------------------------------------------------------------- one level of each scheme */
+
+typedef struct {
+    int V, F, nnz, K;
+    int *off, *fv, *cv;
+    float *cs;
+    double *P;
+} onext;
+
+static int alloc_next(onext *o, int V, int F, int nnz, int Kmax) {
+    o->V = V; o->F = F; o->nnz = nnz; o->K = 0;
+    o->off = malloc(sizeof(int) * ((size_t)F + 1));
+    o->fv = malloc(sizeof(int) * (size_t)nnz);
+    o->P = malloc(sizeof(double) * 3 * (size_t)V);
+    o->cv = malloc(sizeof(int) * 2 * ((size_t)Kmax + 1));
+    o->cs = malloc(sizeof(float) * ((size_t)Kmax + 1));
+    return (o->off && o->fv && o->P && o->cv && o->cs) ? OR_OK : OR_ERR_OOM;
+}
+
+static void push_crease(onext *o, int a, int b, float s) {
+    if (s > 0.0f) { o->cv[2 * o->K] = a; o->cv[2 * o->K + 1] = b; o->cs[o->K] = s; o->K++; }
+}
+
+/* Catmull-Clark, Sec. 3.1 classical rules. */
+static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o, coo *R) {
+    int V = h->V, F = h->F, E = h->E, n = h->nnz;
+    int st = alloc_next(o, V + F + E, n, 4 * n, 2 * E);
+    if (st) return st;
+    double *Pn = o->P;
+    double *fp = Pn + 3 * (size_t)V;           /* face points: |v| + r */
+    double *ep = Pn + 3 * ((size_t)V + F);     /* edge points: |v| + |f| + e */
+    /* 1. face point: barycenter of the polygon (Eq. 1) */
+    for (int r = 0; r < F; r++) {
+        int s = h->off[r], c = h->off[r + 1] - s;
+        for (int d = 0; d < 3; d++) {
+            double acc = 0.0;
+            for (int j = 0; j < c; j++) acc += P[3 * h->fv[s + j] + d];
+            fp[3 * r + d] = acc / c;
+        }
+    }
+    /* 2. edge point: (p_k + p_l + f_r + f_s) / 4 (Eq. 2), then the crease rule */
+    for (int e = 0; e < E; e++) {
+        int c0 = h->eo[e], c1 = h->tw[c0];
+        int a = h->ea[e], b = h->eb[e], r = h->cf[c0], s = h->cf[c1];
+        for (int d = 0; d < 3; d++)
+            ep[3 * e + d] = 0.25 * (P[3 * a + d] + P[3 * b + d] + fp[3 * r + d] + fp[3 * s + d]);
+        if (cr) crease_edge((double)cr->es[e], P + 3 * a, P + 3 * b, ep + 3 * e);
+    }
+    /* 3. vertex update (Eq. pos_update):
+     *    S(p) = 1/n ((n-3) p + 1/n sum f_j + 2/n sum (p + p_j)/2), then the crease rule */
+    for (int v = 0; v < V; v++) {
+        int nv = h->vo[v + 1] - h->vo[v];
+        double sf[3] = {0, 0, 0}, sm[3] = {0, 0, 0};
+        for (int q = h->vo[v]; q < h->vo[v + 1]; q++) {
+            int x = h->vb[q];                           /* corner v -> p_j in face f_j */
+            int pj = h->fv[h->nx[x]], fj = h->cf[x];
+            for (int d = 0; d < 3; d++) {
+                sf[d] += fp[3 * fj + d];
+                sm[d] += 0.5 * (P[3 * v + d] + P[3 * pj + d]);
+            }
+        }
+        for (int d = 0; d < 3; d++)
+            Pn[3 * v + d] = ((nv - 3) * P[3 * v + d] + sf[d] / nv + 2.0 * sm[d] / nv) / nv;
+        if (cr) crease_vertex(cr, P, v, Pn + 3 * v);
+    }
+    /* 4. topology: face r -> c_r quads [v_j, e(j), f_r, e(j-1)] */
+    for (int r = 0; r <= n; r++) o->off[r] = 4 * r;
+    for (int x = 0; x < n; x++) {
+        int r = h->cf[x];
+        o->fv[4 * x + 0] = h->fv[x];
+        o->fv[4 * x + 1] = V + F + h->eid[x];
+        o->fv[4 * x + 2] = V + r;
+        o->fv[4 * x + 3] = V + F + h->eid[h->pv[x]];
+    }
+    /* creases: both halves inherit a Chaikin-style sharpness */
+    if (cr) {
+        for (int e = 0; e < E; e++) {
+            float s = cr->es[e];
+            if (!(s > 0.0f)) continue;
+            int a = h->ea[e], b = h->eb[e];
+            push_crease(o, a, V + F + e, chaikin_child(cr, a, b, s));
+            push_crease(o, V + F + e, b, chaikin_child(cr, b, a, s));
+        }
+    }
+    /* operator rows, same rules as weights */
+    if (R) {
+        row rw = {0, 0, NULL, NULL};
+        for (int v = 0; v < V && !st; v++) {
+            int nv = h->vo[v + 1] - h->vo[v];
+            double inv2 = 1.0 / ((double)nv * nv);
+            st = row_add(&rw, v, (nv - 3.0) / nv + 1.0 / nv);        /* (n-3)/n p + (n/n^2) p */
+            for (int q = h->vo[v]; q < h->vo[v + 1] && !st; q++) {
+                int x = h->vb[q], pj = h->fv[h->nx[x]], fj = h->cf[x];
+                int s0 = h->off[fj], c = h->off[fj + 1] - s0;
+                st = row_add(&rw, pj, inv2);
+                for (int j = 0; j < c && !st; j++) st = row_add(&rw, h->fv[s0 + j], inv2 / c);
+            }
+            if (!st && cr) st = crease_vertex_row(cr, v, &rw);
+            if (!st) st = coo_push_row(R, v, &rw);
+        }
+        for (int r = 0; r < F && !st; r++) {
+            int s0 = h->off[r], c = h->off[r + 1] - s0;
+            for (int j = 0; j < c && !st; j++) st = row_add(&rw, h->fv[s0 + j], 1.0 / c);
+            if (!st) st = coo_push_row(R, V + r, &rw);
+        }
+        for (int e = 0; e < E && !st; e++) {
+            int c0 = h->eo[e], c1 = h->tw[c0];
+            int fs[2] = {h->cf[c0], h->cf[c1]};
+            st = row_add(&rw, h->ea[e], 0.25);
+            if (!st) st = row_add(&rw, h->eb[e], 0.25);
+            for (int t = 0; t < 2 && !st; t++) {
+                int s0 = h->off[fs[t]], c = h->off[fs[t] + 1] - s0;
+                for (int j = 0; j < c && !st; j++) st = row_add(&rw, h->fv[s0 + j], 0.25 / c);
+            }
+            if (!st && cr) st = crease_edge_row((double)cr->es[e], h->ea[e], h->eb[e], &rw);
+            if (!st) st = coo_push_row(R, V + F + e, &rw);
+        }
+        free(rw.c); free(rw.w);
+    }
+    return st;
+}
+
+static double loop_beta(int n) {
+    double t = 0.375 + 0.25 * cos(2.0 * M_PI / n);
+    return (0.625 - t * t) / n;
+}
+
+/* Loop, Appendix B. */
+static int loop_level(const hedge *h, const creases *cr, const double *P, onext *o, coo *R) {
+    int V = h->V, F = h->F, E = h->E;
+    int st = alloc_next(o, V + E, 4 * F, 12 * F, 2 * E);
+    if (st) return st;
+    double *Pn = o->P, *ep = Pn + 3 * (size_t)V;
+    /* edge point: 3/8 (p_i + p_j) + 1/8 (p_k + p_l), k, l opposite (G(i,j), G(j,i)) */
+    for (int e = 0; e < E; e++) {
+        int c0 = h->eo[e], c1 = h->tw[c0];
+        int a = h->ea[e], b = h->eb[e];
+        int k = h->fv[h->pv[c0]], l = h->fv[h->pv[c1]];
+        for (int d = 0; d < 3; d++)
+            ep[3 * e + d] = 0.375 * (P[3 * a + d] + P[3 * b + d]) + 0.125 * (P[3 * k + d] + P[3 * l + d]);
+        if (cr) crease_edge((double)cr->es[e], P + 3 * a, P + 3 * b, ep + 3 * e);
+    }
+    /* vertex: (1 - n beta) p + beta sum p_j (Eq. loop_smooth) */
+    for (int v = 0; v < V; v++) {
+        int nv = h->vo[v + 1] - h->vo[v];
+        double beta = loop_beta(nv), sm[3] = {0, 0, 0};
+        for (int q = h->vo[v]; q < h->vo[v + 1]; q++) {
+            int pj = h->fv[h->nx[h->vb[q]]];
+            for (int d = 0; d < 3; d++) sm[d] += P[3 * pj + d];
+        }
+        for (int d = 0; d < 3; d++) Pn[3 * v + d] = (1.0 - nv * beta) * P[3 * v + d] + beta * sm[d];
+        if (cr) crease_vertex(cr, P, v, Pn + 3 * v);
+    }
+    /* topology: triangle (p_k, p_l, p_m) -> three corner triangles and the centre one */
+    for (int r = 0; r <= 4 * F; r++) o->off[r] = 3 * r;
+    for (int r = 0; r < F; r++) {
+        int s = h->off[r];
+        int e0 = V + h->eid[s], e1 = V + h->eid[s + 1], e2 = V + h->eid[s + 2];
+        int v0 = h->fv[s], v1 = h->fv[s + 1], v2 = h->fv[s + 2];
+        int *t = o->fv + 12 * (size_t)r;
+        t[0] = v0; t[1] = e0; t[2] = e2;
+        t[3] = v1; t[4] = e1; t[5] = e0;
+        t[6] = v2; t[7] = e2; t[8] = e1;
+        t[9] = e0; t[10] = e1; t[11] = e2;
+    }
+    if (cr) {
+        for (int e = 0; e < E; e++) {
+            float s = cr->es[e];
+            if (!(s > 0.0f)) continue;
+            int a = h->ea[e], b = h->eb[e];
+            push_crease(o, a, V + e, chaikin_child(cr, a, b, s));
+            push_crease(o, V + e, b, chaikin_child(cr, b, a, s));
+        }
+    }
+    if (R) {
+        row rw = {0, 0, NULL, NULL};
+        for (int v = 0; v < V && !st; v++) {
+            int nv = h->vo[v + 1] - h->vo[v];
+            double beta = loop_beta(nv);
+            st = row_add(&rw, v, 1.0 - nv * beta);
+            for (int q = h->vo[v]; q < h->vo[v + 1] && !st; q++)
+                st = row_add(&rw, h->fv[h->nx[h->vb[q]]], beta);
+            if (!st && cr) st = crease_vertex_row(cr, v, &rw);
+            if (!st) st = coo_push_row(R, v, &rw);
+        }
+        for (int e = 0; e < E && !st; e++) {
+            int c0 = h->eo[e], c1 = h->tw[c0];
+            st = row_add(&rw, h->ea[e], 0.375);
+            if (!st) st = row_add(&rw, h->eb[e], 0.375);
+            if (!st) st = row_add(&rw, h->fv[h->pv[c0]], 0.125);
+            if (!st) st = row_add(&rw, h->fv[h->pv[c1]], 0.125);
+            if (!st && cr) st = crease_edge_row((double)cr->es[e], h->ea[e], h->eb[e], &rw);
+            if (!st) st = coo_push_row(R, V + e, &rw);
+        }
+        free(rw.c); free(rw.w);
+    }
+    return st;
+}
+
+static double sqrt3_alpha(int n) { return (4.0 - 2.0 * cos(2.0 * M_PI / n)) / 9.0; }
+
+/* sqrt(3), Appendix A (no creases). */
+static int sqrt3_level(const hedge *h, const double *P, onext *o, coo *R) {
+    int V = h->V, F = h->F;
+    int st = alloc_next(o, V + F, 3 * F, 9 * F, 0);
+    if (st) return st;
+    double *Pn = o->P, *fp = Pn + 3 * (size_t)V;
+    for (int r = 0; r < F; r++) {
+        int s = h->off[r];
+        for (int d = 0; d < 3; d++)
+            fp[3 * r + d] = (P[3 * h->fv[s] + d] + P[3 * h->fv[s + 1] + d] + P[3 * h->fv[s + 2] + d]) / 3.0;
+    }
+    /* S(p) = (1 - alpha) p + alpha / n sum p_j (Eq. sqrt2, alpha from Eq. alpha) */
+    for (int v = 0; v < V; v++) {
+        int nv = h->vo[v + 1] - h->vo[v];
+        double al = sqrt3_alpha(nv), sm[3] = {0, 0, 0};
+        for (int q = h->vo[v]; q < h->vo[v + 1]; q++) {
+            int pj = h->fv[h->nx[h->vb[q]]];
+            for (int d = 0; d < 3; d++) sm[d] += P[3 * pj + d];
+        }
+        for (int d = 0; d < 3; d++) Pn[3 * v + d] = (1.0 - al) * P[3 * v + d] + al / nv * sm[d];
+    }
+    /* corner k of triangle i = (k, l, m) -> (p_k, f_{F(l,k)}, f_i) */
+    for (int r = 0; r <= 3 * F; r++) o->off[r] = 3 * r;
+    for (int x = 0; x < h->nnz; x++) {
+        o->fv[3 * x + 0] = h->fv[x];
+        o->fv[3 * x + 1] = V + h->cf[h->tw[x]];
+        o->fv[3 * x + 2] = V + h->cf[x];
+    }
+    if (R) {
+        row rw = {0, 0, NULL, NULL};
+        for (int v = 0; v < V && !st; v++) {
+            int nv = h->vo[v + 1] - h->vo[v];
+            double al = sqrt3_alpha(nv);
+            st = row_add(&rw, v, 1.0 - al);
+            for (int q = h->vo[v]; q < h->vo[v + 1] && !st; q++)
+                st = row_add(&rw, h->fv[h->nx[h->vb[q]]], al / nv);
+            if (!st) st = coo_push_row(R, v, &rw);
+        }
+        for (int r = 0; r < F && !st; r++) {
+            int s = h->off[r];
+            for (int j = 0; j < 3 && !st; j++) st = row_add(&rw, h->fv[s + j], 1.0 / 3.0);
+            if (!st) st = coo_push_row(R, V + r, &rw);
+        }
+        free(rw.c); free(rw.w);
+    }
+    return st;
+}
+
+/* ---------------------------------------------------------------- driver and accessors */
+
+static void level_free(olevel *l) {
+    free(l->off); free(l->fv); free(l->P); free(l->cv); free(l->cs);
+    free(l->rr); free(l->rc); free(l->rw);
+    memset(l, 0, sizeof(*l));
+}
+
+void or_free(oresult *r) {
+    if (!r) return;
+    for (int l = 0; l <= r->levels; l++) level_free(&r->L[l]);
+    free(r->L);
+    free(r);
+}
+
+/*
+ * Refine `levels` times. keep_all = 0 keeps only the last level; want_operator = 1 stores the
+ * operator R_l of every kept level l < levels (COO, FP64).
+ */
+int or_run(int scheme, int levels, int keep_all, int want_operator,
+           int V, int F, const int *off, const int *fv, const double *P0,
+           int K, const int *cv, const float *cs, oresult **out) {
+    *out = NULL;
+    if (scheme < 0 || scheme > 2 || levels < 0 || V <= 0 || F <= 0 || K < 0) return OR_ERR_ARG;
+    if (off[0] != 0) return OR_ERR_ARG;
+    for (int r = 0; r < F; r++) {
+        int c = off[r + 1] - off[r];
+        if (c < 3 || (scheme != OR_CC && c != 3)) return OR_ERR_ARG;
+    }
+    oresult *res = calloc(1, sizeof(oresult));
+    if (!res) return OR_ERR_OOM;
+    res->levels = levels;
+    res->L = calloc((size_t)levels + 1, sizeof(olevel));
+    if (!res->L) { free(res); return OR_ERR_OOM; }
+    /* level 0: copy the input; sigma = 0 creases carry nothing and are dropped */
+    olevel *cur = &res->L[0];
+    cur->V = V; cur->F = F; cur->nnz = off[F];
+    cur->off = malloc(sizeof(int) * ((size_t)F + 1)); cur->fv = malloc(sizeof(int) * (size_t)off[F]);
+    cur->P = malloc(sizeof(double) * 3 * (size_t)V);
+    cur->cv = malloc(sizeof(int) * 2 * ((size_t)K + 1)); cur->cs = malloc(sizeof(float) * ((size_t)K + 1));
+    if (!cur->off || !cur->fv || !cur->P || !cur->cv || !cur->cs) { or_free(res); return OR_ERR_OOM; }
+    memcpy(cur->off, off, sizeof(int) * ((size_t)F + 1));
+    memcpy(cur->fv, fv, sizeof(int) * (size_t)off[F]);
+    memcpy(cur->P, P0, sizeof(double) * 3 * (size_t)V);
+    cur->K = 0;
+    if (scheme != OR_SQRT3) {
+        for (int i = 0; i < K; i++) {
+            if (!(cs[i] >= 0.0f)) { or_free(res); return OR_ERR_CREASE; }
+            if (cs[i] > 0.0f) {
+                cur->cv[2 * cur->K] = cv[2 * i]; cur->cv[2 * cur->K + 1] = cv[2 * i + 1];
+                cur->cs[cur->K] = cs[i]; cur->K++;
+            }
+        }
+    }
+    int st = OR_OK;
+    int last = 0;
+    for (int l = 0; l <= levels && !st; l++) {
+        olevel *L = &res->L[last];
+        hedge h;
+        st = hedge_build(&h, L->V, L->F, L->off, L->fv);
+        if (st) { hedge_free(&h); break; }
+        L->E = h.E;
+        creases cr;
+        memset(&cr, 0, sizeof(cr));
+        int use_cr = (scheme != OR_SQRT3) && L->K > 0;
+        if (use_cr) st = creases_build(&cr, &h, L->K, L->cv, L->cs);
+        if (st || l == levels) { creases_free(&cr); hedge_free(&h); break; }
+        onext o;
+        memset(&o, 0, sizeof(o));
+        coo R = {0, 0, NULL, NULL, NULL};
+        coo *Rp = want_operator ? &R : NULL;
+        if (scheme == OR_CC) st = cc_level(&h, use_cr ? &cr : NULL, L->P, &o, Rp);
+        else if (scheme == OR_LOOP) st = loop_level(&h, use_cr ? &cr : NULL, L->P, &o, Rp);
+        else st = sqrt3_level(&h, L->P, &o, Rp);
+        creases_free(&cr);
+        hedge_free(&h);
+        if (Rp) { L->rnnz = R.n; L->rr = R.r; L->rc = R.c; L->rw = R.w; }
+        olevel *N = &res->L[l + 1];
+        N->V = o.V; N->F = o.F; N->nnz = o.nnz; N->K = o.K;
+        N->off = o.off; N->fv = o.fv; N->P = o.P; N->cv = o.cv; N->cs = o.cs;
+        if (st) break;
+        if (!keep_all) level_free(L);
+        last = l + 1;
+    }
+    if (st) { or_free(res); return st; }
+    *out = res;
+    return OR_OK;
+}
+
+static const olevel *lev(const oresult *r, int l) {
+    if (!r || l < 0 || l > r->levels || !r->L[l].off) return NULL;
+    return &r->L[l];
+}
+
+/* V, F, nnz, E, K, rnnz of a kept level */
+int or_counts(const oresult *r, int l, long long *outv) {
+    const olevel *L = lev(r, l);
+    if (!L) return OR_ERR_ARG;
+    outv[0] = L->V; outv[1] = L->F; outv[2] = L->nnz; outv[3] = L->E; outv[4] = L->K; outv[5] = L->rnnz;
+    return OR_OK;
+}
+
+int or_faces(const oresult *r, int l, int *off, int *fv) {
+    const olevel *L = lev(r, l);
+    if (!L) return OR_ERR_ARG;
+    memcpy(off, L->off, sizeof(int) * ((size_t)L->F + 1));
+    memcpy(fv, L->fv, sizeof(int) * (size_t)L->nnz);
+    return OR_OK;
+}
+
+int or_positions(const oresult *r, int l, double *P) {
+    const olevel *L = lev(r, l);
+    if (!L) return OR_ERR_ARG;
+    memcpy(P, L->P, sizeof(double) * 3 * (size_t)L->V);
+    return OR_OK;
+}
+
+int or_creases(const oresult *r, int l, int *cv, float *cs) {
+    const olevel *L = lev(r, l);
+    if (!L) return OR_ERR_ARG;
+    memcpy(cv, L->cv, sizeof(int) * 2 * (size_t)L->K);
+    memcpy(cs, L->cs, sizeof(float) * (size_t)L->K);
+    return OR_OK;
+}
+
+int or_operator(const oresult *r, int l, int *rows, int *cols, double *w) {
+    const olevel *L = lev(r, l);
+    if (!L || !L->rr) return OR_ERR_ARG;
+    memcpy(rows, L->rr, sizeof(int) * (size_t)L->rnnz);
+    memcpy(cols, L->rc, sizeof(int) * (size_t)L->rnnz);
+    memcpy(w, L->rw, sizeof(double) * (size_t)L->rnnz);
+    return OR_OK;
+}

@@ -1,0 +1,370 @@
+"""Pins for the CPU oracle: closed forms, printed-rule special cases, invariants, brute force.
+
+None of these re-types the oracle's own formulas: every expected value is either a hand-derived
+closed form from the paper's equations (stored under tests/golden/ with its derivation), a
+structural identity (counts, Euler characteristic), an invariant of linear subdivision (affine
+invariance, planarity, linear reproduction, partition of unity), or a reduction to a textbook
+routine (cubic B-spline curve subdivision along an infinitely sharp crease loop).
+"""
+import itertools
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_06047_gb300 import synth
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _frac(s):
+    return float(Fraction(s))
+
+
+def _read_golden(name):
+    counts, points, stencils = None, [], {}
+    for line in open(os.path.join(GOLD, name)):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        tok = line.split()
+        if tok[0] == "counts":
+            counts = tuple(int(t) for t in tok[1:])
+        elif tok[0] == "point":
+            points.append(tuple(_frac(t) for t in tok[1:4]))
+        elif tok[0] in ("vertex", "face", "edge"):
+            n, base = int(tok[1]), [_frac(t) for t in tok[2:5]]
+            cls = set()
+            for perm in itertools.permutations(base):
+                for signs in itertools.product((1, -1), repeat=3):
+                    cls.add(tuple(s * x for s, x in zip(signs, perm)))
+            assert len(cls) == n, (name, line, len(cls))
+            points.extend(sorted(cls))
+        else:
+            stencils[tok[0]] = sorted(_frac(t) for t in tok[1:])
+    return counts, points, stencils
+
+
+def _as_sorted(P):
+    P = np.round(np.asarray(P, dtype=np.float64), 12) + 0.0
+    return P[np.lexsort(P.T[::-1])]
+
+
+@pytest.mark.parametrize("mesh_fn,scheme,gold", [
+    (synth.cube, "cc", "cube_cc_level1.txt"),
+    (synth.octahedron, "loop", "octahedron_loop_level1.txt"),
+    (synth.octahedron, "sqrt3", "octahedron_sqrt3_level1.txt"),
+    (synth.tetrahedron, "sqrt3", "tetrahedron_sqrt3_level1.txt"),
+])
+def test_level1_closed_forms(mesh_fn, scheme, gold):
+    counts, pts, _ = _read_golden(gold)
+    L = oracle.subdivide(mesh_fn(), 1, scheme)
+    assert (L[1]["V"], L[1]["F"], L[1]["E"]) == counts
+    np.testing.assert_allclose(_as_sorted(L[1]["P"]), _as_sorted(pts), atol=1e-14)
+
+
+def _meshes():
+    return [
+        ("cc", synth.cube()),
+        ("cc", synth.pillow(6)),
+        ("cc", synth.torus_cc_mixed(12, 12, seed=11)),
+        ("loop", synth.octahedron()),
+        ("loop", synth.torus_tri(10, 10, seed=12)),
+        ("sqrt3", synth.tetrahedron()),
+        ("sqrt3", synth.torus_tri(10, 10, seed=13, creases=False)),
+    ]
+
+
+@pytest.mark.parametrize("scheme,mesh", _meshes())
+def test_counts_and_euler(scheme, mesh):
+    """Per-level counts (Sec. 3.1 step 4, Appendix A/B) and the Euler characteristic."""
+    levels = 3
+    out = oracle.subdivide(mesh, levels, scheme)
+    chi = out[0]["V"] - out[0]["E"] + out[0]["F"]
+    for l in range(levels):
+        a, b = out[l], out[l + 1]
+        if scheme == "cc":
+            exp = (a["V"] + a["F"] + a["E"], a["nnz"], 2 * a["E"] + a["nnz"])
+            assert np.all(np.diff(b["off"]) == 4)
+        elif scheme == "loop":
+            exp = (a["V"] + a["E"], 4 * a["F"], 2 * a["E"] + 3 * a["F"])
+        else:
+            exp = (a["V"] + a["F"], 3 * a["F"], 9 * a["F"] // 2)
+        assert (b["V"], b["F"], b["E"]) == exp
+        assert b["V"] - b["E"] + b["F"] == chi
+
+
+def _edge_endpoints_from_children(lvl0, lvl1, scheme):
+    """Endpoints of each level-0 edge id, read off the level-1 face table (layout of Sec. 3.2)."""
+    V, F = lvl0["V"], lvl0["F"]
+    off, fv = lvl0["off"], lvl0["fv"]
+    ends = {}
+    for r in range(F):
+        s, c = off[r], off[r + 1] - off[r]
+        for j in range(c):
+            a, b = fv[s + j], fv[s + (j + 1) % c]
+            if scheme == "cc":
+                e = lvl1["fv"][4 * (s + j) + 1] - V - F
+            else:   # loop: child j of triangle r holds e_j at position 1
+                e = lvl1["fv"][3 * (4 * r + j) + 1] - V
+            ends[int(e)] = (int(min(a, b)), int(max(a, b)), r)
+    return ends
+
+
+def _rows(lvl):
+    rows = {}
+    for r, c, w in zip(lvl["R_rows"], lvl["R_cols"], lvl["R_w"]):
+        rows.setdefault(int(r), {})[int(c)] = float(w)
+    return rows
+
+
+def test_regular_stencils_cc():
+    """Regular quad grid: B-spline masks of the gold file (Sec. 3.1, Eqs. 1, 2, pos_update)."""
+    _, _, st = _read_golden("regular_stencils.txt")
+    N = M = 8
+    m = synth.torus_cc_plain(N, M, jitter=0.0)
+    out = oracle.subdivide(m, 1, "cc", operator=True)
+    rows = _rows(out[0])
+    V, F = m["V"], m["F"]
+    for v in range(V):
+        i, j = divmod(v, M)
+        exp = {((i + di) % N) * M + (j + dj) % M: None for di in (-1, 0, 1) for dj in (-1, 0, 1)}
+        assert set(rows[v]) == set(exp)
+        assert sorted(rows[v].values()) == pytest.approx(st["cc_vertex"], abs=1e-15)
+        assert rows[v][v] == pytest.approx(36 / 64, abs=1e-15)
+        assert rows[v][((i + 1) % N) * M + j] == pytest.approx(6 / 64, abs=1e-15)
+        assert rows[v][((i + 1) % N) * M + (j + 1) % M] == pytest.approx(1 / 64, abs=1e-15)
+    for r in range(F):
+        assert sorted(rows[V + r].values()) == pytest.approx(st["cc_face"], abs=1e-15)
+        assert set(rows[V + r]) == set(m["fv"][4 * r:4 * r + 4].tolist())
+    ends = _edge_endpoints_from_children(out[0], out[1], "cc")
+    for e, (a, b, _) in ends.items():
+        row = rows[V + F + e]
+        assert sorted(row.values()) == pytest.approx(st["cc_edge"], abs=1e-15)
+        assert row[a] == pytest.approx(3 / 8) and row[b] == pytest.approx(3 / 8)
+
+
+def test_regular_stencils_loop_sqrt3():
+    """Regular triangulation (valence 6): beta_6 = 1/16 and alpha_6 = 1/3 (Appendices A, B)."""
+    _, _, st = _read_golden("regular_stencils.txt")
+    m = synth.torus_tri(8, 8, flip_frac=0.0, creases=False, jitter=0.0)
+    V, F = m["V"], m["F"]
+    out = oracle.subdivide(m, 1, "loop", operator=True)
+    rows = _rows(out[0])
+    for v in range(V):
+        assert sorted(rows[v].values()) == pytest.approx(st["loop_vertex"], abs=1e-15)
+        assert rows[v][v] == pytest.approx(10 / 16, abs=1e-15)
+    ends = _edge_endpoints_from_children(out[0], out[1], "loop")
+    for e, (a, b, r) in ends.items():
+        row = rows[V + e]
+        assert sorted(row.values()) == pytest.approx(st["loop_edge"], abs=1e-15)
+        assert row[a] == pytest.approx(3 / 8) and row[b] == pytest.approx(3 / 8)
+        third = set(m["fv"][3 * r:3 * r + 3].tolist()) - {a, b}
+        assert all(row[t] == pytest.approx(1 / 8) for t in third)
+    out = oracle.subdivide(m, 1, "sqrt3", operator=True)
+    rows = _rows(out[0])
+    for v in range(V):
+        assert sorted(rows[v].values()) == pytest.approx(st["sqrt3_vertex"], abs=1e-15)
+    for r in range(F):
+        assert sorted(rows[V + r].values()) == pytest.approx(st["sqrt3_face"], abs=1e-15)
+
+
+@pytest.mark.parametrize("scheme,mesh", _meshes())
+def test_partition_of_unity_and_positivity(scheme, mesh):
+    """Every refined vertex is an affine (convex) combination: rows sum to 1, weights >= 0."""
+    out = oracle.subdivide(mesh, 2, scheme, operator=True)
+    for l in range(2):
+        s = np.zeros(out[l + 1]["V"])
+        np.add.at(s, out[l]["R_rows"], out[l]["R_w"])
+        np.testing.assert_allclose(s, 1.0, atol=1e-13)
+        assert out[l]["R_w"].min() >= 0.0
+
+
+@pytest.mark.parametrize("scheme,mesh", _meshes())
+def test_affine_invariance(scheme, mesh):
+    rng = np.random.default_rng(5)
+    A, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    A = A * 1.7
+    b = np.array([0.3, -2.0, 5.0])
+    P = mesh["P"].astype(np.float64)
+    ref = oracle.subdivide(mesh, 2, scheme, P0=P)
+    mov = oracle.subdivide(mesh, 2, scheme, P0=P @ A.T + b)
+    np.testing.assert_allclose(mov[2]["P"], ref[2]["P"] @ A.T + b, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme,mesh", _meshes())
+def test_planarity_exact(scheme, mesh):
+    P = mesh["P"].astype(np.float64).copy()
+    P[:, 2] = 0.0
+    out = oracle.subdivide(mesh, 2, scheme, P0=P)
+    assert np.all(out[2]["P"][:, 2] == 0.0)
+
+
+@pytest.mark.parametrize("scheme", ["cc", "loop", "sqrt3"])
+def test_linear_reproduction_away_from_seam(scheme):
+    """On a regular periodic grid, positions linear in the grid indices are reproduced
+    wherever the stencil does not cross the seam."""
+    N = M = 12
+    if scheme == "cc":
+        m = synth.torus_cc_plain(N, M, jitter=0.0)
+    else:
+        m = synth.torus_tri(N, M, flip_frac=0.0, creases=False, jitter=0.0)
+    ij = np.array([divmod(v, M) for v in range(N * M)], dtype=np.float64)
+    P = np.stack([ij[:, 0], ij[:, 1], 0.5 * ij[:, 0] - 0.25 * ij[:, 1]], axis=1)
+    out = oracle.subdivide(m, 1, scheme, P0=P)
+    inner = (ij[:, 0] >= 2) & (ij[:, 0] <= N - 3) & (ij[:, 1] >= 2) & (ij[:, 1] <= M - 3)
+    np.testing.assert_allclose(out[1]["P"][:N * M][inner], P[inner], atol=1e-12)
+
+
+def _loop_creases(N, M, sigma):
+    """Tag the ring j = 0 of a quad torus: edges (i,0)-(i+1,0)."""
+    cv = np.array([[i * M, ((i + 1) % N) * M] for i in range(N)], dtype=np.int32)
+    return cv, np.full(N, sigma, dtype=np.float32)
+
+
+def _bspline_curve(poly):
+    """Closed uniform cubic B-spline curve subdivision: (1, 6, 1)/8 at vertices, midpoints."""
+    n = len(poly)
+    out = np.zeros((2 * n, 3))
+    for i in range(n):
+        out[2 * i] = (poly[i - 1] + 6 * poly[i] + poly[(i + 1) % n]) / 8.0
+        out[2 * i + 1] = 0.5 * (poly[i] + poly[(i + 1) % n])
+    return out
+
+
+def _ordered_loop(level, start):
+    adj = {}
+    for a, b in level["crease_verts"]:
+        adj.setdefault(int(a), []).append(int(b))
+        adj.setdefault(int(b), []).append(int(a))
+    seq, prev, cur = [start], None, start
+    while True:
+        nxt = [x for x in adj[cur] if x != prev]
+        nxt = nxt[0] if prev is not None else min(adj[cur])
+        if nxt == start:
+            break
+        seq.append(nxt)
+        prev, cur = cur, nxt
+    return seq
+
+
+@pytest.mark.parametrize("scheme", ["cc", "loop"])
+def test_sharp_crease_is_bspline_curve(scheme):
+    """An infinitely sharp crease loop refines as a cubic B-spline curve, independent of the
+    surface around it (Sec. 3.3 with the DeRose crease rules)."""
+    N = M = 10
+    if scheme == "cc":
+        m = synth.torus_cc_plain(N, M, jitter=0.05, seed=99)
+    else:
+        m = synth.torus_tri(N, M, flip_frac=0.0, creases=False, jitter=0.05, seed=99)
+    m["crease_verts"], m["crease_sharp"] = _loop_creases(N, M, np.inf)
+    out = oracle.subdivide(m, 3, scheme)
+    poly = m["P"][[i * M for i in range(N)]].astype(np.float64)
+    for l in range(1, 4):
+        poly = _bspline_curve(poly)
+        seq = _ordered_loop(out[l], 0)
+        got = out[l]["P"][seq]
+        if not np.allclose(got[1], poly[1], atol=1e-12):
+            got = got[[0] + list(range(len(seq) - 1, 0, -1))]
+        assert len(seq) == N * 2 ** l
+        np.testing.assert_allclose(got, poly, atol=1e-12)
+        assert np.all(np.isinf(out[l]["crease_sharp"]))
+
+
+def test_uniform_sharpness_decays_by_one():
+    """A loop of equal sharpness sigma inherits sigma - 1 exactly (Chaikin rule, Sec. 3.3)."""
+    N = M = 8
+    m = synth.torus_cc_plain(N, M, jitter=0.0)
+    m["crease_verts"], m["crease_sharp"] = _loop_creases(N, M, 3.0)
+    out = oracle.subdivide(m, 4, "cc")
+    for l, s in ((1, 2.0), (2, 1.0)):
+        assert out[l]["K"] == N * 2 ** l
+        assert np.all(out[l]["crease_sharp"] == np.float32(s))
+    assert out[3]["K"] == 0 and out[4]["K"] == 0
+
+
+def test_fractional_sharpness_is_affine_at_level1():
+    """For sigma in [0, 1] the level-1 result blends the smooth and sharp results linearly."""
+    N = M = 8
+    base = synth.torus_cc_plain(N, M, jitter=0.03, seed=4)
+    res = {}
+    for s in (0.0, 0.3, 1.0):
+        m = dict(base)
+        m["crease_verts"], m["crease_sharp"] = _loop_creases(N, M, s)
+        res[s] = oracle.subdivide(m, 1, "cc")[1]["P"]
+    np.testing.assert_allclose(res[0.3], 0.7 * res[0.0] + 0.3 * res[1.0], atol=1e-14)
+    m = dict(base)
+    m["crease_verts"], m["crease_sharp"] = _loop_creases(N, M, np.inf)
+    np.testing.assert_allclose(res[1.0], oracle.subdivide(m, 1, "cc")[1]["P"], atol=1e-15)
+
+
+def test_corners_fixed():
+    """k >= 3 infinitely sharp creases at a vertex keep it in place at every level."""
+    m = synth.cube()
+    e = set()
+    for r in range(6):
+        f = m["fv"][4 * r:4 * r + 4]
+        for j in range(4):
+            a, b = int(f[j]), int(f[(j + 1) % 4])
+            e.add((min(a, b), max(a, b)))
+    m["crease_verts"] = np.array(sorted(e), dtype=np.int32)
+    m["crease_sharp"] = np.full(len(e), np.inf, dtype=np.float32)
+    out = oracle.subdivide(m, 3, "cc")
+    for l in range(1, 4):
+        np.testing.assert_array_equal(out[l]["P"][:8], m["P"].astype(np.float64))
+
+
+@pytest.mark.parametrize("scheme,mesh", [
+    ("cc", synth.torus_cc_mixed(6, 6, seed=21)),
+    ("cc", synth.pillow(5)),
+    ("loop", synth.torus_tri(5, 5, seed=22)),
+    ("sqrt3", synth.torus_tri(5, 5, seed=23, creases=False)),
+])
+def test_brute_force_operator(scheme, mesh):
+    """Dense R_l from unit impulses equals the oracle's sparse operator, and the composed
+    operator reproduces two levels of refinement."""
+    import scipy.sparse as sp
+    out = oracle.subdivide(mesh, 2, scheme, operator=True)
+    V0, V1 = out[0]["V"], out[1]["V"]
+    dense = np.zeros((V1, V0))
+    for j in range(V0):
+        P = np.zeros((V0, 3))
+        P[j, 0] = 1.0
+        dense[:, j] = oracle.subdivide(mesh, 1, scheme, P0=P)[1]["P"][:, 0]
+    R0 = sp.csr_matrix((out[0]["R_w"], (out[0]["R_rows"], out[0]["R_cols"])), shape=(V1, V0))
+    np.testing.assert_allclose(R0.toarray(), dense, atol=1e-14)
+    R1 = sp.csr_matrix((out[1]["R_w"], (out[1]["R_rows"], out[1]["R_cols"])),
+                       shape=(out[2]["V"], V1))
+    P0 = mesh["P"].astype(np.float64)
+    np.testing.assert_allclose((R1 @ R0) @ P0, out[2]["P"], atol=1e-13)
+
+
+def test_rejects_invalid_meshes():
+    m = synth.cube()
+    open_mesh = dict(m, F=5, off=m["off"][:6], fv=m["fv"][:20])
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.subdivide(open_mesh, 1, "cc")
+    assert ei.value.code in (1, 3)
+    dup = dict(m, F=7, off=np.append(m["off"], 28).astype(np.int32),
+               fv=np.concatenate([m["fv"], m["fv"][:4]]))
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.subdivide(dup, 1, "cc")
+    assert ei.value.code == 2
+    bad = dict(m, crease_verts=np.array([[0, 7]], np.int32), crease_sharp=np.array([1.0], np.float32))
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.subdivide(bad, 1, "cc")
+    assert ei.value.code == 5
+
+
+def test_loop_beta_sqrt3_alpha_values():
+    """beta_n and alpha_n special values quoted in the text (Appendices A, B)."""
+    def beta(n):
+        return (5 / 8 - (3 / 8 + 0.25 * math.cos(2 * math.pi / n)) ** 2) / n
+    m = synth.torus_tri(6, 6, flip_frac=0.0, creases=False, jitter=0.0)
+    out = oracle.subdivide(m, 1, "loop", operator=True)
+    rows = _rows(out[0])
+    assert max(rows[0].values()) == pytest.approx(1 - 6 * beta(6), abs=1e-15)
+    assert beta(6) == pytest.approx(1 / 16, abs=1e-15)
