@@ -1,0 +1,301 @@
+#!/usr/bin/env python
+"""Throughput of uniform subdivision on GB300: refined faces per second.
+
+One step = one full dynamic-topology subdivision of the workload (Sec. 3.5 "Dynamic topology":
+level-0 adjacency, then per level the fused build + eval kernels, creases included) through the
+C ABI call alsub_subdivide. Default workload: Catmull-Clark with semi-sharp creases, 6 levels of a
+~9.2k-face mixed-polygon torus (37,750,784 refined quads). Inputs are resident in HBM; the step's
+working set (~2.6 GB) is far larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0). With torchrun (N > 1) every rank refines its own copy of the
+workload (independent meshes: weak scaling, no collective on the data path); the time is the max
+over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl alsub|reference] [--workload NAME]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1809_06047_gb300 import synth  # noqa: E402
+
+DEFAULT_WORKLOAD = "cc_creased_torus96_L6"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="alsub", choices=["alsub", "reference"])
+    p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:  # noqa: BLE001
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def level_alg_bytes(c, l):
+    """Algorithmic bytes of one level step l -> l+1: read M_l and P_l, write M_{l+1} and P_{l+1}
+    (int32 face tables, FP32 xyz positions)."""
+    a, b = c[l], c[l + 1]
+    return 4 * a[2] + 12 * a[0] + 4 * b[2] + 12 * b[0]
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:  # noqa: BLE001
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:  # noqa: BLE001
+            self.proc.kill()
+        rows = []
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) >= 9:
+                    rows.append(f)
+            os.unlink(self.path)
+        except Exception:  # noqa: BLE001
+            return None
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        reasons = set()
+        for r in rows:
+            for name, col in (("hw_slowdown", 5), ("hw_thermal_slowdown", 6),
+                              ("sw_thermal_slowdown", 7), ("sw_power_cap", 8)):
+                if r[col].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path)).get(kernel_key)
+    except Exception:  # noqa: BLE001
+        return None
+    if not d:
+        return None
+    src = os.path.join(ROOT, "paper_1809_06047_gb300", "csrc", d["source"])
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    return d["dram_bytes_per_launch"] if h == d["source_sha256_16"] else None
+
+
+def cpu_baseline(m, budget_levels):
+    """The oracle (serial FP64, as it stands) on a bounded sample of the same workload."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    out = oracle.subdivide(m, budget_levels, m["scheme"], keep_all=False)
+    dt = time.perf_counter() - t0
+    F = out[-1]["F"]
+    return {"value": F / dt, "unit": "refined faces/s", "cores": 1, "kind": "oracle",
+            "sample": f"{m['name']} refined to level {budget_levels} ({F} faces) once, "
+                      f"{dt:.1f} s on one host core"}
+
+
+def sample_levels(name):
+    # level whose serial FP64 refinement takes roughly 2-10 s on one core
+    return {"cc_torus16_L3": 3, "cc_creased_torus96_L6": 5, "loop_tri_torus128_L6": 4,
+            "sqrt3_tri_torus128_L8": 5, "cc_creased_torus144_L4": 4}.get(name, 3)
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    m = synth.workload(args.workload)
+    lv = min(sample_levels(args.workload), m["levels"]) - 1
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        oracle.subdivide(m, lv, m["scheme"], keep_all=False)
+    t0 = time.perf_counter()
+    F = 0
+    for _ in range(args.steps):
+        F = oracle.subdivide(m, lv, m["scheme"], keep_all=False)[-1]["F"]
+    dt = time.perf_counter() - t0
+    value = F * args.steps / dt
+    sample = f"{m['name']} refined to level {lv} ({F} faces) per step on one host core"
+    print(json.dumps({
+        "impl": "reference", "metric": "refined faces/s", "value": value, "unit": "refined faces/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample_levels": lv},
+        "cpu_baseline": {"value": value, "unit": "refined faces/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "refined faces/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1809_06047_gb300 import alsub
+
+    m = synth.workload(args.workload)
+    L, scheme = m["levels"], m["scheme"]
+    counts = alsub.plan(scheme, m["V"], m["F"], len(m["fv"]), L)
+    FL, VL = int(counts[L][1]), int(counts[L][0])
+    M = alsub.Mesh.from_dict(m)
+    T = alsub.Topology(M, L, build=False)
+    P0 = torch.from_numpy(m["P"]).cuda()
+    PL = torch.empty((VL, 3), dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        T.subdivide(P0, out=PL)
+    torch.cuda.synchronize()
+    T.status()
+    T.timings()
+    T.set_timing(args.steps)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        T.subdivide(P0, out=PL)
+    e1.record()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stage_ms, calls, launches = T.timings()
+    T.set_timing(0)
+    T.status()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_step = ms / args.steps
+    value = FL * args.steps * world / (ms / 1e3)
+
+    # dominant kernel: the last level's fused build + eval step
+    peak, peak_src = measured_peaks()
+    last = L - 1
+    dur_ms = stage_ms[1 + last] / max(calls, 1)
+    alg = level_alg_bytes(counts, last)
+    achieved = alg / (dur_ms / 1e3) / 1e9
+    pipe_bytes = sum(level_alg_bytes(counts, l) for l in range(L))
+    kernel_key = f"{scheme}_step_level{last}_{args.workload}"
+    traffic = traffic_for(kernel_key)
+
+    # end to end through the same call with host buffers: pinned H2D of P0, D2H of P_L
+    P0_h = torch.from_numpy(m["P"]).pin_memory()
+    PL_h = torch.empty((VL, 3), dtype=torch.float32).pin_memory()
+    P0_d = torch.empty_like(P0)
+    ke = max(1, min(args.steps, 10))
+    barrier()
+    e0.record()
+    for _ in range(ke):
+        P0_d.copy_(P0_h, non_blocking=True)
+        T.subdivide(P0_d, out=PL)
+        PL_h.copy_(PL, non_blocking=True)
+    e1.record()
+    barrier()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+    e2e = {"value": FL * ke * world / (ms_e2e / 1e3), "unit": "refined faces/s",
+           "h2d_bytes_per_step": int(P0_h.numel() * 4), "d2h_bytes_per_step": int(PL_h.numel() * 4)}
+
+    out = {
+        "metric": "refined faces/s", "value": value, "unit": "refined faces/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.workload, "scheme": scheme, "levels": L,
+                   "control_faces": m["F"], "control_verts": m["V"], "creases": int(len(m["crease_sharp"])),
+                   "refined_faces": FL, "refined_verts": VL, "path": "alsub_subdivide (dynamic topology)",
+                   "l2": "no flush: per-step working set ~%.1f GB > 129 MB L2" % (pipe_bytes / 1e9),
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "kernel": f"{scheme} level {last}->{L} fused build+eval step",
+                     "algorithmic_bytes": alg, "avg_launch_ms": dur_ms, "peak_source": peak_src},
+        "pipeline": {"alg_bytes_per_step": pipe_bytes, "gbs": pipe_bytes / (ms_step / 1e3) / 1e9,
+                     "stage_ms": [s / max(calls, 1) for s in stage_ms]},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(m, min(sample_levels(args.workload), L))
+    if rank == 0:
+        print(json.dumps(out))
+    T.close()
+    M.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * alsub.h -- C ABI of libalsub, a GB300 (sm_103a) implementation of uniform subdivision as
+ * sparse linear algebra on the oriented face-vertex mesh matrix (AlSub, Mlakar et al.,
+ * arXiv 1809.06047).
+ *
+ * Scope: one uniform subdivision step, repeated level by level, for Catmull-Clark (Sec. 3),
+ * Loop (Appendix B) and sqrt(3) (Appendix A) on closed 2-manifold meshes, with sharp and
+ * semi-sharp creases for Catmull-Clark and Loop (Sec. 3.3). Topology refinement (the build step
+ * of Fig. module_core) is integer work that emits each level's face table directly; vertex
+ * refinement (the eval step) is FP32. The subdivision operator of Sec. 3.5 "Single SpMV
+ * evaluation" (R_i per level, or the composite R = R_{L-1} ... R_0) can be built once and applied
+ * as one SpMV per frame, and applied transposed for gradients.
+ *
+ * Conventions shared by every call:
+ *  - Every call returns an alsub_status and never aborts, traps or exits. On failure
+ *    alsub_last_error() returns a message for the calling thread.
+ *  - Pointers named *_host are host memory and are only read during the call. Pointers named
+ *    *_dev are device memory owned by the caller, on the current CUDA device, and must stay
+ *    valid until the work enqueued on `stream` has completed.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream). Work is
+ *    enqueued on it without an implicit device synchronisation, except in the calls that say
+ *    they synchronise.
+ *  - Handles own the device memory they allocate; their destroy call frees it (stream ordered on
+ *    the stream they were created with).
+ *  - Errors found on the device (a non-manifold input, a valence beyond the supported bound)
+ *    are latched in a per-handle device status word and reported by alsub_topology_status(),
+ *    which synchronises the handle's stream.
+ *  - Vertex positions are FP32 xyz, packed as float[3*V] (12 bytes per vertex, AoS).
+ *  - Indices are int32; every per-level count of vertices, faces, corners and edges must stay
+ *    below 2^31 - 1 (ALSUB_ERR_UNSUPPORTED otherwise).
+ *
+ * Vertex numbering of a refined level follows the paper's refined mesh matrix (Sec. 3.2,
+ * "Topology refinement"): the old vertices keep their ids, then one face point per face
+ * (Catmull-Clark, sqrt(3): id |v| + r), then one edge point per edge (Catmull-Clark:
+ * |v| + |f| + e; Loop: |v| + e). Faces of level l+1 are the children of level l's faces in
+ * corner order: Catmull-Clark corner x of face r gives quad x = [v_x, e(x), f_r, e(prev x)];
+ * Loop triangle r gives 4r..4r+3 = [v0,e0,e2], [v1,e1,e0], [v2,e2,e1], [e0,e1,e2]; sqrt(3)
+ * corner x of triangle r gives triangle x = [v_x, f_{F(next x, x)}, f_r]. Edge ids are free
+ * (Sec. 3.2 only asks for a unique enumeration); this library numbers them level by level as
+ * described under alsub_refine_topology below.
+ */
+#ifndef ALSUB_H
+#define ALSUB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ALSUB_OK = 0,
+    ALSUB_ERR_INVALID_ARG = 1,   /* a pointer, count, index or sharpness out of range */
+    ALSUB_ERR_NONMANIFOLD = 2,   /* duplicate directed edge, edge of >2 faces, vertex with >1 fan */
+    ALSUB_ERR_UNSUPPORTED = 3,   /* open mesh (boundary), counts beyond int32, valence > 1024 */
+    ALSUB_ERR_OOM = 4,           /* device allocation failed or a budget is exhausted */
+    ALSUB_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
+    ALSUB_ERR_DEVICE = 6,        /* a CUDA runtime error */
+    ALSUB_ERR_BUSY = 7,          /* the server has no free slot and the request was not queued */
+    ALSUB_ERR_NOT_READY = 8      /* the request is still in flight */
+} alsub_status;
+
+typedef enum { ALSUB_CATMULL_CLARK = 0, ALSUB_LOOP = 1, ALSUB_SQRT3 = 2 } alsub_scheme;
+
+typedef struct alsub_mesh_s *alsub_mesh_t;
+typedef struct alsub_topology_s *alsub_topology_t;
+typedef struct alsub_operator_s *alsub_operator_t;
+typedef struct alsub_server_s *alsub_server_t;
+
+/* Message of the last failed call on this thread ("" if none). Never NULL. */
+const char *alsub_last_error(void);
+
+/* Static name of a status code. */
+const char *alsub_status_string(alsub_status s);
+
+/*
+ * Copy `bytes` bytes between host and/or device buffers (unified addressing decides the
+ * direction) on `stream`, then synchronise that stream. Plumbing for bindings that hold raw
+ * device pointers returned by the accessors below. Errors: INVALID_ARG, DEVICE.
+ */
+alsub_status alsub_copy(void *dst, const void *src, size_t bytes, void *stream);
+
+/*
+ * Closed-form per-level counts (host only, no GPU needed). Sec. 3.1 step 4 / Sec. 3.2 for
+ * Catmull-Clark (V' = V + F + E, F' = nnz, nnz' = 4 nnz, E' = 2E + nnz), Appendix B for Loop
+ * (V' = V + E, F' = 4F, E' = 2E + 3F), Appendix A for sqrt(3) (V' = V + F, F' = 3F,
+ * E' = 3F'/2); a closed mesh has E = nnz / 2.
+ *   counts_host: int64[4 * (levels + 1)], filled with (V, F, nnz, E) per level.
+ * Errors: INVALID_ARG for negative or inconsistent inputs, UNSUPPORTED when a count would exceed
+ * int32 or nnz is odd (an open mesh).
+ */
+alsub_status alsub_plan(alsub_scheme scheme, int64_t num_verts, int64_t num_faces, int64_t nnz,
+                        int32_t levels, int64_t *counts_host);
+
+/*
+ * Create a control mesh: the reduced mesh matrix M of Sec. 4.1 as a face table, plus the crease
+ * matrix C of Sec. 3.3 as a list of tagged edges.
+ *   face_offsets_host: int32[num_faces + 1] CSR offsets, or NULL when every face has the
+ *                      scheme's order (4 for a uniform Catmull-Clark quad mesh, 3 for Loop and
+ *                      sqrt(3)).
+ *   face_verts_host:   int32[nnz] vertex ids of each face in counter-clockwise cyclic order.
+ *   crease_verts_host: int32[2 * num_creases] edge endpoints; crease_sharpness_host: float[K]
+ *                      sharpness sigma >= 0 (+inf = infinitely sharp; 0 = smooth, dropped).
+ *                      sqrt(3) ignores creases (the paper gives the scheme no crease rules).
+ * The host validates ranges (vertex ids, face order >= 3, Loop/sqrt(3) triangles only, no
+ * repeated vertex in a face, every vertex used, sigma not NaN or negative) and copies everything
+ * to the device on `stream`; the caller may free its arrays on return. Adjacency is checked on
+ * the device when a topology is built.
+ * Errors: INVALID_ARG, UNSUPPORTED (counts beyond int32, odd nnz), OOM, DEVICE.
+ */
+alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t num_verts, int32_t num_faces,
+                               const int32_t *face_offsets_host, const int32_t *face_verts_host,
+                               int32_t num_creases, const int32_t *crease_verts_host,
+                               const float *crease_sharpness_host, void *stream,
+                               alsub_mesh_t *out);
+
+alsub_status alsub_mesh_destroy(alsub_mesh_t mesh);
+
+/*
+ * Build the topology of `levels` uniform refinement steps (the build step of Fig. module_core,
+ * Sec. 3.5 "Static topology"): for every level the face table M_{l+1}, the per-corner edge
+ * numbering (E, Eq. CC_E; Appendix B for Loop) and the per-corner face adjacency (F, Eq. F), and
+ * the inherited crease lists (Sec. 3.3). Level 0 edges are numbered by an exclusive scan over
+ * the corners that own their edge (a -> b with a < b); each refined level numbers the two halves
+ * of parent edge e as 2e and 2e+1 and the edges interior to parent faces after them. All sizes
+ * are closed-form, so nothing is read back to the host. The handle keeps every level resident
+ * for alsub_refine_vertices and alsub_build_operator. Enqueued on `stream`.
+ * Errors: INVALID_ARG, UNSUPPORTED, OOM, DEVICE; adjacency errors are latched on the device
+ * (see alsub_topology_status).
+ */
+alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stream,
+                                   alsub_topology_t *out);
+
+/*
+ * Allocate a topology handle for `levels` steps of `mesh` without computing anything (sizes are
+ * closed-form). alsub_subdivide fills it; alsub_refine_topology is alsub_topology_create plus the
+ * build. The handle keeps a reference to `mesh`, which must outlive it.
+ * Errors: INVALID_ARG, UNSUPPORTED (a level beyond int32 counts), OOM, DEVICE.
+ */
+alsub_status alsub_topology_create(alsub_mesh_t mesh, int32_t levels, void *stream,
+                                   alsub_topology_t *out);
+
+/* Synchronise the handle's stream and return its latched device status (OK, NONMANIFOLD,
+ * UNSUPPORTED or INVALID_ARG for a crease that is not an edge). */
+alsub_status alsub_topology_status(alsub_topology_t topo);
+
+/*
+ * Sizes and device face table of one level (0 <= level <= levels).
+ *   face_verts_dev: level 0: the input face table (face_offsets_dev gives its CSR offsets);
+ *                   level >= 1: int32[nnz], 4 per face for Catmull-Clark, 3 for Loop/sqrt(3)
+ *                   (face_offsets_dev is then NULL). Owned by the handle.
+ * Any out pointer may be NULL.
+ */
+alsub_status alsub_topology_level(alsub_topology_t topo, int32_t level, int64_t *V, int64_t *F,
+                                  int64_t *nnz, int64_t *E, const int32_t **face_offsets_dev,
+                                  const int32_t **face_verts_dev);
+
+/*
+ * Crease list of one level (Sec. 3.3: the crease matrix C_l as tagged edges). Synchronises the
+ * handle's stream to read the count. crease_verts_dev: int32[2K] endpoints, crease_sharp_dev:
+ * float[K]; both owned by the handle. Inherited sharpness is computed in FP32 in the fixed order
+ * t = 3 sigma; u = sigma_o + t; w = 0.25 u; y = w - 1; max(y, 0), where sigma_o is the other
+ * crease at the end vertex when exactly two creases meet there and it is finite, else sigma.
+ */
+alsub_status alsub_topology_creases(alsub_topology_t topo, int32_t level, int32_t *K,
+                                    const int32_t **crease_verts_dev,
+                                    const float **crease_sharp_dev);
+
+alsub_status alsub_topology_destroy(alsub_topology_t topo);
+
+/*
+ * Vertex refinement of all levels of a built topology (the eval step: Sec. 3.2 face, edge and
+ * vertex points as mapped SpMVs, fused in one pass per level; crease rules overwrite crease
+ * vertices and edge points, Fig. module_creases).
+ *   P0_dev: float[3 * V_0]; PL_dev: float[3 * V_levels].
+ *   scratch_dev: NULL (use the handle's own buffers; then calls on one handle must not overlap)
+ *                or device memory of alsub_refine_vertices_scratch_bytes() bytes.
+ * Crease rules: edge point sigma >= 1 -> midpoint, 0 < sigma < 1 -> (1 - sigma) smooth + sigma
+ * midpoint; vertex with k incident creases, mean sharpness s: k < 2 smooth, k == 2
+ * (p_a + 6 p + p_b) / 8, k >= 3 p, blended w sharp + (1 - w) smooth with w = min(s, 1).
+ */
+alsub_status alsub_refine_vertices(alsub_topology_t topo, const float *P0_dev, float *PL_dev,
+                                   void *scratch_dev, void *stream);
+alsub_status alsub_refine_vertices_scratch_bytes(alsub_topology_t topo, size_t *bytes);
+
+/*
+ * Dynamic-topology subdivision (Sec. 3.5 "Dynamic topology"): rebuild the whole topology of the
+ * handle from its control mesh AND refine the vertices, one fused build+eval pass per level, so
+ * a topology-changing edit costs one call with no preprocessing. The per-corner adjacency of the
+ * last level is not stored (nothing consumes it); face tables and crease lists of every level
+ * are. Same arguments as alsub_refine_vertices.
+ */
+alsub_status alsub_subdivide(alsub_topology_t topo, const float *P0_dev, float *PL_dev,
+                             void *scratch_dev, void *stream);
+
+/*
+ * Live timing of the library's own work on the calling stream. capacity > 0 allocates
+ * capacity x (levels + 2) CUDA events and makes every following alsub_subdivide /
+ * alsub_refine_vertices call on the handle record one event before its level-0 build, one after
+ * it, and one after each level's kernels; capacity = 0 turns timing off. Calls beyond `capacity`
+ * since the last read make the read fail with INVALID_ARG. Errors: INVALID_ARG, OOM, DEVICE.
+ */
+alsub_status alsub_topology_set_timing(alsub_topology_t topo, int32_t capacity);
+
+/*
+ * Read and reset the timings (synchronises the handle's stream).
+ *   ms_host: double[levels + 1]: [0] summed duration of the level-0 builds, [1 + l] summed
+ *            duration of level l's step (the l -> l+1 build and/or eval kernels, crease kernels
+ *            included), over the `*calls` calls recorded since the last read.
+ *   launches: number of kernels the handle launched since the last read (all calls, timed or not).
+ */
+alsub_status alsub_topology_timings(alsub_topology_t topo, double *ms_host, int32_t *calls,
+                                    int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ALSUB_H */

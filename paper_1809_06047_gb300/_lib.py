@@ -1,0 +1,66 @@
+"""ctypes declarations of libalsub's C ABI (include/alsub.h). Argument marshalling only."""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+c_int32, c_int64, c_size_t, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+P = ctypes.POINTER
+H = c_void_p  # opaque handles and raw pointers
+
+# name -> argtypes; every function returns alsub_status (int32) unless listed in _RESTYPE
+SIGNATURES = {
+    "alsub_last_error": [],
+    "alsub_status_string": [c_int32],
+    "alsub_copy": [c_void_p, c_void_p, c_size_t, c_void_p],
+    "alsub_plan": [c_int32, c_int64, c_int64, c_int64, c_int32, P(c_int64)],
+    "alsub_mesh_create": [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                          c_void_p, P(H)],
+    "alsub_mesh_destroy": [H],
+    "alsub_topology_create": [H, c_int32, c_void_p, P(H)],
+    "alsub_refine_topology": [H, c_int32, c_void_p, P(H)],
+    "alsub_topology_status": [H],
+    "alsub_topology_level": [H, c_int32, P(c_int64), P(c_int64), P(c_int64), P(c_int64), P(c_void_p),
+                             P(c_void_p)],
+    "alsub_topology_creases": [H, c_int32, P(c_int32), P(c_void_p), P(c_void_p)],
+    "alsub_topology_destroy": [H],
+    "alsub_refine_vertices": [H, c_void_p, c_void_p, c_void_p, c_void_p],
+    "alsub_refine_vertices_scratch_bytes": [H, P(c_size_t)],
+    "alsub_subdivide": [H, c_void_p, c_void_p, c_void_p, c_void_p],
+    "alsub_topology_set_timing": [H, c_int32],
+    "alsub_topology_timings": [H, P(ctypes.c_double), P(c_int32), P(c_int64)],
+}
+_RESTYPE = {"alsub_last_error": ctypes.c_char_p, "alsub_status_string": ctypes.c_char_p}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_stale: bool = True) -> ctypes.CDLL:
+    """Load the in-tree libalsub.so (building it first if it is missing or stale).
+
+    Raises RuntimeError when the library cannot be built or loaded: there is no fallback path.
+    """
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if build_if_stale:
+            try:
+                path = _build.build()
+            except Exception as e:  # noqa: BLE001 -- surface the compiler output
+                if not os.path.exists(path):
+                    raise RuntimeError(f"libalsub could not be built: {e}") from e
+        if not os.path.exists(path):
+            raise RuntimeError(f"libalsub not found at {path}; run paper_1809_06047_gb300.build")
+        lib = ctypes.CDLL(path)
+        for name, args in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = _RESTYPE.get(name, c_int32)
+        _lib = lib
+        return lib

@@ -1,0 +1,195 @@
+"""Python binding of libalsub with the C ABI's names (argument marshalling only).
+
+PyTorch provides device memory and streams; every step of the subdivision runs in libalsub's
+CUDA kernels. Without a loadable libalsub.so every call raises: there is no CPU path.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+
+SCHEMES = {"cc": 0, "loop": 1, "sqrt3": 2, "catmull-clark": 0}
+
+
+class AlsubError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+def lib():
+    return _lib.load()
+
+
+def _check(st: int):
+    if st:
+        L = lib()
+        raise AlsubError(st, L.alsub_last_error().decode() or L.alsub_status_string(st).decode())
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _ptr(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def plan(scheme: str, V: int, F: int, nnz: int, levels: int) -> np.ndarray:
+    """Closed-form (V, F, nnz, E) per level (host only)."""
+    out = np.zeros(4 * (levels + 1), dtype=np.int64)
+    _check(lib().alsub_plan(SCHEMES[scheme], V, F, nnz, levels,
+                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    return out.reshape(levels + 1, 4)
+
+
+def copy_to_host(ptr: int, nbytes: int, dtype, count: int, stream=None) -> np.ndarray:
+    out = np.empty(count, dtype=dtype)
+    if nbytes:
+        _check(lib().alsub_copy(out.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ptr), nbytes,
+                                ctypes.c_void_p(_stream(stream))))
+    return out
+
+
+class Mesh:
+    """alsub_mesh_create / alsub_mesh_destroy."""
+
+    def __init__(self, scheme: str, V: int, F: int, fv, off=None, crease_verts=None,
+                 crease_sharp=None, stream=None):
+        self.scheme = scheme
+        fv = np.ascontiguousarray(fv, dtype=np.int32)
+        off = None if off is None else np.ascontiguousarray(off, dtype=np.int32)
+        cv = np.ascontiguousarray(crease_verts if crease_verts is not None else np.zeros((0, 2)),
+                                  dtype=np.int32).reshape(-1)
+        cs = np.ascontiguousarray(crease_sharp if crease_sharp is not None else np.zeros(0),
+                                  dtype=np.float32).reshape(-1)
+        self.V, self.F, self.nnz = int(V), int(F), int(fv.size)
+        self._h = ctypes.c_void_p()
+        _check(lib().alsub_mesh_create(SCHEMES[scheme], self.V, self.F, _ptr(off), _ptr(fv),
+                                       int(cs.size), _ptr(cv) if cs.size else None,
+                                       _ptr(cs) if cs.size else None,
+                                       ctypes.c_void_p(_stream(stream)), ctypes.byref(self._h)))
+
+    @classmethod
+    def from_dict(cls, m: dict, scheme: str | None = None, stream=None) -> "Mesh":
+        return cls(scheme or m.get("scheme", "cc"), m["V"], m["F"], m["fv"], m["off"],
+                   m.get("crease_verts"), m.get("crease_sharp"), stream)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _check(lib().alsub_mesh_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 -- interpreter shutdown
+            pass
+
+
+class Topology:
+    """A refined topology: alsub_topology_create / alsub_refine_topology and the per-level calls."""
+
+    def __init__(self, mesh: Mesh, levels: int, build: bool = True, stream=None):
+        self.mesh = mesh          # the mesh must outlive the topology
+        self.levels = int(levels)
+        self._h = ctypes.c_void_p()
+        fn = lib().alsub_refine_topology if build else lib().alsub_topology_create
+        _check(fn(mesh.handle, self.levels, ctypes.c_void_p(_stream(stream)), ctypes.byref(self._h)))
+        self.counts = [self.level_counts(l) for l in range(self.levels + 1)]
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h:
+            _check(lib().alsub_topology_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def status(self):
+        _check(lib().alsub_topology_status(self._h))
+
+    def level_counts(self, level: int) -> dict:
+        V, F, nnz, E = (ctypes.c_int64() for _ in range(4))
+        _check(lib().alsub_topology_level(self._h, level, ctypes.byref(V), ctypes.byref(F),
+                                          ctypes.byref(nnz), ctypes.byref(E), None, None))
+        return dict(V=V.value, F=F.value, nnz=nnz.value, E=E.value)
+
+    def faces(self, level: int, stream=None) -> np.ndarray:
+        """Face table of a level as int32[nnz] (host copy)."""
+        off, fv = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().alsub_topology_level(self._h, level, None, None, None, None,
+                                          ctypes.byref(off), ctypes.byref(fv)))
+        n = self.counts[level]["nnz"]
+        return copy_to_host(fv.value, 4 * n, np.int32, n, stream)
+
+    def face_table_ptr(self, level: int) -> int:
+        fv = ctypes.c_void_p()
+        _check(lib().alsub_topology_level(self._h, level, None, None, None, None, None,
+                                          ctypes.byref(fv)))
+        return fv.value
+
+    def creases(self, level: int, stream=None):
+        """(int32[K, 2] endpoints, float32[K] sharpness) of a level (synchronises)."""
+        K = ctypes.c_int32()
+        cv, cs = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().alsub_topology_creases(self._h, level, ctypes.byref(K), ctypes.byref(cv),
+                                            ctypes.byref(cs)))
+        k = K.value
+        if k == 0:
+            return np.zeros((0, 2), np.int32), np.zeros(0, np.float32)
+        return (copy_to_host(cv.value, 8 * k, np.int32, 2 * k, stream).reshape(k, 2),
+                copy_to_host(cs.value, 4 * k, np.float32, k, stream))
+
+    def scratch_bytes(self) -> int:
+        b = ctypes.c_size_t()
+        _check(lib().alsub_refine_vertices_scratch_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
+    def _run(self, fn, P0: torch.Tensor, out, scratch, stream):
+        assert P0.is_cuda and P0.dtype == torch.float32 and P0.is_contiguous()
+        VL = self.counts[-1]["V"]
+        if out is None:
+            out = torch.empty((VL, 3), dtype=torch.float32, device=P0.device)
+        assert out.is_contiguous() and out.numel() == 3 * VL
+        sp = None if scratch is None else ctypes.c_void_p(scratch.data_ptr())
+        _check(fn(self._h, ctypes.c_void_p(P0.data_ptr()), ctypes.c_void_p(out.data_ptr()), sp,
+                  ctypes.c_void_p(_stream(stream))))
+        return out
+
+    def refine_vertices(self, P0: torch.Tensor, out=None, scratch=None, stream=None) -> torch.Tensor:
+        """alsub_refine_vertices: eval of all levels on the built topology."""
+        return self._run(lib().alsub_refine_vertices, P0, out, scratch, stream)
+
+    def set_timing(self, capacity: int):
+        """alsub_topology_set_timing: record per-level CUDA events for the next `capacity` calls."""
+        _check(lib().alsub_topology_set_timing(self._h, int(capacity)))
+
+    def timings(self):
+        """alsub_topology_timings -> (ms per stage [level-0 build, level 0..L-1], calls, launches)."""
+        ms = np.zeros(self.levels + 1, np.float64)
+        calls, launches = ctypes.c_int32(), ctypes.c_int64()
+        _check(lib().alsub_topology_timings(self._h, ms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                            ctypes.byref(calls), ctypes.byref(launches)))
+        return ms, calls.value, launches.value
+
+    def subdivide(self, P0: torch.Tensor, out=None, scratch=None, stream=None) -> torch.Tensor:
+        """alsub_subdivide: rebuild the topology and refine the vertices, fused per level."""
+        return self._run(lib().alsub_subdivide, P0, out, scratch, stream)

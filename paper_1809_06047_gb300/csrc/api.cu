@@ -1,0 +1,531 @@
+// C ABI of libalsub: host validation, handles, closed-form allocation and the per-level
+// orchestration of the build (topology) and eval (vertex) steps.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+using namespace alsub;
+
+struct alsub_mesh_s {
+    MeshImpl m;
+};
+struct alsub_topology_s {
+    TopoImpl t;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+alsub_status fail(alsub_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+alsub_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(ALSUB_ERR_DEVICE, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                                                   \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess) {                                                   \
+            if (e_ == cudaErrorMemoryAllocation) {                                 \
+                cudaGetLastError();                                                \
+                return fail(ALSUB_ERR_OOM, "%s: out of device memory", #call);     \
+            }                                                                      \
+            return cuda_fail(e_, #call);                                           \
+        }                                                                          \
+    } while (0)
+
+const long long kI32 = 2147483647LL;
+
+// Closed-form counts of one refinement step (Sec. 3.1 step 4, Appendix A, B).
+bool next_counts(alsub_scheme s, long long V, long long F, long long nnz, long long E,
+                 long long *o) {
+    if (s == ALSUB_CATMULL_CLARK) { o[0] = V + F + E; o[1] = nnz; o[2] = 4 * nnz; o[3] = 2 * E + nnz; }
+    else if (s == ALSUB_LOOP) { o[0] = V + E; o[1] = 4 * F; o[2] = 12 * F; o[3] = 2 * E + 3 * F; }
+    else { o[0] = V + F; o[1] = 3 * F; o[2] = 9 * F; o[3] = 9 * F / 2; }
+    for (int i = 0; i < 4; i++)
+        if (o[i] > kI32) return false;
+    return true;
+}
+
+template <class T>
+alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
+    *p = nullptr;
+    if (n == 0) n = 1;
+    void *q = nullptr;
+    cudaError_t e = cudaMallocAsync(&q, n * sizeof(T), s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ALSUB_ERR_OOM, "device allocation of %zu bytes failed", n * sizeof(T));
+    }
+    T_.allocs.push_back(q);
+    *p = (T *)q;
+    return ALSUB_OK;
+}
+
+#define AL(ptr, n)                                                   \
+    do {                                                             \
+        alsub_status st_ = dalloc(T, &(ptr), (size_t)(n), s);        \
+        if (st_ != ALSUB_OK) return st_;                             \
+    } while (0)
+
+void free_topo(TopoImpl &T) {
+    for (void *p : T.allocs) cudaFreeAsync(p, T.stream);
+    T.allocs.clear();
+}
+
+alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, cudaStream_t s) {
+    C.cap = cap;
+    AL(C.count, 1);
+    if (cap > 0) {
+        AL(C.edge, cap);
+        AL(C.own, cap);
+        AL(C.sig, cap);
+        AL(C.verts, 2 * cap);
+    }
+    return ALSUB_OK;
+}
+
+alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
+    T.mesh = &M;
+    T.scheme = M.scheme;
+    T.levels = levels;
+    T.stream = s;
+    T.L.assign(levels + 1, LevelBuf());
+    LevelBuf &L0 = T.L[0];
+    L0.V = M.V; L0.F = M.F; L0.nnz = M.nnz; L0.E = M.nnz / 2;
+    for (int l = 0; l < levels; l++) {
+        long long o[4];
+        LevelBuf &A = T.L[l];
+        if (!next_counts(M.scheme, A.V, A.F, A.nnz, A.E, o))
+            return fail(ALSUB_ERR_UNSUPPORTED, "level %d exceeds int32 counts", l + 1);
+        LevelBuf &B = T.L[l + 1];
+        B.V = o[0]; B.F = o[1]; B.nnz = o[2]; B.E = o[3];
+    }
+    const int V = M.V, nnz = M.nnz, E0 = (int)L0.E;
+    L0.fv = M.d_fv;
+    AL(L0.ce, nnz);
+    AL(L0.tw, nnz);
+    AL(T.cf0, nnz); AL(T.nx0, nnz); AL(T.pv0, nnz); AL(T.own0, nnz); AL(T.vbk, nnz); AL(T.eid, nnz);
+    AL(T.vc0, V); AL(T.deg, V); AL(T.vfill, V); AL(T.voff, V + 1);
+    AL(T.eo0, E0); AL(T.cmap, E0);
+    AL(T.e0count, 1); AL(T.status, 1);
+    // crease capacities: the sharpness of level l is at most sigma_max - l (each inherited
+    // value is at most the parent maximum minus one), so creases are dead once l >= sigma_max
+    bool creases = M.scheme != ALSUB_SQRT3 && M.K > 0;
+    long long maxcap = 0;
+    for (int l = 0; l <= levels; l++) {
+        long long cap = 0;
+        if (creases && (double)l < (double)M.sigma_max)
+            cap = l == 0 ? M.K : std::min(2 * T.L[l - 1].cr.cap, T.L[l].E);
+        alsub_status st = alloc_crease(T, T.L[l].cr, cap, s);
+        if (st) return st;
+        maxcap = std::max(maxcap, cap);
+    }
+    long long nflags = std::max<long long>({(long long)nnz, (long long)E0, 2 * maxcap, 1});
+    AL(T.flags, nflags);
+    AL(T.pos, nflags);
+    T.scan_tmp_bytes = scan_tmp_bytes(std::max<long long>(nflags, V));
+    AL(*(char **)&T.scan_tmp, T.scan_tmp_bytes);
+    if (maxcap > 0) {
+        alsub_status st = alloc_crease(T, T.ctmp, 2 * maxcap, s);
+        if (st) return st;
+    }
+    for (int l = 1; l <= levels; l++) {
+        LevelBuf &B = T.L[l];
+        AL(B.fv, B.nnz);
+        if (l < levels) {
+            if (M.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);
+            AL(B.tw, B.nnz);
+        }
+    }
+    long long vmax = 0;
+    for (int l = 1; l < levels; l++) vmax = std::max(vmax, T.L[l].V);
+    T.scratch_bytes = vmax > 0 ? 2 * 3 * sizeof(float) * (size_t)vmax : 0;
+    if (T.scratch_bytes) AL(*(char **)&T.scratch, T.scratch_bytes);
+    return ALSUB_OK;
+}
+
+void step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
+    if (T.scheme == ALSUB_CATMULL_CLARK) cc_step(T, l, topo, helpers, P, Pn, s);
+    else if (T.scheme == ALSUB_LOOP) loop_step(T, l, topo, helpers, P, Pn, s);
+    else sqrt3_step(T, l, topo, helpers, P, Pn, s);
+}
+
+// Ping-pong buffers of the intermediate levels.
+void level_buffers(TopoImpl &T, const float *P0, float *PL, void *scratch, int l, const float **in,
+                   float **out) {
+    float *buf = scratch ? (float *)scratch : T.scratch;
+    size_t half = T.scratch_bytes / (2 * sizeof(float));
+    *in = l == 0 ? P0 : buf + half * ((l - 1) & 1);
+    *out = l == T.levels - 1 ? PL : buf + half * (l & 1);
+}
+
+alsub_status finish(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    return ALSUB_OK;
+}
+
+// Event k (0 .. levels + 1) of the current timed call, or nothing when timing is off.
+void mark(TopoImpl &T, int k, cudaStream_t s) {
+    if (!T.tcap || T.tcalls >= T.tcap) return;
+    cudaEventRecord(T.tev[(size_t)T.tcalls * (T.levels + 2) + k], s);
+}
+
+void free_events(TopoImpl &T) {
+    for (cudaEvent_t e : T.tev) cudaEventDestroy(e);
+    T.tev.clear();
+    T.tcap = 0;
+    T.tcalls = 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *alsub_last_error(void) { return g_err.c_str(); }
+
+const char *alsub_status_string(alsub_status s) {
+    switch (s) {
+        case ALSUB_OK: return "ALSUB_OK";
+        case ALSUB_ERR_INVALID_ARG: return "ALSUB_ERR_INVALID_ARG";
+        case ALSUB_ERR_NONMANIFOLD: return "ALSUB_ERR_NONMANIFOLD";
+        case ALSUB_ERR_UNSUPPORTED: return "ALSUB_ERR_UNSUPPORTED";
+        case ALSUB_ERR_OOM: return "ALSUB_ERR_OOM";
+        case ALSUB_ERR_TIMEOUT: return "ALSUB_ERR_TIMEOUT";
+        case ALSUB_ERR_DEVICE: return "ALSUB_ERR_DEVICE";
+        case ALSUB_ERR_BUSY: return "ALSUB_ERR_BUSY";
+        case ALSUB_ERR_NOT_READY: return "ALSUB_ERR_NOT_READY";
+    }
+    return "ALSUB_ERR_UNKNOWN";
+}
+
+alsub_status alsub_copy(void *dst, const void *src, size_t bytes, void *stream) {
+    if (bytes == 0) return ALSUB_OK;
+    if (!dst || !src) return fail(ALSUB_ERR_INVALID_ARG, "NULL buffer");
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, s));
+    CK(cudaStreamSynchronize(s));
+    return ALSUB_OK;
+}
+
+alsub_status alsub_plan(alsub_scheme scheme, int64_t V, int64_t F, int64_t nnz, int32_t levels,
+                        int64_t *counts) {
+    if (scheme < ALSUB_CATMULL_CLARK || scheme > ALSUB_SQRT3) return fail(ALSUB_ERR_INVALID_ARG, "bad scheme");
+    if (V <= 0 || F <= 0 || nnz < 3 * F || levels < 0 || !counts)
+        return fail(ALSUB_ERR_INVALID_ARG, "bad counts");
+    if (scheme != ALSUB_CATMULL_CLARK && nnz != 3 * F)
+        return fail(ALSUB_ERR_INVALID_ARG, "Loop and sqrt(3) need a triangle mesh");
+    if (nnz % 2) return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
+    if (V > kI32 || F > kI32 || nnz > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "counts exceed int32");
+    long long c[4] = {V, F, nnz, nnz / 2};
+    for (int l = 0; l <= levels; l++) {
+        for (int i = 0; i < 4; i++) counts[4 * l + i] = c[i];
+        if (l == levels) break;
+        long long o[4];
+        if (!next_counts(scheme, c[0], c[1], c[2], c[3], o))
+            return fail(ALSUB_ERR_UNSUPPORTED, "level %d exceeds int32 counts", l + 1);
+        memcpy(c, o, sizeof(c));
+    }
+    return ALSUB_OK;
+}
+
+alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const int32_t *off_h,
+                               const int32_t *fv_h, int32_t K, const int32_t *cv_h,
+                               const float *cs_h, void *stream, alsub_mesh_t *out) {
+    if (!out) return fail(ALSUB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (scheme < ALSUB_CATMULL_CLARK || scheme > ALSUB_SQRT3) return fail(ALSUB_ERR_INVALID_ARG, "bad scheme");
+    if (V <= 0 || F <= 0 || !fv_h || K < 0 || (K > 0 && (!cv_h || !cs_h)))
+        return fail(ALSUB_ERR_INVALID_ARG, "bad mesh arguments");
+    const int order = scheme == ALSUB_CATMULL_CLARK ? 4 : 3;
+    std::vector<int32_t> off(F + 1);
+    if (off_h) {
+        if (off_h[0] != 0) return fail(ALSUB_ERR_INVALID_ARG, "face_offsets[0] must be 0");
+        for (int r = 0; r < F; r++) {
+            long long c = (long long)off_h[r + 1] - off_h[r];
+            if (c < 3) return fail(ALSUB_ERR_INVALID_ARG, "face %d has order %lld < 3", r, c);
+            if (scheme != ALSUB_CATMULL_CLARK && c != 3)
+                return fail(ALSUB_ERR_INVALID_ARG, "face %d is not a triangle", r);
+        }
+        memcpy(off.data(), off_h, sizeof(int32_t) * (F + 1));
+    } else {
+        if ((long long)F * order > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "counts exceed int32");
+        for (int r = 0; r <= F; r++) off[r] = r * order;
+    }
+    const long long nnz = off[F];
+    if (nnz % 2) return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
+    std::vector<int> used(V, 0), mark(V, -1);
+    for (int r = 0; r < F; r++) {
+        for (int x = off[r]; x < off[r + 1]; x++) {
+            int v = fv_h[x];
+            if (v < 0 || v >= V) return fail(ALSUB_ERR_INVALID_ARG, "face %d: vertex id %d out of range", r, v);
+            if (mark[v] == r) return fail(ALSUB_ERR_INVALID_ARG, "face %d repeats vertex %d", r, v);
+            mark[v] = r;
+            used[v] = 1;
+        }
+    }
+    for (int v = 0; v < V; v++)
+        if (!used[v]) return fail(ALSUB_ERR_INVALID_ARG, "vertex %d is in no face", v);
+    std::vector<int32_t> cv;
+    std::vector<float> cs;
+    float smax = 0.f;
+    for (int i = 0; i < K; i++) {
+        int a = cv_h[2 * i], b = cv_h[2 * i + 1];
+        float sg = cs_h[i];
+        if (a < 0 || a >= V || b < 0 || b >= V || a == b)
+            return fail(ALSUB_ERR_INVALID_ARG, "crease %d: bad endpoints (%d, %d)", i, a, b);
+        if (!(sg >= 0.f)) return fail(ALSUB_ERR_INVALID_ARG, "crease %d: sharpness must be >= 0", i);
+        if (sg == 0.f) continue;
+        cv.push_back(a); cv.push_back(b); cs.push_back(sg);
+        smax = std::max(smax, sg);
+    }
+    alsub_mesh_s *h = new (std::nothrow) alsub_mesh_s();
+    if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
+    MeshImpl &M = h->m;
+    M.scheme = scheme; M.V = V; M.F = F; M.nnz = (int)nnz; M.K = scheme == ALSUB_SQRT3 ? 0 : (int)cs.size();
+    M.sigma_max = smax;
+    M.stream = (cudaStream_t)stream;
+    cudaStream_t s = M.stream;
+    upload_weight_tables();
+    auto cleanup = [&]() {
+        cudaFreeAsync(M.d_off, s); cudaFreeAsync(M.d_fv, s);
+        if (M.d_cv) cudaFreeAsync(M.d_cv, s);
+        if (M.d_cs) cudaFreeAsync(M.d_cs, s);
+        delete h;
+    };
+    cudaError_t e = cudaMallocAsync(&M.d_off, sizeof(int) * (F + 1), s);
+    if (e == cudaSuccess) e = cudaMallocAsync(&M.d_fv, sizeof(int) * nnz, s);
+    if (e == cudaSuccess && M.K) e = cudaMallocAsync(&M.d_cv, sizeof(int) * 2 * M.K, s);
+    if (e == cudaSuccess && M.K) e = cudaMallocAsync(&M.d_cs, sizeof(float) * M.K, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_off, off.data(), sizeof(int) * (F + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_fv, fv_h, sizeof(int) * nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cv, cv.data(), sizeof(int) * 2 * M.K, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cs, cs.data(), sizeof(float) * M.K, cudaMemcpyHostToDevice, s);
+    // the host vectors die on return: make the copies complete first
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cleanup();
+        return cuda_fail(e, "mesh upload");
+    }
+    *out = h;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_mesh_destroy(alsub_mesh_t h) {
+    if (!h) return ALSUB_OK;
+    MeshImpl &M = h->m;
+    cudaFreeAsync(M.d_off, M.stream);
+    cudaFreeAsync(M.d_fv, M.stream);
+    if (M.d_cv) cudaFreeAsync(M.d_cv, M.stream);
+    if (M.d_cs) cudaFreeAsync(M.d_cs, M.stream);
+    delete h;
+    return finish("alsub_mesh_destroy");
+}
+
+alsub_status alsub_topology_create(alsub_mesh_t mesh, int32_t levels, void *stream,
+                                   alsub_topology_t *out) {
+    if (!mesh || !out || levels < 0) return fail(ALSUB_ERR_INVALID_ARG, "bad topology arguments");
+    *out = nullptr;
+    alsub_topology_s *h = new (std::nothrow) alsub_topology_s();
+    if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    alsub_status st = topo_alloc(h->t, mesh->m, levels, s);
+    if (st != ALSUB_OK) {
+        h->t.stream = s;
+        free_topo(h->t);
+        delete h;
+        return st;
+    }
+    st = finish("topology allocation");
+    if (st != ALSUB_OK) { free_topo(h->t); delete h; return st; }
+    *out = h;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stream,
+                                   alsub_topology_t *out) {
+    alsub_status st = alsub_topology_create(mesh, levels, stream, out);
+    if (st != ALSUB_OK) return st;
+    TopoImpl &T = (*out)->t;
+    cudaStream_t s = (cudaStream_t)stream;
+    level0_build(T, s);
+    for (int l = 0; l < levels; l++) {
+        step(T, l, true, l + 1 < levels, nullptr, nullptr, s);
+        crease_inherit(T, l, s);
+    }
+    T.built = true;
+    return finish("alsub_refine_topology");
+}
+
+alsub_status alsub_topology_status(alsub_topology_t h) {
+    if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL topology");
+    TopoImpl &T = h->t;
+    int st = 0;
+    cudaError_t e = cudaMemcpyAsync(&st, T.status, sizeof(int), cudaMemcpyDeviceToHost, T.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(T.stream);
+    if (e != cudaSuccess) return cuda_fail(e, "alsub_topology_status");
+    if (st) return fail((alsub_status)st, "device reported %s", alsub_status_string((alsub_status)st));
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_level(alsub_topology_t h, int32_t level, int64_t *V, int64_t *F,
+                                  int64_t *nnz, int64_t *E, const int32_t **off, const int32_t **fv) {
+    if (!h || level < 0 || level > h->t.levels) return fail(ALSUB_ERR_INVALID_ARG, "bad level");
+    const LevelBuf &B = h->t.L[level];
+    if (V) *V = B.V;
+    if (F) *F = B.F;
+    if (nnz) *nnz = B.nnz;
+    if (E) *E = B.E;
+    if (off) *off = level == 0 ? h->t.mesh->d_off : nullptr;
+    if (fv) *fv = B.fv;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_creases(alsub_topology_t h, int32_t level, int32_t *K,
+                                    const int32_t **cv, const float **cs) {
+    if (!h || level < 0 || level > h->t.levels || !K) return fail(ALSUB_ERR_INVALID_ARG, "bad level");
+    TopoImpl &T = h->t;
+    const CreaseList &C = T.L[level].cr;
+    int k = 0;
+    if (C.count) {
+        cudaError_t e = cudaMemcpyAsync(&k, C.count, sizeof(int), cudaMemcpyDeviceToHost, T.stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(T.stream);
+        if (e != cudaSuccess) return cuda_fail(e, "alsub_topology_creases");
+    }
+    *K = C.cap > 0 ? k : 0;
+    if (cv) *cv = C.verts;
+    if (cs) *cs = C.sig;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_set_timing(alsub_topology_t h, int32_t capacity) {
+    if (!h || capacity < 0) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    TopoImpl &T = h->t;
+    CK(cudaStreamSynchronize(T.stream));
+    free_events(T);
+    if (capacity == 0) return ALSUB_OK;
+    size_t n = (size_t)capacity * (T.levels + 2);
+    T.tev.resize(n);
+    for (size_t i = 0; i < n; i++) {
+        cudaError_t e = cudaEventCreate(&T.tev[i]);
+        if (e != cudaSuccess) {
+            T.tev.resize(i);
+            free_events(T);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    T.tcap = capacity;
+    T.tcalls = 0;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_timings(alsub_topology_t h, double *ms, int32_t *calls, int64_t *launches) {
+    if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL topology");
+    TopoImpl &T = h->t;
+    if (launches) *launches = T.launches;
+    T.launches = 0;
+    int n = std::min(T.tcalls, T.tcap);
+    bool overflow = T.tcalls > T.tcap;
+    if (ms) for (int k = 0; k <= T.levels; k++) ms[k] = 0.0;
+    for (int c = 0; c < n; c++) {
+        size_t b = (size_t)c * (T.levels + 2);
+        for (int k = 0; k <= T.levels; k++) {
+            CK(cudaEventSynchronize(T.tev[b + k + 1]));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, T.tev[b + k], T.tev[b + k + 1]));
+            if (ms) ms[k] += t;
+        }
+    }
+    if (calls) *calls = n;
+    T.tcalls = 0;
+    if (overflow) return fail(ALSUB_ERR_INVALID_ARG, "more timed calls than the timing capacity");
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_destroy(alsub_topology_t h) {
+    if (!h) return ALSUB_OK;
+    free_events(h->t);
+    free_topo(h->t);
+    delete h;
+    return finish("alsub_topology_destroy");
+}
+
+alsub_status alsub_refine_vertices_scratch_bytes(alsub_topology_t h, size_t *bytes) {
+    if (!h || !bytes) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    *bytes = h->t.scratch_bytes;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_refine_vertices(alsub_topology_t h, const float *P0, float *PL, void *scratch,
+                                   void *stream) {
+    if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    TopoImpl &T = h->t;
+    if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (T.levels == 0) {
+        CK(cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s));
+        return ALSUB_OK;
+    }
+    mark(T, 0, s);
+    mark(T, 1, s);
+    for (int l = 0; l < T.levels; l++) {
+        const float *in;
+        float *out;
+        level_buffers(T, P0, PL, scratch, l, &in, &out);
+        step(T, l, false, false, in, out, s);
+        crease_fix(T, l, in, out, s);
+        mark(T, l + 2, s);
+    }
+    if (T.tcap) T.tcalls++;
+    return finish("alsub_refine_vertices");
+}
+
+alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, void *scratch,
+                             void *stream) {
+    if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    TopoImpl &T = h->t;
+    cudaStream_t s = (cudaStream_t)stream;
+    mark(T, 0, s);
+    level0_build(T, s);
+    mark(T, 1, s);
+    if (T.levels == 0) {
+        CK(cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s));
+        if (T.tcap) T.tcalls++;
+        T.built = true;
+        return finish("alsub_subdivide");
+    }
+    for (int l = 0; l < T.levels; l++) {
+        const float *in;
+        float *out;
+        level_buffers(T, P0, PL, scratch, l, &in, &out);
+        step(T, l, true, l + 1 < T.levels, in, out, s);
+        crease_fix(T, l, in, out, s);
+        crease_inherit(T, l, s);
+        mark(T, l + 2, s);
+    }
+    if (T.tcap) T.tcalls++;
+    T.built = true;
+    return finish("alsub_subdivide");
+}
+
+}  // extern "C"

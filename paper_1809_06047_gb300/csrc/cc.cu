@@ -1,0 +1,214 @@
+// Catmull-Clark refinement step (Sec. 3.2), one thread per parent face.
+//
+// Build (Fig. module_core, left): the child face table M_{l+1} (Sec. 3.2 "Topology refinement":
+// corner x of face r becomes quad x = [v_x, |v|+|f|+e(x), |v|+r, |v|+|f|+e(prev x)]) and the
+// per-corner E and F of level l+1, derived analytically from level l's:
+//   child edge ids: the halves of parent edge e are 2e (at the owner's start vertex) and 2e+1;
+//                   the edge from face point r to the edge point of corner c is 2E + c;
+//   child twins:    corner 4c+0 <-> 4 next(tw(c)) + 3, 4c+1 <-> 4 next(c) + 2.
+// On levels >= 1 every face is a quad (the reduced mesh matrix of Sec. 4.1), so M, E and F are
+// int4 rows and corner x of face r is 4r + k.
+//
+// Eval (Fig. module_core, right), the mapped SpMVs fused into one pass:
+//   face point   f = M^T P with val -> 1/c (Eq. spla_fp);
+//   edge point   (p_k + p_l + f_r + f_s) / 4 for the corners that own their edge, with f_s
+//                recomputed from the twin's face row instead of being re-read;
+//   vertex point s1 + s2 + s3 = (1 - 2/n) p + 1/n^2 sum p_j + 1/n^2 sum f_j (Eq. pos_update in
+//                its split form) gathered by the one corner designated for the vertex, walking the
+//                ring x <- twin(prev(x)). The gather replaces the paper's atomic scatter (direct
+//                mapped SpMV, Sec. 4.3) so that results are bit-reproducible.
+#include "common.cuh"
+#include "internal.h"
+
+namespace alsub {
+
+namespace {
+
+struct CCArgs {
+    int l;                        // parent level
+    int V, F, E;                  // parent counts
+    const int *fv, *ce, *tw;      // parent face table / edge ids / twins (flat, per corner)
+    Level0 z;
+    const float *P;               // parent positions
+    float *Pn;                    // child positions
+    int *fvn, *cen, *twn;         // child face table / edge ids / twins
+    int *status;
+};
+
+// Is corner x of level l the designated corner of its start vertex? Follows the vertex back to
+// the level where it was created: an old vertex inherits from its parent corner, the edge point
+// of parent edge e is designated at the child of e's owner corner, the face point of parent face
+// r at the child of r's first corner.
+__device__ __forceinline__ bool cc_vown(int l, int x, const Level0 &z) {
+    while (l > 0) {
+        int k = x & 3, c = x >> 2;
+        if (k == 0) { x = c; --l; continue; }
+        if (k == 3) return false;
+        if (k == 1) return l > 1 ? ((c & 3) < 2) : (__ldg(z.own + c) != 0);
+        return l > 1 ? ((c & 3) == 0) : (c == __ldg(z.off + __ldg(z.cf + c)));
+    }
+    return __ldg(z.vc + __ldg(z.fv + x)) == x;
+}
+
+__device__ __forceinline__ float3 face_point_l0(const Level0 &z, const float *P, int g) {
+    int s = __ldg(z.off + g), c = __ldg(z.off + g + 1) - s;
+    float3 acc = f3(0.f, 0.f, 0.f);
+    for (int j = 0; j < c; j++) acc += ldp(P, __ldg(z.fv + s + j));
+    return (1.0f / (float)c) * acc;
+}
+
+__device__ __forceinline__ int4 ld4(const int *p) { return __ldg(reinterpret_cast<const int4 *>(p)); }
+__device__ __forceinline__ void st4(int *p, int4 v) { *reinterpret_cast<int4 *>(p) = v; }
+__device__ __forceinline__ int comp(int4 v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.F || failed(a.status)) return;
+    const Level0 &z = a.z;
+    const int s = __ldg(z.off + r), c = __ldg(z.off + r + 1) - s;
+    const int VF = a.V + a.F, E2 = 2 * a.E;
+    if (TOPO || HELP) {
+        for (int j = 0; j < c; j++) {
+            int x = s + j, p = (j == 0) ? s + c - 1 : x - 1;
+            int ex = __ldg(z.ce + x), ep = __ldg(z.ce + p);
+            if (TOPO) st4(a.fvn + 4 * (size_t)x, make_int4(__ldg(z.fv + x), VF + ex, a.V + r, VF + ep));
+            if (HELP) {
+                int ox = __ldg(z.own + x), op = __ldg(z.own + p);
+                st4(a.cen + 4 * (size_t)x, make_int4(2 * ex + (ox ? 0 : 1), E2 + x, E2 + p, 2 * ep + (op ? 1 : 0)));
+                st4(a.twn + 4 * (size_t)x, make_int4(4 * __ldg(z.nx + __ldg(z.tw + x)) + 3, 4 * __ldg(z.nx + x) + 2,
+                                                     4 * p + 1, 4 * __ldg(z.tw + p)));
+            }
+        }
+    }
+    if (EVAL) {
+        const float *P = a.P;
+        float3 fr = face_point_l0(z, P, r);
+        stp(a.Pn, a.V + r, fr);
+        for (int j = 0; j < c; j++) {
+            int x = s + j;
+            if (__ldg(z.own + x)) {
+                int t = __ldg(z.tw + x);
+                float3 fs = face_point_l0(z, P, __ldg(z.cf + t));
+                float3 ep = 0.25f * (ldp(P, __ldg(z.fv + x)) + ldp(P, __ldg(z.fv + __ldg(z.nx + x))) + fr + fs);
+                stp(a.Pn, VF + __ldg(z.ce + x), ep);
+            }
+        }
+        for (int j = 0; j < c; j++) {
+            int x = s + j, v = __ldg(z.fv + x);
+            if (__ldg(z.vc + v) != x) continue;
+            int y = x, n = 0;
+            float3 sp = f3(0.f, 0.f, 0.f), sf = f3(0.f, 0.f, 0.f);
+            do {
+                sf += face_point_l0(z, P, __ldg(z.cf + y));
+                sp += ldp(P, __ldg(z.fv + __ldg(z.nx + y)));
+                y = __ldg(z.tw + __ldg(z.pv + y));
+                n++;
+            } while (y != x && n < kMaxValence);
+            if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
+            float inv = 1.0f / (float)n;
+            stp(a.Pn, v, (1.0f - 2.0f * inv) * ldp(P, v) + (inv * inv) * (sp + sf));
+        }
+    }
+}
+
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.F || failed(a.status)) return;
+    const int VF = a.V + a.F, E2 = 2 * a.E, c0 = 4 * r;
+    const int4 v = ld4(a.fv + 4 * (size_t)r);
+    const int4 e = ld4(a.ce + 4 * (size_t)r);
+    int4 t = make_int4(0, 0, 0, 0);
+    if (HELP || EVAL) t = ld4(a.tw + 4 * (size_t)r);
+    if (TOPO) {
+        int *o = a.fvn + 16 * (size_t)r;
+        st4(o + 0, make_int4(v.x, VF + e.x, a.V + r, VF + e.w));
+        st4(o + 4, make_int4(v.y, VF + e.y, a.V + r, VF + e.x));
+        st4(o + 8, make_int4(v.z, VF + e.z, a.V + r, VF + e.y));
+        st4(o + 12, make_int4(v.w, VF + e.w, a.V + r, VF + e.z));
+    }
+    if (HELP) {
+        // corners 4r+0 and 4r+1 own their edges; 4r+2 and 4r+3 do not
+        int *o = a.cen + 16 * (size_t)r;
+        st4(o + 0, make_int4(2 * e.x, E2 + c0, E2 + c0 + 3, 2 * e.w));
+        st4(o + 4, make_int4(2 * e.y, E2 + c0 + 1, E2 + c0, 2 * e.x + 1));
+        st4(o + 8, make_int4(2 * e.z + 1, E2 + c0 + 2, E2 + c0 + 1, 2 * e.y + 1));
+        st4(o + 12, make_int4(2 * e.w + 1, E2 + c0 + 3, E2 + c0 + 2, 2 * e.z));
+        int *w = a.twn + 16 * (size_t)r;
+        st4(w + 0, make_int4(4 * quad_next(t.x) + 3, 4 * (c0 + 1) + 2, 4 * (c0 + 3) + 1, 4 * t.w));
+        st4(w + 4, make_int4(4 * quad_next(t.y) + 3, 4 * (c0 + 2) + 2, 4 * (c0 + 0) + 1, 4 * t.x));
+        st4(w + 8, make_int4(4 * quad_next(t.z) + 3, 4 * (c0 + 3) + 2, 4 * (c0 + 1) + 1, 4 * t.y));
+        st4(w + 12, make_int4(4 * quad_next(t.w) + 3, 4 * (c0 + 0) + 2, 4 * (c0 + 2) + 1, 4 * t.z));
+    }
+    if (EVAL) {
+        const float *P = a.P;
+        const float3 p0 = ldp(P, v.x), p1 = ldp(P, v.y), p2 = ldp(P, v.z), p3 = ldp(P, v.w);
+        const float3 fr = 0.25f * (p0 + p1 + p2 + p3);
+        stp(a.Pn, a.V + r, fr);
+        // edge points of the two owned edges (corners 4r and 4r+1)
+        {
+            int4 g = ld4(a.fv + 4 * (size_t)(t.x >> 2));
+            float3 fs = 0.25f * (ldp(P, g.x) + ldp(P, g.y) + ldp(P, g.z) + ldp(P, g.w));
+            stp(a.Pn, VF + e.x, 0.25f * (p0 + p1 + fr + fs));
+        }
+        {
+            int4 g = ld4(a.fv + 4 * (size_t)(t.y >> 2));
+            float3 fs = 0.25f * (ldp(P, g.x) + ldp(P, g.y) + ldp(P, g.z) + ldp(P, g.w));
+            stp(a.Pn, VF + e.y, 0.25f * (p1 + p2 + fr + fs));
+        }
+        // vertex points gathered by designated corners (k = 3 is never designated)
+#pragma unroll 1
+        for (int k = 0; k < 3; k++) {
+            int x = c0 + k;
+            if (!cc_vown(a.l, x, a.z)) continue;
+            int y = x, n = 0;
+            float3 sp = f3(0.f, 0.f, 0.f), sf = f3(0.f, 0.f, 0.f);
+            do {
+                int4 g = ld4(a.fv + 4 * (size_t)(y >> 2));
+                float3 q0 = ldp(P, g.x), q1 = ldp(P, g.y), q2 = ldp(P, g.z), q3 = ldp(P, g.w);
+                sf += 0.25f * (q0 + q1 + q2 + q3);
+                int kk = (y + 1) & 3;
+                sp += kk == 0 ? q0 : (kk == 1 ? q1 : (kk == 2 ? q2 : q3));
+                y = __ldg(a.tw + quad_prev(y));
+                n++;
+            } while (y != x && n < kMaxValence);
+            if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
+            float inv = 1.0f / (float)n;
+            int vk = comp(v, k);
+            float3 pk = k == 0 ? p0 : (k == 1 ? p1 : p2);
+            stp(a.Pn, vk, (1.0f - 2.0f * inv) * pk + (inv * inv) * (sp + sf));
+        }
+    }
+}
+
+template <bool T, bool H, bool E>
+void launch(const CCArgs &a, cudaStream_t s) {
+    if (a.l == 0) k_cc_l0<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
+    else k_cc_quad<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
+}
+
+}  // namespace
+
+void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
+    LevelBuf &A = T.L[l], &B = T.L[l + 1];
+    CCArgs a;
+    a.l = l;
+    a.V = (int)A.V; a.F = (int)A.F; a.E = (int)A.E;
+    a.fv = A.fv; a.ce = A.ce; a.tw = A.tw;
+    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+    a.P = P; a.Pn = Pn;
+    a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
+    a.status = T.status;
+    bool ev = P != nullptr;
+    if (topo || ev) T.launches += 1;
+    if (topo && helpers && ev) launch<true, true, true>(a, s);
+    else if (topo && helpers) launch<true, true, false>(a, s);
+    else if (topo && ev) launch<true, false, true>(a, s);
+    else if (topo) launch<true, false, false>(a, s);
+    else if (ev) launch<false, false, true>(a, s);
+}
+
+}  // namespace alsub

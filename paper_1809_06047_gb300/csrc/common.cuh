@@ -1,0 +1,93 @@
+// Device-side helpers shared by the libalsub kernels (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "alsub.h"
+
+namespace alsub {
+
+// Largest vertex valence a ring walk follows before it reports ALSUB_ERR_UNSUPPORTED.
+constexpr int kMaxValence = 1024;
+constexpr int kBlock = 256;
+
+// Latch the first device-side error of a handle; later kernels test it and return early.
+__device__ __forceinline__ void set_status(int *st, int code) {
+    if (st) atomicCAS(st, 0, code);
+}
+__device__ __forceinline__ bool failed(const int *st) { return st && *(volatile const int *)st != 0; }
+
+__device__ __forceinline__ float3 f3(float x, float y, float z) { return make_float3(x, y, z); }
+__device__ __forceinline__ float3 operator+(float3 a, float3 b) { return f3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ float3 operator-(float3 a, float3 b) { return f3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ float3 operator*(float s, float3 a) { return f3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ float3 &operator+=(float3 &a, float3 b) { a.x += b.x; a.y += b.y; a.z += b.z; return a; }
+
+// Positions are packed float[3 * V].
+__device__ __forceinline__ float3 ldp(const float *__restrict__ P, int v) {
+    const float *p = P + 3 * (size_t)v;
+    return f3(__ldg(p), __ldg(p + 1), __ldg(p + 2));
+}
+// Plain (coherent) load: used where the same kernel, or an earlier one in the same stream,
+// wrote the value.
+__device__ __forceinline__ float3 ldp_rw(const float *P, int v) {
+    const float *p = P + 3 * (size_t)v;
+    return f3(p[0], p[1], p[2]);
+}
+__device__ __forceinline__ void stp(float *P, int v, float3 a) {
+    float *p = P + 3 * (size_t)v;
+    p[0] = a.x; p[1] = a.y; p[2] = a.z;
+}
+
+// Corner arithmetic of quads (levels >= 1 of Catmull-Clark) and triangles (Loop, sqrt(3)).
+__device__ __forceinline__ int quad_next(int x) { return (x & ~3) | ((x + 1) & 3); }
+__device__ __forceinline__ int quad_prev(int x) { return (x & ~3) | ((x + 3) & 3); }
+__device__ __forceinline__ int tri_next(int x) { int j = x % 3; return x - j + (j == 2 ? 0 : j + 1); }
+__device__ __forceinline__ int tri_prev(int x) { int j = x % 3; return x - j + (j == 0 ? 2 : j - 1); }
+
+// Level-0 (general polygon) adjacency, built on the device from the input face table.
+struct Level0 {
+    const int *off;   // F0 + 1 face offsets
+    const int *fv;    // nnz0 vertex of each corner
+    const int *cf;    // corner -> face
+    const int *nx;    // next corner in the face
+    const int *pv;    // previous corner in the face
+    const int *tw;    // twin corner (the corner of the same edge in the other face)
+    const int *ce;    // edge id of each corner
+    const int *own;   // 1 if the corner owns its edge (start vertex < end vertex)
+    const int *vc;    // designated (smallest) outgoing corner of each vertex
+};
+
+// Corner accessors used by the ring walks of the crease kernels. Each gives next / prev corner
+// in the face, twin, edge id and start vertex of a corner.
+struct AccL0 {
+    Level0 z;
+    __device__ int next(int x) const { return __ldg(z.nx + x); }
+    __device__ int prev(int x) const { return __ldg(z.pv + x); }
+    __device__ int twin(int x) const { return __ldg(z.tw + x); }
+    __device__ int edge(int x) const { return __ldg(z.ce + x); }
+    __device__ int vtx(int x) const { return __ldg(z.fv + x); }
+};
+struct AccQuad {
+    const int *fv, *tw, *ce;
+    __device__ int next(int x) const { return quad_next(x); }
+    __device__ int prev(int x) const { return quad_prev(x); }
+    __device__ int twin(int x) const { return __ldg(tw + x); }
+    __device__ int edge(int x) const { return __ldg(ce + x); }
+    __device__ int vtx(int x) const { return __ldg(fv + x); }
+};
+struct AccTri {
+    const int *fv, *tw, *ce;
+    __device__ int next(int x) const { return tri_next(x); }
+    __device__ int prev(int x) const { return tri_prev(x); }
+    __device__ int twin(int x) const { return __ldg(tw + x); }
+    __device__ int edge(int x) const { return __ldg(ce + x); }
+    __device__ int vtx(int x) const { return __ldg(fv + x); }
+};
+
+inline unsigned grid_for(long long n, int block = kBlock) {
+    long long g = (n + block - 1) / block;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+}  // namespace alsub

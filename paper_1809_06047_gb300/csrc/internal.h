@@ -1,0 +1,97 @@
+// Host-side structures of libalsub and the launchers each .cu file provides.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "alsub.h"
+
+namespace alsub {
+
+// The crease matrix C_l of one level (Sec. 3.3) as a compact list sorted by edge id.
+struct CreaseList {
+    int *edge = nullptr;   // edge id at this level
+    int *own = nullptr;    // corner that owns the edge
+    float *sig = nullptr;  // sharpness (> 0)
+    int *verts = nullptr;  // 2 endpoints per crease
+    int *count = nullptr;  // number of entries (device int)
+    long long cap = 0;     // host-side upper bound of the count
+};
+
+// One level of the refined mesh. fv is the reduced mesh matrix (face table); ce and tw are the
+// per-corner forms of the edge matrix E (Eq. CC_E) and face-adjacency matrix F (Eq. F).
+struct LevelBuf {
+    long long V = 0, F = 0, nnz = 0, E = 0;
+    int *fv = nullptr;
+    int *ce = nullptr;
+    int *tw = nullptr;
+    CreaseList cr;
+};
+
+struct MeshImpl {
+    alsub_scheme scheme;
+    int V = 0, F = 0, nnz = 0, K = 0;
+    float sigma_max = 0.f;     // largest input sharpness (inf allowed)
+    int *d_off = nullptr;      // F + 1
+    int *d_fv = nullptr;       // nnz
+    int *d_cv = nullptr;       // 2K
+    float *d_cs = nullptr;     // K
+    cudaStream_t stream = nullptr;
+};
+
+struct TopoImpl {
+    MeshImpl *mesh = nullptr;
+    alsub_scheme scheme;
+    int levels = 0;
+    std::vector<LevelBuf> L;     // levels + 1
+    // level-0 adjacency
+    int *cf0 = nullptr, *nx0 = nullptr, *pv0 = nullptr, *own0 = nullptr, *vc0 = nullptr;
+    int *eo0 = nullptr, *deg = nullptr, *voff = nullptr, *vfill = nullptr, *vbk = nullptr;
+    int *eid = nullptr, *cmap = nullptr, *e0count = nullptr;
+    int *status = nullptr;       // latched device error
+    // temporaries
+    void *scan_tmp = nullptr;
+    size_t scan_tmp_bytes = 0;
+    int *flags = nullptr;        // max(nnz0, E0, 2 * max crease cap) ints
+    int *pos = nullptr;          // scan output of flags, same size
+    CreaseList ctmp;             // 2 * max crease cap candidate children
+    float *scratch = nullptr;    // intermediate positions (two levels)
+    size_t scratch_bytes = 0;
+    std::vector<void *> allocs;  // everything above, freed on destroy
+    cudaStream_t stream = nullptr;
+    bool built = false;
+    // live timing (alsub_topology_set_timing) and launch count
+    int tcap = 0;
+    int tcalls = 0;
+    std::vector<cudaEvent_t> tev;
+    long long launches = 0;
+};
+
+// ---------------------------------------------------------------- launchers
+
+// Exclusive scan of n ints (elements at index >= *n_dev read as 0 when n_dev is given); the
+// total goes to *total when total is not null. tmp must hold scan_tmp_bytes(n) bytes.
+size_t scan_tmp_bytes(long long n);
+void scan_exclusive(const int *in, int *out, long long n, int *total, const int *n_dev, void *tmp,
+                    cudaStream_t s);
+
+// Level 0: corner maps, twins, ownership, edge numbering, crease list of level 0.
+void level0_build(TopoImpl &T, cudaStream_t s);
+
+// One refinement step from level l to l + 1. topo: emit the child face table; helpers: emit the
+// child's per-corner edge ids and twins; P/Pn: parent/child positions (null = no vertex eval).
+void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s);
+void loop_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s);
+void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s);
+
+// Creases at level l: overwrite crease vertex/edge points of level l + 1 (Fig. module_creases),
+// and inherit the crease list of level l + 1 (Sec. 3.3, count then fill).
+void crease_fix(TopoImpl &T, int l, const float *P, float *Pn, cudaStream_t s);
+void crease_inherit(TopoImpl &T, int l, cudaStream_t s);
+
+// Device-side constant tables (Loop beta_n, sqrt(3) alpha_n) filled once per process.
+void upload_weight_tables();
+
+}  // namespace alsub

@@ -1,0 +1,244 @@
+// Loop (Appendix B) and sqrt(3) (Appendix A) refinement steps, one thread per parent triangle.
+// Every level is a triangle mesh, so corner j of triangle r is 3r + j at every level (the reduced
+// mesh matrix of Sec. 4.1 with an implicit column pointer).
+//
+// Loop. Build: triangle (v0, v1, v2) with edge ids e_j of corners j -> children
+//   4r+0 = [v0, e0, e2], 4r+1 = [v1, e1, e0], 4r+2 = [v2, e2, e1], 4r+3 = [e0, e1, e2]
+// (edge point of edge e has id |v| + e). Child edges: halves 2e (at the owner's start) and 2e+1,
+// interior edge j (cutting corner j) 2E + 3r + j. Eval: edge point 3/8 (p_i + p_j) + 1/8 (p_k +
+// p_l) with the opposite vertices read through G = the twin's third vertex (Appendix B, matrix G);
+// vertex point (1 - n beta_n) p + beta_n sum p_j (Eq. loop_smooth) gathered around the ring.
+//
+// sqrt(3). Build: corner j of triangle r gives child 3r + j = [v_j, |v| + F(next, j), |v| + r]
+// (Appendix A, "Topology refinement"; F(l,k) is the face across the corner's edge, i.e. the twin's
+// face). Eval: face point = barycenter; vertex point (1 - alpha_n) p + alpha_n / n sum p_j
+// (Eq. sqrt2, alpha_n of Eq. alpha).
+#include <math.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace alsub {
+
+namespace {
+
+__constant__ float c_loop_beta[kMaxValence + 1];
+__constant__ float c_sqrt3_alpha[kMaxValence + 1];
+
+struct TriArgs {
+    int l;
+    int V, F, E;
+    const int *fv, *ce, *tw;
+    Level0 z;
+    const float *P;
+    float *Pn;
+    int *fvn, *cen, *twn;
+    int *status;
+};
+
+__device__ __forceinline__ bool loop_own(int l, int x, const Level0 &z) {
+    if (l == 0) return __ldg(z.own + x) != 0;
+    int g = x / 3, i = x - 3 * g;
+    return (g & 3) < 3 && i < 2;
+}
+
+// Designated corner of a vertex (see the Catmull-Clark step): old vertices inherit from the
+// corner-0 child of their parent corner, the edge point of parent edge e_j is designated at
+// corner 1 of child j of e_j's owner face.
+__device__ __forceinline__ bool loop_vown(int l, int x, const Level0 &z) {
+    while (l > 0) {
+        int g = x / 3, i = x - 3 * g, r = g >> 2, j = g & 3;
+        if (j == 3 || i == 2) return false;
+        if (i == 0) { x = 3 * r + j; --l; continue; }
+        return loop_own(l - 1, 3 * r + j, z);
+    }
+    return __ldg(z.vc + __ldg(z.fv + x)) == x;
+}
+
+__device__ __forceinline__ bool sqrt3_vown(int l, int x, const Level0 &z) {
+    while (l > 0) {
+        int c = x / 3, k = x - 3 * c;
+        if (k == 0) { x = c; --l; continue; }
+        if (k == 1) return false;
+        return c % 3 == 0;
+    }
+    return __ldg(z.vc + __ldg(z.fv + x)) == x;
+}
+
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.F || failed(a.status)) return;
+    const int c = 3 * r, V = a.V, E2 = 2 * a.E;
+    int vv[3], ee[3], tt[3];
+    bool ow[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        vv[j] = __ldg(a.fv + c + j);
+        ee[j] = __ldg(a.ce + c + j);
+        tt[j] = (HELP || EVAL) ? __ldg(a.tw + c + j) : 0;
+        ow[j] = loop_own(a.l, c + j, a.z);
+    }
+    if (TOPO) {
+        int *o = a.fvn + 12 * (size_t)r;
+        o[0] = vv[0]; o[1] = V + ee[0]; o[2] = V + ee[2];
+        o[3] = vv[1]; o[4] = V + ee[1]; o[5] = V + ee[0];
+        o[6] = vv[2]; o[7] = V + ee[2]; o[8] = V + ee[1];
+        o[9] = V + ee[0]; o[10] = V + ee[1]; o[11] = V + ee[2];
+    }
+    if (HELP) {
+        int *oe = a.cen + 12 * (size_t)r, *ot = a.twn + 12 * (size_t)r;
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            int jp = j == 0 ? 2 : j - 1;
+            oe[3 * j + 0] = 2 * ee[j] + (ow[j] ? 0 : 1);
+            oe[3 * j + 1] = E2 + c + j;
+            oe[3 * j + 2] = 2 * ee[jp] + (ow[jp] ? 1 : 0);
+            int s = tt[j] / 3, i = tt[j] - 3 * s;
+            ot[3 * j + 0] = 3 * (4 * s + (i == 2 ? 0 : i + 1)) + 2;
+            ot[3 * j + 1] = 3 * (4 * r + 3) + (j + 2) % 3;
+            int s2 = tt[jp] / 3, i2 = tt[jp] - 3 * s2;
+            ot[3 * j + 2] = 3 * (4 * s2 + i2) + 0;
+            oe[9 + j] = E2 + c + (j + 1) % 3;
+            ot[9 + j] = 3 * (4 * r + (j + 1) % 3) + 1;
+        }
+    }
+    if (EVAL) {
+        const float *P = a.P;
+        float3 p[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) p[j] = ldp(P, vv[j]);
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            if (!ow[j]) continue;
+            int d = __ldg(a.fv + tri_prev(tt[j]));
+            float3 ep = 0.375f * (p[j] + p[(j + 1) % 3]) + 0.125f * (p[(j + 2) % 3] + ldp(P, d));
+            stp(a.Pn, V + ee[j], ep);
+        }
+#pragma unroll 1
+        for (int j = 0; j < 3; j++) {
+            int x = c + j;
+            if (!loop_vown(a.l, x, a.z)) continue;
+            int y = x, n = 0;
+            float3 sp = f3(0.f, 0.f, 0.f);
+            do {
+                sp += ldp(P, __ldg(a.fv + tri_next(y)));
+                y = __ldg(a.tw + tri_prev(y));
+                n++;
+            } while (y != x && n < kMaxValence);
+            if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
+            float beta = c_loop_beta[n];
+            stp(a.Pn, vv[j], (1.0f - (float)n * beta) * p[j] + beta * sp);
+        }
+    }
+}
+
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_sqrt3(TriArgs a) {
+    int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.F || failed(a.status)) return;
+    const int c = 3 * r, V = a.V;
+    int vv[3], tt[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        vv[j] = __ldg(a.fv + c + j);
+        tt[j] = __ldg(a.tw + c + j);
+    }
+    if (TOPO) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            int *o = a.fvn + 3 * (size_t)(c + j);
+            o[0] = vv[j]; o[1] = V + tt[j] / 3; o[2] = V + r;
+        }
+    }
+    if (HELP) {
+#pragma unroll
+        for (int j = 0; j < 3; j++) {
+            int *o = a.twn + 3 * (size_t)(c + j);
+            int jp = j == 0 ? 2 : j - 1;
+            o[0] = 3 * tri_next(tt[j]) + 2;
+            o[1] = 3 * tt[j] + 1;
+            o[2] = 3 * tt[jp] + 0;
+        }
+    }
+    if (EVAL) {
+        const float *P = a.P;
+        float3 p[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) p[j] = ldp(P, vv[j]);
+        stp(a.Pn, V + r, (1.0f / 3.0f) * (p[0] + p[1] + p[2]));
+#pragma unroll 1
+        for (int j = 0; j < 3; j++) {
+            int x = c + j;
+            if (!sqrt3_vown(a.l, x, a.z)) continue;
+            int y = x, n = 0;
+            float3 sp = f3(0.f, 0.f, 0.f);
+            do {
+                sp += ldp(P, __ldg(a.fv + tri_next(y)));
+                y = __ldg(a.tw + tri_prev(y));
+                n++;
+            } while (y != x && n < kMaxValence);
+            if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
+            float al = c_sqrt3_alpha[n];
+            stp(a.Pn, vv[j], (1.0f - al) * p[j] + (al / (float)n) * sp);
+        }
+    }
+}
+
+TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
+    LevelBuf &A = T.L[l], &B = T.L[l + 1];
+    TriArgs a;
+    a.l = l;
+    a.V = (int)A.V; a.F = (int)A.F; a.E = (int)A.E;
+    a.fv = A.fv; a.ce = A.ce; a.tw = A.tw;
+    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+    a.P = P; a.Pn = Pn;
+    a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
+    a.status = T.status;
+    return a;
+}
+
+}  // namespace
+
+void upload_weight_tables() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        float beta[kMaxValence + 1], alpha[kMaxValence + 1];
+        beta[0] = alpha[0] = 0.f;
+        for (int n = 1; n <= kMaxValence; n++) {
+            double t = 0.375 + 0.25 * cos(2.0 * M_PI / n);
+            beta[n] = (float)((0.625 - t * t) / n);
+            alpha[n] = (float)((4.0 - 2.0 * cos(2.0 * M_PI / n)) / 9.0);
+        }
+        cudaMemcpyToSymbol(c_loop_beta, beta, sizeof(beta));
+        cudaMemcpyToSymbol(c_sqrt3_alpha, alpha, sizeof(alpha));
+    });
+}
+
+void loop_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
+    TriArgs a = make_args(T, l, P, Pn);
+    unsigned g = grid_for(a.F);
+    bool ev = P != nullptr;
+    if (topo || ev) T.launches += 1;
+    if (topo && helpers && ev) k_loop<true, true, true><<<g, kBlock, 0, s>>>(a);
+    else if (topo && helpers) k_loop<true, true, false><<<g, kBlock, 0, s>>>(a);
+    else if (topo && ev) k_loop<true, false, true><<<g, kBlock, 0, s>>>(a);
+    else if (topo) k_loop<true, false, false><<<g, kBlock, 0, s>>>(a);
+    else if (ev) k_loop<false, false, true><<<g, kBlock, 0, s>>>(a);
+}
+
+void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
+    TriArgs a = make_args(T, l, P, Pn);
+    unsigned g = grid_for(a.F);
+    bool ev = P != nullptr;
+    if (topo || ev) T.launches += 1;
+    if (topo && helpers && ev) k_sqrt3<true, true, true><<<g, kBlock, 0, s>>>(a);
+    else if (topo && helpers) k_sqrt3<true, true, false><<<g, kBlock, 0, s>>>(a);
+    else if (topo && ev) k_sqrt3<true, false, true><<<g, kBlock, 0, s>>>(a);
+    else if (topo) k_sqrt3<true, false, false><<<g, kBlock, 0, s>>>(a);
+    else if (ev) k_sqrt3<false, false, true><<<g, kBlock, 0, s>>>(a);
+}
+
+}  // namespace alsub

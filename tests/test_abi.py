@@ -1,0 +1,107 @@
+"""C-ABI checks that need no GPU: the library builds, loads and exports every symbol that
+include/*.h declares; host-side planning and validation reject bad input before any CUDA call."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1809_06047_gb300 import _lib, alsub, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(alsub_\w+)\s*\(", src))
+    return sorted(names)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = _lib.load()
+    declared = _declared()
+    assert len(declared) >= 15
+    missing = [n for n in declared if not hasattr(lib, n)]
+    assert not missing, missing
+    # the Python binding declares the same set, no more, no fewer
+    assert set(_lib.SIGNATURES) == set(declared)
+
+
+def test_status_strings():
+    lib = _lib.load()
+    assert lib.alsub_status_string(0) == b"ALSUB_OK"
+    assert lib.alsub_status_string(2) == b"ALSUB_ERR_NONMANIFOLD"
+
+
+@pytest.mark.parametrize("name", ["cc_torus16_L3", "cc_creased_torus96_L6", "loop_tri_torus128_L6",
+                                  "sqrt3_tri_torus128_L8"])
+def test_plan_closed_forms(name):
+    m = synth.workload(name)
+    levels = m["levels"]
+    counts = alsub.plan(m["scheme"], m["V"], m["F"], len(m["fv"]), levels)
+    # against the oracle's own counts on the first levels
+    ref = oracle.subdivide(m, min(levels, 2), m["scheme"], keep_all=True)
+    for l, d in enumerate(ref):
+        assert tuple(counts[l]) == (d["V"], d["F"], d["nnz"], d["E"])
+    if name == "cc_creased_torus96_L6":
+        assert counts[6][1] == 37_750_784
+    if name == "loop_tri_torus128_L6":
+        assert counts[6][1] == 134_217_728 and counts[6][0] == 67_108_864
+    if name == "sqrt3_tri_torus128_L8":
+        assert counts[8][1] == 214_990_848 and counts[8][0] == 107_495_424
+
+
+def test_plan_rejects():
+    with pytest.raises(alsub.AlsubError) as e:
+        alsub.plan("cc", 8, 6, 23, 1)              # odd corner count: open mesh
+    assert e.value.status == 3
+    with pytest.raises(alsub.AlsubError) as e:
+        alsub.plan("loop", 8, 6, 24, 1)            # not triangles
+    assert e.value.status == 1
+    with pytest.raises(alsub.AlsubError) as e:
+        alsub.plan("cc", 1 << 20, 1 << 20, 1 << 22, 12)   # beyond int32
+    assert e.value.status == 3
+
+
+def _create(scheme, V, F, fv, off=None, cv=None, cs=None):
+    return alsub.Mesh(scheme, V, F, fv, off, cv, cs, stream=0)
+
+
+def test_mesh_validation_on_host():
+    c = synth.cube()
+    with pytest.raises(alsub.AlsubError) as e:           # vertex id out of range
+        _create("cc", 8, 6, np.where(c["fv"] == 7, 8, c["fv"]), c["off"])
+    assert e.value.status == 1
+    fv = c["fv"].copy()
+    fv[1] = fv[0]                                        # repeated vertex in a face
+    with pytest.raises(alsub.AlsubError) as e:
+        _create("cc", 8, 6, fv, c["off"])
+    assert e.value.status == 1
+    with pytest.raises(alsub.AlsubError) as e:           # unused vertex
+        _create("cc", 9, 6, c["fv"], c["off"])
+    assert e.value.status == 1
+    with pytest.raises(alsub.AlsubError) as e:           # Loop needs triangles
+        _create("loop", 8, 6, c["fv"], c["off"])
+    assert e.value.status == 1
+    with pytest.raises(alsub.AlsubError) as e:           # negative sharpness
+        _create("cc", 8, 6, c["fv"], c["off"], np.array([[0, 1]]), np.array([-1.0]))
+    assert e.value.status == 1
+    with pytest.raises(alsub.AlsubError) as e:           # NaN sharpness
+        _create("cc", 8, 6, c["fv"], c["off"], np.array([[0, 1]]), np.array([np.nan]))
+    assert e.value.status == 1
+    with pytest.raises(alsub.AlsubError) as e:           # open mesh: odd corner count
+        t = synth.tetrahedron()
+        _create("loop", 4, 3, t["fv"][:9], t["off"][:4])
+    assert e.value.status in (1, 3)
+
+
+def test_last_error_message():
+    lib = _lib.load()
+    out = np.zeros(8, np.int64)
+    st = lib.alsub_plan(7, 1, 1, 3, 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
+    assert st == 1 and b"scheme" in lib.alsub_last_error()
