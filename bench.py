@@ -43,6 +43,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="alsub", choices=["alsub", "reference"])
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
+    p.add_argument("--levels", type=int, default=None, help="override the workload's level count")
     p.add_argument("--no-cpu-baseline", action="store_true")
     return p.parse_args()
 
@@ -196,8 +197,10 @@ def main():
     from paper_1809_06047_gb300 import alsub
 
     m = synth.workload(args.workload)
+    if args.levels is not None:
+        m["levels"] = args.levels
     L, scheme = m["levels"], m["scheme"]
-    counts = alsub.plan(scheme, m["V"], m["F"], len(m["fv"]), L)
+    counts = [[int(x) for x in row] for row in alsub.plan(scheme, m["V"], m["F"], len(m["fv"]), L)]
     FL, VL = int(counts[L][1]), int(counts[L][0])
     M = alsub.Mesh.from_dict(m)
     T = alsub.Topology(M, L, build=False)
@@ -272,7 +275,8 @@ def main():
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.workload, "scheme": scheme, "levels": L,
+        "config": {"workload": args.workload if args.levels is None else f"{args.workload} (levels={L})",
+                   "scheme": scheme, "levels": L,
                    "control_faces": m["F"], "control_verts": m["V"], "creases": int(len(m["crease_sharp"])),
                    "refined_faces": FL, "refined_verts": VL, "path": "alsub_subdivide (dynamic topology)",
                    "l2": "no flush: per-step working set ~%.1f GB > 129 MB L2" % (pipe_bytes / 1e9),
@@ -290,7 +294,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(m, min(sample_levels(args.workload), L))
     if rank == 0:
-        print(json.dumps(out))
+        print(json.dumps(out, default=lambda o: o.item() if hasattr(o, "item") else str(o)))
     T.close()
     M.close()
     if dist is not None:

@@ -148,10 +148,17 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
         alsub_status st = alloc_crease(T, T.ctmp, 2 * maxcap, s);
         if (st) return st;
     }
+    // Per-corner edge ids and twins are stored for every level that a later step reads them from.
+    // The last Catmull-Clark step on a level >= 2 derives them from the parent level instead,
+    // unless creases (whose kernels walk rings through the stored arrays) are still alive there.
+    T.L[0].helpers = true;
     for (int l = 1; l <= levels; l++) {
         LevelBuf &B = T.L[l];
         AL(B.fv, B.nnz);
-        if (l < levels) {
+        B.helpers = l < levels;
+        if (M.scheme == ALSUB_CATMULL_CLARK && l == levels - 1 && l >= 2 && B.cr.cap == 0)
+            B.helpers = false;
+        if (B.helpers) {
             if (M.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);
             AL(B.tw, B.nnz);
         }
@@ -370,7 +377,7 @@ alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stre
     cudaStream_t s = (cudaStream_t)stream;
     level0_build(T, s);
     for (int l = 0; l < levels; l++) {
-        step(T, l, true, l + 1 < levels, nullptr, nullptr, s);
+        step(T, l, true, T.L[l + 1].helpers, nullptr, nullptr, s);
         crease_inherit(T, l, s);
     }
     T.built = true;
@@ -518,7 +525,7 @@ alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, voi
         const float *in;
         float *out;
         level_buffers(T, P0, PL, scratch, l, &in, &out);
-        step(T, l, true, l + 1 < T.levels, in, out, s);
+        step(T, l, true, T.L[l + 1].helpers, in, out, s);
         crease_fix(T, l, in, out, s);
         crease_inherit(T, l, s);
         mark(T, l + 2, s);

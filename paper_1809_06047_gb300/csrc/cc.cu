@@ -32,6 +32,8 @@ struct CCArgs {
     const float *P;               // parent positions
     float *Pn;                    // child positions
     int *fvn, *cen, *twn;         // child face table / edge ids / twins
+    const int *pce, *ptw;         // level l - 1 edge ids / twins, used when level l's are not stored
+    int Ep;                       // E of level l - 1
     int *status;
 };
 
@@ -184,10 +186,152 @@ __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// Levels >= 2: the four children 4R..4R+3 of a parent quad R sit in four adjacent lanes. Child
+// j is [a_j, b_j, c, b_{j-1}] with a_j the parent's corners, b_j its edge points and c its face
+// point, so the group holds the 3 x 3 block of vertices in registers and shares them (and its
+// face points) through width-4 shuffles instead of re-reading neighbour faces. The quad stencils
+// below are the mapped SpMVs of Sec. 3.2 specialised to all-quad rows (Sec. 4.3 "Specializations":
+// constant maps, reduced matrix):
+//   edge point  3/8 (p_a + p_b) + 1/16 (the four far vertices of the two faces)  (Eq. 2, f_r, f_s
+//               expanded), or (p_a + p_b + f_r + f_s) / 4 when both face points are in the group;
+//   vertex      (1 - 7/(4n)) p + 3/(2n^2) sum next_g + 1/(4n^2) sum opp_g over the incident quads
+//               g (Eq. pos_update with the face points expanded; n = 4 gives 1/64 [1 6 1; 6 36 6;
+//               1 6 1]).
+// The face point c and the edge points b_0, b_1 are gathered by the group itself (their rings are
+// known analytically: the four siblings, and two siblings plus the two children of the twin
+// corner); only vertices that existed on level l - 1 walk their ring through the twins.
+// DERIVE: level l's per-corner edge ids and twins are not stored; they are derived from the
+// parent level's (one int4 row per group), which saves writing and re-reading them on the last
+// level.
+
+__device__ __forceinline__ float3 shfl4(float3 v, int src) {
+    return f3(__shfl_sync(0xffffffffu, v.x, src, 4), __shfl_sync(0xffffffffu, v.y, src, 4),
+              __shfl_sync(0xffffffffu, v.z, src, 4));
+}
+__device__ __forceinline__ float3 sum4(float3 v) {
+    v += f3(__shfl_xor_sync(0xffffffffu, v.x, 1), __shfl_xor_sync(0xffffffffu, v.y, 1),
+            __shfl_xor_sync(0xffffffffu, v.z, 1));
+    v += f3(__shfl_xor_sync(0xffffffffu, v.x, 2), __shfl_xor_sync(0xffffffffu, v.y, 2),
+            __shfl_xor_sync(0xffffffffu, v.z, 2));
+    return v;
+}
+
+// Twin of corner y of level l >= 2 from the parent level's twins (the rule of the build step).
+__device__ __forceinline__ int derived_twin(const int *__restrict__ ptw, int y) {
+    int c = y >> 2;
+    switch (y & 3) {
+        case 0: return 4 * quad_next(__ldg(ptw + c)) + 3;
+        case 1: return 4 * quad_next(c) + 2;
+        case 2: return 4 * quad_prev(c) + 1;
+        default: return 4 * __ldg(ptw + quad_prev(c));
+    }
+}
+
+template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
+__global__ void __launch_bounds__(kBlock) k_cc_sib(CCArgs a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (failed(a.status)) return;
+    const bool live = r < a.F;                  // F is a multiple of 4: groups are whole
+    const int j = r & 3, R = r >> 2;
+    const int VF = a.V + a.F, E2 = 2 * a.E, c0 = 4 * r;
+    int4 v = make_int4(0, 0, 0, 0), e = v, t = v;
+    if (live) {
+        v = ld4(a.fv + 4 * (size_t)r);
+        if (DERIVE) {
+            const int4 pe = ld4(a.pce + 4 * (size_t)R), pt = ld4(a.ptw + 4 * (size_t)R);
+            const int jp = (j + 3) & 3, po = 4 * R + jp;
+            const int Ep2 = 2 * a.Ep;
+            e = make_int4(2 * comp(pe, j) + (j < 2 ? 0 : 1), Ep2 + r, Ep2 + po,
+                          2 * comp(pe, jp) + (jp < 2 ? 1 : 0));
+            t = make_int4(4 * quad_next(comp(pt, j)) + 3, 4 * quad_next(r) + 2, 4 * po + 1,
+                          4 * comp(pt, jp));
+        } else {
+            e = ld4(a.ce + 4 * (size_t)r);
+            if (HELP || EVAL) t = ld4(a.tw + 4 * (size_t)r);
+        }
+    }
+    if (TOPO && live) {
+        int *o = a.fvn + 16 * (size_t)r;
+        st4(o + 0, make_int4(v.x, VF + e.x, a.V + r, VF + e.w));
+        st4(o + 4, make_int4(v.y, VF + e.y, a.V + r, VF + e.x));
+        st4(o + 8, make_int4(v.z, VF + e.z, a.V + r, VF + e.y));
+        st4(o + 12, make_int4(v.w, VF + e.w, a.V + r, VF + e.z));
+    }
+    if (HELP && live) {
+        int *o = a.cen + 16 * (size_t)r;
+        st4(o + 0, make_int4(2 * e.x, E2 + c0, E2 + c0 + 3, 2 * e.w));
+        st4(o + 4, make_int4(2 * e.y, E2 + c0 + 1, E2 + c0, 2 * e.x + 1));
+        st4(o + 8, make_int4(2 * e.z + 1, E2 + c0 + 2, E2 + c0 + 1, 2 * e.y + 1));
+        st4(o + 12, make_int4(2 * e.w + 1, E2 + c0 + 3, E2 + c0 + 2, 2 * e.z));
+        int *w = a.twn + 16 * (size_t)r;
+        st4(w + 0, make_int4(4 * quad_next(t.x) + 3, 4 * (c0 + 1) + 2, 4 * (c0 + 3) + 1, 4 * t.w));
+        st4(w + 4, make_int4(4 * quad_next(t.y) + 3, 4 * (c0 + 2) + 2, 4 * (c0 + 0) + 1, 4 * t.x));
+        st4(w + 8, make_int4(4 * quad_next(t.z) + 3, 4 * (c0 + 3) + 2, 4 * (c0 + 1) + 1, 4 * t.y));
+        st4(w + 12, make_int4(4 * quad_next(t.w) + 3, 4 * (c0 + 0) + 2, 4 * (c0 + 2) + 1, 4 * t.z));
+    }
+    if (!EVAL) return;
+    const float *P = a.P;
+    float3 pa = f3(0.f, 0.f, 0.f), pb = pa, pc = pa;
+    if (live) {
+        pa = ldp(P, v.x);
+        pb = ldp(P, v.y);
+        if (j == 0) pc = ldp(P, v.z);
+    }
+    pc = shfl4(pc, 0);                              // parent face point c
+    const float3 pd = shfl4(pb, (j + 3) & 3);       // b_{j-1}
+    const float3 fr = 0.25f * (pa + pb + pc + pd);  // face point of child j
+    const float3 fn = shfl4(fr, (j + 1) & 3);       // face point of child j+1
+    const float3 pan = shfl4(pa, (j + 1) & 3);      // a_{j+1}
+    const float3 pbn = shfl4(pb, (j + 1) & 3);      // b_{j+1}
+    const float3 sa = sum4(pa), sb = sum4(pb);
+    if (!live) return;
+    stp(a.Pn, a.V + r, fr);
+    // interior edge (b_j, c) between children j and j+1
+    stp(a.Pn, VF + e.y, 0.25f * (pb + pc + fr + fn));
+    // boundary edge (a_j, b_j); across it lies F1 = [a_j, y, z, b_j], a child of the parent's
+    // neighbour (the twin corner of 4r is always corner 3 of F1)
+    const int s1 = t.x >> 2;
+    const int4 g1 = ld4(a.fv + 4 * (size_t)s1);
+    const float3 py = ldp(P, g1.y), pz = ldp(P, g1.z);
+    stp(a.Pn, VF + e.x, 0.375f * (pa + pb) + 0.0625f * (pc + pd + py + pz));
+    // face point c of the parent (valence 4): designated at child 0
+    if (j == 0) stp(a.Pn, v.z, 0.5625f * pc + 0.09375f * sb + 0.015625f * sa);
+    // edge point b_j of an owned parent edge (j < 2, valence 4): ring = children j, j+1 and the
+    // twin's two children F1 and F2 = [a_{j+1}, b_j, z, w]
+    if (j < 2) {
+        const int4 g2 = ld4(a.fv + 4 * (size_t)quad_prev(s1));
+        const float3 pw = ldp(P, g2.w);
+        stp(a.Pn, v.y, 0.5625f * pb + 0.09375f * (pc + pa + pz + pan) + 0.015625f * (pd + py + pw + pbn));
+    }
+    // a vertex of level l - 1: walk its ring
+    if (cc_vown(a.l, c0, a.z)) {
+        int y = c0, n = 0;
+        float3 sn = f3(0.f, 0.f, 0.f), so = sn;
+        do {
+            const int g = y >> 2, kk = y & 3;
+            const int4 q = g == r ? v : ld4(a.fv + 4 * (size_t)g);
+            sn += ldp(P, comp(q, (kk + 1) & 3));
+            so += ldp(P, comp(q, (kk + 2) & 3));
+            const int yp = quad_prev(y);
+            y = DERIVE ? derived_twin(a.ptw, yp) : __ldg(a.tw + yp);
+            n++;
+        } while (y != c0 && n < kMaxValence);
+        if (y != c0) {
+            set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+        } else {
+            const float inv = 1.0f / (float)n;
+            stp(a.Pn, v.x, (1.0f - 1.75f * inv) * pa + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so);
+        }
+    }
+}
+
 template <bool T, bool H, bool E>
-void launch(const CCArgs &a, cudaStream_t s) {
+void launch(const CCArgs &a, bool derive, cudaStream_t s) {
     if (a.l == 0) k_cc_l0<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else k_cc_quad<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
+    else if (a.l == 1) k_cc_quad<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
+    else if (derive) k_cc_sib<T, false, E, true><<<grid_for(a.F), kBlock, 0, s>>>(a);
+    else k_cc_sib<T, H, E, false><<<grid_for(a.F), kBlock, 0, s>>>(a);
 }
 
 }  // namespace
@@ -202,13 +346,20 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
+    // a level >= 2 without stored edge ids / twins derives them from its parent level
+    const bool derive = l >= 2 && !A.helpers;
+    if (derive) {
+        a.pce = T.L[l - 1].ce; a.ptw = T.L[l - 1].tw; a.Ep = (int)T.L[l - 1].E;
+    } else {
+        a.pce = nullptr; a.ptw = nullptr; a.Ep = 0;
+    }
     bool ev = P != nullptr;
     if (topo || ev) T.launches += 1;
-    if (topo && helpers && ev) launch<true, true, true>(a, s);
-    else if (topo && helpers) launch<true, true, false>(a, s);
-    else if (topo && ev) launch<true, false, true>(a, s);
-    else if (topo) launch<true, false, false>(a, s);
-    else if (ev) launch<false, false, true>(a, s);
+    if (topo && helpers && ev) launch<true, true, true>(a, derive, s);
+    else if (topo && helpers) launch<true, true, false>(a, derive, s);
+    else if (topo && ev) launch<true, false, true>(a, derive, s);
+    else if (topo) launch<true, false, false>(a, derive, s);
+    else if (ev) launch<false, false, true>(a, derive, s);
 }
 
 }  // namespace alsub

@@ -27,6 +27,7 @@ struct LevelBuf {
     int *fv = nullptr;
     int *ce = nullptr;
     int *tw = nullptr;
+    bool helpers = false;  // ce and tw are stored for this level
     CreaseList cr;
 };
 
