@@ -108,6 +108,7 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     T.scheme = M.scheme;
     T.levels = levels;
     T.stream = s;
+    if (levels >= kMaxLevels) return fail(ALSUB_ERR_UNSUPPORTED, "at most %d levels", kMaxLevels - 1);
     T.L.assign(levels + 1, LevelBuf());
     LevelBuf &L0 = T.L[0];
     L0.V = M.V; L0.F = M.F; L0.nnz = M.nnz; L0.E = M.nnz / 2;
@@ -165,7 +166,8 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     }
     long long vmax = 0;
     for (int l = 1; l < levels; l++) vmax = std::max(vmax, T.L[l].V);
-    T.scratch_bytes = vmax > 0 ? 2 * 3 * sizeof(float) * (size_t)vmax : 0;
+    // two intermediate levels in flight, positions padded to float4 rows
+    T.scratch_bytes = vmax > 0 ? 2 * 4 * sizeof(float) * (size_t)vmax : 0;
     if (T.scratch_bytes) AL(*(char **)&T.scratch, T.scratch_bytes);
     return ALSUB_OK;
 }

@@ -34,6 +34,8 @@ struct CCArgs {
     int *fvn, *cen, *twn;         // child face table / edge ids / twins
     const int *pce, *ptw;         // level l - 1 edge ids / twins, used when level l's are not stored
     int Ep;                       // E of level l - 1
+    const int *twl[kMaxLevels];   // stored twins of every level (null where not stored)
+    bool in4, out4;               // parent / child positions in padded float4 rows
     int *status;
 };
 
@@ -88,14 +90,14 @@ __global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
     if (EVAL) {
         const float *P = a.P;
         float3 fr = face_point_l0(z, P, r);
-        stp(a.Pn, a.V + r, fr);
+        stpv(a.Pn, a.V + r, fr, a.out4);
         for (int j = 0; j < c; j++) {
             int x = s + j;
             if (__ldg(z.own + x)) {
                 int t = __ldg(z.tw + x);
                 float3 fs = face_point_l0(z, P, __ldg(z.cf + t));
                 float3 ep = 0.25f * (ldp(P, __ldg(z.fv + x)) + ldp(P, __ldg(z.fv + __ldg(z.nx + x))) + fr + fs);
-                stp(a.Pn, VF + __ldg(z.ce + x), ep);
+                stpv(a.Pn, VF + __ldg(z.ce + x), ep, a.out4);
             }
         }
         for (int j = 0; j < c; j++) {
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
             } while (y != x && n < kMaxValence);
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
             float inv = 1.0f / (float)n;
-            stp(a.Pn, v, (1.0f - 2.0f * inv) * ldp(P, v) + (inv * inv) * (sp + sf));
+            stpv(a.Pn, v, (1.0f - 2.0f * inv) * ldp(P, v) + (inv * inv) * (sp + sf), a.out4);
         }
     }
 }
@@ -147,19 +149,19 @@ __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
     }
     if (EVAL) {
         const float *P = a.P;
-        const float3 p0 = ldp(P, v.x), p1 = ldp(P, v.y), p2 = ldp(P, v.z), p3 = ldp(P, v.w);
+        const float3 p0 = ldpv(P, v.x, a.in4), p1 = ldpv(P, v.y, a.in4), p2 = ldpv(P, v.z, a.in4), p3 = ldpv(P, v.w, a.in4);
         const float3 fr = 0.25f * (p0 + p1 + p2 + p3);
-        stp(a.Pn, a.V + r, fr);
+        stpv(a.Pn, a.V + r, fr, a.out4);
         // edge points of the two owned edges (corners 4r and 4r+1)
         {
             int4 g = ld4(a.fv + 4 * (size_t)(t.x >> 2));
-            float3 fs = 0.25f * (ldp(P, g.x) + ldp(P, g.y) + ldp(P, g.z) + ldp(P, g.w));
-            stp(a.Pn, VF + e.x, 0.25f * (p0 + p1 + fr + fs));
+            float3 fs = 0.25f * (ldpv(P, g.x, a.in4) + ldpv(P, g.y, a.in4) + ldpv(P, g.z, a.in4) + ldpv(P, g.w, a.in4));
+            stpv(a.Pn, VF + e.x, 0.25f * (p0 + p1 + fr + fs), a.out4);
         }
         {
             int4 g = ld4(a.fv + 4 * (size_t)(t.y >> 2));
-            float3 fs = 0.25f * (ldp(P, g.x) + ldp(P, g.y) + ldp(P, g.z) + ldp(P, g.w));
-            stp(a.Pn, VF + e.y, 0.25f * (p1 + p2 + fr + fs));
+            float3 fs = 0.25f * (ldpv(P, g.x, a.in4) + ldpv(P, g.y, a.in4) + ldpv(P, g.z, a.in4) + ldpv(P, g.w, a.in4));
+            stpv(a.Pn, VF + e.y, 0.25f * (p1 + p2 + fr + fs), a.out4);
         }
         // vertex points gathered by designated corners (k = 3 is never designated)
 #pragma unroll 1
@@ -170,7 +172,7 @@ __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
             float3 sp = f3(0.f, 0.f, 0.f), sf = f3(0.f, 0.f, 0.f);
             do {
                 int4 g = ld4(a.fv + 4 * (size_t)(y >> 2));
-                float3 q0 = ldp(P, g.x), q1 = ldp(P, g.y), q2 = ldp(P, g.z), q3 = ldp(P, g.w);
+                float3 q0 = ldpv(P, g.x, a.in4), q1 = ldpv(P, g.y, a.in4), q2 = ldpv(P, g.z, a.in4), q3 = ldpv(P, g.w, a.in4);
                 sf += 0.25f * (q0 + q1 + q2 + q3);
                 int kk = (y + 1) & 3;
                 sp += kk == 0 ? q0 : (kk == 1 ? q1 : (kk == 2 ? q2 : q3));
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
             float inv = 1.0f / (float)n;
             int vk = comp(v, k);
             float3 pk = k == 0 ? p0 : (k == 1 ? p1 : p2);
-            stp(a.Pn, vk, (1.0f - 2.0f * inv) * pk + (inv * inv) * (sp + sf));
+            stpv(a.Pn, vk, (1.0f - 2.0f * inv) * pk + (inv * inv) * (sp + sf), a.out4);
         }
     }
 }
@@ -228,8 +230,129 @@ __device__ __forceinline__ int derived_twin(const int *__restrict__ ptw, int y) 
     }
 }
 
+// Where the vertex at corner x (a corner 0) of level l >= 1 was created, if x is its designated
+// corner: kind 0 = a level-0 vertex (c = its designated level-0 corner), 1 = the edge point of the
+// level-(m-1) edge owned by corner c, 2 = the face point of the level-(m-1) face whose first corner
+// is c. kind -1: x is not the designated corner. Corner 0 of child x is the old vertex again, so
+// following x -> x / 4 walks back to the creation level m without touching memory.
+struct Birth {
+    int kind, m, c;
+};
+__device__ __forceinline__ Birth cc_birth(int l, int x, const Level0 &z) {
+    int m = l;
+    while (m > 0 && (x & 3) == 0) { x >>= 2; --m; }
+    if (m == 0) return Birth{__ldg(z.vc + __ldg(z.fv + x)) == x ? 0 : -1, 0, x};
+    const int k = x & 3, c = x >> 2;
+    bool des;
+    if (k == 3) des = false;
+    else if (k == 1) des = m > 1 ? ((c & 3) < 2) : (__ldg(z.own + c) != 0);
+    else des = m > 1 ? ((c & 3) == 0) : (c == __ldg(z.off + __ldg(z.cf + c)));
+    return Birth{des ? k : -1, m, c};
+}
+
+// Eval part of the sibling-group step (see above). All loads that do not depend on shuffled
+// values are issued before the first shuffle; the stores come last.
+template <bool DERIVE>
+__device__ __forceinline__ void sib_eval(const CCArgs &a, int r, bool live, int4 v, int4 e, int4 t) {
+    const float *__restrict__ P = a.P;
+    const int *__restrict__ fv = a.fv;
+    const Level0 &z = a.z;
+    const int j = r & 3, VF = a.V + a.F;
+    const int s1 = t.x >> 2;                       // F1 = [a_j, y, z, b_j] across edge (a_j, b_j)
+    int4 g1 = make_int4(0, 0, 0, 0), g2 = g1;
+    float3 pa = f3(0.f, 0.f, 0.f), pb = pa, pc = pa;
+    Birth b{-1, 0, 0};
+    if (live) {
+        g1 = ld4(fv + 4 * (size_t)s1);
+        if (j < 2) g2 = ld4(fv + 4 * (size_t)quad_prev(s1));   // F2 = [a_{j+1}, b_j, z, w]
+        pa = ldpv(P, v.x, true);
+        pb = ldpv(P, v.y, true);
+        if (j == 0) pc = ldpv(P, v.z, true);
+        b = cc_birth(a.l, 4 * r, z);
+    }
+    pc = shfl4(pc, 0);                              // parent face point c
+    const float3 pd = shfl4(pb, (j + 3) & 3);       // b_{j-1}
+    const float3 fr = 0.25f * (pa + pb + pc + pd);  // face point of child j
+    const float3 fn = shfl4(fr, (j + 1) & 3);       // face point of child j+1
+    const float3 pan = shfl4(pa, (j + 1) & 3);      // a_{j+1}
+    const float3 pbn = shfl4(pb, (j + 1) & 3);      // b_{j+1}
+    const float3 sa = sum4(pa), sb = sum4(pb);
+    if (!live) return;
+    const float3 py = ldpv(P, g1.y, true), pz = ldpv(P, g1.z, true);
+    const float3 pw = j < 2 ? ldpv(P, g2.w, true) : f3(0.f, 0.f, 0.f);
+    // a vertex that already existed on level l - 1: its ring on level l follows from its birth,
+    // so the rows of its n incident faces are loaded independently of each other
+    float3 vp_old = f3(0.f, 0.f, 0.f);
+    bool has_old = false;
+    if (b.kind >= 0) {
+        const int sh = 2 * (a.l - b.m - 1);        // ring corner y of level m -> face y << sh of level l
+        float3 sn = f3(0.f, 0.f, 0.f), so = sn;
+        int n = 0;
+        auto visit = [&](int y) {
+            const int4 q = ld4(fv + 4 * ((size_t)y << sh));   // the vertex is corner 0 of this face
+            sn += ldpv(P, q.y, true);
+            so += ldpv(P, q.z, true);
+            n++;
+        };
+        if (b.kind == 1 || (b.kind == 2 && b.m > 1)) {
+            // valence 4: the face point of a quad (its four children) or an edge point (the
+            // children of its owner corner c, of c's twin t and of their successors)
+            int y0, y1, y2, y3;
+            if (b.kind == 2) {
+                y0 = 4 * b.c + 2; y1 = y0 + 4; y2 = y0 + 8; y3 = y0 + 12;
+            } else {
+                int tt, nc, nt;
+                if (b.m > 1) {
+                    tt = __ldg(a.twl[b.m - 1] + b.c);
+                    nc = quad_next(b.c);
+                    nt = quad_next(tt);
+                } else {
+                    tt = __ldg(z.tw + b.c);
+                    nc = __ldg(z.nx + b.c);
+                    nt = __ldg(z.nx + tt);
+                }
+                y0 = 4 * b.c + 1; y1 = 4 * nt + 3; y2 = 4 * tt + 1; y3 = 4 * nc + 3;
+            }
+            visit(y0);
+            visit(y1);
+            visit(y2);
+            visit(y3);
+        } else if (b.kind == 2) {
+            // the face point of a level-0 polygon of order c
+            const int Q = __ldg(z.cf + b.c), s0 = __ldg(z.off + Q), c = __ldg(z.off + Q + 1) - s0;
+            for (int i = 0; i < c; i++) visit(4 * (s0 + i) + 2);
+        } else {
+            int y = b.c;
+            do {
+                visit(y);
+                y = __ldg(z.tw + __ldg(z.pv + y));
+            } while (y != b.c && n < kMaxValence);
+            if (y != b.c) {
+                set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                n = 0;
+            }
+        }
+        if (n > 0) {
+            const float inv = 1.0f / (float)n;
+            vp_old = (1.0f - 1.75f * inv) * pa + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so;
+            has_old = true;
+        }
+    }
+    stpv(a.Pn, a.V + r, fr, a.out4);
+    // interior edge (b_j, c) between children j and j+1
+    stpv(a.Pn, VF + e.y, 0.25f * (pb + pc + fr + fn), a.out4);
+    // boundary edge (a_j, b_j) shared with F1
+    stpv(a.Pn, VF + e.x, 0.375f * (pa + pb) + 0.0625f * (pc + pd + py + pz), a.out4);
+    // face point c of the parent (valence 4): designated at child 0
+    if (j == 0) stpv(a.Pn, v.z, 0.5625f * pc + 0.09375f * sb + 0.015625f * sa, a.out4);
+    // edge point b_j of an owned parent edge (j < 2, valence 4): ring = children j, j+1, F1, F2
+    if (j < 2)
+        stpv(a.Pn, v.y, 0.5625f * pb + 0.09375f * (pc + pa + pz + pan) + 0.015625f * (pd + py + pw + pbn), a.out4);
+    if (has_old) stpv(a.Pn, v.x, vp_old, a.out4);
+}
+
 template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
-__global__ void __launch_bounds__(kBlock) k_cc_sib(CCArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) k_cc_sib(CCArgs a) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (failed(a.status)) return;
     const bool live = r < a.F;                  // F is a multiple of 4: groups are whole
@@ -251,6 +374,7 @@ __global__ void __launch_bounds__(kBlock) k_cc_sib(CCArgs a) {
             if (HELP || EVAL) t = ld4(a.tw + 4 * (size_t)r);
         }
     }
+    if (EVAL) sib_eval<DERIVE>(a, r, live, v, e, t);
     if (TOPO && live) {
         int *o = a.fvn + 16 * (size_t)r;
         st4(o + 0, make_int4(v.x, VF + e.x, a.V + r, VF + e.w));
@@ -269,60 +393,6 @@ __global__ void __launch_bounds__(kBlock) k_cc_sib(CCArgs a) {
         st4(w + 4, make_int4(4 * quad_next(t.y) + 3, 4 * (c0 + 2) + 2, 4 * (c0 + 0) + 1, 4 * t.x));
         st4(w + 8, make_int4(4 * quad_next(t.z) + 3, 4 * (c0 + 3) + 2, 4 * (c0 + 1) + 1, 4 * t.y));
         st4(w + 12, make_int4(4 * quad_next(t.w) + 3, 4 * (c0 + 0) + 2, 4 * (c0 + 2) + 1, 4 * t.z));
-    }
-    if (!EVAL) return;
-    const float *P = a.P;
-    float3 pa = f3(0.f, 0.f, 0.f), pb = pa, pc = pa;
-    if (live) {
-        pa = ldp(P, v.x);
-        pb = ldp(P, v.y);
-        if (j == 0) pc = ldp(P, v.z);
-    }
-    pc = shfl4(pc, 0);                              // parent face point c
-    const float3 pd = shfl4(pb, (j + 3) & 3);       // b_{j-1}
-    const float3 fr = 0.25f * (pa + pb + pc + pd);  // face point of child j
-    const float3 fn = shfl4(fr, (j + 1) & 3);       // face point of child j+1
-    const float3 pan = shfl4(pa, (j + 1) & 3);      // a_{j+1}
-    const float3 pbn = shfl4(pb, (j + 1) & 3);      // b_{j+1}
-    const float3 sa = sum4(pa), sb = sum4(pb);
-    if (!live) return;
-    stp(a.Pn, a.V + r, fr);
-    // interior edge (b_j, c) between children j and j+1
-    stp(a.Pn, VF + e.y, 0.25f * (pb + pc + fr + fn));
-    // boundary edge (a_j, b_j); across it lies F1 = [a_j, y, z, b_j], a child of the parent's
-    // neighbour (the twin corner of 4r is always corner 3 of F1)
-    const int s1 = t.x >> 2;
-    const int4 g1 = ld4(a.fv + 4 * (size_t)s1);
-    const float3 py = ldp(P, g1.y), pz = ldp(P, g1.z);
-    stp(a.Pn, VF + e.x, 0.375f * (pa + pb) + 0.0625f * (pc + pd + py + pz));
-    // face point c of the parent (valence 4): designated at child 0
-    if (j == 0) stp(a.Pn, v.z, 0.5625f * pc + 0.09375f * sb + 0.015625f * sa);
-    // edge point b_j of an owned parent edge (j < 2, valence 4): ring = children j, j+1 and the
-    // twin's two children F1 and F2 = [a_{j+1}, b_j, z, w]
-    if (j < 2) {
-        const int4 g2 = ld4(a.fv + 4 * (size_t)quad_prev(s1));
-        const float3 pw = ldp(P, g2.w);
-        stp(a.Pn, v.y, 0.5625f * pb + 0.09375f * (pc + pa + pz + pan) + 0.015625f * (pd + py + pw + pbn));
-    }
-    // a vertex of level l - 1: walk its ring
-    if (cc_vown(a.l, c0, a.z)) {
-        int y = c0, n = 0;
-        float3 sn = f3(0.f, 0.f, 0.f), so = sn;
-        do {
-            const int g = y >> 2, kk = y & 3;
-            const int4 q = g == r ? v : ld4(a.fv + 4 * (size_t)g);
-            sn += ldp(P, comp(q, (kk + 1) & 3));
-            so += ldp(P, comp(q, (kk + 2) & 3));
-            const int yp = quad_prev(y);
-            y = DERIVE ? derived_twin(a.ptw, yp) : __ldg(a.tw + yp);
-            n++;
-        } while (y != c0 && n < kMaxValence);
-        if (y != c0) {
-            set_status(a.status, ALSUB_ERR_UNSUPPORTED);
-        } else {
-            const float inv = 1.0f / (float)n;
-            stp(a.Pn, v.x, (1.0f - 1.75f * inv) * pa + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so);
-        }
     }
 }
 
@@ -346,6 +416,8 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
+    a.in4 = l > 0;                     // only the caller's input level is packed xyz
+    a.out4 = l + 1 < T.levels;         // and the caller's output level
     // a level >= 2 without stored edge ids / twins derives them from its parent level
     const bool derive = l >= 2 && !A.helpers;
     if (derive) {
@@ -353,6 +425,7 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     } else {
         a.pce = nullptr; a.ptw = nullptr; a.Ep = 0;
     }
+    for (int m = 0; m < kMaxLevels; m++) a.twl[m] = m <= T.levels && T.L[m].helpers ? T.L[m].tw : nullptr;
     bool ev = P != nullptr;
     if (topo || ev) T.launches += 1;
     if (topo && helpers && ev) launch<true, true, true>(a, derive, s);

@@ -9,6 +9,8 @@ namespace alsub {
 
 // Largest vertex valence a ring walk follows before it reports ALSUB_ERR_UNSUPPORTED.
 constexpr int kMaxValence = 1024;
+// Largest number of refinement levels of one topology (int32 counts end far earlier in practice).
+constexpr int kMaxLevels = 16;
 constexpr int kBlock = 256;
 
 // Latch the first device-side error of a handle; later kernels test it and return early.
@@ -37,6 +39,28 @@ __device__ __forceinline__ float3 ldp_rw(const float *P, int v) {
 __device__ __forceinline__ void stp(float *P, int v, float3 a) {
     float *p = P + 3 * (size_t)v;
     p[0] = a.x; p[1] = a.y; p[2] = a.z;
+}
+
+// Positions of intermediate levels are padded to 16-byte rows (float4, w unused) so a vertex is one
+// vector load or store; the caller's input and output levels stay packed xyz. `s4` selects the
+// layout of a buffer.
+__device__ __forceinline__ float3 ldpv(const float *__restrict__ P, int v, bool s4) {
+    if (s4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(P) + v);
+        return f3(q.x, q.y, q.z);
+    }
+    return ldp(P, v);
+}
+__device__ __forceinline__ float3 ldpv_rw(const float *P, int v, bool s4) {
+    if (s4) {
+        const float4 q = reinterpret_cast<const float4 *>(P)[v];
+        return f3(q.x, q.y, q.z);
+    }
+    return ldp_rw(P, v);
+}
+__device__ __forceinline__ void stpv(float *P, int v, float3 a, bool s4) {
+    if (s4) reinterpret_cast<float4 *>(P)[v] = make_float4(a.x, a.y, a.z, 0.f);
+    else stp(P, v, a);
 }
 
 // Corner arithmetic of quads (levels >= 1 of Catmull-Clark) and triangles (Loop, sqrt(3)).

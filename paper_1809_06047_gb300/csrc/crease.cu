@@ -32,6 +32,7 @@ struct CreaseArgs {
     int *flags;
     const float *P;
     float *Pn;
+    bool in4, out4;             // level l / l + 1 positions in padded float4 rows
     int *status;
 };
 
@@ -95,11 +96,11 @@ __global__ void k_crease_fix(Acc A, CreaseArgs a) {
     float s = a.in.sig[i];
     int t = A.twin(o);
     int va = A.vtx(o), vb = A.vtx(t);
-    float3 pa = ldp(a.P, va), pb = ldp(a.P, vb);
+    float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
     float3 mid = 0.5f * (pa + pb);
     int idx = a.epbase + e;
-    if (s >= 1.0f) stp(a.Pn, idx, mid);
-    else stp(a.Pn, idx, (1.0f - s) * ldp_rw(a.Pn, idx) + s * mid);
+    if (s >= 1.0f) stpv(a.Pn, idx, mid, a.out4);
+    else stpv(a.Pn, idx, (1.0f - s) * ldpv_rw(a.Pn, idx, a.out4) + s * mid, a.out4);
     int starts[2] = {o, t};
     int verts[2] = {va, vb};
     for (int h = 0; h < 2; h++) {
@@ -108,9 +109,9 @@ __global__ void k_crease_fix(Acc A, CreaseArgs a) {
         int v = verts[h];
         float sv = r.S / (float)r.k;
         float w = sv < 1.0f ? sv : 1.0f;
-        float3 p = ldp(a.P, v);
-        float3 sharp = r.k == 2 ? 0.125f * (ldp(a.P, r.n1) + 6.0f * p + ldp(a.P, r.n2)) : p;
-        stp(a.Pn, v, w * sharp + (1.0f - w) * ldp_rw(a.Pn, v));
+        float3 p = ldpv(a.P, v, a.in4);
+        float3 sharp = r.k == 2 ? 0.125f * (ldpv(a.P, r.n1, a.in4) + 6.0f * p + ldpv(a.P, r.n2, a.in4)) : p;
+        stpv(a.Pn, v, w * sharp + (1.0f - w) * ldpv_rw(a.Pn, v, a.out4), a.out4);
     }
 }
 
@@ -187,6 +188,8 @@ CreaseArgs base_args(TopoImpl &T, int l) {
     a.flags = T.flags;
     a.P = nullptr; a.Pn = nullptr;
     a.status = T.status;
+    a.in4 = l > 0;
+    a.out4 = l + 1 < T.levels;
     return a;
 }
 

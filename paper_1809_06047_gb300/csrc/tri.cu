@@ -35,6 +35,7 @@ struct TriArgs {
     const float *P;
     float *Pn;
     int *fvn, *cen, *twn;
+    bool in4, out4;               // parent / child positions in padded float4 rows
     int *status;
 };
 
@@ -109,13 +110,13 @@ __global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
         const float *P = a.P;
         float3 p[3];
 #pragma unroll
-        for (int j = 0; j < 3; j++) p[j] = ldp(P, vv[j]);
+        for (int j = 0; j < 3; j++) p[j] = ldpv(P, vv[j], a.in4);
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             if (!ow[j]) continue;
             int d = __ldg(a.fv + tri_prev(tt[j]));
-            float3 ep = 0.375f * (p[j] + p[(j + 1) % 3]) + 0.125f * (p[(j + 2) % 3] + ldp(P, d));
-            stp(a.Pn, V + ee[j], ep);
+            float3 ep = 0.375f * (p[j] + p[(j + 1) % 3]) + 0.125f * (p[(j + 2) % 3] + ldpv(P, d, a.in4));
+            stpv(a.Pn, V + ee[j], ep, a.out4);
         }
 #pragma unroll 1
         for (int j = 0; j < 3; j++) {
@@ -124,13 +125,13 @@ __global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
             int y = x, n = 0;
             float3 sp = f3(0.f, 0.f, 0.f);
             do {
-                sp += ldp(P, __ldg(a.fv + tri_next(y)));
+                sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
                 y = __ldg(a.tw + tri_prev(y));
                 n++;
             } while (y != x && n < kMaxValence);
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
             float beta = c_loop_beta[n];
-            stp(a.Pn, vv[j], (1.0f - (float)n * beta) * p[j] + beta * sp);
+            stpv(a.Pn, vv[j], (1.0f - (float)n * beta) * p[j] + beta * sp, a.out4);
         }
     }
 }
@@ -167,8 +168,8 @@ __global__ void __launch_bounds__(kBlock) k_sqrt3(TriArgs a) {
         const float *P = a.P;
         float3 p[3];
 #pragma unroll
-        for (int j = 0; j < 3; j++) p[j] = ldp(P, vv[j]);
-        stp(a.Pn, V + r, (1.0f / 3.0f) * (p[0] + p[1] + p[2]));
+        for (int j = 0; j < 3; j++) p[j] = ldpv(P, vv[j], a.in4);
+        stpv(a.Pn, V + r, (1.0f / 3.0f) * (p[0] + p[1] + p[2]), a.out4);
 #pragma unroll 1
         for (int j = 0; j < 3; j++) {
             int x = c + j;
@@ -176,13 +177,13 @@ __global__ void __launch_bounds__(kBlock) k_sqrt3(TriArgs a) {
             int y = x, n = 0;
             float3 sp = f3(0.f, 0.f, 0.f);
             do {
-                sp += ldp(P, __ldg(a.fv + tri_next(y)));
+                sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
                 y = __ldg(a.tw + tri_prev(y));
                 n++;
             } while (y != x && n < kMaxValence);
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
             float al = c_sqrt3_alpha[n];
-            stp(a.Pn, vv[j], (1.0f - al) * p[j] + (al / (float)n) * sp);
+            stpv(a.Pn, vv[j], (1.0f - al) * p[j] + (al / (float)n) * sp, a.out4);
         }
     }
 }
@@ -197,6 +198,8 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
+    a.in4 = l > 0;
+    a.out4 = l + 1 < T.levels;
     return a;
 }
 
