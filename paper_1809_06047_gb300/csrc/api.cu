@@ -91,7 +91,7 @@ void free_topo(TopoImpl &T) {
     T.allocs.clear();
 }
 
-alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, cudaStream_t s) {
+alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table, cudaStream_t s) {
     C.cap = cap;
     AL(C.count, 1);
     if (cap > 0) {
@@ -99,6 +99,13 @@ alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, cudaStream_
         AL(C.own, cap);
         AL(C.sig, cap);
         AL(C.verts, 2 * cap);
+        if (table) {
+            int k = 4;                                   // at least 16 slots, load factor <= 1/2
+            while ((1LL << k) < 2 * cap) k++;
+            C.hmask = (1 << k) - 1;
+            C.hshift = 32 - k;
+            AL(C.tab, (size_t)1 << k);
+        }
     }
     return ALSUB_OK;
 }
@@ -136,7 +143,7 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
         long long cap = 0;
         if (creases && (double)l < (double)M.sigma_max)
             cap = l == 0 ? M.K : std::min(2 * T.L[l - 1].cr.cap, T.L[l].E);
-        alsub_status st = alloc_crease(T, T.L[l].cr, cap, s);
+        alsub_status st = alloc_crease(T, T.L[l].cr, cap, true, s);
         if (st) return st;
         maxcap = std::max(maxcap, cap);
     }
@@ -146,7 +153,7 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     T.scan_tmp_bytes = scan_tmp_bytes(std::max<long long>(nflags, V));
     AL(*(char **)&T.scan_tmp, T.scan_tmp_bytes);
     if (maxcap > 0) {
-        alsub_status st = alloc_crease(T, T.ctmp, 2 * maxcap, s);
+        alsub_status st = alloc_crease(T, T.ctmp, 2 * maxcap, false, s);
         if (st) return st;
     }
     // Per-corner edge ids and twins are stored for every level that a later step reads them from.
@@ -380,7 +387,7 @@ alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stre
     level0_build(T, s);
     for (int l = 0; l < levels; l++) {
         step(T, l, true, T.L[l + 1].helpers, nullptr, nullptr, s);
-        crease_inherit(T, l, s);
+        crease_level(T, l, nullptr, nullptr, true, s);
     }
     T.built = true;
     return finish("alsub_refine_topology");
@@ -502,7 +509,7 @@ alsub_status alsub_refine_vertices(alsub_topology_t h, const float *P0, float *P
         float *out;
         level_buffers(T, P0, PL, scratch, l, &in, &out);
         step(T, l, false, false, in, out, s);
-        crease_fix(T, l, in, out, s);
+        crease_level(T, l, in, out, false, s);
         mark(T, l + 2, s);
     }
     if (T.tcap) T.tcalls++;
@@ -528,8 +535,7 @@ alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, voi
         float *out;
         level_buffers(T, P0, PL, scratch, l, &in, &out);
         step(T, l, true, T.L[l + 1].helpers, in, out, s);
-        crease_fix(T, l, in, out, s);
-        crease_inherit(T, l, s);
+        crease_level(T, l, in, out, true, s);
         mark(T, l + 2, s);
     }
     if (T.tcap) T.tcalls++;

@@ -219,17 +219,6 @@ __device__ __forceinline__ float3 sum4(float3 v) {
     return v;
 }
 
-// Twin of corner y of level l >= 2 from the parent level's twins (the rule of the build step).
-__device__ __forceinline__ int derived_twin(const int *__restrict__ ptw, int y) {
-    int c = y >> 2;
-    switch (y & 3) {
-        case 0: return 4 * quad_next(__ldg(ptw + c)) + 3;
-        case 1: return 4 * quad_next(c) + 2;
-        case 2: return 4 * quad_prev(c) + 1;
-        default: return 4 * __ldg(ptw + quad_prev(c));
-    }
-}
-
 // Where the vertex at corner x (a corner 0) of level l >= 1 was created, if x is its designated
 // corner: kind 0 = a level-0 vertex (c = its designated level-0 corner), 1 = the edge point of the
 // level-(m-1) edge owned by corner c, 2 = the face point of the level-(m-1) face whose first corner

@@ -4,6 +4,7 @@
 #include <stdint.h>
 
 #include "alsub.h"
+#include "internal.h"
 
 namespace alsub {
 
@@ -108,6 +109,32 @@ struct AccTri {
     __device__ int edge(int x) const { return __ldg(ce + x); }
     __device__ int vtx(int x) const { return __ldg(fv + x); }
 };
+
+// Crease hash table (CreaseList::tab): linear probing from a multiplicative hash.
+__device__ __forceinline__ unsigned crease_slot(int e, int shift) {
+    return shift >= 32 ? 0u : ((unsigned)e * 2654435761u) >> shift;
+}
+__device__ __forceinline__ float crease_lookup(const CreaseList &C, int e) {
+    unsigned h = crease_slot(e, C.hshift);
+    for (int probe = 0; probe <= C.hmask; probe++) {
+        const int2 q = __ldg(C.tab + h);
+        if (q.x == e) return __int_as_float(q.y);
+        if (q.x < 0) return 0.f;
+        h = (h + 1) & C.hmask;
+    }
+    return 0.f;
+}
+__device__ __forceinline__ void crease_insert(const CreaseList &C, int e, float s) {
+    unsigned h = crease_slot(e, C.hshift);
+    for (int probe = 0; probe <= C.hmask; probe++) {
+        const int old = atomicCAS(&C.tab[h].x, -1, e);
+        if (old == -1 || old == e) {
+            C.tab[h].y = __float_as_int(s);
+            return;
+        }
+        h = (h + 1) & C.hmask;
+    }
+}
 
 inline unsigned grid_for(long long n, int block = kBlock) {
     long long g = (n + block - 1) / block;

@@ -1,19 +1,21 @@
 // Creases (Sec. 3.3) for Catmull-Clark and Loop.
 //
-// The crease matrix C_l is kept as a list of tagged edges sorted by edge id; a crease is looked up
-// by binary search. For each crease end vertex the ring walk computes the crease valency k (Eq.
-// CC_crease_valency) and the sharpness sum in the same pass (the fused k / s SpMV of Sec. 4.4),
-// so s = S / k (Eq. CC_crease_vsharpness).
+// The crease matrix C_l is kept as a list of tagged edges sorted by edge id, plus an
+// open-addressing hash table (edge id -> sharpness) for the O(1) lookups of the ring walks. For
+// each crease end vertex one ring walk computes the crease valency k (Eq. CC_crease_valency) and
+// the sharpness sum in the same pass (the fused k / s SpMV of Sec. 4.4), so s = S / k
+// (Eq. CC_crease_vsharpness).
 //
-// crease_fix runs after the smooth eval of a level and overwrites (Fig. module_creases):
-//   the edge point of a crease: sigma >= 1 -> midpoint, else (1 - sigma) smooth + sigma midpoint;
-//   a crease vertex with k >= 2: w sharp + (1 - w) smooth, w = min(s, 1), sharp =
-//   (p_a + 6 p + p_b) / 8 for k == 2 and p for k >= 3. Exactly one crease thread writes a vertex:
-//   the one whose outgoing corner at that vertex is the smallest among the vertex's creases.
-// crease_inherit produces C_{l+1} in two passes (count, then fill, Sec. 3.3): each crease yields
-// its two halves with sigma' = max((sigma_o + 3 sigma) / 4 - 1, 0) (the Chaikin-style rule),
-// evaluated with correctly rounded FP32 operations in a fixed order; halves with sigma' = 0 are
-// dropped by a scan-based compaction, which keeps the list sorted by edge id.
+// One kernel per level does both crease jobs from that single analysis:
+//  fix (after the smooth eval of the level, Fig. module_creases) overwrites
+//    the edge point of a crease: sigma >= 1 -> midpoint, else (1 - sigma) smooth + sigma midpoint;
+//    a crease vertex with k >= 2: w sharp + (1 - w) smooth, w = min(s, 1), sharp =
+//    (p_a + 6 p + p_b) / 8 for k == 2 and p for k >= 3. Exactly one crease thread writes a vertex:
+//    the one whose outgoing corner at that vertex is the smallest among the vertex's creases;
+//  inherit (Sec. 3.3, count then fill) gives each crease's two halves the sharpness
+//    max((sigma_o + 3 sigma) / 4 - 1, 0) (the Chaikin-style rule), evaluated with correctly rounded
+//    FP32 operations in a fixed order; a scan-based compaction drops the zeros and keeps the list
+//    sorted by edge id, and fills the next level's hash table.
 #include <float.h>
 #include <math.h>
 
@@ -36,18 +38,6 @@ struct CreaseArgs {
     int *status;
 };
 
-__device__ __forceinline__ float lookup(const CreaseList &C, int K, int e) {
-    int lo = 0, hi = K - 1;
-    while (lo <= hi) {
-        int mid = (lo + hi) >> 1;
-        int m = __ldg(C.edge + mid);
-        if (m == e) return __ldg(C.sig + mid);
-        if (m < e) lo = mid + 1;
-        else hi = mid - 1;
-    }
-    return 0.f;
-}
-
 struct EndInfo {
     int k;          // incident creases
     float S;        // their sharpness sum, in ring order from the start corner
@@ -57,14 +47,14 @@ struct EndInfo {
 };
 
 template <class Acc>
-__device__ EndInfo analyse(const Acc &A, const CreaseList &C, int K, int start, int *status) {
+__device__ EndInfo analyse(const Acc &A, const CreaseList &C, int start, int *status) {
     EndInfo r;
     r.k = 0; r.S = 0.f; r.n1 = r.n2 = -1; r.s1 = r.s2 = 0.f; r.minc = 0x7fffffff;
     int y = start, steps = 0;
     do {
-        float sy = lookup(C, K, A.edge(y));
+        const float sy = crease_lookup(C, A.edge(y));
         if (sy > 0.f) {
-            int nb = A.vtx(A.next(y));
+            const int nb = A.vtx(A.next(y));
             if (r.k == 0) { r.n1 = nb; r.s1 = sy; }
             else if (r.k == 1) { r.n2 = nb; r.s2 = sy; }
             r.k++;
@@ -86,82 +76,119 @@ __device__ __forceinline__ float chaikin(float so, float s) {
     return y > 0.f ? y : 0.f;
 }
 
-template <class Acc>
-__global__ void k_crease_fix(Acc A, CreaseArgs a) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (failed(a.status)) return;
-    const int K = *a.in.count;
-    if (i >= K) return;
-    int e = a.in.edge[i], o = a.in.own[i];
-    float s = a.in.sig[i];
-    int t = A.twin(o);
-    int va = A.vtx(o), vb = A.vtx(t);
-    float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
-    float3 mid = 0.5f * (pa + pb);
-    int idx = a.epbase + e;
-    if (s >= 1.0f) stpv(a.Pn, idx, mid, a.out4);
-    else stpv(a.Pn, idx, (1.0f - s) * ldpv_rw(a.Pn, idx, a.out4) + s * mid, a.out4);
-    int starts[2] = {o, t};
-    int verts[2] = {va, vb};
-    for (int h = 0; h < 2; h++) {
-        EndInfo r = analyse(A, a.in, K, starts[h], a.status);
-        if (r.minc != starts[h] || r.k < 2) continue;
-        int v = verts[h];
-        float sv = r.S / (float)r.k;
-        float w = sv < 1.0f ? sv : 1.0f;
-        float3 p = ldpv(a.P, v, a.in4);
-        float3 sharp = r.k == 2 ? 0.125f * (ldpv(a.P, r.n1, a.in4) + 6.0f * p + ldpv(a.P, r.n2, a.in4)) : p;
-        stpv(a.Pn, v, w * sharp + (1.0f - w) * ldpv_rw(a.Pn, v, a.out4), a.out4);
-    }
-}
-
 __device__ __forceinline__ int child_corner(int x, int tri) {
     if (!tri) return 4 * x;                 // Catmull-Clark: corner 0 of child quad x
     int r = x / 3, j = x - 3 * r;           // Loop: corner 0 of child j of triangle r
     return 3 * (4 * r + j);
 }
 
-template <class Acc>
-__global__ void k_crease_inherit(Acc A, CreaseArgs a, int cap) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+template <class Acc, bool FIX, bool INHERIT>
+__global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
     const int K = failed(a.status) ? 0 : *a.in.count;
-    if (i >= K) { a.flags[2 * i] = 0; a.flags[2 * i + 1] = 0; return; }
-    int e = a.in.edge[i], o = a.in.own[i];
-    float s = a.in.sig[i];
-    int t = A.twin(o);
-    int va = A.vtx(o), vb = A.vtx(t);
-    EndInfo ra = analyse(A, a.in, K, o, a.status);
-    EndInfo rb = analyse(A, a.in, K, t, a.status);
-    float oa = s, ob = s;
-    if (ra.k == 2) { float x = ra.n1 == vb ? ra.s2 : ra.s1; if (isfinite(x)) oa = x; }
-    if (rb.k == 2) { float x = rb.n1 == va ? rb.s2 : rb.s1; if (isfinite(x)) ob = x; }
-    float ca = chaikin(oa, s), cb = chaikin(ob, s);
-    int ep = a.epbase + e;
-    a.out.edge[2 * i] = 2 * e;
-    a.out.own[2 * i] = child_corner(o, a.child_tri);
-    a.out.sig[2 * i] = ca;
-    a.out.verts[4 * i] = va;
-    a.out.verts[4 * i + 1] = ep;
-    a.out.edge[2 * i + 1] = 2 * e + 1;
-    a.out.own[2 * i + 1] = child_corner(t, a.child_tri);
-    a.out.sig[2 * i + 1] = cb;
-    a.out.verts[4 * i + 2] = ep;
-    a.out.verts[4 * i + 3] = vb;
-    a.flags[2 * i] = ca > 0.f;
-    a.flags[2 * i + 1] = cb > 0.f;
+    if (i >= K) {
+        if (INHERIT) { a.flags[2 * i] = 0; a.flags[2 * i + 1] = 0; }
+        return;
+    }
+    const int e = a.in.edge[i], o = a.in.own[i];
+    const float s = a.in.sig[i];
+    const int t = A.twin(o);
+    const int va = A.vtx(o), vb = A.vtx(t);
+    const EndInfo ra = analyse(A, a.in, o, a.status);
+    const EndInfo rb = analyse(A, a.in, t, a.status);
+    const int ep = a.epbase + e;
+    if (FIX) {
+        const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
+        const float3 mid = 0.5f * (pa + pb);
+        if (s >= 1.0f) stpv(a.Pn, ep, mid, a.out4);
+        else stpv(a.Pn, ep, (1.0f - s) * ldpv_rw(a.Pn, ep, a.out4) + s * mid, a.out4);
+        const EndInfo *rr[2] = {&ra, &rb};
+        const int starts[2] = {o, t}, verts[2] = {va, vb};
+        for (int h = 0; h < 2; h++) {
+            const EndInfo &r = *rr[h];
+            if (r.minc != starts[h] || r.k < 2) continue;
+            const int v = verts[h];
+            const float sv = r.S / (float)r.k;
+            const float w = sv < 1.0f ? sv : 1.0f;
+            const float3 p = h == 0 ? pa : pb;
+            const float3 sharp =
+                r.k == 2 ? 0.125f * (ldpv(a.P, r.n1, a.in4) + 6.0f * p + ldpv(a.P, r.n2, a.in4)) : p;
+            stpv(a.Pn, v, w * sharp + (1.0f - w) * ldpv_rw(a.Pn, v, a.out4), a.out4);
+        }
+    }
+    if (INHERIT) {
+        float oa = s, ob = s;
+        if (ra.k == 2) { float x = ra.n1 == vb ? ra.s2 : ra.s1; if (isfinite(x)) oa = x; }
+        if (rb.k == 2) { float x = rb.n1 == va ? rb.s2 : rb.s1; if (isfinite(x)) ob = x; }
+        const float ca = chaikin(oa, s), cb = chaikin(ob, s);
+        a.out.edge[2 * i] = 2 * e;
+        a.out.own[2 * i] = child_corner(o, a.child_tri);
+        a.out.sig[2 * i] = ca;
+        a.out.verts[4 * i] = va;
+        a.out.verts[4 * i + 1] = ep;
+        a.out.edge[2 * i + 1] = 2 * e + 1;
+        a.out.own[2 * i + 1] = child_corner(t, a.child_tri);
+        a.out.sig[2 * i + 1] = cb;
+        a.out.verts[4 * i + 2] = ep;
+        a.out.verts[4 * i + 3] = vb;
+        a.flags[2 * i] = ca > 0.f;
+        a.flags[2 * i + 1] = cb > 0.f;
+    }
 }
 
-__global__ void k_crease_compact(int n, const int *__restrict__ flags, const int *__restrict__ pos,
-                                 CreaseList src, CreaseList dst) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || !flags[i]) return;
-    int k = pos[i];
+__device__ __forceinline__ void emit(const CreaseList &src, int i, const CreaseList &dst, int k) {
     dst.edge[k] = src.edge[i];
     dst.own[k] = src.own[i];
     dst.sig[k] = src.sig[i];
     dst.verts[2 * k] = src.verts[2 * i];
     dst.verts[2 * k + 1] = src.verts[2 * i + 1];
+    crease_insert(dst, src.edge[i], src.sig[i]);
+}
+
+// Compaction of up to kSmall candidates by one CTA (scan in shared memory, carried across tiles).
+constexpr int kCompactThreads = 1024;
+constexpr long long kSmall = 1 << 20;
+
+__global__ void __launch_bounds__(kCompactThreads) k_compact_small(int n, const int *__restrict__ flags,
+                                                                   CreaseList src, CreaseList dst) {
+    __shared__ int warp_off[kCompactThreads / 32];
+    __shared__ int tile_total, carry;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += kCompactThreads) {
+        const int i = base + threadIdx.x;
+        const int f = (i < n && flags[i]) ? 1 : 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int before = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_off[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {
+            const int v = warp_off[lane];
+            int inc = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int x = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += x;
+            }
+            warp_off[lane] = inc - v;
+            if (lane == 31) tile_total = inc;
+        }
+        __syncthreads();
+        if (f) emit(src, i, dst, carry + warp_off[w] + before);
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tile_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *dst.count = carry;
+}
+
+__global__ void k_compact(int n, const int *__restrict__ flags, const int *__restrict__ pos,
+                          CreaseList src, CreaseList dst) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !flags[i]) return;
+    emit(src, i, dst, pos[i]);
 }
 
 template <class F>
@@ -195,28 +222,43 @@ CreaseArgs base_args(TopoImpl &T, int l) {
 
 }  // namespace
 
-void crease_fix(TopoImpl &T, int l, const float *P, float *Pn, cudaStream_t s) {
-    if (T.scheme == ALSUB_SQRT3 || T.L[l].cr.cap == 0) return;
-    CreaseArgs a = base_args(T, l);
-    a.P = P; a.Pn = Pn;
-    unsigned g = grid_for(T.L[l].cr.cap);
-    with_acc(T, l, [&](auto acc) { k_crease_fix<<<g, kBlock, 0, s>>>(acc, a); });
-    T.launches += 1;
+void crease_table_clear(const CreaseList &C, cudaStream_t s) {
+    if (C.tab) cudaMemsetAsync(C.tab, 0xff, sizeof(int2) * ((size_t)C.hmask + 1), s);
 }
 
-void crease_inherit(TopoImpl &T, int l, cudaStream_t s) {
-    if (T.scheme == ALSUB_SQRT3) return;
-    CreaseList &dst = T.L[l + 1].cr;
-    if (dst.cap == 0 || T.L[l].cr.cap == 0) {
-        if (dst.count) cudaMemsetAsync(dst.count, 0, sizeof(int), s);
+void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, cudaStream_t s) {
+    if (T.scheme == ALSUB_SQRT3 || T.L[l].cr.cap == 0) {
+        if (inherit && l + 1 <= T.levels && T.L[l + 1].cr.count)
+            cudaMemsetAsync(T.L[l + 1].cr.count, 0, sizeof(int), s);
         return;
     }
+    const bool fix = P != nullptr;
+    CreaseList &dst = T.L[l + 1].cr;
+    inherit = inherit && dst.cap > 0;
+    if (!inherit && dst.count) cudaMemsetAsync(dst.count, 0, sizeof(int), s);
+    if (!fix && !inherit) return;
     CreaseArgs a = base_args(T, l);
-    int cap = (int)T.L[l].cr.cap;
-    with_acc(T, l, [&](auto acc) { k_crease_inherit<<<grid_for(cap), kBlock, 0, s>>>(acc, a, cap); });
-    scan_exclusive(T.flags, T.pos, 2LL * cap, dst.count, nullptr, T.scan_tmp, s);
-    k_crease_compact<<<grid_for(2LL * cap), kBlock, 0, s>>>(2 * cap, T.flags, T.pos, T.ctmp, dst);
-    T.launches += 5;
+    a.P = P; a.Pn = Pn;
+    const int cap = (int)T.L[l].cr.cap;
+    const unsigned g = grid_for(cap);
+    with_acc(T, l, [&](auto acc) {
+        using A = decltype(acc);
+        if (fix && inherit) k_crease<A, true, true><<<g, kBlock, 0, s>>>(acc, a, cap);
+        else if (fix) k_crease<A, true, false><<<g, kBlock, 0, s>>>(acc, a, cap);
+        else k_crease<A, false, true><<<g, kBlock, 0, s>>>(acc, a, cap);
+    });
+    T.launches += 1;
+    if (!inherit) return;
+    crease_table_clear(dst, s);
+    const long long n = 2LL * cap;
+    if (n <= kSmall) {
+        k_compact_small<<<1, kCompactThreads, 0, s>>>((int)n, T.flags, T.ctmp, dst);
+        T.launches += 1;
+    } else {
+        T.launches += scan_exclusive(T.flags, T.pos, n, dst.count, nullptr, T.scan_tmp, s);
+        k_compact<<<grid_for(n), kBlock, 0, s>>>((int)n, T.flags, T.pos, T.ctmp, dst);
+        T.launches += 1;
+    }
 }
 
 }  // namespace alsub

@@ -18,6 +18,10 @@ struct CreaseList {
     int *verts = nullptr;  // 2 endpoints per crease
     int *count = nullptr;  // number of entries (device int)
     long long cap = 0;     // host-side upper bound of the count
+    // open-addressing table edge id -> sharpness bits (key -1 = empty), hmask + 1 = 2^k slots
+    int2 *tab = nullptr;
+    int hmask = 0;
+    int hshift = 32;       // slot = (edge * 2654435761) >> hshift
 };
 
 // One level of the refined mesh. fv is the reduced mesh matrix (face table); ce and tw are the
@@ -75,8 +79,8 @@ struct TopoImpl {
 // Exclusive scan of n ints (elements at index >= *n_dev read as 0 when n_dev is given); the
 // total goes to *total when total is not null. tmp must hold scan_tmp_bytes(n) bytes.
 size_t scan_tmp_bytes(long long n);
-void scan_exclusive(const int *in, int *out, long long n, int *total, const int *n_dev, void *tmp,
-                    cudaStream_t s);
+int scan_exclusive(const int *in, int *out, long long n, int *total, const int *n_dev, void *tmp,
+                   cudaStream_t s);  // returns the number of kernels launched
 
 // Level 0: corner maps, twins, ownership, edge numbering, crease list of level 0.
 void level0_build(TopoImpl &T, cudaStream_t s);
@@ -87,10 +91,11 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
 void loop_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s);
 void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s);
 
-// Creases at level l: overwrite crease vertex/edge points of level l + 1 (Fig. module_creases),
-// and inherit the crease list of level l + 1 (Sec. 3.3, count then fill).
-void crease_fix(TopoImpl &T, int l, const float *P, float *Pn, cudaStream_t s);
-void crease_inherit(TopoImpl &T, int l, cudaStream_t s);
+// Creases at level l in one kernel: with P/Pn, overwrite the crease vertex and edge points of
+// level l + 1 (Fig. module_creases); with `inherit`, build the crease list and hash table of
+// level l + 1 (Sec. 3.3, count then fill).
+void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, cudaStream_t s);
+void crease_table_clear(const CreaseList &C, cudaStream_t s);
 
 // Device-side constant tables (Loop beta_n, sqrt(3) alpha_n) filled once per process.
 void upload_weight_tables();

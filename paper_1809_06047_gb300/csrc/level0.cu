@@ -135,6 +135,7 @@ __global__ void k_crease_emit(int E0, const int *__restrict__ cmap, const int *_
     out.sig[k] = cs[i];
     out.verts[2 * k] = fv[o];
     out.verts[2 * k + 1] = fv[tw[o]];
+    crease_insert(out, e, cs[i]);
 }
 
 }  // namespace
@@ -147,24 +148,23 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     cudaMemsetAsync(T.deg, 0, sizeof(int) * (size_t)V, s);
     cudaMemsetAsync(T.vfill, 0, sizeof(int) * (size_t)V, s);
     k_faces<<<grid_for(F), kBlock, 0, s>>>(F, M.d_off, M.d_fv, T.cf0, T.nx0, T.pv0, T.deg);
-    scan_exclusive(T.deg, T.voff, V, T.voff + V, nullptr, T.scan_tmp, s);
+    T.launches += 5 + scan_exclusive(T.deg, T.voff, V, T.voff + V, nullptr, T.scan_tmp, s);
     k_bucket<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.voff, T.vfill, T.vbk);
     k_twin<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.voff, T.vbk, L0.tw, T.own0, T.status);
     k_vertex<<<grid_for(V), kBlock, 0, s>>>(V, T.voff, T.vbk, L0.tw, T.pv0, T.vc0, T.status);
-    scan_exclusive(T.own0, T.eid, nnz, T.e0count, nullptr, T.scan_tmp, s);
+    T.launches += scan_exclusive(T.own0, T.eid, nnz, T.e0count, nullptr, T.scan_tmp, s);
     k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.e0count, E0, L0.ce, T.eo0,
                                              T.status);
-    T.launches += 11;
     CreaseList &C = L0.cr;
     if (C.cap > 0) {
         cudaMemsetAsync(T.cmap, 0xff, sizeof(int) * (size_t)E0, s);
         k_crease_map<<<grid_for(M.K), kBlock, 0, s>>>(M.K, M.d_cv, M.d_cs, M.d_fv, T.nx0, T.voff,
                                                       T.vbk, L0.ce, V, T.cmap, T.status);
         k_crease_flags<<<grid_for(E0), kBlock, 0, s>>>(E0, T.cmap, T.flags);
-        scan_exclusive(T.flags, T.pos, E0, C.count, nullptr, T.scan_tmp, s);
+        T.launches += 3 + scan_exclusive(T.flags, T.pos, E0, C.count, nullptr, T.scan_tmp, s);
+        crease_table_clear(C, s);
         k_crease_emit<<<grid_for(E0), kBlock, 0, s>>>(E0, T.cmap, T.pos, M.d_cs, T.eo0, L0.tw,
                                                       M.d_fv, C);
-        T.launches += 6;
     } else if (C.count) {
         cudaMemsetAsync(C.count, 0, sizeof(int), s);
     }

@@ -97,6 +97,38 @@ __global__ void k_scan_tiles(const int *__restrict__ in, int *out, long long n, 
     }
 }
 
+// Small inputs: one CTA scans the whole array in tiles, carrying the running total.
+constexpr long long kSmallScan = 1 << 16;
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int *__restrict__ in, int *out,
+                                                              long long n, const int *n_dev, int *total) {
+    __shared__ int carry;
+    const long long lim = limit_of(n, n_dev);
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (long long base0 = 0; base0 < n; base0 += kTile) {
+        const long long base = base0 + (long long)threadIdx.x * kItems;
+        int v[kItems];
+        int s = 0;
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            v[i] = (base + i < lim) ? in[base + i] : 0;
+            s += v[i];
+        }
+        int tot;
+        int ex = block_excl_scan(s, &tot) + carry;
+#pragma unroll
+        for (int i = 0; i < kItems; i++) {
+            if (base + i < n) out[base + i] = ex;
+            ex += v[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) carry += tot;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && total) *total = carry;
+}
+
 }  // namespace
 
 size_t scan_tmp_bytes(long long n) {
@@ -104,17 +136,22 @@ size_t scan_tmp_bytes(long long n) {
     return sizeof(int) * (size_t)(nt < 1 ? 1 : nt);
 }
 
-void scan_exclusive(const int *in, int *out, long long n, int *total, const int *n_dev, void *tmp,
-                    cudaStream_t s) {
+int scan_exclusive(const int *in, int *out, long long n, int *total, const int *n_dev, void *tmp,
+                   cudaStream_t s) {
     if (n <= 0) {
         if (total) cudaMemsetAsync(total, 0, sizeof(int), s);
-        return;
+        return 0;
+    }
+    if (n <= kSmallScan) {
+        k_scan_single<<<1, kScanThreads, 0, s>>>(in, out, n, n_dev, total);
+        return 1;
     }
     int nt = (int)((n + kTile - 1) / kTile);
     int *sums = (int *)tmp;
     k_tile_sums<<<nt, kScanThreads, 0, s>>>(in, n, n_dev, sums);
     k_scan_sums<<<1, kScanThreads, 0, s>>>(sums, nt, total);
     k_scan_tiles<<<nt, kScanThreads, 0, s>>>(in, out, n, n_dev, sums);
+    return 3;
 }
 
 }  // namespace alsub
