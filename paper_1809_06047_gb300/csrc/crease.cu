@@ -234,8 +234,10 @@ void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, c
     }
     const bool fix = P != nullptr;
     CreaseList &dst = T.L[l + 1].cr;
-    inherit = inherit && dst.cap > 0;
-    if (!inherit && dst.count) cudaMemsetAsync(dst.count, 0, sizeof(int), s);
+    if (inherit && dst.cap == 0) {          // all creases have decayed: level l + 1 has none
+        if (dst.count) cudaMemsetAsync(dst.count, 0, sizeof(int), s);
+        inherit = false;
+    }
     if (!fix && !inherit) return;
     CreaseArgs a = base_args(T, l);
     a.P = P; a.Pn = Pn;
