@@ -105,6 +105,9 @@ alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table,
             C.hmask = (1 << k) - 1;
             C.hshift = 32 - k;
             AL(C.tab, (size_t)1 << k);
+            AL(C.xverts, 2 * cap);
+            AL(C.xsig, cap);
+            AL(C.xcount, 1);
         }
     }
     return ALSUB_OK;
@@ -133,7 +136,7 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     AL(L0.tw, nnz);
     AL(T.cf0, nnz); AL(T.nx0, nnz); AL(T.pv0, nnz); AL(T.own0, nnz); AL(T.vbk, nnz); AL(T.eid, nnz);
     AL(T.vc0, V); AL(T.deg, V); AL(T.vfill, V); AL(T.voff, V + 1);
-    AL(T.eo0, E0); AL(T.cmap, E0);
+    AL(T.eo0, E0);
     AL(T.e0count, 1); AL(T.status, 1);
     // crease capacities: the sharpness of level l is at most sigma_max - l (each inherited
     // value is at most the parent maximum minus one), so creases are dead once l >= sigma_max
@@ -152,10 +155,6 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     AL(T.pos, nflags);
     T.scan_tmp_bytes = scan_tmp_bytes(std::max<long long>(nflags, V));
     AL(*(char **)&T.scan_tmp, T.scan_tmp_bytes);
-    if (maxcap > 0) {
-        alsub_status st = alloc_crease(T, T.ctmp, 2 * maxcap, false, s);
-        if (st) return st;
-    }
     // Per-corner edge ids and twins are stored for every level that a later step reads them from.
     // The last Catmull-Clark step on a level >= 2 derives them from the parent level instead,
     // unless creases (whose kernels walk rings through the stored arrays) are still alive there.
@@ -423,58 +422,15 @@ alsub_status alsub_topology_creases(alsub_topology_t h, int32_t level, int32_t *
     TopoImpl &T = h->t;
     const CreaseList &C = T.L[level].cr;
     int k = 0;
-    if (C.count) {
-        cudaError_t e = cudaMemcpyAsync(&k, C.count, sizeof(int), cudaMemcpyDeviceToHost, T.stream);
+    if (C.cap > 0) {
+        T.launches += crease_export(T, level, T.stream);
+        cudaError_t e = cudaMemcpyAsync(&k, C.xcount, sizeof(int), cudaMemcpyDeviceToHost, T.stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(T.stream);
         if (e != cudaSuccess) return cuda_fail(e, "alsub_topology_creases");
     }
-    *K = C.cap > 0 ? k : 0;
-    if (cv) *cv = C.verts;
-    if (cs) *cs = C.sig;
-    return ALSUB_OK;
-}
-
-alsub_status alsub_topology_set_timing(alsub_topology_t h, int32_t capacity) {
-    if (!h || capacity < 0) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
-    TopoImpl &T = h->t;
-    CK(cudaStreamSynchronize(T.stream));
-    free_events(T);
-    if (capacity == 0) return ALSUB_OK;
-    size_t n = (size_t)capacity * (T.levels + 2);
-    T.tev.resize(n);
-    for (size_t i = 0; i < n; i++) {
-        cudaError_t e = cudaEventCreate(&T.tev[i]);
-        if (e != cudaSuccess) {
-            T.tev.resize(i);
-            free_events(T);
-            return cuda_fail(e, "cudaEventCreate");
-        }
-    }
-    T.tcap = capacity;
-    T.tcalls = 0;
-    return ALSUB_OK;
-}
-
-alsub_status alsub_topology_timings(alsub_topology_t h, double *ms, int32_t *calls, int64_t *launches) {
-    if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL topology");
-    TopoImpl &T = h->t;
-    if (launches) *launches = T.launches;
-    T.launches = 0;
-    int n = std::min(T.tcalls, T.tcap);
-    bool overflow = T.tcalls > T.tcap;
-    if (ms) for (int k = 0; k <= T.levels; k++) ms[k] = 0.0;
-    for (int c = 0; c < n; c++) {
-        size_t b = (size_t)c * (T.levels + 2);
-        for (int k = 0; k <= T.levels; k++) {
-            CK(cudaEventSynchronize(T.tev[b + k + 1]));
-            float t = 0.f;
-            CK(cudaEventElapsedTime(&t, T.tev[b + k], T.tev[b + k + 1]));
-            if (ms) ms[k] += t;
-        }
-    }
-    if (calls) *calls = n;
-    T.tcalls = 0;
-    if (overflow) return fail(ALSUB_ERR_INVALID_ARG, "more timed calls than the timing capacity");
+    *K = k;
+    if (cv) *cv = C.xverts;
+    if (cs) *cs = C.xsig;
     return ALSUB_OK;
 }
 

@@ -124,16 +124,19 @@ __device__ __forceinline__ float crease_lookup(const CreaseList &C, int e) {
     }
     return 0.f;
 }
-__device__ __forceinline__ void crease_insert(const CreaseList &C, int e, float s) {
+// Returns false when the edge was already in the table.
+__device__ __forceinline__ bool crease_insert(const CreaseList &C, int e, float s) {
     unsigned h = crease_slot(e, C.hshift);
     for (int probe = 0; probe <= C.hmask; probe++) {
         const int old = atomicCAS(&C.tab[h].x, -1, e);
-        if (old == -1 || old == e) {
+        if (old == -1) {
             C.tab[h].y = __float_as_int(s);
-            return;
+            return true;
         }
+        if (old == e) return false;
         h = (h + 1) & C.hmask;
     }
+    return false;
 }
 
 inline unsigned grid_for(long long n, int block = kBlock) {

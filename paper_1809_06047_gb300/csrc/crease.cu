@@ -1,7 +1,7 @@
 // Creases (Sec. 3.3) for Catmull-Clark and Loop.
 //
-// The crease matrix C_l is kept as a list of tagged edges sorted by edge id, plus an
-// open-addressing hash table (edge id -> sharpness) for the O(1) lookups of the ring walks. For
+// The crease matrix C_l is kept as a list of tagged edges, plus an open-addressing hash table
+// (edge id -> sharpness) for the O(1) lookups of the ring walks. For
 // each crease end vertex one ring walk computes the crease valency k (Eq. CC_crease_valency) and
 // the sharpness sum in the same pass (the fused k / s SpMV of Sec. 4.4), so s = S / k
 // (Eq. CC_crease_vsharpness).
@@ -12,10 +12,12 @@
 //    a crease vertex with k >= 2: w sharp + (1 - w) smooth, w = min(s, 1), sharp =
 //    (p_a + 6 p + p_b) / 8 for k == 2 and p for k >= 3. Exactly one crease thread writes a vertex:
 //    the one whose outgoing corner at that vertex is the smallest among the vertex's creases;
-//  inherit (Sec. 3.3, count then fill) gives each crease's two halves the sharpness
-//    max((sigma_o + 3 sigma) / 4 - 1, 0) (the Chaikin-style rule), evaluated with correctly rounded
-//    FP32 operations in a fixed order; a scan-based compaction drops the zeros and keeps the list
-//    sorted by edge id, and fills the next level's hash table.
+//  inherit (Sec. 3.3) gives each crease's two halves the sharpness max((sigma_o + 3 sigma) / 4 - 1,
+//    0) (the Chaikin-style rule), evaluated with correctly rounded FP32 operations in a fixed
+//    order. The halves go straight to entries 2i, 2i + 1 of the next level's list (so its order
+//    follows the input order of level 0) and the live ones into its hash table; halves that
+//    decayed to 0 stay as inert entries. The paper's count-then-fill compaction is done only when
+//    a level's list is exported (crease_export).
 #include <float.h>
 #include <math.h>
 
@@ -30,7 +32,7 @@ struct CreaseArgs {
     int epbase;                 // id of edge point 0 in level l + 1 (CC: V + F, Loop: V)
     int child_tri;              // 1: Loop child-corner mapping, 0: Catmull-Clark
     CreaseList in;
-    CreaseList out;             // candidates (2 per crease)
+    CreaseList out;             // the next level's list
     int *flags;
     const float *P;
     float *Pn;
@@ -87,12 +89,23 @@ __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap)
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
     const int K = failed(a.status) ? 0 : *a.in.count;
-    if (i >= K) {
-        if (INHERIT) { a.flags[2 * i] = 0; a.flags[2 * i + 1] = 0; }
-        return;
-    }
+    if (INHERIT && i == 0) *a.out.count = 2 * K;
+    if (i >= K) return;
     const int e = a.in.edge[i], o = a.in.own[i];
     const float s = a.in.sig[i];
+    if (!(s > 0.f)) {
+        // an inherited zero: no crease any more; its children stay inert entries
+        if (INHERIT) {
+            for (int h = 0; h < 2; h++) {
+                a.out.edge[2 * i + h] = 2 * e + h;
+                a.out.own[2 * i + h] = 0;
+                a.out.sig[2 * i + h] = 0.f;
+                a.out.verts[4 * i + 2 * h] = 0;
+                a.out.verts[4 * i + 2 * h + 1] = 0;
+            }
+        }
+        return;
+    }
     const int t = A.twin(o);
     const int va = A.vtx(o), vb = A.vtx(t);
     const EndInfo ra = analyse(A, a.in, o, a.status);
@@ -122,6 +135,7 @@ __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap)
         if (ra.k == 2) { float x = ra.n1 == vb ? ra.s2 : ra.s1; if (isfinite(x)) oa = x; }
         if (rb.k == 2) { float x = rb.n1 == va ? rb.s2 : rb.s1; if (isfinite(x)) ob = x; }
         const float ca = chaikin(oa, s), cb = chaikin(ob, s);
+        // the half at v_o is 2e (o owns e), the half at v_t is 2e + 1
         a.out.edge[2 * i] = 2 * e;
         a.out.own[2 * i] = child_corner(o, a.child_tri);
         a.out.sig[2 * i] = ca;
@@ -132,63 +146,24 @@ __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap)
         a.out.sig[2 * i + 1] = cb;
         a.out.verts[4 * i + 2] = ep;
         a.out.verts[4 * i + 3] = vb;
-        a.flags[2 * i] = ca > 0.f;
-        a.flags[2 * i + 1] = cb > 0.f;
+        if (ca > 0.f) crease_insert(a.out, 2 * e, ca);
+        if (cb > 0.f) crease_insert(a.out, 2 * e + 1, cb);
     }
 }
 
-__device__ __forceinline__ void emit(const CreaseList &src, int i, const CreaseList &dst, int k) {
-    dst.edge[k] = src.edge[i];
-    dst.own[k] = src.own[i];
-    dst.sig[k] = src.sig[i];
-    dst.verts[2 * k] = src.verts[2 * i];
-    dst.verts[2 * k + 1] = src.verts[2 * i + 1];
-    crease_insert(dst, src.edge[i], src.sig[i]);
+__global__ void k_export_flags(int n, const CreaseList c, int *flags) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    flags[i] = i < *c.count && c.sig[i] > 0.f;
 }
 
-// Compaction of up to kSmall candidates by one CTA (scan in shared memory, carried across tiles).
-constexpr int kCompactThreads = 1024;
-constexpr long long kSmall = 1 << 20;
-
-__global__ void __launch_bounds__(kCompactThreads) k_compact_small(int n, const int *__restrict__ flags,
-                                                                   CreaseList src, CreaseList dst) {
-    __shared__ int warp_off[kCompactThreads / 32];
-    __shared__ int tile_total, carry;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += kCompactThreads) {
-        const int i = base + threadIdx.x;
-        const int f = (i < n && flags[i]) ? 1 : 0;
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        const int before = __popc(bal & ((1u << lane) - 1u));
-        if (lane == 0) warp_off[w] = __popc(bal);
-        __syncthreads();
-        if (w == 0) {
-            const int v = warp_off[lane];
-            int inc = v;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int x = __shfl_up_sync(0xffffffffu, inc, o);
-                if (lane >= o) inc += x;
-            }
-            warp_off[lane] = inc - v;
-            if (lane == 31) tile_total = inc;
-        }
-        __syncthreads();
-        if (f) emit(src, i, dst, carry + warp_off[w] + before);
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tile_total;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) *dst.count = carry;
-}
-
-__global__ void k_compact(int n, const int *__restrict__ flags, const int *__restrict__ pos,
-                          CreaseList src, CreaseList dst) {
+__global__ void k_export(int n, const int *__restrict__ flags, const int *__restrict__ pos, CreaseList c) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || !flags[i]) return;
-    emit(src, i, dst, pos[i]);
+    const int k = pos[i];
+    c.xverts[2 * k] = c.verts[2 * i];
+    c.xverts[2 * k + 1] = c.verts[2 * i + 1];
+    c.xsig[k] = c.sig[i];
 }
 
 template <class F>
@@ -211,7 +186,7 @@ CreaseArgs base_args(TopoImpl &T, int l) {
     a.epbase = (int)(T.scheme == ALSUB_CATMULL_CLARK ? A.V + A.F : A.V);
     a.child_tri = T.scheme == ALSUB_LOOP;
     a.in = A.cr;
-    a.out = T.ctmp;
+    a.out = T.L[l + 1 <= T.levels ? l + 1 : l].cr;
     a.flags = T.flags;
     a.P = nullptr; a.Pn = nullptr;
     a.status = T.status;
@@ -239,8 +214,10 @@ void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, c
         inherit = false;
     }
     if (!fix && !inherit) return;
+    if (inherit) crease_table_clear(dst, s);
     CreaseArgs a = base_args(T, l);
     a.P = P; a.Pn = Pn;
+    if (inherit) a.out = dst;
     const int cap = (int)T.L[l].cr.cap;
     const unsigned g = grid_for(cap);
     with_acc(T, l, [&](auto acc) {
@@ -250,17 +227,16 @@ void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, c
         else k_crease<A, false, true><<<g, kBlock, 0, s>>>(acc, a, cap);
     });
     T.launches += 1;
-    if (!inherit) return;
-    crease_table_clear(dst, s);
-    const long long n = 2LL * cap;
-    if (n <= kSmall) {
-        k_compact_small<<<1, kCompactThreads, 0, s>>>((int)n, T.flags, T.ctmp, dst);
-        T.launches += 1;
-    } else {
-        T.launches += scan_exclusive(T.flags, T.pos, n, dst.count, nullptr, T.scan_tmp, s);
-        k_compact<<<grid_for(n), kBlock, 0, s>>>((int)n, T.flags, T.pos, T.ctmp, dst);
-        T.launches += 1;
-    }
+}
+
+int crease_export(TopoImpl &T, int l, cudaStream_t s) {
+    CreaseList &C = T.L[l].cr;
+    if (C.cap == 0) return 0;
+    const long long n = C.cap;
+    k_export_flags<<<grid_for(n), kBlock, 0, s>>>((int)n, C, T.flags);
+    int k = 2 + scan_exclusive(T.flags, T.pos, n, C.xcount, nullptr, T.scan_tmp, s);
+    k_export<<<grid_for(n), kBlock, 0, s>>>((int)n, T.flags, T.pos, C);
+    return k;
 }
 
 }  // namespace alsub

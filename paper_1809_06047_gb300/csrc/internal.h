@@ -10,11 +10,13 @@
 
 namespace alsub {
 
-// The crease matrix C_l of one level (Sec. 3.3) as a compact list sorted by edge id.
+// The crease matrix C_l of one level (Sec. 3.3) as a list of tagged edges. Level 0 keeps the
+// input order; level l + 1 holds the two halves of entry i at 2i and 2i + 1, so entries whose
+// sharpness decayed to 0 stay in the list as inert entries.
 struct CreaseList {
     int *edge = nullptr;   // edge id at this level
     int *own = nullptr;    // corner that owns the edge
-    float *sig = nullptr;  // sharpness (> 0)
+    float *sig = nullptr;  // sharpness (0 = inert)
     int *verts = nullptr;  // 2 endpoints per crease
     int *count = nullptr;  // number of entries (device int)
     long long cap = 0;     // host-side upper bound of the count
@@ -22,6 +24,10 @@ struct CreaseList {
     int2 *tab = nullptr;
     int hmask = 0;
     int hshift = 32;       // slot = (edge * 2654435761) >> hshift
+    // compacted copy (live creases only) written by crease_export
+    int *xverts = nullptr;
+    float *xsig = nullptr;
+    int *xcount = nullptr;
 };
 
 // One level of the refined mesh. fv is the reduced mesh matrix (face table); ce and tw are the
@@ -54,14 +60,13 @@ struct TopoImpl {
     // level-0 adjacency
     int *cf0 = nullptr, *nx0 = nullptr, *pv0 = nullptr, *own0 = nullptr, *vc0 = nullptr;
     int *eo0 = nullptr, *deg = nullptr, *voff = nullptr, *vfill = nullptr, *vbk = nullptr;
-    int *eid = nullptr, *cmap = nullptr, *e0count = nullptr;
+    int *eid = nullptr, *e0count = nullptr;
     int *status = nullptr;       // latched device error
     // temporaries
     void *scan_tmp = nullptr;
     size_t scan_tmp_bytes = 0;
     int *flags = nullptr;        // max(nnz0, E0, 2 * max crease cap) ints
     int *pos = nullptr;          // scan output of flags, same size
-    CreaseList ctmp;             // 2 * max crease cap candidate children
     float *scratch = nullptr;    // intermediate positions (two levels)
     size_t scratch_bytes = 0;
     std::vector<void *> allocs;  // everything above, freed on destroy
@@ -96,6 +101,9 @@ void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, flo
 // level l + 1 (Sec. 3.3, count then fill).
 void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, cudaStream_t s);
 void crease_table_clear(const CreaseList &C, cudaStream_t s);
+// Compact level l's list (drop the inert zero-sharpness entries) into its x* arrays; returns the
+// number of kernels launched.
+int crease_export(TopoImpl &T, int l, cudaStream_t s);
 
 // Device-side constant tables (Loop beta_n, sqrt(3) alpha_n) filled once per process.
 void upload_weight_tables();

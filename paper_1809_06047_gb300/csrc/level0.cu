@@ -94,48 +94,34 @@ __global__ void k_edges(int nnz, const int *__restrict__ own, const int *__restr
     if (own[x]) eo[e] = x;
 }
 
-// Map each input crease (a, b, sigma) to its edge; a crease that is not an edge, or an edge
-// tagged twice, is an input error.
-__global__ void k_crease_map(int K, const int *__restrict__ cv, const float *__restrict__ cs,
-                             const int *__restrict__ fv, const int *__restrict__ nx,
-                             const int *__restrict__ voff, const int *__restrict__ vbk,
-                             const int *__restrict__ ce, int V, int *cmap, int *status) {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+// Level-0 crease list, in input order (the crease matrix C of Sec. 3.3): each input crease
+// (a, b, sigma) is mapped to its edge and owner corner and entered into the level's hash table.
+// A crease that is not an edge of the mesh, or an edge tagged twice, is an input error.
+__global__ void k_crease0(int K, const int *__restrict__ cv, const float *__restrict__ cs,
+                          const int *__restrict__ fv, const int *__restrict__ nx,
+                          const int *__restrict__ voff, const int *__restrict__ vbk,
+                          const int *__restrict__ ce, const int *__restrict__ own,
+                          const int *__restrict__ tw, CreaseList out, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0) *out.count = K;
     if (i >= K) return;
+    out.edge[i] = 0; out.own[i] = 0; out.sig[i] = 0.f; out.verts[2 * i] = 0; out.verts[2 * i + 1] = 0;
     if (failed(status)) return;
-    int a = cv[2 * i], b = cv[2 * i + 1];
+    const int a = cv[2 * i], b = cv[2 * i + 1];
     int x = -1;
     for (int q = voff[a]; q < voff[a + 1] && x < 0; q++) {
-        int d = vbk[q];
+        const int d = vbk[q];
         if (fv[nx[d]] == b) x = d;
     }
     if (x < 0) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
-    int e = ce[x];
-    if (atomicCAS(cmap + e, -1, i) != -1) set_status(status, ALSUB_ERR_INVALID_ARG);
-}
-
-__global__ void k_crease_flags(int E0, const int *__restrict__ cmap, int *flags) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E0) return;
-    flags[e] = cmap[e] >= 0 ? 1 : 0;
-}
-
-__global__ void k_crease_emit(int E0, const int *__restrict__ cmap, const int *__restrict__ pos,
-                              const float *__restrict__ cs, const int *__restrict__ eo,
-                              const int *__restrict__ tw, const int *__restrict__ fv,
-                              CreaseList out) {
-    int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= E0) return;
-    int i = cmap[e];
-    if (i < 0) return;
-    int k = pos[e];
-    int o = eo[e];
-    out.edge[k] = e;
-    out.own[k] = o;
-    out.sig[k] = cs[i];
-    out.verts[2 * k] = fv[o];
-    out.verts[2 * k + 1] = fv[tw[o]];
-    crease_insert(out, e, cs[i]);
+    const int o = own[x] ? x : tw[x], e = ce[x];
+    const float s = cs[i];
+    if (!crease_insert(out, e, s)) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
+    out.edge[i] = e;
+    out.own[i] = o;
+    out.sig[i] = s;
+    out.verts[2 * i] = fv[o];
+    out.verts[2 * i + 1] = fv[tw[o]];
 }
 
 }  // namespace
@@ -157,14 +143,10 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
                                              T.status);
     CreaseList &C = L0.cr;
     if (C.cap > 0) {
-        cudaMemsetAsync(T.cmap, 0xff, sizeof(int) * (size_t)E0, s);
-        k_crease_map<<<grid_for(M.K), kBlock, 0, s>>>(M.K, M.d_cv, M.d_cs, M.d_fv, T.nx0, T.voff,
-                                                      T.vbk, L0.ce, V, T.cmap, T.status);
-        k_crease_flags<<<grid_for(E0), kBlock, 0, s>>>(E0, T.cmap, T.flags);
-        T.launches += 3 + scan_exclusive(T.flags, T.pos, E0, C.count, nullptr, T.scan_tmp, s);
         crease_table_clear(C, s);
-        k_crease_emit<<<grid_for(E0), kBlock, 0, s>>>(E0, T.cmap, T.pos, M.d_cs, T.eo0, L0.tw,
-                                                      M.d_fv, C);
+        k_crease0<<<grid_for(M.K), kBlock, 0, s>>>(M.K, M.d_cv, M.d_cs, M.d_fv, T.nx0, T.voff, T.vbk,
+                                                   L0.ce, T.own0, L0.tw, C, T.status);
+        T.launches += 1;
     } else if (C.count) {
         cudaMemsetAsync(C.count, 0, sizeof(int), s);
     }

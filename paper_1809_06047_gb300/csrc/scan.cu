@@ -98,7 +98,7 @@ __global__ void k_scan_tiles(const int *__restrict__ in, int *out, long long n, 
 }
 
 // Small inputs: one CTA scans the whole array in tiles, carrying the running total.
-constexpr long long kSmallScan = 1 << 16;
+constexpr long long kSmallScan = 1 << 14;
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_single(const int *__restrict__ in, int *out,
                                                               long long n, const int *n_dev, int *total) {
