@@ -434,6 +434,50 @@ alsub_status alsub_topology_creases(alsub_topology_t h, int32_t level, int32_t *
     return ALSUB_OK;
 }
 
+alsub_status alsub_topology_set_timing(alsub_topology_t h, int32_t capacity) {
+    if (!h || capacity < 0) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    TopoImpl &T = h->t;
+    CK(cudaStreamSynchronize(T.stream));
+    free_events(T);
+    if (capacity == 0) return ALSUB_OK;
+    size_t n = (size_t)capacity * (T.levels + 2);
+    T.tev.resize(n);
+    for (size_t i = 0; i < n; i++) {
+        cudaError_t e = cudaEventCreate(&T.tev[i]);
+        if (e != cudaSuccess) {
+            T.tev.resize(i);
+            free_events(T);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    T.tcap = capacity;
+    T.tcalls = 0;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_timings(alsub_topology_t h, double *ms, int32_t *calls, int64_t *launches) {
+    if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL topology");
+    TopoImpl &T = h->t;
+    if (launches) *launches = T.launches;
+    T.launches = 0;
+    int n = std::min(T.tcalls, T.tcap);
+    bool overflow = T.tcalls > T.tcap;
+    if (ms) for (int k = 0; k <= T.levels; k++) ms[k] = 0.0;
+    for (int c = 0; c < n; c++) {
+        size_t b = (size_t)c * (T.levels + 2);
+        for (int k = 0; k <= T.levels; k++) {
+            CK(cudaEventSynchronize(T.tev[b + k + 1]));
+            float t = 0.f;
+            CK(cudaEventElapsedTime(&t, T.tev[b + k], T.tev[b + k + 1]));
+            if (ms) ms[k] += t;
+        }
+    }
+    if (calls) *calls = n;
+    T.tcalls = 0;
+    if (overflow) return fail(ALSUB_ERR_INVALID_ARG, "more timed calls than the timing capacity");
+    return ALSUB_OK;
+}
+
 alsub_status alsub_topology_destroy(alsub_topology_t h) {
     if (!h) return ALSUB_OK;
     free_events(h->t);
