@@ -219,125 +219,29 @@ __device__ __forceinline__ float3 sum4(float3 v) {
     return v;
 }
 
-// Where the vertex at corner x (a corner 0) of level l >= 1 was created, if x is its designated
-// corner: kind 0 = a level-0 vertex (c = its designated level-0 corner), 1 = the edge point of the
-// level-(m-1) edge owned by corner c, 2 = the face point of the level-(m-1) face whose first corner
-// is c. kind -1: x is not the designated corner. Corner 0 of child x is the old vertex again, so
-// following x -> x / 4 walks back to the creation level m without touching memory.
+// The vertex at corner 4r (corner 0 of child r) existed on level l - 1; following x -> x / 4
+// while x is a corner 0 walks back, with integer arithmetic only, to the level m where it was
+// created, and tells which corner of that level designates it:
+//   kind 1: the edge point of the level-(m-1) edge owned by corner c;
+//   kind 2: the face point of the level-(m-1) face whose first corner is c;
+//   kind 0: a vertex of the control mesh (c = one of its level-0 corners).
+// Vertices created on levels >= 2 (all but a vanishing share on deep levels) are classified and
+// get their four ring faces without touching memory apart from one stored twin; those created on
+// levels 0 and 1 need the level-0 arrays and take the general path.
 struct Birth {
-    int kind, m, c;
+    int m, k, c;
 };
-__device__ __forceinline__ Birth cc_birth(int l, int x, const Level0 &z) {
+__device__ __forceinline__ Birth cc_descend(int l, int x) {
     int m = l;
     while (m > 0 && (x & 3) == 0) { x >>= 2; --m; }
-    if (m == 0) return Birth{__ldg(z.vc + __ldg(z.fv + x)) == x ? 0 : -1, 0, x};
-    const int k = x & 3, c = x >> 2;
-    bool des;
-    if (k == 3) des = false;
-    else if (k == 1) des = m > 1 ? ((c & 3) < 2) : (__ldg(z.own + c) != 0);
-    else des = m > 1 ? ((c & 3) == 0) : (c == __ldg(z.off + __ldg(z.cf + c)));
-    return Birth{des ? k : -1, m, c};
+    return Birth{m, m == 0 ? 0 : (x & 3), m == 0 ? x : (x >> 2)};
 }
-
-// Eval part of the sibling-group step (see above). All loads that do not depend on shuffled
-// values are issued before the first shuffle; the stores come last.
-template <bool DERIVE>
-__device__ __forceinline__ void sib_eval(const CCArgs &a, int r, bool live, int4 v, int4 e, int4 t) {
-    const float *__restrict__ P = a.P;
-    const int *__restrict__ fv = a.fv;
-    const Level0 &z = a.z;
-    const int j = r & 3, VF = a.V + a.F;
-    const int s1 = t.x >> 2;                       // F1 = [a_j, y, z, b_j] across edge (a_j, b_j)
-    int4 g1 = make_int4(0, 0, 0, 0), g2 = g1;
-    float3 pa = f3(0.f, 0.f, 0.f), pb = pa, pc = pa;
-    Birth b{-1, 0, 0};
-    if (live) {
-        g1 = ld4(fv + 4 * (size_t)s1);
-        if (j < 2) g2 = ld4(fv + 4 * (size_t)quad_prev(s1));   // F2 = [a_{j+1}, b_j, z, w]
-        pa = ldpv(P, v.x, true);
-        pb = ldpv(P, v.y, true);
-        if (j == 0) pc = ldpv(P, v.z, true);
-        b = cc_birth(a.l, 4 * r, z);
-    }
-    pc = shfl4(pc, 0);                              // parent face point c
-    const float3 pd = shfl4(pb, (j + 3) & 3);       // b_{j-1}
-    const float3 fr = 0.25f * (pa + pb + pc + pd);  // face point of child j
-    const float3 fn = shfl4(fr, (j + 1) & 3);       // face point of child j+1
-    const float3 pan = shfl4(pa, (j + 1) & 3);      // a_{j+1}
-    const float3 pbn = shfl4(pb, (j + 1) & 3);      // b_{j+1}
-    const float3 sa = sum4(pa), sb = sum4(pb);
-    if (!live) return;
-    const float3 py = ldpv(P, g1.y, true), pz = ldpv(P, g1.z, true);
-    const float3 pw = j < 2 ? ldpv(P, g2.w, true) : f3(0.f, 0.f, 0.f);
-    // a vertex that already existed on level l - 1: its ring on level l follows from its birth,
-    // so the rows of its n incident faces are loaded independently of each other
-    float3 vp_old = f3(0.f, 0.f, 0.f);
-    bool has_old = false;
-    if (b.kind >= 0) {
-        const int sh = 2 * (a.l - b.m - 1);        // ring corner y of level m -> face y << sh of level l
-        float3 sn = f3(0.f, 0.f, 0.f), so = sn;
-        int n = 0;
-        auto visit = [&](int y) {
-            const int4 q = ld4(fv + 4 * ((size_t)y << sh));   // the vertex is corner 0 of this face
-            sn += ldpv(P, q.y, true);
-            so += ldpv(P, q.z, true);
-            n++;
-        };
-        if (b.kind == 1 || (b.kind == 2 && b.m > 1)) {
-            // valence 4: the face point of a quad (its four children) or an edge point (the
-            // children of its owner corner c, of c's twin t and of their successors)
-            int y0, y1, y2, y3;
-            if (b.kind == 2) {
-                y0 = 4 * b.c + 2; y1 = y0 + 4; y2 = y0 + 8; y3 = y0 + 12;
-            } else {
-                int tt, nc, nt;
-                if (b.m > 1) {
-                    tt = __ldg(a.twl[b.m - 1] + b.c);
-                    nc = quad_next(b.c);
-                    nt = quad_next(tt);
-                } else {
-                    tt = __ldg(z.tw + b.c);
-                    nc = __ldg(z.nx + b.c);
-                    nt = __ldg(z.nx + tt);
-                }
-                y0 = 4 * b.c + 1; y1 = 4 * nt + 3; y2 = 4 * tt + 1; y3 = 4 * nc + 3;
-            }
-            visit(y0);
-            visit(y1);
-            visit(y2);
-            visit(y3);
-        } else if (b.kind == 2) {
-            // the face point of a level-0 polygon of order c
-            const int Q = __ldg(z.cf + b.c), s0 = __ldg(z.off + Q), c = __ldg(z.off + Q + 1) - s0;
-            for (int i = 0; i < c; i++) visit(4 * (s0 + i) + 2);
-        } else {
-            int y = b.c;
-            do {
-                visit(y);
-                y = __ldg(z.tw + __ldg(z.pv + y));
-            } while (y != b.c && n < kMaxValence);
-            if (y != b.c) {
-                set_status(a.status, ALSUB_ERR_UNSUPPORTED);
-                n = 0;
-            }
-        }
-        if (n > 0) {
-            const float inv = 1.0f / (float)n;
-            vp_old = (1.0f - 1.75f * inv) * pa + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so;
-            has_old = true;
-        }
-    }
-    stpv(a.Pn, a.V + r, fr, a.out4);
-    // interior edge (b_j, c) between children j and j+1
-    stpv(a.Pn, VF + e.y, 0.25f * (pb + pc + fr + fn), a.out4);
-    // boundary edge (a_j, b_j) shared with F1
-    stpv(a.Pn, VF + e.x, 0.375f * (pa + pb) + 0.0625f * (pc + pd + py + pz), a.out4);
-    // face point c of the parent (valence 4): designated at child 0
-    if (j == 0) stpv(a.Pn, v.z, 0.5625f * pc + 0.09375f * sb + 0.015625f * sa, a.out4);
-    // edge point b_j of an owned parent edge (j < 2, valence 4): ring = children j, j+1, F1, F2
-    if (j < 2)
-        stpv(a.Pn, v.y, 0.5625f * pb + 0.09375f * (pc + pa + pz + pan) + 0.015625f * (pd + py + pw + pbn), a.out4);
-    if (has_old) stpv(a.Pn, v.x, vp_old, a.out4);
+// designated on levels >= 2 (ALU only)
+__device__ __forceinline__ int fast_kind(const Birth &b) {
+    if (b.m < 2) return -1;
+    if (b.k == 1 && (b.c & 3) < 2) return 1;
+    if (b.k == 2 && (b.c & 3) == 0) return 2;
+    return 0;   // not designated here
 }
 
 template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
@@ -347,9 +251,18 @@ __global__ void __launch_bounds__(kBlock, 4) k_cc_sib(CCArgs a) {
     const bool live = r < a.F;                  // F is a multiple of 4: groups are whole
     const int j = r & 3, R = r >> 2;
     const int VF = a.V + a.F, E2 = 2 * a.E, c0 = 4 * r;
+    const int *__restrict__ fv = a.fv;
+    const float *__restrict__ P = a.P;
+    const Level0 &z = a.z;
+
+    // ---- round trip 1: own row, adjacency rows, the twin an old vertex's ring needs
+    const Birth b = cc_descend(a.l, c0);
+    const int fk = (EVAL && live) ? fast_kind(b) : 0;
+    int tt = 0;
+    if (fk == 1) tt = __ldg(a.twl[b.m - 1] + b.c);
     int4 v = make_int4(0, 0, 0, 0), e = v, t = v;
     if (live) {
-        v = ld4(a.fv + 4 * (size_t)r);
+        v = ld4(fv + 4 * (size_t)r);
         if (DERIVE) {
             const int4 pe = ld4(a.pce + 4 * (size_t)R), pt = ld4(a.ptw + 4 * (size_t)R);
             const int jp = (j + 3) & 3, po = 4 * R + jp;
@@ -363,7 +276,108 @@ __global__ void __launch_bounds__(kBlock, 4) k_cc_sib(CCArgs a) {
             if (HELP || EVAL) t = ld4(a.tw + 4 * (size_t)r);
         }
     }
-    if (EVAL) sib_eval<DERIVE>(a, r, live, v, e, t);
+    if (EVAL) {
+        // ---- round trip 2: own positions, rows of the two faces across edge (a_j, b_j),
+        //      rows of the old vertex's ring
+        const int s1 = t.x >> 2;                   // F1 = [a_j, y, z, b_j]
+        int4 g1 = make_int4(0, 0, 0, 0), g2 = g1, q0 = g1, q1 = g1, q2 = g1, q3 = g1;
+        float3 pa = f3(0.f, 0.f, 0.f), pb = pa, pc = pa;
+        if (live) {
+            g1 = ld4(fv + 4 * (size_t)s1);
+            if (j < 2) g2 = ld4(fv + 4 * (size_t)quad_prev(s1));   // F2 = [a_{j+1}, b_j, z, w]
+            pa = ldpv(P, v.x, true);
+            pb = ldpv(P, v.y, true);
+            if (j == 0) pc = ldpv(P, v.z, true);
+        }
+        if (fk > 0) {
+            // ring corners y on level m; the vertex is corner 0 of face y << sh on level l
+            const int sh = 2 * (a.l - b.m - 1);
+            int y0, y1, y2, y3;
+            if (fk == 2) {
+                y0 = 4 * b.c + 2; y1 = y0 + 4; y2 = y0 + 8; y3 = y0 + 12;
+            } else {
+                y0 = 4 * b.c + 1; y1 = 4 * quad_next(tt) + 3; y2 = 4 * tt + 1; y3 = 4 * quad_next(b.c) + 3;
+            }
+            q0 = ld4(fv + 4 * ((size_t)y0 << sh));
+            q1 = ld4(fv + 4 * ((size_t)y1 << sh));
+            q2 = ld4(fv + 4 * ((size_t)y2 << sh));
+            q3 = ld4(fv + 4 * ((size_t)y3 << sh));
+        }
+        pc = shfl4(pc, 0);                              // parent face point c
+        const float3 pd = shfl4(pb, (j + 3) & 3);       // b_{j-1}
+        const float3 fr = 0.25f * (pa + pb + pc + pd);  // face point of child j
+        const float3 fn = shfl4(fr, (j + 1) & 3);       // face point of child j+1
+        const float3 pan = shfl4(pa, (j + 1) & 3);      // a_{j+1}
+        const float3 pbn = shfl4(pb, (j + 1) & 3);      // b_{j+1}
+        const float3 sa = sum4(pa), sb = sum4(pb);
+        if (live) {
+            // ---- round trip 3: far vertices across (a_j, b_j), the old vertex's ring
+            const float3 py = ldpv(P, g1.y, true), pz = ldpv(P, g1.z, true);
+            const float3 pw = j < 2 ? ldpv(P, g2.w, true) : f3(0.f, 0.f, 0.f);
+            float3 vp_old = f3(0.f, 0.f, 0.f);
+            if (fk > 0) {
+                // valence 4: (1 - 7/16) p + 3/32 sum next + 1/64 sum opp
+                const float3 sn = ldpv(P, q0.y, true) + ldpv(P, q1.y, true) + ldpv(P, q2.y, true) + ldpv(P, q3.y, true);
+                const float3 so = ldpv(P, q0.z, true) + ldpv(P, q1.z, true) + ldpv(P, q2.z, true) + ldpv(P, q3.z, true);
+                vp_old = 0.5625f * pa + 0.09375f * sn + 0.015625f * so;
+            }
+            stpv(a.Pn, a.V + r, fr, a.out4);
+            // interior edge (b_j, c) between children j and j+1
+            stpv(a.Pn, VF + e.y, 0.25f * (pb + pc + fr + fn), a.out4);
+            // boundary edge (a_j, b_j) shared with F1
+            stpv(a.Pn, VF + e.x, 0.375f * (pa + pb) + 0.0625f * (pc + pd + py + pz), a.out4);
+            // face point c of the parent (valence 4): designated at child 0
+            if (j == 0) stpv(a.Pn, v.z, 0.5625f * pc + 0.09375f * sb + 0.015625f * sa, a.out4);
+            // edge point b_j of an owned parent edge (j < 2, valence 4): ring = children j, j+1, F1, F2
+            if (j < 2)
+                stpv(a.Pn, v.y, 0.5625f * pb + 0.09375f * (pc + pa + pz + pan) + 0.015625f * (pd + py + pw + pbn),
+                     a.out4);
+            if (fk > 0) stpv(a.Pn, v.x, vp_old, a.out4);
+            if (fk < 0 && b.k != 3) {
+                // created on level 0 or 1: designation and ring need the level-0 arrays
+                bool des;
+                if (b.m == 0) des = __ldg(z.vc + __ldg(z.fv + b.c)) == b.c;
+                else if (b.k == 1) des = __ldg(z.own + b.c) != 0;
+                else des = b.c == __ldg(z.off + __ldg(z.cf + b.c));
+                if (des) {
+                    const int sh = 2 * (a.l - b.m - 1);
+                    float3 sn = f3(0.f, 0.f, 0.f), so = sn;
+                    int n = 0;
+                    auto visit = [&](int y) {
+                        const int4 q = ld4(fv + 4 * ((size_t)y << sh));
+                        sn += ldpv(P, q.y, true);
+                        so += ldpv(P, q.z, true);
+                        n++;
+                    };
+                    bool ok = true;
+                    if (b.m == 0) {
+                        int y = b.c;
+                        do {
+                            visit(y);
+                            y = __ldg(z.tw + __ldg(z.pv + y));
+                        } while (y != b.c && n < kMaxValence);
+                        ok = y == b.c;
+                    } else if (b.k == 1) {
+                        const int t0 = __ldg(z.tw + b.c);
+                        visit(4 * b.c + 1);
+                        visit(4 * __ldg(z.nx + t0) + 3);
+                        visit(4 * t0 + 1);
+                        visit(4 * __ldg(z.nx + b.c) + 3);
+                    } else {
+                        const int Q = __ldg(z.cf + b.c), s0 = __ldg(z.off + Q), c = __ldg(z.off + Q + 1) - s0;
+                        for (int i = 0; i < c; i++) visit(4 * (s0 + i) + 2);
+                    }
+                    if (!ok) {
+                        set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                    } else {
+                        const float inv = 1.0f / (float)n;
+                        stpv(a.Pn, v.x, (1.0f - 1.75f * inv) * pa + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so,
+                             a.out4);
+                    }
+                }
+            }
+        }
+    }
     if (TOPO && live) {
         int *o = a.fvn + 16 * (size_t)r;
         st4(o + 0, make_int4(v.x, VF + e.x, a.V + r, VF + e.w));
