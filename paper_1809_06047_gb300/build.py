@@ -16,6 +16,8 @@ SOURCES = ["scan.cu", "level0.cu", "cc.cu", "tri.cu", "crease.cu", "api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "-I", CSRC, "--expt-relaxed-constexpr"]
+# extra definitions for tuning builds, e.g. ALSUB_NVCC_DEFS="-DALSUB_SIB_MIN_BLOCKS=5"
+NVCC_FLAGS += os.environ.get("ALSUB_NVCC_DEFS", "").split()
 
 
 def _nvcc() -> str:

@@ -20,6 +20,11 @@
 #include "common.cuh"
 #include "internal.h"
 
+// Resident 256-thread blocks per SM the sibling kernel is compiled for (register budget).
+#ifndef ALSUB_SIB_MIN_BLOCKS
+#define ALSUB_SIB_MIN_BLOCKS 4
+#endif
+
 namespace alsub {
 
 namespace {
@@ -245,7 +250,7 @@ __device__ __forceinline__ int fast_kind(const Birth &b) {
 }
 
 template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
-__global__ void __launch_bounds__(kBlock, 4) k_cc_sib(CCArgs a) {
+__global__ void __launch_bounds__(kBlock, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (failed(a.status)) return;
     const bool live = r < a.F;                  // F is a multiple of 4: groups are whole
