@@ -213,6 +213,27 @@ alsub_status alsub_topology_set_timing(alsub_topology_t topo, int32_t capacity);
 alsub_status alsub_topology_timings(alsub_topology_t topo, double *ms_host, int32_t *calls,
                                     int64_t *launches);
 
+/*
+ * Vertex refinement that allocates nothing. The paper has no counterpart: this entry point exists
+ * for callers that cannot allocate device memory at the point where they refine (for example
+ * code running inside another allocator's callback, or a process that forbids device allocation
+ * after start-up) and cannot pass a scratch buffer of their own.
+ * It computes exactly what alsub_refine_vertices computes, with the intermediate levels held in a
+ * fixed 32 MiB array compiled into the library (every GPU that loads the library keeps it until
+ * the process exits) instead of the handle's or the caller's scratch. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   P0_dev: float[3 * V_0]; PL_dev: float[3 * V_levels]; both caller-owned device memory.
+ * The first call on a device looks up the array's device address on the current device; make
+ * that first call before any stream capture. All calls share the one array and it keeps the last
+ * call's contents (nothing in it needs to start at zero): calls that overlap on the GPU race, so
+ * serialise them (one stream, or events).
+ * Errors: INVALID_ARG (NULL argument), UNSUPPORTED when the topology's intermediate levels need
+ * more than 32 MiB (alsub_refine_vertices_scratch_bytes tells the need), DEVICE, and the errors
+ * of alsub_refine_vertices.
+ */
+alsub_status alsub_refine_vertices_static(alsub_topology_t topo, const float *P0_dev, float *PL_dev,
+                                          void *stream);
+
 #ifdef __cplusplus
 }
 #endif

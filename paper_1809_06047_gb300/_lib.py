@@ -32,6 +32,7 @@ SIGNATURES = {
     "alsub_subdivide": [H, c_void_p, c_void_p, c_void_p, c_void_p],
     "alsub_topology_set_timing": [H, c_int32],
     "alsub_topology_timings": [H, P(ctypes.c_double), P(c_int32), P(c_int64)],
+    "alsub_refine_vertices_static": [H, c_void_p, c_void_p, c_void_p],
 }
 _RESTYPE = {"alsub_last_error": ctypes.c_char_p, "alsub_status_string": ctypes.c_char_p}
 

@@ -178,6 +178,18 @@ class Topology:
         """alsub_refine_vertices: eval of all levels on the built topology."""
         return self._run(lib().alsub_refine_vertices, P0, out, scratch, stream)
 
+    def refine_vertices_static(self, P0: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        """alsub_refine_vertices_static: the same eval with the library's fixed scratch array."""
+        assert P0.is_cuda and P0.dtype == torch.float32 and P0.is_contiguous()
+        VL = self.counts[-1]["V"]
+        if out is None:
+            out = torch.empty((VL, 3), dtype=torch.float32, device=P0.device)
+        assert out.is_contiguous() and out.numel() == 3 * VL
+        _check(lib().alsub_refine_vertices_static(self._h, ctypes.c_void_p(P0.data_ptr()),
+                                                  ctypes.c_void_p(out.data_ptr()),
+                                                  ctypes.c_void_p(_stream(stream))))
+        return out
+
     def set_timing(self, capacity: int):
         """alsub_topology_set_timing: record per-level CUDA events for the next `capacity` calls."""
         _check(lib().alsub_topology_set_timing(self._h, int(capacity)))

@@ -214,6 +214,8 @@ void free_events(TopoImpl &T) {
 
 }  // namespace
 
+alsub_status alsub::report(alsub_status s, const char *msg) { return fail(s, "%s", msg); }
+
 extern "C" {
 
 const char *alsub_last_error(void) { return g_err.c_str(); }

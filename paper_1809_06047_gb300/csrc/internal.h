@@ -108,4 +108,7 @@ int crease_export(TopoImpl &T, int l, cudaStream_t s);
 // Device-side constant tables (Loop beta_n, sqrt(3) alpha_n) filled once per process.
 void upload_weight_tables();
 
+// Record `msg` as the calling thread's last error and return `s`.
+alsub_status report(alsub_status s, const char *msg);
+
 }  // namespace alsub
