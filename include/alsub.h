@@ -195,6 +195,50 @@ alsub_status alsub_subdivide(alsub_topology_t topo, const float *P0_dev, float *
                              void *scratch_dev, void *stream);
 
 /*
+ * Subdivision operator (Sec. 3.5 "Single SpMV evaluation", Eq. singleSpMV): R_l maps the positions
+ * of level l to those of level l+1 (P_{l+1} = R_l P_l), R = R_{L-1} ... R_0 maps the control mesh
+ * to the last level. Built from a built topology in the paper's two stages (count the non-zeros
+ * of every row, then fill column indices and FP32 weights); rows are sorted by column.
+ *   flags: ALSUB_OP_CHAIN keeps every R_l (apply = L SpMVs); ALSUB_OP_COMPOSE forms R by row-wise
+ *          sparse products (apply = one SpMV; memory ~ rows x support); ALSUB_OP_TRANSPOSE also
+ *          builds the transposes for alsub_apply_operator_transpose (the adjoint g_0 = R^T g_L).
+ * Weights: Catmull-Clark face row 1/c; edge row 1/4 on the endpoints and 1/(4c) on every vertex of
+ * both faces (Eq. 2 with Eq. 1 expanded); vertex row (1 - 2/n) on the vertex, 1/n^2 on each
+ * neighbour and 1/(n^2 c) on every vertex of each incident face (Eq. pos_update); Loop and sqrt(3)
+ * per Appendices B and A; crease rows blended as in alsub_refine_vertices.
+ * The operator keeps a pointer to the topology, which must outlive it. Synchronises `stream`
+ * (the non-zero counts size the allocations).
+ * Errors: INVALID_ARG (topology not built, no flags), UNSUPPORTED (a stencil row of more than 192
+ * entries), OOM, DEVICE.
+ */
+typedef enum { ALSUB_OP_CHAIN = 1, ALSUB_OP_COMPOSE = 2, ALSUB_OP_TRANSPOSE = 4 } alsub_operator_flags;
+
+alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *stream,
+                                  alsub_operator_t *out);
+
+/*
+ * Size and device CSR arrays of one matrix of the operator: level >= 0 for R_level (needs
+ * ALSUB_OP_CHAIN), level < 0 for the composite R (needs ALSUB_OP_COMPOSE). rowptr: int64[rows+1],
+ * col: int32[nnz], w: float[nnz], owned by the operator. Any out pointer may be NULL.
+ */
+alsub_status alsub_operator_info(alsub_operator_t op, int32_t level, int64_t *rows, int64_t *cols,
+                                 int64_t *nnz, const int64_t **rowptr_dev, const int32_t **col_dev,
+                                 const float **w_dev);
+
+/* P_L = R P_0 on `stream` (one SpMV with the composite, else the chain of R_l). P0_dev:
+ * float[3 V_0], PL_dev: float[3 V_L] (packed xyz). Calls on one operator must not overlap when
+ * the chain is used (it keeps intermediate levels in the operator). */
+alsub_status alsub_apply_operator(alsub_operator_t op, const float *P0_dev, float *PL_dev, void *stream);
+
+/* g_0 = R^T g_L (the adjoint of vertex refinement: vertex refinement is linear in P, so this is
+ * the exact gradient of any loss of P_L with respect to P_0 given g_L = dLoss/dP_L). Needs
+ * ALSUB_OP_TRANSPOSE. gL_dev: float[3 V_L], g0_dev: float[3 V_0]. */
+alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL_dev, float *g0_dev,
+                                            void *stream);
+
+alsub_status alsub_operator_destroy(alsub_operator_t op);
+
+/*
  * Live timing of the library's own work on the calling stream. capacity > 0 allocates
  * capacity x (levels + 2) CUDA events and makes every following alsub_subdivide /
  * alsub_refine_vertices call on the handle record one event before its level-0 build, one after

@@ -33,6 +33,12 @@ SIGNATURES = {
     "alsub_topology_set_timing": [H, c_int32],
     "alsub_topology_timings": [H, P(ctypes.c_double), P(c_int32), P(c_int64)],
     "alsub_refine_vertices_static": [H, c_void_p, c_void_p, c_void_p],
+    "alsub_build_operator": [H, ctypes.c_uint32, c_void_p, P(H)],
+    "alsub_operator_info": [H, c_int32, P(c_int64), P(c_int64), P(c_int64), P(c_void_p), P(c_void_p),
+                            P(c_void_p)],
+    "alsub_apply_operator": [H, c_void_p, c_void_p, c_void_p],
+    "alsub_apply_operator_transpose": [H, c_void_p, c_void_p, c_void_p],
+    "alsub_operator_destroy": [H],
 }
 _RESTYPE = {"alsub_last_error": ctypes.c_char_p, "alsub_status_string": ctypes.c_char_p}
 

@@ -205,3 +205,68 @@ class Topology:
     def subdivide(self, P0: torch.Tensor, out=None, scratch=None, stream=None) -> torch.Tensor:
         """alsub_subdivide: rebuild the topology and refine the vertices, fused per level."""
         return self._run(lib().alsub_subdivide, P0, out, scratch, stream)
+
+
+class Operator:
+    """alsub_build_operator and friends: R_l per level and/or the composite R = R_{L-1}...R_0."""
+
+    CHAIN, COMPOSE, TRANSPOSE = 1, 2, 4
+
+    def __init__(self, topo: Topology, chain: bool = True, compose: bool = False,
+                 transpose: bool = False, stream=None):
+        self.topo = topo          # the topology must outlive the operator
+        flags = (self.CHAIN if chain else 0) | (self.COMPOSE if compose else 0) | \
+            (self.TRANSPOSE if transpose else 0)
+        self._h = ctypes.c_void_p()
+        _check(lib().alsub_build_operator(topo.handle, flags, ctypes.c_void_p(_stream(stream)),
+                                          ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            _check(lib().alsub_operator_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+    def info(self, level: int = -1) -> dict:
+        rows, cols, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().alsub_operator_info(self._h, level, ctypes.byref(rows), ctypes.byref(cols),
+                                         ctypes.byref(nnz), None, None, None))
+        return dict(rows=rows.value, cols=cols.value, nnz=nnz.value)
+
+    def csr(self, level: int = -1, stream=None):
+        """Host copies (rowptr int64[rows+1], col int32[nnz], w float32[nnz]) of one matrix."""
+        rows, cols, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        rp, cl, w = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().alsub_operator_info(self._h, level, ctypes.byref(rows), ctypes.byref(cols),
+                                         ctypes.byref(nnz), ctypes.byref(rp), ctypes.byref(cl),
+                                         ctypes.byref(w)))
+        n, z = rows.value, nnz.value
+        return (copy_to_host(rp.value, 8 * (n + 1), np.int64, n + 1, stream),
+                copy_to_host(cl.value, 4 * z, np.int32, z, stream),
+                copy_to_host(w.value, 4 * z, np.float32, z, stream))
+
+    def apply(self, P0: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        """alsub_apply_operator: P_L = R P_0."""
+        assert P0.is_cuda and P0.dtype == torch.float32 and P0.is_contiguous()
+        VL = self.topo.counts[-1]["V"]
+        if out is None:
+            out = torch.empty((VL, 3), dtype=torch.float32, device=P0.device)
+        _check(lib().alsub_apply_operator(self._h, ctypes.c_void_p(P0.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream(stream))))
+        return out
+
+    def apply_transpose(self, gL: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        """alsub_apply_operator_transpose: g_0 = R^T g_L."""
+        assert gL.is_cuda and gL.dtype == torch.float32 and gL.is_contiguous()
+        V0 = self.topo.counts[0]["V"]
+        if out is None:
+            out = torch.empty((V0, 3), dtype=torch.float32, device=gL.device)
+        _check(lib().alsub_apply_operator_transpose(self._h, ctypes.c_void_p(gL.data_ptr()),
+                                                    ctypes.c_void_p(out.data_ptr()),
+                                                    ctypes.c_void_p(_stream(stream))))
+        return out

@@ -216,6 +216,21 @@ void free_events(TopoImpl &T) {
 
 alsub_status alsub::report(alsub_status s, const char *msg) { return fail(s, "%s", msg); }
 
+TopoImpl *alsub::topology_impl(alsub_topology_t h) { return &h->t; }
+
+alsub_status alsub::ensure_helpers(TopoImpl &T, cudaStream_t s) {
+    for (int l = 1; l < T.levels; l++) {
+        LevelBuf &B = T.L[l];
+        if (B.helpers) continue;
+        if (T.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);
+        AL(B.tw, B.nnz);
+        B.helpers = true;
+        // redo the build of level l from level l - 1, now also emitting its edge ids and twins
+        step(T, l - 1, true, true, nullptr, nullptr, s);
+    }
+    return finish("ensure_helpers");
+}
+
 extern "C" {
 
 const char *alsub_last_error(void) { return g_err.c_str(); }

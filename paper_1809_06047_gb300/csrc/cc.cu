@@ -44,32 +44,11 @@ struct CCArgs {
     int *status;
 };
 
-// Is corner x of level l the designated corner of its start vertex? Follows the vertex back to
-// the level where it was created: an old vertex inherits from its parent corner, the edge point
-// of parent edge e is designated at the child of e's owner corner, the face point of parent face
-// r at the child of r's first corner.
-__device__ __forceinline__ bool cc_vown(int l, int x, const Level0 &z) {
-    while (l > 0) {
-        int k = x & 3, c = x >> 2;
-        if (k == 0) { x = c; --l; continue; }
-        if (k == 3) return false;
-        if (k == 1) return l > 1 ? ((c & 3) < 2) : (__ldg(z.own + c) != 0);
-        return l > 1 ? ((c & 3) == 0) : (c == __ldg(z.off + __ldg(z.cf + c)));
-    }
-    return __ldg(z.vc + __ldg(z.fv + x)) == x;
-}
-
 __device__ __forceinline__ float3 face_point_l0(const Level0 &z, const float *P, int g) {
     int s = __ldg(z.off + g), c = __ldg(z.off + g + 1) - s;
     float3 acc = f3(0.f, 0.f, 0.f);
     for (int j = 0; j < c; j++) acc += ldp(P, __ldg(z.fv + s + j));
     return (1.0f / (float)c) * acc;
-}
-
-__device__ __forceinline__ int4 ld4(const int *p) { return __ldg(reinterpret_cast<const int4 *>(p)); }
-__device__ __forceinline__ void st4(int *p, int4 v) { *reinterpret_cast<int4 *>(p) = v; }
-__device__ __forceinline__ int comp(int4 v, int k) {
-    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
 }
 
 template <bool TOPO, bool HELP, bool EVAL>

@@ -110,6 +110,59 @@ struct AccTri {
     __device__ int vtx(int x) const { return __ldg(fv + x); }
 };
 
+__device__ __forceinline__ int4 ld4(const int *p) { return __ldg(reinterpret_cast<const int4 *>(p)); }
+__device__ __forceinline__ void st4(int *p, int4 v) { *reinterpret_cast<int4 *>(p) = v; }
+__device__ __forceinline__ int comp(int4 v, int k) {
+    return k == 0 ? v.x : (k == 1 ? v.y : (k == 2 ? v.z : v.w));
+}
+
+// ---- designated corners. Every vertex of a level is gathered (or gets its operator row) from
+// exactly one of its corners. Each test follows the vertex back to the level where it was
+// created: an old vertex inherits from its parent corner, an edge point is designated at a child
+// of its edge's owner corner, a face point at a child of its face's first corner; level-0 vertices
+// use their smallest outgoing corner (vc).
+
+// Catmull-Clark, corner x of level l (levels >= 1 are quads: child k of parent corner c is 4c+k).
+__device__ __forceinline__ bool cc_vown(int l, int x, const Level0 &z) {
+    while (l > 0) {
+        int k = x & 3, c = x >> 2;
+        if (k == 0) { x = c; --l; continue; }
+        if (k == 3) return false;
+        if (k == 1) return l > 1 ? ((c & 3) < 2) : (__ldg(z.own + c) != 0);
+        return l > 1 ? ((c & 3) == 0) : (c == __ldg(z.off + __ldg(z.cf + c)));
+    }
+    return __ldg(z.vc + __ldg(z.fv + x)) == x;
+}
+
+// Loop: does corner x of level l own its edge?
+__device__ __forceinline__ bool loop_own(int l, int x, const Level0 &z) {
+    if (l == 0) return __ldg(z.own + x) != 0;
+    int g = x / 3, i = x - 3 * g;
+    return (g & 3) < 3 && i < 2;
+}
+
+// Loop: corner i of child j of triangle r is 3(4r + j) + i.
+__device__ __forceinline__ bool loop_vown(int l, int x, const Level0 &z) {
+    while (l > 0) {
+        int g = x / 3, i = x - 3 * g, r = g >> 2, j = g & 3;
+        if (j == 3 || i == 2) return false;
+        if (i == 0) { x = 3 * r + j; --l; continue; }
+        return loop_own(l - 1, 3 * r + j, z);
+    }
+    return __ldg(z.vc + __ldg(z.fv + x)) == x;
+}
+
+// sqrt(3): corner k of child c (the child of parent corner c) is 3c + k.
+__device__ __forceinline__ bool sqrt3_vown(int l, int x, const Level0 &z) {
+    while (l > 0) {
+        int c = x / 3, k = x - 3 * c;
+        if (k == 0) { x = c; --l; continue; }
+        if (k == 1) return false;
+        return c % 3 == 0;
+    }
+    return __ldg(z.vc + __ldg(z.fv + x)) == x;
+}
+
 // Crease hash table (CreaseList::tab): linear probing from a multiplicative hash.
 __device__ __forceinline__ unsigned crease_slot(int e, int shift) {
     return shift >= 32 ? 0u : ((unsigned)e * 2654435761u) >> shift;

@@ -86,6 +86,9 @@ struct TopoImpl {
 size_t scan_tmp_bytes(long long n);
 int scan_exclusive(const int *in, int *out, long long n, int *total, const int *n_dev, void *tmp,
                    cudaStream_t s);  // returns the number of kernels launched
+// Same over int32 counts into int64 offsets (operator row pointers).
+int scan_exclusive64(const int *in, long long *out, long long n, long long *total, void *tmp,
+                     cudaStream_t s);
 
 // Level 0: corner maps, twins, ownership, edge numbering, crease list of level 0.
 void level0_build(TopoImpl &T, cudaStream_t s);
@@ -110,5 +113,11 @@ void upload_weight_tables();
 
 // Record `msg` as the calling thread's last error and return `s`.
 alsub_status report(alsub_status s, const char *msg);
+
+// The implementation behind a topology handle.
+TopoImpl *topology_impl(alsub_topology_t h);
+// Store the per-corner edge ids and twins of every level below the last one (the last
+// Catmull-Clark step normally derives them on the fly); the operator builder reads them.
+alsub_status ensure_helpers(TopoImpl &T, cudaStream_t s);
 
 }  // namespace alsub

@@ -39,34 +39,6 @@ struct TriArgs {
     int *status;
 };
 
-__device__ __forceinline__ bool loop_own(int l, int x, const Level0 &z) {
-    if (l == 0) return __ldg(z.own + x) != 0;
-    int g = x / 3, i = x - 3 * g;
-    return (g & 3) < 3 && i < 2;
-}
-
-// Designated corner of a vertex (see the Catmull-Clark step): old vertices inherit from the
-// corner-0 child of their parent corner, the edge point of parent edge e_j is designated at
-// corner 1 of child j of e_j's owner face.
-__device__ __forceinline__ bool loop_vown(int l, int x, const Level0 &z) {
-    while (l > 0) {
-        int g = x / 3, i = x - 3 * g, r = g >> 2, j = g & 3;
-        if (j == 3 || i == 2) return false;
-        if (i == 0) { x = 3 * r + j; --l; continue; }
-        return loop_own(l - 1, 3 * r + j, z);
-    }
-    return __ldg(z.vc + __ldg(z.fv + x)) == x;
-}
-
-__device__ __forceinline__ bool sqrt3_vown(int l, int x, const Level0 &z) {
-    while (l > 0) {
-        int c = x / 3, k = x - 3 * c;
-        if (k == 0) { x = c; --l; continue; }
-        if (k == 1) return false;
-        return c % 3 == 0;
-    }
-    return __ldg(z.vc + __ldg(z.fv + x)) == x;
-}
 
 template <bool TOPO, bool HELP, bool EVAL>
 __global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
