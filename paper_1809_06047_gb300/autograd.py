@@ -1,0 +1,38 @@
+"""Differentiable subdivision: a torch.autograd.Function around libalsub.
+
+Vertex refinement is linear in the control positions (P_L = R P_0, Sec. 3.5 Eq. singleSpMV), so
+the gradient of any loss of P_L is g_0 = R^T g_L. Forward runs the fused eval kernels
+(alsub_refine_vertices); backward applies the transposed per-level operators
+g_l = R_l^T g_{l+1} (alsub_apply_operator_transpose on an ALSUB_OP_CHAIN operator), which depend
+on the topology only: no intermediate positions are kept for the backward pass.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import alsub
+
+
+class Refine(torch.autograd.Function):
+    """P_L = refine(P_0) on a fixed topology; d/dP_0 = R^T."""
+
+    @staticmethod
+    def forward(ctx, P0: torch.Tensor, topo: alsub.Topology, op: alsub.Operator):
+        ctx.op = op
+        return topo.refine_vertices(P0.detach().contiguous())
+
+    @staticmethod
+    def backward(ctx, gL: torch.Tensor):
+        return ctx.op.apply_transpose(gL.contiguous()), None, None
+
+
+class Subdivider:
+    """A topology plus its transposed per-level operators, ready for forward and backward."""
+
+    def __init__(self, mesh: dict, levels: int | None = None, scheme: str | None = None):
+        self.mesh = alsub.Mesh.from_dict(mesh, scheme)
+        self.topo = alsub.Topology(self.mesh, levels if levels is not None else mesh["levels"])
+        self.op = alsub.Operator(self.topo, chain=True, transpose=True)
+
+    def __call__(self, P0: torch.Tensor) -> torch.Tensor:
+        return Refine.apply(P0, self.topo, self.op)
