@@ -239,6 +239,38 @@ alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL
 alsub_status alsub_operator_destroy(alsub_operator_t op);
 
 /*
+ * Ragged batches (no counterpart in the paper's text; it processes one mesh per call): vertex
+ * refinement of n built topologies of uneven sizes, any mix of schemes and level counts, with one
+ * kernel launch per level per kernel class over a flattened work list of face tiles (per-member
+ * closed-form sizes; persistent grid). Member i reads P0_dev[i] (float[3 V_0]) and writes PL_dev[i]
+ * (float[3 V_L]) exactly as alsub_refine_vertices(topos[i], ...) would, using that topology's own
+ * scratch, so a topology may appear only once and must not be refined elsewhere while the batch
+ * runs. The buffers are bound at creation: to refine new positions, write them into P0_dev[i].
+ */
+typedef struct alsub_batch_s *alsub_batch_t;
+
+alsub_status alsub_batch_create(int32_t n, const alsub_topology_t *topos, const float *const *P0_dev,
+                                float *const *PL_dev, alsub_batch_t *out);
+
+/* Run the batch on `stream`. On a non-default stream the first call captures the whole launch
+ * sequence into a CUDA graph, later calls on that stream replay it. */
+alsub_status alsub_batch_refine(alsub_batch_t batch, void *stream);
+
+/* Set the block size (128, 256 or 512 faces per tile) and the persistent grid (blocks per SM,
+ * 0 = one block per tile); synchronises the device. */
+alsub_status alsub_batch_configure(alsub_batch_t batch, int32_t block, int32_t blocks_per_sm);
+
+/* Autotuner: time every block size x persistence candidate on this batch (2 warm-up and 5 timed
+ * runs each, CUDA events on `stream`), keep the fastest and return it. */
+alsub_status alsub_batch_tune(alsub_batch_t batch, void *stream, int32_t *block,
+                              int32_t *blocks_per_sm, float *best_ms);
+
+/* Kernels launched by all alsub_batch_refine calls so far. */
+alsub_status alsub_batch_launches(alsub_batch_t batch, int64_t *launches);
+
+alsub_status alsub_batch_destroy(alsub_batch_t batch);
+
+/*
  * Live timing of the library's own work on the calling stream. capacity > 0 allocates
  * capacity x (levels + 2) CUDA events and makes every following alsub_subdivide /
  * alsub_refine_vertices call on the handle record one event before its level-0 build, one after

@@ -39,6 +39,12 @@ SIGNATURES = {
     "alsub_apply_operator": [H, c_void_p, c_void_p, c_void_p],
     "alsub_apply_operator_transpose": [H, c_void_p, c_void_p, c_void_p],
     "alsub_operator_destroy": [H],
+    "alsub_batch_create": [c_int32, c_void_p, c_void_p, c_void_p, P(H)],
+    "alsub_batch_refine": [H, c_void_p],
+    "alsub_batch_configure": [H, c_int32, c_int32],
+    "alsub_batch_tune": [H, c_void_p, P(c_int32), P(c_int32), P(ctypes.c_float)],
+    "alsub_batch_launches": [H, P(c_int64)],
+    "alsub_batch_destroy": [H],
 }
 _RESTYPE = {"alsub_last_error": ctypes.c_char_p, "alsub_status_string": ctypes.c_char_p}
 

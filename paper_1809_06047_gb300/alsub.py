@@ -270,3 +270,50 @@ class Operator:
                                                     ctypes.c_void_p(out.data_ptr()),
                                                     ctypes.c_void_p(_stream(stream))))
         return out
+
+
+class Batch:
+    """alsub_batch_*: vertex refinement of many built topologies in one launch per level and
+    kernel class, replayed from a CUDA graph."""
+
+    def __init__(self, topos, P0s, PLs=None):
+        self.topos = list(topos)
+        self.P0s = list(P0s)
+        self.PLs = PLs if PLs is not None else [
+            torch.empty((t.counts[-1]["V"], 3), dtype=torch.float32, device=p.device)
+            for t, p in zip(self.topos, self.P0s)]
+        n = len(self.topos)
+        th = (ctypes.c_void_p * n)(*[t.handle.value for t in self.topos])
+        p0 = (ctypes.c_void_p * n)(*[p.data_ptr() for p in self.P0s])
+        pl = (ctypes.c_void_p * n)(*[p.data_ptr() for p in self.PLs])
+        self._h = ctypes.c_void_p()
+        _check(lib().alsub_batch_create(n, th, p0, pl, ctypes.byref(self._h)))
+
+    def refine(self, stream=None):
+        _check(lib().alsub_batch_refine(self._h, ctypes.c_void_p(_stream(stream))))
+        return self.PLs
+
+    def configure(self, block: int, blocks_per_sm: int):
+        _check(lib().alsub_batch_configure(self._h, block, blocks_per_sm))
+
+    def tune(self, stream=None):
+        b, p, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        _check(lib().alsub_batch_tune(self._h, ctypes.c_void_p(_stream(stream)), ctypes.byref(b),
+                                      ctypes.byref(p), ctypes.byref(ms)))
+        return dict(block=b.value, blocks_per_sm=p.value, ms=ms.value)
+
+    def launches(self) -> int:
+        n = ctypes.c_int64()
+        _check(lib().alsub_batch_launches(self._h, ctypes.byref(n)))
+        return n.value
+
+    def close(self):
+        if self._h:
+            _check(lib().alsub_batch_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass

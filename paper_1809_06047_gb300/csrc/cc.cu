@@ -17,6 +17,8 @@
 //                its split form) gathered by the one corner designated for the vertex, walking the
 //                ring x <- twin(prev(x)). The gather replaces the paper's atomic scatter (direct
 //                mapped SpMV, Sec. 4.3) so that results are bit-reproducible.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -52,8 +54,7 @@ __device__ __forceinline__ float3 face_point_l0(const Level0 &z, const float *P,
 }
 
 template <bool TOPO, bool HELP, bool EVAL>
-__global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const Level0 &z = a.z;
     const int s = __ldg(z.off + r), c = __ldg(z.off + r + 1) - s;
@@ -103,8 +104,7 @@ __global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
 }
 
 template <bool TOPO, bool HELP, bool EVAL>
-__global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cc_quad_body(const CCArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const int VF = a.V + a.F, E2 = 2 * a.E, c0 = 4 * r;
     const int4 v = ld4(a.fv + 4 * (size_t)r);
@@ -229,8 +229,7 @@ __device__ __forceinline__ int fast_kind(const Birth &b) {
 }
 
 template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
-__global__ void __launch_bounds__(kBlock, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
     if (failed(a.status)) return;
     const bool live = r < a.F;                  // F is a multiple of 4: groups are whole
     const int j = r & 3, R = r >> 2;
@@ -383,6 +382,47 @@ __global__ void __launch_bounds__(kBlock, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs 
     }
 }
 
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
+    cc_l0_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
+    cc_quad_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
+__global__ void __launch_bounds__(kBlock, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
+    cc_sib_body<TOPO, HELP, EVAL, DERIVE>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Ragged batches: the eval steps of many topologies at one level in one persistent launch per
+// kernel class. The work list is the concatenation of every item's faces cut into tiles of
+// blockDim.x faces (tile_begin[i] = first tile of item i, closed-form sizes); each CTA walks
+// tiles with a grid stride and finds its item by binary search.
+__device__ __forceinline__ int item_of(const int *__restrict__ tile_begin, int n, int tile) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (__ldg(tile_begin + mid) <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <int KIND>   // 0 level 0, 1 level 1, 2 levels >= 2, 3 levels >= 2 with derived E/F
+__global__ void __launch_bounds__(512, 2) k_cc_batch(const CCArgs *__restrict__ items,
+                                                     const int *__restrict__ tile_begin, int n, int tiles) {
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int i = item_of(tile_begin, n, tile);
+        const int r = (tile - __ldg(tile_begin + i)) * blockDim.x + threadIdx.x;
+        const CCArgs a = items[i];
+        if (KIND == 0) cc_l0_body<false, false, true>(a, r);
+        else if (KIND == 1) cc_quad_body<false, false, true>(a, r);
+        else if (KIND == 2) cc_sib_body<false, false, true, false>(a, r);
+        else cc_sib_body<false, false, true, true>(a, r);
+    }
+}
+
 template <bool T, bool H, bool E>
 void launch(const CCArgs &a, bool derive, cudaStream_t s) {
     if (a.l == 0) k_cc_l0<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
@@ -393,7 +433,9 @@ void launch(const CCArgs &a, bool derive, cudaStream_t s) {
 
 }  // namespace
 
-void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
+namespace {
+
+CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, bool *derive_out) {
     LevelBuf &A = T.L[l], &B = T.L[l + 1];
     CCArgs a;
     a.l = l;
@@ -413,6 +455,15 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
         a.pce = nullptr; a.ptw = nullptr; a.Ep = 0;
     }
     for (int m = 0; m < kMaxLevels; m++) a.twl[m] = m <= T.levels && T.L[m].helpers ? T.L[m].tw : nullptr;
+    *derive_out = derive;
+    return a;
+}
+
+}  // namespace
+
+void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
+    bool derive = false;
+    CCArgs a = make_args(T, l, P, Pn, &derive);
     bool ev = P != nullptr;
     if (topo || ev) T.launches += 1;
     if (topo && helpers && ev) launch<true, true, true>(a, derive, s);
@@ -420,6 +471,49 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     else if (topo && ev) launch<true, false, true>(a, derive, s);
     else if (topo) launch<true, false, false>(a, derive, s);
     else if (ev) launch<false, false, true>(a, derive, s);
+}
+
+std::vector<BatchClass> cc_batch_plan(const std::vector<EvalItem> &items, int block) {
+    std::vector<CCArgs> args[4];
+    std::vector<int> tiles[4];
+    for (const EvalItem &it : items) {
+        bool derive = false;
+        CCArgs a = make_args(*it.T, it.l, it.P, it.Pn, &derive);
+        const int kind = it.l == 0 ? 0 : (it.l == 1 ? 1 : (derive ? 3 : 2));
+        if (tiles[kind].empty()) tiles[kind].push_back(0);
+        args[kind].push_back(a);
+        tiles[kind].push_back(tiles[kind].back() + (a.F + block - 1) / block);
+    }
+    std::vector<BatchClass> out;
+    for (int k = 0; k < 4; k++) {
+        if (args[k].empty()) continue;
+        BatchClass c;
+        c.kind = k;
+        c.n = (int)args[k].size();
+        c.tiles = tiles[k].back();
+        if (cudaMalloc(&c.args, sizeof(CCArgs) * args[k].size()) != cudaSuccess ||
+            cudaMalloc(&c.tile_begin, sizeof(int) * tiles[k].size()) != cudaSuccess) {
+            cudaGetLastError();
+            c.tiles = -1;  // allocation failed: caller reports OOM
+            out.push_back(c);
+            return out;
+        }
+        cudaMemcpy(c.args, args[k].data(), sizeof(CCArgs) * args[k].size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(c.tile_begin, tiles[k].data(), sizeof(int) * tiles[k].size(), cudaMemcpyHostToDevice);
+        out.push_back(c);
+    }
+    return out;
+}
+
+void cc_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s) {
+    const CCArgs *a = (const CCArgs *)c.args;
+    const int g = std::max(1, std::min(grid, c.tiles));
+    switch (c.kind) {
+        case 0: k_cc_batch<0><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
+        case 1: k_cc_batch<1><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
+        case 2: k_cc_batch<2><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
+        default: k_cc_batch<3><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
+    }
 }
 
 }  // namespace alsub

@@ -114,6 +114,25 @@ void upload_weight_tables();
 // Record `msg` as the calling thread's last error and return `s`.
 alsub_status report(alsub_status s, const char *msg);
 
+// ---- ragged batches: the eval steps of many topologies at one level in one launch per class
+struct EvalItem {
+    TopoImpl *T;
+    int l;                 // level whose step is evaluated (l -> l + 1)
+    const float *P;        // level-l positions
+    float *Pn;             // level-(l+1) positions
+};
+struct BatchClass {
+    int kind = 0;          // kernel variant
+    int n = 0;             // items
+    int tiles = 0;         // total tiles (blockDim.x faces each); -1 when the plan failed
+    void *args = nullptr;  // device array of per-item kernel arguments (cudaMalloc)
+    int *tile_begin = nullptr;  // n + 1 tile offsets (cudaMalloc)
+};
+std::vector<BatchClass> cc_batch_plan(const std::vector<EvalItem> &items, int block);
+void cc_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s);
+std::vector<BatchClass> tri_batch_plan(const std::vector<EvalItem> &items, int block);
+void tri_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s);
+
 // The implementation behind a topology handle.
 TopoImpl *topology_impl(alsub_topology_t h);
 // Store the per-corner edge ids and twins of every level below the last one (the last

@@ -41,8 +41,7 @@ struct TriArgs {
 
 
 template <bool TOPO, bool HELP, bool EVAL>
-__global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const int c = 3 * r, V = a.V, E2 = 2 * a.E;
     int vv[3], ee[3], tt[3];
@@ -109,8 +108,7 @@ __global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
 }
 
 template <bool TOPO, bool HELP, bool EVAL>
-__global__ void __launch_bounds__(kBlock) k_sqrt3(TriArgs a) {
-    int r = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const int c = 3 * r, V = a.V;
     int vv[3], tt[3];
@@ -175,7 +173,73 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     return a;
 }
 
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
+    loop_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+template <bool TOPO, bool HELP, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_sqrt3(TriArgs a) {
+    sqrt3_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Ragged batches (see the Catmull-Clark batch kernel): eval of many topologies at one level,
+// tiles of blockDim.x triangles, grid-stride over tiles.
+template <int KIND>   // 0 Loop, 1 sqrt(3)
+__global__ void __launch_bounds__(512, 2) k_tri_batch(const TriArgs *__restrict__ items,
+                                                      const int *__restrict__ tile_begin, int n, int tiles) {
+    for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(tile_begin + mid) <= tile) lo = mid;
+            else hi = mid - 1;
+        }
+        const int r = (tile - __ldg(tile_begin + lo)) * blockDim.x + threadIdx.x;
+        const TriArgs a = items[lo];
+        if (KIND == 0) loop_body<false, false, true>(a, r);
+        else sqrt3_body<false, false, true>(a, r);
+    }
+}
+
 }  // namespace
+
+std::vector<BatchClass> tri_batch_plan(const std::vector<EvalItem> &items, int block) {
+    std::vector<TriArgs> args[2];
+    std::vector<int> tiles[2];
+    for (const EvalItem &it : items) {
+        TriArgs a = make_args(*it.T, it.l, it.P, it.Pn);
+        const int kind = it.T->scheme == ALSUB_LOOP ? 0 : 1;
+        if (tiles[kind].empty()) tiles[kind].push_back(0);
+        args[kind].push_back(a);
+        tiles[kind].push_back(tiles[kind].back() + (a.F + block - 1) / block);
+    }
+    std::vector<BatchClass> out;
+    for (int k = 0; k < 2; k++) {
+        if (args[k].empty()) continue;
+        BatchClass c;
+        c.kind = k;
+        c.n = (int)args[k].size();
+        c.tiles = tiles[k].back();
+        if (cudaMalloc(&c.args, sizeof(TriArgs) * args[k].size()) != cudaSuccess ||
+            cudaMalloc(&c.tile_begin, sizeof(int) * tiles[k].size()) != cudaSuccess) {
+            cudaGetLastError();
+            c.tiles = -1;
+            out.push_back(c);
+            return out;
+        }
+        cudaMemcpy(c.args, args[k].data(), sizeof(TriArgs) * args[k].size(), cudaMemcpyHostToDevice);
+        cudaMemcpy(c.tile_begin, tiles[k].data(), sizeof(int) * tiles[k].size(), cudaMemcpyHostToDevice);
+        out.push_back(c);
+    }
+    return out;
+}
+
+void tri_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s) {
+    const TriArgs *a = (const TriArgs *)c.args;
+    const int g = grid < c.tiles ? (grid < 1 ? 1 : grid) : c.tiles;
+    if (c.kind == 0) k_tri_batch<0><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles);
+    else k_tri_batch<1><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles);
+}
 
 void upload_weight_tables() {
     static std::once_flag once;
