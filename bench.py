@@ -36,7 +36,7 @@ DEFAULT_WORKLOAD = "cc_creased_torus96_L6"
 FALLBACK_HBM_GBS = 6800.0
 
 
-def parse():
+def parse(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
     p.add_argument("--steps", type=int, default=20)
@@ -45,7 +45,8 @@ def parse():
     p.add_argument("--workload", default=DEFAULT_WORKLOAD)
     p.add_argument("--levels", type=int, default=None, help="override the workload's level count")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    return p.parse_args()
+    p.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
+    return p.parse_args(argv)
 
 
 def measured_peaks():
@@ -116,6 +117,131 @@ class Clocks:
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": float(rows[0][2]) if rows[0][2].replace(".", "").isdigit() else None,
                 "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def reduce_max(x: float, dist=None, device="cpu") -> float:
+    """Max of a per-rank number over all ranks (identity without a process group)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Units all ranks processed / the slowest rank's time: each replica does the same work."""
+    return units_per_rank * world / (ms_max / 1e3)
+
+
+def percentile(xs, p):
+    """Nearest-rank percentile."""
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = max(1, int(np.ceil(p * len(xs))))
+    return xs[min(k, len(xs)) - 1]
+
+
+def serving_leg(n_slots: int = 16, budget: float = 40e9):
+    """The serving loop on the request mix of synth.serving_requests (512 requests, Poisson arrivals
+    at 2000/s, 32 resident topologies, 70% frames), replayed in real time, against the plain path
+    (the same arrivals served one at a time by mesh create + topology build + vertex refinement,
+    nothing cached). Results go by DMA into page-locked host buffers in both. Latency = completion
+    - arrival time."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    w = synth.serving_requests()
+    res, reqs = w["resident"], w["requests"]
+
+    def mesh_of(q):
+        return res[q["resident"]] if q["kind"] == "frame" else q["mesh"]
+
+    plans = [alsub.plan(mesh_of(q)["scheme"], mesh_of(q)["V"], mesh_of(q)["F"], len(mesh_of(q)["fv"]),
+                        mesh_of(q)["levels"])[-1] for q in reqs]
+    n_out = [3 * int(c[0]) for c in plans]
+    faces = sum(int(c[1]) for c in plans)
+    arena = torch.empty(sum(n_out), dtype=torch.float32, pin_memory=True).numpy()
+    outs, o = [], 0
+    for n in n_out:
+        outs.append(arena[o:o + n])
+        o += n
+
+    S = alsub.Server(budget_bytes=int(budget), max_slots=n_slots)
+    t = time.perf_counter()
+    rids = [S.register(m, m["scheme"], m["levels"], use_operator=True) for m in res]
+    register_s = time.perf_counter() - t
+
+    def submit(i, q):
+        m = mesh_of(q)
+        if q["kind"] == "frame":
+            return S.submit_frame(rids[q["resident"]], q["P"], out=outs[i])
+        return S.submit_mesh(m, m["scheme"], m["levels"], out=outs[i])
+
+    for i, q in enumerate(reqs[:16]):               # warm-up (not timed)
+        S.poll(submit(i, q), timeout_us=120_000_000)
+    base = S.stats()
+
+    def replay(run_one):
+        t0 = time.monotonic() + 0.05
+        done = []
+        for i, q in enumerate(reqs):
+            due = t0 + q["arrival"]
+            while True:
+                dt = due - time.monotonic()
+                if dt <= 0:
+                    break
+                if dt > 2e-3:
+                    time.sleep(dt - 1e-3)
+            done.append(run_one(i, q, due))
+        return t0, done
+
+    t0, tickets = replay(lambda i, q, due: (submit(i, q), due))
+    lat, last = [], 0.0
+    for tk, due in tickets:
+        r = S.poll(tk, timeout_us=300_000_000)
+        if r is None or r["status"] != 0:
+            raise RuntimeError(f"serving request failed: {r and r['status']}")
+        lat.append(r["done_s"] - due)
+        last = max(last, r["done_s"])
+    st = S.stats()
+    S.close()
+    served = {"p50_ms": 1e3 * percentile(lat, 0.50), "p99_ms": 1e3 * percentile(lat, 0.99),
+              "mean_ms": 1e3 * float(np.mean(lat)), "max_ms": 1e3 * max(lat),
+              "throughput_rps": len(reqs) / (last - t0), "refined_faces_per_s": faces / (last - t0)}
+
+    def plain_one(i, q, due):
+        m = mesh_of(q)
+        M = alsub.Mesh.from_dict(m, m["scheme"])
+        T = alsub.Topology(M, m["levels"])
+        P0 = torch.from_numpy(q["P"] if q["kind"] == "frame" else m["P"]).cuda()
+        PL = T.refine_vertices(P0)
+        torch.from_numpy(outs[i]).view(-1, 3).copy_(PL)
+        torch.cuda.synchronize()
+        T.status()
+        T.close()
+        M.close()
+        return time.monotonic() - due, time.monotonic()
+
+    for i, q in enumerate(reqs[:16]):               # warm-up (not timed)
+        plain_one(i, q, time.monotonic())
+    t0p, done = replay(plain_one)
+    plat = [d[0] for d in done]
+    span = max(d[1] for d in done) - t0p
+    plain = {"p50_ms": 1e3 * percentile(plat, 0.50), "p99_ms": 1e3 * percentile(plat, 0.99),
+             "mean_ms": 1e3 * float(np.mean(plat)), "throughput_rps": len(reqs) / span,
+             "refined_faces_per_s": faces / span}
+    return {
+        "workload": "serve_mix512: 512 requests, Poisson arrivals at 2000/s, 32 resident topologies "
+                    "(CC/Loop/sqrt3 60/25/15, 1k-60k control faces, levels 2-5), 70% frames",
+        "requests": len(reqs), "refined_faces": faces, "d2h_bytes": 4 * sum(n_out),
+        "max_slots": n_slots, "hbm_budget_gb": budget / 1e9, "register_s": register_s,
+        "served": served, "plain": plain,
+        "frames_operator": st["frames_operator"] - base["frames_operator"],
+        "frames_eval": st["frames_eval"] - base["frames_eval"],
+        "meshes": st["meshes"] - base["meshes"], "hbm_peak_gb": st["hbm_peak"] / 1e9,
+        "latency": "completion seen by the server's worker (plain: after the host copy) - arrival",
+    }
 
 
 def traffic_for(kernel_key):
@@ -232,12 +358,9 @@ def main():
     stage_ms, calls, launches = T.timings()
     T.set_timing(0)
     T.status()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = reduce_max(ms, dist, "cuda")
     ms_step = ms / args.steps
-    value = FL * args.steps * world / (ms / 1e3)
+    value = whole_job_rate(FL * args.steps, world, ms)
 
     # dominant kernel: the last level's fused build + eval step
     peak, peak_src = measured_peaks()
@@ -263,11 +386,8 @@ def main():
     e1.record()
     barrier()
     ms_e2e = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
-    e2e = {"value": FL * ke * world / (ms_e2e / 1e3), "unit": "refined faces/s",
+    ms_e2e = reduce_max(ms_e2e, dist, "cuda")
+    e2e = {"value": whole_job_rate(FL * ke, world, ms_e2e), "unit": "refined faces/s",
            "h2d_bytes_per_step": int(P0_h.numel() * 4), "d2h_bytes_per_step": int(PL_h.numel() * 4)}
 
     out = {
@@ -291,12 +411,17 @@ def main():
         "gpu_launches": int(launches),
         "clocks": clk,
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(m, min(sample_levels(args.workload), L))
-    if rank == 0:
-        print(json.dumps(out, default=lambda o: o.item() if hasattr(o, "item") else str(o)))
     T.close()
     M.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(m, min(sample_levels(args.workload), L))
+    if rank == 0 and world == 1 and not args.no_serving:
+        try:
+            out["serving"] = serving_leg()
+        except Exception as e:  # noqa: BLE001 -- the headline line must still print
+            out["serving"] = {"error": f"{type(e).__name__}: {e}"}
+    if rank == 0:
+        print(json.dumps(out, default=lambda o: o.item() if hasattr(o, "item") else str(o)))
     if dist is not None:
         dist.destroy_process_group()
 

@@ -310,6 +310,123 @@ alsub_status alsub_topology_timings(alsub_topology_t topo, double *ms_host, int3
 alsub_status alsub_refine_vertices_static(alsub_topology_t topo, const float *P0_dev, float *PL_dev,
                                           void *stream);
 
+/*
+ * Device bytes that alsub_topology_create(levels) allocates for a mesh of these sizes (host only,
+ * no GPU needed; the same closed-form sizes the create call uses). sigma_max is the largest
+ * crease sharpness (+inf allowed; it bounds how many levels keep crease lists). The mesh itself
+ * holds 4 (F + 1) + 4 nnz + 12 K bytes more. Errors: those of alsub_plan.
+ */
+alsub_status alsub_plan_bytes(alsub_scheme scheme, int32_t num_verts, int32_t num_faces, int32_t nnz,
+                              int32_t num_creases, float sigma_max, int32_t levels, size_t *bytes);
+
+/* Device bytes a handle holds now (grows when alsub_build_operator stores the per-corner arrays
+ * of a level that did not keep them). */
+alsub_status alsub_topology_bytes(alsub_topology_t topo, size_t *bytes);
+alsub_status alsub_operator_bytes(alsub_operator_t op, size_t *bytes);
+
+/*
+ * Serving loop (no counterpart in the paper's text; its "Static topology" mode of Sec. 3.5, build
+ * once and evaluate every frame, is what the resident cache serves). A worker thread owned by the
+ * server admits queued requests first come first served into `max_slots` slots, each with its own
+ * CUDA stream, as soon as a slot is free and the request's device bytes fit the HBM budget, so
+ * requests overlap on the GPU (continuous batching: a request joins as soon as another leaves).
+ * Requests are one of:
+ *   ALSUB_REQ_FRAME  new control positions for a resident topology (alsub_serve_register): one
+ *                    SpMV with the cached composite operator, or the eval kernels on the cached
+ *                    topology, whichever was faster when the resident was registered;
+ *   ALSUB_REQ_MESH   a new control mesh: topology build and vertex refinement of every level in
+ *                    one fused pass per level (alsub_subdivide), handles freed afterwards.
+ * Admission counts, per request, the closed-form bytes of its topology (alsub_plan_bytes), its mesh
+ * and its input/output positions (plus eval scratch for frames without an operator); residents
+ * count their topology and operator for as long as the server lives. A request larger than the
+ * budget left by the residents is refused at submit with ALSUB_ERR_OOM; if one is found over budget
+ * at admission with nothing in flight it finishes with status ALSUB_ERR_OOM.
+ * Latency of a request = completion seen by the worker (the slot's event done and the result in
+ * host memory) - submit time; alsub_serve_stats gives percentiles over all completed requests.
+ * While it lives the server raises the release threshold of the current device's default memory
+ * pool to the budget (restored by alsub_serve_destroy), so stream-ordered allocations of
+ * consecutive requests reuse memory instead of mapping it anew.
+ */
+typedef enum { ALSUB_REQ_FRAME = 0, ALSUB_REQ_MESH = 1 } alsub_request_kind;
+
+typedef struct {
+    int32_t kind;                          /* alsub_request_kind */
+    int32_t resident;                      /* FRAME: id returned by alsub_serve_register */
+    int32_t scheme;                        /* MESH: alsub_scheme */
+    int32_t levels;                        /* MESH: refinement steps (0..15) */
+    int32_t num_verts, num_faces;          /* MESH: as alsub_mesh_create */
+    const int32_t *face_offsets_host;      /* MESH: as alsub_mesh_create (may be NULL) */
+    const int32_t *face_verts_host;        /* MESH */
+    int32_t num_creases;                   /* MESH */
+    const int32_t *crease_verts_host;      /* MESH */
+    const float *crease_sharpness_host;    /* MESH */
+    const float *P0_host;                  /* float[3 V_0]; copied by the submit call */
+    float *PL_host;                        /* optional caller-owned output float[3 V_L], written
+                                              before the request completes; page-locked memory is
+                                              written by DMA, pageable memory through a staging
+                                              copy. NULL: the server keeps the result until
+                                              alsub_serve_release. */
+} alsub_request;
+
+typedef struct {
+    int32_t status;                        /* the request's own outcome (alsub_status) */
+    int32_t kind;
+    int64_t num_verts;                     /* V_L */
+    const float *PL_host;                  /* float[3 V_L]: the caller's buffer or the server's */
+    double submit_s, start_s, done_s;      /* steady-clock seconds */
+} alsub_result;
+
+typedef struct {
+    int64_t completed, failed, queued, in_flight;
+    double p50_ms, p99_ms, mean_ms, max_ms;
+    double throughput_rps;                 /* completed / (last completion - first submit) */
+    uint64_t hbm_budget, hbm_in_use, hbm_peak;   /* admission accounting, bytes */
+    int64_t frames_operator;               /* frames served by the cached composite operator */
+    int64_t frames_eval;                   /* frames served by eval kernels on a cached topology */
+    int64_t meshes;                        /* MESH requests completed */
+} alsub_serve_stats;
+
+/* Start a server on the current device. max_slots 1..64 (concurrent requests), budget > 0.
+ * Errors: INVALID_ARG, OOM, DEVICE. */
+alsub_status alsub_serve_create(size_t hbm_budget_bytes, int32_t max_slots, alsub_server_t *out);
+
+/*
+ * Make a resident topology: build it (synchronously, on a stream of the server's own) and, when
+ * use_operator is set and the composite operator fits the budget, build that too and keep
+ * whichever of the two frame paths ran faster in a timed trial. Mesh arguments as
+ * alsub_mesh_create. *resident receives the id FRAME requests name. Errors: those of the mesh,
+ * topology and operator calls, OOM when the topology does not fit the budget.
+ */
+alsub_status alsub_serve_register(alsub_server_t server, alsub_scheme scheme, int32_t num_verts,
+                                  int32_t num_faces, const int32_t *face_offsets_host,
+                                  const int32_t *face_verts_host, int32_t num_creases,
+                                  const int32_t *crease_verts_host, const float *crease_sharpness_host,
+                                  int32_t levels, int32_t use_operator, int32_t *resident);
+
+/* Queue a request; *ticket identifies it. The host arrays of the request are copied before
+ * return. Errors: INVALID_ARG (bad request, unknown resident), UNSUPPORTED (counts), OOM (larger
+ * than the budget left by the residents). Mesh validity is checked when the request runs and
+ * reported in its result status. */
+alsub_status alsub_serve_submit(alsub_server_t server, const alsub_request *request, uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (0 = do not wait; at most 2^31 - 1) for a request. OK: done,
+ * *result filled (result->status is the request's outcome). NOT_READY (timeout 0) or TIMEOUT:
+ * still queued or in flight. INVALID_ARG: unknown ticket. */
+alsub_status alsub_serve_poll(alsub_server_t server, uint64_t ticket, int32_t timeout_us,
+                              alsub_result *result);
+
+/* Forget a finished request and free the result the server kept for it. */
+alsub_status alsub_serve_release(alsub_server_t server, uint64_t ticket);
+
+/* paused != 0: admit nothing new (requests in flight finish, submitted ones wait); 0: resume. */
+alsub_status alsub_serve_pause(alsub_server_t server, int32_t paused);
+
+alsub_status alsub_serve_stats_get(alsub_server_t server, alsub_serve_stats *stats);
+
+/* Stop the worker after the requests in flight finish (queued ones are dropped), free everything
+ * the server holds, residents included. */
+alsub_status alsub_serve_destroy(alsub_server_t server);
+
 #ifdef __cplusplus
 }
 #endif

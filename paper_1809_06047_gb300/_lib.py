@@ -11,6 +11,31 @@ c_int32, c_int64, c_size_t, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 P = ctypes.POINTER
 H = c_void_p  # opaque handles and raw pointers
 
+
+
+class Request(ctypes.Structure):
+    """alsub_request."""
+    _fields_ = [("kind", c_int32), ("resident", c_int32), ("scheme", c_int32), ("levels", c_int32),
+                ("num_verts", c_int32), ("num_faces", c_int32), ("face_offsets_host", c_void_p),
+                ("face_verts_host", c_void_p), ("num_creases", c_int32), ("crease_verts_host", c_void_p),
+                ("crease_sharpness_host", c_void_p), ("P0_host", c_void_p), ("PL_host", c_void_p)]
+
+
+class Result(ctypes.Structure):
+    """alsub_result."""
+    _fields_ = [("status", c_int32), ("kind", c_int32), ("num_verts", c_int64), ("PL_host", c_void_p),
+                ("submit_s", ctypes.c_double), ("start_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class ServeStats(ctypes.Structure):
+    """alsub_serve_stats."""
+    _fields_ = [("completed", c_int64), ("failed", c_int64), ("queued", c_int64), ("in_flight", c_int64),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("throughput_rps", ctypes.c_double),
+                ("hbm_budget", ctypes.c_uint64), ("hbm_in_use", ctypes.c_uint64), ("hbm_peak", ctypes.c_uint64),
+                ("frames_operator", c_int64), ("frames_eval", c_int64), ("meshes", c_int64)]
+
+
 # name -> argtypes; every function returns alsub_status (int32) unless listed in _RESTYPE
 SIGNATURES = {
     "alsub_last_error": [],
@@ -45,6 +70,18 @@ SIGNATURES = {
     "alsub_batch_tune": [H, c_void_p, P(c_int32), P(c_int32), P(ctypes.c_float)],
     "alsub_batch_launches": [H, P(c_int64)],
     "alsub_batch_destroy": [H],
+    "alsub_plan_bytes": [c_int32, c_int32, c_int32, c_int32, c_int32, ctypes.c_float, c_int32, P(c_size_t)],
+    "alsub_topology_bytes": [H, P(c_size_t)],
+    "alsub_operator_bytes": [H, P(c_size_t)],
+    "alsub_serve_create": [c_size_t, c_int32, P(H)],
+    "alsub_serve_register": [H, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                             c_int32, c_int32, P(c_int32)],
+    "alsub_serve_submit": [H, P(Request), P(ctypes.c_uint64)],
+    "alsub_serve_poll": [H, ctypes.c_uint64, c_int32, P(Result)],
+    "alsub_serve_release": [H, ctypes.c_uint64],
+    "alsub_serve_pause": [H, c_int32],
+    "alsub_serve_stats_get": [H, P(ServeStats)],
+    "alsub_serve_destroy": [H],
 }
 _RESTYPE = {"alsub_last_error": ctypes.c_char_p, "alsub_status_string": ctypes.c_char_p}
 

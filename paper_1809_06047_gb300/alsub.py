@@ -49,6 +49,15 @@ def plan(scheme: str, V: int, F: int, nnz: int, levels: int) -> np.ndarray:
     return out.reshape(levels + 1, 4)
 
 
+def plan_bytes(scheme: str, V: int, F: int, nnz: int, levels: int, creases: int = 0,
+               sigma_max: float = 0.0) -> int:
+    """alsub_plan_bytes: device bytes alsub_topology_create allocates (host only)."""
+    b = ctypes.c_size_t()
+    _check(lib().alsub_plan_bytes(SCHEMES[scheme], V, F, nnz, creases, ctypes.c_float(sigma_max), levels,
+                                  ctypes.byref(b)))
+    return b.value
+
+
 def copy_to_host(ptr: int, nbytes: int, dtype, count: int, stream=None) -> np.ndarray:
     out = np.empty(count, dtype=dtype)
     if nbytes:
@@ -163,6 +172,12 @@ class Topology:
         _check(lib().alsub_refine_vertices_scratch_bytes(self._h, ctypes.byref(b)))
         return b.value
 
+    def bytes(self) -> int:
+        """alsub_topology_bytes: device bytes the handle holds."""
+        b = ctypes.c_size_t()
+        _check(lib().alsub_topology_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
     def _run(self, fn, P0: torch.Tensor, out, scratch, stream):
         assert P0.is_cuda and P0.dtype == torch.float32 and P0.is_contiguous()
         VL = self.counts[-1]["V"]
@@ -231,6 +246,12 @@ class Operator:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+    def bytes(self) -> int:
+        """alsub_operator_bytes: device bytes the operator holds."""
+        b = ctypes.c_size_t()
+        _check(lib().alsub_operator_bytes(self._h, ctypes.byref(b)))
+        return b.value
 
     def info(self, level: int = -1) -> dict:
         rows, cols, nnz = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -311,6 +332,111 @@ class Batch:
         if self._h:
             _check(lib().alsub_batch_destroy(self._h))
             self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001
+            pass
+
+
+# ---------------------------------------------------------------------------- serving loop
+
+REQ_FRAME, REQ_MESH = 0, 1
+OK, ERR_OOM, ERR_TIMEOUT, ERR_NOT_READY = 0, 4, 5, 8
+
+
+def _mesh_arrays(m: dict):
+    fv = np.ascontiguousarray(m["fv"], dtype=np.int32)
+    off = None if m.get("off") is None else np.ascontiguousarray(m["off"], dtype=np.int32)
+    cv = np.ascontiguousarray(m["crease_verts"] if m.get("crease_verts") is not None else np.zeros((0, 2)),
+                              dtype=np.int32).reshape(-1)
+    cs = np.ascontiguousarray(m["crease_sharp"] if m.get("crease_sharp") is not None else np.zeros(0),
+                              dtype=np.float32).reshape(-1)
+    return fv, off, cv, cs
+
+
+class Server:
+    """alsub_serve_*: the serving loop (admission by HBM budget, slots on their own CUDA streams,
+    resident topologies and operators, latency percentiles)."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 8):
+        self._h = ctypes.c_void_p()
+        self._keep = {}
+        _check(lib().alsub_serve_create(int(budget_bytes), int(max_slots), ctypes.byref(self._h)))
+
+    def register(self, m: dict, scheme: str, levels: int, use_operator: bool = True) -> int:
+        """alsub_serve_register: make `m` a resident topology of `levels` steps; returns its id."""
+        fv, off, cv, cs = _mesh_arrays(m)
+        rid = ctypes.c_int32()
+        _check(lib().alsub_serve_register(self._h, SCHEMES[scheme], int(m["V"]), int(m["F"]), _ptr(off),
+                                          _ptr(fv), int(cs.size), _ptr(cv) if cs.size else None,
+                                          _ptr(cs) if cs.size else None, int(levels), int(use_operator),
+                                          ctypes.byref(rid)))
+        return rid.value
+
+    def submit_frame(self, resident: int, P0: np.ndarray, out: np.ndarray | None = None) -> int:
+        P0 = np.ascontiguousarray(P0, dtype=np.float32)
+        r = _lib.Request(kind=REQ_FRAME, resident=int(resident), P0_host=P0.ctypes.data,
+                         PL_host=None if out is None else out.ctypes.data)
+        return self._submit(r, (P0, out))
+
+    def submit_mesh(self, m: dict, scheme: str, levels: int, P0: np.ndarray | None = None,
+                    out: np.ndarray | None = None) -> int:
+        fv, off, cv, cs = _mesh_arrays(m)
+        P0 = np.ascontiguousarray(m["P"] if P0 is None else P0, dtype=np.float32)
+        r = _lib.Request(kind=REQ_MESH, scheme=SCHEMES[scheme], levels=int(levels), num_verts=int(m["V"]),
+                         num_faces=int(m["F"]), face_offsets_host=None if off is None else off.ctypes.data,
+                         face_verts_host=fv.ctypes.data, num_creases=int(cs.size),
+                         crease_verts_host=cv.ctypes.data if cs.size else None,
+                         crease_sharpness_host=cs.ctypes.data if cs.size else None,
+                         P0_host=P0.ctypes.data, PL_host=None if out is None else out.ctypes.data)
+        return self._submit(r, (P0, out))
+
+    def _submit(self, r, keep) -> int:
+        t = ctypes.c_uint64()
+        _check(lib().alsub_serve_submit(self._h, ctypes.byref(r), ctypes.byref(t)))
+        if keep[1] is not None:
+            self._keep[t.value] = keep[1]      # the caller's output buffer stays alive until polled
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """alsub_serve_poll: None while the request is in flight, else a dict with status, the
+        positions (float32[V_L, 3]; a copy of the server's buffer unless the caller gave one) and
+        the timestamps. The finished request is released."""
+        res = _lib.Result()
+        st = lib().alsub_serve_poll(self._h, int(ticket), int(timeout_us), ctypes.byref(res))
+        if st in (ERR_TIMEOUT, ERR_NOT_READY):
+            return None
+        _check(st)
+        P = None
+        if res.status == OK:
+            out = self._keep.get(ticket)
+            if out is not None:
+                P = out.reshape(-1, 3)
+            else:
+                n = 3 * res.num_verts
+                P = np.ctypeslib.as_array(ctypes.cast(res.PL_host, ctypes.POINTER(ctypes.c_float)),
+                                          shape=(n,)).copy().reshape(-1, 3)
+        d = dict(status=res.status, kind=res.kind, P=P, submit_s=res.submit_s, start_s=res.start_s,
+                 done_s=res.done_s, latency_s=res.done_s - res.submit_s)
+        self._keep.pop(ticket, None)
+        _check(lib().alsub_serve_release(self._h, int(ticket)))
+        return d
+
+    def pause(self, paused: bool = True):
+        _check(lib().alsub_serve_pause(self._h, int(bool(paused))))
+
+    def stats(self) -> dict:
+        s = _lib.ServeStats()
+        _check(lib().alsub_serve_stats_get(self._h, ctypes.byref(s)))
+        return {name: getattr(s, name) for name, _ in _lib.ServeStats._fields_}
+
+    def close(self):
+        if self._h:
+            _check(lib().alsub_serve_destroy(self._h))
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
 
     def __del__(self):
         try:

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libalsub.so")
-SOURCES = ["scan.cu", "level0.cu", "cc.cu", "tri.cu", "crease.cu", "api.cu", "operator.cu", "batch.cu", "noalloc.cu"]
+SOURCES = ["scan.cu", "level0.cu", "cc.cu", "tri.cu", "crease.cu", "api.cu", "operator.cu", "batch.cu", "noalloc.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "-I", CSRC, "--expt-relaxed-constexpr"]
@@ -61,7 +61,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     with ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -69,6 +69,8 @@ template <class T>
 alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
     *p = nullptr;
     if (n == 0) n = 1;
+    T_.bytes += n * sizeof(T);
+    if (T_.dry) return ALSUB_OK;
     void *q = nullptr;
     cudaError_t e = cudaMallocAsync(&q, n * sizeof(T), s);
     if (e != cudaSuccess) {
@@ -89,6 +91,7 @@ alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
 void free_topo(TopoImpl &T) {
     for (void *p : T.allocs) cudaFreeAsync(p, T.stream);
     T.allocs.clear();
+    T.bytes = 0;
 }
 
 alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table, cudaStream_t s) {
@@ -506,6 +509,30 @@ alsub_status alsub_topology_destroy(alsub_topology_t h) {
 alsub_status alsub_refine_vertices_scratch_bytes(alsub_topology_t h, size_t *bytes) {
     if (!h || !bytes) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     *bytes = h->t.scratch_bytes;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_plan_bytes(alsub_scheme scheme, int32_t V, int32_t F, int32_t nnz, int32_t K,
+                              float sigma_max, int32_t levels, size_t *bytes) {
+    if (!bytes || K < 0 || !(sigma_max >= 0.f)) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    std::vector<int64_t> c(4 * ((size_t)std::max(levels, 0) + 1));
+    alsub_status st = alsub_plan(scheme, V, F, nnz, levels, c.data());
+    if (st != ALSUB_OK) return st;
+    MeshImpl M;
+    M.scheme = scheme; M.V = V; M.F = F; M.nnz = nnz;
+    M.K = scheme == ALSUB_SQRT3 ? 0 : K;
+    M.sigma_max = M.K ? sigma_max : 0.f;
+    TopoImpl T;
+    T.dry = true;
+    st = topo_alloc(T, M, levels, nullptr);
+    if (st != ALSUB_OK) return st;
+    *bytes = T.bytes;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_bytes(alsub_topology_t h, size_t *bytes) {
+    if (!h || !bytes) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    *bytes = h->t.bytes;
     return ALSUB_OK;
 }
 

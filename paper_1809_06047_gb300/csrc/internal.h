@@ -70,6 +70,8 @@ struct TopoImpl {
     float *scratch = nullptr;    // intermediate positions (two levels)
     size_t scratch_bytes = 0;
     std::vector<void *> allocs;  // everything above, freed on destroy
+    size_t bytes = 0;            // device bytes in allocs
+    bool dry = false;            // size the allocations without making them (alsub_plan_bytes)
     cudaStream_t stream = nullptr;
     bool built = false;
     // live timing (alsub_topology_set_timing) and launch count

@@ -356,7 +356,8 @@ struct alsub_operator_s {
     size_t buf_floats = 0;
     int *cnt = nullptr;            // scratch counts
     void *scan_tmp = nullptr;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;   // with their sizes in bytes
+    size_t bytes = 0;
     int *status = nullptr;
 };
 
@@ -371,7 +372,8 @@ alsub_status oalloc(alsub_operator_s &O, T **p, size_t n) {
         cudaGetLastError();
         return report(ALSUB_ERR_OOM, "operator: device allocation failed");
     }
-    O.allocs.push_back(q);
+    O.allocs.push_back({q, n * sizeof(T)});
+    O.bytes += n * sizeof(T);
     *p = (T *)q;
     return ALSUB_OK;
 }
@@ -475,8 +477,23 @@ void spmv(alsub_operator_s &O, const Csr &M, const float *x, float *y, cudaStrea
 }
 
 void free_op(alsub_operator_s *O) {
-    for (void *p : O->allocs) cudaFreeAsync(p, O->stream);
+    for (auto &a : O->allocs) cudaFreeAsync(a.first, O->stream);
     O->allocs.clear();
+    O->bytes = 0;
+}
+
+// Free the arrays of a matrix that is no longer needed (stream ordered).
+void release(alsub_operator_s &O, Csr &M) {
+    for (void *p : {(void *)M.rowptr, (void *)M.col, (void *)M.w}) {
+        for (size_t i = 0; i < O.allocs.size(); i++) {
+            if (O.allocs[i].first != p) continue;
+            cudaFreeAsync(p, O.stream);
+            O.bytes -= O.allocs[i].second;
+            O.allocs.erase(O.allocs.begin() + i);
+            break;
+        }
+    }
+    M = Csr();
 }
 
 }  // namespace
@@ -525,10 +542,13 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
     }
     if (flags & ALSUB_OP_COMPOSE) {
         if (T.levels == 0) return bail(report(ALSUB_ERR_INVALID_ARG, "no levels to compose"));
+        // with no chain kept, each factor and partial product is freed once it has been used
+        const bool keep = flags & ALSUB_OP_CHAIN;
         Csr acc = R[0];
         for (int l = 1; l < T.levels; l++) {
             Csr next;
             if ((st = build_product(*O, R[l], acc, next))) return bail(st);
+            if (!keep) { release(*O, acc); release(*O, R[l]); }
             acc = next;
         }
         O->C = acc;
@@ -595,6 +615,12 @@ alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL
     }
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ALSUB_OK : report(ALSUB_ERR_DEVICE, cudaGetErrorString(e));
+}
+
+alsub_status alsub_operator_bytes(alsub_operator_t op, size_t *bytes) {
+    if (!op || !bytes) return report(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    *bytes = op->bytes;
+    return ALSUB_OK;
 }
 
 alsub_status alsub_operator_destroy(alsub_operator_t op) {

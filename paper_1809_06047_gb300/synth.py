@@ -93,13 +93,15 @@ def _pack(faces: list[list[int]], P: np.ndarray, cverts, csharp) -> dict:
 
 def _undirected_edges(faces: list[list[int]]) -> np.ndarray:
     """Unique undirected edges (min, max), sorted lexicographically (an input-side listing)."""
-    s = set()
-    for f in faces:
-        c = len(f)
-        for j in range(c):
-            a, b = f[j], f[(j + 1) % c]
-            s.add((a, b) if a < b else (b, a))
-    return np.array(sorted(s), dtype=np.int64).reshape(-1, 2)
+    lens = np.fromiter((len(f) for f in faces), dtype=np.int64, count=len(faces))
+    fv = np.fromiter((v for f in faces for v in f), dtype=np.int64, count=int(lens.sum()))
+    off = np.zeros(len(faces) + 1, dtype=np.int64)
+    off[1:] = np.cumsum(lens)
+    nxt = np.arange(1, fv.size + 1)
+    nxt[off[1:] - 1] = off[:-1]                     # the last corner of a face wraps to its first
+    a, b = fv, fv[nxt]
+    e = np.stack([np.minimum(a, b), np.maximum(a, b)], axis=1)
+    return np.unique(e, axis=0).reshape(-1, 2)      # unique rows, lexicographic order
 
 
 def _tag_creases(faces, rng: SplitMix64, frac: float, mode: str):

@@ -105,3 +105,25 @@ def test_last_error_message():
     out = np.zeros(8, np.int64)
     st = lib.alsub_plan(7, 1, 1, 3, 0, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)))
     assert st == 1 and b"scheme" in lib.alsub_last_error()
+
+
+def test_plan_bytes_host_only():
+    """Closed-form device sizes the serving admission uses: host only, no CUDA call."""
+    m = synth.torus_cc_mixed(20, 20, seed=5)
+    nnz = len(m["fv"])
+    sizes = [alsub.plan_bytes("cc", m["V"], m["F"], nnz, L) for L in range(7)]
+    assert all(b > a for a, b in zip(sizes, sizes[1:]))
+    # the per-level arrays grow by 4x per level, so the total does too, asymptotically
+    assert 3.5 < sizes[6] / sizes[5] < 4.5
+    K = len(m["crease_sharp"])
+    with_creases = alsub.plan_bytes("cc", m["V"], m["F"], nnz, 3, K, float(m["crease_sharp"].max()))
+    assert with_creases > sizes[3]
+    # sqrt(3) has no crease rules: creases cost nothing
+    t = synth.torus_tri(10, 10, seed=6)
+    assert (alsub.plan_bytes("sqrt3", t["V"], t["F"], len(t["fv"]), 3, 50, float("inf"))
+            == alsub.plan_bytes("sqrt3", t["V"], t["F"], len(t["fv"]), 3))
+    for bad in [dict(nnz=nnz + 1), dict(levels=-1)]:
+        with pytest.raises(alsub.AlsubError):
+            alsub.plan_bytes("cc", m["V"], m["F"], bad.get("nnz", nnz), bad.get("levels", 2))
+    with pytest.raises(alsub.AlsubError):
+        alsub.plan_bytes("cc", m["V"], m["F"], nnz, 2, 3, -1.0)
