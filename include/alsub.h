@@ -333,7 +333,7 @@ alsub_status alsub_operator_bytes(alsub_operator_t op, size_t *bytes);
  * Requests are one of:
  *   ALSUB_REQ_FRAME  new control positions for a resident topology (alsub_serve_register): one
  *                    SpMV with the cached composite operator, or the eval kernels on the cached
- *                    topology, whichever was faster when the resident was registered;
+ *                    topology, as chosen when the resident was registered;
  *   ALSUB_REQ_MESH   a new control mesh: topology build and vertex refinement of every level in
  *                    one fused pass per level (alsub_subdivide), handles freed afterwards.
  * Admission counts, per request, the closed-form bytes of its topology (alsub_plan_bytes), its mesh
@@ -391,17 +391,23 @@ typedef struct {
 alsub_status alsub_serve_create(size_t hbm_budget_bytes, int32_t max_slots, alsub_server_t *out);
 
 /*
- * Make a resident topology: build it (synchronously, on a stream of the server's own) and, when
- * use_operator is set and the composite operator fits the budget, build that too and keep
- * whichever of the two frame paths ran faster in a timed trial. Mesh arguments as
- * alsub_mesh_create. *resident receives the id FRAME requests name. Errors: those of the mesh,
- * topology and operator calls, OOM when the topology does not fit the budget.
+ * Make a resident topology: build it (synchronously, on a stream of the server's own) and choose
+ * how its frames are served:
+ *   ALSUB_FRAMES_EVAL      the eval kernels on the cached topology (no operator is built);
+ *   ALSUB_FRAMES_OPERATOR  one SpMV with the cached composite operator R (Sec. 3.5 "Single SpMV
+ *                          evaluation"); falls back to EVAL when R does not fit the budget;
+ *   ALSUB_FRAMES_FASTEST   build R, time one frame by each path and keep the faster.
+ * Mesh arguments as alsub_mesh_create. *resident receives the id FRAME requests name.
+ * Errors: those of the mesh, topology and operator calls, INVALID_ARG for an unknown mode, OOM when
+ * the topology does not fit the budget.
  */
+typedef enum { ALSUB_FRAMES_EVAL = 0, ALSUB_FRAMES_OPERATOR = 1, ALSUB_FRAMES_FASTEST = 2 } alsub_frame_path;
+
 alsub_status alsub_serve_register(alsub_server_t server, alsub_scheme scheme, int32_t num_verts,
                                   int32_t num_faces, const int32_t *face_offsets_host,
                                   const int32_t *face_verts_host, int32_t num_creases,
                                   const int32_t *crease_verts_host, const float *crease_sharpness_host,
-                                  int32_t levels, int32_t use_operator, int32_t *resident);
+                                  int32_t levels, int32_t frame_path, int32_t *resident);
 
 /* Queue a request; *ticket identifies it. The host arrays of the request are copied before
  * return. Errors: INVALID_ARG (bad request, unknown resident), UNSUPPORTED (counts), OOM (larger

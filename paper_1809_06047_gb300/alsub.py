@@ -365,13 +365,16 @@ class Server:
         self._keep = {}
         _check(lib().alsub_serve_create(int(budget_bytes), int(max_slots), ctypes.byref(self._h)))
 
-    def register(self, m: dict, scheme: str, levels: int, use_operator: bool = True) -> int:
-        """alsub_serve_register: make `m` a resident topology of `levels` steps; returns its id."""
+    FRAMES = {"eval": 0, "operator": 1, "fastest": 2}
+
+    def register(self, m: dict, scheme: str, levels: int, frames: str = "operator") -> int:
+        """alsub_serve_register: make `m` a resident topology of `levels` steps whose frames are
+        served by the eval kernels, the cached composite operator, or the faster of the two."""
         fv, off, cv, cs = _mesh_arrays(m)
         rid = ctypes.c_int32()
         _check(lib().alsub_serve_register(self._h, SCHEMES[scheme], int(m["V"]), int(m["F"]), _ptr(off),
                                           _ptr(fv), int(cs.size), _ptr(cv) if cs.size else None,
-                                          _ptr(cs) if cs.size else None, int(levels), int(use_operator),
+                                          _ptr(cs) if cs.size else None, int(levels), self.FRAMES[frames],
                                           ctypes.byref(rid)))
         return rid.value
 

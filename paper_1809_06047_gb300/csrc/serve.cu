@@ -7,8 +7,8 @@
 // requests overlap on the device and a new one joins as soon as another leaves. Two kinds:
 //   FRAME  new control positions for a resident topology (Sec. 3.5 "Static topology": build once,
 //          evaluate per frame): H2D, then one SpMV with the cached composite operator (Sec. 3.5
-//          "Single SpMV evaluation") or the eval kernels on the cached topology, whichever was
-//          faster in the trial run at registration; D2H.
+//          "Single SpMV evaluation") or the eval kernels on the cached topology, as chosen at
+//          registration (optionally by a timed trial of both); D2H.
 //   MESH   a new control mesh (Sec. 3.5 "Dynamic topology"): mesh upload, fused build + eval of
 //          every level (alsub_subdivide), D2H; its handles are freed when the slot retires.
 // Per-request device buffers come from the stream-ordered allocator on the slot's stream, so
@@ -355,8 +355,9 @@ alsub_status alsub_serve_create(size_t budget, int32_t max_slots, alsub_server_t
 
 alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t V, int32_t F,
                                   const int32_t *off, const int32_t *fv, int32_t K, const int32_t *cv,
-                                  const float *cs, int32_t levels, int32_t use_operator, int32_t *resident) {
-    if (!S || !resident) return report(ALSUB_ERR_INVALID_ARG, "bad arguments");
+                                  const float *cs, int32_t levels, int32_t frame_path, int32_t *resident) {
+    if (!S || !resident || frame_path < ALSUB_FRAMES_EVAL || frame_path > ALSUB_FRAMES_FASTEST)
+        return report(ALSUB_ERR_INVALID_ARG, "bad arguments");
     cudaSetDevice(S->device);
     cudaStream_t s = S->reg_stream;
     std::unique_ptr<Resident> R(new (std::nothrow) Resident());
@@ -390,7 +391,7 @@ alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t
     size_t tbytes = 0;
     alsub_topology_bytes(R->topo, &tbytes);
     R->bytes = tbytes + mb;
-    if (use_operator && levels > 0) {
+    if (frame_path != ALSUB_FRAMES_EVAL && levels > 0) {
         alsub_operator_t op = nullptr;
         if (alsub_build_operator(R->topo, ALSUB_OP_COMPOSE, s, &op) == ALSUB_OK) {
             size_t ob = 0;
@@ -401,8 +402,10 @@ alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t
                 std::lock_guard<std::mutex> g(S->mu);
                 fits = S->used + tbytes + mb + ob <= S->budget;
             }
-            float t_op = 1e30f, t_eval = 0.f;
-            if (fits) {
+            float t_op = 0.f, t_eval = 1.f;   // OPERATOR: keep R whenever it fits
+            if (fits && frame_path == ALSUB_FRAMES_FASTEST) {
+                t_op = 1e30f;
+                t_eval = 0.f;
                 // trial: frames by each path on zero positions (the values do not change the time)
                 void *buf = nullptr;
                 const size_t n0 = align256(12 * (size_t)R->V0), nl = align256(12 * (size_t)R->VL);

@@ -54,7 +54,7 @@ def test_mix_equals_alone():
     w = synth.serving_requests(n_requests=40, n_resident=4, fmin=200, fmax=3000, rate_hz=1e5, seed=777)
     S = alsub.Server(budget_bytes=8 << 30, max_slots=6)
     try:
-        rids = [S.register(m, m["scheme"], m["levels"], use_operator=(i % 2 == 0))
+        rids = [S.register(m, m["scheme"], m["levels"], frames=("operator", "eval", "fastest")[i % 3])
                 for i, m in enumerate(w["resident"])]
         tickets = []
         for q in w["requests"]:
@@ -91,12 +91,13 @@ def test_frame_against_oracle_and_pinned_output():
     m = synth.torus_cc_mixed(10, 12, seed=95)
     S = alsub.Server(budget_bytes=1 << 30, max_slots=2)
     try:
-        rid = S.register(m, "cc", 3, use_operator=True)
+        rid = S.register(m, "cc", 3, frames="operator")
         P = (m["P"] * 1.25 + 0.5).astype(np.float32)
         VL = int(alsub.plan("cc", m["V"], m["F"], len(m["fv"]), 3)[3][0])
         out = torch.empty((VL, 3), dtype=torch.float32, pin_memory=True).numpy()
         r = S.poll(S.submit_frame(rid, P, out=out), timeout_us=30_000_000)
         r2 = S.poll(S.submit_frame(rid, P), timeout_us=30_000_000)
+        assert S.stats()["frames_operator"] == 2
     finally:
         S.close()
     assert r["status"] == 0 and r["P"] is not None
@@ -155,7 +156,7 @@ def test_budget_refusals():
     try:
         S.pause(True)
         t = S.submit_mesh(m, "cc", 4)
-        S.register(m, "cc", 4, use_operator=False)     # takes about `need` of the budget
+        S.register(m, "cc", 4, frames="eval")          # takes about `need` of the budget
         S.pause(False)
         r = S.poll(t, timeout_us=30_000_000)
         assert r["status"] == 4 and r["P"] is None
