@@ -103,8 +103,8 @@ alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table,
         AL(C.sig, cap);
         AL(C.verts, 2 * cap);
         if (table) {
-            int k = 4;                                   // at least 16 slots, load factor <= 1/2
-            while ((1LL << k) < 2 * cap) k++;
+            int k = 4;                                   // at least 16 slots, load factor <= 1/4
+            while ((1LL << k) < 4 * cap) k++;
             C.hmask = (1 << k) - 1;
             C.hshift = 32 - k;
             AL(C.tab, (size_t)1 << k);

@@ -263,7 +263,7 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
         // ---- round trip 2: own positions, rows of the two faces across edge (a_j, b_j),
         //      rows of the old vertex's ring
         const int s1 = t.x >> 2;                   // F1 = [a_j, y, z, b_j]
-        int4 g1 = make_int4(0, 0, 0, 0), g2 = g1, q0 = g1, q1 = g1, q2 = g1, q3 = g1;
+        int4 g1 = make_int4(0, 0, 0, 0), g2 = g1, q0 = g1, q1 = g1;
         float3 pa = f3(0.f, 0.f, 0.f), pb = pa, pc = pa;
         if (live) {
             g1 = ld4(fv + 4 * (size_t)s1);
@@ -273,18 +273,22 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
             if (j == 0) pc = ldpv(P, v.z, true);
         }
         if (fk > 0) {
-            // ring corners y on level m; the vertex is corner 0 of face y << sh on level l
+            // The old vertex a_j is corner 0 of each of its four ring faces on level l (the ring
+            // corners y on level m, shifted by sh): this face r (y0), F1 across (a_j, b_j), F3
+            // across (d_j, a_j) = t.w's face, and the diagonal face F4. Rows r and F1 are loaded
+            // already; F3 and F4 are the ones this vertex adds.
             const int sh = 2 * (a.l - b.m - 1);
-            int y0, y1, y2, y3;
+            int y1, y2, y3;
             if (fk == 2) {
-                y0 = 4 * b.c + 2; y1 = y0 + 4; y2 = y0 + 8; y3 = y0 + 12;
+                y1 = 4 * b.c + 6; y2 = y1 + 4; y3 = y1 + 8;
             } else {
-                y0 = 4 * b.c + 1; y1 = 4 * quad_next(tt) + 3; y2 = 4 * tt + 1; y3 = 4 * quad_next(b.c) + 3;
+                y1 = 4 * quad_next(tt) + 3; y2 = 4 * tt + 1; y3 = 4 * quad_next(b.c) + 3;
             }
-            q0 = ld4(fv + 4 * ((size_t)y0 << sh));
-            q1 = ld4(fv + 4 * ((size_t)y1 << sh));
-            q2 = ld4(fv + 4 * ((size_t)y2 << sh));
-            q3 = ld4(fv + 4 * ((size_t)y3 << sh));
+            const int f3 = t.w >> 2;
+            const int z1 = y1 << sh, z2 = y2 << sh, z3 = y3 << sh;
+            const int f4 = (z1 != s1 && z1 != f3) ? z1 : ((z2 != s1 && z2 != f3) ? z2 : z3);
+            q0 = ld4(fv + 4 * (size_t)f3);
+            q1 = ld4(fv + 4 * (size_t)f4);
         }
         pc = shfl4(pc, 0);                              // parent face point c
         const float3 pd = shfl4(pb, (j + 3) & 3);       // b_{j-1}
@@ -299,9 +303,11 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
             const float3 pw = j < 2 ? ldpv(P, g2.w, true) : f3(0.f, 0.f, 0.f);
             float3 vp_old = f3(0.f, 0.f, 0.f);
             if (fk > 0) {
-                // valence 4: (1 - 7/16) p + 3/32 sum next + 1/64 sum opp
-                const float3 sn = ldpv(P, q0.y, true) + ldpv(P, q1.y, true) + ldpv(P, q2.y, true) + ldpv(P, q3.y, true);
-                const float3 so = ldpv(P, q0.z, true) + ldpv(P, q1.z, true) + ldpv(P, q2.z, true) + ldpv(P, q3.z, true);
+                // valence 4: (1 - 7/16) p + 3/32 sum next + 1/64 sum opp. Ring faces r = [a, b_j,
+                // c, d_j], F1 = [a, y, z, b_j], F3 = [a, d_j, o3, u], F4 = [a, u, o4, y].
+                const float3 pu = ldpv(P, q0.w, true), po3 = ldpv(P, q0.z, true), po4 = ldpv(P, q1.z, true);
+                const float3 sn = (pb + pd) + (py + pu);
+                const float3 so = (pc + pz) + (po3 + po4);
                 vp_old = 0.5625f * pa + 0.09375f * sn + 0.015625f * so;
             }
             stpv(a.Pn, a.V + r, fr, a.out4);

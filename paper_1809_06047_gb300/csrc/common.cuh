@@ -164,30 +164,42 @@ __device__ __forceinline__ bool sqrt3_vown(int l, int x, const Level0 &z) {
 }
 
 // Crease hash table (CreaseList::tab): linear probing from a multiplicative hash.
-__device__ __forceinline__ unsigned crease_slot(int e, int shift) {
-    return shift >= 32 ? 0u : ((unsigned)e * 2654435761u) >> shift;
+// The table holds 2^k int2 slots (key = edge id, -1 = empty; value = sharpness bits) at load
+// factor <= 1/4, probed linearly in aligned pairs: bucket b is slots 2b, 2b + 1, read by one
+// 16-byte load, then bucket b + 1 and so on. Inserts fill the same sequence, so an empty slot ends
+// a search.
+__device__ __forceinline__ unsigned crease_bucket(int e, int shift) {
+    return shift >= 31 ? 0u : ((unsigned)e * 2654435761u) >> (shift + 1);
 }
 __device__ __forceinline__ float crease_lookup(const CreaseList &C, int e) {
-    unsigned h = crease_slot(e, C.hshift);
-    for (int probe = 0; probe <= C.hmask; probe++) {
-        const int2 q = __ldg(C.tab + h);
+    const int4 *__restrict__ t = reinterpret_cast<const int4 *>(C.tab);
+    const unsigned bmask = (unsigned)C.hmask >> 1;
+    unsigned b = crease_bucket(e, C.hshift);
+    for (unsigned probe = 0; probe <= bmask; probe++) {
+        const int4 q = __ldg(t + b);
         if (q.x == e) return __int_as_float(q.y);
         if (q.x < 0) return 0.f;
-        h = (h + 1) & C.hmask;
+        if (q.z == e) return __int_as_float(q.w);
+        if (q.z < 0) return 0.f;
+        b = (b + 1) & bmask;
     }
     return 0.f;
 }
 // Returns false when the edge was already in the table.
 __device__ __forceinline__ bool crease_insert(const CreaseList &C, int e, float s) {
-    unsigned h = crease_slot(e, C.hshift);
-    for (int probe = 0; probe <= C.hmask; probe++) {
-        const int old = atomicCAS(&C.tab[h].x, -1, e);
-        if (old == -1) {
-            C.tab[h].y = __float_as_int(s);
-            return true;
+    const unsigned bmask = (unsigned)C.hmask >> 1;
+    unsigned b = crease_bucket(e, C.hshift);
+    for (unsigned probe = 0; probe <= bmask; probe++) {
+        for (int h = 0; h < 2; h++) {
+            int2 *slot = C.tab + 2 * b + h;
+            const int old = atomicCAS(&slot->x, -1, e);
+            if (old == -1) {
+                slot->y = __float_as_int(s);
+                return true;
+            }
+            if (old == e) return false;
         }
-        if (old == e) return false;
-        h = (h + 1) & C.hmask;
+        b = (b + 1) & bmask;
     }
     return false;
 }

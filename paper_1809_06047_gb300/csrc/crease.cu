@@ -48,26 +48,57 @@ struct EndInfo {
     int minc;       // smallest outgoing crease corner at the vertex
 };
 
-template <class Acc>
-__device__ EndInfo analyse(const Acc &A, const CreaseList &C, int start, int *status) {
-    EndInfo r;
+__device__ __forceinline__ void end_init(EndInfo &r) {
     r.k = 0; r.S = 0.f; r.n1 = r.n2 = -1; r.s1 = r.s2 = 0.f; r.minc = 0x7fffffff;
-    int y = start, steps = 0;
-    do {
-        const float sy = crease_lookup(C, A.edge(y));
-        if (sy > 0.f) {
-            const int nb = A.vtx(A.next(y));
-            if (r.k == 0) { r.n1 = nb; r.s1 = sy; }
-            else if (r.k == 1) { r.n2 = nb; r.s2 = sy; }
-            r.k++;
-            r.S += sy;
-            r.minc = min(r.minc, y);
+}
+__device__ __forceinline__ void end_add(EndInfo &r, int y, float sy, int nb) {
+    if (!(sy > 0.f)) return;
+    if (r.k == 0) { r.n1 = nb; r.s1 = sy; }
+    else if (r.k == 1) { r.n2 = nb; r.s2 = sy; }
+    r.k++;
+    r.S += sy;
+    r.minc = min(r.minc, y);
+}
+
+// Both end vertices of a crease in one pass. The rings are walked in lockstep, kW corners per
+// round: first the twin chain of the round (the only dependent loads), then the edge-id, table
+// and neighbour loads of all kW corners, which are independent of one another. Crease valency k,
+// sharpness sum S (added in ring order from the start corner), the first two crease neighbours
+// and the smallest crease corner come out exactly as a one-corner-at-a-time walk gives them.
+template <class Acc>
+__device__ void analyse2(const Acc &A, const CreaseList &C, int sa, int sb, EndInfo &ra, EndInfo &rb,
+                         int *status) {
+    constexpr int kW = 4;
+    end_init(ra);
+    end_init(rb);
+    int ya = sa, yb = sb;
+    bool da = false, db = false;
+    for (int steps = 0; !(da && db) && steps < kMaxValence; steps += kW) {
+        int ca[kW], cb[kW];
+        bool ua[kW], ub[kW];
+#pragma unroll
+        for (int q = 0; q < kW; q++) {
+            ua[q] = !da; ca[q] = ya;
+            ub[q] = !db; cb[q] = yb;
+            if (!da) { ya = A.twin(A.prev(ya)); da = ya == sa; }
+            if (!db) { yb = A.twin(A.prev(yb)); db = yb == sb; }
         }
-        y = A.twin(A.prev(y));
-        steps++;
-    } while (y != start && steps < kMaxValence);
-    if (y != start) set_status(status, ALSUB_ERR_UNSUPPORTED);
-    return r;
+        float fa[kW], fb[kW];
+        int na[kW], nb[kW];
+#pragma unroll
+        for (int q = 0; q < kW; q++) {
+            fa[q] = ua[q] ? crease_lookup(C, A.edge(ca[q])) : 0.f;
+            fb[q] = ub[q] ? crease_lookup(C, A.edge(cb[q])) : 0.f;
+            na[q] = ua[q] ? A.vtx(A.next(ca[q])) : -1;
+            nb[q] = ub[q] ? A.vtx(A.next(cb[q])) : -1;
+        }
+#pragma unroll
+        for (int q = 0; q < kW; q++) {
+            if (ua[q]) end_add(ra, ca[q], fa[q], na[q]);
+            if (ub[q]) end_add(rb, cb[q], fb[q], nb[q]);
+        }
+    }
+    if (!(da && db)) set_status(status, ALSUB_ERR_UNSUPPORTED);
 }
 
 __device__ __forceinline__ float chaikin(float so, float s) {
@@ -88,11 +119,12 @@ template <class Acc, bool FIX, bool INHERIT>
 __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
+    // the entry is read together with the count (slots past the count are allocated, unused)
+    const int e = a.in.edge[i], o = a.in.own[i];
+    const float s = a.in.sig[i];
     const int K = failed(a.status) ? 0 : *a.in.count;
     if (INHERIT && i == 0) *a.out.count = 2 * K;
     if (i >= K) return;
-    const int e = a.in.edge[i], o = a.in.own[i];
-    const float s = a.in.sig[i];
     if (!(s > 0.f)) {
         // an inherited zero: no crease any more; its children stay inert entries
         if (INHERIT) {
@@ -108,8 +140,8 @@ __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap)
     }
     const int t = A.twin(o);
     const int va = A.vtx(o), vb = A.vtx(t);
-    const EndInfo ra = analyse(A, a.in, o, a.status);
-    const EndInfo rb = analyse(A, a.in, t, a.status);
+    EndInfo ra, rb;
+    analyse2(A, a.in, o, t, ra, rb, a.status);
     const int ep = a.epbase + e;
     if (FIX) {
         const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);

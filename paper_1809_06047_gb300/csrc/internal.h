@@ -21,9 +21,10 @@ struct CreaseList {
     int *count = nullptr;  // number of entries (device int)
     long long cap = 0;     // host-side upper bound of the count
     // open-addressing table edge id -> sharpness bits (key -1 = empty), hmask + 1 = 2^k slots
+    // probed in aligned pairs (bucket = (edge * 2654435761) >> (hshift + 1))
     int2 *tab = nullptr;
     int hmask = 0;
-    int hshift = 32;       // slot = (edge * 2654435761) >> hshift
+    int hshift = 32;       // 32 - k
     // compacted copy (live creases only) written by crease_export
     int *xverts = nullptr;
     float *xsig = nullptr;

@@ -50,13 +50,16 @@ __global__ void k_twin(int nnz, const int *__restrict__ fv, const int *__restric
     if (x >= nnz) return;
     int a = fv[x], b = fv[nx[x]];
     int found = x, cnt = 0;
-    for (int q = voff[b]; q < voff[b + 1]; q++) {
+    const int qb0 = voff[b], qb1 = voff[b + 1], qa0 = voff[a], qa1 = voff[a + 1];
+#pragma unroll 4
+    for (int q = qb0; q < qb1; q++) {
         int d = vbk[q];
         if (fv[nx[d]] == a) { found = d; cnt++; }
     }
     if (cnt == 0) set_status(status, ALSUB_ERR_UNSUPPORTED);      // open edge: boundary
     else if (cnt > 1) set_status(status, ALSUB_ERR_NONMANIFOLD);
-    for (int q = voff[a]; q < voff[a + 1]; q++) {                  // duplicate directed edge
+#pragma unroll 4
+    for (int q = qa0; q < qa1; q++) {                              // duplicate directed edge
         int d = vbk[q];
         if (d != x && fv[nx[d]] == b) set_status(status, ALSUB_ERR_NONMANIFOLD);
     }
@@ -108,10 +111,14 @@ __global__ void k_crease0(int K, const int *__restrict__ cv, const float *__rest
     out.edge[i] = 0; out.own[i] = 0; out.sig[i] = 0.f; out.verts[2 * i] = 0; out.verts[2 * i + 1] = 0;
     if (failed(status)) return;
     const int a = cv[2 * i], b = cv[2 * i + 1];
+    // every candidate of a's bucket is tested (no early exit), so the loads of different
+    // candidates do not wait on one another; the first match is taken
     int x = -1;
-    for (int q = voff[a]; q < voff[a + 1] && x < 0; q++) {
+    const int q0 = voff[a], q1 = voff[a + 1];
+#pragma unroll 4
+    for (int q = q0; q < q1; q++) {
         const int d = vbk[q];
-        if (fv[nx[d]] == b) x = d;
+        if (x < 0 && fv[nx[d]] == b) x = d;
     }
     if (x < 0) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
     const int o = own[x] ? x : tw[x], e = ce[x];
