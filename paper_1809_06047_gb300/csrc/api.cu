@@ -202,17 +202,145 @@ alsub_status finish(const char *what) {
     return ALSUB_OK;
 }
 
-// Event k (0 .. levels + 1) of the current timed call, or nothing when timing is off.
+// Event k (0 .. levels + 1) of the current timed call, or nothing when timing is off. While a
+// call is captured, slot 0's events stand in: the replay points the nodes at the call's slot.
 void mark(TopoImpl &T, int k, cudaStream_t s) {
-    if (!T.tcap || T.tcalls >= T.tcap) return;
-    cudaEventRecord(T.tev[(size_t)T.tcalls * (T.levels + 2) + k], s);
+    if (!T.tcap) return;
+    if (T.capturing) {
+        cudaEventRecordWithFlags(T.tev[k], s, cudaEventRecordExternal);
+        return;
+    }
+    const int slot = std::min(T.tcalls, T.tcap);
+    cudaEventRecord(T.tev[(size_t)slot * (T.levels + 2) + k], s);
+}
+
+void drop_graph(CallGraph &G) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    if (G.graph) cudaGraphDestroy(G.graph);
+    G = CallGraph();
+}
+
+void drop_graphs(TopoImpl &T) {
+    for (auto &kind : T.graphs)
+        for (CallGraph &G : kind) drop_graph(G);
 }
 
 void free_events(TopoImpl &T) {
+    drop_graphs(T);                 // timed graphs hold these events
     for (cudaEvent_t e : T.tev) cudaEventDestroy(e);
     T.tev.clear();
     T.tcap = 0;
     T.tcalls = 0;
+}
+
+using Body = void (*)(TopoImpl &, const float *, float *, void *, cudaStream_t);
+
+// Run one refine call through a CUDA graph: captured (on a private stream) when a call repeats
+// the previous call's pointers, replayed on `s` while they stay the same, so a repeated call costs
+// one graph launch instead of one launch per kernel and memset. One-off calls and graphs that
+// cannot be made launch the kernels directly.
+alsub_status run_call(TopoImpl &T, int kind, const float *P0, float *PL, void *scratch, cudaStream_t s,
+                      Body body) {
+    const bool timed = T.tcap > 0;
+    CallGraph *G = nullptr, *lru = &T.graphs[kind][0];
+    for (CallGraph &g : T.graphs[kind]) {
+        if (g.exec && g.P0 == P0 && g.PL == PL && g.scratch == scratch && g.timed == timed) G = &g;
+        if (g.used < lru->used) lru = &g;
+    }
+    if (!G) {
+        const void **prev = T.last[kind];
+        const bool repeat = prev[0] == P0 && prev[1] == PL && prev[2] == scratch;
+        prev[0] = P0; prev[1] = PL; prev[2] = scratch;
+        if (!repeat) {              // a one-off call: plain launches, no capture cost
+            body(T, P0, PL, scratch, s);
+            return finish("refine call");
+        }
+        G = lru;
+        drop_graph(*G);
+        bool ok = T.cap || cudaStreamCreateWithFlags(&T.cap, cudaStreamNonBlocking) == cudaSuccess;
+        const long long before = T.launches;
+        cudaGraph_t g = nullptr;
+        if (ok) ok = cudaStreamBeginCapture(T.cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        if (ok) {
+            T.capturing = true;
+            body(T, P0, PL, scratch, T.cap);
+            T.capturing = false;
+            ok = cudaStreamEndCapture(T.cap, &g) == cudaSuccess && g;
+        }
+        G->launches = T.launches - before;
+        T.launches = before;
+        if (ok && timed) {
+            size_t n = 0;
+            cudaGraphGetNodes(g, nullptr, &n);
+            std::vector<cudaGraphNode_t> nodes(n);
+            cudaGraphGetNodes(g, nodes.data(), &n);
+            G->marks.assign(T.levels + 2, nullptr);
+            for (cudaGraphNode_t nd : nodes) {
+                cudaGraphNodeType t;
+                cudaEvent_t ev;
+                if (cudaGraphNodeGetType(nd, &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+                if (cudaGraphEventRecordNodeGetEvent(nd, &ev) != cudaSuccess) continue;
+                for (int k = 0; k < T.levels + 2; k++)
+                    if (ev == T.tev[k]) G->marks[k] = nd;
+            }
+            for (cudaGraphNode_t nd : G->marks) ok = ok && nd;
+        }
+        if (ok) ok = cudaGraphInstantiate(&G->exec, g, 0) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            if (g) cudaGraphDestroy(g);
+            *G = CallGraph();
+            body(T, P0, PL, scratch, s);
+            return finish("refine call");
+        }
+        G->graph = g;
+        G->P0 = P0; G->PL = PL; G->scratch = scratch;
+        G->timed = timed;
+    }
+    G->used = ++T.graph_clock;
+    if (timed) {
+        const size_t b = (size_t)std::min(T.tcalls, T.tcap) * (T.levels + 2);
+        for (int k = 0; k < T.levels + 2; k++)
+            CK(cudaGraphExecEventRecordNodeSetEvent(G->exec, G->marks[k], T.tev[b + k]));
+    }
+    CK(cudaGraphLaunch(G->exec, s));
+    T.launches += G->launches;
+    return finish("refine call");
+}
+
+void refine_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s) {
+    if (T.levels == 0) {
+        cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s);
+        return;
+    }
+    mark(T, 0, s);
+    mark(T, 1, s);
+    for (int l = 0; l < T.levels; l++) {
+        const float *in;
+        float *out;
+        level_buffers(T, P0, PL, scratch, l, &in, &out);
+        step(T, l, false, false, in, out, s);
+        crease_level(T, l, in, out, false, s);
+        mark(T, l + 2, s);
+    }
+}
+
+void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s) {
+    mark(T, 0, s);
+    level0_build(T, s);
+    mark(T, 1, s);
+    if (T.levels == 0) {
+        cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s);
+        return;
+    }
+    for (int l = 0; l < T.levels; l++) {
+        const float *in;
+        float *out;
+        level_buffers(T, P0, PL, scratch, l, &in, &out);
+        step(T, l, true, T.L[l + 1].helpers, in, out, s);
+        crease_level(T, l, in, out, true, s);
+        mark(T, l + 2, s);
+    }
 }
 
 }  // namespace
@@ -222,15 +350,18 @@ alsub_status alsub::report(alsub_status s, const char *msg) { return fail(s, "%s
 TopoImpl *alsub::topology_impl(alsub_topology_t h) { return &h->t; }
 
 alsub_status alsub::ensure_helpers(TopoImpl &T, cudaStream_t s) {
+    bool changed = false;
     for (int l = 1; l < T.levels; l++) {
         LevelBuf &B = T.L[l];
         if (B.helpers) continue;
         if (T.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);
         AL(B.tw, B.nnz);
         B.helpers = true;
+        changed = true;
         // redo the build of level l from level l - 1, now also emitting its edge ids and twins
         step(T, l - 1, true, true, nullptr, nullptr, s);
     }
+    if (changed) drop_graphs(T);   // captured subdivide calls skipped those arrays
     return finish("ensure_helpers");
 }
 
@@ -460,7 +591,7 @@ alsub_status alsub_topology_set_timing(alsub_topology_t h, int32_t capacity) {
     CK(cudaStreamSynchronize(T.stream));
     free_events(T);
     if (capacity == 0) return ALSUB_OK;
-    size_t n = (size_t)capacity * (T.levels + 2);
+    size_t n = ((size_t)capacity + 1) * (T.levels + 2);
     T.tev.resize(n);
     for (size_t i = 0; i < n; i++) {
         cudaError_t e = cudaEventCreate(&T.tev[i]);
@@ -501,6 +632,8 @@ alsub_status alsub_topology_timings(alsub_topology_t h, double *ms, int32_t *cal
 alsub_status alsub_topology_destroy(alsub_topology_t h) {
     if (!h) return ALSUB_OK;
     free_events(h->t);
+    drop_graphs(h->t);
+    if (h->t.cap) cudaStreamDestroy(h->t.cap);
     free_topo(h->t);
     delete h;
     return finish("alsub_topology_destroy");
@@ -541,50 +674,19 @@ alsub_status alsub_refine_vertices(alsub_topology_t h, const float *P0, float *P
     if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     TopoImpl &T = h->t;
     if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
-    cudaStream_t s = (cudaStream_t)stream;
-    if (T.levels == 0) {
-        CK(cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s));
-        return ALSUB_OK;
-    }
-    mark(T, 0, s);
-    mark(T, 1, s);
-    for (int l = 0; l < T.levels; l++) {
-        const float *in;
-        float *out;
-        level_buffers(T, P0, PL, scratch, l, &in, &out);
-        step(T, l, false, false, in, out, s);
-        crease_level(T, l, in, out, false, s);
-        mark(T, l + 2, s);
-    }
-    if (T.tcap) T.tcalls++;
-    return finish("alsub_refine_vertices");
+    alsub_status st = run_call(T, 0, P0, PL, scratch, (cudaStream_t)stream, refine_body);
+    if (T.tcap && T.levels > 0) T.tcalls++;
+    return st;
 }
 
 alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, void *scratch,
                              void *stream) {
     if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     TopoImpl &T = h->t;
-    cudaStream_t s = (cudaStream_t)stream;
-    mark(T, 0, s);
-    level0_build(T, s);
-    mark(T, 1, s);
-    if (T.levels == 0) {
-        CK(cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s));
-        if (T.tcap) T.tcalls++;
-        T.built = true;
-        return finish("alsub_subdivide");
-    }
-    for (int l = 0; l < T.levels; l++) {
-        const float *in;
-        float *out;
-        level_buffers(T, P0, PL, scratch, l, &in, &out);
-        step(T, l, true, T.L[l + 1].helpers, in, out, s);
-        crease_level(T, l, in, out, true, s);
-        mark(T, l + 2, s);
-    }
+    alsub_status st = run_call(T, 1, P0, PL, scratch, (cudaStream_t)stream, subdivide_body);
     if (T.tcap) T.tcalls++;
-    T.built = true;
-    return finish("alsub_subdivide");
+    if (st == ALSUB_OK) T.built = true;
+    return st;
 }
 
 }  // extern "C"

@@ -53,6 +53,17 @@ struct MeshImpl {
     cudaStream_t stream = nullptr;
 };
 
+// A captured refine call: replayed while its pointers (and timing mode) stay the same.
+struct CallGraph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    const void *P0 = nullptr, *PL = nullptr, *scratch = nullptr;
+    bool timed = false;
+    long long launches = 0;                 // kernels one replay runs
+    std::vector<cudaGraphNode_t> marks;     // timing event-record nodes, by mark index
+    unsigned long long used = 0;            // last use (LRU)
+};
+
 struct TopoImpl {
     MeshImpl *mesh = nullptr;
     alsub_scheme scheme;
@@ -78,8 +89,17 @@ struct TopoImpl {
     // live timing (alsub_topology_set_timing) and launch count
     int tcap = 0;
     int tcalls = 0;
-    std::vector<cudaEvent_t> tev;
+    std::vector<cudaEvent_t> tev;           // (tcap + 1) slots of levels + 2 events; the last
+                                            // slot absorbs calls beyond the capacity
     long long launches = 0;
+    // CUDA graphs of alsub_refine_vertices ([0]) and alsub_subdivide ([1]) calls, a few per kind
+    static constexpr int kGraphs = 4;
+    CallGraph graphs[2][kGraphs];
+    unsigned long long graph_clock = 0;
+    const void *last[2][3] = {};            // pointers of the previous call of each kind: a call is
+                                            // captured the second time its arguments repeat
+    cudaStream_t cap = nullptr;             // private stream the calls are captured on
+    bool capturing = false;
 };
 
 // ---------------------------------------------------------------- launchers
