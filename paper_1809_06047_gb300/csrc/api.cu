@@ -102,6 +102,7 @@ alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table,
         AL(C.own, cap);
         AL(C.sig, cap);
         AL(C.verts, 2 * cap);
+        AL(C.info, 2 * cap);
         if (table) {
             int k = 4;                                   // at least 16 slots, load factor <= 1/4
             while ((1LL << k) < 4 * cap) k++;
@@ -320,16 +321,67 @@ void refine_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStr
         float *out;
         level_buffers(T, P0, PL, scratch, l, &in, &out);
         step(T, l, false, false, in, out, s);
-        crease_level(T, l, in, out, false, s);
+        crease_fix(T, l, in, out, s);     // from the analysis kept at build time
         mark(T, l + 2, s);
     }
 }
 
+// The side stream and fork / join events of alsub_subdivide (made before any capture).
+alsub_status ensure_side(TopoImpl &T) {
+    if (T.side || !crease_alive(T, 0)) return ALSUB_OK;
+    if (cudaStreamCreateWithFlags(&T.side, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        T.side = nullptr;
+        return ALSUB_OK;                    // no side branch: everything runs on the caller's stream
+    }
+    T.fork_ev.assign(T.levels + 1, nullptr);
+    T.join_ev.assign(T.levels + 1, nullptr);
+    for (int l = 0; l <= T.levels; l++)
+        if (cudaEventCreateWithFlags(&T.fork_ev[l], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&T.join_ev[l], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ALSUB_ERR_DEVICE, "event creation failed");
+        }
+    return ALSUB_OK;
+}
+
+void free_side(TopoImpl &T) {
+    for (cudaEvent_t e : T.fork_ev) if (e) cudaEventDestroy(e);
+    for (cudaEvent_t e : T.join_ev) if (e) cudaEventDestroy(e);
+    T.fork_ev.clear();
+    T.join_ev.clear();
+    if (T.side) cudaStreamDestroy(T.side);
+    T.side = nullptr;
+}
+
+// Dynamic topology. The crease analysis of level l needs level l's adjacency but no positions, so
+// it runs on a side branch beside the build + eval of level l (forked when the step that built
+// level l has been enqueued) and joins before the crease fix of level l:
+//   main:  L0 build | step 0 | fix 0 | step 1 | fix 1 | ...
+//   side:           L0 creases, analyse 0 | analyse 1 | ...
 void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s) {
+    cudaStream_t z = T.side ? T.side : s;
+    // analysis of level l on the side branch: it starts once everything enqueued on s so far (the
+    // build of level l) is done, and its join event is recorded before anything else goes on z
+    auto analyse_beside = [&](int l, bool level0) {
+        if (z != s) {
+            cudaEventRecord(T.fork_ev[l], s);
+            cudaStreamWaitEvent(z, T.fork_ev[l], 0);
+        }
+        if (level0) level0_creases(T, z);
+        crease_analyse(T, l, true, z);
+        if (z != s) cudaEventRecord(T.join_ev[l], z);
+    };
+    auto wait_analysis = [&](int l) {
+        if (z != s) cudaStreamWaitEvent(s, T.join_ev[l], 0);
+    };
     mark(T, 0, s);
     level0_build(T, s);
+    if (crease_alive(T, 0)) analyse_beside(0, true);
+    else level0_creases(T, s);
     mark(T, 1, s);
     if (T.levels == 0) {
+        if (crease_alive(T, 0)) wait_analysis(0);
         cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s);
         return;
     }
@@ -338,7 +390,14 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
         float *out;
         level_buffers(T, P0, PL, scratch, l, &in, &out);
         step(T, l, true, T.L[l + 1].helpers, in, out, s);
-        crease_level(T, l, in, out, true, s);
+        if (l + 1 < T.levels) {
+            if (crease_alive(T, l + 1)) analyse_beside(l + 1, false);
+            else crease_analyse(T, l + 1, true, s);    // nothing alive: at most a count reset
+        }
+        if (crease_alive(T, l)) {
+            wait_analysis(l);
+            crease_fix(T, l, in, out, s);
+        }
         mark(T, l + 2, s);
     }
 }
@@ -535,9 +594,10 @@ alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stre
     TopoImpl &T = (*out)->t;
     cudaStream_t s = (cudaStream_t)stream;
     level0_build(T, s);
+    level0_creases(T, s);
     for (int l = 0; l < levels; l++) {
         step(T, l, true, T.L[l + 1].helpers, nullptr, nullptr, s);
-        crease_level(T, l, nullptr, nullptr, true, s);
+        crease_analyse(T, l, true, s);
     }
     T.built = true;
     return finish("alsub_refine_topology");
@@ -634,6 +694,7 @@ alsub_status alsub_topology_destroy(alsub_topology_t h) {
     free_events(h->t);
     drop_graphs(h->t);
     if (h->t.cap) cudaStreamDestroy(h->t.cap);
+    free_side(h->t);
     free_topo(h->t);
     delete h;
     return finish("alsub_topology_destroy");
@@ -683,7 +744,8 @@ alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, voi
                              void *stream) {
     if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     TopoImpl &T = h->t;
-    alsub_status st = run_call(T, 1, P0, PL, scratch, (cudaStream_t)stream, subdivide_body);
+    alsub_status st = ensure_side(T);
+    if (st == ALSUB_OK) st = run_call(T, 1, P0, PL, scratch, (cudaStream_t)stream, subdivide_body);
     if (T.tcap) T.tcalls++;
     if (st == ALSUB_OK) T.built = true;
     return st;

@@ -93,11 +93,11 @@ int enqueue(alsub_batch_s &B, cudaStream_t s) {
         for (const BatchClass &c : B.tri[l]) { tri_batch_launch(c, B.block, grid, s); k++; }
         for (size_t i = 0; i < B.T.size(); i++) {
             TopoImpl &T = *B.T[i];
-            if (l >= T.levels || T.scheme == ALSUB_SQRT3 || T.L[l].cr.cap == 0) continue;
+            if (l >= T.levels || !crease_alive(T, l)) continue;
             const float *in;
             float *out;
             member_buffers(B, (int)i, l, &in, &out);
-            crease_level(T, l, in, out, false, s);
+            crease_fix(T, l, in, out, s);
             k++;
         }
     }

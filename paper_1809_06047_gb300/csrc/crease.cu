@@ -6,7 +6,8 @@
 // the sharpness sum in the same pass (the fused k / s SpMV of Sec. 4.4), so s = S / k
 // (Eq. CC_crease_vsharpness).
 //
-// One kernel per level does both crease jobs from that single analysis:
+// Per level, an analysis kernel walks the rings (it needs only the level's adjacency, so it can run
+// beside the level's eval) and keeps each entry's result; a fix kernel then applies the rules:
 //  fix (after the smooth eval of the level, Fig. module_creases) overwrites
 //    the edge point of a crease: sigma >= 1 -> midpoint, else (1 - sigma) smooth + sigma midpoint;
 //    a crease vertex with k >= 2: w sharp + (1 - w) smooth, w = min(s, 1), sharp =
@@ -115,8 +116,11 @@ __device__ __forceinline__ int child_corner(int x, int tri) {
     return 3 * (4 * r + j);
 }
 
-template <class Acc, bool FIX, bool INHERIT>
-__global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap) {
+// Analysis of one crease entry: both end vertices' crease valency, sharpness sum, first two crease
+// neighbours and whether this entry designates the vertex (kept in info for the fix), and with
+// INHERIT the entry's two halves in the next level's list and table.
+template <class Acc, bool INHERIT>
+__global__ void __launch_bounds__(kBlock) k_crease_analyse(Acc A, CreaseArgs a, int cap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
     // the entry is read together with the count (slots past the count are allocated, unused)
@@ -127,6 +131,8 @@ __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap)
     if (i >= K) return;
     if (!(s > 0.f)) {
         // an inherited zero: no crease any more; its children stay inert entries
+        a.in.info[2 * i] = make_int4(0, 0, -1, -1);
+        a.in.info[2 * i + 1] = make_int4(0, 0, -1, -1);
         if (INHERIT) {
             for (int h = 0; h < 2; h++) {
                 a.out.edge[2 * i + h] = 2 * e + h;
@@ -140,29 +146,16 @@ __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap)
     }
     const int t = A.twin(o);
     const int va = A.vtx(o), vb = A.vtx(t);
+    const int first = a.in.verts[2 * i];    // the list's endpoint order, which the fix reads
     EndInfo ra, rb;
     analyse2(A, a.in, o, t, ra, rb, a.status);
-    const int ep = a.epbase + e;
-    if (FIX) {
-        const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
-        const float3 mid = 0.5f * (pa + pb);
-        if (s >= 1.0f) stpv(a.Pn, ep, mid, a.out4);
-        else stpv(a.Pn, ep, (1.0f - s) * ldpv_rw(a.Pn, ep, a.out4) + s * mid, a.out4);
-        const EndInfo *rr[2] = {&ra, &rb};
-        const int starts[2] = {o, t}, verts[2] = {va, vb};
-        for (int h = 0; h < 2; h++) {
-            const EndInfo &r = *rr[h];
-            if (r.minc != starts[h] || r.k < 2) continue;
-            const int v = verts[h];
-            const float sv = r.S / (float)r.k;
-            const float w = sv < 1.0f ? sv : 1.0f;
-            const float3 p = h == 0 ? pa : pb;
-            const float3 sharp =
-                r.k == 2 ? 0.125f * (ldpv(a.P, r.n1, a.in4) + 6.0f * p + ldpv(a.P, r.n2, a.in4)) : p;
-            stpv(a.Pn, v, w * sharp + (1.0f - w) * ldpv_rw(a.Pn, v, a.out4), a.out4);
-        }
-    }
+    const int4 ia = make_int4(ra.k | (ra.minc == o ? 1 << 16 : 0), __float_as_int(ra.S), ra.n1, ra.n2);
+    const int4 ib = make_int4(rb.k | (rb.minc == t ? 1 << 16 : 0), __float_as_int(rb.S), rb.n1, rb.n2);
+    const bool swap = first != va;          // the odd half of a parent crease lists (ep, v_t)
+    a.in.info[2 * i] = swap ? ib : ia;
+    a.in.info[2 * i + 1] = swap ? ia : ib;
     if (INHERIT) {
+        const int ep = a.epbase + e;
         float oa = s, ob = s;
         if (ra.k == 2) { float x = ra.n1 == vb ? ra.s2 : ra.s1; if (isfinite(x)) oa = x; }
         if (rb.k == 2) { float x = rb.n1 == va ? rb.s2 : rb.s1; if (isfinite(x)) ob = x; }
@@ -180,6 +173,38 @@ __global__ void __launch_bounds__(kBlock) k_crease(Acc A, CreaseArgs a, int cap)
         a.out.verts[4 * i + 3] = vb;
         if (ca > 0.f) crease_insert(a.out, 2 * e, ca);
         if (cb > 0.f) crease_insert(a.out, 2 * e + 1, cb);
+    }
+}
+
+// Fix of one crease entry from its stored analysis: the crease edge point, and each end vertex the
+// entry designates (exactly one crease per crease vertex does).
+__global__ void __launch_bounds__(kBlock) k_crease_fix(CreaseArgs a, int cap) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= cap) return;
+    const int e = a.in.edge[i];
+    const float s = a.in.sig[i];
+    const int va = a.in.verts[2 * i], vb = a.in.verts[2 * i + 1];
+    const int4 ia = a.in.info[2 * i], ib = a.in.info[2 * i + 1];
+    const int K = failed(a.status) ? 0 : *a.in.count;
+    if (i >= K || !(s > 0.f)) return;
+    const int ep = a.epbase + e;
+    const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
+    const float3 mid = 0.5f * (pa + pb);
+    if (s >= 1.0f) stpv(a.Pn, ep, mid, a.out4);
+    else stpv(a.Pn, ep, (1.0f - s) * ldpv_rw(a.Pn, ep, a.out4) + s * mid, a.out4);
+    const int4 info[2] = {ia, ib};
+    const int verts[2] = {va, vb};
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+        const int k = info[h].x & 0xffff;
+        if (!(info[h].x >> 16) || k < 2) continue;
+        const int v = verts[h];
+        const float sv = __int_as_float(info[h].y) / (float)k;
+        const float w = sv < 1.0f ? sv : 1.0f;
+        const float3 p = h == 0 ? pa : pb;
+        const float3 sharp =
+            k == 2 ? 0.125f * (ldpv(a.P, info[h].z, a.in4) + 6.0f * p + ldpv(a.P, info[h].w, a.in4)) : p;
+        stpv(a.Pn, v, w * sharp + (1.0f - w) * ldpv_rw(a.Pn, v, a.out4), a.out4);
     }
 }
 
@@ -233,31 +258,38 @@ void crease_table_clear(const CreaseList &C, cudaStream_t s) {
     if (C.tab) cudaMemsetAsync(C.tab, 0xff, sizeof(int2) * ((size_t)C.hmask + 1), s);
 }
 
-void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, cudaStream_t s) {
-    if (T.scheme == ALSUB_SQRT3 || T.L[l].cr.cap == 0) {
-        if (inherit && l + 1 <= T.levels && T.L[l + 1].cr.count)
-            cudaMemsetAsync(T.L[l + 1].cr.count, 0, sizeof(int), s);
-        return;
-    }
-    const bool fix = P != nullptr;
-    CreaseList &dst = T.L[l + 1].cr;
-    if (inherit && dst.cap == 0) {          // all creases have decayed: level l + 1 has none
-        if (dst.count) cudaMemsetAsync(dst.count, 0, sizeof(int), s);
+bool crease_alive(const TopoImpl &T, int l) {
+    return T.scheme != ALSUB_SQRT3 && l <= T.levels && T.L[l].cr.cap > 0;
+}
+
+void crease_analyse(TopoImpl &T, int l, bool inherit, cudaStream_t s) {
+    CreaseList *dst = l + 1 <= T.levels ? &T.L[l + 1].cr : nullptr;
+    if (inherit && dst && dst->cap == 0) {  // all creases have decayed: level l + 1 has none
+        if (dst->count) cudaMemsetAsync(dst->count, 0, sizeof(int), s);
         inherit = false;
     }
-    if (!fix && !inherit) return;
-    if (inherit) crease_table_clear(dst, s);
+    if (!dst) inherit = false;
+    if (!crease_alive(T, l)) return;
+    if (inherit) crease_table_clear(*dst, s);
     CreaseArgs a = base_args(T, l);
-    a.P = P; a.Pn = Pn;
-    if (inherit) a.out = dst;
+    if (inherit) a.out = *dst;
     const int cap = (int)T.L[l].cr.cap;
     const unsigned g = grid_for(cap);
     with_acc(T, l, [&](auto acc) {
         using A = decltype(acc);
-        if (fix && inherit) k_crease<A, true, true><<<g, kBlock, 0, s>>>(acc, a, cap);
-        else if (fix) k_crease<A, true, false><<<g, kBlock, 0, s>>>(acc, a, cap);
-        else k_crease<A, false, true><<<g, kBlock, 0, s>>>(acc, a, cap);
+        if (inherit) k_crease_analyse<A, true><<<g, kBlock, 0, s>>>(acc, a, cap);
+        else k_crease_analyse<A, false><<<g, kBlock, 0, s>>>(acc, a, cap);
     });
+    T.launches += 1;
+}
+
+void crease_fix(TopoImpl &T, int l, const float *P, float *Pn, cudaStream_t s) {
+    if (!crease_alive(T, l) || l >= T.levels) return;
+    CreaseArgs a = base_args(T, l);
+    a.P = P;
+    a.Pn = Pn;
+    const int cap = (int)T.L[l].cr.cap;
+    k_crease_fix<<<grid_for(cap), kBlock, 0, s>>>(a, cap);
     T.launches += 1;
 }
 

@@ -25,6 +25,9 @@ struct CreaseList {
     int2 *tab = nullptr;
     int hmask = 0;
     int hshift = 32;       // 32 - k
+    // per entry and end, in the order of verts (2i: verts[2i], 2i + 1: verts[2i + 1]), written
+    // by the analysis and read by the fix: (k | designated << 16, sharpness sum bits, n1, n2)
+    int4 *info = nullptr;
     // compacted copy (live creases only) written by crease_export
     int *xverts = nullptr;
     float *xsig = nullptr;
@@ -100,6 +103,10 @@ struct TopoImpl {
                                             // captured the second time its arguments repeat
     cudaStream_t cap = nullptr;             // private stream the calls are captured on
     bool capturing = false;
+    // side branch of alsub_subdivide: the crease analysis of level l runs beside the level's
+    // build + eval step (fork after the step that built level l, join before the crease fix)
+    cudaStream_t side = nullptr;
+    std::vector<cudaEvent_t> fork_ev, join_ev;   // levels + 1 each
 };
 
 // ---------------------------------------------------------------- launchers
@@ -113,8 +120,10 @@ int scan_exclusive(const int *in, int *out, long long n, int *total, const int *
 int scan_exclusive64(const int *in, long long *out, long long n, long long *total, void *tmp,
                      cudaStream_t s);
 
-// Level 0: corner maps, twins, ownership, edge numbering, crease list of level 0.
+// Level 0: corner maps, twins, ownership, edge numbering.
 void level0_build(TopoImpl &T, cudaStream_t s);
+// Level 0's crease list and hash table (needs level0_build's arrays).
+void level0_creases(TopoImpl &T, cudaStream_t s);
 
 // One refinement step from level l to l + 1. topo: emit the child face table; helpers: emit the
 // child's per-corner edge ids and twins; P/Pn: parent/child positions (null = no vertex eval).
@@ -122,10 +131,15 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
 void loop_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s);
 void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s);
 
-// Creases at level l in one kernel: with P/Pn, overwrite the crease vertex and edge points of
-// level l + 1 (Fig. module_creases); with `inherit`, build the crease list and hash table of
-// level l + 1 (Sec. 3.3, count then fill).
-void crease_level(TopoImpl &T, int l, const float *P, float *Pn, bool inherit, cudaStream_t s);
+// True when level l has a crease list to analyse and fix.
+bool crease_alive(const TopoImpl &T, int l);
+// Analysis of level l's creases (crease valency and sharpness sum at both ends from the ring
+// walks, kept per entry for crease_fix); with `inherit`, also the crease list and hash table of
+// level l + 1 (Sec. 3.3). Needs level l's adjacency, not positions.
+void crease_analyse(TopoImpl &T, int l, bool inherit, cudaStream_t s);
+// Overwrite the crease edge points and crease vertices of level l + 1 (Fig. module_creases) from
+// the stored analysis of level l, after the smooth eval of the level.
+void crease_fix(TopoImpl &T, int l, const float *P, float *Pn, cudaStream_t s);
 void crease_table_clear(const CreaseList &C, cudaStream_t s);
 // Compact level l's list (drop the inert zero-sharpness entries) into its x* arrays; returns the
 // number of kernels launched.

@@ -148,6 +148,11 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     T.launches += scan_exclusive(T.own0, T.eid, nnz, T.e0count, nullptr, T.scan_tmp, s);
     k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.e0count, E0, L0.ce, T.eo0,
                                              T.status);
+}
+
+void level0_creases(TopoImpl &T, cudaStream_t s) {
+    MeshImpl &M = *T.mesh;
+    LevelBuf &L0 = T.L[0];
     CreaseList &C = L0.cr;
     if (C.cap > 0) {
         crease_table_clear(C, s);
