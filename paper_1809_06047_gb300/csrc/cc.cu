@@ -22,9 +22,13 @@
 #include "common.cuh"
 #include "internal.h"
 
-// Resident 256-thread blocks per SM the sibling kernel is compiled for (register budget).
+// Block size of the sibling kernel and the resident blocks per SM it is compiled for (register
+// budget: 65536 / (block x blocks)).
+#ifndef ALSUB_SIB_BLOCK
+#define ALSUB_SIB_BLOCK 128
+#endif
 #ifndef ALSUB_SIB_MIN_BLOCKS
-#define ALSUB_SIB_MIN_BLOCKS 4
+#define ALSUB_SIB_MIN_BLOCKS (1024 / ALSUB_SIB_BLOCK)
 #endif
 
 namespace alsub {
@@ -397,7 +401,7 @@ __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
     cc_quad_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
-__global__ void __launch_bounds__(kBlock, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
+__global__ void __launch_bounds__(ALSUB_SIB_BLOCK, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
     cc_sib_body<TOPO, HELP, EVAL, DERIVE>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -433,8 +437,8 @@ template <bool T, bool H, bool E>
 void launch(const CCArgs &a, bool derive, cudaStream_t s) {
     if (a.l == 0) k_cc_l0<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
     else if (a.l == 1) k_cc_quad<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else if (derive) k_cc_sib<T, false, E, true><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else k_cc_sib<T, H, E, false><<<grid_for(a.F), kBlock, 0, s>>>(a);
+    else if (derive) k_cc_sib<T, false, E, true><<<grid_for(a.F, ALSUB_SIB_BLOCK), ALSUB_SIB_BLOCK, 0, s>>>(a);
+    else k_cc_sib<T, H, E, false><<<grid_for(a.F, ALSUB_SIB_BLOCK), ALSUB_SIB_BLOCK, 0, s>>>(a);
 }
 
 }  // namespace
