@@ -160,14 +160,18 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     T.scan_tmp_bytes = scan_tmp_bytes(std::max<long long>(nflags, V));
     AL(*(char **)&T.scan_tmp, T.scan_tmp_bytes);
     // Per-corner edge ids and twins are stored for every level that a later step reads them from.
-    // The last Catmull-Clark step on a level >= 2 derives them from the parent level instead,
-    // unless creases (whose kernels walk rings through the stored arrays) are still alive there.
+    // The last two Catmull-Clark steps derive them instead: level levels - 1 (>= 2) from its
+    // parent, and level levels - 2 (>= 2) from its parent too, the last step then going back two
+    // levels; a level whose creases are still alive keeps them (its crease analysis walks rings
+    // through them).
     T.L[0].helpers = true;
     for (int l = 1; l <= levels; l++) {
         LevelBuf &B = T.L[l];
         AL(B.fv, B.nnz);
         B.helpers = l < levels;
-        if (M.scheme == ALSUB_CATMULL_CLARK && l == levels - 1 && l >= 2 && B.cr.cap == 0)
+        const bool cc = M.scheme == ALSUB_CATMULL_CLARK;
+        if (cc && l == levels - 1 && l >= 2 && B.cr.cap == 0) B.helpers = false;
+        if (cc && l == levels - 2 && l >= 2 && B.cr.cap == 0 && T.L[levels - 1].cr.cap == 0)
             B.helpers = false;
         if (B.helpers) {
             if (M.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);

@@ -43,8 +43,10 @@ struct CCArgs {
     const float *P;               // parent positions
     float *Pn;                    // child positions
     int *fvn, *cen, *twn;         // child face table / edge ids / twins
-    const int *pce, *ptw;         // level l - 1 edge ids / twins, used when level l's are not stored
+    const int *pce, *ptw;         // edge ids / twins of the nearest stored ancestor level (l - 1 or
+                                  // l - 2), used when level l's are not stored
     int Ep;                       // E of level l - 1
+    int Epp;                      // E of level l - 2
     const int *twl[kMaxLevels];   // stored twins of every level (null where not stored)
     bool in4, out4;               // parent / child positions in padded float4 rows
     int *status;
@@ -232,7 +234,7 @@ __device__ __forceinline__ int fast_kind(const Birth &b) {
     return 0;   // not designated here
 }
 
-template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
+template <bool TOPO, bool HELP, bool EVAL, int DERIVE>
 __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
     if (failed(a.status)) return;
     const bool live = r < a.F;                  // F is a multiple of 4: groups are whole
@@ -251,7 +253,19 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
     if (live) {
         v = ld4(fv + 4 * (size_t)r);
         if (DERIVE) {
-            const int4 pe = ld4(a.pce + 4 * (size_t)R), pt = ld4(a.ptw + 4 * (size_t)R);
+            int4 pe, pt;                           // parent R's row of edge ids and twins
+            if (DERIVE == 1) {
+                pe = ld4(a.pce + 4 * (size_t)R);
+                pt = ld4(a.ptw + 4 * (size_t)R);
+            } else {
+                // R is child k of grandparent G: the same child rules give R's rows from G's
+                const int G = R >> 2, k = R & 3, kp = (k + 3) & 3, go = 4 * G + kp;
+                const int4 ge = ld4(a.pce + 4 * (size_t)G), gt = ld4(a.ptw + 4 * (size_t)G);
+                const int Epp2 = 2 * a.Epp;
+                pe = make_int4(2 * comp(ge, k) + (k < 2 ? 0 : 1), Epp2 + R, Epp2 + go,
+                               2 * comp(ge, kp) + (kp < 2 ? 1 : 0));
+                pt = make_int4(4 * quad_next(comp(gt, k)) + 3, 4 * quad_next(R) + 2, 4 * go + 1, 4 * comp(gt, kp));
+            }
             const int jp = (j + 3) & 3, po = 4 * R + jp;
             const int Ep2 = 2 * a.Ep;
             e = make_int4(2 * comp(pe, j) + (j < 2 ? 0 : 1), Ep2 + r, Ep2 + po,
@@ -400,7 +414,7 @@ template <bool TOPO, bool HELP, bool EVAL>
 __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
     cc_quad_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
-template <bool TOPO, bool HELP, bool EVAL, bool DERIVE>
+template <bool TOPO, bool HELP, bool EVAL, int DERIVE>
 __global__ void __launch_bounds__(ALSUB_SIB_BLOCK, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
     cc_sib_body<TOPO, HELP, EVAL, DERIVE>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
@@ -419,33 +433,37 @@ __device__ __forceinline__ int item_of(const int *__restrict__ tile_begin, int n
     return lo;
 }
 
-template <int KIND>   // 0 level 0, 1 level 1, 2 levels >= 2, 3 levels >= 2 with derived E/F
+template <int KIND>   // 0 level 0, 1 level 1, 2 levels >= 2, 3 / 4 levels >= 2 with E/F derived
+                      // from the parent / grandparent level
 __global__ void __launch_bounds__(512, 2) k_cc_batch(const CCArgs *__restrict__ items,
                                                      const int *__restrict__ tile_begin, int n, int tiles) {
     for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
         const int i = item_of(tile_begin, n, tile);
         const int r = (tile - __ldg(tile_begin + i)) * blockDim.x + threadIdx.x;
-        const CCArgs a = items[i];
+        const CCArgs &a = items[i];          // read in place: a copy would not fit in registers
         if (KIND == 0) cc_l0_body<false, false, true>(a, r);
         else if (KIND == 1) cc_quad_body<false, false, true>(a, r);
-        else if (KIND == 2) cc_sib_body<false, false, true, false>(a, r);
-        else cc_sib_body<false, false, true, true>(a, r);
+        else if (KIND == 2) cc_sib_body<false, false, true, 0>(a, r);
+        else if (KIND == 3) cc_sib_body<false, false, true, 1>(a, r);
+        else cc_sib_body<false, false, true, 2>(a, r);
     }
 }
 
 template <bool T, bool H, bool E>
-void launch(const CCArgs &a, bool derive, cudaStream_t s) {
+void launch(const CCArgs &a, int derive, cudaStream_t s) {
+    const unsigned g = grid_for(a.F, ALSUB_SIB_BLOCK);
     if (a.l == 0) k_cc_l0<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
     else if (a.l == 1) k_cc_quad<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else if (derive) k_cc_sib<T, false, E, true><<<grid_for(a.F, ALSUB_SIB_BLOCK), ALSUB_SIB_BLOCK, 0, s>>>(a);
-    else k_cc_sib<T, H, E, false><<<grid_for(a.F, ALSUB_SIB_BLOCK), ALSUB_SIB_BLOCK, 0, s>>>(a);
+    else if (derive == 2) k_cc_sib<T, false, E, 2><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
+    else if (derive == 1) k_cc_sib<T, false, E, 1><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
+    else k_cc_sib<T, H, E, 0><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
 }
 
 }  // namespace
 
 namespace {
 
-CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, bool *derive_out) {
+CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, int *derive_out) {
     LevelBuf &A = T.L[l], &B = T.L[l + 1];
     CCArgs a;
     a.l = l;
@@ -457,12 +475,16 @@ CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, bool *derive_out
     a.status = T.status;
     a.in4 = l > 0;                     // only the caller's input level is packed xyz
     a.out4 = l + 1 < T.levels;         // and the caller's output level
-    // a level >= 2 without stored edge ids / twins derives them from its parent level
-    const bool derive = l >= 2 && !A.helpers;
-    if (derive) {
-        a.pce = T.L[l - 1].ce; a.ptw = T.L[l - 1].tw; a.Ep = (int)T.L[l - 1].E;
-    } else {
-        a.pce = nullptr; a.ptw = nullptr; a.Ep = 0;
+    // a level >= 2 without stored edge ids / twins derives them from its parent level, or (level
+    // >= 3 whose parent stores none either) from its grandparent
+    int derive = 0;
+    a.pce = nullptr; a.ptw = nullptr; a.Ep = 0; a.Epp = 0;
+    if (l >= 2 && !A.helpers) {
+        derive = T.L[l - 1].helpers ? 1 : 2;
+        const LevelBuf &S = T.L[l - derive];
+        a.pce = S.ce; a.ptw = S.tw;
+        a.Ep = (int)T.L[l - 1].E;
+        a.Epp = (int)T.L[l - 2].E;
     }
     for (int m = 0; m < kMaxLevels; m++) a.twl[m] = m <= T.levels && T.L[m].helpers ? T.L[m].tw : nullptr;
     *derive_out = derive;
@@ -472,7 +494,7 @@ CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, bool *derive_out
 }  // namespace
 
 void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
-    bool derive = false;
+    int derive = 0;
     CCArgs a = make_args(T, l, P, Pn, &derive);
     bool ev = P != nullptr;
     if (topo || ev) T.launches += 1;
@@ -484,18 +506,18 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
 }
 
 std::vector<BatchClass> cc_batch_plan(const std::vector<EvalItem> &items, int block) {
-    std::vector<CCArgs> args[4];
-    std::vector<int> tiles[4];
+    std::vector<CCArgs> args[5];
+    std::vector<int> tiles[5];
     for (const EvalItem &it : items) {
-        bool derive = false;
+        int derive = 0;
         CCArgs a = make_args(*it.T, it.l, it.P, it.Pn, &derive);
-        const int kind = it.l == 0 ? 0 : (it.l == 1 ? 1 : (derive ? 3 : 2));
+        const int kind = it.l == 0 ? 0 : (it.l == 1 ? 1 : 2 + derive);
         if (tiles[kind].empty()) tiles[kind].push_back(0);
         args[kind].push_back(a);
         tiles[kind].push_back(tiles[kind].back() + (a.F + block - 1) / block);
     }
     std::vector<BatchClass> out;
-    for (int k = 0; k < 4; k++) {
+    for (int k = 0; k < 5; k++) {
         if (args[k].empty()) continue;
         BatchClass c;
         c.kind = k;
@@ -522,7 +544,8 @@ void cc_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s) {
         case 0: k_cc_batch<0><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
         case 1: k_cc_batch<1><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
         case 2: k_cc_batch<2><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
-        default: k_cc_batch<3><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
+        case 3: k_cc_batch<3><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
+        default: k_cc_batch<4><<<g, block, 0, s>>>(a, c.tile_begin, c.n, c.tiles); break;
     }
 }
 

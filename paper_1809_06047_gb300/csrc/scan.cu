@@ -1,5 +1,5 @@
 // Device-wide exclusive scan (deterministic: fixed-order block reduce, one-CTA scan of the block
-// sums, block-local scan plus offset; small inputs in one CTA). Used for edge numbering (Sec. 3.2:
+// sums, block-local scan plus offset; inputs up to 65536 elements in one CTA). Used for edge numbering (Sec. 3.2:
 // enumerate the non-zeros of the upper triangle of E), vertex buckets, crease-list compaction and
 // the row offsets of the subdivision operators (Sec. 3.5, count then fill).
 #include "common.cuh"
@@ -12,7 +12,6 @@ namespace {
 constexpr int kScanThreads = 512;
 constexpr int kItems = 8;                         // per thread
 constexpr int kTile = kScanThreads * kItems;      // 4096 elements per CTA
-constexpr long long kSmallScan = 1 << 14;         // one CTA below this size
 
 template <class T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
@@ -103,34 +102,45 @@ __global__ void k_scan_tiles(const int *__restrict__ in, T *out, long long n, co
     }
 }
 
+// Up to kBlockScanMax elements in one 1024-thread CTA and one launch. Warp w owns a contiguous
+// segment and reads it 32 consecutive elements at a time (coalesced): pass 1 sums the segment,
+// one scan of the 32 segment sums gives each warp its offset, pass 2 (from L1) scans each group
+// of 32 with shuffles and carries the running total across the groups.
+constexpr int kBlockScanThreads = 1024;
+constexpr long long kBlockScanMax = 1 << 16;
+
 template <class T>
-__global__ void __launch_bounds__(kScanThreads) k_scan_single(const int *__restrict__ in, T *out,
-                                                              long long n, const int *n_dev, T *total) {
-    __shared__ T carry;
+__global__ void __launch_bounds__(kBlockScanThreads) k_scan_block(const int *__restrict__ in, T *out,
+                                                                  long long n, const int *n_dev, T *total) {
+    __shared__ T wsum[kBlockScanThreads / 32 + 1];
     const long long lim = limit_of(n, n_dev);
-    if (threadIdx.x == 0) carry = 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long seg = ((n + 32 * 32 - 1) / (32 * 32)) * 32;      // multiple of 32
+    const long long b = (long long)w * seg, e = b + seg < n ? b + seg : n;
+    T sum = 0;
+#pragma unroll 8
+    for (long long i = b + lane; i < e; i += 32) sum += i < lim ? (T)in[i] : T(0);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) wsum[w] = sum;
     __syncthreads();
-    for (long long base0 = 0; base0 < n; base0 += kTile) {
-        const long long base = base0 + (long long)threadIdx.x * kItems;
-        T v[kItems];
-        T s = 0;
-#pragma unroll
-        for (int i = 0; i < kItems; i++) {
-            v[i] = (base + i < lim) ? (T)in[base + i] : T(0);
-            s += v[i];
-        }
-        T tot;
-        T ex = block_excl_scan<T>(s, &tot) + carry;
-#pragma unroll
-        for (int i = 0; i < kItems; i++) {
-            if (base + i < n) out[base + i] = ex;
-            ex += v[i];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) carry += tot;
-        __syncthreads();
+    if (w == 0) {
+        const T x = wsum[lane];                                       // exactly 32 warps
+        const T xi = warp_incl_scan(x);
+        wsum[lane] = xi - x;
+        if (lane == 31) wsum[32] = xi;
     }
-    if (threadIdx.x == 0 && total) *total = carry;
+    __syncthreads();
+    T carry = wsum[w];
+#pragma unroll 4
+    for (long long i0 = b; i0 < e; i0 += 32) {
+        const long long i = i0 + lane;
+        const T v = (i < e && i < lim) ? (T)in[i] : T(0);
+        const T inc = warp_incl_scan(v);
+        if (i < e) out[i] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+    }
+    if (threadIdx.x == 0 && total) *total = wsum[32];
 }
 
 template <class T>
@@ -139,8 +149,8 @@ int scan_impl(const int *in, T *out, long long n, T *total, const int *n_dev, vo
         if (total) cudaMemsetAsync(total, 0, sizeof(T), s);
         return 0;
     }
-    if (n <= kSmallScan) {
-        k_scan_single<T><<<1, kScanThreads, 0, s>>>(in, out, n, n_dev, total);
+    if (n <= kBlockScanMax) {
+        k_scan_block<T><<<1, kBlockScanThreads, 0, s>>>(in, out, n, n_dev, total);
         return 1;
     }
     int nt = (int)((n + kTile - 1) / kTile);
