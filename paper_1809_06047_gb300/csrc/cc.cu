@@ -22,6 +22,13 @@
 #include "common.cuh"
 #include "internal.h"
 
+// L2 prefetch distance of the sibling kernel, in blocks (0 = none): each block asks the copy
+// engine to bring the face rows (and the derived levels' ancestor rows) of the block this many
+// indices ahead into L2, so that its first round trip starts from L2 instead of DRAM. One wave of
+// a GB300 (152 SMs x 8 resident blocks); half a wave to two waves measured the same.
+#ifndef ALSUB_SIB_PREFETCH
+#define ALSUB_SIB_PREFETCH 1216
+#endif
 // Block size of the sibling kernel and the resident blocks per SM it is compiled for (register
 // budget: 65536 / (block x blocks)).
 #ifndef ALSUB_SIB_BLOCK
@@ -234,8 +241,28 @@ __device__ __forceinline__ int fast_kind(const Birth &b) {
     return 0;   // not designated here
 }
 
+__device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// Face rows [f0, f0 + n) of a level with 4-int rows, clipped to its F faces (16-byte granules).
+__device__ __forceinline__ void prefetch_rows(const int *rows, long long f0, long long n, long long F) {
+    if (f0 >= F) return;
+    if (f0 + n > F) n = F - f0;
+    l2_prefetch(rows + 4 * f0, (unsigned)(16 * n));
+}
+
 template <bool TOPO, bool HELP, bool EVAL, int DERIVE>
 __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
+    if (ALSUB_SIB_PREFETCH > 0 && threadIdx.x == 0) {
+        const long long f0 = ((long long)blockIdx.x + ALSUB_SIB_PREFETCH) * blockDim.x;
+        prefetch_rows(a.fv, f0, blockDim.x, a.F);
+        if (DERIVE) {
+            const int sh = 2 * DERIVE;        // ancestor rows: one per 4^DERIVE faces
+            prefetch_rows(a.pce, f0 >> sh, (blockDim.x >> sh) + 1, (long long)a.F >> sh);
+            prefetch_rows(a.ptw, f0 >> sh, (blockDim.x >> sh) + 1, (long long)a.F >> sh);
+        }
+    }
     if (failed(a.status)) return;
     const bool live = r < a.F;                  // F is a multiple of 4: groups are whole
     const int j = r & 3, R = r >> 2;
