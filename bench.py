@@ -46,6 +46,7 @@ def parse(argv=None):
     p.add_argument("--levels", type=int, default=None, help="override the workload's level count")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
+    p.add_argument("--no-extras", action="store_true", help="skip the operator, adjoint and batch legs")
     return p.parse_args(argv)
 
 
@@ -143,7 +144,7 @@ def percentile(xs, p):
     return xs[min(k, len(xs)) - 1]
 
 
-def serving_leg(n_slots: int = 16, budget: float = 40e9):
+def serving_leg(w, n_slots: int = 16, budget: float = 40e9):
     """The serving loop on the request mix of synth.serving_requests (512 requests, Poisson arrivals
     at 2000/s, 32 resident topologies, 70% frames), replayed in real time, against the plain path
     (the same arrivals served one at a time by mesh create + topology build + vertex refinement,
@@ -152,7 +153,6 @@ def serving_leg(n_slots: int = 16, budget: float = 40e9):
     whichever of operator and eval kernels was faster for each resident."""
     import torch
     from paper_1809_06047_gb300 import alsub
-    w = synth.serving_requests()
     res, reqs = w["resident"], w["requests"]
 
     def mesh_of(q):
@@ -249,6 +249,122 @@ def serving_leg(n_slots: int = 16, budget: float = 40e9):
         "served": out_served, "served_fastest_path": out_fastest, "plain": plain,
         "latency": "completion seen by the server's worker (plain: after the host copy) - arrival",
     }
+
+
+def _events_ms(fn, reps, warmup=3):
+    """Mean device time of fn() over `reps` calls on the current stream (CUDA events)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def spmv_bytes(rows, cols, nnz):
+    """Algorithmic bytes of one CSR SpMV on xyz rows: column ids and weights, int64 row pointers,
+    the output rows and the input rows read once."""
+    return 8 * nnz + 8 * (rows + 1) + 12 * rows + 12 * cols
+
+
+def operator_leg(peak):
+    """The subdivision operator of Sec. 3.5 on the headline workload: composite R = R_5 ... R_0 built
+    in the paper's two stages, then one SpMV per frame, against the fused eval kernels on the same
+    cached topology."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = synth.workload(DEFAULT_WORKLOAD)
+    L = m["levels"]
+    M = alsub.Mesh.from_dict(m)
+    T = alsub.Topology(M, L)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    O = alsub.Operator(T, chain=False, compose=True)
+    torch.cuda.synchronize()
+    build_s = time.perf_counter() - t
+    info = O.info(-1)
+    P0 = torch.from_numpy(m["P"]).cuda()
+    PL = torch.empty((info["rows"], 3), dtype=torch.float32, device="cuda")
+    ms_spmv = _events_ms(lambda: O.apply(P0, out=PL), 10)
+    ms_eval = _events_ms(lambda: T.refine_vertices(P0, out=PL), 10)
+    b = spmv_bytes(info["rows"], info["cols"], info["nnz"])
+    gbs = b / (ms_spmv / 1e3) / 1e9
+    out = {"workload": f"{DEFAULT_WORKLOAD}: composite operator R, {info['rows']} x {info['cols']}, "
+                       f"{info['nnz']} non-zeros ({info['nnz'] / info['rows']:.2f} per row)",
+           "build_s": build_s, "bytes_held": O.bytes(), "apply_ms": ms_spmv,
+           "apply_refined_verts_per_s": info["rows"] / (ms_spmv / 1e3),
+           "eval_kernels_ms": ms_eval,
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "kernel": "k_spmv (one CSR SpMV, xyz rows)", "algorithmic_bytes": b}}
+    O.close()
+    T.close()
+    M.close()
+    return out
+
+
+def adjoint_leg(peak):
+    """Differentiable subdivision on the 144 x 144 creased torus, 4 levels (5.3 M refined quads):
+    forward = fused eval, backward = g_0 = R^T g_L through the transposed per-level operators
+    (autograd), loss = sum of squared distances to a displaced target."""
+    import torch
+    from paper_1809_06047_gb300 import autograd
+    m = synth.workload("cc_creased_torus144_L4")
+    S = autograd.Subdivider(m)
+    P0 = torch.from_numpy(m["P"]).cuda().requires_grad_(True)
+    with torch.no_grad():
+        target = S(P0.detach()) + 0.05
+
+    def step():
+        P0.grad = None
+        loss = ((S(P0) - target) ** 2).sum()
+        loss.backward()
+
+    ms_step = _events_ms(step, 10)
+    gL = torch.ones((S.topo.counts[-1]["V"], 3), dtype=torch.float32, device="cuda")
+    g0 = torch.empty_like(P0.detach())
+    ms_bwd = _events_ms(lambda: S.op.apply_transpose(gL, out=g0), 10)
+    rows_cols = [(S.topo.counts[l]["V"], S.topo.counts[l + 1]["V"]) for l in range(S.topo.levels)]
+    nnz = sum(S.op.info(l)["nnz"] for l in range(S.topo.levels))
+    b = sum(spmv_bytes(r, c, 0) for r, c in rows_cols) + 8 * nnz
+    gbs = b / (ms_bwd / 1e3) / 1e9
+    return {"workload": "cc_creased_torus144_L4: 20,736 control faces -> "
+                        f"{S.topo.counts[-1]['F']} refined quads, loss = sum |P_L - target|^2",
+            "forward_backward_ms": ms_step, "backward_ms": ms_bwd,
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "kernel": "k_spmv on the transposed per-level operators (chain of 4)",
+                         "algorithmic_bytes": b}}
+
+
+def batch_leg(w):
+    """Ragged batch: the 32 resident topologies of the serving mix refined by one batched call (one
+    launch per level per kernel class, CUDA-graph replay, autotuned) against the same 32 refined
+    one call at a time."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    res = w["resident"]
+    keep, topos, P0s = [], [], []
+    for m in res:
+        M = alsub.Mesh.from_dict(m, m["scheme"])
+        keep.append(M)
+        topos.append(alsub.Topology(M, m["levels"]))
+        P0s.append(torch.from_numpy(np.ascontiguousarray(m["P"], dtype=np.float32)).cuda())
+    faces = sum(t.counts[-1]["F"] for t in topos)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        B = alsub.Batch(topos, P0s)
+        best = B.tune(stream=s)
+        ms_batch = _events_ms(lambda: B.refine(stream=s), 10)
+        outs = [torch.empty_like(p) for p in B.PLs]
+        ms_each = _events_ms(lambda: [t.refine_vertices(p, out=o) for t, p, o in zip(topos, P0s, outs)], 10)
+    B.close()
+    return {"workload": f"32 resident topologies of the serving mix ({faces} refined faces in all)",
+            "batch_ms": ms_batch, "one_at_a_time_ms": ms_each, "refined_faces_per_s": faces / (ms_batch / 1e3),
+            "tuned": best}
 
 
 def traffic_for(kernel_key):
@@ -431,9 +547,19 @@ def main():
     M.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(m, min(sample_levels(args.workload), L))
+    mix = None
+    if rank == 0 and world == 1 and not (args.no_extras and args.no_serving):
+        mix = synth.serving_requests()           # the 512-request mix and its 32 residents
+    if rank == 0 and world == 1 and not args.no_extras:
+        for key, leg in (("operator", lambda: operator_leg(peak)), ("adjoint", lambda: adjoint_leg(peak)),
+                         ("batch", lambda: batch_leg(mix))):
+            try:
+                out[key] = leg()
+            except Exception as e:  # noqa: BLE001 -- the headline line must still print
+                out[key] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0 and world == 1 and not args.no_serving:
         try:
-            out["serving"] = serving_leg()
+            out["serving"] = serving_leg(mix)
         except Exception as e:  # noqa: BLE001 -- the headline line must still print
             out["serving"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
