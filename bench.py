@@ -204,18 +204,21 @@ def serving_leg(w, n_slots: int = 16, budget: float = 40e9):
                 S.poll(submit(i, q), timeout_us=120_000_000)
             base = S.stats()
             t0, tickets = replay(lambda i, q, due: (submit(i, q), due))
-            lat, last = [], 0.0
+            lat, wait, serve, last = [], [], [], 0.0
             for tk, due in tickets:
                 r = S.poll(tk, timeout_us=300_000_000)
                 if r is None or r["status"] != 0:
                     raise RuntimeError(f"serving request failed: {r and r['status']}")
                 lat.append(r["done_s"] - due)
+                wait.append(r["start_s"] - due)
+                serve.append(r["done_s"] - r["start_s"])
                 last = max(last, r["done_s"])
             st = S.stats()
         finally:
             S.close()
         d = summary(lat, last - t0)
-        d.update(register_s=register_s, hbm_peak_gb=st["hbm_peak"] / 1e9,
+        d.update(queue_wait_ms_mean=1e3 * float(np.mean(wait)), service_ms_mean=1e3 * float(np.mean(serve)),
+                 register_s=register_s, hbm_peak_gb=st["hbm_peak"] / 1e9,
                  frames_operator=st["frames_operator"] - base["frames_operator"],
                  frames_eval=st["frames_eval"] - base["frames_eval"], meshes=st["meshes"] - base["meshes"])
         return d

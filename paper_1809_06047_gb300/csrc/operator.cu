@@ -331,13 +331,32 @@ __global__ void k_gemm(long long rows, const long long *__restrict__ ap, const i
 
 // ---------------------------------------------------------------- SpMV on packed xyz
 
-__global__ void k_spmv(long long rows, const long long *__restrict__ rowptr, const int *__restrict__ col,
-                       const float *__restrict__ w, const float *__restrict__ x, float *y) {
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= rows) return;
-    float3 acc = f3(0.f, 0.f, 0.f);
-    for (long long q = rowptr[i], e = rowptr[i + 1]; q < e; q++) acc += __ldg(w + q) * ldp(x, __ldg(col + q));
-    stp(y, (int)i, acc);
+// y = A x on xyz rows, S lanes per row: lane k of a row's group takes entries start + k,
+// start + k + S, ... (the group reads the row's column ids and weights contiguously), then the
+// group sums its partials with shuffles in a fixed order (deterministic). A resident grid walks
+// the rows with a grid stride.
+template <int S>
+__global__ void __launch_bounds__(256) k_spmv(long long rows, const long long *__restrict__ rowptr,
+                                              const int *__restrict__ col, const float *__restrict__ w,
+                                              const float *__restrict__ x, float *y) {
+    const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long groups = (long long)gridDim.x * blockDim.x / S;
+    const int k = (int)(t % S);
+    const long long iters = (rows + groups - 1) / groups;   // the same for every lane (shuffles)
+    for (long long n = 0; n < iters; n++) {
+        const long long i = t / S + n * groups;
+        float3 acc = f3(0.f, 0.f, 0.f);
+        if (i < rows)
+            for (long long q = rowptr[i] + k, e = rowptr[i + 1]; q < e; q += S)
+                acc += __ldg(w + q) * ldp(x, __ldg(col + q));
+#pragma unroll
+        for (int o = S / 2; o > 0; o >>= 1) {
+            acc.x += __shfl_down_sync(0xffffffffu, acc.x, o, S);
+            acc.y += __shfl_down_sync(0xffffffffu, acc.y, o, S);
+            acc.z += __shfl_down_sync(0xffffffffu, acc.z, o, S);
+        }
+        if (i < rows && k == 0) stp(y, (int)i, acc);
+    }
 }
 
 }  // namespace
@@ -471,8 +490,26 @@ alsub_status build_product(alsub_operator_s &O, const Csr &A, const Csr &B, Csr 
                                                O.cnt, M.rowptr, M.col, M.w, O.status); });
 }
 
+// Lanes per row from the mean row length, about eight entries per lane (measured on the composite
+// operator, 16 per row: 2 lanes; the adjoint's transposed levels, ~38 per row: 4 lanes); a
+// resident grid of 8 blocks per SM.
+#ifndef ALSUB_SPMV_LANES
+#define ALSUB_SPMV_LANES 0          // 0: chosen from the mean row length
+#endif
 void spmv(alsub_operator_s &O, const Csr &M, const float *x, float *y, cudaStream_t s) {
-    k_spmv<<<grid_for(M.rows), kBlock, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
+    const double mean = M.rows ? (double)M.nnz / (double)M.rows : 0.0;
+    int S = mean > 96 ? 16 : (mean > 48 ? 8 : (mean > 24 ? 4 : (mean > 12 ? 2 : 1)));
+    if (ALSUB_SPMV_LANES) S = ALSUB_SPMV_LANES;
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long long want = (M.rows * S + 255) / 256;
+    const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>(want, 8LL * sms));
+    if (S == 16) k_spmv<16><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
+    else if (S == 8) k_spmv<8><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
+    else if (S == 4) k_spmv<4><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
+    else if (S == 2) k_spmv<2><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
+    else k_spmv<1><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
     O.T->launches += 1;
 }
 
