@@ -101,14 +101,6 @@ struct AccQuad {
     __device__ int edge(int x) const { return __ldg(ce + x); }
     __device__ int vtx(int x) const { return __ldg(fv + x); }
 };
-struct AccTri {
-    const int *fv, *tw, *ce;
-    __device__ int next(int x) const { return tri_next(x); }
-    __device__ int prev(int x) const { return tri_prev(x); }
-    __device__ int twin(int x) const { return __ldg(tw + x); }
-    __device__ int edge(int x) const { return __ldg(ce + x); }
-    __device__ int vtx(int x) const { return __ldg(fv + x); }
-};
 
 __device__ __forceinline__ int4 ld4(const int *p) { return __ldg(reinterpret_cast<const int4 *>(p)); }
 __device__ __forceinline__ void st4(int *p, int4 v) { *reinterpret_cast<int4 *>(p) = v; }
@@ -152,6 +144,48 @@ __device__ __forceinline__ bool loop_vown(int l, int x, const Level0 &z) {
     return __ldg(z.vc + __ldg(z.fv + x)) == x;
 }
 
+// Per-corner edge ids and twins of a Loop or sqrt(3) level: read from the level's arrays, or, for a
+// level that does not store them, derived from its parent level's arrays by the same child rules
+// the build writes them with (one load per derived value; some need none).
+//   Loop, corner i of child j of parent triangle R (corner x = 3(4R + j) + i):
+//     j < 3, i = 0: edge 2 e_R(j) + (R's corner j owns its edge ? 0 : 1),
+//                   twin 3(4s + (k == 2 ? 0 : k + 1)) + 2 with tw_R(j) = 3s + k;
+//     j < 3, i = 1: edge 2E + 3R + j, twin 3(4R + 3) + (j + 2) % 3;
+//     j < 3, i = 2: edge 2 e_R(j - 1) + (owns ? 1 : 0), twin 3 tw_R(j - 1) rounded to its
+//                   child 0 (3(4s + k));
+//     j = 3:        edge 2E + 3R + (i + 1) % 3, twin 3(4R + (i + 1) % 3) + 1;
+//   sqrt(3), corner k of child c (the child of parent corner c, x = 3c + k):
+//     k = 0: 3 next(tw(c)) + 2;  k = 1: 3 tw(c) + 1;  k = 2: 3 tw(prev c).
+struct TriLevel {
+    const int *ce = nullptr, *tw = nullptr;    // this level's arrays (stored)
+    const int *pce = nullptr, *ptw = nullptr;  // the parent level's arrays (derived)
+    int E2p = 0;                               // 2 E of the parent level
+    int lp = 0;                                // parent level
+    bool derive = false, sqrt3 = false;
+    Level0 z;
+
+    // Branch-free: the lanes of a warp take different cases, so each case must not issue a load
+    // of its own (one predicated load, then selects).
+    __device__ int twin(int x) const {
+        if (!derive) return __ldg(tw + x);
+        if (sqrt3) {
+            const int c = x / 3, k = x - 3 * c;
+            const int t = __ldg(ptw + (k == 2 ? tri_prev(c) : c));
+            return k == 0 ? 3 * tri_next(t) + 2 : (k == 1 ? 3 * t + 1 : 3 * t);
+        }
+        const int g = x / 3, i = x - 3 * g, R = g >> 2, j = g & 3;
+        const int jm = j == 0 ? 2 : j - 1;
+        const bool need = j != 3 && i != 1;
+        const int t = need ? __ldg(ptw + 3 * R + (i == 0 ? j : jm)) : 0;
+        const int s = t / 3, k = t - 3 * s;
+        const int fromParent = i == 0 ? 3 * (4 * s + (k == 2 ? 0 : k + 1)) + 2 : 3 * (4 * s + k);
+        const int interior = j == 3 ? 3 * (4 * R + (i == 2 ? 0 : i + 1)) + 1 : 3 * (4 * R + 3) + jm;
+        return need ? fromParent : interior;
+    }
+    // Loop only (sqrt(3) has no edge ids)
+    __device__ int edge(int x) const;
+};
+
 // sqrt(3): corner k of child c (the child of parent corner c) is 3c + k.
 __device__ __forceinline__ bool sqrt3_vown(int l, int x, const Level0 &z) {
     while (l > 0) {
@@ -162,6 +196,28 @@ __device__ __forceinline__ bool sqrt3_vown(int l, int x, const Level0 &z) {
     }
     return __ldg(z.vc + __ldg(z.fv + x)) == x;
 }
+
+__device__ __forceinline__ int TriLevel::edge(int x) const {
+    if (!derive) return __ldg(ce + x);
+    const int g = x / 3, i = x - 3 * g, R = g >> 2, j = g & 3;
+    const bool need = j != 3 && i != 1;
+    const int pc = 3 * R + (i == 0 ? j : (j == 0 ? 2 : j - 1));
+    const int pe = need ? __ldg(pce + pc) : 0;
+    const bool own = need && loop_own(lp, pc, z);
+    const int fromParent = 2 * pe + (i == 0 ? (own ? 0 : 1) : (own ? 1 : 0));
+    const int interior = E2p + 3 * R + (j == 3 ? (i == 2 ? 0 : i + 1) : j);
+    return need ? fromParent : interior;
+}
+
+struct AccTri {
+    const int *fv;
+    TriLevel t;
+    __device__ int next(int x) const { return tri_next(x); }
+    __device__ int prev(int x) const { return tri_prev(x); }
+    __device__ int twin(int x) const { return t.twin(x); }
+    __device__ int edge(int x) const { return t.edge(x); }
+    __device__ int vtx(int x) const { return __ldg(fv + x); }
+};
 
 // Crease hash table (CreaseList::tab): linear probing from a multiplicative hash.
 // The table holds 2^k int2 slots (key = edge id, -1 = empty; value = sharpness bits) at load

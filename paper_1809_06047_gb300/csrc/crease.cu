@@ -233,7 +233,7 @@ void with_acc(TopoImpl &T, int l, F f) {
     } else if (T.scheme == ALSUB_CATMULL_CLARK) {
         f(AccQuad{A.fv, A.tw, A.ce});
     } else {
-        f(AccTri{A.fv, A.tw, A.ce});
+        f(AccTri{A.fv, tri_level(T, l)});
     }
 }
 

@@ -170,6 +170,11 @@ void cc_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s);
 std::vector<BatchClass> tri_batch_plan(const std::vector<EvalItem> &items, int block);
 void tri_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s);
 
+// Edge ids and twins of a Loop / sqrt(3) level, stored or derived from the parent level's
+// (TriLevel is defined with the device helpers).
+struct TriLevel;
+TriLevel tri_level(const TopoImpl &T, int l);
+
 // The implementation behind a topology handle.
 TopoImpl *topology_impl(alsub_topology_t h);
 // Store the per-corner edge ids and twins of every level below the last one (the last

@@ -30,7 +30,8 @@ __constant__ float c_sqrt3_alpha[kMaxValence + 1];
 struct TriArgs {
     int l;
     int V, F, E;
-    const int *fv, *ce, *tw;
+    const int *fv;
+    TriLevel t;                   // edge ids / twins of level l (stored or derived)
     Level0 z;
     const float *P;
     float *Pn;
@@ -49,19 +50,19 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         vv[j] = __ldg(a.fv + c + j);
-        ee[j] = __ldg(a.ce + c + j);
-        tt[j] = (HELP || EVAL) ? __ldg(a.tw + c + j) : 0;
+        ee[j] = a.t.edge(c + j);
+        tt[j] = (HELP || EVAL) ? a.t.twin(c + j) : 0;
         ow[j] = loop_own(a.l, c + j, a.z);
     }
     if (TOPO) {
-        int *o = a.fvn + 12 * (size_t)r;
-        o[0] = vv[0]; o[1] = V + ee[0]; o[2] = V + ee[2];
-        o[3] = vv[1]; o[4] = V + ee[1]; o[5] = V + ee[0];
-        o[6] = vv[2]; o[7] = V + ee[2]; o[8] = V + ee[1];
-        o[9] = V + ee[0]; o[10] = V + ee[1]; o[11] = V + ee[2];
+        // the 12 ints of the four children, 48 bytes at 48 r: three 16-byte stores
+        int4 *o = reinterpret_cast<int4 *>(a.fvn + 12 * (size_t)r);
+        o[0] = make_int4(vv[0], V + ee[0], V + ee[2], vv[1]);
+        o[1] = make_int4(V + ee[1], V + ee[0], vv[2], V + ee[2]);
+        o[2] = make_int4(V + ee[1], V + ee[0], V + ee[1], V + ee[2]);
     }
     if (HELP) {
-        int *oe = a.cen + 12 * (size_t)r, *ot = a.twn + 12 * (size_t)r;
+        int oe[12], ot[12];
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             int jp = j == 0 ? 2 : j - 1;
@@ -75,6 +76,13 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
             ot[3 * j + 2] = 3 * (4 * s2 + i2) + 0;
             oe[9 + j] = E2 + c + (j + 1) % 3;
             ot[9 + j] = 3 * (4 * r + (j + 1) % 3) + 1;
+        }
+        int4 *pe = reinterpret_cast<int4 *>(a.cen + 12 * (size_t)r);
+        int4 *pt = reinterpret_cast<int4 *>(a.twn + 12 * (size_t)r);
+#pragma unroll
+        for (int q = 0; q < 3; q++) {
+            pe[q] = make_int4(oe[4 * q], oe[4 * q + 1], oe[4 * q + 2], oe[4 * q + 3]);
+            pt[q] = make_int4(ot[4 * q], ot[4 * q + 1], ot[4 * q + 2], ot[4 * q + 3]);
         }
     }
     if (EVAL) {
@@ -97,12 +105,14 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
             float3 sp = f3(0.f, 0.f, 0.f);
             do {
                 sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
-                y = __ldg(a.tw + tri_prev(y));
+                y = a.t.twin(tri_prev(y));
                 n++;
             } while (y != x && n < kMaxValence);
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
             float beta = c_loop_beta[n];
-            stpv(a.Pn, vv[j], (1.0f - (float)n * beta) * p[j] + beta * sp, a.out4);
+            const float3 pj = j == 0 ? p[0] : (j == 1 ? p[1] : p[2]);   // constant indices: registers
+            const int vj = j == 0 ? vv[0] : (j == 1 ? vv[1] : vv[2]);
+            stpv(a.Pn, vj, (1.0f - (float)n * beta) * pj + beta * sp, a.out4);
         }
     }
 }
@@ -115,7 +125,7 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         vv[j] = __ldg(a.fv + c + j);
-        tt[j] = __ldg(a.tw + c + j);
+        tt[j] = a.t.twin(c + j);
     }
     if (TOPO) {
 #pragma unroll
@@ -148,12 +158,14 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
             float3 sp = f3(0.f, 0.f, 0.f);
             do {
                 sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
-                y = __ldg(a.tw + tri_prev(y));
+                y = a.t.twin(tri_prev(y));
                 n++;
             } while (y != x && n < kMaxValence);
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
             float al = c_sqrt3_alpha[n];
-            stpv(a.Pn, vv[j], (1.0f - al) * p[j] + (al / (float)n) * sp, a.out4);
+            const float3 pj = j == 0 ? p[0] : (j == 1 ? p[1] : p[2]);   // constant indices: registers
+            const int vj = j == 0 ? vv[0] : (j == 1 ? vv[1] : vv[2]);
+            stpv(a.Pn, vj, (1.0f - al) * pj + (al / (float)n) * sp, a.out4);
         }
     }
 }
@@ -163,7 +175,8 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     TriArgs a;
     a.l = l;
     a.V = (int)A.V; a.F = (int)A.F; a.E = (int)A.E;
-    a.fv = A.fv; a.ce = A.ce; a.tw = A.tw;
+    a.fv = A.fv;
+    a.t = tri_level(T, l);
     a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
@@ -195,13 +208,32 @@ __global__ void __launch_bounds__(512, 2) k_tri_batch(const TriArgs *__restrict_
             else hi = mid - 1;
         }
         const int r = (tile - __ldg(tile_begin + lo)) * blockDim.x + threadIdx.x;
-        const TriArgs a = items[lo];
+        const TriArgs &a = items[lo];          // read in place
         if (KIND == 0) loop_body<false, false, true>(a, r);
         else sqrt3_body<false, false, true>(a, r);
     }
 }
 
 }  // namespace
+
+TriLevel tri_level(const TopoImpl &T, int l) {
+    const LevelBuf &A = T.L[l];
+    TriLevel t;
+    t.sqrt3 = T.scheme == ALSUB_SQRT3;
+    t.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+    if (A.helpers || l == 0) {
+        t.ce = A.ce;
+        t.tw = A.tw;
+    } else {
+        const LevelBuf &Pl = T.L[l - 1];
+        t.derive = true;
+        t.pce = Pl.ce;
+        t.ptw = Pl.tw;
+        t.E2p = (int)(2 * Pl.E);
+        t.lp = l - 1;
+    }
+    return t;
+}
 
 std::vector<BatchClass> tri_batch_plan(const std::vector<EvalItem> &items, int block) {
     std::vector<TriArgs> args[2];
