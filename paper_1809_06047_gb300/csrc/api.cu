@@ -138,8 +138,15 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     L0.fv = M.d_fv;
     AL(L0.ce, nnz);
     AL(L0.tw, nnz);
-    AL(T.cf0, nnz); AL(T.nx0, nnz); AL(T.pv0, nnz); AL(T.own0, nnz); AL(T.vbk, nnz); AL(T.eid, nnz);
-    AL(T.vc0, V); AL(T.deg, V); AL(T.vfill, V); AL(T.voff, V + 1);
+    AL(T.cf0, nnz); AL(T.nx0, nnz); AL(T.pv0, nnz); AL(T.own0, nnz); AL(T.rn0, nnz); AL(T.eid, nnz);
+    AL(T.vc0, V); AL(T.deg, V);
+    {
+        int k = 4;                                   // directed-edge table: load factor <= 1/2
+        while ((1LL << k) < 2LL * nnz) k++;
+        T.dir.mask = (unsigned)((1LL << k) - 1);
+        AL(T.dir.key, (size_t)1 << k);
+        AL(T.dir.val, (size_t)1 << k);
+    }
     AL(T.eo0, E0);
     AL(T.e0count, 1); AL(T.status, 1);
     // crease capacities: the sharpness of level l is at most sigma_max - l (each inherited
@@ -337,7 +344,7 @@ void refine_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStr
 
 // The side stream and fork / join events of alsub_subdivide (made before any capture).
 alsub_status ensure_side(TopoImpl &T) {
-    if (T.side || !crease_alive(T, 0)) return ALSUB_OK;
+    if (T.side) return ALSUB_OK;
     if (cudaStreamCreateWithFlags(&T.side, cudaStreamNonBlocking) != cudaSuccess) {
         cudaGetLastError();
         T.side = nullptr;
@@ -386,11 +393,26 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
     };
     mark(T, 0, s);
     level0_build(T, s);
-    if (crease_alive(T, 0)) analyse_beside(0, true);
-    else level0_creases(T, s);
+    // the side branch: the level-0 crease list and analysis, then the level-0 vertex checks (they
+    // only set the status word, so nothing waits for them before the end of the call)
+    if (crease_alive(T, 0)) {
+        analyse_beside(0, true);
+    } else {
+        level0_creases(T, s);
+        if (z != s) {
+            cudaEventRecord(T.fork_ev[0], s);
+            cudaStreamWaitEvent(z, T.fork_ev[0], 0);
+        }
+    }
+    level0_validate(T, z);
     mark(T, 1, s);
+    auto join_all = [&] {                   // everything on the side branch, before the call ends
+        if (z == s) return;
+        cudaEventRecord(T.join_ev[T.levels], z);
+        cudaStreamWaitEvent(s, T.join_ev[T.levels], 0);
+    };
     if (T.levels == 0) {
-        if (crease_alive(T, 0)) wait_analysis(0);
+        join_all();
         cudaMemcpyAsync(PL, P0, sizeof(float) * 3 * (size_t)T.L[0].V, cudaMemcpyDeviceToDevice, s);
         return;
     }
@@ -407,6 +429,7 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
             wait_analysis(l);
             crease_fix(T, l, in, out, s);
         }
+        if (l == T.levels - 1) join_all();
         mark(T, l + 2, s);
     }
 }
@@ -603,6 +626,7 @@ alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stre
     TopoImpl &T = (*out)->t;
     cudaStream_t s = (cudaStream_t)stream;
     level0_build(T, s);
+    level0_validate(T, s);
     level0_creases(T, s);
     for (int l = 0; l < levels; l++) {
         step(T, l, true, T.L[l + 1].helpers, nullptr, nullptr, s);

@@ -106,7 +106,7 @@ __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
             do {
                 sf += face_point_l0(z, P, __ldg(z.cf + y));
                 sp += ldp(P, __ldg(z.fv + __ldg(z.nx + y)));
-                y = __ldg(z.tw + __ldg(z.pv + y));
+                y = __ldg(z.rn + y);
                 n++;
             } while (y != x && n < kMaxValence);
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
@@ -388,7 +388,7 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
                         int y = b.c;
                         do {
                             visit(y);
-                            y = __ldg(z.tw + __ldg(z.pv + y));
+                            y = __ldg(z.rn + y);
                         } while (y != b.c && n < kMaxValence);
                         ok = y == b.c;
                     } else if (b.k == 1) {
@@ -496,7 +496,7 @@ CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, int *derive_out)
     a.l = l;
     a.V = (int)A.V; a.F = (int)A.F; a.E = (int)A.E;
     a.fv = A.fv; a.ce = A.ce; a.tw = A.tw;
-    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;

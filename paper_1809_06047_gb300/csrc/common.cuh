@@ -81,22 +81,27 @@ struct Level0 {
     const int *ce;    // edge id of each corner
     const int *own;   // 1 if the corner owns its edge (start vertex < end vertex)
     const int *vc;    // designated (smallest) outgoing corner of each vertex
+    const int *rn;    // ring step twin(prev(x)): the next outgoing corner around the start vertex
 };
 
 // Corner accessors used by the ring walks of the crease kernels. Each gives next / prev corner
-// in the face, twin, edge id and start vertex of a corner.
+// in the face, the ring step twin(prev), twin, edge id and start vertex of a corner.
 struct AccL0 {
+    static constexpr int kRound = 8;
     Level0 z;
     __device__ int next(int x) const { return __ldg(z.nx + x); }
     __device__ int prev(int x) const { return __ldg(z.pv + x); }
+    __device__ int ring(int x) const { return __ldg(z.rn + x); }
     __device__ int twin(int x) const { return __ldg(z.tw + x); }
     __device__ int edge(int x) const { return __ldg(z.ce + x); }
     __device__ int vtx(int x) const { return __ldg(z.fv + x); }
 };
 struct AccQuad {
+    static constexpr int kRound = 4;
     const int *fv, *tw, *ce;
     __device__ int next(int x) const { return quad_next(x); }
     __device__ int prev(int x) const { return quad_prev(x); }
+    __device__ int ring(int x) const { return __ldg(tw + quad_prev(x)); }
     __device__ int twin(int x) const { return __ldg(tw + x); }
     __device__ int edge(int x) const { return __ldg(ce + x); }
     __device__ int vtx(int x) const { return __ldg(fv + x); }
@@ -210,10 +215,12 @@ __device__ __forceinline__ int TriLevel::edge(int x) const {
 }
 
 struct AccTri {
+    static constexpr int kRound = 8;
     const int *fv;
     TriLevel t;
     __device__ int next(int x) const { return tri_next(x); }
     __device__ int prev(int x) const { return tri_prev(x); }
+    __device__ int ring(int x) const { return t.twin(tri_prev(x)); }
     __device__ int twin(int x) const { return t.twin(x); }
     __device__ int edge(int x) const { return t.edge(x); }
     __device__ int vtx(int x) const { return __ldg(fv + x); }

@@ -62,14 +62,14 @@ __device__ __forceinline__ void end_add(EndInfo &r, int y, float sy, int nb) {
 }
 
 // Both end vertices of a crease in one pass. The rings are walked in lockstep, kW corners per
-// round: first the twin chain of the round (the only dependent loads), then the edge-id, table
+// round (4 for quads, 8 for the level-0 polygons and triangles): first the twin chain of the round (the only dependent loads), then the edge-id, table
 // and neighbour loads of all kW corners, which are independent of one another. Crease valency k,
 // sharpness sum S (added in ring order from the start corner), the first two crease neighbours
 // and the smallest crease corner come out exactly as a one-corner-at-a-time walk gives them.
 template <class Acc>
 __device__ void analyse2(const Acc &A, const CreaseList &C, int sa, int sb, EndInfo &ra, EndInfo &rb,
                          int *status) {
-    constexpr int kW = 4;
+    constexpr int kW = Acc::kRound;         // valence of a typical vertex: one round
     end_init(ra);
     end_init(rb);
     int ya = sa, yb = sb;
@@ -81,8 +81,8 @@ __device__ void analyse2(const Acc &A, const CreaseList &C, int sa, int sb, EndI
         for (int q = 0; q < kW; q++) {
             ua[q] = !da; ca[q] = ya;
             ub[q] = !db; cb[q] = yb;
-            if (!da) { ya = A.twin(A.prev(ya)); da = ya == sa; }
-            if (!db) { yb = A.twin(A.prev(yb)); db = yb == sb; }
+            if (!da) { ya = A.ring(ya); da = ya == sa; }
+            if (!db) { yb = A.ring(yb); db = yb == sb; }
         }
         float fa[kW], fb[kW];
         int na[kW], nb[kW];
@@ -228,7 +228,7 @@ void with_acc(TopoImpl &T, int l, F f) {
     LevelBuf &A = T.L[l];
     if (l == 0) {
         AccL0 acc;
-        acc.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+        acc.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
         f(acc);
     } else if (T.scheme == ALSUB_CATMULL_CLARK) {
         f(AccQuad{A.fv, A.tw, A.ce});

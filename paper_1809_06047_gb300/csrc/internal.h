@@ -67,6 +67,13 @@ struct CallGraph {
     unsigned long long used = 0;            // last use (LRU)
 };
 
+// Open-addressing table of the level-0 directed edges (a, b) -> corner, 2^k slots (key ~0 = empty).
+struct DirTable {
+    unsigned long long *key = nullptr;
+    int *val = nullptr;
+    unsigned mask = 0;
+};
+
 struct TopoImpl {
     MeshImpl *mesh = nullptr;
     alsub_scheme scheme;
@@ -74,7 +81,8 @@ struct TopoImpl {
     std::vector<LevelBuf> L;     // levels + 1
     // level-0 adjacency
     int *cf0 = nullptr, *nx0 = nullptr, *pv0 = nullptr, *own0 = nullptr, *vc0 = nullptr;
-    int *eo0 = nullptr, *deg = nullptr, *voff = nullptr, *vfill = nullptr, *vbk = nullptr;
+    int *eo0 = nullptr, *deg = nullptr, *rn0 = nullptr;   // rn0: twin(prev(x)), the ring step
+    DirTable dir;
     int *eid = nullptr, *e0count = nullptr;
     int *status = nullptr;       // latched device error
     // temporaries
@@ -120,8 +128,10 @@ int scan_exclusive(const int *in, int *out, long long n, int *total, const int *
 int scan_exclusive64(const int *in, long long *out, long long n, long long *total, void *tmp,
                      cudaStream_t s);
 
-// Level 0: corner maps, twins, ownership, edge numbering.
+// Level 0: corner maps, twins, ownership, edge numbering, ring steps.
 void level0_build(TopoImpl &T, cudaStream_t s);
+// Level 0's per-vertex checks (in some face, valence, single fan); only sets the status word.
+void level0_validate(TopoImpl &T, cudaStream_t s);
 // Level 0's crease list and hash table (needs level0_build's arrays).
 void level0_creases(TopoImpl &T, cudaStream_t s);
 

@@ -3,9 +3,10 @@
 //
 //  * face order c = M^T 1 (Eq. fo) and the cyclic next / previous corner (the circulant action
 //    maps Q_c, Q_c^{c-1} of Eq. CC_E, evaluated on demand);
-//  * the vertex -> corner incidence (a counting sort of M by row: the symbolic pass of the implicit
-//    mapped SpGEMM, Sec. 4.2) and from it the twin of every corner: the corner b -> a of corner
-//    a -> b, i.e. the face-adjacency matrix F (Eq. F) stored per corner;
+//  * the twin of every corner: the corner b -> a of corner a -> b, i.e. the face-adjacency matrix F
+//    (Eq. F) stored per corner, found through an open-addressing table of directed edges (the
+//    symbolic pass of the implicit mapped SpGEMM of Sec. 4.2 done as one hash join: every corner
+//    inserts its directed edge, every corner looks up the reverse one);
 //  * the edge numbering: a corner owns its edge when its start vertex is the smaller endpoint
 //    (the upper triangle of E, Eq. CC_E); an exclusive scan over the owner flags numbers the
 //    edges deterministically;
@@ -18,76 +19,130 @@ namespace alsub {
 
 namespace {
 
+constexpr unsigned long long kEmptyKey = ~0ull;
+
+__device__ __forceinline__ unsigned long long dir_key(int a, int b) {
+    return ((unsigned long long)(unsigned)a << 32) | (unsigned)b;
+}
+__device__ __forceinline__ unsigned dir_slot(unsigned long long k, unsigned mask) {
+    k ^= k >> 33;                       // 64-bit finaliser (multiply-xorshift)
+    k *= 0xff51afd7ed558ccdull;
+    k ^= k >> 33;
+    return (unsigned)k & mask;
+}
+// Returns false when the directed edge is already in the table (a duplicate: non-manifold).
+__device__ bool dir_insert(const DirTable &t, int a, int b, int x) {
+    const unsigned long long k = dir_key(a, b);
+    unsigned h = dir_slot(k, t.mask);
+    for (unsigned probe = 0; probe <= t.mask; probe++) {
+        const unsigned long long old = atomicCAS(t.key + h, kEmptyKey, k);
+        if (old == kEmptyKey) {
+            t.val[h] = x;
+            return true;
+        }
+        if (old == k) return false;
+        h = (h + 1) & t.mask;
+    }
+    return false;
+}
+__device__ int dir_find(const DirTable &t, int a, int b) {
+    const unsigned long long k = dir_key(a, b);
+    unsigned h = dir_slot(k, t.mask);
+    for (unsigned probe = 0; probe <= t.mask; probe++) {
+        const unsigned long long q = __ldg(t.key + h);
+        if (q == k) return __ldg(t.val + h);
+        if (q == kEmptyKey) return -1;
+        h = (h + 1) & t.mask;
+    }
+    return -1;
+}
+
+// Corner maps, vertex degrees (M 1) and each vertex's smallest outgoing corner.
 __global__ void k_faces(int F, const int *__restrict__ off, const int *__restrict__ fv, int *cf,
-                        int *nx, int *pv, int *deg) {
+                        int *nx, int *pv, int *deg, unsigned *vc) {
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= F) return;
-    int s = off[r], c = off[r + 1] - s;
+    const int s = off[r], c = off[r + 1] - s;
     for (int j = 0; j < c; j++) {
-        int x = s + j;
+        const int x = s + j, v = fv[x];
         cf[x] = r;
         nx[x] = s + (j + 1 == c ? 0 : j + 1);
         pv[x] = s + (j == 0 ? c - 1 : j - 1);
-        atomicAdd(deg + fv[x], 1);
+        atomicAdd(deg + v, 1);
+        atomicMin(vc + v, (unsigned)x);
     }
 }
 
-__global__ void k_bucket(int nnz, const int *__restrict__ fv, const int *__restrict__ voff,
-                         int *vfill, int *vbk) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
+// The directed edge of every corner into the table, one corner per thread.
+__global__ void k_insert(int nnz, const int *__restrict__ fv, const int *__restrict__ nx, DirTable tab,
+                         int *status) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nnz) return;
-    int v = fv[x];
-    int pos = atomicAdd(vfill + v, 1);
-    vbk[voff[v] + pos] = x;
+    if (!dir_insert(tab, fv[x], fv[nx[x]], x)) set_status(status, ALSUB_ERR_NONMANIFOLD);  // duplicate
 }
 
-// Twin of a -> b: the unique corner b -> a in b's bucket. The bucket order is not deterministic,
-// but the result of the search is.
-__global__ void k_twin(int nnz, const int *__restrict__ fv, const int *__restrict__ nx,
-                       const int *__restrict__ voff, const int *__restrict__ vbk, int *tw, int *own,
-                       int *status) {
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= nnz) return;
-    int a = fv[x], b = fv[nx[x]];
-    int found = x, cnt = 0;
-    const int qb0 = voff[b], qb1 = voff[b + 1], qa0 = voff[a], qa1 = voff[a + 1];
-#pragma unroll 4
-    for (int q = qb0; q < qb1; q++) {
-        int d = vbk[q];
-        if (fv[nx[d]] == a) { found = d; cnt++; }
+// Twin of a -> b: the corner of b -> a (none: an open edge, i.e. a boundary). A corner owns its
+// edge when a < b; each block also counts its owner corners (the edge numbering scans the counts).
+__global__ void __launch_bounds__(kBlock) k_twin(int nnz, const int *__restrict__ fv, const int *__restrict__ nx,
+                                                 DirTable tab, int *tw, int *own, int *bcount, int *status) {
+    __shared__ int wsum[kBlock / 32];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    int o = 0;
+    if (x < nnz) {
+        const int a = fv[x], b = fv[nx[x]];
+        const int t = dir_find(tab, b, a);
+        if (t < 0) set_status(status, ALSUB_ERR_UNSUPPORTED);
+        tw[x] = t < 0 ? x : t;
+        o = a < b ? 1 : 0;
+        own[x] = o;
     }
-    if (cnt == 0) set_status(status, ALSUB_ERR_UNSUPPORTED);      // open edge: boundary
-    else if (cnt > 1) set_status(status, ALSUB_ERR_NONMANIFOLD);
-#pragma unroll 4
-    for (int q = qa0; q < qa1; q++) {                              // duplicate directed edge
-        int d = vbk[q];
-        if (d != x && fv[nx[d]] == b) set_status(status, ALSUB_ERR_NONMANIFOLD);
+    const unsigned bal = __ballot_sync(0xffffffffu, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int sum = 0;
+        for (int w = 0; w < kBlock / 32; w++) sum += wsum[w];
+        bcount[blockIdx.x] = sum;
     }
-    tw[x] = cnt == 1 ? found : x;
-    own[x] = a < b ? 1 : 0;
 }
 
-// Designated outgoing corner of each vertex (the smallest) and the single-fan check: the ring
-// walk x <- twin(prev(x)) must return to the start after exactly deg(v) steps.
-__global__ void k_vertex(int V, const int *__restrict__ voff, const int *__restrict__ vbk,
-                         const int *__restrict__ tw, const int *__restrict__ pv, int *vc, int *status) {
+// Edge id of every owner corner: its block's offset (the scan of the block counts) plus its rank
+// among the block's owner corners (ballots), so the numbering is the owner corners in corner order.
+__global__ void __launch_bounds__(kBlock) k_eid(int nnz, const int *__restrict__ own, const int *__restrict__ boff,
+                                                int *eid) {
+    __shared__ int wpre[kBlock / 32];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int o = x < nnz ? own[x] : 0;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const unsigned bal = __ballot_sync(0xffffffffu, o);
+    if (lane == 0) wpre[w] = __popc(bal);
+    __syncthreads();
+    int before = 0;
+    for (int q = 0; q < w; q++) before += wpre[q];
+    if (o) eid[x] = boff[blockIdx.x] + before + __popc(bal & ((1u << lane) - 1u));
+}
+
+// Validation of each vertex: it is in some face, its valence is supported, and its corners form a
+// single fan (the ring walk x <- twin(prev(x)) returns to the start after exactly deg(v) steps).
+__global__ void k_vertex(int V, const int *__restrict__ deg, const unsigned *__restrict__ vc,
+                         const int *__restrict__ rn, int *status) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    int s = voff[v], deg = voff[v + 1] - s;
-    if (deg == 0) { set_status(status, ALSUB_ERR_INVALID_ARG); vc[v] = 0; return; }
-    if (deg > kMaxValence) { set_status(status, ALSUB_ERR_UNSUPPORTED); vc[v] = vbk[s]; return; }
-    int m = vbk[s];
-    for (int q = s + 1; q < s + deg; q++) m = min(m, vbk[q]);
-    vc[v] = m;
+    const int d = deg[v];
+    if (d == 0) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
+    if (d > kMaxValence) { set_status(status, ALSUB_ERR_UNSUPPORTED); return; }
     if (failed(status)) return;
+    const int m = (int)vc[v];
     int x = m, steps = 0;
-    do { x = tw[pv[x]]; steps++; } while (x != m && steps <= deg);
-    if (steps != deg) set_status(status, ALSUB_ERR_NONMANIFOLD);
+    do { x = rn[x]; steps++; } while (x != m && steps <= d);
+    if (steps != d) set_status(status, ALSUB_ERR_NONMANIFOLD);
 }
 
+// Edge ids (an owner's own, else its twin's), owner corner of each edge, and the ring step
+// twin(prev(x)).
 __global__ void k_edges(int nnz, const int *__restrict__ own, const int *__restrict__ eid,
-                        const int *__restrict__ tw, const int *e0count, int E0, int *ce, int *eo,
-                        int *status) {
+                        const int *__restrict__ tw, const int *__restrict__ pv, const int *e0count, int E0,
+                        int *ce, int *eo, int *rn, int *status) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x == 0 && *e0count != E0) set_status(status, ALSUB_ERR_NONMANIFOLD);
     if (x >= nnz) return;
@@ -95,31 +150,23 @@ __global__ void k_edges(int nnz, const int *__restrict__ own, const int *__restr
     e = min(max(e, 0), E0 - 1);
     ce[x] = e;
     if (own[x]) eo[e] = x;
+    rn[x] = tw[pv[x]];
 }
 
 // Level-0 crease list, in input order (the crease matrix C of Sec. 3.3): each input crease
-// (a, b, sigma) is mapped to its edge and owner corner and entered into the level's hash table.
-// A crease that is not an edge of the mesh, or an edge tagged twice, is an input error.
+// (a, b, sigma) is mapped to its edge (the corner a -> b, from the directed-edge table) and owner
+// corner and entered into the level's hash table. A crease that is not an edge of the mesh, or an
+// edge tagged twice, is an input error.
 __global__ void k_crease0(int K, const int *__restrict__ cv, const float *__restrict__ cs,
-                          const int *__restrict__ fv, const int *__restrict__ nx,
-                          const int *__restrict__ voff, const int *__restrict__ vbk,
-                          const int *__restrict__ ce, const int *__restrict__ own,
-                          const int *__restrict__ tw, CreaseList out, int *status) {
+                          const int *__restrict__ fv, DirTable tab, const int *__restrict__ ce,
+                          const int *__restrict__ own, const int *__restrict__ tw, CreaseList out,
+                          int *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i == 0) *out.count = K;
     if (i >= K) return;
     out.edge[i] = 0; out.own[i] = 0; out.sig[i] = 0.f; out.verts[2 * i] = 0; out.verts[2 * i + 1] = 0;
     if (failed(status)) return;
-    const int a = cv[2 * i], b = cv[2 * i + 1];
-    // every candidate of a's bucket is tested (no early exit), so the loads of different
-    // candidates do not wait on one another; the first match is taken
-    int x = -1;
-    const int q0 = voff[a], q1 = voff[a + 1];
-#pragma unroll 4
-    for (int q = q0; q < q1; q++) {
-        const int d = vbk[q];
-        if (x < 0 && fv[nx[d]] == b) x = d;
-    }
+    const int x = dir_find(tab, cv[2 * i], cv[2 * i + 1]);
     if (x < 0) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
     const int o = own[x] ? x : tw[x], e = ce[x];
     const float s = cs[i];
@@ -139,15 +186,23 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     const int V = M.V, F = M.F, nnz = M.nnz, E0 = (int)L0.E;
     cudaMemsetAsync(T.status, 0, sizeof(int), s);
     cudaMemsetAsync(T.deg, 0, sizeof(int) * (size_t)V, s);
-    cudaMemsetAsync(T.vfill, 0, sizeof(int) * (size_t)V, s);
-    k_faces<<<grid_for(F), kBlock, 0, s>>>(F, M.d_off, M.d_fv, T.cf0, T.nx0, T.pv0, T.deg);
-    T.launches += 5 + scan_exclusive(T.deg, T.voff, V, T.voff + V, nullptr, T.scan_tmp, s);
-    k_bucket<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.voff, T.vfill, T.vbk);
-    k_twin<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.voff, T.vbk, L0.tw, T.own0, T.status);
-    k_vertex<<<grid_for(V), kBlock, 0, s>>>(V, T.voff, T.vbk, L0.tw, T.pv0, T.vc0, T.status);
-    T.launches += scan_exclusive(T.own0, T.eid, nnz, T.e0count, nullptr, T.scan_tmp, s);
-    k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.e0count, E0, L0.ce, T.eo0,
-                                             T.status);
+    cudaMemsetAsync(T.vc0, 0xff, sizeof(int) * (size_t)V, s);
+    cudaMemsetAsync(T.dir.key, 0xff, sizeof(unsigned long long) * ((size_t)T.dir.mask + 1), s);
+    k_faces<<<grid_for(F), kBlock, 0, s>>>(F, M.d_off, M.d_fv, T.cf0, T.nx0, T.pv0, T.deg,
+                                           reinterpret_cast<unsigned *>(T.vc0));
+    k_insert<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, T.status);
+    const unsigned nb = grid_for(nnz);
+    k_twin<<<nb, kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, L0.tw, T.own0, T.flags, T.status);
+    T.launches += 5 + scan_exclusive(T.flags, T.pos, nb, T.e0count, nullptr, T.scan_tmp, s);
+    k_eid<<<nb, kBlock, 0, s>>>(nnz, T.own0, T.pos, T.eid);
+    k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.pv0, T.e0count, E0, L0.ce, T.eo0,
+                                             T.rn0, T.status);
+}
+
+void level0_validate(TopoImpl &T, cudaStream_t s) {
+    k_vertex<<<grid_for(T.mesh->V), kBlock, 0, s>>>(T.mesh->V, T.deg, reinterpret_cast<unsigned *>(T.vc0),
+                                                    T.rn0, T.status);
+    T.launches += 1;
 }
 
 void level0_creases(TopoImpl &T, cudaStream_t s) {
@@ -156,8 +211,8 @@ void level0_creases(TopoImpl &T, cudaStream_t s) {
     CreaseList &C = L0.cr;
     if (C.cap > 0) {
         crease_table_clear(C, s);
-        k_crease0<<<grid_for(M.K), kBlock, 0, s>>>(M.K, M.d_cv, M.d_cs, M.d_fv, T.nx0, T.voff, T.vbk,
-                                                   L0.ce, T.own0, L0.tw, C, T.status);
+        k_crease0<<<grid_for(M.K), kBlock, 0, s>>>(M.K, M.d_cv, M.d_cs, M.d_fv, T.dir, L0.ce, T.own0, L0.tw,
+                                                   C, T.status);
         T.launches += 1;
     } else if (C.count) {
         cudaMemsetAsync(C.count, 0, sizeof(int), s);

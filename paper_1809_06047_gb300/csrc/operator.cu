@@ -447,7 +447,7 @@ OpLevel op_level(TopoImpl &T, int l) {
     OpLevel L;
     L.scheme = T.scheme; L.l = l;
     L.V = (int)A.V; L.F = (int)A.F; L.E = (int)A.E;
-    L.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+    L.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
     L.fv = l == 0 ? T.mesh->d_fv : A.fv;
     L.ce = A.ce;
     L.tw = A.tw;

@@ -177,7 +177,7 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     a.V = (int)A.V; a.F = (int)A.F; a.E = (int)A.E;
     a.fv = A.fv;
     a.t = tri_level(T, l);
-    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
@@ -220,7 +220,7 @@ TriLevel tri_level(const TopoImpl &T, int l) {
     const LevelBuf &A = T.L[l];
     TriLevel t;
     t.sqrt3 = T.scheme == ALSUB_SQRT3;
-    t.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0};
+    t.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
     if (A.helpers || l == 0) {
         t.ce = A.ce;
         t.tw = A.tw;
