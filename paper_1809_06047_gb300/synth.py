@@ -359,6 +359,18 @@ def pillow(n: int = 6) -> dict:
     return _pack(faces, P, np.zeros((0, 2)), np.zeros(0))
 
 
+def prism(n: int = 12, h: float = 0.7) -> dict:
+    """Closed n-gon prism: two n-gon caps (faces of n corners) and n side quads; valence 3."""
+    t = 2.0 * math.pi * np.arange(n) / n
+    top = np.stack([np.cos(t), np.sin(t), np.full(n, h)], axis=1)
+    bot = np.stack([np.cos(t), np.sin(t), np.full(n, -h)], axis=1)
+    P = np.concatenate([top, bot]).astype(np.float32)
+    faces = [list(range(n)),                                      # top, CCW seen from +z
+             [n + i for i in range(n - 1, -1, -1)]]               # bottom, CCW seen from -z
+    faces += [[n + i, n + (i + 1) % n, (i + 1) % n, i] for i in range(n)]
+    return _pack(faces, P, np.zeros((0, 2)), np.zeros(0))
+
+
 def serving_requests(n_requests: int = 512, rate_hz: float = 2000.0, n_resident: int = 32,
                      seed: int = SEED_BASE + 4, fmin: float = 1e3, fmax: float = 6e4,
                      frac_frame: float = 0.70) -> dict:

@@ -52,6 +52,8 @@ def test_sqrt3_tri_torus128_L5(mode):
 SMALL = [
     ("cc", synth.cube, 4),
     ("cc", lambda: synth.pillow(6), 3),
+    ("cc", lambda: synth.pillow(11), 3),
+    ("cc", lambda: synth.prism(12), 4),
     ("cc", lambda: synth.torus_cc_mixed(7, 9, seed=41), 3),
     ("loop", synth.octahedron, 4),
     ("loop", synth.tetrahedron, 4),

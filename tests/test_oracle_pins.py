@@ -70,6 +70,7 @@ def _meshes():
     return [
         ("cc", synth.cube()),
         ("cc", synth.pillow(6)),
+        ("cc", synth.prism(12)),
         ("cc", synth.torus_cc_mixed(12, 12, seed=11)),
         ("loop", synth.octahedron()),
         ("loop", synth.torus_tri(10, 10, seed=12)),
