@@ -32,6 +32,9 @@ struct TriArgs {
     int V, F, E;
     const int *fv;
     TriLevel t;                   // edge ids / twins of level l (stored or derived)
+    // level l - 1 (l >= 1; always stored): face table, edge ids, twins, vertex count
+    const int *pfv = nullptr, *pce = nullptr, *ptw = nullptr;
+    int Vp = 0;
     Level0 z;
     const float *P;
     float *Pn;
@@ -97,22 +100,60 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
             float3 ep = 0.375f * (p[j] + p[(j + 1) % 3]) + 0.125f * (p[(j + 2) % 3] + ldpv(P, d, a.in4));
             stpv(a.Pn, V + ee[j], ep, a.out4);
         }
+        if (a.l == 0) {
 #pragma unroll 1
-        for (int j = 0; j < 3; j++) {
-            int x = c + j;
-            if (!loop_vown(a.l, x, a.z)) continue;
-            int y = x, n = 0;
-            float3 sp = f3(0.f, 0.f, 0.f);
-            do {
-                sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
-                y = a.t.twin(tri_prev(y));
-                n++;
-            } while (y != x && n < kMaxValence);
-            if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
-            float beta = c_loop_beta[n];
-            const float3 pj = j == 0 ? p[0] : (j == 1 ? p[1] : p[2]);   // constant indices: registers
-            const int vj = j == 0 ? vv[0] : (j == 1 ? vv[1] : vv[2]);
-            stpv(a.Pn, vj, (1.0f - (float)n * beta) * pj + beta * sp, a.out4);
+            for (int j = 0; j < 3; j++) {
+                int x = c + j;
+                if (!loop_vown(a.l, x, a.z)) continue;
+                int y = x, n = 0;
+                float3 sp = f3(0.f, 0.f, 0.f);
+                do {
+                    sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
+                    y = a.t.twin(tri_prev(y));
+                    n++;
+                } while (y != x && n < kMaxValence);
+                if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
+                float beta = c_loop_beta[n];
+                const float3 pj = j == 0 ? p[0] : (j == 1 ? p[1] : p[2]);   // constant indices: registers
+                const int vj = j == 0 ? vv[0] : (j == 1 ? vv[1] : vv[2]);
+                stpv(a.Pn, vj, (1.0f - (float)n * beta) * pj + beta * sp, a.out4);
+            }
+        } else {
+            // Level l >= 1: this triangle is child k of triangle R of level l - 1, so its corner 0
+            // is R's vertex v_k and its corner 1 the edge point E_k of R's edge k. Their rings on
+            // level l are read from level l - 1, whose arrays are stored: the neighbours of v_k
+            // are the edge points of its level-(l-1) edges (a walk of the stored parent ring);
+            // those of E_k are v_k, v_k+1, E_k-1, E_k+1 and the two other edge points of the
+            // triangle across edge k (valence 6).
+            const int R = r >> 2, k = r & 3;
+            if (k < 3 && loop_vown(a.l, c, a.z)) {
+                const int x0 = 3 * R + k;
+                int y = x0, n = 0;
+                float3 sp = f3(0.f, 0.f, 0.f);
+                do {
+                    sp += ldpv(P, a.Vp + __ldg(a.pce + y), a.in4);
+                    y = __ldg(a.ptw + tri_prev(y));
+                    n++;
+                } while (y != x0 && n < kMaxValence);
+                if (y != x0) {
+                    set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                } else {
+                    const float beta = c_loop_beta[n];
+                    stpv(a.Pn, vv[0], (1.0f - (float)n * beta) * p[0] + beta * sp, a.out4);
+                }
+            }
+            if (k < 3 && loop_own(a.l - 1, 3 * R + k, a.z)) {
+                const int k1 = k == 2 ? 0 : k + 1;
+                const int t = __ldg(a.ptw + 3 * R + k);
+                const int vn = __ldg(a.pfv + 3 * R + k1), en = a.Vp + __ldg(a.pce + 3 * R + k1);
+                const int R2 = t / 3, k2 = t - 3 * R2;
+                const int ea = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 2 ? 0 : k2 + 1));
+                const int eb = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 0 ? 2 : k2 - 1));
+                const float3 sp = (p[0] + p[2]) + (ldpv(P, vn, a.in4) + ldpv(P, en, a.in4)) +
+                                  (ldpv(P, ea, a.in4) + ldpv(P, eb, a.in4));
+                const float beta = c_loop_beta[6];
+                stpv(a.Pn, vv[1], (1.0f - 6.0f * beta) * p[1] + beta * sp, a.out4);
+            }
         }
     }
 }
@@ -177,6 +218,13 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     a.V = (int)A.V; a.F = (int)A.F; a.E = (int)A.E;
     a.fv = A.fv;
     a.t = tri_level(T, l);
+    if (l >= 1) {
+        const LevelBuf &Pl = T.L[l - 1];
+        a.pfv = Pl.fv;
+        a.pce = Pl.ce;
+        a.ptw = Pl.tw;
+        a.Vp = (int)Pl.V;
+    }
     a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
