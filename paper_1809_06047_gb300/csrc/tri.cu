@@ -191,22 +191,54 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
 #pragma unroll
         for (int j = 0; j < 3; j++) p[j] = ldpv(P, vv[j], a.in4);
         stpv(a.Pn, V + r, (1.0f / 3.0f) * (p[0] + p[1] + p[2]), a.out4);
+        if (a.l == 0) {
 #pragma unroll 1
-        for (int j = 0; j < 3; j++) {
-            int x = c + j;
-            if (!sqrt3_vown(a.l, x, a.z)) continue;
-            int y = x, n = 0;
-            float3 sp = f3(0.f, 0.f, 0.f);
-            do {
-                sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
-                y = a.t.twin(tri_prev(y));
-                n++;
-            } while (y != x && n < kMaxValence);
-            if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
-            float al = c_sqrt3_alpha[n];
-            const float3 pj = j == 0 ? p[0] : (j == 1 ? p[1] : p[2]);   // constant indices: registers
-            const int vj = j == 0 ? vv[0] : (j == 1 ? vv[1] : vv[2]);
-            stpv(a.Pn, vj, (1.0f - al) * pj + (al / (float)n) * sp, a.out4);
+            for (int j = 0; j < 3; j++) {
+                int x = c + j;
+                if (!sqrt3_vown(a.l, x, a.z)) continue;
+                int y = x, n = 0;
+                float3 sp = f3(0.f, 0.f, 0.f);
+                do {
+                    sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
+                    y = a.t.twin(tri_prev(y));
+                    n++;
+                } while (y != x && n < kMaxValence);
+                if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
+                float al = c_sqrt3_alpha[n];
+                const float3 pj = j == 0 ? p[0] : (j == 1 ? p[1] : p[2]);   // constant indices: registers
+                const int vj = j == 0 ? vv[0] : (j == 1 ? vv[1] : vv[2]);
+                stpv(a.Pn, vj, (1.0f - al) * pj + (al / (float)n) * sp, a.out4);
+            }
+        } else {
+            // Level l >= 1: this triangle is the child of parent corner r, [v_r, f_F(r), f_T] with
+            // T = r / 3. Rings on level l, read from the stored level l - 1: the old vertex v_r
+            // neighbours the face points of its parent-level triangles (a walk of the parent
+            // ring); f_T (designated at the child of T's corner 0) neighbours T's three vertices
+            // and the face points of T's three neighbours (valence 6).
+            if (sqrt3_vown(a.l, c, a.z)) {
+                int y = r, n = 0;
+                float3 sp = f3(0.f, 0.f, 0.f);
+                do {
+                    sp += ldpv(P, a.Vp + y / 3, a.in4);
+                    y = __ldg(a.ptw + tri_prev(y));
+                    n++;
+                } while (y != r && n < kMaxValence);
+                if (y != r) {
+                    set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                } else {
+                    const float al = c_sqrt3_alpha[n];
+                    stpv(a.Pn, vv[0], (1.0f - al) * p[0] + (al / (float)n) * sp, a.out4);
+                }
+            }
+            if (r % 3 == 0) {
+                // v_r = T's vertex 0 and f_F(r) = the face point across T's edge 0 are p[0], p[1]
+                const int v1 = __ldg(a.pfv + r + 1), v2 = __ldg(a.pfv + r + 2);
+                const int n1 = a.Vp + __ldg(a.ptw + r + 1) / 3, n2 = a.Vp + __ldg(a.ptw + r + 2) / 3;
+                const float3 sp = (p[0] + p[1]) + (ldpv(P, v1, a.in4) + ldpv(P, v2, a.in4)) +
+                                  (ldpv(P, n1, a.in4) + ldpv(P, n2, a.in4));
+                const float al = c_sqrt3_alpha[6];
+                stpv(a.Pn, vv[2], (1.0f - al) * p[2] + (al / 6.0f) * sp, a.out4);
+            }
         }
     }
 }
