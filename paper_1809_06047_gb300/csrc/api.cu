@@ -167,8 +167,8 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     T.scan_tmp_bytes = scan_tmp_bytes(std::max<long long>(nflags, V));
     AL(*(char **)&T.scan_tmp, T.scan_tmp_bytes);
     // Per-corner edge ids and twins are stored for every level that a later step reads them from.
-    // Loop derives the last level's from its parent's. The last two Catmull-Clark steps derive them
-    // instead: level levels - 1 (>= 2) from its
+    // Loop and sqrt(3) derive the last level's from its parent's. The last two Catmull-Clark steps
+    // derive them instead: level levels - 1 (>= 2) from its
     // parent, and level levels - 2 (>= 2) from its parent too, the last step then going back two
     // levels; a level whose creases are still alive keeps them (its crease analysis walks rings
     // through them).
@@ -181,10 +181,9 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
         if (cc && l == levels - 1 && l >= 2 && B.cr.cap == 0) B.helpers = false;
         if (cc && l == levels - 2 && l >= 2 && B.cr.cap == 0 && T.L[levels - 1].cr.cap == 0)
             B.helpers = false;
-        // Loop: the last step derives its level's edge ids and twins from the parent level (crease
-        // analysis included). sqrt(3) keeps them: its last step's ring walks measured slower on
-        // derived twins than the write they save.
-        if (M.scheme == ALSUB_LOOP && l == levels - 1 && l >= 1) B.helpers = false;
+        // Loop and sqrt(3): the last step derives its level's edge ids and twins from the parent
+        // level (crease analysis included); its vertex rings are read from the parent level.
+        if (!cc && l == levels - 1 && l >= 1) B.helpers = false;
         if (B.helpers) {
             if (M.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);
             AL(B.tw, B.nnz);
