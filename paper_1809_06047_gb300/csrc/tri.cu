@@ -54,7 +54,8 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
     for (int j = 0; j < 3; j++) {
         vv[j] = __ldg(a.fv + c + j);
         ee[j] = a.t.edge(c + j);
-        tt[j] = (HELP || EVAL) ? a.t.twin(c + j) : 0;
+        // the eval of levels >= 1 reads its neighbours from the parent level: no twins needed
+        tt[j] = (HELP || (EVAL && a.l == 0)) ? a.t.twin(c + j) : 0;
         ow[j] = loop_own(a.l, c + j, a.z);
     }
     if (TOPO) {
@@ -93,14 +94,14 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
         float3 p[3];
 #pragma unroll
         for (int j = 0; j < 3; j++) p[j] = ldpv(P, vv[j], a.in4);
-#pragma unroll
-        for (int j = 0; j < 3; j++) {
-            if (!ow[j]) continue;
-            int d = __ldg(a.fv + tri_prev(tt[j]));
-            float3 ep = 0.375f * (p[j] + p[(j + 1) % 3]) + 0.125f * (p[(j + 2) % 3] + ldpv(P, d, a.in4));
-            stpv(a.Pn, V + ee[j], ep, a.out4);
-        }
         if (a.l == 0) {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                if (!ow[j]) continue;
+                int d = __ldg(a.fv + tri_prev(tt[j]));
+                float3 ep = 0.375f * (p[j] + p[(j + 1) % 3]) + 0.125f * (p[(j + 2) % 3] + ldpv(P, d, a.in4));
+                stpv(a.Pn, V + ee[j], ep, a.out4);
+            }
 #pragma unroll 1
             for (int j = 0; j < 3; j++) {
                 int x = c + j;
@@ -126,6 +127,27 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
             // those of E_k are v_k, v_k+1, E_k-1, E_k+1 and the two other edge points of the
             // triangle across edge k (valence 6).
             const int R = r >> 2, k = r & 3;
+            if (k < 3) {
+                // The corner children own their corner-0 edge (the half v_k E_k of R's edge k) and
+                // corner-1 edge (E_k E_k-1, inside R). Far vertices: across the half, E'_k2+1 of
+                // the triangle R2 across edge k (twin 3 R2 + k2); across the inner edge, E_k+1.
+                const int k1 = k == 2 ? 0 : k + 1;
+                const int t = __ldg(a.ptw + 3 * R + k);
+                const int R2 = t / 3, k2 = t - 3 * R2;
+                const int en = a.Vp + __ldg(a.pce + 3 * R + k1);
+                const int ea = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 2 ? 0 : k2 + 1));
+                const float3 pen = ldpv(P, en, a.in4), pea = ldpv(P, ea, a.in4);
+                stpv(a.Pn, V + ee[0], 0.375f * (p[0] + p[1]) + 0.125f * (p[2] + pea), a.out4);
+                stpv(a.Pn, V + ee[1], 0.375f * (p[1] + p[2]) + 0.125f * (p[0] + pen), a.out4);
+                if (loop_own(a.l - 1, 3 * R + k, a.z)) {
+                    // E_k: v_k, E_k-1 (this triangle), v_k+1, E_k+1, and E'_k2+1, E'_k2-1 across
+                    const int vn = __ldg(a.pfv + 3 * R + k1);
+                    const int eb = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 0 ? 2 : k2 - 1));
+                    const float3 sp = (p[0] + p[2]) + (ldpv(P, vn, a.in4) + pen) + (pea + ldpv(P, eb, a.in4));
+                    const float beta = c_loop_beta[6];
+                    stpv(a.Pn, vv[1], (1.0f - 6.0f * beta) * p[1] + beta * sp, a.out4);
+                }
+            }
             if (k < 3 && loop_vown(a.l, c, a.z)) {
                 const int x0 = 3 * R + k;
                 int y = x0, n = 0;
@@ -141,18 +163,6 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
                     const float beta = c_loop_beta[n];
                     stpv(a.Pn, vv[0], (1.0f - (float)n * beta) * p[0] + beta * sp, a.out4);
                 }
-            }
-            if (k < 3 && loop_own(a.l - 1, 3 * R + k, a.z)) {
-                const int k1 = k == 2 ? 0 : k + 1;
-                const int t = __ldg(a.ptw + 3 * R + k);
-                const int vn = __ldg(a.pfv + 3 * R + k1), en = a.Vp + __ldg(a.pce + 3 * R + k1);
-                const int R2 = t / 3, k2 = t - 3 * R2;
-                const int ea = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 2 ? 0 : k2 + 1));
-                const int eb = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 0 ? 2 : k2 - 1));
-                const float3 sp = (p[0] + p[2]) + (ldpv(P, vn, a.in4) + ldpv(P, en, a.in4)) +
-                                  (ldpv(P, ea, a.in4) + ldpv(P, eb, a.in4));
-                const float beta = c_loop_beta[6];
-                stpv(a.Pn, vv[1], (1.0f - 6.0f * beta) * p[1] + beta * sp, a.out4);
             }
         }
     }
