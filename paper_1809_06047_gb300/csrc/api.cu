@@ -341,25 +341,6 @@ void refine_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStr
     }
 }
 
-// The side stream and fork / join events of alsub_subdivide (made before any capture).
-alsub_status ensure_side(TopoImpl &T) {
-    if (T.side) return ALSUB_OK;
-    if (cudaStreamCreateWithFlags(&T.side, cudaStreamNonBlocking) != cudaSuccess) {
-        cudaGetLastError();
-        T.side = nullptr;
-        return ALSUB_OK;                    // no side branch: everything runs on the caller's stream
-    }
-    T.fork_ev.assign(T.levels + 1, nullptr);
-    T.join_ev.assign(T.levels + 1, nullptr);
-    for (int l = 0; l <= T.levels; l++)
-        if (cudaEventCreateWithFlags(&T.fork_ev[l], cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&T.join_ev[l], cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(ALSUB_ERR_DEVICE, "event creation failed");
-        }
-    return ALSUB_OK;
-}
-
 void free_side(TopoImpl &T) {
     for (cudaEvent_t e : T.fork_ev) if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : T.join_ev) if (e) cudaEventDestroy(e);
@@ -368,6 +349,24 @@ void free_side(TopoImpl &T) {
     if (T.side) cudaStreamDestroy(T.side);
     T.side = nullptr;
 }
+
+// The side stream and fork / join events of alsub_subdivide (made before any capture). If any of
+// them cannot be made, everything made is released and the call runs on the caller's stream alone.
+void ensure_side(TopoImpl &T) {
+    if (T.side) return;
+    bool ok = cudaStreamCreateWithFlags(&T.side, cudaStreamNonBlocking) == cudaSuccess;
+    if (!ok) T.side = nullptr;
+    T.fork_ev.assign(T.levels + 1, nullptr);
+    T.join_ev.assign(T.levels + 1, nullptr);
+    for (int l = 0; ok && l <= T.levels; l++)
+        ok = cudaEventCreateWithFlags(&T.fork_ev[l], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&T.join_ev[l], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_side(T);
+    }
+}
+
 
 // Dynamic topology. The crease analysis of level l needs level l's adjacency but no positions, so
 // it runs on a side branch beside the build + eval of level l (forked when the step that built
@@ -776,8 +775,8 @@ alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, voi
                              void *stream) {
     if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     TopoImpl &T = h->t;
-    alsub_status st = ensure_side(T);
-    if (st == ALSUB_OK) st = run_call(T, 1, P0, PL, scratch, (cudaStream_t)stream, subdivide_body);
+    ensure_side(T);
+    alsub_status st = run_call(T, 1, P0, PL, scratch, (cudaStream_t)stream, subdivide_body);
     if (T.tcap) T.tcalls++;
     if (st == ALSUB_OK) T.built = true;
     return st;

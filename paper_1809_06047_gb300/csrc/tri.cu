@@ -35,6 +35,9 @@ struct TriArgs {
     // level l - 1 (l >= 1; always stored): face table, edge ids, twins, vertex count
     const int *pfv = nullptr, *pce = nullptr, *ptw = nullptr;
     int Vp = 0;
+    // every level's stored edge ids and twins (null where not stored) and edge counts
+    const int *cel[kMaxLevels], *twl[kMaxLevels];
+    int El[kMaxLevels];
     Level0 z;
     const float *P;
     float *Pn;
@@ -149,19 +152,52 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
                 }
             }
             if (k < 3 && loop_vown(a.l, c, a.z)) {
-                const int x0 = 3 * R + k;
-                int y = x0, n = 0;
-                float3 sp = f3(0.f, 0.f, 0.f);
-                do {
-                    sp += ldpv(P, a.Vp + __ldg(a.pce + y), a.in4);
-                    y = __ldg(a.ptw + tri_prev(y));
-                    n++;
-                } while (y != x0 && n < kMaxValence);
-                if (y != x0) {
-                    set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                // v_k = R's corner k. Follow it up while it is corner 0 of a corner child: it was
+                // born on level m >= 1 as the midpoint of edge kb of triangle G of level m - 1
+                // (valence 6), or is a control-mesh vertex (m = 0, any valence: walk the parent ring).
+                int m = a.l - 1, x = 3 * R + k, kb = 0;
+                while (m > 0) {
+                    const int g = x / 3, i = x - 3 * g, j = g & 3;
+                    if (i == 0 && j != 3) { x = 3 * (g >> 2) + j; --m; continue; }
+                    kb = j == 3 ? i : (i == 1 ? j : (j == 0 ? 2 : j - 1));
+                    x = g >> 2;                      // G
+                    break;
+                }
+                if (m > 0) {
+                    // v's six edges on level m: the halves 2e, 2e + 1 of its birth edge e, and the
+                    // interior edges kb, kb + 1 of G and kb2, kb2 + 1 of the triangle G2 across e;
+                    // on each later level the half at v keeps v as an endpoint, its id doubling
+                    // (plus one on the first split when v is not the edge owner's start).
+                    const int G = x, c0 = 3 * G + kb;
+                    const int eb = __ldg(a.cel[m - 1] + c0), t = __ldg(a.twl[m - 1] + c0);
+                    const int G2 = t / 3, kb2 = t - 3 * G2, I = 2 * a.El[m - 1];
+                    const int id[6] = {2 * eb, 2 * eb + 1, I + 3 * G + kb, I + 3 * G + (kb == 2 ? 0 : kb + 1),
+                                       I + 3 * G2 + kb2, I + 3 * G2 + (kb2 == 2 ? 0 : kb2 + 1)};
+                    const int h[6] = {1, 1, 0, 1, 0, 1};
+                    const int sh = a.l - 2 - m;          // levels after the first split
+                    float3 sp = f3(0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int u = 0; u < 6; u++) {
+                        const int e = m == a.l - 1 ? id[u] : ((2 * id[u] + h[u]) << sh);
+                        sp += ldpv(P, a.Vp + e, a.in4);
+                    }
+                    const float beta = c_loop_beta[6];
+                    stpv(a.Pn, vv[0], (1.0f - 6.0f * beta) * p[0] + beta * sp, a.out4);
                 } else {
-                    const float beta = c_loop_beta[n];
-                    stpv(a.Pn, vv[0], (1.0f - (float)n * beta) * p[0] + beta * sp, a.out4);
+                    const int x0 = 3 * R + k;
+                    int y = x0, n = 0;
+                    float3 sp = f3(0.f, 0.f, 0.f);
+                    do {
+                        sp += ldpv(P, a.Vp + __ldg(a.pce + y), a.in4);
+                        y = __ldg(a.ptw + tri_prev(y));
+                        n++;
+                    } while (y != x0 && n < kMaxValence);
+                    if (y != x0) {
+                        set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                    } else {
+                        const float beta = c_loop_beta[n];
+                        stpv(a.Pn, vv[0], (1.0f - (float)n * beta) * p[0] + beta * sp, a.out4);
+                    }
                 }
             }
         }
@@ -267,6 +303,12 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
         a.ptw = Pl.tw;
         a.Vp = (int)Pl.V;
     }
+    for (int m = 0; m < kMaxLevels; m++) {
+        const bool st = m <= T.levels && T.L[m].helpers;
+        a.cel[m] = st ? T.L[m].ce : nullptr;
+        a.twl[m] = st ? T.L[m].tw : nullptr;
+        a.El[m] = m <= T.levels ? (int)T.L[m].E : 0;
+    }
     a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
@@ -276,8 +318,12 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     return a;
 }
 
+// Resident 256-thread blocks per SM the Loop kernel is compiled for (register budget).
+#ifndef ALSUB_LOOP_MIN_BLOCKS
+#define ALSUB_LOOP_MIN_BLOCKS 6
+#endif
 template <bool TOPO, bool HELP, bool EVAL>
-__global__ void __launch_bounds__(kBlock) k_loop(TriArgs a) {
+__global__ void __launch_bounds__(kBlock, ALSUB_LOOP_MIN_BLOCKS) k_loop(TriArgs a) {
     loop_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 template <bool TOPO, bool HELP, bool EVAL>
