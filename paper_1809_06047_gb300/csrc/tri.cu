@@ -262,18 +262,48 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
             // ring); f_T (designated at the child of T's corner 0) neighbours T's three vertices
             // and the face points of T's three neighbours (valence 6).
             if (sqrt3_vown(a.l, c, a.z)) {
-                int y = r, n = 0;
-                float3 sp = f3(0.f, 0.f, 0.f);
-                do {
-                    sp += ldpv(P, a.Vp + y / 3, a.in4);
-                    y = __ldg(a.ptw + tri_prev(y));
-                    n++;
-                } while (y != r && n < kMaxValence);
-                if (y != r) {
-                    set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                // v_r = the vertex of parent corner r. Follow it up while it is corner 0 of a
+                // child: the designated corner ends at corner 2 of the child of corner 3T of some
+                // triangle T of level m - 1, i.e. v_r was born on level m >= 1 as T's face point
+                // (valence 6), or is a control-mesh vertex (m = 0: walk the parent ring).
+                int m = a.l - 1, x = r;
+                while (m > 0 && x % 3 == 0) { x /= 3; --m; }
+                if (m > 0 && x % 3 == 2) {
+                    // x = corner 2 of triangle g = x / 3 of level m, the child of corner g of
+                    // triangle T = g / 3 of level m - 1. On level m, f_T lies in the children 3T + j
+                    // of T's corners (corner 2) and in the children t = tw(3T + j) of the corners
+                    // across (corner 1); on every later level in their corner-0 descendants (index
+                    // x 3). Its neighbours on level l are the face points of these triangles on
+                    // level l - 1.
+                    const int T = x / 9;
+                    float3 sp = f3(0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int j = 0; j < 3; j++) {
+                        const int t = __ldg(a.twl[m - 1] + 3 * T + j);
+                        int X1 = 3 * T + j, X2 = t;                 // level m
+                        if (m < a.l - 1) {
+                            X1 = 3 * X1 + 2;                        // level m + 1
+                            X2 = 3 * t + 1;
+                            for (int q = m + 1; q < a.l - 1; q++) { X1 *= 3; X2 *= 3; }
+                        }
+                        sp += ldpv(P, a.Vp + X1, a.in4) + ldpv(P, a.Vp + X2, a.in4);
+                    }
+                    const float al = c_sqrt3_alpha[6];
+                    stpv(a.Pn, vv[0], (1.0f - al) * p[0] + (al / 6.0f) * sp, a.out4);
                 } else {
-                    const float al = c_sqrt3_alpha[n];
-                    stpv(a.Pn, vv[0], (1.0f - al) * p[0] + (al / (float)n) * sp, a.out4);
+                    int y = r, n = 0;
+                    float3 sp = f3(0.f, 0.f, 0.f);
+                    do {
+                        sp += ldpv(P, a.Vp + y / 3, a.in4);
+                        y = __ldg(a.ptw + tri_prev(y));
+                        n++;
+                    } while (y != r && n < kMaxValence);
+                    if (y != r) {
+                        set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                    } else {
+                        const float al = c_sqrt3_alpha[n];
+                        stpv(a.Pn, vv[0], (1.0f - al) * p[0] + (al / (float)n) * sp, a.out4);
+                    }
                 }
             }
             if (r % 3 == 0) {
@@ -318,7 +348,8 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     return a;
 }
 
-// Resident 256-thread blocks per SM the Loop kernel is compiled for (register budget).
+// Resident 256-thread blocks per SM the Loop and sqrt(3) kernels are compiled for (register budget:
+// 40 registers, measured faster than 5 blocks at 48 and than 8 blocks at 32 with spills).
 #ifndef ALSUB_LOOP_MIN_BLOCKS
 #define ALSUB_LOOP_MIN_BLOCKS 6
 #endif
@@ -327,7 +358,7 @@ __global__ void __launch_bounds__(kBlock, ALSUB_LOOP_MIN_BLOCKS) k_loop(TriArgs 
     loop_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 template <bool TOPO, bool HELP, bool EVAL>
-__global__ void __launch_bounds__(kBlock) k_sqrt3(TriArgs a) {
+__global__ void __launch_bounds__(kBlock, ALSUB_LOOP_MIN_BLOCKS) k_sqrt3(TriArgs a) {
     sqrt3_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
