@@ -222,7 +222,8 @@ def serving_leg(w, n_slots: int = 16, budget: float = 40e9, fastest: bool = Fals
         d.update(queue_wait_ms_mean=1e3 * float(np.mean(wait)), service_ms_mean=1e3 * float(np.mean(serve)),
                  register_s=register_s, hbm_peak_gb=st["hbm_peak"] / 1e9,
                  frames_operator=st["frames_operator"] - base["frames_operator"],
-                 frames_eval=st["frames_eval"] - base["frames_eval"], meshes=st["meshes"] - base["meshes"])
+                 frames_eval=st["frames_eval"] - base["frames_eval"], meshes=st["meshes"] - base["meshes"],
+                 host_start_ms_mean=st["host_start_ms_mean"], host_finish_ms_mean=st["host_finish_ms_mean"])
         return d
 
     out_served = served("operator")

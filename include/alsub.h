@@ -384,6 +384,9 @@ typedef struct {
     int64_t frames_operator;               /* frames served by the cached composite operator */
     int64_t frames_eval;                   /* frames served by eval kernels on a cached topology */
     int64_t meshes;                        /* MESH requests completed */
+    double host_start_ms_mean;             /* worker time to enqueue a request (validation,
+                                              allocation, launches), mean over completed ones */
+    double host_finish_ms_mean;            /* worker time to retire one (status, copies, frees) */
 } alsub_serve_stats;
 
 /* Start a server on the current device. max_slots 1..64 (concurrent requests), budget > 0.

@@ -33,7 +33,8 @@ class ServeStats(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("mean_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("throughput_rps", ctypes.c_double),
                 ("hbm_budget", ctypes.c_uint64), ("hbm_in_use", ctypes.c_uint64), ("hbm_peak", ctypes.c_uint64),
-                ("frames_operator", c_int64), ("frames_eval", c_int64), ("meshes", c_int64)]
+                ("frames_operator", c_int64), ("frames_eval", c_int64), ("meshes", c_int64),
+                ("host_start_ms_mean", ctypes.c_double), ("host_finish_ms_mean", ctypes.c_double)]
 
 
 # name -> argtypes; every function returns alsub_status (int32) unless listed in _RESTYPE

@@ -65,12 +65,20 @@ bool next_counts(alsub_scheme s, long long V, long long F, long long nnz, long l
     return true;
 }
 
+// Device arrays of a handle: sizes rounded to 256 bytes; carved from the handle's arena while it
+// has room (the arrays made at creation), else allocated one by one (arrays added later).
 template <class T>
 alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
     *p = nullptr;
     if (n == 0) n = 1;
-    T_.bytes += n * sizeof(T);
+    const size_t b = (n * sizeof(T) + 255) & ~(size_t)255;
+    T_.bytes += b;
     if (T_.dry) return ALSUB_OK;
+    if (T_.arena && T_.arena_off + b <= T_.arena_size) {
+        *p = (T *)(T_.arena + T_.arena_off);
+        T_.arena_off += b;
+        return ALSUB_OK;
+    }
     void *q = nullptr;
     cudaError_t e = cudaMallocAsync(&q, n * sizeof(T), s);
     if (e != cudaSuccess) {
@@ -92,6 +100,8 @@ void free_topo(TopoImpl &T) {
     for (void *p : T.allocs) cudaFreeAsync(p, T.stream);
     T.allocs.clear();
     T.bytes = 0;
+    T.arena = nullptr;
+    T.arena_off = T.arena_size = 0;
 }
 
 alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table, cudaStream_t s) {
@@ -117,7 +127,31 @@ alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table,
     return ALSUB_OK;
 }
 
+alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s);
+
+// Sizes every array of the handle in a dry pass, makes one allocation of that size, and lays the
+// arrays out in it (the same pass, for real).
 alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
+    if (T.dry) return topo_layout(T, M, levels, s);
+    TopoImpl D;
+    D.dry = true;
+    alsub_status st = topo_layout(D, M, levels, s);
+    if (st != ALSUB_OK) return st;
+    void *q = nullptr;
+    if (cudaMallocAsync(&q, D.bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ALSUB_ERR_OOM, "device allocation of %zu bytes failed", D.bytes);
+    }
+    T.allocs.push_back(q);
+    T.arena = (char *)q;
+    T.arena_size = D.bytes;
+    T.arena_off = 0;
+    st = topo_layout(T, M, levels, s);
+    T.arena_size = T.arena_off;                  // later arrays are allocated on their own
+    return st;
+}
+
+alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     T.mesh = &M;
     T.scheme = M.scheme;
     T.levels = levels;
@@ -250,11 +284,13 @@ void free_events(TopoImpl &T) {
 }
 
 using Body = void (*)(TopoImpl &, const float *, float *, void *, cudaStream_t);
+void ensure_side(TopoImpl &T);
 
 // Run one refine call through a CUDA graph: captured (on a private stream) when a call repeats
 // the previous call's pointers, replayed on `s` while they stay the same, so a repeated call costs
 // one graph launch instead of one launch per kernel and memset. One-off calls and graphs that
-// cannot be made launch the kernels directly.
+// cannot be made launch the kernels directly, on `s` alone (the parallel crease branch of a
+// subdivide call, with its stream and events, is made only for a graph).
 alsub_status run_call(TopoImpl &T, int kind, const float *P0, float *PL, void *scratch, cudaStream_t s,
                       Body body) {
     const bool timed = T.tcap > 0;
@@ -273,6 +309,7 @@ alsub_status run_call(TopoImpl &T, int kind, const float *P0, float *PL, void *s
         }
         G = lru;
         drop_graph(*G);
+        if (kind == 1) ensure_side(T);      // the crease branch, for the graph of a repeated call
         bool ok = T.cap || cudaStreamCreateWithFlags(&T.cap, cudaStreamNonBlocking) == cudaSuccess;
         const long long before = T.launches;
         cudaGraph_t g = nullptr;
@@ -775,7 +812,6 @@ alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, voi
                              void *stream) {
     if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     TopoImpl &T = h->t;
-    ensure_side(T);
     alsub_status st = run_call(T, 1, P0, PL, scratch, (cudaStream_t)stream, subdivide_body);
     if (T.tcap) T.tcalls++;
     if (st == ALSUB_OK) T.built = true;

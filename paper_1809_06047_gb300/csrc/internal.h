@@ -95,6 +95,8 @@ struct TopoImpl {
     std::vector<void *> allocs;  // everything above, freed on destroy
     size_t bytes = 0;            // device bytes in allocs
     bool dry = false;            // size the allocations without making them (alsub_plan_bytes)
+    char *arena = nullptr;       // the handle's arrays are carved from one allocation
+    size_t arena_off = 0, arena_size = 0;
     cudaStream_t stream = nullptr;
     bool built = false;
     // live timing (alsub_topology_set_timing) and launch count

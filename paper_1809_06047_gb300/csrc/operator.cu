@@ -377,6 +377,7 @@ struct alsub_operator_s {
     void *scan_tmp = nullptr;
     std::vector<std::pair<void *, size_t>> allocs;   // with their sizes in bytes
     size_t bytes = 0;
+    int sms = 152;                 // SMs of the device (SpMV grid)
     int *status = nullptr;
 };
 
@@ -500,11 +501,8 @@ void spmv(alsub_operator_s &O, const Csr &M, const float *x, float *y, cudaStrea
     const double mean = M.rows ? (double)M.nnz / (double)M.rows : 0.0;
     int S = mean > 96 ? 16 : (mean > 48 ? 8 : (mean > 24 ? 4 : (mean > 12 ? 2 : 1)));
     if (ALSUB_SPMV_LANES) S = ALSUB_SPMV_LANES;
-    int dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long want = (M.rows * S + 255) / 256;
-    const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>(want, 8LL * sms));
+    const unsigned g = (unsigned)std::max<long long>(1, std::min<long long>(want, 8LL * O.sms));
     if (S == 16) k_spmv<16><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
     else if (S == 8) k_spmv<8><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
     else if (S == 4) k_spmv<4><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
@@ -552,6 +550,11 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
     O->T = &T;
     O->stream = s;
     O->flags = flags;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&O->sms, cudaDevAttrMultiProcessorCount, dev);
+    }
     auto bail = [&](alsub_status e) { cudaStreamSynchronize(s); free_op(O); delete O; return e; };
     long long vmax = 1;
     for (int l = 0; l <= T.levels; l++) vmax = std::max(vmax, T.L[l].V);

@@ -69,6 +69,7 @@ struct Job {
     float *user_out = nullptr;       // caller's output buffer (or null)
     bool user_pinned = false;
     double t_submit = 0, t_start = 0, t_done = 0;
+    double host_start = 0, host_finish = 0;   // worker time spent enqueueing / retiring (s)
     alsub_status status = ALSUB_OK;
     bool done = false;
     bool by_operator = false;
@@ -119,6 +120,7 @@ struct alsub_server_s {
     cudaMemPool_t pool = nullptr;
     uint64_t old_threshold = 0;
     std::vector<double> lat;         // latencies of completed requests (s)
+    double host_start_sum = 0, host_finish_sum = 0;
     int64_t completed = 0, failed = 0, frames_op = 0, frames_eval = 0, meshes = 0;
     double first_submit = -1, last_done = 0;
 };
@@ -170,6 +172,7 @@ alsub_status start(Slot &sl, Job &j) {
 // Retire a slot whose work has completed (or failed to enqueue). Worker thread, lock not held.
 void finish(alsub_server_s &S, Slot &sl, alsub_status st) {
     Job &j = *sl.job;
+    const double h0 = now_s();
     if (st == ALSUB_OK && sl.topo) st = alsub_topology_status(sl.topo);  // latched device checks
     if (st == ALSUB_OK) {
         const size_t n_out = 3 * (size_t)j.VL;
@@ -184,6 +187,7 @@ void finish(alsub_server_s &S, Slot &sl, alsub_status st) {
     sl.mesh = nullptr;
     cudaGetLastError();
     const double t = now_s();
+    j.host_finish = t - h0;
     std::lock_guard<std::mutex> g(S.mu);
     j.status = st;
     j.t_done = t;
@@ -192,6 +196,8 @@ void finish(alsub_server_s &S, Slot &sl, alsub_status st) {
     S.running--;
     if (st == ALSUB_OK) {
         S.lat.push_back(t - j.t_submit);
+        S.host_start_sum += j.host_start;
+        S.host_finish_sum += j.host_finish;
         S.completed++;
         S.last_done = t;
         if (j.kind == ALSUB_REQ_MESH) S.meshes++;
@@ -261,6 +267,7 @@ void worker_loop(alsub_server_s *Sp, int first, int count) {
                 continue;
             }
             const alsub_status st = start(*free_slot, *j);
+            j->host_start = now_s() - j->t_start;
             if (st != ALSUB_OK) {
                 cudaStreamSynchronize(free_slot->stream);
                 finish(S, *free_slot, st);
@@ -597,6 +604,8 @@ alsub_status alsub_serve_stats_get(alsub_server_t S, alsub_serve_stats *st) {
     st->frames_operator = S->frames_op;
     st->frames_eval = S->frames_eval;
     st->meshes = S->meshes;
+    st->host_start_ms_mean = S->completed ? 1e3 * S->host_start_sum / (double)S->completed : 0;
+    st->host_finish_ms_mean = S->completed ? 1e3 * S->host_finish_sum / (double)S->completed : 0;
     return ALSUB_OK;
 }
 
