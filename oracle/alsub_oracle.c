@@ -26,6 +26,13 @@
  *                  is evaluated in FP32, in the fixed order t = 3*s; u = s_o + t; w = u * 0.25;
  *                  y = w - 1; max(y, 0) (compile with -ffp-contract=off).
  *                  sqrt(3) ignores sharpness (the paper gives it no crease treatment).
+ *   Boundaries     Catmull-Clark only (Sec. 3.1 "Boundaries", Eq. CC_boundary): an edge with one
+ *                  face is a boundary edge; its edge point is its midpoint, and a boundary vertex
+ *                  becomes 3/4 p + 1/8 (p_prev + p_next) with its two boundary neighbours. Every
+ *                  other point follows the closed-mesh rules. A vertex on more than two boundary
+ *                  edges (several fans) is non-manifold; a crease that touches a boundary vertex
+ *                  is refused (the paper defines no combination). Loop and sqrt(3) refuse open
+ *                  meshes (the paper gives them no boundary rule).
  * Edge numbering follows Sec. 3.2: edges are numbered in the order of the non-zeros of the upper
  * triangle of E, i.e. lexicographically by (min vertex, max vertex).
  * Child faces: face r with corners j = 0..c-1 is replaced by its children in corner order; the
@@ -73,12 +80,14 @@ typedef struct {
     int *eid;          /* edge id per corner (lexicographic numbering) */
     int E;
     int *ea, *eb;      /* edge endpoints, ea < eb */
-    int *eo;           /* a corner of each edge */
+    int *eo;           /* a corner of each edge (the boundary corner of a boundary edge) */
+    int B;             /* boundary corners (corners without a twin) */
+    int *bo;           /* per vertex: its outgoing boundary corner, or -1 for an interior vertex */
 } hedge;
 
 static void hedge_free(hedge *h) {
     free(h->cf); free(h->nx); free(h->pv); free(h->tw); free(h->vo); free(h->vb);
-    free(h->eid); free(h->ea); free(h->eb); free(h->eo);
+    free(h->eid); free(h->ea); free(h->eb); free(h->eo); free(h->bo);
     memset(h, 0, sizeof(*h));
 }
 
@@ -91,8 +100,9 @@ static int ekey_cmp(const void *x, const void *y) {
     return 0;
 }
 
-/* Build corners, twins and the lexicographic edge numbering. Closed 2-manifolds only. */
-static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv) {
+/* Build corners, twins and the lexicographic edge numbering. 2-manifolds, closed unless
+ * open != 0 (then a corner whose edge has no second face gets twin -1). */
+static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv, int open) {
     memset(h, 0, sizeof(*h));
     h->V = V; h->F = F; h->nnz = off[F]; h->off = off; h->fv = fv;
     int n = h->nnz;
@@ -100,7 +110,8 @@ static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv) {
     h->pv = malloc(sizeof(int) * (size_t)n); h->tw = malloc(sizeof(int) * (size_t)n);
     h->vo = calloc((size_t)V + 1, sizeof(int)); h->vb = malloc(sizeof(int) * (size_t)n);
     h->eid = malloc(sizeof(int) * (size_t)n);
-    if (!h->cf || !h->nx || !h->pv || !h->tw || !h->vo || !h->vb || !h->eid) return OR_ERR_OOM;
+    h->bo = malloc(sizeof(int) * (size_t)V);
+    if (!h->cf || !h->nx || !h->pv || !h->tw || !h->vo || !h->vb || !h->eid || !h->bo) return OR_ERR_OOM;
     for (int r = 0; r < F; r++) {
         int s = off[r], c = off[r + 1] - off[r];
         if (c < 3) return OR_ERR_ARG;
@@ -131,29 +142,48 @@ static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv) {
             int d = h->vb[q];
             if (fv[h->nx[d]] == a) { found = d; cnt++; }
         }
-        if (cnt == 0) return OR_ERR_BOUNDARY;
+        if (cnt == 0 && !open) return OR_ERR_BOUNDARY;
         if (cnt > 1) return OR_ERR_NONMANIFOLD;
-        h->tw[i] = found;
+        h->tw[i] = cnt ? found : -1;
         for (int q = h->vo[a]; q < h->vo[a + 1]; q++) {   /* duplicate directed edge */
             int d = h->vb[q];
             if (d != i && fv[h->nx[d]] == b) return OR_ERR_NONMANIFOLD;
         }
     }
-    /* every vertex: its outgoing corners form a single fan (one cycle under tw(pv(.))) */
+    /* every vertex: its outgoing corners form a single fan. Interior vertex: one cycle under
+     * x -> tw(pv(x)). Boundary vertex: exactly one outgoing boundary corner, where the chain under
+     * the same step starts (no corner steps onto it) and which reaches every corner before it
+     * ends at the incoming boundary edge. */
+    h->B = 0;
     for (int v = 0; v < V; v++) {
-        int start = h->vb[h->vo[v]], x = start, steps = 0, deg = h->vo[v + 1] - h->vo[v];
-        do { x = h->tw[h->pv[x]]; steps++; } while (x != start && steps <= deg);
+        int deg = h->vo[v + 1] - h->vo[v], nb = 0, start = h->vb[h->vo[v]];
+        for (int q = h->vo[v]; q < h->vo[v + 1]; q++)
+            if (h->tw[h->vb[q]] < 0) { nb++; start = h->vb[q]; }
+        h->bo[v] = nb ? start : -1;
+        h->B += nb;
+        if (nb > 1) return OR_ERR_NONMANIFOLD;
+        int x = start, steps = 0;
+        if (nb == 0) {
+            do { x = h->tw[h->pv[x]]; steps++; } while (x != start && steps <= deg);
+        } else {
+            steps = 1;
+            while (h->tw[h->pv[x]] >= 0 && steps <= deg) { x = h->tw[h->pv[x]]; steps++; }
+        }
         if (steps != deg) return OR_ERR_NONMANIFOLD;
     }
-    /* edges: one per corner pair; number them lexicographically by (min, max) */
-    if (n % 2) return OR_ERR_BOUNDARY;
-    int E = n / 2;
+    /* edges: one per corner pair (or boundary corner); number them lexicographically by
+     * (min, max) */
+    if ((n + h->B) % 2) return OR_ERR_NONMANIFOLD;
+    int E = (n + h->B) / 2;
     ekey *keys = malloc(sizeof(ekey) * (size_t)E);
     if (!keys) return OR_ERR_OOM;
     int k = 0;
     for (int i = 0; i < n; i++) {
         int a = fv[i], b = fv[h->nx[i]];
-        if (a < b) { keys[k].a = a; keys[k].b = b; keys[k].c = i; k++; }
+        if (h->tw[i] < 0 || a < b) {
+            if (k == E) { free(keys); return OR_ERR_NONMANIFOLD; }
+            keys[k].a = a < b ? a : b; keys[k].b = a < b ? b : a; keys[k].c = i; k++;
+        }
     }
     if (k != E) { free(keys); return OR_ERR_NONMANIFOLD; }
     qsort(keys, (size_t)E, sizeof(ekey), ekey_cmp);
@@ -164,18 +194,21 @@ static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv) {
     for (int e = 0; e < E; e++) {
         h->ea[e] = keys[e].a; h->eb[e] = keys[e].b; h->eo[e] = keys[e].c;
         h->eid[keys[e].c] = e;
-        h->eid[h->tw[keys[e].c]] = e;
+        if (h->tw[keys[e].c] >= 0) h->eid[h->tw[keys[e].c]] = e;
     }
     free(keys);
     return OR_OK;
 }
 
-/* edge id of (a, b) or -1 */
+/* edge id of the undirected edge {a, b} or -1 (a boundary edge holds only one direction) */
 static int hedge_find_edge(const hedge *h, int a, int b) {
     if (a < 0 || b < 0 || a >= h->V || b >= h->V) return -1;
-    for (int q = h->vo[a]; q < h->vo[a + 1]; q++) {
-        int d = h->vb[q];
-        if (h->fv[h->nx[d]] == b) return h->eid[d];
+    for (int t = 0; t < 2; t++) {
+        int u = t ? b : a, w = t ? a : b;
+        for (int q = h->vo[u]; q < h->vo[u + 1]; q++) {
+            int d = h->vb[q];
+            if (h->fv[h->nx[d]] == w) return h->eid[d];
+        }
     }
     return -1;
 }
@@ -208,6 +241,7 @@ static int creases_build(creases *c, const hedge *h, int K, const int *cv, const
         if (!(s >= 0.0f)) return OR_ERR_CREASE;        /* negative or NaN */
         int e = hedge_find_edge(h, cv[2 * i], cv[2 * i + 1]);
         if (e < 0) return OR_ERR_CREASE;
+        if (h->bo[cv[2 * i]] >= 0 || h->bo[cv[2 * i + 1]] >= 0) return OR_ERR_BOUNDARY;
         if (c->es[e] != 0.0f) return OR_ERR_CREASE;    /* tagged twice */
         c->es[e] = s;
     }
@@ -356,6 +390,18 @@ static void push_crease(onext *o, int a, int b, float s) {
     if (s > 0.0f) { o->cv[2 * o->K] = a; o->cv[2 * o->K + 1] = b; o->cs[o->K] = s; o->K++; }
 }
 
+/* The two boundary neighbours of v: the end of its outgoing boundary edge (nb) and the start of
+ * its incoming one (pb), found by walking the fan from the outgoing boundary corner to the corner
+ * after which it ends. Returns 0 for an interior vertex. */
+static int boundary_neighbours(const hedge *h, int v, int *nb, int *pb) {
+    int x = h->bo[v];
+    if (x < 0) return 0;
+    *nb = h->fv[h->nx[x]];
+    while (h->tw[h->pv[x]] >= 0) x = h->tw[h->pv[x]];
+    *pb = h->fv[h->pv[x]];
+    return 1;
+}
+
 /* Catmull-Clark, Sec. 3.1 classical rules. */
 static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o, coo *R) {
     int V = h->V, F = h->F, E = h->E, n = h->nnz;
@@ -376,7 +422,12 @@ static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o
     /* 2. edge point: (p_k + p_l + f_r + f_s) / 4 (Eq. 2), then the crease rule */
     for (int e = 0; e < E; e++) {
         int c0 = h->eo[e], c1 = h->tw[c0];
-        int a = h->ea[e], b = h->eb[e], r = h->cf[c0], s = h->cf[c1];
+        int a = h->ea[e], b = h->eb[e], r = h->cf[c0];
+        if (c1 < 0) {                              /* boundary edge: its midpoint */
+            for (int d = 0; d < 3; d++) ep[3 * e + d] = 0.5 * (P[3 * a + d] + P[3 * b + d]);
+            continue;
+        }
+        int s = h->cf[c1];
         for (int d = 0; d < 3; d++)
             ep[3 * e + d] = 0.25 * (P[3 * a + d] + P[3 * b + d] + fp[3 * r + d] + fp[3 * s + d]);
         if (cr) crease_edge((double)cr->es[e], P + 3 * a, P + 3 * b, ep + 3 * e);
@@ -384,6 +435,12 @@ static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o
     /* 3. vertex update (Eq. pos_update):
      *    S(p) = 1/n ((n-3) p + 1/n sum f_j + 2/n sum (p + p_j)/2), then the crease rule */
     for (int v = 0; v < V; v++) {
+        int nb, pb;
+        if (boundary_neighbours(h, v, &nb, &pb)) {  /* Eq. CC_boundary */
+            for (int d = 0; d < 3; d++)
+                Pn[3 * v + d] = 0.75 * P[3 * v + d] + 0.125 * (P[3 * pb + d] + P[3 * nb + d]);
+            continue;
+        }
         int nv = h->vo[v + 1] - h->vo[v];
         double sf[3] = {0, 0, 0}, sm[3] = {0, 0, 0};
         for (int q = h->vo[v]; q < h->vo[v + 1]; q++) {
@@ -421,6 +478,14 @@ static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o
     if (R) {
         row rw = {0, 0, NULL, NULL};
         for (int v = 0; v < V && !st; v++) {
+            int nb, pb;
+            if (boundary_neighbours(h, v, &nb, &pb)) {
+                st = row_add(&rw, v, 0.75);
+                if (!st) st = row_add(&rw, pb, 0.125);
+                if (!st) st = row_add(&rw, nb, 0.125);
+                if (!st) st = coo_push_row(R, v, &rw);
+                continue;
+            }
             int nv = h->vo[v + 1] - h->vo[v];
             double inv2 = 1.0 / ((double)nv * nv);
             st = row_add(&rw, v, (nv - 3.0) / nv + 1.0 / nv);        /* (n-3)/n p + (n/n^2) p */
@@ -440,6 +505,12 @@ static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o
         }
         for (int e = 0; e < E && !st; e++) {
             int c0 = h->eo[e], c1 = h->tw[c0];
+            if (c1 < 0) {
+                st = row_add(&rw, h->ea[e], 0.5);
+                if (!st) st = row_add(&rw, h->eb[e], 0.5);
+                if (!st) st = coo_push_row(R, V + F + e, &rw);
+                continue;
+            }
             int fs[2] = {h->cf[c0], h->cf[c1]};
             st = row_add(&rw, h->ea[e], 0.25);
             if (!st) st = row_add(&rw, h->eb[e], 0.25);
@@ -641,7 +712,7 @@ int or_run(int scheme, int levels, int keep_all, int want_operator,
     for (int l = 0; l <= levels && !st; l++) {
         olevel *L = &res->L[last];
         hedge h;
-        st = hedge_build(&h, L->V, L->F, L->off, L->fv);
+        st = hedge_build(&h, L->V, L->F, L->off, L->fv, scheme == OR_CC);
         if (st) { hedge_free(&h); break; }
         L->E = h.E;
         creases cr;

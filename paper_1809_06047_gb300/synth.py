@@ -14,6 +14,8 @@ mesh_info_CC, mesh_info_L, mesh_info_S), which are not available:
   triangle pairs (valences 3..6) and a share of edges tagged with FP32 crease sharpness.
 * ``torus_tri``       -- triangulated torus with a share of edges flipped (valences 4..8) and a
   share of edges infinitely sharp.
+* ``tube_cc``, ``sheet_cc``, ``holed_cc_mixed`` -- open Catmull-Clark meshes (boundary loops,
+  valence-2 corners, holes cut into the mixed torus) for the boundary rules.
 
 A mesh is a dict with ``V``, ``F``, ``off`` (int32[F+1]), ``fv`` (int32[nnz], faces in CCW cyclic
 order), ``P`` (float32[V,3]), ``crease_verts`` (int32[K,2]) and ``crease_sharp`` (float32[K]).
@@ -369,6 +371,71 @@ def prism(n: int = 12, h: float = 0.7) -> dict:
              [n + i for i in range(n - 1, -1, -1)]]               # bottom, CCW seen from -z
     faces += [[n + i, n + (i + 1) % n, (i + 1) % n, i] for i in range(n)]
     return _pack(faces, P, np.zeros((0, 2)), np.zeros(0))
+
+
+def tube_cc(N: int = 16, M: int = 9, jitter: float = 0.05, z_step: float = 0.25,
+            seed: int = SEED_BASE + 6) -> dict:
+    """Open quad cylinder: N vertices around, M vertex rows, M - 1 rows of quads, two boundary
+    loops (rows 0 and M - 1). Vertex (i, j) -> index j*N + i at angle 2 pi i / N; the radius is
+    jittered by U(-jitter, jitter) per vertex, z = j * z_step exactly (a power of two keeps z
+    exact in FP32). Face (i, j) = [(i,j), (i+1,j), (i+1,j+1), (i,j+1)], face index j*N + i."""
+    rng = SplitMix64(seed)
+    i = np.tile(np.arange(N, dtype=np.float64), M)
+    j = np.repeat(np.arange(M, dtype=np.float64), N)
+    u = 2.0 * math.pi * i / N
+    rad = 1.0 + (rng.uniform(N * M) * 2.0 - 1.0) * jitter
+    P = np.stack([rad * np.cos(u), rad * np.sin(u), j * z_step], axis=1).astype(np.float32)
+    faces = [[jj * N + ii, jj * N + (ii + 1) % N, (jj + 1) * N + (ii + 1) % N, (jj + 1) * N + ii]
+             for jj in range(M - 1) for ii in range(N)]
+    return _pack(faces, P, np.zeros((0, 2)), np.zeros(0))
+
+
+def sheet_cc(NX: int = 12, NY: int = 9, split_frac: float = 0.1, jitter: float = 0.02,
+             seed: int = SEED_BASE + 7) -> dict:
+    """Open planar NX x NY grid of quads (one boundary loop with four valence-2 corners), a share
+    of quads split into triangle pairs, xy jittered and z a seeded bump. Vertex (i, j) -> j*(NX+1)+i."""
+    rng = SplitMix64(seed)
+    W = NX + 1
+    faces = []
+    split = rng.uniform(NX * NY)
+    for jj in range(NY):
+        for ii in range(NX):
+            q = [jj * W + ii, jj * W + ii + 1, (jj + 1) * W + ii + 1, (jj + 1) * W + ii]
+            if split[jj * NX + ii] < split_frac:
+                faces += [[q[0], q[1], q[2]], [q[0], q[2], q[3]]]
+            else:
+                faces.append(q)
+    x = np.tile(np.arange(W, dtype=np.float64), NY + 1) / NX
+    y = np.repeat(np.arange(NY + 1, dtype=np.float64), W) / NY
+    d = (rng.uniform(2 * W * (NY + 1)).reshape(-1, 2) * 2.0 - 1.0) * jitter
+    z = 0.2 * np.sin(3.0 * x) * np.cos(2.0 * y)
+    P = np.stack([x + d[:, 0], y + d[:, 1], z], axis=1).astype(np.float32)
+    return _pack(faces, P, np.zeros((0, 2)), np.zeros(0))
+
+
+def holed_cc_mixed(N: int = 32, M: int = 24, holes: int = 6, seed: int = SEED_BASE + 8,
+                   creases: bool = True) -> dict:
+    """``torus_cc_mixed`` with ``holes`` faces cut out (each hole one boundary loop). The removed
+    faces are drawn from a seeded permutation, skipping any face that shares a vertex with a face
+    already removed (so every vertex keeps a single fan); creases touching a hole are dropped."""
+    m = torus_cc_mixed(N, M, seed=seed, creases=creases)
+    off, fv = m["off"], m["fv"]
+    rng = SplitMix64(seed ^ 0x5EED)
+    used = np.zeros(m["V"], dtype=bool)
+    gone = []
+    for f in rng.permutation(m["F"]):
+        if len(gone) >= holes:
+            break
+        vs = fv[off[f]:off[f + 1]]
+        if used[vs].any():
+            continue
+        used[vs] = True
+        gone.append(int(f))
+    gone_set = set(gone)
+    faces = [list(fv[off[f]:off[f + 1]]) for f in range(m["F"]) if f not in gone_set]
+    cv, cs = m["crease_verts"], m["crease_sharp"]
+    keep = ~(used[cv[:, 0]] | used[cv[:, 1]]) if len(cs) else np.zeros(0, dtype=bool)
+    return _pack(faces, m["P"], cv[keep], cs[keep])
 
 
 def serving_requests(n_requests: int = 512, rate_hz: float = 2000.0, n_resident: int = 32,

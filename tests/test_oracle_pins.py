@@ -72,6 +72,9 @@ def _meshes():
         ("cc", synth.pillow(6)),
         ("cc", synth.prism(12)),
         ("cc", synth.torus_cc_mixed(12, 12, seed=11)),
+        ("cc", synth.tube_cc(8, 5)),
+        ("cc", synth.sheet_cc(5, 4)),
+        ("cc", synth.holed_cc_mixed(12, 12, holes=3, seed=14)),
         ("loop", synth.octahedron()),
         ("loop", synth.torus_tri(10, 10, seed=12)),
         ("sqrt3", synth.tetrahedron()),
@@ -321,6 +324,7 @@ def test_corners_fixed():
 @pytest.mark.parametrize("scheme,mesh", [
     ("cc", synth.torus_cc_mixed(6, 6, seed=21)),
     ("cc", synth.pillow(5)),
+    ("cc", synth.sheet_cc(3, 3, seed=24)),
     ("loop", synth.torus_tri(5, 5, seed=22)),
     ("sqrt3", synth.torus_tri(5, 5, seed=23, creases=False)),
 ])
@@ -345,10 +349,26 @@ def test_brute_force_operator(scheme, mesh):
 
 def test_rejects_invalid_meshes():
     m = synth.cube()
-    open_mesh = dict(m, F=5, off=m["off"][:6], fv=m["fv"][:20])
+    o = synth.octahedron()
+    open_tri = dict(o, F=7, off=o["off"][:8], fv=o["fv"][:21])
+    for scheme in ("loop", "sqrt3"):              # no boundary rule for the triangle schemes
+        with pytest.raises(oracle.OracleError) as ei:
+            oracle.subdivide(open_tri, 1, scheme)
+        assert ei.value.code == 3
+    # two squares sharing only vertex 0: two fans at one vertex
+    bow = dict(V=7, F=2, off=np.array([0, 4, 8], np.int32),
+               fv=np.array([0, 1, 2, 3, 0, 4, 5, 6], np.int32), P=np.zeros((7, 3), np.float32),
+               crease_verts=np.zeros((0, 2), np.int32), crease_sharp=np.zeros(0, np.float32))
     with pytest.raises(oracle.OracleError) as ei:
-        oracle.subdivide(open_mesh, 1, "cc")
-    assert ei.value.code in (1, 3)
+        oracle.subdivide(bow, 1, "cc")
+    assert ei.value.code == 2
+    # a crease touching a boundary vertex (open box: vertices of the missing face)
+    box = dict(m, F=5, off=m["off"][:6], fv=m["fv"][:20])
+    f5 = m["fv"][20:24]
+    cre = dict(box, crease_verts=np.array([[f5[0], f5[1]]], np.int32), crease_sharp=np.array([2.0], np.float32))
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.subdivide(cre, 1, "cc")
+    assert ei.value.code == 3
     dup = dict(m, F=7, off=np.append(m["off"], 28).astype(np.int32),
                fv=np.concatenate([m["fv"], m["fv"][:4]]))
     with pytest.raises(oracle.OracleError) as ei:
@@ -369,3 +389,120 @@ def test_loop_beta_sqrt3_alpha_values():
     rows = _rows(out[0])
     assert max(rows[0].values()) == pytest.approx(1 - 6 * beta(6), abs=1e-15)
     assert beta(6) == pytest.approx(1 / 16, abs=1e-15)
+
+
+# ---------------------------------------------------------------- boundaries (Catmull-Clark)
+
+def _boundary_loops(level):
+    """Directed boundary edges a -> b (no face holds b -> a), chained into closed loops."""
+    off, fv = level["off"], level["fv"]
+    directed = set()
+    for r in range(level["F"]):
+        f = fv[off[r]:off[r + 1]]
+        for j in range(len(f)):
+            directed.add((int(f[j]), int(f[(j + 1) % len(f)])))
+    nxt = {a: b for a, b in directed if (b, a) not in directed}
+    loops, seen = [], set()
+    for a0 in sorted(nxt):
+        if a0 in seen:
+            continue
+        loop, a = [], a0
+        while a not in seen:
+            seen.add(a)
+            loop.append(a)
+            a = nxt[a]
+        loops.append(loop)
+    return loops
+
+
+def _cox_de_boor(t, i, k):
+    """Uniform B-spline basis N_{i,k}(t) on the integer knots, order k (degree k - 1)."""
+    if k == 1:
+        return ((t >= i) & (t < i + 1)).astype(np.float64)
+    return ((t - i) / (k - 1)) * _cox_de_boor(t, i, k - 1) + ((i + k - t) / (k - 1)) * _cox_de_boor(t, i + 1, k - 1)
+
+
+def _cubic_two_scale_mask():
+    """The coefficients c_k of N(t) = sum_k c_k N(2t - k) for the uniform cubic B-spline N,
+    found by least squares on samples of the Cox-de Boor basis (not typed in)."""
+    t = np.linspace(0.0, 4.0, 801)[:-1]
+    A = np.stack([_cox_de_boor(2 * t - k, 0, 4) for k in range(5)], axis=1)
+    c, *_ = np.linalg.lstsq(A, _cox_de_boor(t, 0, 4), rcond=None)
+    return c
+
+
+def _refine_closed_polygon(P, c):
+    """Control polygon of the same closed cubic B-spline on the halved knot spacing:
+    Q_m = sum_j c_{m - 2j} P_j (indices cyclic)."""
+    n = len(P)
+    Q = np.zeros((2 * n, 3))
+    for m in range(2 * n):
+        for j in range(n):
+            k = (m - 2 * j) % (2 * n)
+            if k < len(c):
+                Q[m] += c[k] * P[j]
+    return Q
+
+
+@pytest.mark.parametrize("mesh", [synth.tube_cc(10, 6, jitter=0.2, seed=31), synth.sheet_cc(6, 5, seed=32),
+                                  synth.holed_cc_mixed(16, 14, holes=3, seed=33)],
+                         ids=["tube", "sheet", "holes"])
+def test_boundary_is_cubic_bspline_curve(mesh):
+    """Every boundary loop of the refined mesh is the control polygon of the cubic B-spline curve
+    of the level-0 boundary loop, refined l times (Eq. CC_boundary with midpoint edge points;
+    the mask comes from the Cox-de Boor basis), whatever the surface inside it."""
+    c = _cubic_two_scale_mask()
+    np.testing.assert_allclose(c * 8.0, [1, 4, 6, 4, 1], atol=1e-9)   # sanity of the derivation
+    levels = 3
+    out = oracle.subdivide(mesh, levels, "cc")
+    loops0 = _boundary_loops(out[0])
+    assert len(loops0) >= 1
+    expected = []
+    for loop in loops0:
+        poly = out[0]["P"][loop].astype(np.float64)
+        expected.append(poly)
+    for l in range(1, levels + 1):
+        expected = [_refine_closed_polygon(poly, c) for poly in expected]
+        loops = _boundary_loops(out[l])
+        assert sorted(len(x) for x in loops) == sorted(len(x) for x in expected)
+        got = np.concatenate([out[l]["P"][x] for x in loops])
+        np.testing.assert_allclose(_as_sorted(got), _as_sorted(np.concatenate(expected)), atol=1e-9)
+
+
+def test_boundary_tube_height_is_linear():
+    """Heights linear in the row index are reproduced exactly by every rule at every level
+    (face, edge and vertex points are affine combinations symmetric across the rows, and the
+    boundary rules act along rows), so the refined tube has n 2^l vertices on each of the
+    (M - 1) 2^l + 1 dyadic heights -- a boundary vertex taking the smooth half-ring rule
+    would leave its row."""
+    N, M, levels, h = 9, 6, 3, 0.25
+    out = oracle.subdivide(synth.tube_cc(N, M, jitter=0.3, z_step=h, seed=34), levels, "cc")
+    for l in range(1, levels + 1):
+        z = out[l]["P"][:, 2] / (h / 2 ** l)
+        k = np.round(z)
+        np.testing.assert_array_equal(z, k)
+        counts = np.bincount(k.astype(np.int64))
+        assert len(counts) == (M - 1) * 2 ** l + 1
+        assert np.all(counts == N * 2 ** l)
+
+
+def test_boundary_leaves_far_interior_unchanged():
+    """Cutting a ring of faces out of a closed torus changes nothing at the level-l vertices of
+    faces at least three rings away from the cut: the boundary rules only reach about two
+    level-0 rings inwards over any number of levels (the stencils halve in size every level)."""
+    N, M, levels = 12, 8, 3
+    closed = synth.torus_cc_plain(N, M, jitter=0.05, seed=35)
+    F = closed["F"] - M                              # faces i = N - 1 are the last M
+    cut = dict(closed, F=F, off=closed["off"][:F + 1], fv=closed["fv"][:4 * F])
+    a = oracle.subdivide(closed, levels, "cc")[levels]
+    b = oracle.subdivide(cut, levels, "cc")[levels]
+    q = 4 ** levels
+    for i in range(3, N - 4):                       # face columns 3 .. N-5 touch vertex columns <= N-4
+        for j in range(M):
+            r = i * M + j
+            ca = a["fv"][4 * q * r:4 * q * (r + 1)]
+            cb = b["fv"][4 * q * r:4 * q * (r + 1)]
+            np.testing.assert_array_equal(a["P"][ca], b["P"][cb])
+    # and the cut does change the faces next to it
+    r = 0
+    assert not np.array_equal(a["P"][a["fv"][:4 * q]], b["P"][b["fv"][:4 * q]])
