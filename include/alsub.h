@@ -88,10 +88,21 @@ alsub_status alsub_copy(void *dst, const void *src, size_t bytes, void *stream);
  * E' = 3F'/2); a closed mesh has E = nnz / 2.
  *   counts_host: int64[4 * (levels + 1)], filled with (V, F, nnz, E) per level.
  * Errors: INVALID_ARG for negative or inconsistent inputs, UNSUPPORTED when a count would exceed
- * int32 or nnz is odd (an open mesh).
+ * int32 or nnz is odd (an open mesh: see alsub_plan_open).
  */
 alsub_status alsub_plan(alsub_scheme scheme, int64_t num_verts, int64_t num_faces, int64_t nnz,
                         int32_t levels, int64_t *counts_host);
+
+/*
+ * alsub_plan for a Catmull-Clark mesh with `boundary_edges` edges of one face (Sec. 3.1 and 3.2
+ * "Boundaries"): E = (nnz + boundary_edges) / 2 on level 0, the same recurrences after it (each
+ * boundary edge splits into two boundary edges). boundary_edges = 0 is alsub_plan.
+ * Errors: those of alsub_plan; INVALID_ARG when nnz + boundary_edges is odd or boundary_edges is
+ * negative or above nnz; UNSUPPORTED for boundary_edges > 0 with Loop or sqrt(3) (the paper
+ * gives them no boundary rule).
+ */
+alsub_status alsub_plan_open(alsub_scheme scheme, int64_t num_verts, int64_t num_faces, int64_t nnz,
+                             int64_t boundary_edges, int32_t levels, int64_t *counts_host);
 
 /*
  * Create a control mesh: the reduced mesh matrix M of Sec. 4.1 as a face table, plus the crease
@@ -107,7 +118,16 @@ alsub_status alsub_plan(alsub_scheme scheme, int64_t num_verts, int64_t num_face
  * repeated vertex in a face, every vertex used, sigma not NaN or negative) and copies everything
  * to the device on `stream`; the caller may free its arrays on return. Adjacency is checked on
  * the device when a topology is built.
- * Errors: INVALID_ARG, UNSUPPORTED (counts beyond int32, odd nnz), OOM, DEVICE.
+ * Catmull-Clark meshes may be open (Sec. 3.1 and 3.2 "Boundaries"): an edge of one face is a
+ * boundary edge, refined by the midpoint rule, and a vertex on boundary edges by Eq. CC_boundary
+ * (3/4 p + 1/8 of its two boundary neighbours). The create call counts the boundary edges on the
+ * device (it synchronises `stream`); alsub_mesh_boundary_edges reports the count, which sizes the
+ * levels (alsub_plan_open). A vertex must lie on at most two boundary edges (one fan; checked when
+ * the topology is built), and no crease may touch a boundary vertex (the paper defines no such
+ * combination: UNSUPPORTED). Loop and sqrt(3) meshes must be closed.
+ * Errors: INVALID_ARG, NONMANIFOLD (a repeated directed edge found by the boundary count),
+ * UNSUPPORTED (counts beyond int32, odd nnz for Loop / sqrt(3), a crease at the boundary), OOM,
+ * DEVICE.
  */
 alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t num_verts, int32_t num_faces,
                                const int32_t *face_offsets_host, const int32_t *face_verts_host,
@@ -116,6 +136,10 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t num_verts, int32_t n
                                alsub_mesh_t *out);
 
 alsub_status alsub_mesh_destroy(alsub_mesh_t mesh);
+
+/* Number of boundary edges (edges of one face) of a mesh; 0 for a closed mesh and for Loop and
+ * sqrt(3) meshes (those must be closed). Host only. Errors: INVALID_ARG. */
+alsub_status alsub_mesh_boundary_edges(alsub_mesh_t mesh, int64_t *boundary_edges);
 
 /*
  * Build the topology of `levels` uniform refinement steps (the build step of Fig. module_core,
@@ -246,6 +270,7 @@ alsub_status alsub_operator_destroy(alsub_operator_t op);
  * (float[3 V_L]) exactly as alsub_refine_vertices(topos[i], ...) would, using that topology's own
  * scratch, so a topology may appear only once and must not be refined elsewhere while the batch
  * runs. The buffers are bound at creation: to refine new positions, write them into P0_dev[i].
+ * Members must be closed meshes (UNSUPPORTED otherwise: the batch has no boundary repair step).
  */
 typedef struct alsub_batch_s *alsub_batch_t;
 
@@ -312,12 +337,14 @@ alsub_status alsub_refine_vertices_static(alsub_topology_t topo, const float *P0
 
 /*
  * Device bytes that alsub_topology_create(levels) allocates for a mesh of these sizes (host only,
- * no GPU needed; the same closed-form sizes the create call uses). sigma_max is the largest
- * crease sharpness (+inf allowed; it bounds how many levels keep crease lists). The mesh itself
- * holds 4 (F + 1) + 4 nnz + 12 K bytes more. Errors: those of alsub_plan.
+ * no GPU needed; the same closed-form sizes the create call uses). boundary_edges as in
+ * alsub_plan_open (0 for a closed mesh). sigma_max is the largest crease sharpness (+inf
+ * allowed; it bounds how many levels keep crease lists). The mesh itself holds 4 (F + 1) +
+ * 4 nnz + 12 K bytes more. Errors: those of alsub_plan_open.
  */
 alsub_status alsub_plan_bytes(alsub_scheme scheme, int32_t num_verts, int32_t num_faces, int32_t nnz,
-                              int32_t num_creases, float sigma_max, int32_t levels, size_t *bytes);
+                              int32_t boundary_edges, int32_t num_creases, float sigma_max, int32_t levels,
+                              size_t *bytes);
 
 /* Device bytes a handle holds now (grows when alsub_build_operator stores the per-corner arrays
  * of a level that did not keep them). */
@@ -358,6 +385,10 @@ typedef struct {
     const int32_t *face_offsets_host;      /* MESH: as alsub_mesh_create (may be NULL) */
     const int32_t *face_verts_host;        /* MESH */
     int32_t num_creases;                   /* MESH */
+    int32_t num_boundary_edges;            /* MESH: edges of one face (alsub_mesh_boundary_edges;
+                                              0 for a closed mesh). It sizes V_L as
+                                              alsub_plan_open does; a mesh with another count
+                                              fails with INVALID_ARG. */
     const int32_t *crease_verts_host;      /* MESH */
     const float *crease_sharpness_host;    /* MESH */
     const float *P0_host;                  /* float[3 V_0]; copied by the submit call */

@@ -17,7 +17,8 @@ class Request(ctypes.Structure):
     """alsub_request."""
     _fields_ = [("kind", c_int32), ("resident", c_int32), ("scheme", c_int32), ("levels", c_int32),
                 ("num_verts", c_int32), ("num_faces", c_int32), ("face_offsets_host", c_void_p),
-                ("face_verts_host", c_void_p), ("num_creases", c_int32), ("crease_verts_host", c_void_p),
+                ("face_verts_host", c_void_p), ("num_creases", c_int32), ("num_boundary_edges", c_int32),
+                ("crease_verts_host", c_void_p),
                 ("crease_sharpness_host", c_void_p), ("P0_host", c_void_p), ("PL_host", c_void_p)]
 
 
@@ -43,6 +44,8 @@ SIGNATURES = {
     "alsub_status_string": [c_int32],
     "alsub_copy": [c_void_p, c_void_p, c_size_t, c_void_p],
     "alsub_plan": [c_int32, c_int64, c_int64, c_int64, c_int32, P(c_int64)],
+    "alsub_plan_open": [c_int32, c_int64, c_int64, c_int64, c_int64, c_int32, P(c_int64)],
+    "alsub_mesh_boundary_edges": [c_void_p, P(c_int64)],
     "alsub_mesh_create": [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                           c_void_p, P(H)],
     "alsub_mesh_destroy": [H],
@@ -71,7 +74,8 @@ SIGNATURES = {
     "alsub_batch_tune": [H, c_void_p, P(c_int32), P(c_int32), P(ctypes.c_float)],
     "alsub_batch_launches": [H, P(c_int64)],
     "alsub_batch_destroy": [H],
-    "alsub_plan_bytes": [c_int32, c_int32, c_int32, c_int32, c_int32, ctypes.c_float, c_int32, P(c_size_t)],
+    "alsub_plan_bytes": [c_int32, c_int32, c_int32, c_int32, c_int32, c_int32, ctypes.c_float, c_int32,
+                         P(c_size_t)],
     "alsub_topology_bytes": [H, P(c_size_t)],
     "alsub_operator_bytes": [H, P(c_size_t)],
     "alsub_serve_create": [c_size_t, c_int32, P(H)],

@@ -41,20 +41,24 @@ def _ptr(a: np.ndarray | None):
     return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
 
 
-def plan(scheme: str, V: int, F: int, nnz: int, levels: int) -> np.ndarray:
-    """Closed-form (V, F, nnz, E) per level (host only)."""
+def plan(scheme: str, V: int, F: int, nnz: int, levels: int, boundary: int = 0) -> np.ndarray:
+    """Closed-form (V, F, nnz, E) per level (host only); ``boundary`` = boundary edges of an open
+    Catmull-Clark mesh (alsub_plan_open)."""
     out = np.zeros(4 * (levels + 1), dtype=np.int64)
-    _check(lib().alsub_plan(SCHEMES[scheme], V, F, nnz, levels,
-                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+    p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+    if boundary:
+        _check(lib().alsub_plan_open(SCHEMES[scheme], V, F, nnz, boundary, levels, p))
+    else:
+        _check(lib().alsub_plan(SCHEMES[scheme], V, F, nnz, levels, p))
     return out.reshape(levels + 1, 4)
 
 
 def plan_bytes(scheme: str, V: int, F: int, nnz: int, levels: int, creases: int = 0,
-               sigma_max: float = 0.0) -> int:
+               sigma_max: float = 0.0, boundary: int = 0) -> int:
     """alsub_plan_bytes: device bytes alsub_topology_create allocates (host only)."""
     b = ctypes.c_size_t()
-    _check(lib().alsub_plan_bytes(SCHEMES[scheme], V, F, nnz, creases, ctypes.c_float(sigma_max), levels,
-                                  ctypes.byref(b)))
+    _check(lib().alsub_plan_bytes(SCHEMES[scheme], V, F, nnz, boundary, creases, ctypes.c_float(sigma_max),
+                                  levels, ctypes.byref(b)))
     return b.value
 
 
@@ -84,6 +88,9 @@ class Mesh:
                                        int(cs.size), _ptr(cv) if cs.size else None,
                                        _ptr(cs) if cs.size else None,
                                        ctypes.c_void_p(_stream(stream)), ctypes.byref(self._h)))
+        b = ctypes.c_int64()
+        _check(lib().alsub_mesh_boundary_edges(self._h, ctypes.byref(b)))
+        self.boundary_edges = int(b.value)
 
     @classmethod
     def from_dict(cls, m: dict, scheme: str | None = None, stream=None) -> "Mesh":
@@ -385,13 +392,14 @@ class Server:
         return self._submit(r, (P0, out))
 
     def submit_mesh(self, m: dict, scheme: str, levels: int, P0: np.ndarray | None = None,
-                    out: np.ndarray | None = None) -> int:
+                    out: np.ndarray | None = None, boundary_edges: int = 0) -> int:
+        """A one-off mesh; ``boundary_edges`` as Mesh.boundary_edges (0 for a closed mesh)."""
         fv, off, cv, cs = _mesh_arrays(m)
         P0 = np.ascontiguousarray(m["P"] if P0 is None else P0, dtype=np.float32)
         r = _lib.Request(kind=REQ_MESH, scheme=SCHEMES[scheme], levels=int(levels), num_verts=int(m["V"]),
                          num_faces=int(m["F"]), face_offsets_host=None if off is None else off.ctypes.data,
                          face_verts_host=fv.ctypes.data, num_creases=int(cs.size),
-                         crease_verts_host=cv.ctypes.data if cs.size else None,
+                         num_boundary_edges=int(boundary_edges), crease_verts_host=cv.ctypes.data if cs.size else None,
                          crease_sharpness_host=cs.ctypes.data if cs.size else None,
                          P0_host=P0.ctypes.data, PL_host=None if out is None else out.ctypes.data)
         return self._submit(r, (P0, out))

@@ -159,7 +159,8 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     if (levels >= kMaxLevels) return fail(ALSUB_ERR_UNSUPPORTED, "at most %d levels", kMaxLevels - 1);
     T.L.assign(levels + 1, LevelBuf());
     LevelBuf &L0 = T.L[0];
-    L0.V = M.V; L0.F = M.F; L0.nnz = M.nnz; L0.E = M.nnz / 2;
+    // every edge has two corners except the B boundary edges (one each)
+    L0.V = M.V; L0.F = M.F; L0.nnz = M.nnz; L0.E = (M.nnz + M.B) / 2;
     for (int l = 0; l < levels; l++) {
         long long o[4];
         LevelBuf &A = T.L[l];
@@ -183,6 +184,17 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     }
     AL(T.eo0, E0);
     AL(T.e0count, 1); AL(T.status, 1);
+    // boundary lists of an open mesh, levels 0 .. levels - 1: the B_l = 2^l B boundary edges of
+    // level l (each boundary edge splits into two, Sec. 3.2 "Boundaries")
+    if (M.B > 0) {
+        AL(T.bcount, 1);
+        for (int l = 0; l < levels; l++) {
+            LevelBuf &A = T.L[l];
+            A.B = M.B << l;
+            if (A.B > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "level %d exceeds int32 counts", l);
+            AL(A.bA, A.B); AL(A.bE, A.B); AL(A.bS, A.B);
+        }
+    }
     // crease capacities: the sharpness of level l is at most sigma_max - l (each inherited
     // value is at most the parent maximum minus one), so creases are dead once l >= sigma_max
     bool creases = M.scheme != ALSUB_SQRT3 && M.K > 0;
@@ -521,14 +533,24 @@ alsub_status alsub_copy(void *dst, const void *src, size_t bytes, void *stream) 
 
 alsub_status alsub_plan(alsub_scheme scheme, int64_t V, int64_t F, int64_t nnz, int32_t levels,
                         int64_t *counts) {
+    return alsub_plan_open(scheme, V, F, nnz, 0, levels, counts);
+}
+
+alsub_status alsub_plan_open(alsub_scheme scheme, int64_t V, int64_t F, int64_t nnz, int64_t B,
+                             int32_t levels, int64_t *counts) {
     if (scheme < ALSUB_CATMULL_CLARK || scheme > ALSUB_SQRT3) return fail(ALSUB_ERR_INVALID_ARG, "bad scheme");
-    if (V <= 0 || F <= 0 || nnz < 3 * F || levels < 0 || !counts)
+    if (V <= 0 || F <= 0 || nnz < 3 * F || levels < 0 || !counts || B < 0 || B > nnz)
         return fail(ALSUB_ERR_INVALID_ARG, "bad counts");
     if (scheme != ALSUB_CATMULL_CLARK && nnz != 3 * F)
         return fail(ALSUB_ERR_INVALID_ARG, "Loop and sqrt(3) need a triangle mesh");
-    if (nnz % 2) return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
+    if (B > 0 && scheme != ALSUB_CATMULL_CLARK)
+        return fail(ALSUB_ERR_UNSUPPORTED, "boundaries are supported for Catmull-Clark only");
+    if ((nnz + B) % 2) {
+        if (B == 0) return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
+        return fail(ALSUB_ERR_INVALID_ARG, "nnz + boundary edges must be even");
+    }
     if (V > kI32 || F > kI32 || nnz > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "counts exceed int32");
-    long long c[4] = {V, F, nnz, nnz / 2};
+    long long c[4] = {V, F, nnz, (nnz + B) / 2};
     for (int l = 0; l <= levels; l++) {
         for (int i = 0; i < 4; i++) counts[4 * l + i] = c[i];
         if (l == levels) break;
@@ -564,7 +586,8 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
         for (int r = 0; r <= F; r++) off[r] = r * order;
     }
     const long long nnz = off[F];
-    if (nnz % 2) return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
+    if (scheme != ALSUB_CATMULL_CLARK && nnz % 2)
+        return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
     std::vector<int> used(V, 0), mark(V, -1);
     for (int r = 0; r < F; r++) {
         for (int x = off[r]; x < off[r + 1]; x++) {
@@ -619,7 +642,29 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
         cleanup();
         return cuda_fail(e, "mesh upload");
     }
+    if (scheme == ALSUB_CATMULL_CLARK) {
+        // boundary edges (Sec. 3.2 "Boundaries"): their number sizes every level; the paper gives
+        // no rule for a crease that meets the boundary, so such input is refused
+        long long B = 0;
+        bool crease_at_boundary = false;
+        alsub_status st = mesh_boundary_scan(M, s, &B, &crease_at_boundary);
+        if (st == ALSUB_OK && crease_at_boundary)
+            st = fail(ALSUB_ERR_UNSUPPORTED, "a crease touches a boundary vertex");
+        if (st == ALSUB_OK && ((nnz + B) % 2 || B > kI32))
+            st = fail(ALSUB_ERR_NONMANIFOLD, "inconsistent boundary (a directed edge repeats)");
+        if (st != ALSUB_OK) {
+            cleanup();
+            return st;
+        }
+        M.B = (int)B;
+    }
     *out = h;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_mesh_boundary_edges(alsub_mesh_t h, int64_t *boundary_edges) {
+    if (!h || !boundary_edges) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    *boundary_edges = h->m.B;
     return ALSUB_OK;
 }
 
@@ -774,14 +819,14 @@ alsub_status alsub_refine_vertices_scratch_bytes(alsub_topology_t h, size_t *byt
     return ALSUB_OK;
 }
 
-alsub_status alsub_plan_bytes(alsub_scheme scheme, int32_t V, int32_t F, int32_t nnz, int32_t K,
+alsub_status alsub_plan_bytes(alsub_scheme scheme, int32_t V, int32_t F, int32_t nnz, int32_t B, int32_t K,
                               float sigma_max, int32_t levels, size_t *bytes) {
     if (!bytes || K < 0 || !(sigma_max >= 0.f)) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     std::vector<int64_t> c(4 * ((size_t)std::max(levels, 0) + 1));
-    alsub_status st = alsub_plan(scheme, V, F, nnz, levels, c.data());
+    alsub_status st = alsub_plan_open(scheme, V, F, nnz, B, levels, c.data());
     if (st != ALSUB_OK) return st;
     MeshImpl M;
-    M.scheme = scheme; M.V = V; M.F = F; M.nnz = nnz;
+    M.scheme = scheme; M.V = V; M.F = F; M.nnz = nnz; M.B = B;
     M.K = scheme == ALSUB_SQRT3 ? 0 : K;
     M.sigma_max = M.K ? sigma_max : 0.f;
     TopoImpl T;

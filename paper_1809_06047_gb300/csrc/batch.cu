@@ -150,6 +150,10 @@ alsub_status alsub_batch_create(int32_t n, const alsub_topology_t *topos, const 
         if (!topos[i] || !P0_dev[i] || !PL_dev[i]) { delete B; return report(ALSUB_ERR_INVALID_ARG, "NULL member"); }
         TopoImpl *T = topology_impl(topos[i]);
         if (!T->built) { delete B; return report(ALSUB_ERR_INVALID_ARG, "batch member topology not built"); }
+        if (T->mesh->B > 0) {
+            delete B;
+            return report(ALSUB_ERR_UNSUPPORTED, "batch members must be closed meshes (no boundary repair)");
+        }
         for (TopoImpl *U : B->T)
             if (U == T) { delete B; return report(ALSUB_ERR_INVALID_ARG, "a topology appears twice in the batch"); }
         B->T.push_back(T);

@@ -17,6 +17,11 @@
 //                its split form) gathered by the one corner designated for the vertex, walking the
 //                ring x <- twin(prev(x)). The gather replaces the paper's atomic scatter (direct
 //                mapped SpMV, Sec. 4.3) so that results are bit-reproducible.
+//
+// Open meshes (Sec. 3.2 "Boundaries", build and repair): corners without a twin carry twin -1 and
+// the child rules keep it (a boundary edge splits into two boundary halves). The BND variants of
+// the kernels skip every point whose stencil would cross the boundary (boundary edge points,
+// boundary vertices); cc_boundary then writes those from the level's boundary list.
 #include <algorithm>
 
 #include "common.cuh"
@@ -57,7 +62,15 @@ struct CCArgs {
     const int *twl[kMaxLevels];   // stored twins of every level (null where not stored)
     bool in4, out4;               // parent / child positions in padded float4 rows
     int *status;
+    bool bnd;                     // the mesh is open (twins may be -1)
 };
+
+// Child twins across the halves of a parent edge (corner 0 and corner 3 of the children), or -1
+// when the parent edge is a boundary edge.
+template <bool BND>
+__device__ __forceinline__ int twin_half0(int t) { return (BND && t < 0) ? -1 : 4 * quad_next(t) + 3; }
+template <bool BND>
+__device__ __forceinline__ int twin_half3(int t) { return (BND && t < 0) ? -1 : 4 * t; }
 
 __device__ __forceinline__ float3 face_point_l0(const Level0 &z, const float *P, int g) {
     int s = __ldg(z.off + g), c = __ldg(z.off + g + 1) - s;
@@ -66,7 +79,7 @@ __device__ __forceinline__ float3 face_point_l0(const Level0 &z, const float *P,
     return (1.0f / (float)c) * acc;
 }
 
-template <bool TOPO, bool HELP, bool EVAL>
+template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const Level0 &z = a.z;
@@ -80,8 +93,9 @@ __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
             if (HELP) {
                 int ox = __ldg(z.own + x), op = __ldg(z.own + p);
                 st4(a.cen + 4 * (size_t)x, make_int4(2 * ex + (ox ? 0 : 1), E2 + x, E2 + p, 2 * ep + (op ? 1 : 0)));
-                st4(a.twn + 4 * (size_t)x, make_int4(4 * __ldg(z.nx + __ldg(z.tw + x)) + 3, 4 * __ldg(z.nx + x) + 2,
-                                                     4 * p + 1, 4 * __ldg(z.tw + p)));
+                const int tx = __ldg(z.tw + x), tp = __ldg(z.tw + p);
+                st4(a.twn + 4 * (size_t)x, make_int4((BND && tx < 0) ? -1 : 4 * __ldg(z.nx + tx) + 3,
+                                                     4 * __ldg(z.nx + x) + 2, 4 * p + 1, twin_half3<BND>(tp)));
             }
         }
     }
@@ -93,6 +107,7 @@ __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
             int x = s + j;
             if (__ldg(z.own + x)) {
                 int t = __ldg(z.tw + x);
+                if (BND && t < 0) continue;          // boundary edge: repaired
                 float3 fs = face_point_l0(z, P, __ldg(z.cf + t));
                 float3 ep = 0.25f * (ldp(P, __ldg(z.fv + x)) + ldp(P, __ldg(z.fv + __ldg(z.nx + x))) + fr + fs);
                 stpv(a.Pn, VF + __ldg(z.ce + x), ep, a.out4);
@@ -108,7 +123,8 @@ __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
                 sp += ldp(P, __ldg(z.fv + __ldg(z.nx + y)));
                 y = __ldg(z.rn + y);
                 n++;
-            } while (y != x && n < kMaxValence);
+            } while ((!BND || y >= 0) && y != x && n < kMaxValence);
+            if (BND && y < 0) continue;              // boundary vertex: repaired
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
             float inv = 1.0f / (float)n;
             stpv(a.Pn, v, (1.0f - 2.0f * inv) * ldp(P, v) + (inv * inv) * (sp + sf), a.out4);
@@ -116,7 +132,7 @@ __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
     }
 }
 
-template <bool TOPO, bool HELP, bool EVAL>
+template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __device__ __forceinline__ void cc_quad_body(const CCArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const int VF = a.V + a.F, E2 = 2 * a.E, c0 = 4 * r;
@@ -138,11 +154,12 @@ __device__ __forceinline__ void cc_quad_body(const CCArgs &a, int r) {
         st4(o + 4, make_int4(2 * e.y, E2 + c0 + 1, E2 + c0, 2 * e.x + 1));
         st4(o + 8, make_int4(2 * e.z + 1, E2 + c0 + 2, E2 + c0 + 1, 2 * e.y + 1));
         st4(o + 12, make_int4(2 * e.w + 1, E2 + c0 + 3, E2 + c0 + 2, 2 * e.z));
+        // corners 1 and 2 are interior edges of the parent face: only t.x and t.w can be -1
         int *w = a.twn + 16 * (size_t)r;
-        st4(w + 0, make_int4(4 * quad_next(t.x) + 3, 4 * (c0 + 1) + 2, 4 * (c0 + 3) + 1, 4 * t.w));
-        st4(w + 4, make_int4(4 * quad_next(t.y) + 3, 4 * (c0 + 2) + 2, 4 * (c0 + 0) + 1, 4 * t.x));
+        st4(w + 0, make_int4(twin_half0<BND>(t.x), 4 * (c0 + 1) + 2, 4 * (c0 + 3) + 1, twin_half3<BND>(t.w)));
+        st4(w + 4, make_int4(4 * quad_next(t.y) + 3, 4 * (c0 + 2) + 2, 4 * (c0 + 0) + 1, twin_half3<BND>(t.x)));
         st4(w + 8, make_int4(4 * quad_next(t.z) + 3, 4 * (c0 + 3) + 2, 4 * (c0 + 1) + 1, 4 * t.y));
-        st4(w + 12, make_int4(4 * quad_next(t.w) + 3, 4 * (c0 + 0) + 2, 4 * (c0 + 2) + 1, 4 * t.z));
+        st4(w + 12, make_int4(twin_half0<BND>(t.w), 4 * (c0 + 0) + 2, 4 * (c0 + 2) + 1, 4 * t.z));
     }
     if (EVAL) {
         const float *P = a.P;
@@ -150,7 +167,7 @@ __device__ __forceinline__ void cc_quad_body(const CCArgs &a, int r) {
         const float3 fr = 0.25f * (p0 + p1 + p2 + p3);
         stpv(a.Pn, a.V + r, fr, a.out4);
         // edge points of the two owned edges (corners 4r and 4r+1)
-        {
+        if (!BND || t.x >= 0) {
             int4 g = ld4(a.fv + 4 * (size_t)(t.x >> 2));
             float3 fs = 0.25f * (ldpv(P, g.x, a.in4) + ldpv(P, g.y, a.in4) + ldpv(P, g.z, a.in4) + ldpv(P, g.w, a.in4));
             stpv(a.Pn, VF + e.x, 0.25f * (p0 + p1 + fr + fs), a.out4);
@@ -175,7 +192,8 @@ __device__ __forceinline__ void cc_quad_body(const CCArgs &a, int r) {
                 sp += kk == 0 ? q0 : (kk == 1 ? q1 : (kk == 2 ? q2 : q3));
                 y = __ldg(a.tw + quad_prev(y));
                 n++;
-            } while (y != x && n < kMaxValence);
+            } while ((!BND || y >= 0) && y != x && n < kMaxValence);
+            if (BND && y < 0) continue;              // boundary vertex: repaired
             if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
             float inv = 1.0f / (float)n;
             int vk = comp(v, k);
@@ -252,7 +270,7 @@ __device__ __forceinline__ void prefetch_rows(const int *rows, long long f0, lon
     l2_prefetch(rows + 4 * f0, (unsigned)(16 * n));
 }
 
-template <bool TOPO, bool HELP, bool EVAL, int DERIVE>
+template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND>
 __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
     if (ALSUB_SIB_PREFETCH > 0 && threadIdx.x == 0) {
         const long long f0 = ((long long)blockIdx.x + ALSUB_SIB_PREFETCH) * blockDim.x;
@@ -273,9 +291,10 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
 
     // ---- round trip 1: own row, adjacency rows, the twin an old vertex's ring needs
     const Birth b = cc_descend(a.l, c0);
-    const int fk = (EVAL && live) ? fast_kind(b) : 0;
+    int fk = (EVAL && live) ? fast_kind(b) : 0;
     int tt = 0;
     if (fk == 1) tt = __ldg(a.twl[b.m - 1] + b.c);
+    if (BND && fk == 1 && tt < 0) fk = 0;       // an edge point of a boundary edge: repaired
     int4 v = make_int4(0, 0, 0, 0), e = v, t = v;
     if (live) {
         v = ld4(fv + 4 * (size_t)r);
@@ -291,14 +310,15 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
                 const int Epp2 = 2 * a.Epp;
                 pe = make_int4(2 * comp(ge, k) + (k < 2 ? 0 : 1), Epp2 + R, Epp2 + go,
                                2 * comp(ge, kp) + (kp < 2 ? 1 : 0));
-                pt = make_int4(4 * quad_next(comp(gt, k)) + 3, 4 * quad_next(R) + 2, 4 * go + 1, 4 * comp(gt, kp));
+                pt = make_int4(twin_half0<BND>(comp(gt, k)), 4 * quad_next(R) + 2, 4 * go + 1,
+                               twin_half3<BND>(comp(gt, kp)));
             }
             const int jp = (j + 3) & 3, po = 4 * R + jp;
             const int Ep2 = 2 * a.Ep;
             e = make_int4(2 * comp(pe, j) + (j < 2 ? 0 : 1), Ep2 + r, Ep2 + po,
                           2 * comp(pe, jp) + (jp < 2 ? 1 : 0));
-            t = make_int4(4 * quad_next(comp(pt, j)) + 3, 4 * quad_next(r) + 2, 4 * po + 1,
-                          4 * comp(pt, jp));
+            t = make_int4(twin_half0<BND>(comp(pt, j)), 4 * quad_next(r) + 2, 4 * po + 1,
+                          twin_half3<BND>(comp(pt, jp)));
         } else {
             e = ld4(a.ce + 4 * (size_t)r);
             if (HELP || EVAL) t = ld4(a.tw + 4 * (size_t)r);
@@ -308,11 +328,12 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
         // ---- round trip 2: own positions, rows of the two faces across edge (a_j, b_j),
         //      rows of the old vertex's ring
         const int s1 = t.x >> 2;                   // F1 = [a_j, y, z, b_j]
+        const bool ob = BND && t.x < 0;            // (a_j, b_j) is a boundary edge: no F1, F2
         int4 g1 = make_int4(0, 0, 0, 0), g2 = g1, q0 = g1, q1 = g1;
         float3 pa = f3(0.f, 0.f, 0.f), pb = pa, pc = pa;
         if (live) {
-            g1 = ld4(fv + 4 * (size_t)s1);
-            if (j < 2) g2 = ld4(fv + 4 * (size_t)quad_prev(s1));   // F2 = [a_{j+1}, b_j, z, w]
+            if (!ob) g1 = ld4(fv + 4 * (size_t)s1);
+            if (j < 2 && !ob) g2 = ld4(fv + 4 * (size_t)quad_prev(s1));   // F2 = [a_{j+1}, b_j, z, w]
             pa = ldpv(P, v.x, true);
             pb = ldpv(P, v.y, true);
             if (j == 0) pc = ldpv(P, v.z, true);
@@ -344,8 +365,9 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
         const float3 sa = sum4(pa), sb = sum4(pb);
         if (live) {
             // ---- round trip 3: far vertices across (a_j, b_j), the old vertex's ring
-            const float3 py = ldpv(P, g1.y, true), pz = ldpv(P, g1.z, true);
-            const float3 pw = j < 2 ? ldpv(P, g2.w, true) : f3(0.f, 0.f, 0.f);
+            const float3 py = ob ? f3(0.f, 0.f, 0.f) : ldpv(P, g1.y, true);
+            const float3 pz = ob ? f3(0.f, 0.f, 0.f) : ldpv(P, g1.z, true);
+            const float3 pw = (j < 2 && !ob) ? ldpv(P, g2.w, true) : f3(0.f, 0.f, 0.f);
             float3 vp_old = f3(0.f, 0.f, 0.f);
             if (fk > 0) {
                 // valence 4: (1 - 7/16) p + 3/32 sum next + 1/64 sum opp. Ring faces r = [a, b_j,
@@ -358,12 +380,12 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
             stpv(a.Pn, a.V + r, fr, a.out4);
             // interior edge (b_j, c) between children j and j+1
             stpv(a.Pn, VF + e.y, 0.25f * (pb + pc + fr + fn), a.out4);
-            // boundary edge (a_j, b_j) shared with F1
-            stpv(a.Pn, VF + e.x, 0.375f * (pa + pb) + 0.0625f * (pc + pd + py + pz), a.out4);
+            // edge (a_j, b_j) on the parent's edge, shared with F1
+            if (!ob) stpv(a.Pn, VF + e.x, 0.375f * (pa + pb) + 0.0625f * (pc + pd + py + pz), a.out4);
             // face point c of the parent (valence 4): designated at child 0
             if (j == 0) stpv(a.Pn, v.z, 0.5625f * pc + 0.09375f * sb + 0.015625f * sa, a.out4);
             // edge point b_j of an owned parent edge (j < 2, valence 4): ring = children j, j+1, F1, F2
-            if (j < 2)
+            if (j < 2 && !ob)
                 stpv(a.Pn, v.y, 0.5625f * pb + 0.09375f * (pc + pa + pz + pan) + 0.015625f * (pd + py + pw + pbn),
                      a.out4);
             if (fk > 0) stpv(a.Pn, v.x, vp_old, a.out4);
@@ -383,25 +405,31 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
                         so += ldpv(P, q.z, true);
                         n++;
                     };
-                    bool ok = true;
+                    bool ok = true, open = false;     // open: a boundary vertex, repaired
                     if (b.m == 0) {
                         int y = b.c;
                         do {
                             visit(y);
                             y = __ldg(z.rn + y);
-                        } while (y != b.c && n < kMaxValence);
+                        } while ((!BND || y >= 0) && y != b.c && n < kMaxValence);
+                        open = BND && y < 0;
                         ok = y == b.c;
                     } else if (b.k == 1) {
                         const int t0 = __ldg(z.tw + b.c);
-                        visit(4 * b.c + 1);
-                        visit(4 * __ldg(z.nx + t0) + 3);
-                        visit(4 * t0 + 1);
-                        visit(4 * __ldg(z.nx + b.c) + 3);
+                        if (BND && t0 < 0) {
+                            open = true;
+                        } else {
+                            visit(4 * b.c + 1);
+                            visit(4 * __ldg(z.nx + t0) + 3);
+                            visit(4 * t0 + 1);
+                            visit(4 * __ldg(z.nx + b.c) + 3);
+                        }
                     } else {
                         const int Q = __ldg(z.cf + b.c), s0 = __ldg(z.off + Q), c = __ldg(z.off + Q + 1) - s0;
                         for (int i = 0; i < c; i++) visit(4 * (s0 + i) + 2);
                     }
-                    if (!ok) {
+                    if (open) {
+                    } else if (!ok) {
                         set_status(a.status, ALSUB_ERR_UNSUPPORTED);
                     } else {
                         const float inv = 1.0f / (float)n;
@@ -426,24 +454,58 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
         st4(o + 8, make_int4(2 * e.z + 1, E2 + c0 + 2, E2 + c0 + 1, 2 * e.y + 1));
         st4(o + 12, make_int4(2 * e.w + 1, E2 + c0 + 3, E2 + c0 + 2, 2 * e.z));
         int *w = a.twn + 16 * (size_t)r;
-        st4(w + 0, make_int4(4 * quad_next(t.x) + 3, 4 * (c0 + 1) + 2, 4 * (c0 + 3) + 1, 4 * t.w));
-        st4(w + 4, make_int4(4 * quad_next(t.y) + 3, 4 * (c0 + 2) + 2, 4 * (c0 + 0) + 1, 4 * t.x));
+        st4(w + 0, make_int4(twin_half0<BND>(t.x), 4 * (c0 + 1) + 2, 4 * (c0 + 3) + 1, twin_half3<BND>(t.w)));
+        st4(w + 4, make_int4(4 * quad_next(t.y) + 3, 4 * (c0 + 2) + 2, 4 * (c0 + 0) + 1, twin_half3<BND>(t.x)));
         st4(w + 8, make_int4(4 * quad_next(t.z) + 3, 4 * (c0 + 3) + 2, 4 * (c0 + 1) + 1, 4 * t.y));
-        st4(w + 12, make_int4(4 * quad_next(t.w) + 3, 4 * (c0 + 0) + 2, 4 * (c0 + 2) + 1, 4 * t.z));
+        st4(w + 12, make_int4(twin_half0<BND>(t.w), 4 * (c0 + 0) + 2, 4 * (c0 + 2) + 1, 4 * t.z));
     }
 }
 
-template <bool TOPO, bool HELP, bool EVAL>
+template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
-    cc_l0_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    cc_l0_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
-template <bool TOPO, bool HELP, bool EVAL>
+template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
-    cc_quad_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    cc_quad_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
-template <bool TOPO, bool HELP, bool EVAL, int DERIVE>
+template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND>
 __global__ void __launch_bounds__(ALSUB_SIB_BLOCK, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
-    cc_sib_body<TOPO, HELP, EVAL, DERIVE>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    cc_sib_body<TOPO, HELP, EVAL, DERIVE, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Boundary repair of step l (Sec. 3.2 "Boundaries"): entry i of level l's boundary list is the
+// boundary edge a -> b, its successor the edge b -> c. It writes the edge point of (a, b) as the
+// midpoint and the vertex point of b by Eq. CC_boundary, 3/4 p_b + 1/8 (p_a + p_c), over what the
+// smooth step left there; every boundary edge and vertex has exactly one entry. With a child list,
+// it also writes the two halves of (a, b) on level l + 1: a -> e at 2i (edge id 2e + 0 when the
+// corner of (a, b) owns its edge, as level 0's boundary corners and levels >= 1's even entries,
+// the corners 0 of their quads, do) and e -> b at 2i + 1, followed by the first half of b -> c.
+__global__ void __launch_bounds__(kBlock) k_cc_bnd(int n, bool lvl0, const int *__restrict__ A,
+                                                   const int *__restrict__ E, const int *__restrict__ S,
+                                                   int *An, int *En, int *Sn, int V, int El, int VF,
+                                                   const float *__restrict__ P, float *Pn, bool in4, bool out4,
+                                                   int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || failed(status)) return;
+    auto clampi = [](int x, int hi) { return min(max(x, 0), hi - 1); };
+    const int a = clampi(__ldg(A + i), V), e = clampi(__ldg(E + i), El), s1 = clampi(__ldg(S + i), n);
+    const int b = clampi(__ldg(A + s1), V);
+    if (P) {
+        const int c = clampi(__ldg(A + clampi(__ldg(S + s1), n)), V);
+        const float3 pa = ldpv(P, a, in4), pb = ldpv(P, b, in4), pc = ldpv(P, c, in4);
+        stpv(Pn, VF + e, 0.5f * (pa + pb), out4);
+        stpv(Pn, b, 0.75f * pb + 0.125f * (pa + pc), out4);
+    }
+    if (An) {
+        const int h = (lvl0 || (i & 1) == 0) ? 0 : 1;
+        An[2 * i] = a;
+        En[2 * i] = 2 * e + h;
+        Sn[2 * i] = 2 * i + 1;
+        An[2 * i + 1] = VF + e;
+        En[2 * i + 1] = 2 * e + 1 - h;
+        Sn[2 * i + 1] = 2 * s1;
+    }
 }
 
 // Ragged batches: the eval steps of many topologies at one level in one persistent launch per
@@ -468,22 +530,27 @@ __global__ void __launch_bounds__(512, 2) k_cc_batch(const CCArgs *__restrict__ 
         const int i = item_of(tile_begin, n, tile);
         const int r = (tile - __ldg(tile_begin + i)) * blockDim.x + threadIdx.x;
         const CCArgs &a = items[i];          // read in place: a copy would not fit in registers
-        if (KIND == 0) cc_l0_body<false, false, true>(a, r);
-        else if (KIND == 1) cc_quad_body<false, false, true>(a, r);
-        else if (KIND == 2) cc_sib_body<false, false, true, 0>(a, r);
-        else if (KIND == 3) cc_sib_body<false, false, true, 1>(a, r);
-        else cc_sib_body<false, false, true, 2>(a, r);
+        if (KIND == 0) cc_l0_body<false, false, true, false>(a, r);
+        else if (KIND == 1) cc_quad_body<false, false, true, false>(a, r);
+        else if (KIND == 2) cc_sib_body<false, false, true, 0, false>(a, r);
+        else if (KIND == 3) cc_sib_body<false, false, true, 1, false>(a, r);
+        else cc_sib_body<false, false, true, 2, false>(a, r);
     }
 }
 
+template <bool T, bool H, bool E, bool B>
+void launch_b(const CCArgs &a, int derive, cudaStream_t s) {
+    const unsigned g = grid_for(a.F, ALSUB_SIB_BLOCK);
+    if (a.l == 0) k_cc_l0<T, H, E, B><<<grid_for(a.F), kBlock, 0, s>>>(a);
+    else if (a.l == 1) k_cc_quad<T, H, E, B><<<grid_for(a.F), kBlock, 0, s>>>(a);
+    else if (derive == 2) k_cc_sib<T, false, E, 2, B><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
+    else if (derive == 1) k_cc_sib<T, false, E, 1, B><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
+    else k_cc_sib<T, H, E, 0, B><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
+}
 template <bool T, bool H, bool E>
 void launch(const CCArgs &a, int derive, cudaStream_t s) {
-    const unsigned g = grid_for(a.F, ALSUB_SIB_BLOCK);
-    if (a.l == 0) k_cc_l0<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else if (a.l == 1) k_cc_quad<T, H, E><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else if (derive == 2) k_cc_sib<T, false, E, 2><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
-    else if (derive == 1) k_cc_sib<T, false, E, 1><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
-    else k_cc_sib<T, H, E, 0><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
+    if (a.bnd) launch_b<T, H, E, true>(a, derive, s);
+    else launch_b<T, H, E, false>(a, derive, s);
 }
 
 }  // namespace
@@ -500,6 +567,7 @@ CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, int *derive_out)
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
+    a.bnd = T.mesh->B > 0;
     a.in4 = l > 0;                     // only the caller's input level is packed xyz
     a.out4 = l + 1 < T.levels;         // and the caller's output level
     // a level >= 2 without stored edge ids / twins derives them from its parent level, or (level
@@ -530,6 +598,17 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     else if (topo && ev) launch<true, false, true>(a, derive, s);
     else if (topo) launch<true, false, false>(a, derive, s);
     else if (ev) launch<false, false, true>(a, derive, s);
+    if (a.bnd) cc_boundary(T, l, topo && l + 1 < T.levels, P, Pn, s);
+}
+
+void cc_boundary(TopoImpl &T, int l, bool list, const float *P, float *Pn, cudaStream_t s) {
+    const LevelBuf &A = T.L[l];
+    if (A.B == 0 || (!list && !P)) return;
+    LevelBuf *N = list ? &T.L[l + 1] : nullptr;
+    k_cc_bnd<<<grid_for(A.B), kBlock, 0, s>>>((int)A.B, l == 0, A.bA, A.bE, A.bS, N ? N->bA : nullptr,
+                                             N ? N->bE : nullptr, N ? N->bS : nullptr, (int)A.V, (int)A.E,
+                                             (int)(A.V + A.F), P, Pn, l > 0, l + 1 < T.levels, T.status);
+    T.launches += 1;
 }
 
 std::vector<BatchClass> cc_batch_plan(const std::vector<EvalItem> &items, int block) {

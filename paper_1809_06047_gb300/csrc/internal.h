@@ -43,6 +43,12 @@ struct LevelBuf {
     int *tw = nullptr;
     bool helpers = false;  // ce and tw are stored for this level
     CreaseList cr;
+    // boundary list of an open Catmull-Clark mesh (levels below the last): entry i is a boundary
+    // edge a -> b of this level with a = bA[i], edge id bE[i] and bS[i] = the entry of the next
+    // boundary edge b -> c along the loop. Level 0 lists the boundary corners in any order;
+    // level l + 1 holds the two halves of entry i at 2i (a -> edge point) and 2i + 1.
+    long long B = 0;
+    int *bA = nullptr, *bE = nullptr, *bS = nullptr;
 };
 
 struct MeshImpl {
@@ -53,6 +59,7 @@ struct MeshImpl {
     int *d_fv = nullptr;       // nnz
     int *d_cv = nullptr;       // 2K
     float *d_cs = nullptr;     // K
+    int B = 0;                 // boundary edges (Catmull-Clark open meshes)
     cudaStream_t stream = nullptr;
 };
 
@@ -84,6 +91,7 @@ struct TopoImpl {
     int *eo0 = nullptr, *deg = nullptr, *rn0 = nullptr;   // rn0: twin(prev(x)), the ring step
     DirTable dir;
     int *eid = nullptr, *e0count = nullptr;
+    int *bcount = nullptr;       // boundary corners found on level 0
     int *status = nullptr;       // latched device error
     // temporaries
     void *scan_tmp = nullptr;
@@ -136,6 +144,13 @@ void level0_build(TopoImpl &T, cudaStream_t s);
 void level0_validate(TopoImpl &T, cudaStream_t s);
 // Level 0's crease list and hash table (needs level0_build's arrays).
 void level0_creases(TopoImpl &T, cudaStream_t s);
+// Boundary edges of a Catmull-Clark control mesh (corners whose reverse edge is in no face) and
+// whether a crease touches a boundary vertex; synchronises `s`.
+alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary);
+// Boundary repair of one Catmull-Clark step (Sec. 3.2 "Boundaries", Fig. module_boundary): with
+// positions, overwrite the boundary edge points (midpoints) and boundary vertices (Eq.
+// CC_boundary) of level l + 1; with `list`, write level l + 1's boundary list.
+void cc_boundary(TopoImpl &T, int l, bool list, const float *P, float *Pn, cudaStream_t s);
 
 // One refinement step from level l to l + 1. topo: emit the child face table; helpers: emit the
 // child's per-corner edge ids and twins; P/Pn: parent/child positions (null = no vertex eval).

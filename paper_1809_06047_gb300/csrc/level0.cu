@@ -8,8 +8,11 @@
 //    symbolic pass of the implicit mapped SpGEMM of Sec. 4.2 done as one hash join: every corner
 //    inserts its directed edge, every corner looks up the reverse one);
 //  * the edge numbering: a corner owns its edge when its start vertex is the smaller endpoint
-//    (the upper triangle of E, Eq. CC_E); an exclusive scan over the owner flags numbers the
-//    edges deterministically;
+//    (the upper triangle of E, Eq. CC_E), or when it has no twin (a boundary edge, the entries
+//    of value 1 in E that Sec. 3.2 "Boundaries" identifies); an exclusive scan over the owner
+//    flags numbers the edges deterministically;
+//  * for an open Catmull-Clark mesh, the list of boundary corners with each one's successor
+//    along its boundary loop (the input of the boundary repair step, Fig. module_boundary);
 //  * the level-0 crease list (C of Sec. 3.3) sorted by edge id.
 // Non-manifold input is reported through the handle's status word, never by trapping.
 #include "common.cuh"
@@ -81,19 +84,21 @@ __global__ void k_insert(int nnz, const int *__restrict__ fv, const int *__restr
     if (!dir_insert(tab, fv[x], fv[nx[x]], x)) set_status(status, ALSUB_ERR_NONMANIFOLD);  // duplicate
 }
 
-// Twin of a -> b: the corner of b -> a (none: an open edge, i.e. a boundary). A corner owns its
-// edge when a < b; each block also counts its owner corners (the edge numbering scans the counts).
+// Twin of a -> b: the corner of b -> a (none: an open edge, i.e. a boundary: twin -1 when the
+// scheme has boundary rules, else an error). A corner owns its edge when a < b or it has no
+// twin; each block also counts its owner corners (the edge numbering scans the counts).
 __global__ void __launch_bounds__(kBlock) k_twin(int nnz, const int *__restrict__ fv, const int *__restrict__ nx,
-                                                 DirTable tab, int *tw, int *own, int *bcount, int *status) {
+                                                 DirTable tab, bool open, int *tw, int *own, int *bcount,
+                                                 int *status) {
     __shared__ int wsum[kBlock / 32];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     int o = 0;
     if (x < nnz) {
         const int a = fv[x], b = fv[nx[x]];
         const int t = dir_find(tab, b, a);
-        if (t < 0) set_status(status, ALSUB_ERR_UNSUPPORTED);
-        tw[x] = t < 0 ? x : t;
-        o = a < b ? 1 : 0;
+        if (t < 0 && !open) set_status(status, ALSUB_ERR_UNSUPPORTED);
+        tw[x] = t < 0 ? (open ? -1 : x) : t;
+        o = (a < b || (t < 0 && open)) ? 1 : 0;
         own[x] = o;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, o);
@@ -123,9 +128,13 @@ __global__ void __launch_bounds__(kBlock) k_eid(int nnz, const int *__restrict__
 }
 
 // Validation of each vertex: it is in some face, its valence is supported, and its corners form a
-// single fan (the ring walk x <- twin(prev(x)) returns to the start after exactly deg(v) steps).
+// single fan. Interior vertex: the ring walk x <- twin(prev(x)) returns to the start after
+// exactly deg(v) steps. Boundary vertex (the walk meets a corner without twin): the walk forward
+// from the start to the fan's end plus the walk backward x <- next(twin(x)) to its beginning
+// visit deg(v) corners (a second fan would be missed by both).
 __global__ void k_vertex(int V, const int *__restrict__ deg, const unsigned *__restrict__ vc,
-                         const int *__restrict__ rn, int *status) {
+                         const int *__restrict__ rn, const int *__restrict__ tw, const int *__restrict__ nx,
+                         int *status) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const int d = deg[v];
@@ -134,8 +143,70 @@ __global__ void k_vertex(int V, const int *__restrict__ deg, const unsigned *__r
     if (failed(status)) return;
     const int m = (int)vc[v];
     int x = m, steps = 0;
-    do { x = rn[x]; steps++; } while (x != m && steps <= d);
+    do { x = rn[x]; steps++; } while (x >= 0 && x != m && steps <= d);
+    if (x < 0) {
+        int y = m;
+        while (tw[y] >= 0 && steps <= d) { y = nx[tw[y]]; steps++; }
+    }
     if (steps != d) set_status(status, ALSUB_ERR_NONMANIFOLD);
+}
+
+// Boundary corners of an open mesh (twin -1), appended in any order: entry i holds the corner's
+// start vertex and edge id; bidx maps the corner back to its entry.
+__global__ void k_bnd0(int nnz, const int *__restrict__ fv, const int *__restrict__ tw, const int *__restrict__ ce,
+                       int B, int *count, int *A, int *E, int *S, int *bidx) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nnz || tw[x] >= 0) return;
+    const int i = atomicAdd(count, 1);
+    if (i >= B) return;
+    A[i] = fv[x];
+    E[i] = ce[x];
+    S[i] = x;                      // the corner, until k_bnd0_link replaces it
+    bidx[x] = i;
+}
+
+// Successor of entry i along its loop: the boundary corner leaving the end vertex b of corner
+// x = a -> b. The fan of b is walked from next(x) with y <- next(twin(y)) until the corner
+// without twin (Sec. 3.2 "Boundaries": the boundary neighbours of a vertex).
+__global__ void k_bnd0_link(int B, const int *__restrict__ count, const int *__restrict__ tw,
+                            const int *__restrict__ nx, const int *__restrict__ bidx, int *S, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i == 0 && *count != B) set_status(status, ALSUB_ERR_NONMANIFOLD);
+    if (i >= B || i >= *count) return;
+    const int x = S[i];
+    int y = nx[x], steps = 0;
+    while (tw[y] >= 0 && steps < kMaxValence) { y = nx[tw[y]]; steps++; }
+    if (tw[y] >= 0) { set_status(status, ALSUB_ERR_UNSUPPORTED); S[i] = i; return; }
+    const int j = bidx[y];
+    S[i] = (j >= 0 && j < B) ? j : i;
+}
+
+// Boundary scan of a Catmull-Clark control mesh at creation: every face inserts its directed
+// edges, then every corner whose reverse edge is missing is a boundary corner (counted) and its
+// endpoints are boundary vertices (flagged), and a crease touching a boundary vertex is flagged.
+__global__ void k_mb_insert(int F, const int *__restrict__ off, const int *__restrict__ fv, DirTable tab) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= F) return;
+    const int s = off[r], c = off[r + 1] - s;
+    for (int j = 0; j < c; j++) dir_insert(tab, fv[s + j], fv[s + (j + 1 == c ? 0 : j + 1)], s + j);
+}
+__global__ void k_mb_count(int F, const int *__restrict__ off, const int *__restrict__ fv, DirTable tab,
+                           int *bv, int *out) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= F) return;
+    const int s = off[r], c = off[r + 1] - s;
+    for (int j = 0; j < c; j++) {
+        const int a = fv[s + j], b = fv[s + (j + 1 == c ? 0 : j + 1)];
+        if (dir_find(tab, b, a) < 0) {
+            atomicAdd(out, 1);
+            bv[a] = 1;
+            bv[b] = 1;
+        }
+    }
+}
+__global__ void k_mb_crease(int K, const int *__restrict__ cv, const int *__restrict__ bv, int *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < K && (bv[cv[2 * i]] || bv[cv[2 * i + 1]])) out[1] = 1;
 }
 
 // Edge ids (an owner's own, else its twin's), owner corner of each edge, and the ring step
@@ -192,16 +263,60 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
                                            reinterpret_cast<unsigned *>(T.vc0));
     k_insert<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, T.status);
     const unsigned nb = grid_for(nnz);
-    k_twin<<<nb, kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, L0.tw, T.own0, T.flags, T.status);
+    const bool open = M.scheme == ALSUB_CATMULL_CLARK;
+    k_twin<<<nb, kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, open, L0.tw, T.own0, T.flags, T.status);
     T.launches += 5 + scan_exclusive(T.flags, T.pos, nb, T.e0count, nullptr, T.scan_tmp, s);
     k_eid<<<nb, kBlock, 0, s>>>(nnz, T.own0, T.pos, T.eid);
     k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.pv0, T.e0count, E0, L0.ce, T.eo0,
                                              T.rn0, T.status);
+    if (M.B > 0) {
+        // the per-corner edge-id temporaries are dead: they map boundary corners to entries
+        cudaMemsetAsync(T.bcount, 0, sizeof(int), s);
+        k_bnd0<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, L0.tw, L0.ce, M.B, T.bcount, L0.bA, L0.bE, L0.bS,
+                                                T.eid);
+        k_bnd0_link<<<grid_for(M.B), kBlock, 0, s>>>(M.B, T.bcount, L0.tw, T.nx0, T.eid, L0.bS, T.status);
+        T.launches += 2;
+    }
+}
+
+alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary) {
+    *B = 0;
+    *crease_at_boundary = false;
+    int k = 4;
+    while ((1LL << k) < 2LL * M.nnz) k++;
+    const size_t slots = (size_t)1 << k;
+    char *buf = nullptr;
+    const size_t bytes = slots * (sizeof(unsigned long long) + sizeof(int)) + sizeof(int) * ((size_t)M.V + 2);
+    if (cudaMallocAsync((void **)&buf, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return report(ALSUB_ERR_OOM, "mesh boundary scan: device allocation failed");
+    }
+    DirTable tab;
+    tab.key = (unsigned long long *)buf;
+    tab.val = (int *)(buf + slots * sizeof(unsigned long long));
+    tab.mask = (unsigned)(slots - 1);
+    int *bv = tab.val + slots, *out = bv + M.V;
+    cudaMemsetAsync(tab.key, 0xff, slots * sizeof(unsigned long long), s);
+    cudaMemsetAsync(bv, 0, sizeof(int) * ((size_t)M.V + 2), s);
+    k_mb_insert<<<grid_for(M.F), kBlock, 0, s>>>(M.F, M.d_off, M.d_fv, tab);
+    k_mb_count<<<grid_for(M.F), kBlock, 0, s>>>(M.F, M.d_off, M.d_fv, tab, bv, out);
+    if (M.K > 0) k_mb_crease<<<grid_for(M.K), kBlock, 0, s>>>(M.K, M.d_cv, bv, out);
+    int h[2] = {0, 0};
+    cudaError_t e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFreeAsync(buf, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return report(ALSUB_ERR_DEVICE, "mesh boundary scan failed");
+    }
+    *B = h[0];
+    *crease_at_boundary = h[1] != 0;
+    return ALSUB_OK;
 }
 
 void level0_validate(TopoImpl &T, cudaStream_t s) {
     k_vertex<<<grid_for(T.mesh->V), kBlock, 0, s>>>(T.mesh->V, T.deg, reinterpret_cast<unsigned *>(T.vc0),
-                                                    T.rn0, T.status);
+                                                    T.rn0, T.L[0].tw, T.nx0, T.status);
     T.launches += 1;
 }
 

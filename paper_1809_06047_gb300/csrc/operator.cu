@@ -39,6 +39,9 @@ struct OpLevel {
     Level0 z;
     CreaseList cr;
     bool creases;
+    bool bnd;                      // open mesh: twins may be -1, boundary rows come from the list
+    int B;                         // boundary list of the level (entries a -> b, successor b -> c)
+    const int *bA, *bE, *bS;
 };
 
 __device__ __forceinline__ int o_next(const OpLevel &L, int x) {
@@ -100,10 +103,12 @@ struct Row {
     }
 };
 
+// Valence of the vertex of corner x from its ring walk; 0 when the walk leaves the mesh (a
+// boundary vertex), -1 when it does not close within the supported valence.
 __device__ int ring_valence(const OpLevel &L, int x) {
     int y = x, n = 0;
-    do { n++; y = o_twin(L, o_prev(L, y)); } while (y != x && n < kMaxValence);
-    return y == x ? n : -1;
+    do { n++; y = o_twin(L, o_prev(L, y)); } while (y >= 0 && y != x && n < kMaxValence);
+    return y == x ? n : (y < 0 ? 0 : -1);
 }
 
 // crease blend of a vertex row: w sharp + (1 - w) smooth for k >= 2 incident creases
@@ -154,9 +159,10 @@ __device__ void face_row(const OpLevel &L, int g, Row &R) {
     for (int k = 0; k < c; k++) R.add(o_vtx(L, s0 + k), wf);
 }
 
-__device__ bool vertex_row(const OpLevel &L, int x, Row &R) {
+// 1: row written; 0: a boundary vertex (its row comes from the boundary list); -1: unsupported.
+__device__ int vertex_row(const OpLevel &L, int x, Row &R) {
     const int n = ring_valence(L, x);
-    if (n <= 0) return false;
+    if (n <= 0) return n;
     const int v = o_vtx(L, x);
     const float inv = 1.f / (float)n;
     if (L.scheme == ALSUB_CATMULL_CLARK) {
@@ -191,7 +197,7 @@ __device__ bool vertex_row(const OpLevel &L, int x, Row &R) {
         }
     }
     if (L.scheme != ALSUB_SQRT3) crease_vertex(L, x, R);
-    return true;
+    return 1;
 }
 
 __device__ void edge_row(const OpLevel &L, int o, Row &R) {
@@ -241,17 +247,48 @@ __global__ void k_op_rows(OpLevel L, int *cnt, const long long *rowptr, int *col
     }
     for (int k = 0; k < c; k++) {
         const int x = s0 + k;
-        if (L.scheme != ALSUB_SQRT3 && o_own(L, x)) {
+        if (L.scheme != ALSUB_SQRT3 && o_own(L, x) && !(L.bnd && o_twin(L, x) < 0)) {
             R.clear();
             edge_row(L, x, R);
             emit((L.scheme == ALSUB_CATMULL_CLARK ? VF : L.V) + o_edge(L, x));
         }
         if (o_vown(L, x)) {
             R.clear();
-            if (!vertex_row(L, x, R)) { set_status(status, ALSUB_ERR_UNSUPPORTED); continue; }
-            emit(o_vtx(L, x));
+            const int got = vertex_row(L, x, R);
+            if (got < 0 || (got == 0 && !L.bnd)) { set_status(status, ALSUB_ERR_UNSUPPORTED); continue; }
+            if (got > 0) emit(o_vtx(L, x));
         }
     }
+}
+
+// Boundary rows of a Catmull-Clark level (Sec. 3.2 "Boundaries"), one thread per boundary-list
+// entry a -> b with successor b -> c: the midpoint row of edge (a, b) and the row 3/4 b + 1/8
+// (a + c) of vertex b (Eq. CC_boundary).
+template <bool FILL>
+__global__ void k_op_bnd(OpLevel L, int *cnt, const long long *rowptr, int *col, float *w, int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= L.B || failed(status)) return;
+    auto clampi = [](int x, int hi) { return min(max(x, 0), hi - 1); };
+    const int a = clampi(__ldg(L.bA + i), L.V), e = clampi(__ldg(L.bE + i), L.E);
+    const int s1 = clampi(__ldg(L.bS + i), L.B);
+    const int b = clampi(__ldg(L.bA + s1), L.V), c = clampi(__ldg(L.bA + clampi(__ldg(L.bS + s1), L.B)), L.V);
+    const int re = L.V + L.F + e;
+    const int ce[2] = {min(a, b), max(a, b)};
+    int cv[3] = {a, b, c};
+    float wv[3] = {0.125f, 0.75f, 0.125f};
+    for (int p = 1; p < 3; p++)            // sort the vertex row by column
+        for (int q = p; q > 0 && cv[q - 1] > cv[q]; q--) {
+            int tc = cv[q]; cv[q] = cv[q - 1]; cv[q - 1] = tc;
+            float tw = wv[q]; wv[q] = wv[q - 1]; wv[q - 1] = tw;
+        }
+    if (!FILL) {
+        cnt[re] = 2;
+        cnt[b] = 3;
+        return;
+    }
+    const long long pe = rowptr[re], pv = rowptr[b];
+    for (int k = 0; k < 2; k++) { col[pe + k] = ce[k]; w[pe + k] = 0.5f; }
+    for (int k = 0; k < 3; k++) { col[pv + k] = cv[k]; w[pv + k] = wv[k]; }
 }
 
 // ---------------------------------------------------------------- transpose
@@ -454,6 +491,9 @@ OpLevel op_level(TopoImpl &T, int l) {
     L.tw = A.tw;
     L.cr = A.cr;
     L.creases = T.scheme != ALSUB_SQRT3 && A.cr.cap > 0;
+    L.bnd = T.mesh->B > 0;
+    L.B = (int)A.B;
+    L.bA = A.bA; L.bE = A.bE; L.bS = A.bS;
     return L;
 }
 
@@ -463,9 +503,16 @@ alsub_status build_level(alsub_operator_s &O, int l, Csr &M) {
     const long long rows = T.L[l + 1].V;
     unsigned g = grid_for(L.F);
     cudaStream_t s = O.stream;
+    const unsigned gb = grid_for(L.B);
     return two_stage(O, M, rows, T.L[l].V,
-        [&] { k_op_rows<false><<<g, kBlock, 0, s>>>(L, O.cnt, nullptr, nullptr, nullptr, O.status); },
-        [&] { k_op_rows<true><<<g, kBlock, 0, s>>>(L, O.cnt, M.rowptr, M.col, M.w, O.status); });
+        [&] {
+            k_op_rows<false><<<g, kBlock, 0, s>>>(L, O.cnt, nullptr, nullptr, nullptr, O.status);
+            if (L.B) k_op_bnd<false><<<gb, kBlock, 0, s>>>(L, O.cnt, nullptr, nullptr, nullptr, O.status);
+        },
+        [&] {
+            k_op_rows<true><<<g, kBlock, 0, s>>>(L, O.cnt, M.rowptr, M.col, M.w, O.status);
+            if (L.B) k_op_bnd<true><<<gb, kBlock, 0, s>>>(L, O.cnt, M.rowptr, M.col, M.w, O.status);
+        });
 }
 
 alsub_status build_transpose(alsub_operator_s &O, const Csr &A, Csr &M) {

@@ -61,7 +61,7 @@ struct Job {
     Resident *res = nullptr;
     alsub_scheme scheme = ALSUB_CATMULL_CLARK;
     int levels = 0;
-    int V = 0, F = 0, K = 0;
+    int V = 0, F = 0, K = 0, B = 0;   // B: boundary edges the request states (MESH)
     std::vector<int32_t> off, fv, cv;
     std::vector<float> cs, P0;
     int64_t VL = 0;
@@ -137,6 +137,10 @@ alsub_status start(Slot &sl, Job &j) {
     if (j.kind == ALSUB_REQ_MESH) {
         st = alsub_mesh_create(j.scheme, j.V, j.F, j.off.data(), j.fv.data(), j.K,
                                j.K ? j.cv.data() : nullptr, j.K ? j.cs.data() : nullptr, sl.stream, &sl.mesh);
+        int64_t B = 0;
+        if (st == ALSUB_OK) alsub_mesh_boundary_edges(sl.mesh, &B);
+        if (st == ALSUB_OK && B != j.B)
+            st = report(ALSUB_ERR_INVALID_ARG, "server: the mesh's boundary edge count differs from the request's");
         if (st == ALSUB_OK) st = alsub_topology_create(sl.mesh, j.levels, sl.stream, &sl.topo);
         if (st != ALSUB_OK) return st;
     }
@@ -377,7 +381,9 @@ alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t
         for (int i = 0; i < K; i++) smax = std::max(smax, cs[i]);
         const int32_t nnz = off ? off[F] : F * (scheme == ALSUB_CATMULL_CLARK ? 4 : 3);
         size_t tb = 0;
-        st = alsub_plan_bytes(scheme, V, F, nnz, K, smax, levels, &tb);
+        int64_t B = 0;
+        alsub_mesh_boundary_edges(R->mesh, &B);
+        st = alsub_plan_bytes(scheme, V, F, nnz, (int32_t)B, K, smax, levels, &tb);
         std::lock_guard<std::mutex> g(S->mu);
         if (st == ALSUB_OK && S->used + tb > S->budget)
             st = report(ALSUB_ERR_OOM, "server: the resident topology does not fit the budget");
@@ -501,10 +507,11 @@ alsub_status alsub_serve_submit(alsub_server_t S, const alsub_request *r, uint64
                 if (x > smax) smax = x;   // NaN or negative values are refused when the request runs
         }
         size_t tb = 0;
-        alsub_status st = alsub_plan_bytes(j->scheme, j->V, j->F, nnz, j->K, smax, j->levels, &tb);
+        j->B = r->num_boundary_edges;
+        alsub_status st = alsub_plan_bytes(j->scheme, j->V, j->F, nnz, j->B, j->K, smax, j->levels, &tb);
         if (st != ALSUB_OK) return st;
         std::vector<int64_t> c(4 * ((size_t)j->levels + 1));
-        alsub_plan(j->scheme, j->V, j->F, nnz, j->levels, c.data());
+        alsub_plan_open(j->scheme, j->V, j->F, nnz, j->B, j->levels, c.data());
         j->VL = c[4 * (size_t)j->levels];
         j->need = tb + mesh_bytes(j->F, nnz, j->K) + align256(12 * (size_t)j->V) + align256(12 * (size_t)j->VL);
     } else {

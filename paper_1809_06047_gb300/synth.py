@@ -413,6 +413,19 @@ def sheet_cc(NX: int = 12, NY: int = 9, split_frac: float = 0.1, jitter: float =
     return _pack(faces, P, np.zeros((0, 2)), np.zeros(0))
 
 
+def open_box() -> dict:
+    """The unit cube without its z = +1 face: one boundary loop of four valence-3 vertices."""
+    m = cube()
+    return _pack([list(m["fv"][4 * r:4 * r + 4]) for r in range(5)], m["P"], np.zeros((0, 2)), np.zeros(0))
+
+
+def polygon(n: int = 4) -> dict:
+    """A single n-gon (one face, all vertices on the boundary, each in one face only)."""
+    t = 2.0 * math.pi * np.arange(n) / n
+    P = np.stack([np.cos(t), 0.8 * np.sin(t), 0.2 * np.sin(2 * t)], axis=1).astype(np.float32)
+    return _pack([list(range(n))], P, np.zeros((0, 2)), np.zeros(0))
+
+
 def holed_cc_mixed(N: int = 32, M: int = 24, holes: int = 6, seed: int = SEED_BASE + 8,
                    creases: bool = True) -> dict:
     """``torus_cc_mixed`` with ``holes`` faces cut out (each hole one boundary loop). The removed
