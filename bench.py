@@ -374,6 +374,55 @@ def batch_leg(w):
             "tuned": best}
 
 
+def boundary_leg(peak):
+    """Open Catmull-Clark mesh at the headline's size (Sec. 3.2 "Boundaries", build and repair): the
+    96 x 96 mixed torus with 64 faces cut out (64 boundary loops), 6 levels through alsub_subdivide,
+    against the closed headline mesh. Reports the refined faces/s, the last step's roofline and the
+    time of the boundary repair kernels."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = synth.holed_cc_mixed(96, 96, holes=64, seed=synth.SEED_BASE + 9)
+    L = 6
+    M = alsub.Mesh.from_dict(m, "cc")
+    B = M.boundary_edges
+    counts = [[int(x) for x in row] for row in alsub.plan("cc", m["V"], m["F"], len(m["fv"]), L, boundary=B)]
+    T = alsub.Topology(M, L, build=False)
+    P0 = torch.from_numpy(m["P"]).cuda()
+    PL = torch.empty((counts[L][0], 3), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        T.subdivide(P0, out=PL)
+    torch.cuda.synchronize()
+    T.status()
+    reps = 10
+    T.timings()
+    T.set_timing(reps)
+    T.subdivide(P0, out=PL)               # capture the timed graph
+    torch.cuda.synchronize()
+    T.timings()
+    ms = _events_ms(lambda: T.subdivide(P0, out=PL), reps, warmup=0)
+    stage_ms, calls, _ = T.timings()
+    T.set_timing(0)
+    T.status()
+    last_ms = stage_ms[L] / max(calls, 1)
+    alg = level_alg_bytes(counts, L - 1)
+    gbs = alg / (last_ms / 1e3) / 1e9
+    # the repair kernels alone: one per level over the boundary lists (2^l B entries)
+    S = alsub.Topology(M, L, build=True)
+    ev = _events_ms(lambda: S.refine_vertices(P0, out=PL), reps)
+    out = {"workload": f"holed_cc_mixed 96 x 96, 64 holes ({B} boundary edges, {m['F']} control faces), "
+                       f"{L} levels -> {counts[L][1]} quads, {B << (L - 1)} boundary edges on level {L - 1}",
+           "ms_per_step": ms, "refined_faces_per_s": counts[L][1] / (ms / 1e3),
+           "static_eval_ms": ev,
+           "stage_ms": [x / max(calls, 1) for x in stage_ms],
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "kernel": "cc level 5->6 fused build+eval step (BND variant) + boundary repair",
+                        "algorithmic_bytes": alg}}
+    S.close()
+    T.close()
+    M.close()
+    return out
+
+
 def traffic_for(kernel_key):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -559,7 +608,7 @@ def main():
         mix = synth.serving_requests()           # the 512-request mix and its 32 residents
     if rank == 0 and world == 1 and not args.no_extras:
         for key, leg in (("operator", lambda: operator_leg(peak)), ("adjoint", lambda: adjoint_leg(peak)),
-                         ("batch", lambda: batch_leg(mix))):
+                         ("batch", lambda: batch_leg(mix)), ("boundary", lambda: boundary_leg(peak))):
             try:
                 out[key] = leg()
             except Exception as e:  # noqa: BLE001 -- the headline line must still print
