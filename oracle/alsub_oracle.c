@@ -40,6 +40,13 @@
  *
  * Parity of the crease rule reading has no printed example in the paper: it is pinned only by its
  * limit cases (sigma = 0 smooth, sigma = inf cubic B-spline curve, sigma = 1 one sharp step).
+ *
+ * Patch mode (patch != 0, one level): the input is a patch cut out of a larger closed mesh, so
+ * every scheme accepts its open edges and every point whose rule would need what lies beyond the
+ * cut is NaN (an edge point of an open edge, a vertex point of a vertex on one, a sqrt(3) child
+ * vertex across one is -1); a crease touching the cut is dropped and the vertex points of its ends
+ * are NaN (their crease valency is unknown). All other points are exactly what the closed mesh
+ * gives, which lets a test check sampled outputs of a mesh too large for the oracle.
  */
 #include <math.h>
 #include <stdint.h>
@@ -82,6 +89,7 @@ typedef struct {
     int *ea, *eb;      /* edge endpoints, ea < eb */
     int *eo;           /* a corner of each edge (the boundary corner of a boundary edge) */
     int B;             /* boundary corners (corners without a twin) */
+    int patch;         /* patch mode: NaN instead of boundary rules */
     int *bo;           /* per vertex: its outgoing boundary corner, or -1 for an interior vertex */
 } hedge;
 
@@ -101,7 +109,8 @@ static int ekey_cmp(const void *x, const void *y) {
 }
 
 /* Build corners, twins and the lexicographic edge numbering. 2-manifolds, closed unless
- * open != 0 (then a corner whose edge has no second face gets twin -1). */
+ * open != 0 (then a corner whose edge has no second face gets twin -1); open == 2 (a patch) also
+ * accepts a vertex with several open fans (a pinch where the patch was cut). */
 static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv, int open) {
     memset(h, 0, sizeof(*h));
     h->V = V; h->F = F; h->nnz = off[F]; h->off = off; h->fv = fv;
@@ -161,6 +170,7 @@ static int hedge_build(hedge *h, int V, int F, const int *off, const int *fv, in
             if (h->tw[h->vb[q]] < 0) { nb++; start = h->vb[q]; }
         h->bo[v] = nb ? start : -1;
         h->B += nb;
+        if (nb > 1 && open == 2) continue;
         if (nb > 1) return OR_ERR_NONMANIFOLD;
         int x = start, steps = 0;
         if (nb == 0) {
@@ -221,10 +231,11 @@ typedef struct {
     double *S;         /* sum of incident crease sharpness */
     int *n1, *n2;      /* the first two crease neighbours (for k == 2) */
     float *s1, *s2;    /* their crease sharpness */
+    int *taint;        /* patch mode: the vertex lost a crease at the cut (its point is NaN) */
 } creases;
 
 static void creases_free(creases *c) {
-    free(c->es); free(c->k); free(c->S); free(c->n1); free(c->n2); free(c->s1); free(c->s2);
+    free(c->es); free(c->k); free(c->S); free(c->n1); free(c->n2); free(c->s1); free(c->s2); free(c->taint);
     memset(c, 0, sizeof(*c));
 }
 
@@ -235,13 +246,22 @@ static int creases_build(creases *c, const hedge *h, int K, const int *cv, const
     c->S = calloc((size_t)h->V, sizeof(double));
     c->n1 = malloc(sizeof(int) * (size_t)h->V); c->n2 = malloc(sizeof(int) * (size_t)h->V);
     c->s1 = calloc((size_t)h->V, sizeof(float)); c->s2 = calloc((size_t)h->V, sizeof(float));
-    if (!c->es || !c->k || !c->S || !c->n1 || !c->n2 || !c->s1 || !c->s2) return OR_ERR_OOM;
+    c->taint = calloc((size_t)h->V, sizeof(int));
+    if (!c->es || !c->k || !c->S || !c->n1 || !c->n2 || !c->s1 || !c->s2 || !c->taint) return OR_ERR_OOM;
     for (int i = 0; i < K; i++) {
         float s = cs[i];
         if (!(s >= 0.0f)) return OR_ERR_CREASE;        /* negative or NaN */
         int e = hedge_find_edge(h, cv[2 * i], cv[2 * i + 1]);
+        if (e < 0 && h->patch && cv[2 * i] >= 0 && cv[2 * i] < h->V && cv[2 * i + 1] >= 0 && cv[2 * i + 1] < h->V) {
+            c->taint[cv[2 * i]] = c->taint[cv[2 * i + 1]] = 1;   /* its faces lie beyond the cut */
+            continue;
+        }
         if (e < 0) return OR_ERR_CREASE;
-        if (h->bo[cv[2 * i]] >= 0 || h->bo[cv[2 * i + 1]] >= 0) return OR_ERR_BOUNDARY;
+        if (h->bo[cv[2 * i]] >= 0 || h->bo[cv[2 * i + 1]] >= 0) {
+            if (!h->patch) return OR_ERR_BOUNDARY;
+            c->taint[cv[2 * i]] = c->taint[cv[2 * i + 1]] = 1;
+            continue;
+        }
         if (c->es[e] != 0.0f) return OR_ERR_CREASE;    /* tagged twice */
         c->es[e] = s;
     }
@@ -424,7 +444,7 @@ static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o
         int c0 = h->eo[e], c1 = h->tw[c0];
         int a = h->ea[e], b = h->eb[e], r = h->cf[c0];
         if (c1 < 0) {                              /* boundary edge: its midpoint */
-            for (int d = 0; d < 3; d++) ep[3 * e + d] = 0.5 * (P[3 * a + d] + P[3 * b + d]);
+            for (int d = 0; d < 3; d++) ep[3 * e + d] = h->patch ? NAN : 0.5 * (P[3 * a + d] + P[3 * b + d]);
             continue;
         }
         int s = h->cf[c1];
@@ -438,7 +458,7 @@ static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o
         int nb, pb;
         if (boundary_neighbours(h, v, &nb, &pb)) {  /* Eq. CC_boundary */
             for (int d = 0; d < 3; d++)
-                Pn[3 * v + d] = 0.75 * P[3 * v + d] + 0.125 * (P[3 * pb + d] + P[3 * nb + d]);
+                Pn[3 * v + d] = h->patch ? NAN : 0.75 * P[3 * v + d] + 0.125 * (P[3 * pb + d] + P[3 * nb + d]);
             continue;
         }
         int nv = h->vo[v + 1] - h->vo[v];
@@ -454,6 +474,7 @@ static int cc_level(const hedge *h, const creases *cr, const double *P, onext *o
         for (int d = 0; d < 3; d++)
             Pn[3 * v + d] = ((nv - 3) * P[3 * v + d] + sf[d] / nv + 2.0 * sm[d] / nv) / nv;
         if (cr) crease_vertex(cr, P, v, Pn + 3 * v);
+        if (cr && cr->taint[v]) for (int d = 0; d < 3; d++) Pn[3 * v + d] = NAN;
     }
     /* 4. topology: face r -> c_r quads [v_j, e(j), f_r, e(j-1)] */
     for (int r = 0; r <= n; r++) o->off[r] = 4 * r;
@@ -541,6 +562,10 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
     for (int e = 0; e < E; e++) {
         int c0 = h->eo[e], c1 = h->tw[c0];
         int a = h->ea[e], b = h->eb[e];
+        if (c1 < 0) {                              /* patch mode only: beyond the cut */
+            for (int d = 0; d < 3; d++) ep[3 * e + d] = NAN;
+            continue;
+        }
         int k = h->fv[h->pv[c0]], l = h->fv[h->pv[c1]];
         for (int d = 0; d < 3; d++)
             ep[3 * e + d] = 0.375 * (P[3 * a + d] + P[3 * b + d]) + 0.125 * (P[3 * k + d] + P[3 * l + d]);
@@ -556,6 +581,7 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
         }
         for (int d = 0; d < 3; d++) Pn[3 * v + d] = (1.0 - nv * beta) * P[3 * v + d] + beta * sm[d];
         if (cr) crease_vertex(cr, P, v, Pn + 3 * v);
+        if (h->bo[v] >= 0 || (cr && cr->taint[v])) for (int d = 0; d < 3; d++) Pn[3 * v + d] = NAN;
     }
     /* topology: triangle (p_k, p_l, p_m) -> three corner triangles and the centre one */
     for (int r = 0; r <= 4 * F; r++) o->off[r] = 3 * r;
@@ -625,12 +651,13 @@ static int sqrt3_level(const hedge *h, const double *P, onext *o, coo *R) {
             for (int d = 0; d < 3; d++) sm[d] += P[3 * pj + d];
         }
         for (int d = 0; d < 3; d++) Pn[3 * v + d] = (1.0 - al) * P[3 * v + d] + al / nv * sm[d];
+        if (h->bo[v] >= 0) for (int d = 0; d < 3; d++) Pn[3 * v + d] = NAN;   /* patch mode only */
     }
     /* corner k of triangle i = (k, l, m) -> (p_k, f_{F(l,k)}, f_i) */
     for (int r = 0; r <= 3 * F; r++) o->off[r] = 3 * r;
     for (int x = 0; x < h->nnz; x++) {
         o->fv[3 * x + 0] = h->fv[x];
-        o->fv[3 * x + 1] = V + h->cf[h->tw[x]];
+        o->fv[3 * x + 1] = h->tw[x] < 0 ? -1 : V + h->cf[h->tw[x]];
         o->fv[3 * x + 2] = V + h->cf[x];
     }
     if (R) {
@@ -672,11 +699,12 @@ void or_free(oresult *r) {
  * Refine `levels` times. keep_all = 0 keeps only the last level; want_operator = 1 stores the
  * operator R_l of every kept level l < levels (COO, FP64).
  */
-int or_run(int scheme, int levels, int keep_all, int want_operator,
+int or_run(int scheme, int levels, int keep_all, int want_operator, int patch,
            int V, int F, const int *off, const int *fv, const double *P0,
            int K, const int *cv, const float *cs, oresult **out) {
     *out = NULL;
     if (scheme < 0 || scheme > 2 || levels < 0 || V <= 0 || F <= 0 || K < 0) return OR_ERR_ARG;
+    if (patch && (levels != 1 || want_operator)) return OR_ERR_ARG;
     if (off[0] != 0) return OR_ERR_ARG;
     for (int r = 0; r < F; r++) {
         int c = off[r + 1] - off[r];
@@ -711,8 +739,10 @@ int or_run(int scheme, int levels, int keep_all, int want_operator,
     int last = 0;
     for (int l = 0; l <= levels && !st; l++) {
         olevel *L = &res->L[last];
+        if (patch && l == levels) break;          /* a patch's child may reference the cut (-1) */
         hedge h;
-        st = hedge_build(&h, L->V, L->F, L->off, L->fv, scheme == OR_CC);
+        st = hedge_build(&h, L->V, L->F, L->off, L->fv, patch ? 2 : scheme == OR_CC);
+        h.patch = patch;
         if (st) { hedge_free(&h); break; }
         L->E = h.E;
         creases cr;

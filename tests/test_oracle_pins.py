@@ -506,3 +506,27 @@ def test_boundary_leaves_far_interior_unchanged():
     # and the cut does change the faces next to it
     r = 0
     assert not np.array_equal(a["P"][a["fv"][:4 * q]], b["P"][b["fv"][:4 * q]])
+
+
+@pytest.mark.parametrize("scheme,mesh", [
+    ("cc", synth.torus_cc_mixed(20, 18, crease_frac=0.1, seed=36)),
+    ("loop", synth.torus_tri(16, 14, seed=37)),
+    ("sqrt3", synth.torus_tri(14, 12, seed=38, creases=False)),
+])
+def test_patch_mode_matches_whole_mesh(scheme, mesh):
+    """Patch mode (used for sampled checks of meshes too large for the oracle): the children of
+    faces two rings inside a patch equal the whole mesh's children exactly, and points reaching
+    beyond the cut are NaN."""
+    from tests import patch
+    whole = oracle.subdivide(mesh, 1, scheme)
+    lvl0 = dict(whole[0], P=mesh["P"].astype(np.float64))
+    faces = patch.sample_faces(mesh["F"], 12, seed=1)
+    pm, local = patch.extract(lvl0, faces)
+    assert pm["F"] < mesh["F"]
+    part = oracle.subdivide(pm, 1, scheme, patch=True)
+    for r, q in zip(faces, local):
+        a = whole[1]["fv"][patch.child_corners(scheme, whole[0]["off"], int(r))]
+        b = part[1]["fv"][patch.child_corners(scheme, pm["off"], int(q))]
+        assert np.all(b >= 0)
+        np.testing.assert_array_equal(whole[1]["P"][a], part[1]["P"][b])
+    assert np.isnan(part[1]["P"]).any()          # the cut is there and marked
