@@ -423,6 +423,44 @@ def boundary_leg(peak):
     return out
 
 
+def ordering_leg():
+    """Control-mesh order (the reordering question of Sec. 4.5): the headline mesh with its vertex
+    ids and face order shuffled (seeded) against the generator's order, same call and levels. The
+    refined numbering keeps each face's children contiguous, so the order only matters on the
+    first levels."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = synth.workload(DEFAULT_WORKLOAD)
+    rng = np.random.default_rng(synth.SEED_BASE & 0xFFFF)
+    pv = rng.permutation(m["V"])                  # new id of each vertex
+    order = rng.permutation(m["F"])
+    off, fv = m["off"], m["fv"]
+    faces = [pv[fv[off[r]:off[r + 1]]] for r in order]
+    noff = np.zeros(m["F"] + 1, np.int32)
+    noff[1:] = np.cumsum([len(f) for f in faces])
+    sh = dict(m, off=noff, fv=np.concatenate(faces).astype(np.int32),
+              P=np.ascontiguousarray(m["P"][np.argsort(pv)]), crease_verts=pv[m["crease_verts"]].astype(np.int32))
+    out = {"workload": f"{DEFAULT_WORKLOAD}, generator order vs shuffled vertex ids and face order"}
+    for key, mesh in (("ordered", m), ("shuffled", sh)):
+        M = alsub.Mesh.from_dict(mesh, "cc")
+        T = alsub.Topology(M, m["levels"], build=False)
+        P0 = torch.from_numpy(np.ascontiguousarray(mesh["P"])).cuda()
+        PL = torch.empty((T.counts[-1]["V"], 3), dtype=torch.float32, device="cuda")
+        T.set_timing(10)
+        T.subdivide(P0, out=PL)
+        torch.cuda.synchronize()
+        T.timings()
+        ms = _events_ms(lambda: T.subdivide(P0, out=PL), 10, warmup=0)
+        st, calls, _ = T.timings()
+        T.set_timing(0)
+        T.status()
+        out[key] = {"ms_per_step": ms, "stage_ms": [x / max(calls, 1) for x in st]}
+        T.close()
+        M.close()
+    out["slowdown"] = out["shuffled"]["ms_per_step"] / out["ordered"]["ms_per_step"]
+    return out
+
+
 def traffic_for(kernel_key):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -608,7 +646,8 @@ def main():
         mix = synth.serving_requests()           # the 512-request mix and its 32 residents
     if rank == 0 and world == 1 and not args.no_extras:
         for key, leg in (("operator", lambda: operator_leg(peak)), ("adjoint", lambda: adjoint_leg(peak)),
-                         ("batch", lambda: batch_leg(mix)), ("boundary", lambda: boundary_leg(peak))):
+                         ("batch", lambda: batch_leg(mix)), ("boundary", lambda: boundary_leg(peak)),
+                         ("ordering", ordering_leg)):
             try:
                 out[key] = leg()
             except Exception as e:  # noqa: BLE001 -- the headline line must still print

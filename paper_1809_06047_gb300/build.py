@@ -33,8 +33,17 @@ def _deps() -> list[str]:
     return deps + [os.path.abspath(__file__)]
 
 
+STAMP = os.path.join(BUILD, "flags.txt")
+
+
 def stale() -> bool:
+    """The library is missing, older than a source, or was built with other flags."""
     if not os.path.exists(LIB):
+        return True
+    try:
+        if open(STAMP).read() != " ".join(NVCC_FLAGS):
+            return True
+    except OSError:
         return True
     t = os.path.getmtime(LIB)
     return any(os.path.getmtime(d) > t for d in _deps())
@@ -66,6 +75,8 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(STAMP, "w") as f:
+        f.write(" ".join(NVCC_FLAGS))
     return LIB
 
 
