@@ -219,6 +219,22 @@ alsub_status alsub_subdivide(alsub_topology_t topo, const float *P0_dev, float *
                              void *scratch_dev, void *stream);
 
 /*
+ * alsub_subdivide with the control positions and the result in HOST memory: the call copies
+ * P0_host (float[3 * V_0]) into page-locked staging before it returns (the caller may reuse the
+ * buffer at once), uploads it, runs the dynamic-topology subdivision into one of two device
+ * buffers the handle owns, and downloads the result into PL_host (float[3 * V_levels];
+ * page-locked memory is written by DMA, pageable memory through the runtime's staging). `stream`
+ * completes when PL_host holds the result, so synchronising it (or an event recorded on it)
+ * publishes the result. The upload and eval run on a private stream and the download on another:
+ * call k + 1's upload and eval overlap call k's download (double-buffered on the device), so a
+ * sequence of calls moves at the pace of the slower of the two. A caller must not read PL_host of
+ * call k while a later call that writes the same buffer may be in flight. The handle's device
+ * buffers (2 x 12 V_levels bytes plus 12 V_0) are allocated at the first call and freed with the
+ * handle. Errors: INVALID_ARG, OOM, DEVICE and those of alsub_subdivide.
+ */
+alsub_status alsub_subdivide_host(alsub_topology_t topo, const float *P0_host, float *PL_host, void *stream);
+
+/*
  * Subdivision operator (Sec. 3.5 "Single SpMV evaluation", Eq. singleSpMV): R_l maps the positions
  * of level l to those of level l+1 (P_{l+1} = R_l P_l), R = R_{L-1} ... R_0 maps the control mesh
  * to the last level. Built from a built topology in the paper's two stages (count the non-zeros

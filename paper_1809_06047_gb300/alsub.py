@@ -228,6 +228,30 @@ class Topology:
         """alsub_subdivide: rebuild the topology and refine the vertices, fused per level."""
         return self._run(lib().alsub_subdivide, P0, out, scratch, stream)
 
+    def subdivide_host(self, P0, out=None, stream=None):
+        """alsub_subdivide_host: host positions in, host positions out (CPU tensors or numpy
+        arrays, float32, contiguous; page-locked tensors are copied by DMA). The result is in
+        ``out`` once ``stream`` (default: torch's current stream) has completed."""
+        VL = self.counts[-1]["V"]
+        if out is None:
+            out = torch.empty((VL, 3), dtype=torch.float32).pin_memory()
+        for a in (P0, out):
+            if isinstance(a, torch.Tensor):
+                assert not a.is_cuda and a.dtype == torch.float32 and a.is_contiguous()
+            else:
+                assert a.dtype == np.float32 and a.flags["C_CONTIGUOUS"]
+        def size(a):
+            return a.size if isinstance(a, np.ndarray) else a.numel()
+
+        assert size(P0) == 3 * self.counts[0]["V"] and size(out) == 3 * VL
+
+        def ptr(a):
+            return a.data_ptr() if isinstance(a, torch.Tensor) else a.ctypes.data
+
+        _check(lib().alsub_subdivide_host(self._h, ctypes.c_void_p(ptr(P0)), ctypes.c_void_p(ptr(out)),
+                                          ctypes.c_void_p(_stream(stream))))
+        return out
+
 
 class Operator:
     """alsub_build_operator and friends: R_l per level and/or the composite R = R_{L-1}...R_0."""

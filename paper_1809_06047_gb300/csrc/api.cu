@@ -302,9 +302,10 @@ void ensure_side(TopoImpl &T);
 // the previous call's pointers, replayed on `s` while they stay the same, so a repeated call costs
 // one graph launch instead of one launch per kernel and memset. One-off calls and graphs that
 // cannot be made launch the kernels directly, on `s` alone (the parallel crease branch of a
-// subdivide call, with its stream and events, is made only for a graph).
+// subdivide call, with its stream and events, is made only for a graph). Calls on the handle's
+// own buffers (own_buffers) are captured at once: they recur by construction.
 alsub_status run_call(TopoImpl &T, int kind, const float *P0, float *PL, void *scratch, cudaStream_t s,
-                      Body body) {
+                      Body body, bool own_buffers = false) {
     const bool timed = T.tcap > 0;
     CallGraph *G = nullptr, *lru = &T.graphs[kind][0];
     for (CallGraph &g : T.graphs[kind]) {
@@ -315,7 +316,7 @@ alsub_status run_call(TopoImpl &T, int kind, const float *P0, float *PL, void *s
         const void **prev = T.last[kind];
         const bool repeat = prev[0] == P0 && prev[1] == PL && prev[2] == scratch;
         prev[0] = P0; prev[1] = PL; prev[2] = scratch;
-        if (!repeat) {              // a one-off call: plain launches, no capture cost
+        if (!repeat && !own_buffers) {   // a one-off call: plain launches, no capture cost
             body(T, P0, PL, scratch, s);
             return finish("refine call");
         }
@@ -416,6 +417,45 @@ void ensure_side(TopoImpl &T) {
     }
 }
 
+
+void free_hostio(TopoImpl &T) {
+    TopoImpl::HostIO &io = T.io;
+    if (io.cs) cudaStreamSynchronize(io.cs);
+    if (io.ds) cudaStreamSynchronize(io.ds);
+    for (int b = 0; b < 2; b++) {
+        if (io.dPL[b]) cudaFree(io.dPL[b]);
+        if (io.hP0[b]) cudaFreeHost(io.hP0[b]);
+        for (cudaEvent_t e : {io.up[b], io.done[b], io.copied[b]})
+            if (e) cudaEventDestroy(e);
+    }
+    if (io.dP0) cudaFree(io.dP0);
+    if (io.cs) cudaStreamDestroy(io.cs);
+    if (io.ds) cudaStreamDestroy(io.ds);
+    io = TopoImpl::HostIO();
+    cudaGetLastError();
+}
+
+// Streams, events and buffers of alsub_subdivide_host, made at its first call (all or nothing).
+alsub_status ensure_hostio(TopoImpl &T) {
+    TopoImpl::HostIO &io = T.io;
+    if (io.ready) return ALSUB_OK;
+    const size_t n0 = 12 * (size_t)T.L[0].V, nl = 12 * (size_t)T.L[T.levels].V;
+    bool ok = cudaStreamCreateWithFlags(&io.cs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaStreamCreateWithFlags(&io.ds, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMalloc(&io.dP0, n0) == cudaSuccess;
+    for (int b = 0; ok && b < 2; b++)
+        ok = cudaMalloc(&io.dPL[b], nl) == cudaSuccess && cudaMallocHost(&io.hP0[b], n0) == cudaSuccess &&
+             cudaEventCreateWithFlags(&io.up[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&io.done[b], cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&io.copied[b], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        free_hostio(T);
+        return fail(ALSUB_ERR_OOM, "host-buffer subdivision: allocation failed");
+    }
+    io.ready = true;
+    return ALSUB_OK;
+}
 
 // Dynamic topology. The crease analysis of level l needs level l's adjacency but no positions, so
 // it runs on a side branch beside the build + eval of level l (forked when the step that built
@@ -804,6 +844,7 @@ alsub_status alsub_topology_timings(alsub_topology_t h, double *ms, int32_t *cal
 
 alsub_status alsub_topology_destroy(alsub_topology_t h) {
     if (!h) return ALSUB_OK;
+    free_hostio(h->t);
     free_events(h->t);
     drop_graphs(h->t);
     if (h->t.cap) cudaStreamDestroy(h->t.cap);
@@ -851,6 +892,33 @@ alsub_status alsub_refine_vertices(alsub_topology_t h, const float *P0, float *P
     alsub_status st = run_call(T, 0, P0, PL, scratch, (cudaStream_t)stream, refine_body);
     if (T.tcap && T.levels > 0) T.tcalls++;
     return st;
+}
+
+alsub_status alsub_subdivide_host(alsub_topology_t h, const float *P0_host, float *PL_host, void *stream) {
+    if (!h || !P0_host || !PL_host) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    TopoImpl &T = h->t;
+    alsub_status st = ensure_hostio(T);
+    if (st != ALSUB_OK) return st;
+    TopoImpl::HostIO &io = T.io;
+    const int b = (int)(io.calls & 1);
+    const size_t n0 = 12 * (size_t)T.L[0].V, nl = 12 * (size_t)T.L[T.levels].V;
+    // the staging buffer was last read by the upload of call k - 2
+    CK(cudaEventSynchronize(io.up[b]));
+    memcpy(io.hP0[b], P0_host, n0);
+    CK(cudaMemcpyAsync(io.dP0, io.hP0[b], n0, cudaMemcpyHostToDevice, io.cs));
+    CK(cudaEventRecord(io.up[b], io.cs));
+    CK(cudaStreamWaitEvent(io.cs, io.copied[b], 0));     // output buffer b: call k - 2's download done
+    st = run_call(T, 1, io.dP0, io.dPL[b], nullptr, io.cs, subdivide_body, true);   // the handle's buffers recur
+    if (T.tcap) T.tcalls++;
+    if (st != ALSUB_OK) return st;
+    T.built = true;
+    CK(cudaEventRecord(io.done[b], io.cs));
+    CK(cudaStreamWaitEvent(io.ds, io.done[b], 0));
+    CK(cudaMemcpyAsync(PL_host, io.dPL[b], nl, cudaMemcpyDeviceToHost, io.ds));
+    CK(cudaEventRecord(io.copied[b], io.ds));
+    CK(cudaStreamWaitEvent((cudaStream_t)stream, io.copied[b], 0));
+    io.calls++;
+    return ALSUB_OK;
 }
 
 alsub_status alsub_subdivide(alsub_topology_t h, const float *P0, float *PL, void *scratch,

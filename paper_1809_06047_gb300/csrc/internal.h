@@ -125,6 +125,15 @@ struct TopoImpl {
     // build + eval step (fork after the step that built level l, join before the crease fix)
     cudaStream_t side = nullptr;
     std::vector<cudaEvent_t> fork_ev, join_ev;   // levels + 1 each
+    // alsub_subdivide_host: upload + eval stream, download stream, device input, two device
+    // outputs, two page-locked input stagings and their events (indexed by call parity)
+    struct HostIO {
+        cudaStream_t cs = nullptr, ds = nullptr;
+        float *dP0 = nullptr, *dPL[2] = {nullptr, nullptr}, *hP0[2] = {nullptr, nullptr};
+        cudaEvent_t up[2] = {nullptr, nullptr}, done[2] = {nullptr, nullptr}, copied[2] = {nullptr, nullptr};
+        unsigned long long calls = 0;
+        bool ready = false;
+    } io;
 };
 
 // ---------------------------------------------------------------- launchers
