@@ -141,6 +141,38 @@ alsub_status alsub_mesh_destroy(alsub_mesh_t mesh);
  * sqrt(3) meshes (those must be closed). Host only. Errors: INVALID_ARG. */
 alsub_status alsub_mesh_boundary_edges(alsub_mesh_t mesh, int64_t *boundary_edges);
 
+/* Scheme, vertex, face, corner and crease counts of a mesh (host only; any pointer may be NULL).
+ * Errors: INVALID_ARG. */
+alsub_status alsub_mesh_info(alsub_mesh_t mesh, int32_t *scheme, int64_t *num_verts, int64_t *num_faces,
+                             int64_t *nnz, int64_t *num_creases);
+
+/*
+ * Selective subdivision (Sec. 3.4, Fig. module_selective): extract the region around selected
+ * vertices of level `level` (0 = the control mesh) of a built Catmull-Clark topology as a new mesh,
+ * which the ordinary calls then refine (it is open: its cut is refined by the boundary rules, so
+ * only faces about two rings inside it match the uniform refinement).
+ *   select_dev: uint8[V_level] on the device, 1 = selected; NULL selects the extraordinary vertices
+ *               (valence != 4, Eq. vo, among the vertices on no boundary edge) and both ends of every
+ *               live crease of the level.
+ *   rings >= 1: propagation steps q = M^T x (faces with a selected vertex), x = M q (their vertices);
+ *               the mesh keeps the faces of the last q and their vertices, in their original order
+ *               (M' = X M X-ring with X, X-ring rows / columns of the identity), and the creases
+ *               whose both ends have every face around them kept.
+ * The new handle owns its arrays and the maps (alsub_mesh_extract_maps); positions follow with
+ * alsub_mesh_gather. Synchronises `stream` (the sizes are read back). Errors: INVALID_ARG (bad
+ * level or rings, topology not built, nothing selected), UNSUPPORTED (Loop, sqrt(3)), OOM, DEVICE.
+ */
+alsub_status alsub_topology_extract(alsub_topology_t topo, int32_t level, const uint8_t *select_dev,
+                                    int32_t rings, void *stream, alsub_mesh_t *out);
+
+/* Device maps of an extracted mesh (owned by it): vmap[i] = the source level's vertex of vertex i
+ * (int32[V']), fmap[f] = the source face of face f (int32[F']). Errors: INVALID_ARG. */
+alsub_status alsub_mesh_extract_maps(alsub_mesh_t mesh, const int32_t **vmap_dev, const int32_t **fmap_dev);
+
+/* P' = X P for an extracted mesh: row i of out_dev (float[3 V']) = row vmap[i] of P_dev (the
+ * source level's positions, float[3 V_level]); enqueued on `stream`. Errors: INVALID_ARG, DEVICE. */
+alsub_status alsub_mesh_gather(alsub_mesh_t mesh, const float *P_dev, float *out_dev, void *stream);
+
 /*
  * Build the topology of `levels` uniform refinement steps (the build step of Fig. module_core,
  * Sec. 3.5 "Static topology"): for every level the face table M_{l+1}, the per-corner edge

@@ -139,3 +139,81 @@ def operator_matrix(level: dict, n_cols: int):
     import scipy.sparse as sp
     n_rows = int(level["R_rows"].max()) + 1 if level["R_rows"].size else 0
     return sp.csr_matrix((level["R_w"], (level["R_rows"], level["R_cols"])), shape=(n_rows, n_cols))
+
+
+def extract(mesh: dict, select=None, rings: int = 1, scheme: str = "cc") -> dict:
+    """Extraction of selective subdivision (Sec. 3.4), written from its definition.
+
+    The selected vertices x_0 (bool[V]; default: the extraordinary vertices, valence != 4 for
+    Catmull-Clark or != 6 for Loop / sqrt(3) with valence = corners at the vertex, Eq. vo, among the
+    vertices on no boundary edge, and both ends of every crease with sigma > 0) are propagated ``rings`` times: q_i = M^T x_i marks the faces
+    with a selected vertex, x_{i+1} = M q_i the vertices of those faces. The extracted mesh keeps
+    the faces of the last q (X-ring, columns of the identity: fmap, increasing) and their vertices
+    (X, rows of the identity: vmap, increasing), M' = X M X-ring with the vertices renumbered, P' = X P.
+    Where the region touches itself at a vertex only (two fans of kept faces there), every face
+    around that vertex is kept too, repeatedly, so the extracted mesh is a manifold.
+    A crease is kept when every face around both its ends is kept (so none touches the cut).
+    """
+    V, F = int(mesh["V"]), int(mesh["F"])
+    off = np.asarray(mesh["off"], dtype=np.int64)
+    fv = np.asarray(mesh["fv"], dtype=np.int64)
+    cv = np.asarray(mesh.get("crease_verts", np.zeros((0, 2))), dtype=np.int64).reshape(-1, 2)
+    cs = np.asarray(mesh.get("crease_sharp", np.zeros(0)), dtype=np.float32).reshape(-1)
+    valence = np.bincount(fv, minlength=V)
+    if select is None:
+        # vertices on a boundary edge (an edge whose reverse direction is in no face) are not
+        # extraordinary in this sense
+        nxt = np.arange(1, fv.size + 1)
+        nxt[off[1:] - 1] = off[:-1]
+        a, b = fv, fv[nxt]
+        fwd = set(zip(a.tolist(), b.tolist()))
+        on_bnd = np.zeros(V, dtype=bool)
+        for u, w in fwd:
+            if (w, u) not in fwd:
+                on_bnd[u] = on_bnd[w] = True
+        x = (valence != (4 if scheme == "cc" else 6)) & ~on_bnd
+        live = cs > 0
+        x[cv[live, 0]] = True
+        x[cv[live, 1]] = True
+    else:
+        x = np.asarray(select).astype(bool).copy()
+    face_of = np.repeat(np.arange(F), np.diff(off))
+    nxt = np.arange(1, fv.size + 1)
+    nxt[off[1:] - 1] = off[:-1]
+    q = np.zeros(F, dtype=bool)
+    for _ in range(rings):
+        q = np.zeros(F, dtype=bool)
+        q[face_of[x[fv]]] = True                    # q = M^T x
+        x = np.zeros(V, dtype=bool)
+        x[fv[q[face_of]]] = True                    # x = M q
+    # a vertex where the region touches itself (two or more fans of kept faces: as many boundary
+    # edges of the region leave it) takes all its faces, until no such vertex is left
+    while True:
+        kc = np.flatnonzero(q[face_of])
+        fwd = set(zip(fv[kc].tolist(), fv[nxt[kc]].tolist()))
+        out_b = np.zeros(V, dtype=np.int64)
+        for u, w in fwd:
+            if (w, u) not in fwd:
+                out_b[u] += 1
+        pinch = out_b >= 2
+        if not pinch.any():
+            break
+        q[face_of[pinch[fv]]] = True
+    x = np.zeros(V, dtype=bool)
+    x[fv[q[face_of]]] = True
+    fmap = np.flatnonzero(q)
+    vmap = np.flatnonzero(x)
+    new_id = np.full(V, -1, dtype=np.int64)
+    new_id[vmap] = np.arange(vmap.size)
+    corners = np.flatnonzero(q[face_of])
+    noff = np.zeros(fmap.size + 1, dtype=np.int64)
+    noff[1:] = np.cumsum(np.diff(off)[fmap])
+    kept_faces_at = np.bincount(fv[corners], minlength=V)
+    inner = kept_faces_at == valence
+    keep_c = (cs > 0) & inner[cv[:, 0]] & inner[cv[:, 1]] if cs.size else np.zeros(0, dtype=bool)
+    out = dict(V=int(vmap.size), F=int(fmap.size), off=noff.astype(np.int32),
+               fv=new_id[fv[corners]].astype(np.int32), vmap=vmap.astype(np.int32), fmap=fmap.astype(np.int32),
+               crease_verts=new_id[cv[keep_c]].astype(np.int32).reshape(-1, 2), crease_sharp=cs[keep_c])
+    if "P" in mesh:
+        out["P"] = np.asarray(mesh["P"])[vmap]
+    return out

@@ -93,6 +93,37 @@ class Mesh:
         self.boundary_edges = int(b.value)
 
     @classmethod
+    def _wrap(cls, h: ctypes.c_void_p) -> "Mesh":
+        """A Mesh object around a handle the library made (an extracted mesh)."""
+        self = cls.__new__(cls)
+        self._h = h
+        sch, V, F, nnz, K = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().alsub_mesh_info(h, ctypes.byref(sch), ctypes.byref(V), ctypes.byref(F), ctypes.byref(nnz),
+                                     ctypes.byref(K)))
+        self.scheme = {v: k for k, v in SCHEMES.items()}[sch.value]
+        self.V, self.F, self.nnz, self.K = V.value, F.value, nnz.value, K.value
+        b = ctypes.c_int64()
+        _check(lib().alsub_mesh_boundary_edges(h, ctypes.byref(b)))
+        self.boundary_edges = int(b.value)
+        return self
+
+    def maps(self):
+        """(vertex map int32[V], face map int32[F]) of an extracted mesh: source vertex / face ids."""
+        vm, fm = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().alsub_mesh_extract_maps(self._h, ctypes.byref(vm), ctypes.byref(fm)))
+        return (copy_to_host(vm.value, 4 * self.V, np.int32, self.V),
+                copy_to_host(fm.value, 4 * self.F, np.int32, self.F))
+
+    def gather(self, P: torch.Tensor, out=None, stream=None) -> torch.Tensor:
+        """alsub_mesh_gather: this extracted mesh's rows of the source level's positions."""
+        assert P.is_cuda and P.dtype == torch.float32 and P.is_contiguous()
+        if out is None:
+            out = torch.empty((self.V, 3), dtype=torch.float32, device=P.device)
+        _check(lib().alsub_mesh_gather(self._h, ctypes.c_void_p(P.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                       ctypes.c_void_p(_stream(stream))))
+        return out
+
+    @classmethod
     def from_dict(cls, m: dict, scheme: str | None = None, stream=None) -> "Mesh":
         return cls(scheme or m.get("scheme", "cc"), m["V"], m["F"], m["fv"], m["off"],
                    m.get("crease_verts"), m.get("crease_sharp"), stream)
@@ -227,6 +258,17 @@ class Topology:
     def subdivide(self, P0: torch.Tensor, out=None, scratch=None, stream=None) -> torch.Tensor:
         """alsub_subdivide: rebuild the topology and refine the vertices, fused per level."""
         return self._run(lib().alsub_subdivide, P0, out, scratch, stream)
+
+    def extract(self, level: int = 0, select: torch.Tensor | None = None, rings: int = 2, stream=None) -> Mesh:
+        """alsub_topology_extract (selective subdivision, Sec. 3.4): the region of a level around
+        the selected vertices (uint8 device mask; None: extraordinary vertices and crease ends)."""
+        h = ctypes.c_void_p()
+        sel = None if select is None else ctypes.c_void_p(select.data_ptr())
+        if select is not None:
+            assert select.is_cuda and select.dtype == torch.uint8 and select.numel() == self.counts[level]["V"]
+        _check(lib().alsub_topology_extract(self._h, int(level), sel, int(rings), ctypes.c_void_p(_stream(stream)),
+                                            ctypes.byref(h)))
+        return Mesh._wrap(h)
 
     def subdivide_host(self, P0, out=None, stream=None):
         """alsub_subdivide_host: host positions in, host positions out (CPU tensors or numpy

@@ -702,6 +702,59 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
     return ALSUB_OK;
 }
 
+alsub_status alsub_mesh_info(alsub_mesh_t h, int32_t *scheme, int64_t *V, int64_t *F, int64_t *nnz,
+                             int64_t *K) {
+    if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL mesh");
+    if (scheme) *scheme = h->m.scheme;
+    if (V) *V = h->m.V;
+    if (F) *F = h->m.F;
+    if (nnz) *nnz = h->m.nnz;
+    if (K) *K = h->m.K;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_topology_extract(alsub_topology_t topo, int32_t level, const uint8_t *select_dev,
+                                    int32_t rings, void *stream, alsub_mesh_t *out) {
+    if (!topo || !out || rings < 1) return fail(ALSUB_ERR_INVALID_ARG, "bad extraction arguments");
+    *out = nullptr;
+    TopoImpl &T = topo->t;
+    if (level < 0 || level > T.levels) return fail(ALSUB_ERR_INVALID_ARG, "bad level");
+    if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
+    if (T.scheme != ALSUB_CATMULL_CLARK)
+        return fail(ALSUB_ERR_UNSUPPORTED, "extraction is for Catmull-Clark (the extracted mesh is open)");
+    alsub_mesh_s *h = new (std::nothrow) alsub_mesh_s();
+    if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
+    cudaStream_t s = (cudaStream_t)stream;
+    alsub_status st = extract_level(T, level, select_dev, rings, s, h->m);
+    long long B = 0;
+    bool crease_at_boundary = false;
+    if (st == ALSUB_OK) st = mesh_boundary_scan(h->m, s, &B, &crease_at_boundary);
+    if (st == ALSUB_OK && crease_at_boundary)
+        st = fail(ALSUB_ERR_UNSUPPORTED, "an extracted crease touches the cut");
+    if (st != ALSUB_OK) {
+        alsub_mesh_destroy(h);
+        return st;
+    }
+    h->m.B = (int)B;
+    *out = h;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_mesh_extract_maps(alsub_mesh_t h, const int32_t **vmap_dev, const int32_t **fmap_dev) {
+    if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL mesh");
+    if (!h->m.d_vmap) return fail(ALSUB_ERR_INVALID_ARG, "not an extracted mesh");
+    if (vmap_dev) *vmap_dev = h->m.d_vmap;
+    if (fmap_dev) *fmap_dev = h->m.d_fmap;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_mesh_gather(alsub_mesh_t h, const float *P_dev, float *out_dev, void *stream) {
+    if (!h || !P_dev || !out_dev) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
+    if (!h->m.d_vmap) return fail(ALSUB_ERR_INVALID_ARG, "not an extracted mesh");
+    gather_rows(h->m.V, h->m.d_vmap, P_dev, out_dev, (cudaStream_t)stream);
+    return finish("alsub_mesh_gather");
+}
+
 alsub_status alsub_mesh_boundary_edges(alsub_mesh_t h, int64_t *boundary_edges) {
     if (!h || !boundary_edges) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
     *boundary_edges = h->m.B;
@@ -711,10 +764,12 @@ alsub_status alsub_mesh_boundary_edges(alsub_mesh_t h, int64_t *boundary_edges) 
 alsub_status alsub_mesh_destroy(alsub_mesh_t h) {
     if (!h) return ALSUB_OK;
     MeshImpl &M = h->m;
-    cudaFreeAsync(M.d_off, M.stream);
-    cudaFreeAsync(M.d_fv, M.stream);
+    if (M.d_off) cudaFreeAsync(M.d_off, M.stream);
+    if (M.d_fv) cudaFreeAsync(M.d_fv, M.stream);
     if (M.d_cv) cudaFreeAsync(M.d_cv, M.stream);
     if (M.d_cs) cudaFreeAsync(M.d_cs, M.stream);
+    if (M.d_vmap) cudaFreeAsync(M.d_vmap, M.stream);
+    if (M.d_fmap) cudaFreeAsync(M.d_fmap, M.stream);
     delete h;
     return finish("alsub_mesh_destroy");
 }

@@ -60,6 +60,8 @@ struct MeshImpl {
     int *d_cv = nullptr;       // 2K
     float *d_cs = nullptr;     // K
     int B = 0;                 // boundary edges (Catmull-Clark open meshes)
+    int *d_vmap = nullptr;     // extracted meshes (selective subdivision): kept vertex -> source vertex
+    int *d_fmap = nullptr;     //                                           kept face -> source face
     cudaStream_t stream = nullptr;
 };
 
@@ -156,6 +158,15 @@ void level0_creases(TopoImpl &T, cudaStream_t s);
 // Boundary edges of a Catmull-Clark control mesh (corners whose reverse edge is in no face) and
 // whether a crease touches a boundary vertex; synchronises `s`.
 alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary);
+// Vertices on a boundary edge (flag 1) of a face table (off == nullptr: uniform quads).
+alsub_status level_boundary_flags(int V, int F, long long nnz, const int *off, const int *fv, int *flag,
+                                  cudaStream_t s);
+// Extraction of selective subdivision (Sec. 3.4) from level `level` of a built topology into a new
+// mesh (device arrays, maps, creases; B not yet set); synchronises `s`.
+alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, int rings, cudaStream_t s,
+                           MeshImpl &out);
+// P' = X P: rows vmap[i] of P into row i of out (xyz rows).
+void gather_rows(int n, const int *vmap, const float *P, float *out, cudaStream_t s);
 // Boundary repair of one Catmull-Clark step (Sec. 3.2 "Boundaries", Fig. module_boundary): with
 // positions, overwrite the boundary edge points (midpoints) and boundary vertices (Eq.
 // CC_boundary) of level l + 1; with `list`, write level l + 1's boundary list.

@@ -187,14 +187,14 @@ __global__ void k_bnd0_link(int B, const int *__restrict__ count, const int *__r
 __global__ void k_mb_insert(int F, const int *__restrict__ off, const int *__restrict__ fv, DirTable tab) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= F) return;
-    const int s = off[r], c = off[r + 1] - s;
+    const int s = off ? off[r] : 4 * r, c = off ? off[r + 1] - s : 4;
     for (int j = 0; j < c; j++) dir_insert(tab, fv[s + j], fv[s + (j + 1 == c ? 0 : j + 1)], s + j);
 }
 __global__ void k_mb_count(int F, const int *__restrict__ off, const int *__restrict__ fv, DirTable tab,
                            int *bv, int *out) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= F) return;
-    const int s = off[r], c = off[r + 1] - s;
+    const int s = off ? off[r] : 4 * r, c = off ? off[r + 1] - s : 4;
     for (int j = 0; j < c; j++) {
         const int a = fv[s + j], b = fv[s + (j + 1 == c ? 0 : j + 1)];
         if (dir_find(tab, b, a) < 0) {
@@ -269,14 +269,39 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     k_eid<<<nb, kBlock, 0, s>>>(nnz, T.own0, T.pos, T.eid);
     k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.pv0, T.e0count, E0, L0.ce, T.eo0,
                                              T.rn0, T.status);
-    if (M.B > 0) {
-        // the per-corner edge-id temporaries are dead: they map boundary corners to entries
+    if (L0.B > 0) {
+        // (the list exists when a step follows: levels >= 1.) The per-corner edge-id temporaries
+        // are dead: they map boundary corners to entries
         cudaMemsetAsync(T.bcount, 0, sizeof(int), s);
         k_bnd0<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, L0.tw, L0.ce, M.B, T.bcount, L0.bA, L0.bE, L0.bS,
                                                 T.eid);
         k_bnd0_link<<<grid_for(M.B), kBlock, 0, s>>>(M.B, T.bcount, L0.tw, T.nx0, T.eid, L0.bS, T.status);
         T.launches += 2;
     }
+}
+
+alsub_status level_boundary_flags(int V, int F, long long n, const int *off, const int *fv, int *flag,
+                                  cudaStream_t s) {
+    int k = 4;
+    while ((1LL << k) < 2 * n) k++;
+    const size_t slots = (size_t)1 << k;
+    char *buf = nullptr;
+    if (cudaMallocAsync((void **)&buf, slots * (sizeof(unsigned long long) + sizeof(int)) + 16, s) != cudaSuccess) {
+        cudaGetLastError();
+        return report(ALSUB_ERR_OOM, "boundary flags: device allocation failed");
+    }
+    DirTable tab;
+    tab.key = (unsigned long long *)buf;
+    tab.val = (int *)(buf + slots * sizeof(unsigned long long));
+    tab.mask = (unsigned)(slots - 1);
+    int *count = tab.val + slots;              // k_mb_count's boundary edge counter (unused here)
+    cudaMemsetAsync(tab.key, 0xff, slots * sizeof(unsigned long long), s);
+    cudaMemsetAsync(count, 0, sizeof(int), s);
+    cudaMemsetAsync(flag, 0, sizeof(int) * (size_t)V, s);
+    k_mb_insert<<<grid_for(F), kBlock, 0, s>>>(F, off, fv, tab);
+    k_mb_count<<<grid_for(F), kBlock, 0, s>>>(F, off, fv, tab, flag, count);
+    cudaFreeAsync(buf, s);
+    return ALSUB_OK;
 }
 
 alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary) {

@@ -23,6 +23,8 @@ OPEN = [
     ("box", synth.open_box, 5),
     ("quad", lambda: synth.polygon(4), 5),
     ("heptagon", lambda: synth.polygon(7), 4),
+    ("sheet_L0", lambda: synth.sheet_cc(6, 5, seed=60), 0),
+    ("box_L1", synth.open_box, 1),
 ]
 
 

@@ -530,3 +530,55 @@ def test_patch_mode_matches_whole_mesh(scheme, mesh):
         assert np.all(b >= 0)
         np.testing.assert_array_equal(whole[1]["P"][a], part[1]["P"][b])
     assert np.isnan(part[1]["P"]).any()          # the cut is there and marked
+
+
+# ---------------------------------------------------------------- selective subdivision (Sec. 3.4)
+
+def test_extraction_rings_closed_forms():
+    """Around one vertex of a regular quad grid, r propagation rings keep the (2r)^2 faces and
+    (2r+1)^2 vertices of the square block around it, a disk (Euler characteristic 1)."""
+    m = synth.torus_cc_plain(12, 12, jitter=0.0)
+    sel = np.zeros(m["V"], bool)
+    sel[5 * 12 + 5] = True
+    for r in (1, 2, 3):
+        e = oracle.extract(m, sel, r)
+        assert (e["F"], e["V"]) == ((2 * r) ** 2, (2 * r + 1) ** 2)
+        sub = oracle.subdivide(e, 0, "cc")[0]
+        assert sub["V"] - sub["E"] + sub["F"] == 1
+
+
+def test_extraction_interior_is_exact():
+    """One level of the extracted region's refinement equals the whole mesh's refinement on the
+    faces two rings inside the cut (the region's own cut is refined by the boundary rules)."""
+    m = synth.torus_cc_mixed(16, 14, merge_frac=0.02, split_frac=0.01, crease_frac=0.0, seed=39)
+    whole = oracle.subdivide(m, 1, "cc")
+    sel = np.zeros(m["V"], bool)
+    sel[[40, 100, 150]] = True
+    e = oracle.extract(m, sel, 3)
+    part = oracle.subdivide(e, 1, "cc")
+    inner = oracle.extract(m, sel, 1)["fmap"]          # faces touching the selected vertices
+    local = np.searchsorted(e["fmap"], inner)
+    assert np.array_equal(e["fmap"][local], inner)
+    for r, q in zip(inner, local):
+        a = whole[1]["fv"][4 * whole[0]["off"][r]:4 * whole[0]["off"][r + 1]]
+        b = part[1]["fv"][4 * e["off"][q]:4 * e["off"][q + 1]]
+        np.testing.assert_array_equal(whole[1]["P"][a], part[1]["P"][b])
+
+
+def test_adaptive_refinement_tracks_extraordinary_vertices_exactly():
+    """Feature-adaptive refinement (extract two rings around the extraordinary vertices, refine one
+    level, repeat) puts every extraordinary vertex exactly where uniform refinement puts it."""
+    m = synth.torus_cc_mixed(14, 12, merge_frac=0.03, split_frac=0.02, crease_frac=0.0, seed=40)
+    levels = 3
+    uni = oracle.subdivide(m, levels, "cc", keep_all=False)[levels]
+    valence = np.bincount(m["fv"], minlength=m["V"])
+    evs = np.flatnonzero(valence != 4)
+    assert evs.size > 0
+    cur, ids = dict(m, P=m["P"].astype(np.float64)), evs.copy()
+    for _ in range(levels):
+        e = oracle.extract(cur, None, 2)
+        pos = np.searchsorted(e["vmap"], ids)
+        assert np.array_equal(e["vmap"][pos], ids)    # every extraordinary vertex is kept
+        nxt = oracle.subdivide(e, 1, "cc")[1]
+        cur, ids = nxt, pos                          # old vertices keep their ids when refined
+    np.testing.assert_array_equal(cur["P"][ids], uni["P"][evs])
