@@ -461,6 +461,53 @@ def ordering_leg():
     return out
 
 
+def adaptive_leg():
+    """Feature-adaptive refinement (Sec. 3.4): a 96 x 96 mixed torus with sparse extraordinary
+    vertices (1% of the quads merged, 0.5% split), six rounds of (extract two rings around the
+    extraordinary vertices, refine one level), against uniform refinement of the same mesh to the
+    same depth. The rounds read their sizes back (the extraction is data dependent), so the time is
+    wall clock around the whole pass."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = synth.torus_cc_mixed(96, 96, merge_frac=0.01, split_frac=0.005, crease_frac=0.0,
+                             seed=synth.SEED_BASE + 10)
+    L = 6
+    M = alsub.Mesh.from_dict(m, "cc")
+    P0 = torch.from_numpy(np.ascontiguousarray(m["P"])).cuda()
+    base = alsub.Topology(M, 0, build=True)
+
+    def one_pass():
+        T, P, lvl, keep = base, P0, 0, []
+        for _ in range(L):
+            sub = T.extract(lvl, None, 2)
+            Ps = sub.gather(P)
+            T = alsub.Topology(sub, 1, build=True)
+            P = T.refine_vertices(Ps)
+            keep += [sub, T]
+            lvl = 1
+        torch.cuda.synchronize()
+        T.status()
+        return T.counts[1]["F"], keep
+
+    one_pass()
+    reps = 5
+    t = time.perf_counter()
+    for _ in range(reps):
+        faces, keep = one_pass()
+    ms = (time.perf_counter() - t) / reps * 1e3
+    del keep
+    U = alsub.Topology(M, L, build=False)
+    PL = torch.empty((U.counts[-1]["V"], 3), dtype=torch.float32, device="cuda")
+    ms_uni = _events_ms(lambda: U.subdivide(P0, out=PL), 10)
+    valence = np.bincount(m["fv"], minlength=m["V"])
+    out = {"workload": f"torus_cc_mixed 96 x 96 with {int((valence != 4).sum())} extraordinary vertices, depth {L}, "
+                       "two rings per round",
+           "adaptive_ms_per_pass": ms, "adaptive_faces": int(faces),
+           "uniform_ms": ms_uni, "uniform_faces": int(U.counts[-1]["F"])}
+    U.close()
+    return out
+
+
 def traffic_for(kernel_key):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -662,7 +709,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         for key, leg in (("operator", lambda: operator_leg(peak)), ("adjoint", lambda: adjoint_leg(peak)),
                          ("batch", lambda: batch_leg(mix)), ("boundary", lambda: boundary_leg(peak)),
-                         ("ordering", ordering_leg)):
+                         ("ordering", ordering_leg), ("adaptive", adaptive_leg)):
             try:
                 out[key] = leg()
             except Exception as e:  # noqa: BLE001 -- the headline line must still print
