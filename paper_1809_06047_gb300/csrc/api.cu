@@ -675,9 +675,11 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
     if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_fv, fv_h, sizeof(int) * nnz, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cv, cv.data(), sizeof(int) * 2 * M.K, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cs, cs.data(), sizeof(float) * M.K, cudaMemcpyHostToDevice, s);
-    // the host vectors die on return: make the copies complete first
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    // the host vectors die on return: the copies complete at the stream synchronisation below
+    // (for Catmull-Clark, the boundary scan's, which runs after them on the same stream)
+    if (e == cudaSuccess && scheme != ALSUB_CATMULL_CLARK) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
         cudaGetLastError();
         cleanup();
         return cuda_fail(e, "mesh upload");
@@ -693,6 +695,8 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
         if (st == ALSUB_OK && ((nnz + B) % 2 || B > kI32))
             st = fail(ALSUB_ERR_NONMANIFOLD, "inconsistent boundary (a directed edge repeats)");
         if (st != ALSUB_OK) {
+            cudaStreamSynchronize(s);          // the uploads read the host vectors
+            cudaGetLastError();
             cleanup();
             return st;
         }
