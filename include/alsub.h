@@ -468,7 +468,9 @@ typedef struct {
     double host_finish_ms_mean;            /* worker time to retire one (status, copies, frees) */
 } alsub_serve_stats;
 
-/* Start a server on the current device. max_slots 1..64 (concurrent requests), budget > 0.
+/* Start a server on the current device. max_slots 1..64 (concurrent requests), budget > 0. The
+ * slots are served by max_slots / 2 worker threads (at most 8; the environment variable
+ * ALSUB_SERVE_WORKERS sets another count, 1 .. max_slots).
  * Errors: INVALID_ARG, OOM, DEVICE. */
 alsub_status alsub_serve_create(size_t hbm_budget_bytes, int32_t max_slots, alsub_server_t *out);
 

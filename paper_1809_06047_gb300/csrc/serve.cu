@@ -17,6 +17,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -353,8 +354,13 @@ alsub_status alsub_serve_create(size_t budget, int32_t max_slots, alsub_server_t
     }
     cudaGetLastError();
     // one worker thread per two slots (at most 8): the host side of a request (validation,
-    // allocation, launches) takes long enough that one thread would cap the request rate
-    const int nw = std::max(1, std::min(8, max_slots / 2));
+    // allocation, launches) takes long enough that one thread would cap the request rate.
+    // ALSUB_SERVE_WORKERS overrides the count (1 .. max_slots).
+    int nw = std::max(1, std::min(8, max_slots / 2));
+    if (const char *env = getenv("ALSUB_SERVE_WORKERS")) {
+        const int w = atoi(env);
+        if (w >= 1) nw = std::min(w, max_slots);
+    }
     for (int w = 0, first = 0; w < nw; w++) {
         const int count = max_slots / nw + (w < max_slots % nw ? 1 : 0);
         S->workers.emplace_back(worker_loop, S.get(), first, count);
