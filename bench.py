@@ -61,11 +61,14 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def level_alg_bytes(c, l):
+def level_alg_bytes(c, l, with_ids=False):
     """Algorithmic bytes of one level step l -> l+1: read M_l and P_l, write M_{l+1} and P_{l+1}
-    (int32 face tables, FP32 xyz positions)."""
+    (int32 face tables, FP32 xyz positions); with_ids adds one int32 per corner of both levels,
+    the edge-id array that a design materialising E per level (as the paper does) reads and
+    writes too."""
     a, b = c[l], c[l + 1]
-    return 4 * a[2] + 12 * a[0] + 4 * b[2] + 12 * b[0]
+    ids = 4 * a[2] + 4 * b[2] if with_ids else 0
+    return 4 * a[2] + 12 * a[0] + 4 * b[2] + 12 * b[0] + ids
 
 
 class Clocks:
@@ -638,6 +641,7 @@ def main():
     alg = level_alg_bytes(counts, last)
     achieved = alg / (dur_ms / 1e3) / 1e9
     pipe_bytes = sum(level_alg_bytes(counts, l) for l in range(L))
+    pipe_ids = sum(level_alg_bytes(counts, l, with_ids=True) for l in range(L))
     kernel_key = f"{scheme}_step_level{last}_{args.workload}"
     traffic = traffic_for(kernel_key)
 
@@ -694,6 +698,9 @@ def main():
                      "kernel": f"{scheme} level {last}->{L} fused build+eval step",
                      "algorithmic_bytes": alg, "avg_launch_ms": dur_ms, "peak_source": peak_src},
         "pipeline": {"alg_bytes_per_step": pipe_bytes, "gbs": pipe_bytes / (ms_step / 1e3) / 1e9,
+                     "frac": pipe_bytes / (ms_step / 1e3) / 1e9 / peak,
+                     "alg_bytes_with_ids_per_step": pipe_ids,
+                     "equivalent_frac_with_ids": pipe_ids / (ms_step / 1e3) / 1e9 / peak,
                      "stage_ms": [s / max(calls, 1) for s in stage_ms]},
         "e2e": e2e,
         "gpu_launches": int(launches),
