@@ -4,8 +4,10 @@
  * arXiv 1809.06047).
  *
  * Scope: one uniform subdivision step, repeated level by level, for Catmull-Clark (Sec. 3),
- * Loop (Appendix B) and sqrt(3) (Appendix A) on closed 2-manifold meshes, with sharp and
- * semi-sharp creases for Catmull-Clark and Loop (Sec. 3.3). Topology refinement (the build step
+ * Loop (Appendix B) and sqrt(3) (Appendix A) on 2-manifold meshes -- closed, or open with
+ * boundaries for Catmull-Clark (Sec. 3.1 and 3.2 "Boundaries") -- with sharp and semi-sharp
+ * creases for Catmull-Clark and Loop (Sec. 3.3), and the extraction of selective subdivision
+ * (Sec. 3.4). Topology refinement (the build step
  * of Fig. module_core) is integer work that emits each level's face table directly; vertex
  * refinement (the eval step) is FP32. The subdivision operator of Sec. 3.5 "Single SpMV
  * evaluation" (R_i per level, or the composite R = R_{L-1} ... R_0) can be built once and applied
@@ -53,7 +55,8 @@ typedef enum {
     ALSUB_OK = 0,
     ALSUB_ERR_INVALID_ARG = 1,   /* a pointer, count, index or sharpness out of range */
     ALSUB_ERR_NONMANIFOLD = 2,   /* duplicate directed edge, edge of >2 faces, vertex with >1 fan */
-    ALSUB_ERR_UNSUPPORTED = 3,   /* open mesh (boundary), counts beyond int32, valence > 1024 */
+    ALSUB_ERR_UNSUPPORTED = 3,   /* open Loop / sqrt(3) mesh, crease at a boundary, counts beyond
+                                    int32, valence > 1024 */
     ALSUB_ERR_OOM = 4,           /* device allocation failed or a budget is exhausted */
     ALSUB_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
     ALSUB_ERR_DEVICE = 6,        /* a CUDA runtime error */
@@ -178,7 +181,8 @@ alsub_status alsub_mesh_gather(alsub_mesh_t mesh, const float *P_dev, float *out
  * Sec. 3.5 "Static topology"): for every level the face table M_{l+1}, the per-corner edge
  * numbering (E, Eq. CC_E; Appendix B for Loop) and the per-corner face adjacency (F, Eq. F), and
  * the inherited crease lists (Sec. 3.3). Level 0 edges are numbered by an exclusive scan over
- * the corners that own their edge (a -> b with a < b); each refined level numbers the two halves
+ * the corners that own their edge (a -> b with a < b, or a boundary corner: no twin, twin -1 in
+ * the per-corner adjacency of every level); each refined level numbers the two halves
  * of parent edge e as 2e and 2e+1 and the edges interior to parent faces after them. All sizes
  * are closed-form, so nothing is read back to the host. The handle keeps every level resident
  * for alsub_refine_vertices and alsub_build_operator. Enqueued on `stream`.
