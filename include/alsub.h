@@ -271,6 +271,21 @@ alsub_status alsub_subdivide(alsub_topology_t topo, const float *P0_dev, float *
 alsub_status alsub_subdivide_host(alsub_topology_t topo, const float *P0_host, float *PL_host, void *stream);
 
 /*
+ * Hierarchical edits / displacement between levels (Sec. 3.4 "Other effects": the vertex data of
+ * every level is at hand after its iteration and may be modified before the next one). After level
+ * `level` (1 .. levels) has been refined (smooth rules, crease fix, boundary repair), offset i
+ * (off_dev[3i .. 3i+2]) is added to vertex vid_dev[i] of that level, before the next step reads it
+ * or, for the last level, in the output. The ids of one level must be distinct; an id out of range
+ * latches INVALID_ARG. The arrays are copied (device or host memory); n = 0 clears the level's
+ * edits. Applied by alsub_refine_vertices, alsub_subdivide and alsub_subdivide_host; operators
+ * ignore them (with edits the result is R P_0 plus the refined edits, no longer R P_0).
+ * Synchronises the handle's and `stream`'s work (calls in flight may read the old edits).
+ * Errors: INVALID_ARG, OOM, DEVICE.
+ */
+alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int32_t n, const int32_t *vid_dev,
+                                      const float *off_dev, void *stream);
+
+/*
  * Subdivision operator (Sec. 3.5 "Single SpMV evaluation", Eq. singleSpMV): R_l maps the positions
  * of level l to those of level l+1 (P_{l+1} = R_l P_l), R = R_{L-1} ... R_0 maps the control mesh
  * to the last level. Built from a built topology in the paper's two stages (count the non-zeros
@@ -323,6 +338,8 @@ alsub_status alsub_operator_destroy(alsub_operator_t op);
  * scratch, so a topology may appear only once and must not be refined elsewhere while the batch
  * runs. The buffers are bound at creation: to refine new positions, write them into P0_dev[i].
  * Members must be closed meshes (UNSUPPORTED otherwise: the batch has no boundary repair step).
+ * Members' hierarchical edits (alsub_topology_set_edits) are applied as set when the batch first
+ * runs on a stream (its captured graph keeps them).
  */
 typedef struct alsub_batch_s *alsub_batch_t;
 

@@ -217,3 +217,21 @@ def extract(mesh: dict, select=None, rings: int = 1, scheme: str = "cc") -> dict
     if "P" in mesh:
         out["P"] = np.asarray(mesh["P"])[vmap]
     return out
+
+
+def subdivide_edits(mesh: dict, levels: int, scheme: str, edits: dict) -> list[dict]:
+    """Refinement with hierarchical edits (Sec. 3.4 "Other effects"): one level at a time, the
+    offsets edits[l] = (vertex ids, float[n, 3]) added to level l's positions once it is refined,
+    before the next level is computed from them. Returns the levels 0 .. levels."""
+    cur = dict(mesh, P=np.asarray(mesh["P"], dtype=np.float64))
+    out = [dict(cur, **subdivide(cur, 0, scheme)[0])]
+    for l in range(1, levels + 1):
+        nxt = subdivide(cur, 1, scheme)[1]
+        if l in edits:
+            vid, off = edits[l]
+            P = nxt["P"].copy()
+            P[np.asarray(vid)] += np.asarray(off, dtype=np.float64).reshape(-1, 3)
+            nxt["P"] = P
+        out.append(nxt)
+        cur = nxt
+    return out

@@ -270,6 +270,27 @@ class Topology:
                                             ctypes.byref(h)))
         return Mesh._wrap(h)
 
+    def set_edits(self, level: int, vid=None, offsets=None, stream=None):
+        """alsub_topology_set_edits: offsets added to vertices of `level` after it is refined
+        (None clears the level's edits). vid int32[n], offsets float32[n, 3]; host or device."""
+        if vid is None or len(vid) == 0:
+            _check(lib().alsub_topology_set_edits(self._h, int(level), 0, None, None, ctypes.c_void_p(_stream(stream))))
+            return
+
+        def ptr(a, dt):
+            if isinstance(a, torch.Tensor):
+                assert a.dtype == dt and a.is_contiguous()
+                return a, a.data_ptr()
+            a = np.ascontiguousarray(a, dtype={torch.int32: np.int32, torch.float32: np.float32}[dt])
+            return a, a.ctypes.data
+
+        v, pv = ptr(vid, torch.int32)
+        o, po = ptr(offsets, torch.float32)
+        n = len(v)
+        assert (o.numel() if isinstance(o, torch.Tensor) else o.size) == 3 * n
+        _check(lib().alsub_topology_set_edits(self._h, int(level), n, ctypes.c_void_p(pv), ctypes.c_void_p(po),
+                                              ctypes.c_void_p(_stream(stream))))
+
     def subdivide_host(self, P0, out=None, stream=None):
         """alsub_subdivide_host: host positions in, host positions out (CPU tensors or numpy
         arrays, float32, contiguous; page-locked tensors are copied by DMA). The result is in

@@ -387,6 +387,7 @@ void refine_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStr
         level_buffers(T, P0, PL, scratch, l, &in, &out);
         step(T, l, false, false, in, out, s);
         crease_fix(T, l, in, out, s);     // from the analysis kept at build time
+        apply_edits(T, l + 1, out, s);
         mark(T, l + 2, s);
     }
 }
@@ -516,12 +517,36 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
             wait_analysis(l);
             crease_fix(T, l, in, out, s);
         }
+        apply_edits(T, l + 1, out, s);
         if (l == T.levels - 1) join_all();
         mark(T, l + 2, s);
     }
 }
 
 }  // namespace
+
+namespace alsub {
+namespace {
+__global__ void k_edit(int n, const int *__restrict__ vid, const float *__restrict__ off, int V, float *P, bool s4,
+                       int *status) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int v = vid[i];
+    if (v < 0 || v >= V) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
+    const float3 d = f3(off[3 * i], off[3 * i + 1], off[3 * i + 2]);
+    stpv(P, v, ldpv_rw(P, v, s4) + d, s4);
+}
+
+}  // namespace
+}  // namespace alsub
+
+// The edits of level k (1 .. levels) on its freshly refined positions `out`.
+void alsub::apply_edits(TopoImpl &T, int k, float *out, cudaStream_t s) {
+    if (k >= (int)T.edits.size() || T.edits[k].n == 0) return;
+    const TopoImpl::LevelEdits &e = T.edits[k];
+    k_edit<<<grid_for(e.n), kBlock, 0, s>>>(e.n, e.vid, e.off, (int)T.L[k].V, out, k < T.levels, T.status);
+    T.launches += 1;
+}
 
 alsub_status alsub::report(alsub_status s, const char *msg) { return fail(s, "%s", msg); }
 
@@ -901,8 +926,35 @@ alsub_status alsub_topology_timings(alsub_topology_t h, double *ms, int32_t *cal
     return ALSUB_OK;
 }
 
+alsub_status alsub_topology_set_edits(alsub_topology_t h, int32_t level, int32_t n, const int32_t *vid_dev,
+                                      const float *off_dev, void *stream) {
+    if (!h || n < 0 || (n > 0 && (!vid_dev || !off_dev))) return fail(ALSUB_ERR_INVALID_ARG, "bad edit arguments");
+    TopoImpl &T = h->t;
+    if (level < 1 || level > T.levels) return fail(ALSUB_ERR_INVALID_ARG, "edits apply to levels 1 .. levels");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (T.edits.size() != (size_t)T.levels + 1) T.edits.assign(T.levels + 1, TopoImpl::LevelEdits());
+    TopoImpl::LevelEdits &e = T.edits[level];
+    CK(cudaStreamSynchronize(T.stream));          // calls in flight may still read the old edits
+    CK(cudaStreamSynchronize(s));
+    if (e.vid) cudaFreeAsync(e.vid, s);
+    if (e.off) cudaFreeAsync(e.off, s);
+    e = TopoImpl::LevelEdits();
+    drop_graphs(T);                               // captured calls hold the old edit launches
+    if (n == 0) return finish("alsub_topology_set_edits");
+    CK(cudaMallocAsync(&e.vid, sizeof(int) * (size_t)n, s));
+    CK(cudaMallocAsync(&e.off, sizeof(float) * 3 * (size_t)n, s));
+    CK(cudaMemcpyAsync(e.vid, vid_dev, sizeof(int) * (size_t)n, cudaMemcpyDefault, s));
+    CK(cudaMemcpyAsync(e.off, off_dev, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, s));
+    e.n = n;
+    return finish("alsub_topology_set_edits");
+}
+
 alsub_status alsub_topology_destroy(alsub_topology_t h) {
     if (!h) return ALSUB_OK;
+    for (TopoImpl::LevelEdits &e : h->t.edits) {
+        if (e.vid) cudaFreeAsync(e.vid, h->t.stream);
+        if (e.off) cudaFreeAsync(e.off, h->t.stream);
+    }
     free_hostio(h->t);
     free_events(h->t);
     drop_graphs(h->t);

@@ -93,12 +93,15 @@ int enqueue(alsub_batch_s &B, cudaStream_t s) {
         for (const BatchClass &c : B.tri[l]) { tri_batch_launch(c, B.block, grid, s); k++; }
         for (size_t i = 0; i < B.T.size(); i++) {
             TopoImpl &T = *B.T[i];
-            if (l >= T.levels || !crease_alive(T, l)) continue;
+            if (l >= T.levels) continue;
+            const bool fix = crease_alive(T, l);
+            const bool ed = l + 1 < (int)T.edits.size() && T.edits[l + 1].n > 0;
+            if (!fix && !ed) continue;
             const float *in;
             float *out;
             member_buffers(B, (int)i, l, &in, &out);
-            crease_fix(T, l, in, out, s);
-            k++;
+            if (fix) { crease_fix(T, l, in, out, s); k++; }
+            if (ed) { apply_edits(T, l + 1, out, s); k++; }
         }
     }
     return k;

@@ -127,6 +127,14 @@ struct TopoImpl {
     // build + eval step (fork after the step that built level l, join before the crease fix)
     cudaStream_t side = nullptr;
     std::vector<cudaEvent_t> fork_ev, join_ev;   // levels + 1 each
+    // hierarchical edits (alsub_topology_set_edits): per level, offsets added to its vertices after
+    // the level has been refined
+    struct LevelEdits {
+        int n = 0;
+        int *vid = nullptr;
+        float *off = nullptr;
+    };
+    std::vector<LevelEdits> edits;           // levels + 1 (level 0 unused)
     // alsub_subdivide_host: upload + eval stream, download stream, device input, two device
     // outputs, two page-locked input stagings and their events (indexed by call parity)
     struct HostIO {
@@ -165,6 +173,8 @@ alsub_status level_boundary_flags(int V, int F, long long nnz, const int *off, c
 // mesh (device arrays, maps, creases; B not yet set); synchronises `s`.
 alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, int rings, cudaStream_t s,
                            MeshImpl &out);
+// The hierarchical edits of level k (1 .. levels) added to its freshly refined positions `out`.
+void apply_edits(TopoImpl &T, int k, float *out, cudaStream_t s);
 // P' = X P: rows vmap[i] of P into row i of out (xyz rows).
 void gather_rows(int n, const int *vmap, const float *P, float *out, cudaStream_t s);
 // Boundary repair of one Catmull-Clark step (Sec. 3.2 "Boundaries", Fig. module_boundary): with

@@ -582,3 +582,37 @@ def test_adaptive_refinement_tracks_extraordinary_vertices_exactly():
         nxt = oracle.subdivide(e, 1, "cc")[1]
         cur, ids = nxt, pos                          # old vertices keep their ids when refined
     np.testing.assert_array_equal(cur["P"][ids], uni["P"][evs])
+
+
+# ---------------------------------------------------------------- hierarchical edits (Sec. 3.4)
+
+@pytest.mark.parametrize("scheme,mesh", [
+    ("cc", synth.torus_cc_mixed(10, 9, crease_frac=0.1, seed=41)),
+    ("cc", synth.sheet_cc(5, 4, seed=42)),
+    ("loop", synth.torus_tri(8, 7, seed=43)),
+])
+def test_edits_are_refined_by_the_remaining_operators(scheme, mesh):
+    """Refinement is linear in the positions, so an edit added on level l reaches level L as
+    R_{L-1} ... R_l applied to it (the operator rows, pinned separately by brute force), and no
+    edit gives plain refinement bit for bit."""
+    import scipy.sparse as sp
+    L = 3
+    plain = oracle.subdivide(mesh, L, scheme, operator=True)
+    none = oracle.subdivide_edits(mesh, L, scheme, {})
+    np.testing.assert_array_equal(none[L]["P"], plain[L]["P"])
+    rng = np.random.default_rng(8)
+    edits = {}
+    for l in (1, 2):
+        vid = rng.choice(plain[l]["V"], 5, replace=False)
+        edits[l] = (vid, rng.standard_normal((5, 3)))
+    got = oracle.subdivide_edits(mesh, L, scheme, edits)
+    R = [sp.csr_matrix((plain[l]["R_w"], (plain[l]["R_rows"], plain[l]["R_cols"])),
+                       shape=(plain[l + 1]["V"], plain[l]["V"])) for l in range(L)]
+    want = plain[L]["P"].copy()
+    for l, (vid, off) in edits.items():
+        d = np.zeros((plain[l]["V"], 3))
+        d[vid] = off
+        for k in range(l, L):
+            d = R[k] @ d
+        want += d
+    np.testing.assert_allclose(got[L]["P"], want, atol=1e-12)
