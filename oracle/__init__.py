@@ -235,3 +235,100 @@ def subdivide_edits(mesh: dict, levels: int, scheme: str, edits: dict) -> list[d
         out.append(nxt)
         cur = nxt
     return out
+
+
+def _cubic_bspline(t):
+    """The uniform cubic B-spline N (support [0, 4], integer knots) by the Cox-de Boor recursion."""
+    t = np.asarray(t, dtype=np.float64)
+
+    def n(i, k):
+        if k == 1:
+            return ((t >= i) & (t < i + 1)).astype(np.float64)
+        return ((t - i) / (k - 1)) * n(i, k - 1) + ((i + k - t) / (k - 1)) * n(i + 1, k - 1)
+    return n(0, 4)
+
+
+def regular_patches(level: dict, samples: int):
+    """Regular faces of a Catmull-Clark level and their bicubic B-spline patches (Sec. 3.4: faces
+    whose vertices all have valence 4 are bicubic patches whose limit surface is evaluated
+    directly), written from the definitions.
+
+    A face is regular when it is a quad, its 3 x 3 block of faces (the faces sharing a vertex with
+    it) is 9 quads around 4 interior valence-4 vertices, and no crease with sigma > 0 has an end
+    among the 16 vertices of the block. The control net: the face [v0, v1, v2, v3] spans grid
+    cells (1..2, 1..2) with u along v0 -> v1 and v along v0 -> v3; every other vertex of the block
+    gets its grid position from the faces it shares edges with. Returns (flags bool[F], {face:
+    float[samples, samples, 3]}) with sample (b, a) = S(a / (s - 1), b / (s - 1)) and
+    S(u, v) = sum_ij N(u + 3 - i) N(v + 3 - j) P_ij (N evaluated just inside its support at 1).
+    """
+    off = np.asarray(level["off"], dtype=np.int64)
+    fv = np.asarray(level["fv"], dtype=np.int64)
+    P = np.asarray(level["P"], dtype=np.float64)
+    F, V = int(level["F"]), int(level["V"])
+    faces = [list(fv[off[r]:off[r + 1]]) for r in range(F)]
+    vfaces = [[] for _ in range(V)]
+    for r, f in enumerate(faces):
+        for v in f:
+            vfaces[v].append(r)
+    edge_faces = {}
+    for r, f in enumerate(faces):
+        for j in range(len(f)):
+            edge_faces.setdefault(frozenset((f[j], f[(j + 1) % len(f)])), []).append(r)
+    crease_v = set()
+    cv = np.asarray(level.get("crease_verts", np.zeros((0, 2))), dtype=np.int64).reshape(-1, 2)
+    cs = np.asarray(level.get("crease_sharp", np.zeros(0)), dtype=np.float32).reshape(-1)
+    for (a, b), s in zip(cv, cs):
+        if s > 0:
+            crease_v.update((int(a), int(b)))
+    flags = np.zeros(F, dtype=bool)
+    grids = {}
+    t = np.linspace(0.0, 1.0, samples)
+    t[-1] = 1.0 - 1e-12                               # the support of N is half open
+    B = np.stack([_cubic_bspline(t + 3 - i) for i in range(4)], axis=1)   # [samples, 4]
+    for r, f in enumerate(faces):
+        if len(f) != 4:
+            continue
+        block = sorted({q for v in f for q in vfaces[v]})
+        if len(block) != 9 or any(len(faces[q]) != 4 for q in block):
+            continue
+        if any(len(vfaces[v]) != 4 for v in f):
+            continue
+        if any(len(edge_faces[frozenset((f[j], f[(j + 1) % 4]))]) != 2 for j in range(4)):
+            continue
+        # grid positions: the face's own vertices, then repeatedly a vertex of a block face whose
+        # three other vertices are placed (the fourth corner of a unit square)
+        pos = {f[0]: (1, 1), f[1]: (2, 1), f[2]: (2, 2), f[3]: (1, 2)}
+        changed = True
+        while changed:
+            changed = False
+            for q in block:
+                g = faces[q]
+                known = [v for v in g if v in pos]
+                if len(known) == 3 and len(g) == 4:
+                    miss = [v for v in g if v not in pos][0]
+                    k = g.index(miss)
+                    a, b, c = g[(k + 1) % 4], g[(k + 2) % 4], g[(k + 3) % 4]   # b is opposite miss
+                    pa, pb, pc = np.array(pos[a]), np.array(pos[b]), np.array(pos[c])
+                    pos[miss] = tuple(int(x) for x in pa + pc - pb)
+                    changed = True
+                elif len(known) == 2 and len(g) == 4:
+                    # an edge p -> q of g is placed: g = [p, q, x, y] is the unit square on its left
+                    for k in range(4):
+                        p_, q_ = g[k], g[(k + 1) % 4]
+                        if p_ in pos and q_ in pos:
+                            d = np.array(pos[q_]) - np.array(pos[p_])
+                            left = np.array([-d[1], d[0]])
+                            pos[g[(k + 2) % 4]] = tuple(int(x) for x in np.array(pos[q_]) + left)
+                            pos[g[(k + 3) % 4]] = tuple(int(x) for x in np.array(pos[p_]) + left)
+                            changed = True
+                            break
+        if len(pos) != 16 or sorted(pos.values()) != [(i, j) for i in range(4) for j in range(4)]:
+            continue
+        if crease_v.intersection(pos.keys()):
+            continue
+        ctrl = np.zeros((4, 4, 3))
+        for v, (i, j) in pos.items():
+            ctrl[i, j] = P[v]
+        flags[r] = True
+        grids[r] = np.einsum("ai,bj,ijd->bad", B, B, ctrl)
+    return flags, grids

@@ -616,3 +616,48 @@ def test_edits_are_refined_by_the_remaining_operators(scheme, mesh):
             d = R[k] @ d
         want += d
     np.testing.assert_allclose(got[L]["P"], want, atol=1e-12)
+
+
+# ---------------------------------------------------------------- regular patches (Sec. 3.4)
+
+def test_regular_patch_is_the_limit_of_subdivision():
+    """On regular faces Catmull-Clark converges to the bicubic B-spline patch: the positions of a
+    face's face point and corner vertex after l levels approach the patch at (1/2, 1/2) and (0, 0),
+    the error shrinking by 4 per level (the patch from the Cox-de Boor basis, the subdivision from
+    the classical rules)."""
+    m = synth.torus_cc_plain(8, 8, jitter=0.05, seed=3)
+    lvl = dict(m, P=m["P"].astype(np.float64))
+    flags, g = oracle.regular_patches(lvl, 5)
+    assert flags.all()
+    V = m["V"]
+    corner_face = {int(m["fv"][4 * r]): r for r in range(m["F"])}
+    prev = None
+    for L in (2, 3, 4, 5):
+        P = oracle.subdivide(m, L, "cc", keep_all=False)[L]["P"]
+        ef = max(np.abs(P[V + f] - g[f][2, 2]).max() for f in range(m["F"]))
+        ev = max(np.abs(P[v] - g[r][0, 0]).max() for v, r in corner_face.items())
+        if prev is not None:
+            assert 3.5 < prev[0] / ef < 4.5 and 3.5 < prev[1] / ev < 4.5
+        prev = (ef, ev)
+    assert prev[0] < 2e-4
+
+
+def test_regular_patch_reproduces_linear_functions_and_detects_irregularity():
+    """A control net linear in the grid indices gives the bilinear image of the parameter square;
+    faces next to an extraordinary vertex or a crease are not regular."""
+    N = M = 10
+    m = synth.torus_cc_plain(N, M, jitter=0.0)
+    ij = np.array([divmod(v, M) for v in range(N * M)], dtype=np.float64)
+    P = np.stack([ij[:, 0], ij[:, 1], 0.5 * ij[:, 0] - 0.25 * ij[:, 1]], axis=1)
+    flags, g = oracle.regular_patches(dict(m, P=P), 3)
+    u = np.array([0.0, 0.5, 1.0 - 1e-12])
+    for r in range(m["F"]):
+        i0, j0 = divmod(int(m["fv"][4 * r]), M)
+        if not (1 <= i0 <= N - 3 and 1 <= j0 <= M - 3):
+            continue                                   # the control net crosses the seam
+        want = np.stack(np.meshgrid(i0 + u, j0 + u), axis=-1)      # [b, a] -> (x = i0 + u_a, y = j0 + u_b)
+        np.testing.assert_allclose(g[r][..., 0], want[..., 0], atol=1e-9)
+        np.testing.assert_allclose(g[r][..., 1], want[..., 1], atol=1e-9)
+    mm = dict(m, P=P, crease_verts=np.array([[0, 1]], np.int32), crease_sharp=np.array([2.0], np.float32))
+    fl2, _ = oracle.regular_patches(mm, 3)
+    assert fl2.sum() < flags.sum()
