@@ -511,6 +511,35 @@ def adaptive_leg():
     return out
 
 
+def patches_leg(peak):
+    """Regular-patch evaluation (Sec. 3.4): the bicubic patches of every regular face of level 2 of
+    the headline mesh, sampled 16 x 16, against the same faces refined uniformly to the same
+    resolution (4 levels more: 16 x 16 quads per face)."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = synth.workload(DEFAULT_WORKLOAD)
+    M = alsub.Mesh.from_dict(m, "cc")
+    T = alsub.Topology(M, 3, build=True)
+    P0 = torch.from_numpy(m["P"]).cuda()
+    P2 = alsub.Topology(M, 2, build=True).refine_vertices(P0)
+    flags = T.regular_faces(2)
+    faces = torch.nonzero(flags).to(torch.int32).reshape(-1).contiguous()
+    s = 16
+    out = torch.empty((faces.numel(), s, s, 3), dtype=torch.float32, device="cuda")
+    ms = _events_ms(lambda: T.eval_patches(2, faces, P2, s, out=out), 10)
+    T.status()
+    bytes_out = out.numel() * 4
+    gbs = bytes_out / (ms / 1e3) / 1e9
+    res = {"workload": f"{DEFAULT_WORKLOAD} level 2: {faces.numel()} regular faces of {T.counts[2]['F']}, "
+                       f"{s} x {s} samples each",
+           "eval_ms": ms, "points_per_s": out.numel() / 3 / (ms / 1e3),
+           "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "kernel": "k_patch_nets + k_patch_eval (written samples only)", "algorithmic_bytes": bytes_out}}
+    T.close()
+    M.close()
+    return res
+
+
 def traffic_for(kernel_key):
     """DRAM bytes per launch from a committed ncu summary, if it was taken on the current source."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -716,7 +745,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_extras:
         for key, leg in (("operator", lambda: operator_leg(peak)), ("adjoint", lambda: adjoint_leg(peak)),
                          ("batch", lambda: batch_leg(mix)), ("boundary", lambda: boundary_leg(peak)),
-                         ("ordering", ordering_leg), ("adaptive", adaptive_leg)):
+                         ("ordering", ordering_leg), ("adaptive", adaptive_leg),
+                         ("patches", lambda: patches_leg(peak))):
             try:
                 out[key] = leg()
             except Exception as e:  # noqa: BLE001 -- the headline line must still print

@@ -168,6 +168,26 @@ alsub_status alsub_mesh_info(alsub_mesh_t mesh, int32_t *scheme, int64_t *num_ve
 alsub_status alsub_topology_extract(alsub_topology_t topo, int32_t level, const uint8_t *select_dev,
                                     int32_t rings, void *stream, alsub_mesh_t *out);
 
+/*
+ * Regular-patch evaluation (Sec. 3.4, the other half of feature-adaptive subdivision: faces whose
+ * vertices all have valence 4 are bicubic B-spline patches whose limit surface is evaluated
+ * directly). A face of level `level` (0 .. levels - 1 of a built Catmull-Clark topology: the level
+ * needs its twins) is regular when its 3 x 3 block of faces is 9 quads around its 4 interior
+ * valence-4 vertices and no live crease touches the block's 16 vertices.
+ * alsub_topology_regular_faces: flags_dev uint8[F_level] = 1 for the regular faces; *count (when
+ *   not NULL) receives their number, which synchronises `stream`.
+ * alsub_topology_eval_patches: for face faces_dev[i] (int32[n]) samples the patch at the
+ *   samples x samples grid u = a / (samples - 1), v = b / (samples - 1) (u along the face's corner
+ *   0 -> 1, v along corner 0 -> 3; samples = 1 gives u = v = 0) from the level's positions P_dev
+ *   (float[3 V_level], packed xyz) into out_dev float[3 * n * samples^2] (patch i, row b, column a);
+ *   a face that is not regular gets NaN. Uniform cubic B-spline basis, FP32.
+ * Errors: INVALID_ARG (level, sizes, NULL), UNSUPPORTED (Loop, sqrt(3)), OOM, DEVICE.
+ */
+alsub_status alsub_topology_regular_faces(alsub_topology_t topo, int32_t level, uint8_t *flags_dev, int64_t *count,
+                                          void *stream);
+alsub_status alsub_topology_eval_patches(alsub_topology_t topo, int32_t level, int32_t n, const int32_t *faces_dev,
+                                         const float *P_dev, int32_t samples, float *out_dev, void *stream);
+
 /* Device maps of an extracted mesh (owned by it): vmap[i] = the source level's vertex of vertex i
  * (int32[V']), fmap[f] = the source face of face f (int32[F']). Errors: INVALID_ARG. */
 alsub_status alsub_mesh_extract_maps(alsub_mesh_t mesh, const int32_t **vmap_dev, const int32_t **fmap_dev);

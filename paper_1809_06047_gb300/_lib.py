@@ -48,6 +48,8 @@ SIGNATURES = {
     "alsub_mesh_boundary_edges": [c_void_p, P(c_int64)],
     "alsub_subdivide_host": [c_void_p, c_void_p, c_void_p, c_void_p],
     "alsub_topology_set_edits": [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p],
+    "alsub_topology_regular_faces": [c_void_p, c_int32, c_void_p, P(c_int64), c_void_p],
+    "alsub_topology_eval_patches": [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p],
     "alsub_mesh_info": [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int64), P(c_int64)],
     "alsub_topology_extract": [c_void_p, c_int32, c_void_p, c_int32, c_void_p, P(c_void_p)],
     "alsub_mesh_extract_maps": [c_void_p, P(c_void_p), P(c_void_p)],

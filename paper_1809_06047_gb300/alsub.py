@@ -270,6 +270,27 @@ class Topology:
                                             ctypes.byref(h)))
         return Mesh._wrap(h)
 
+    def regular_faces(self, level: int = 0, stream=None) -> torch.Tensor:
+        """alsub_topology_regular_faces: uint8 device mask of the level's regular (bicubic) faces."""
+        flags = torch.empty(self.counts[level]["F"], dtype=torch.uint8, device="cuda")
+        n = ctypes.c_int64()
+        _check(lib().alsub_topology_regular_faces(self._h, int(level), ctypes.c_void_p(flags.data_ptr()),
+                                                  ctypes.byref(n), ctypes.c_void_p(_stream(stream))))
+        return flags
+
+    def eval_patches(self, level: int, faces: torch.Tensor, P: torch.Tensor, samples: int, out=None,
+                     stream=None) -> torch.Tensor:
+        """alsub_topology_eval_patches: float32[n, samples, samples, 3] samples of the bicubic patches
+        of `faces` (int32 device tensor) from the level's positions P (device, packed xyz)."""
+        assert faces.is_cuda and faces.dtype == torch.int32 and P.is_cuda and P.dtype == torch.float32
+        n = faces.numel()
+        if out is None:
+            out = torch.empty((n, samples, samples, 3), dtype=torch.float32, device="cuda")
+        _check(lib().alsub_topology_eval_patches(self._h, int(level), n, ctypes.c_void_p(faces.data_ptr()),
+                                                 ctypes.c_void_p(P.data_ptr()), int(samples),
+                                                 ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(_stream(stream))))
+        return out
+
     def set_edits(self, level: int, vid=None, offsets=None, stream=None):
         """alsub_topology_set_edits: offsets added to vertices of `level` after it is refined
         (None clears the level's edits). vid int32[n], offsets float32[n, 3]; host or device."""
