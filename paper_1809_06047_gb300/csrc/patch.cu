@@ -142,6 +142,56 @@ __global__ void k_patch_eval(long long total, int samples, const int *__restrict
     out[3 * t + 2] = acc.z;
 }
 
+// A block per patch for samples^2 <= 1024 (tpp threads; the kernel takes several patches per block,
+// kPatchSlots at most): the 16 control points into shared memory, then its 4 rows interpolated along u
+// (R_j(a) = sum_i B_i(u_a) P_ij), then each sample S(a, b) = sum_j B_j(v_b) R_j(a); a patch's
+// samples are written as one contiguous run.
+constexpr int kPatchSlots = 1;
+__global__ void __launch_bounds__(1024) k_patch_eval_block(int n, int samples, int tpp, const int *__restrict__ nets,
+                                                           const float *__restrict__ P, float *out) {
+    __shared__ float4 sp[kPatchSlots][16];
+    __shared__ float4 sr[kPatchSlots][4][32];
+    const int slot = threadIdx.x / tpp, lt = threadIdx.x - slot * tpp;
+    const long long i = (long long)blockIdx.x * (blockDim.x / tpp) + slot;
+    const int per = samples * samples;
+    const float inv = samples > 1 ? 1.f / (float)(samples - 1) : 0.f;
+    const bool live = i < n;
+    if (live && lt < 16) {
+        const int id = __ldg(nets + 16 * i + lt);
+        const float nan = __int_as_float(0x7fc00000);
+        const float3 q = id < 0 ? f3(nan, nan, nan) : ldp(P, id);
+        sp[slot][lt] = make_float4(q.x, q.y, q.z, 0.f);
+    }
+    __syncthreads();
+    if (live && lt < 4 * samples) {
+        const int j = lt / samples, a = lt - j * samples;
+        float B[4];
+        cubic_basis((float)a * inv, B);
+        float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const float4 c = sp[slot][4 * j + q];
+            r.x += B[q] * c.x; r.y += B[q] * c.y; r.z += B[q] * c.z;
+        }
+        sr[slot][j][a] = r;
+    }
+    __syncthreads();
+    if (!live || lt >= per) return;
+    const int b = lt / samples, a = lt - b * samples;
+    float B[4];
+    cubic_basis((float)b * inv, B);
+    float3 acc = f3(0.f, 0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+        const float4 r = sr[slot][j][a];
+        acc += B[j] * f3(r.x, r.y, r.z);
+    }
+    float *o = out + 3 * ((size_t)i * per + lt);
+    o[0] = acc.x;
+    o[1] = acc.y;
+    o[2] = acc.z;
+}
+
 __global__ void k_patch_crease_flags(const int *__restrict__ count, int cap, const int *__restrict__ cv,
                                      const float *__restrict__ cs, unsigned char *flag) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -247,7 +297,15 @@ alsub_status alsub_topology_eval_patches(alsub_topology_t topo, int32_t level, i
     }
     k_patch_nets<<<grid_for(n), kBlock, 0, s>>>(A, n, faces_dev, (int)L.F, crease_v, nets);
     const long long total = (long long)n * samples * samples;
-    k_patch_eval<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, s>>>(total, samples, nets, P_dev, out_dev);
+    if (samples <= 32) {
+        const int tpp = std::max(64, ((samples * samples + 31) / 32) * 32);
+        // one patch per block measured faster than four (1024 threads, 2 resident blocks per SM)
+        const int per_block = 1;
+        k_patch_eval_block<<<(n + per_block - 1) / per_block, per_block * tpp, 0, s>>>(n, samples, tpp, nets, P_dev,
+                                                                                      out_dev);
+    } else {
+        k_patch_eval<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, s>>>(total, samples, nets, P_dev, out_dev);
+    }
     T->launches += 2;
     cudaFreeAsync(buf, s);
     cudaError_t e = cudaGetLastError();
