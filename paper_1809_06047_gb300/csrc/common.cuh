@@ -138,6 +138,22 @@ __device__ __forceinline__ bool loop_own(int l, int x, const Level0 &z) {
     return (g & 3) < 3 && i < 2;
 }
 
+// The same two tests with the corner given as (triangle g, corner i): no division by 3. A corner-0
+// vertex of a corner child is corner j of the parent triangle g >> 2, i.e. (g >> 2, j) again.
+__device__ __forceinline__ bool loop_own_gi(int l, int g, int i, const Level0 &z) {
+    if (l == 0) return __ldg(z.own + 3 * g + i) != 0;
+    return (g & 3) < 3 && i < 2;
+}
+__device__ __forceinline__ bool loop_vown_gi(int l, int g, int i, const Level0 &z) {
+    while (l > 0) {
+        const int r = g >> 2, j = g & 3;
+        if (j == 3 || i == 2) return false;
+        if (i == 0) { g = r; i = j; --l; continue; }
+        return loop_own_gi(l - 1, r, j, z);
+    }
+    return __ldg(z.vc + __ldg(z.fv + 3 * g + i)) == 3 * g + i;
+}
+
 // Loop: corner i of child j of triangle r is 3(4r + j) + i.
 __device__ __forceinline__ bool loop_vown(int l, int x, const Level0 &z) {
     while (l > 0) {
@@ -187,8 +203,9 @@ struct TriLevel {
         const int interior = j == 3 ? 3 * (4 * R + (i == 2 ? 0 : i + 1)) + 1 : 3 * (4 * R + 3) + jm;
         return need ? fromParent : interior;
     }
-    // Loop only (sqrt(3) has no edge ids)
+    // Loop only (sqrt(3) has no edge ids); edge_gi takes corner i of triangle g
     __device__ int edge(int x) const;
+    __device__ int edge_gi(int g, int i) const;
 };
 
 // sqrt(3): corner k of child c (the child of parent corner c) is 3c + k.
@@ -204,11 +221,16 @@ __device__ __forceinline__ bool sqrt3_vown(int l, int x, const Level0 &z) {
 
 __device__ __forceinline__ int TriLevel::edge(int x) const {
     if (!derive) return __ldg(ce + x);
-    const int g = x / 3, i = x - 3 * g, R = g >> 2, j = g & 3;
+    const int g = x / 3;
+    return edge_gi(g, x - 3 * g);
+}
+__device__ __forceinline__ int TriLevel::edge_gi(int g, int i) const {
+    if (!derive) return __ldg(ce + 3 * g + i);
+    const int R = g >> 2, j = g & 3;
     const bool need = j != 3 && i != 1;
     const int pc = 3 * R + (i == 0 ? j : (j == 0 ? 2 : j - 1));
     const int pe = need ? __ldg(pce + pc) : 0;
-    const bool own = need && loop_own(lp, pc, z);
+    const bool own = need && loop_own_gi(lp, R, i == 0 ? j : (j == 0 ? 2 : j - 1), z);
     const int fromParent = 2 * pe + (i == 0 ? (own ? 0 : 1) : (own ? 1 : 0));
     const int interior = E2p + 3 * R + (j == 3 ? (i == 2 ? 0 : i + 1) : j);
     return need ? fromParent : interior;

@@ -56,10 +56,10 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         vv[j] = __ldg(a.fv + c + j);
-        ee[j] = a.t.edge(c + j);
+        ee[j] = a.t.edge_gi(r, j);
         // the eval of levels >= 1 reads its neighbours from the parent level: no twins needed
         tt[j] = (HELP || (EVAL && a.l == 0)) ? a.t.twin(c + j) : 0;
-        ow[j] = loop_own(a.l, c + j, a.z);
+        ow[j] = loop_own_gi(a.l, r, j, a.z);
     }
     if (TOPO) {
         // the 12 ints of the four children, 48 bytes at 48 r: three 16-byte stores
@@ -142,7 +142,7 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
                 const float3 pen = ldpv(P, en, a.in4), pea = ldpv(P, ea, a.in4);
                 stpv(a.Pn, V + ee[0], 0.375f * (p[0] + p[1]) + 0.125f * (p[2] + pea), a.out4);
                 stpv(a.Pn, V + ee[1], 0.375f * (p[1] + p[2]) + 0.125f * (p[0] + pen), a.out4);
-                if (loop_own(a.l - 1, 3 * R + k, a.z)) {
+                if (loop_own_gi(a.l - 1, R, k, a.z)) {
                     // E_k: v_k, E_k-1 (this triangle), v_k+1, E_k+1, and E'_k2+1, E'_k2-1 across
                     const int vn = __ldg(a.pfv + 3 * R + k1);
                     const int eb = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 0 ? 2 : k2 - 1));
@@ -151,14 +151,14 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
                     stpv(a.Pn, vv[1], (1.0f - 6.0f * beta) * p[1] + beta * sp, a.out4);
                 }
             }
-            if (k < 3 && loop_vown(a.l, c, a.z)) {
+            if (k < 3 && loop_vown_gi(a.l, r, 0, a.z)) {
                 // v_k = R's corner k. Follow it up while it is corner 0 of a corner child: it was
                 // born on level m >= 1 as the midpoint of edge kb of triangle G of level m - 1
                 // (valence 6), or is a control-mesh vertex (m = 0, any valence: walk the parent ring).
-                int m = a.l - 1, x = 3 * R + k, kb = 0;
+                int m = a.l - 1, x = 0, kb = 0, g = R, i = k;     // corner i of triangle g
                 while (m > 0) {
-                    const int g = x / 3, i = x - 3 * g, j = g & 3;
-                    if (i == 0 && j != 3) { x = 3 * (g >> 2) + j; --m; continue; }
+                    const int j = g & 3;
+                    if (i == 0 && j != 3) { i = j; g >>= 2; --m; continue; }
                     kb = j == 3 ? i : (i == 1 ? j : (j == 0 ? 2 : j - 1));
                     x = g >> 2;                      // G
                     break;
