@@ -261,14 +261,16 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
             // neighbours the face points of its parent-level triangles (a walk of the parent
             // ring); f_T (designated at the child of T's corner 0) neighbours T's three vertices
             // and the face points of T's three neighbours (valence 6).
-            if (sqrt3_vown(a.l, c, a.z)) {
-                // v_r = the vertex of parent corner r. Follow it up while it is corner 0 of a
-                // child: the designated corner ends at corner 2 of the child of corner 3T of some
-                // triangle T of level m - 1, i.e. v_r was born on level m >= 1 as T's face point
-                // (valence 6), or is a control-mesh vertex (m = 0: walk the parent ring).
-                int m = a.l - 1, x = r;
-                while (m > 0 && x % 3 == 0) { x /= 3; --m; }
-                if (m > 0 && x % 3 == 2) {
+            // v_r = the vertex of parent corner r. Follow it up while it is corner 0 of a child:
+            // the designated corner ends at corner 2 of the child of corner 3T of some triangle T
+            // of level m - 1, i.e. v_r was born on level m >= 1 as T's face point (valence 6), or
+            // is a control-mesh vertex (m = 0: its smallest corner designates it; walk the parent
+            // ring). One descent serves the designation test and the ring.
+            int m = a.l - 1, x = r;
+            while (m > 0 && x % 3 == 0) { x /= 3; --m; }
+            const bool des = m > 0 ? (x % 3 == 2 && (x / 3) % 3 == 0) : __ldg(a.z.vc + __ldg(a.z.fv + x)) == x;
+            if (des) {
+                if (m > 0) {
                     // x = corner 2 of triangle g = x / 3 of level m, the child of corner g of
                     // triangle T = g / 3 of level m - 1. On level m, f_T lies in the children 3T + j
                     // of T's corners (corner 2) and in the children t = tw(3T + j) of the corners
