@@ -9,7 +9,11 @@ working set (~2.6 GB) is far larger than L2, so no flush is needed between steps
 
 Prints one JSON line (rank 0). With torchrun (N > 1) every rank refines its own copy of the
 workload (independent meshes: weak scaling, no collective on the data path); the time is the max
-over ranks.
+over ranks. `e2e` runs the same step through alsub_subdivide_host (host buffers, upload and
+download inside the timed region). Further legs at N = 1 (skipped by --no-extras): the composite
+operator (one SpMV per frame), the adjoint, ragged batches, an open mesh with boundaries, control-
+mesh ordering, feature-adaptive refinement and regular-patch evaluation; the serving loop
+(--no-serving skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl alsub|reference] [--workload NAME]
 """
@@ -46,7 +50,8 @@ def parse(argv=None):
     p.add_argument("--levels", type=int, default=None, help="override the workload's level count")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
-    p.add_argument("--no-extras", action="store_true", help="skip the operator, adjoint and batch legs")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the operator, adjoint, batch, boundary, ordering, adaptive and patches legs")
     p.add_argument("--serving-fastest", action="store_true",
                    help="also replay the serving mix with each resident's faster frame path")
     return p.parse_args(argv)
