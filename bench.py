@@ -1,7 +1,7 @@
 #!/usr/bin/env python
 """Throughput of uniform subdivision on GB300: refined faces per second.
 
-One step = one full dynamic-topology subdivision of the workload (Sec. 3.5 "Dynamic topology":
+One step = one full dynamic-topology subdivision of the workload (Sec. 3.6 "Dynamic topology":
 level-0 adjacency, then per level the fused build + eval kernels, creases included) through the
 C ABI call alsub_subdivide (repeated calls replay the CUDA graph the library captures of them). Default workload: Catmull-Clark with semi-sharp creases, 6 levels of a
 ~9.2k-face mixed-polygon torus (37,750,784 refined quads). Inputs are resident in HBM; the step's
@@ -288,7 +288,7 @@ def spmv_bytes(rows, cols, nnz):
 
 
 def operator_leg(peak):
-    """The subdivision operator of Sec. 3.5 on the headline workload: composite R = R_5 ... R_0 built
+    """The subdivision operator of Sec. 3.6 on the headline workload: composite R = R_5 ... R_0 built
     in the paper's two stages, then one SpMV per frame, against the fused eval kernels on the same
     cached topology."""
     import torch

@@ -9,7 +9,7 @@
  * creases for Catmull-Clark and Loop (Sec. 3.3), and the extraction of selective subdivision
  * (Sec. 3.4). Topology refinement (the build step
  * of Fig. module_core) is integer work that emits each level's face table directly; vertex
- * refinement (the eval step) is FP32. The subdivision operator of Sec. 3.5 "Single SpMV
+ * refinement (the eval step) is FP32. The subdivision operator of Sec. 3.6 "Single SpMV
  * evaluation" (R_i per level, or the composite R = R_{L-1} ... R_0) can be built once and applied
  * as one SpMV per frame, and applied transposed for gradients.
  *
@@ -198,7 +198,7 @@ alsub_status alsub_mesh_gather(alsub_mesh_t mesh, const float *P_dev, float *out
 
 /*
  * Build the topology of `levels` uniform refinement steps (the build step of Fig. module_core,
- * Sec. 3.5 "Static topology"): for every level the face table M_{l+1}, the per-corner edge
+ * Sec. 3.6 "Static topology"): for every level the face table M_{l+1}, the per-corner edge
  * numbering (E, Eq. CC_E; Appendix B for Loop) and the per-corner face adjacency (F, Eq. F), and
  * the inherited crease lists (Sec. 3.3). Level 0 edges are numbered by an exclusive scan over
  * the corners that own their edge (a -> b with a < b, or a boundary corner: no twin, twin -1 in
@@ -265,7 +265,7 @@ alsub_status alsub_refine_vertices(alsub_topology_t topo, const float *P0_dev, f
 alsub_status alsub_refine_vertices_scratch_bytes(alsub_topology_t topo, size_t *bytes);
 
 /*
- * Dynamic-topology subdivision (Sec. 3.5 "Dynamic topology"): rebuild the whole topology of the
+ * Dynamic-topology subdivision (Sec. 3.6 "Dynamic topology"): rebuild the whole topology of the
  * handle from its control mesh AND refine the vertices, one fused build+eval pass per level, so
  * a topology-changing edit costs one call with no preprocessing. The per-corner adjacency of the
  * last level is not stored (nothing consumes it); face tables and crease lists of every level
@@ -291,7 +291,7 @@ alsub_status alsub_subdivide(alsub_topology_t topo, const float *P0_dev, float *
 alsub_status alsub_subdivide_host(alsub_topology_t topo, const float *P0_host, float *PL_host, void *stream);
 
 /*
- * Hierarchical edits / displacement between levels (Sec. 3.4 "Other effects": the vertex data of
+ * Hierarchical edits / displacement between levels (Sec. 3.5 "Other effects": the vertex data of
  * every level is at hand after its iteration and may be modified before the next one). After level
  * `level` (1 .. levels) has been refined (smooth rules, crease fix, boundary repair), offset i
  * (off_dev[3i .. 3i+2]) is added to vertex vid_dev[i] of that level, before the next step reads it
@@ -306,7 +306,7 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
                                       const float *off_dev, void *stream);
 
 /*
- * Subdivision operator (Sec. 3.5 "Single SpMV evaluation", Eq. singleSpMV): R_l maps the positions
+ * Subdivision operator (Sec. 3.6 "Single SpMV evaluation", Eq. singleSpMV): R_l maps the positions
  * of level l to those of level l+1 (P_{l+1} = R_l P_l), R = R_{L-1} ... R_0 maps the control mesh
  * to the last level. Built from a built topology in the paper's two stages (count the non-zeros
  * of every row, then fill column indices and FP32 weights); rows are sorted by column.
@@ -441,7 +441,7 @@ alsub_status alsub_topology_bytes(alsub_topology_t topo, size_t *bytes);
 alsub_status alsub_operator_bytes(alsub_operator_t op, size_t *bytes);
 
 /*
- * Serving loop (no counterpart in the paper's text; its "Static topology" mode of Sec. 3.5, build
+ * Serving loop (no counterpart in the paper's text; its "Static topology" mode of Sec. 3.6, build
  * once and evaluate every frame, is what the resident cache serves). A worker thread owned by the
  * server admits queued requests first come first served into `max_slots` slots, each with its own
  * CUDA stream, as soon as a slot is free and the request's device bytes fit the HBM budget, so
@@ -519,7 +519,7 @@ alsub_status alsub_serve_create(size_t hbm_budget_bytes, int32_t max_slots, alsu
  * Make a resident topology: build it (synchronously, on a stream of the server's own) and choose
  * how its frames are served:
  *   ALSUB_FRAMES_EVAL      the eval kernels on the cached topology (no operator is built);
- *   ALSUB_FRAMES_OPERATOR  one SpMV with the cached composite operator R (Sec. 3.5 "Single SpMV
+ *   ALSUB_FRAMES_OPERATOR  one SpMV with the cached composite operator R (Sec. 3.6 "Single SpMV
  *                          evaluation"); falls back to EVAL when R does not fit the budget;
  *   ALSUB_FRAMES_FASTEST   build R, time one frame by each path and keep the faster.
  * Mesh arguments as alsub_mesh_create. *resident receives the id FRAME requests name.

@@ -220,7 +220,7 @@ def extract(mesh: dict, select=None, rings: int = 1, scheme: str = "cc") -> dict
 
 
 def subdivide_edits(mesh: dict, levels: int, scheme: str, edits: dict) -> list[dict]:
-    """Refinement with hierarchical edits (Sec. 3.4 "Other effects"): one level at a time, the
+    """Refinement with hierarchical edits (Sec. 3.5 "Other effects"): one level at a time, the
     offsets edits[l] = (vertex ids, float[n, 3]) added to level l's positions once it is refined,
     before the next level is computed from them. Returns the levels 0 .. levels."""
     cur = dict(mesh, P=np.asarray(mesh["P"], dtype=np.float64))

@@ -1,6 +1,6 @@
 """Differentiable subdivision: a torch.autograd.Function around libalsub.
 
-Vertex refinement is linear in the control positions (P_L = R P_0, Sec. 3.5 Eq. singleSpMV), so
+Vertex refinement is linear in the control positions (P_L = R P_0, Sec. 3.6 Eq. singleSpMV), so
 the gradient of any loss of P_L is g_0 = R^T g_L. Forward runs the fused eval kernels
 (alsub_refine_vertices); backward applies the transposed per-level operators
 g_l = R_l^T g_{l+1} (alsub_apply_operator_transpose on an ALSUB_OP_CHAIN operator), which depend

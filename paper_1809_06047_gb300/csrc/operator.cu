@@ -1,4 +1,4 @@
-// The subdivision operator (Sec. 3.5, "Single SpMV evaluation"): R_l maps the positions of level
+// The subdivision operator (Sec. 3.6, "Single SpMV evaluation"): R_l maps the positions of level
 // l to those of level l+1, so P_{l+1} = R_l P_l and P_L = R P_0 with R = R_{L-1} ... R_0
 // (Eq. singleSpMV). Built on the device in the paper's two stages: count the non-zeros of every
 // row, scan, then fill column indices and weights. The weights are the stencils of the eval step

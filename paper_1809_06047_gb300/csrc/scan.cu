@@ -1,7 +1,7 @@
 // Device-wide exclusive scan (deterministic: fixed-order block reduce, one-CTA scan of the block
 // sums, block-local scan plus offset; inputs up to 65536 elements in one CTA). Used for edge numbering (Sec. 3.2:
 // enumerate the non-zeros of the upper triangle of E), vertex buckets, crease-list compaction and
-// the row offsets of the subdivision operators (Sec. 3.5, count then fill).
+// the row offsets of the subdivision operators (Sec. 3.6, count then fill).
 #include "common.cuh"
 #include "internal.h"
 

@@ -5,11 +5,11 @@
 // staging buffers), admit the head of the queue as soon as one of their slots is free and the
 // request's device bytes fit the HBM budget, and retire slots whose event has completed, so
 // requests overlap on the device and a new one joins as soon as another leaves. Two kinds:
-//   FRAME  new control positions for a resident topology (Sec. 3.5 "Static topology": build once,
-//          evaluate per frame): H2D, then one SpMV with the cached composite operator (Sec. 3.5
+//   FRAME  new control positions for a resident topology (Sec. 3.6 "Static topology": build once,
+//          evaluate per frame): H2D, then one SpMV with the cached composite operator (Sec. 3.6
 //          "Single SpMV evaluation") or the eval kernels on the cached topology, as chosen at
 //          registration (optionally by a timed trial of both); D2H.
-//   MESH   a new control mesh (Sec. 3.5 "Dynamic topology"): mesh upload, fused build + eval of
+//   MESH   a new control mesh (Sec. 3.6 "Dynamic topology"): mesh upload, fused build + eval of
 //          every level (alsub_subdivide), D2H; its handles are freed when the slot retires.
 // Per-request device buffers come from the stream-ordered allocator on the slot's stream, so
 // nothing in the loop synchronises the device. Every wait is bounded.

@@ -1,4 +1,4 @@
-"""Hierarchical edits between levels (Sec. 3.4 "Other effects") on the CUDA path against the
+"""Hierarchical edits between levels (Sec. 3.5 "Other effects") on the CUDA path against the
 oracle's level-by-level refinement with the same offsets (vertex ids translated by the canonical
 relabelling), through the static, dynamic (graph-replayed) and host-buffer calls."""
 import numpy as np

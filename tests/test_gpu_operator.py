@@ -1,4 +1,4 @@
-"""Parity of the subdivision operator (Sec. 3.5, single SpMV) with the oracle's operator.
+"""Parity of the subdivision operator (Sec. 3.6, single SpMV) with the oracle's operator.
 
 R_l from the CUDA path is compared entry by entry with the oracle's R_l after canonical
 relabelling of rows (level l+1 vertices) and columns (level l vertices): identical sparsity, FP32
