@@ -34,6 +34,11 @@
 #ifndef ALSUB_SIB_PREFETCH
 #define ALSUB_SIB_PREFETCH 1216
 #endif
+// The last step's face rows go out through shared memory, 512 contiguous bytes per store
+// instruction (1), or straight from each lane, 64 bytes at a 64-byte stride (0).
+#ifndef ALSUB_SIB_TOPO_SMEM
+#define ALSUB_SIB_TOPO_SMEM 1
+#endif
 // Block size of the sibling kernel and the resident blocks per SM it is compiled for (register
 // budget: 65536 / (block x blocks)).
 #ifndef ALSUB_SIB_BLOCK
@@ -440,7 +445,26 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
             }
         }
     }
-    if (TOPO && live) {
+    if (TOPO && ALSUB_SIB_TOPO_SMEM && DERIVE == 2) {
+        // the warp's 32 faces write 128 consecutive int4 rows: staged in shared memory and
+        // written back so that every store instruction covers 512 contiguous bytes (measured on
+        // the last step only: 0.379 against 0.389 ms; the steps before it ran a little slower)
+        __shared__ int4 stopo[ALSUB_SIB_BLOCK / 32][128];
+        const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        int4 *sb = stopo[w];
+        sb[4 * lane + 0] = make_int4(v.x, VF + e.x, a.V + r, VF + e.w);
+        sb[4 * lane + 1] = make_int4(v.y, VF + e.y, a.V + r, VF + e.x);
+        sb[4 * lane + 2] = make_int4(v.z, VF + e.z, a.V + r, VF + e.y);
+        sb[4 * lane + 3] = make_int4(v.w, VF + e.w, a.V + r, VF + e.z);
+        __syncwarp();
+        const int r0 = r - lane;
+        int4 *o = reinterpret_cast<int4 *>(a.fvn) + 4 * (size_t)r0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int q = 32 * k + lane;
+            if (r0 + (q >> 2) < a.F) o[q] = sb[q];
+        }
+    } else if (TOPO && live) {
         int *o = a.fvn + 16 * (size_t)r;
         st4(o + 0, make_int4(v.x, VF + e.x, a.V + r, VF + e.w));
         st4(o + 4, make_int4(v.y, VF + e.y, a.V + r, VF + e.x));
