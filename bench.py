@@ -12,8 +12,8 @@ workload (independent meshes: weak scaling, no collective on the data path); the
 over ranks. `e2e` runs the same step through alsub_subdivide_host (host buffers, upload and
 download inside the timed region). Further legs at N = 1 (skipped by --no-extras): the composite
 operator (one SpMV per frame), the adjoint, ragged batches, an open mesh with boundaries, control-
-mesh ordering, feature-adaptive refinement and regular-patch evaluation; the serving loop
-(--no-serving skips it).
+mesh ordering and its RCM reordering, feature-adaptive refinement and regular-patch evaluation;
+the serving loop (--no-serving skips it).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl alsub|reference] [--workload NAME]
 """
@@ -431,11 +431,22 @@ def boundary_leg(peak):
     return out
 
 
+def _bandwidth(off, fv) -> int:
+    """Bandwidth of the mesh Laplacian: the largest index gap along a face edge."""
+    off = np.asarray(off, dtype=np.int64)
+    fv = np.asarray(fv, dtype=np.int64)
+    nxt = np.arange(1, fv.size + 1)
+    nxt[off[1:] - 1] = off[:-1]
+    return int(np.abs(fv - fv[nxt]).max())
+
+
 def ordering_leg():
-    """Control-mesh order (the reordering question of Sec. 4.5): the headline mesh with its vertex
-    ids and face order shuffled (seeded) against the generator's order, same call and levels. The
-    refined numbering keeps each face's children contiguous, so the order only matters on the
-    first levels."""
+    """Control-mesh order (mesh reordering, Sec. 4.5): the headline mesh with its vertex ids and
+    face order shuffled (seeded) against the generator's order, and the shuffled mesh reordered on
+    the device by alsub_mesh_reorder (RCM on the graph of the mesh Laplacian, faces by their least
+    vertex); same call and levels. The refined numbering keeps each face's children contiguous, so
+    the order only matters on the first levels. `reorder_ms`: wall clock of the reordering itself
+    (it reads back each breadth-first level's size)."""
     import torch
     from paper_1809_06047_gb300 import alsub
     m = synth.workload(DEFAULT_WORKLOAD)
@@ -448,11 +459,29 @@ def ordering_leg():
     noff[1:] = np.cumsum([len(f) for f in faces])
     sh = dict(m, off=noff, fv=np.concatenate(faces).astype(np.int32),
               P=np.ascontiguousarray(m["P"][np.argsort(pv)]), crease_verts=pv[m["crease_verts"]].astype(np.int32))
-    out = {"workload": f"{DEFAULT_WORKLOAD}, generator order vs shuffled vertex ids and face order"}
-    for key, mesh in (("ordered", m), ("shuffled", sh)):
-        M = alsub.Mesh.from_dict(mesh, "cc")
+    out = {"workload": f"{DEFAULT_WORKLOAD}, generator order vs shuffled vertex ids and face order vs "
+                       "the shuffled mesh reordered by RCM"}
+    Msh = alsub.Mesh.from_dict(sh, "cc")
+    Msh.reorder()                                 # warm-up (first launches of its kernels)
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(5):
+        t0 = time.perf_counter()
+        R = Msh.reorder()
+        torch.cuda.synchronize()
+        times.append(1e3 * (time.perf_counter() - t0))
+        if len(times) < 5:
+            R.close()
+    Psh = torch.from_numpy(np.ascontiguousarray(sh["P"])).cuda()
+    ra = R.arrays()
+    out["reorder_ms"] = float(np.median(times))
+    out["rcm_levels"] = R.rcm_levels
+    variants = (("ordered", alsub.Mesh.from_dict(m, "cc"), torch.from_numpy(np.ascontiguousarray(m["P"])).cuda(),
+                 _bandwidth(m["off"], m["fv"])),
+                ("shuffled", Msh, Psh, _bandwidth(sh["off"], sh["fv"])),
+                ("rcm", R, R.gather(Psh), _bandwidth(ra["off"], ra["fv"])))
+    for key, M, P0, bw in variants:
         T = alsub.Topology(M, m["levels"], build=False)
-        P0 = torch.from_numpy(np.ascontiguousarray(mesh["P"])).cuda()
         PL = torch.empty((T.counts[-1]["V"], 3), dtype=torch.float32, device="cuda")
         T.set_timing(10)
         T.subdivide(P0, out=PL)
@@ -462,10 +491,12 @@ def ordering_leg():
         st, calls, _ = T.timings()
         T.set_timing(0)
         T.status()
-        out[key] = {"ms_per_step": ms, "stage_ms": [x / max(calls, 1) for x in st]}
+        out[key] = {"ms_per_step": ms, "stage_ms": [x / max(calls, 1) for x in st], "bandwidth": bw}
         T.close()
+    for _, M, _, _ in variants:
         M.close()
     out["slowdown"] = out["shuffled"]["ms_per_step"] / out["ordered"]["ms_per_step"]
+    out["rcm_vs_ordered"] = out["rcm"]["ms_per_step"] / out["ordered"]["ms_per_step"]
     return out
 
 

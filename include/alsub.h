@@ -188,12 +188,38 @@ alsub_status alsub_topology_regular_faces(alsub_topology_t topo, int32_t level, 
 alsub_status alsub_topology_eval_patches(alsub_topology_t topo, int32_t level, int32_t n, const int32_t *faces_dev,
                                          const float *P_dev, int32_t samples, float *out_dev, void *stream);
 
-/* Device maps of an extracted mesh (owned by it): vmap[i] = the source level's vertex of vertex i
- * (int32[V']), fmap[f] = the source face of face f (int32[F']). Errors: INVALID_ARG. */
+/*
+ * Mesh reordering (Sec. 4.5): a new mesh with the same faces, vertices renumbered by reverse
+ * Cuthill-McKee (Cuthill and McKee 1969, reversed as in George 1971) on the graph of the mesh
+ * Laplacian (u ~ w when an edge of some face joins them) and faces sorted by their first non-zero
+ * row of M, i.e. by the least new index among their vertices.
+ *   Cuthill-McKee: each connected component starts at its unlabelled vertex of least (degree,
+ *   index); labelled vertices are visited in label order and each labels its unlabelled neighbours
+ *   in increasing (degree, index); the new index of a vertex is V - 1 - its label. Faces with the
+ *   same least vertex keep their input order; each face keeps its corners in order from the same
+ *   first corner; creases keep their order with their ends renamed. The result is unique.
+ * Runs on the device, one breadth-first level at a time (synchronises `stream` once per level).
+ * The new handle owns its arrays and the maps (alsub_mesh_extract_maps: vmap[new] = old vertex,
+ * fmap[new] = old face); positions follow with alsub_mesh_gather. *levels (may be NULL): the
+ * breadth-first levels it took. Errors: INVALID_ARG (NULL), UNSUPPORTED (more than 2^30 corners),
+ * OOM, DEVICE.
+ */
+alsub_status alsub_mesh_reorder(alsub_mesh_t mesh, void *stream, alsub_mesh_t *out, int32_t *levels);
+
+/* Device arrays of a mesh (owned by it; any pointer may be NULL): off int32[F + 1], fv int32[nnz],
+ * crease ends int32[2K] and sharpness float[K] (NULL when K = 0; creases of sharpness 0 were
+ * dropped at creation). Read them after the call that made the mesh has completed on its stream.
+ * Errors: INVALID_ARG. */
+alsub_status alsub_mesh_arrays(alsub_mesh_t mesh, const int32_t **off_dev, const int32_t **fv_dev,
+                               const int32_t **crease_verts_dev, const float **crease_sharp_dev);
+
+/* Device maps of an extracted or reordered mesh (owned by it): vmap[i] = the source vertex of
+ * vertex i (int32[V']), fmap[f] = the source face of face f (int32[F']). Errors: INVALID_ARG (a
+ * mesh made by alsub_mesh_create has no maps). */
 alsub_status alsub_mesh_extract_maps(alsub_mesh_t mesh, const int32_t **vmap_dev, const int32_t **fmap_dev);
 
-/* P' = X P for an extracted mesh: row i of out_dev (float[3 V']) = row vmap[i] of P_dev (the
- * source level's positions, float[3 V_level]); enqueued on `stream`. Errors: INVALID_ARG, DEVICE. */
+/* P' = X P for an extracted or reordered mesh: row i of out_dev (float[3 V']) = row vmap[i] of P_dev
+ * (the source's positions, float[3 V_source]); enqueued on `stream`. Errors: INVALID_ARG, DEVICE. */
 alsub_status alsub_mesh_gather(alsub_mesh_t mesh, const float *P_dev, float *out_dev, void *stream);
 
 /*

@@ -332,3 +332,87 @@ def regular_patches(level: dict, samples: int):
         flags[r] = True
         grids[r] = np.einsum("ai,bj,ijd->bad", B, B, ctrl)
     return flags, grids
+
+
+def vertex_graph(mesh: dict) -> list[list[int]]:
+    """The graph of the mesh Laplacian (Sec. 4.5): vertices u, w adjacent when an edge of some face
+    joins them; each list increasing, without repeats."""
+    V = int(mesh["V"])
+    off = np.asarray(mesh["off"], dtype=np.int64)
+    fv = np.asarray(mesh["fv"], dtype=np.int64)
+    nbr = [set() for _ in range(V)]
+    for f in range(len(off) - 1):
+        ring = fv[off[f]:off[f + 1]].tolist()
+        for i, u in enumerate(ring):
+            w = ring[(i + 1) % len(ring)]
+            if u != w:
+                nbr[u].add(w)
+                nbr[w].add(u)
+    return [sorted(s) for s in nbr]
+
+
+def cuthill_mckee(adj: list[list[int]]) -> np.ndarray:
+    """Cuthill-McKee order (Cuthill and McKee 1969) of a graph: order[k] = the vertex labelled k.
+
+    Each connected component starts at its unlabelled vertex of least degree (least index on ties);
+    the labelled vertices are visited in label order, and each labels its unlabelled neighbours in
+    increasing (degree, index). Components follow one another in the order their start vertices
+    are found."""
+    V = len(adj)
+    deg = [len(a) for a in adj]
+    label = [-1] * V
+    order = []
+    by_degree = sorted(range(V), key=lambda v: (deg[v], v))
+    for s in by_degree:
+        if label[s] >= 0:
+            continue
+        label[s] = len(order)
+        order.append(s)
+        head = label[s]
+        while head < len(order):
+            u = order[head]
+            head += 1
+            fresh = sorted((w for w in adj[u] if label[w] < 0), key=lambda w: (deg[w], w))
+            for w in fresh:
+                label[w] = len(order)
+                order.append(w)
+    return np.asarray(order, dtype=np.int64)
+
+
+def bandwidth(adj: list[list[int]], new_id=None) -> int:
+    """max |new_id[u] - new_id[w]| over the edges (the bandwidth of the Laplacian)."""
+    b = 0
+    for u, a in enumerate(adj):
+        for w in a:
+            b = max(b, abs(int(new_id[u] if new_id is not None else u) - int(new_id[w] if new_id is not None else w)))
+    return b
+
+
+def rcm_reorder(mesh: dict) -> dict:
+    """Mesh reordering of Sec. 4.5: reverse Cuthill-McKee (George 1971: the Cuthill-McKee order
+    reversed) on the graph of the mesh Laplacian permutes the vertices (the rows of M); the faces
+    (the columns) are then sorted by their first non-zero row, i.e. by the least new index among
+    their vertices, faces with the same least vertex keeping their input order. Each face keeps its
+    corners in their cyclic order from the same first corner; creases keep their order with their
+    ends renamed. vmap[new vertex] = old vertex, fmap[new face] = old face."""
+    V, F = int(mesh["V"]), int(mesh["F"])
+    off = np.asarray(mesh["off"], dtype=np.int64)
+    fv = np.asarray(mesh["fv"], dtype=np.int64)
+    order = cuthill_mckee(vertex_graph(mesh))
+    vmap = order[::-1].copy()
+    new_id = np.empty(V, dtype=np.int64)
+    new_id[vmap] = np.arange(V)
+    first = np.array([new_id[fv[off[f]:off[f + 1]]].min() for f in range(F)], dtype=np.int64)
+    fmap = np.argsort(first, kind="stable")
+    sizes = np.diff(off)[fmap]
+    noff = np.zeros(F + 1, dtype=np.int64)
+    noff[1:] = np.cumsum(sizes)
+    nfv = np.concatenate([new_id[fv[off[f]:off[f + 1]]] for f in fmap]) if F else np.zeros(0, np.int64)
+    cv = np.asarray(mesh.get("crease_verts", np.zeros((0, 2))), dtype=np.int64).reshape(-1, 2)
+    cs = np.asarray(mesh.get("crease_sharp", np.zeros(0)), dtype=np.float32).reshape(-1)
+    out = dict(V=V, F=F, off=noff.astype(np.int32), fv=nfv.astype(np.int32), vmap=vmap.astype(np.int32),
+               fmap=fmap.astype(np.int32), crease_verts=new_id[cv].astype(np.int32).reshape(-1, 2),
+               crease_sharp=cs.copy())
+    if "P" in mesh:
+        out["P"] = np.asarray(mesh["P"])[vmap]
+    return out

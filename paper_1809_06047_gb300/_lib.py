@@ -52,6 +52,8 @@ SIGNATURES = {
     "alsub_topology_eval_patches": [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p],
     "alsub_mesh_info": [c_void_p, P(c_int32), P(c_int64), P(c_int64), P(c_int64), P(c_int64)],
     "alsub_topology_extract": [c_void_p, c_int32, c_void_p, c_int32, c_void_p, P(c_void_p)],
+    "alsub_mesh_reorder": [c_void_p, c_void_p, P(c_void_p), P(c_int32)],
+    "alsub_mesh_arrays": [c_void_p, P(c_void_p), P(c_void_p), P(c_void_p), P(c_void_p)],
     "alsub_mesh_extract_maps": [c_void_p, P(c_void_p), P(c_void_p)],
     "alsub_mesh_gather": [c_void_p, c_void_p, c_void_p, c_void_p],
     "alsub_mesh_create": [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,

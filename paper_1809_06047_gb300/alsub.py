@@ -94,7 +94,7 @@ class Mesh:
 
     @classmethod
     def _wrap(cls, h: ctypes.c_void_p) -> "Mesh":
-        """A Mesh object around a handle the library made (an extracted mesh)."""
+        """A Mesh object around a handle the library made (an extracted or reordered mesh)."""
         self = cls.__new__(cls)
         self._h = h
         sch, V, F, nnz, K = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
@@ -107,15 +107,39 @@ class Mesh:
         self.boundary_edges = int(b.value)
         return self
 
+    def reorder(self, stream=None) -> "Mesh":
+        """alsub_mesh_reorder (Sec. 4.5): the same mesh with its vertices in reverse Cuthill-McKee
+        order and its faces sorted by their least new vertex; maps() and gather() relate it to this
+        one. The breadth-first levels it took are in `.rcm_levels`."""
+        h, lv = ctypes.c_void_p(), ctypes.c_int32()
+        _check(lib().alsub_mesh_reorder(self._h, ctypes.c_void_p(_stream(stream)), ctypes.byref(h), ctypes.byref(lv)))
+        out = Mesh._wrap(h)
+        out.rcm_levels = int(lv.value)
+        return out
+
+    def arrays(self, stream=None) -> dict:
+        """alsub_mesh_arrays, copied to the host: off, fv, crease_verts (K x 2), crease_sharp."""
+        o, f, cv, cs = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(lib().alsub_mesh_arrays(self._h, ctypes.byref(o), ctypes.byref(f), ctypes.byref(cv), ctypes.byref(cs)))
+        Kc = ctypes.c_int64()
+        _check(lib().alsub_mesh_info(self._h, None, None, None, None, ctypes.byref(Kc)))
+        K = int(Kc.value)
+        return dict(V=self.V, F=self.F,
+                    off=copy_to_host(o.value, 4 * (self.F + 1), np.int32, self.F + 1, stream),
+                    fv=copy_to_host(f.value, 4 * self.nnz, np.int32, self.nnz, stream),
+                    crease_verts=copy_to_host(cv.value, 8 * K, np.int32, 2 * K, stream).reshape(-1, 2),
+                    crease_sharp=copy_to_host(cs.value, 4 * K, np.float32, K, stream))
+
     def maps(self):
-        """(vertex map int32[V], face map int32[F]) of an extracted mesh: source vertex / face ids."""
+        """(vertex map int32[V], face map int32[F]) of an extracted or reordered mesh: source vertex /
+        face ids."""
         vm, fm = ctypes.c_void_p(), ctypes.c_void_p()
         _check(lib().alsub_mesh_extract_maps(self._h, ctypes.byref(vm), ctypes.byref(fm)))
         return (copy_to_host(vm.value, 4 * self.V, np.int32, self.V),
                 copy_to_host(fm.value, 4 * self.F, np.int32, self.F))
 
     def gather(self, P: torch.Tensor, out=None, stream=None) -> torch.Tensor:
-        """alsub_mesh_gather: this extracted mesh's rows of the source level's positions."""
+        """alsub_mesh_gather: this extracted or reordered mesh's rows of the source's positions."""
         assert P.is_cuda and P.dtype == torch.float32 and P.is_contiguous()
         if out is None:
             out = torch.empty((self.V, 3), dtype=torch.float32, device=P.device)

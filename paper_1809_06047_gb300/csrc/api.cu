@@ -769,9 +769,35 @@ alsub_status alsub_topology_extract(alsub_topology_t topo, int32_t level, const 
     return ALSUB_OK;
 }
 
+alsub_status alsub_mesh_reorder(alsub_mesh_t mesh, void *stream, alsub_mesh_t *out, int32_t *levels) {
+    if (!mesh || !out) return fail(ALSUB_ERR_INVALID_ARG, "bad reorder arguments");
+    *out = nullptr;
+    alsub_mesh_s *h = new (std::nothrow) alsub_mesh_s();
+    if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
+    int lv = 0;
+    alsub_status st = reorder_mesh(mesh->m, (cudaStream_t)stream, h->m, &lv);
+    if (st != ALSUB_OK) {
+        alsub_mesh_destroy(h);
+        return st;
+    }
+    if (levels) *levels = lv;
+    *out = h;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_mesh_arrays(alsub_mesh_t h, const int32_t **off_dev, const int32_t **fv_dev,
+                               const int32_t **crease_verts_dev, const float **crease_sharp_dev) {
+    if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL mesh");
+    if (off_dev) *off_dev = h->m.d_off;
+    if (fv_dev) *fv_dev = h->m.d_fv;
+    if (crease_verts_dev) *crease_verts_dev = h->m.d_cv;
+    if (crease_sharp_dev) *crease_sharp_dev = h->m.d_cs;
+    return ALSUB_OK;
+}
+
 alsub_status alsub_mesh_extract_maps(alsub_mesh_t h, const int32_t **vmap_dev, const int32_t **fmap_dev) {
     if (!h) return fail(ALSUB_ERR_INVALID_ARG, "NULL mesh");
-    if (!h->m.d_vmap) return fail(ALSUB_ERR_INVALID_ARG, "not an extracted mesh");
+    if (!h->m.d_vmap) return fail(ALSUB_ERR_INVALID_ARG, "mesh has no source maps (not extracted or reordered)");
     if (vmap_dev) *vmap_dev = h->m.d_vmap;
     if (fmap_dev) *fmap_dev = h->m.d_fmap;
     return ALSUB_OK;
@@ -779,7 +805,7 @@ alsub_status alsub_mesh_extract_maps(alsub_mesh_t h, const int32_t **vmap_dev, c
 
 alsub_status alsub_mesh_gather(alsub_mesh_t h, const float *P_dev, float *out_dev, void *stream) {
     if (!h || !P_dev || !out_dev) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
-    if (!h->m.d_vmap) return fail(ALSUB_ERR_INVALID_ARG, "not an extracted mesh");
+    if (!h->m.d_vmap) return fail(ALSUB_ERR_INVALID_ARG, "mesh has no source maps (not extracted or reordered)");
     gather_rows(h->m.V, h->m.d_vmap, P_dev, out_dev, (cudaStream_t)stream);
     return finish("alsub_mesh_gather");
 }

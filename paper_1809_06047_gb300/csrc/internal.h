@@ -177,6 +177,10 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
 void apply_edits(TopoImpl &T, int k, float *out, cudaStream_t s);
 // P' = X P: rows vmap[i] of P into row i of out (xyz rows).
 void gather_rows(int n, const int *vmap, const float *P, float *out, cudaStream_t s);
+// Mesh reordering (Sec. 4.5): RCM on the graph of the mesh Laplacian, faces sorted by their least
+// new vertex; fills `out` (arrays, maps, counts) on `s`, which it synchronises once per
+// breadth-first level. *levels_out: breadth-first levels over all components.
+alsub_status reorder_mesh(const MeshImpl &M, cudaStream_t s, MeshImpl &out, int *levels_out);
 // Boundary repair of one Catmull-Clark step (Sec. 3.2 "Boundaries", Fig. module_boundary): with
 // positions, overwrite the boundary edge points (midpoints) and boundary vertices (Eq.
 // CC_boundary) of level l + 1; with `list`, write level l + 1's boundary list.

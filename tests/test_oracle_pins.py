@@ -661,3 +661,115 @@ def test_regular_patch_reproduces_linear_functions_and_detects_irregularity():
     mm = dict(m, P=P, crease_verts=np.array([[0, 1]], np.int32), crease_sharp=np.array([2.0], np.float32))
     fl2, _ = oracle.regular_patches(mm, 3)
     assert fl2.sum() < flags.sum()
+
+
+# ---------------------------------------------------------------- mesh reordering (Sec. 4.5)
+
+def test_cuthill_mckee_matches_scipy_when_the_start_is_unique():
+    """With one connected component whose least-degree vertex is unique, the reverse Cuthill-McKee
+    order is scipy's (its siblings are visited by degree, ties in index order)."""
+    sp = pytest.importorskip("scipy.sparse")
+    csgraph = pytest.importorskip("scipy.sparse.csgraph")
+    rng = np.random.default_rng(11)
+    checked = 0
+    for _ in range(120):
+        n = int(rng.integers(6, 60))
+        A = rng.random((n, n)) < rng.uniform(0.06, 0.3)
+        A = np.triu(A, 1)
+        A = A | A.T
+        for i in range(n):                       # every vertex of degree >= 2 ...
+            if A[i].sum() < 2:
+                for j in ((i + 1) % n, (i + 2) % n):
+                    A[i, j] = A[j, i] = True
+        B = np.zeros((n + 1, n + 1), dtype=bool)  # ... and one pendant vertex: the unique start
+        B[:n, :n] = A
+        p = int(rng.integers(0, n))
+        B[n, p] = B[p, n] = True
+        G = sp.csr_matrix(B.astype(np.int32))
+        if csgraph.connected_components(G)[0] != 1:
+            continue
+        adj = [np.flatnonzero(B[i]).tolist() for i in range(n + 1)]
+        rcm = oracle.cuthill_mckee(adj)[::-1]
+        np.testing.assert_array_equal(rcm, csgraph.reverse_cuthill_mckee(G, symmetric_mode=True))
+        checked += 1
+    assert checked > 100
+
+
+def _ladder(n):
+    """A strip of n quads: bottom row 0 .. n, top row n+1 .. 2n+1."""
+    fv = []
+    for i in range(n):
+        fv += [i, i + 1, n + 2 + i, n + 1 + i]
+    return dict(V=2 * (n + 1), F=n, off=np.arange(n + 1, dtype=np.int32) * 4, fv=np.asarray(fv, np.int32))
+
+
+@pytest.mark.parametrize("n", [2, 3, 7])
+def test_cuthill_mckee_of_a_ladder_alternates_the_rows(n):
+    """Closed form: the start is corner 0 (degree 2, least index); its neighbours are top vertex
+    n+1 (degree 2) and bottom vertex 1 (degree 3), so the top one comes first, and from there every
+    rung follows: bottom vertex i at position 2i, top vertex n+1+i at 2i+1. RCM bandwidth 2, against
+    n+1 for the row-by-row numbering. (A single quad, n = 1, is a 4-cycle: 0, 1, 2, 3.)"""
+    m = _ladder(n)
+    order = oracle.cuthill_mckee(oracle.vertex_graph(m))
+    expect = np.empty(2 * (n + 1), dtype=np.int64)
+    expect[0::2] = np.arange(n + 1)
+    expect[1::2] = np.arange(n + 1, 2 * n + 2)
+    np.testing.assert_array_equal(order, expect)
+    r = oracle.rcm_reorder(m)
+    assert oracle.bandwidth(oracle.vertex_graph(r)) == 2
+    assert oracle.bandwidth(oracle.vertex_graph(m)) == n + 1
+    np.testing.assert_array_equal(oracle.cuthill_mckee(oracle.vertex_graph(_ladder(1))), [0, 1, 2, 3])
+
+
+def _shuffled(m, seed):
+    rng = np.random.default_rng(seed)
+    pv = rng.permutation(m["V"])
+    order = rng.permutation(m["F"])
+    off, fv = np.asarray(m["off"]), np.asarray(m["fv"])
+    faces = [pv[fv[off[r]:off[r + 1]]] for r in order]
+    noff = np.zeros(m["F"] + 1, np.int32)
+    noff[1:] = np.cumsum([len(f) for f in faces])
+    out = dict(m, off=noff, fv=np.concatenate(faces).astype(np.int32), P=np.asarray(m["P"])[np.argsort(pv)])
+    if "crease_verts" in m:
+        out["crease_verts"] = pv[np.asarray(m["crease_verts"])].astype(np.int32).reshape(-1, 2)
+    return out
+
+
+@pytest.mark.parametrize("scheme,mesh", [
+    ("cc", lambda: synth.torus_cc_mixed(10, 8, merge_frac=0.05, split_frac=0.05, crease_frac=0.08, seed=41)),
+    ("cc", lambda: synth.holed_cc_mixed(12, 10, holes=3, seed=42)),
+    ("loop", lambda: synth.torus_tri(8, 6, seed=43)),
+])
+def test_reordering_keeps_the_surface(scheme, mesh):
+    """Renumbering changes no point of the refined surface: two levels of the reordered mesh give
+    the same set of points as two levels of the input (creases and boundaries included), while the
+    reordered faces are sorted by their least vertex and keep their corners' cyclic order."""
+    m = _shuffled(mesh(), 44)
+    r = oracle.rcm_reorder(m)
+    assert sorted(r["vmap"].tolist()) == list(range(m["V"]))
+    assert sorted(r["fmap"].tolist()) == list(range(m["F"]))
+    off, noff = np.asarray(m["off"]), r["off"]
+    new_id = np.empty(m["V"], np.int64)
+    new_id[r["vmap"]] = np.arange(m["V"])
+    least = [r["fv"][noff[f]:noff[f + 1]].min() for f in range(r["F"])]
+    assert all(a <= b for a, b in zip(least, least[1:]))
+    ties = [f for f in range(1, r["F"]) if least[f] == least[f - 1]]
+    assert ties and all(r["fmap"][f - 1] < r["fmap"][f] for f in ties)   # stable: input order
+    for f, g in enumerate(r["fmap"]):
+        np.testing.assert_array_equal(r["fv"][noff[f]:noff[f + 1]], new_id[m["fv"][off[g]:off[g + 1]]])
+    a = oracle.subdivide(m, 2, scheme, keep_all=False)[2]["P"]
+    b = oracle.subdivide(r, 2, scheme, keep_all=False)[2]["P"]
+    assert a.shape == b.shape
+    a = a[np.lexsort(a.T[::-1])]
+    b = b[np.lexsort(b.T[::-1])]
+    np.testing.assert_allclose(a, b, rtol=0, atol=1e-12)
+
+
+def test_reordering_restores_a_small_bandwidth():
+    """A shuffled 24 x 20 torus: its bandwidth is of the order of V; after RCM it is below twice
+    the widest breadth-first level of a torus grid (the diagonal of its 24 x 20 cross-section)."""
+    m = _shuffled(synth.torus_cc_plain(24, 20), 45)
+    g = oracle.vertex_graph(m)
+    r = oracle.rcm_reorder(m)
+    assert oracle.bandwidth(g) > m["V"] // 2
+    assert oracle.bandwidth(oracle.vertex_graph(r)) <= 2 * (24 + 20)
