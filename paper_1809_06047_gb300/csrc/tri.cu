@@ -47,9 +47,26 @@ struct TriArgs {
 };
 
 
+// The face rows of a Loop / sqrt(3) step go out through shared memory, 512 contiguous bytes per
+// store instruction (1), or straight from each lane, 48 / 36 bytes at that lane stride (0).
+// Measured on the 128 x 128 tori: sqrt(3) L8 3.06 against 3.51 ms per step (its rows are 9 scalar
+// ints); Loop L6 1.79 against 1.73 ms (its rows are three 16-byte stores already, and staging
+// adds a spill).
+#ifndef ALSUB_LOOP_TOPO_SMEM
+#define ALSUB_LOOP_TOPO_SMEM 0
+#endif
+#ifndef ALSUB_SQRT3_TOPO_SMEM
+#define ALSUB_SQRT3_TOPO_SMEM 1
+#endif
+
 template <bool TOPO, bool HELP, bool EVAL>
-__device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
-    if (r >= a.F || failed(a.status)) return;
+__device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
+    // with staged face rows every lane of the warp takes part in the stores (a lane past the end
+    // works on face 0 and writes nothing); otherwise such a lane leaves at once
+    constexpr bool STAGE = TOPO && ALSUB_LOOP_TOPO_SMEM;
+    const bool live = r_in < a.F && !failed(a.status);
+    if (!STAGE && !live) return;
+    const int r = live ? r_in : 0;
     const int c = 3 * r, V = a.V, E2 = 2 * a.E;
     int vv[3], ee[3], tt[3];
     bool ow[3];
@@ -62,11 +79,33 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
         ow[j] = loop_own_gi(a.l, r, j, a.z);
     }
     if (TOPO) {
-        // the 12 ints of the four children, 48 bytes at 48 r: three 16-byte stores
-        int4 *o = reinterpret_cast<int4 *>(a.fvn + 12 * (size_t)r);
-        o[0] = make_int4(vv[0], V + ee[0], V + ee[2], vv[1]);
-        o[1] = make_int4(V + ee[1], V + ee[0], vv[2], V + ee[2]);
-        o[2] = make_int4(V + ee[1], V + ee[0], V + ee[1], V + ee[2]);
+        // the 12 ints of the four children, 48 bytes at 48 r
+        const int4 q0 = make_int4(vv[0], V + ee[0], V + ee[2], vv[1]);
+        const int4 q1 = make_int4(V + ee[1], V + ee[0], vv[2], V + ee[2]);
+        const int4 q2 = make_int4(V + ee[1], V + ee[0], V + ee[1], V + ee[2]);
+        if (STAGE) {
+            // the warp's 32 faces own 96 consecutive int4: staged in shared memory and written
+            // back 512 contiguous bytes per store instruction
+            __shared__ int4 st[kBlock / 32][96];
+            const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            st[w][3 * lane + 0] = q0;
+            st[w][3 * lane + 1] = q1;
+            st[w][3 * lane + 2] = q2;
+            __syncwarp();
+            const int base = r_in - lane;
+            int4 *o = reinterpret_cast<int4 *>(a.fvn) + 3 * (size_t)base;
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int q = 32 * k + lane;
+                if (base + q / 3 < a.F) o[q] = st[w][q];
+            }
+            if (!live) return;
+        } else {
+            int4 *o = reinterpret_cast<int4 *>(a.fvn + 12 * (size_t)r);
+            o[0] = q0;
+            o[1] = q1;
+            o[2] = q2;
+        }
     }
     if (HELP) {
         int oe[12], ot[12];
@@ -205,8 +244,11 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r) {
 }
 
 template <bool TOPO, bool HELP, bool EVAL>
-__device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
-    if (r >= a.F || failed(a.status)) return;
+__device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r_in) {
+    constexpr bool STAGE = TOPO && ALSUB_SQRT3_TOPO_SMEM;   // as in loop_body
+    const bool live = r_in < a.F && !failed(a.status);
+    if (!STAGE && !live) return;
+    const int r = live ? r_in : 0;
     const int c = 3 * r, V = a.V;
     int vv[3], tt[3];
 #pragma unroll
@@ -215,10 +257,42 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r) {
         tt[j] = a.t.twin(c + j);
     }
     if (TOPO) {
+        if (STAGE) {
+            // the three children (9 ints, 36 bytes at 36 r): the warp's 288 consecutive ints are
+            // staged in shared memory and written back as 72 int4, 512 contiguous bytes per store
+            // instruction (the warp's first int is at 1152-byte alignment)
+            __shared__ __align__(16) int st[kBlock / 32][288];
+            const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-        for (int j = 0; j < 3; j++) {
-            int *o = a.fvn + 3 * (size_t)(c + j);
-            o[0] = vv[j]; o[1] = V + tt[j] / 3; o[2] = V + r;
+            for (int j = 0; j < 3; j++) {
+                st[w][9 * lane + 3 * j + 0] = vv[j];
+                st[w][9 * lane + 3 * j + 1] = V + tt[j] / 3;
+                st[w][9 * lane + 3 * j + 2] = V + r;
+            }
+            __syncwarp();
+            const long long g0 = 9LL * (r_in - lane), n = 9LL * a.F;
+            int4 *o4 = reinterpret_cast<int4 *>(a.fvn + g0);
+            const int4 *s4 = reinterpret_cast<const int4 *>(st[w]);
+#pragma unroll
+            for (int k = 0; k < 3; k++) {
+                const int q = 32 * k + lane;
+                if (q < 72) {
+                    const long long e = g0 + 4 * q;
+                    if (e + 4 <= n) {
+                        o4[q] = s4[q];
+                    } else {
+                        for (int t = 0; t < 4; t++)
+                            if (e + t < n) a.fvn[e + t] = st[w][4 * q + t];
+                    }
+                }
+            }
+            if (!live) return;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                int *o = a.fvn + 3 * (size_t)(c + j);
+                o[0] = vv[j]; o[1] = V + tt[j] / 3; o[2] = V + r;
+            }
         }
     }
     if (HELP) {
