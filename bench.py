@@ -462,7 +462,7 @@ def ordering_leg():
     out = {"workload": f"{DEFAULT_WORKLOAD}, generator order vs shuffled vertex ids and face order vs "
                        "the shuffled mesh reordered by RCM"}
     Msh = alsub.Mesh.from_dict(sh, "cc")
-    Msh.reorder()                                 # warm-up (first launches of its kernels)
+    Msh.reorder().close()                         # warm-up (first launches of its kernels)
     torch.cuda.synchronize()
     times = []
     for _ in range(5):

@@ -5,7 +5,7 @@
  *
  * Scope: one uniform subdivision step, repeated level by level, for Catmull-Clark (Sec. 3),
  * Loop (Appendix B) and sqrt(3) (Appendix A) on 2-manifold meshes -- closed, or open with
- * boundaries for Catmull-Clark (Sec. 3.1 and 3.2 "Boundaries") -- with sharp and semi-sharp
+ * boundaries for Catmull-Clark (Sec. 3.1 and 3.2 "Boundaries") and Loop -- with sharp and semi-sharp
  * creases for Catmull-Clark and Loop (Sec. 3.3), and the extraction of selective subdivision
  * (Sec. 3.4). Topology refinement (the build step
  * of Fig. module_core) is integer work that emits each level's face table directly; vertex
@@ -55,7 +55,7 @@ typedef enum {
     ALSUB_OK = 0,
     ALSUB_ERR_INVALID_ARG = 1,   /* a pointer, count, index or sharpness out of range */
     ALSUB_ERR_NONMANIFOLD = 2,   /* duplicate directed edge, edge of >2 faces, vertex with >1 fan */
-    ALSUB_ERR_UNSUPPORTED = 3,   /* open Loop / sqrt(3) mesh, crease at a boundary, counts beyond
+    ALSUB_ERR_UNSUPPORTED = 3,   /* open sqrt(3) mesh, crease at a boundary, counts beyond
                                     int32, valence > 1024 */
     ALSUB_ERR_OOM = 4,           /* device allocation failed or a budget is exhausted */
     ALSUB_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
@@ -101,8 +101,8 @@ alsub_status alsub_plan(alsub_scheme scheme, int64_t num_verts, int64_t num_face
  * "Boundaries"): E = (nnz + boundary_edges) / 2 on level 0, the same recurrences after it (each
  * boundary edge splits into two boundary edges). boundary_edges = 0 is alsub_plan.
  * Errors: those of alsub_plan; INVALID_ARG when nnz + boundary_edges is odd or boundary_edges is
- * negative or above nnz; UNSUPPORTED for boundary_edges > 0 with Loop or sqrt(3) (the paper
- * gives them no boundary rule).
+ * negative or above nnz; UNSUPPORTED for boundary_edges > 0 with sqrt(3) (Appendix A omits its
+ * boundary rule). Loop takes the Catmull-Clark counts' boundary rule: a boundary edge splits in two.
  */
 alsub_status alsub_plan_open(alsub_scheme scheme, int64_t num_verts, int64_t num_faces, int64_t nnz,
                              int64_t boundary_edges, int32_t levels, int64_t *counts_host);
@@ -127,9 +127,12 @@ alsub_status alsub_plan_open(alsub_scheme scheme, int64_t num_verts, int64_t num
  * device (it synchronises `stream`); alsub_mesh_boundary_edges reports the count, which sizes the
  * levels (alsub_plan_open). A vertex must lie on at most two boundary edges (one fan; checked when
  * the topology is built), and no crease may touch a boundary vertex (the paper defines no such
- * combination: UNSUPPORTED). Loop and sqrt(3) meshes must be closed.
+ * combination: UNSUPPORTED). Loop meshes may be open too, with the same two boundary rules (Appendix
+ * B gives Loop none of its own; these keep its boundary the cubic B-spline curve of the control
+ * polygon, as for Catmull-Clark); the Loop operator (alsub_build_operator) refuses them. sqrt(3)
+ * meshes must be closed.
  * Errors: INVALID_ARG, NONMANIFOLD (a repeated directed edge found by the boundary count),
- * UNSUPPORTED (counts beyond int32, odd nnz for Loop / sqrt(3), a crease at the boundary), OOM,
+ * UNSUPPORTED (counts beyond int32, odd nnz for sqrt(3), a crease at the boundary), OOM,
  * DEVICE.
  */
 alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t num_verts, int32_t num_faces,
@@ -140,8 +143,8 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t num_verts, int32_t n
 
 alsub_status alsub_mesh_destroy(alsub_mesh_t mesh);
 
-/* Number of boundary edges (edges of one face) of a mesh; 0 for a closed mesh and for Loop and
- * sqrt(3) meshes (those must be closed). Host only. Errors: INVALID_ARG. */
+/* Number of boundary edges (edges of one face) of a mesh; 0 for a closed mesh and for sqrt(3)
+ * meshes (those must be closed). Host only. Errors: INVALID_ARG. */
 alsub_status alsub_mesh_boundary_edges(alsub_mesh_t mesh, int64_t *boundary_edges);
 
 /* Scheme, vertex, face, corner and crease counts of a mesh (host only; any pointer may be NULL).
@@ -346,7 +349,7 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
  * The operator keeps a pointer to the topology, which must outlive it. Synchronises `stream`
  * (the non-zero counts size the allocations).
  * Errors: INVALID_ARG (topology not built, no flags), UNSUPPORTED (a stencil row of more than 192
- * entries), OOM, DEVICE.
+ * entries; an open Loop mesh), OOM, DEVICE.
  */
 typedef enum { ALSUB_OP_CHAIN = 1, ALSUB_OP_COMPOSE = 2, ALSUB_OP_TRANSPOSE = 4 } alsub_operator_flags;
 

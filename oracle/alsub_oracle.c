@@ -26,13 +26,15 @@
  *                  is evaluated in FP32, in the fixed order t = 3*s; u = s_o + t; w = u * 0.25;
  *                  y = w - 1; max(y, 0) (compile with -ffp-contract=off).
  *                  sqrt(3) ignores sharpness (the paper gives it no crease treatment).
- *   Boundaries     Catmull-Clark only (Sec. 3.1 "Boundaries", Eq. CC_boundary): an edge with one
+ *   Boundaries     Catmull-Clark (Sec. 3.1 "Boundaries", Eq. CC_boundary): an edge with one
  *                  face is a boundary edge; its edge point is its midpoint, and a boundary vertex
  *                  becomes 3/4 p + 1/8 (p_prev + p_next) with its two boundary neighbours. Every
  *                  other point follows the closed-mesh rules. A vertex on more than two boundary
  *                  edges (several fans) is non-manifold; a crease that touches a boundary vertex
- *                  is refused (the paper defines no combination). Loop and sqrt(3) refuse open
- *                  meshes (the paper gives them no boundary rule).
+ *                  is refused (the paper defines no combination). Loop (Appendix B gives no
+ *                  boundary rule) takes the same two rules on its boundary, so that the boundary
+ *                  is again the cubic B-spline curve of its control polygon; sqrt(3) refuses open
+ *                  meshes (Appendix A omits its boundary treatment).
  * Edge numbering follows Sec. 3.2: edges are numbered in the order of the non-zeros of the upper
  * triangle of E, i.e. lexicographically by (min vertex, max vertex).
  * Child faces: face r with corners j = 0..c-1 is replaced by its children in corner order; the
@@ -562,8 +564,8 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
     for (int e = 0; e < E; e++) {
         int c0 = h->eo[e], c1 = h->tw[c0];
         int a = h->ea[e], b = h->eb[e];
-        if (c1 < 0) {                              /* patch mode only: beyond the cut */
-            for (int d = 0; d < 3; d++) ep[3 * e + d] = NAN;
+        if (c1 < 0) {                              /* boundary edge: its midpoint */
+            for (int d = 0; d < 3; d++) ep[3 * e + d] = h->patch ? NAN : 0.5 * (P[3 * a + d] + P[3 * b + d]);
             continue;
         }
         int k = h->fv[h->pv[c0]], l = h->fv[h->pv[c1]];
@@ -571,8 +573,15 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
             ep[3 * e + d] = 0.375 * (P[3 * a + d] + P[3 * b + d]) + 0.125 * (P[3 * k + d] + P[3 * l + d]);
         if (cr) crease_edge((double)cr->es[e], P + 3 * a, P + 3 * b, ep + 3 * e);
     }
-    /* vertex: (1 - n beta) p + beta sum p_j (Eq. loop_smooth) */
+    /* vertex: (1 - n beta) p + beta sum p_j (Eq. loop_smooth); a boundary vertex as in
+     * Eq. CC_boundary */
     for (int v = 0; v < V; v++) {
+        int nb, pb;
+        if (boundary_neighbours(h, v, &nb, &pb)) {
+            for (int d = 0; d < 3; d++)
+                Pn[3 * v + d] = h->patch ? NAN : 0.75 * P[3 * v + d] + 0.125 * (P[3 * pb + d] + P[3 * nb + d]);
+            continue;
+        }
         int nv = h->vo[v + 1] - h->vo[v];
         double beta = loop_beta(nv), sm[3] = {0, 0, 0};
         for (int q = h->vo[v]; q < h->vo[v + 1]; q++) {
@@ -581,7 +590,7 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
         }
         for (int d = 0; d < 3; d++) Pn[3 * v + d] = (1.0 - nv * beta) * P[3 * v + d] + beta * sm[d];
         if (cr) crease_vertex(cr, P, v, Pn + 3 * v);
-        if (h->bo[v] >= 0 || (cr && cr->taint[v])) for (int d = 0; d < 3; d++) Pn[3 * v + d] = NAN;
+        if (cr && cr->taint[v]) for (int d = 0; d < 3; d++) Pn[3 * v + d] = NAN;
     }
     /* topology: triangle (p_k, p_l, p_m) -> three corner triangles and the centre one */
     for (int r = 0; r <= 4 * F; r++) o->off[r] = 3 * r;
@@ -607,6 +616,14 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
     if (R) {
         row rw = {0, 0, NULL, NULL};
         for (int v = 0; v < V && !st; v++) {
+            int nb, pb;
+            if (boundary_neighbours(h, v, &nb, &pb)) {
+                st = row_add(&rw, v, 0.75);
+                if (!st) st = row_add(&rw, pb, 0.125);
+                if (!st) st = row_add(&rw, nb, 0.125);
+                if (!st) st = coo_push_row(R, v, &rw);
+                continue;
+            }
             int nv = h->vo[v + 1] - h->vo[v];
             double beta = loop_beta(nv);
             st = row_add(&rw, v, 1.0 - nv * beta);
@@ -617,6 +634,12 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
         }
         for (int e = 0; e < E && !st; e++) {
             int c0 = h->eo[e], c1 = h->tw[c0];
+            if (c1 < 0) {
+                st = row_add(&rw, h->ea[e], 0.5);
+                if (!st) st = row_add(&rw, h->eb[e], 0.5);
+                if (!st) st = coo_push_row(R, V + e, &rw);
+                continue;
+            }
             st = row_add(&rw, h->ea[e], 0.375);
             if (!st) st = row_add(&rw, h->eb[e], 0.375);
             if (!st) st = row_add(&rw, h->fv[h->pv[c0]], 0.125);
@@ -741,7 +764,7 @@ int or_run(int scheme, int levels, int keep_all, int want_operator, int patch,
         olevel *L = &res->L[last];
         if (patch && l == levels) break;          /* a patch's child may reference the cut (-1) */
         hedge h;
-        st = hedge_build(&h, L->V, L->F, L->off, L->fv, patch ? 2 : scheme == OR_CC);
+        st = hedge_build(&h, L->V, L->F, L->off, L->fv, patch ? 2 : scheme != OR_SQRT3);
         h.patch = patch;
         if (st) { hedge_free(&h); break; }
         L->E = h.E;

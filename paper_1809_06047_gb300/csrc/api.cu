@@ -608,8 +608,8 @@ alsub_status alsub_plan_open(alsub_scheme scheme, int64_t V, int64_t F, int64_t 
         return fail(ALSUB_ERR_INVALID_ARG, "bad counts");
     if (scheme != ALSUB_CATMULL_CLARK && nnz != 3 * F)
         return fail(ALSUB_ERR_INVALID_ARG, "Loop and sqrt(3) need a triangle mesh");
-    if (B > 0 && scheme != ALSUB_CATMULL_CLARK)
-        return fail(ALSUB_ERR_UNSUPPORTED, "boundaries are supported for Catmull-Clark only");
+    if (B > 0 && scheme == ALSUB_SQRT3)
+        return fail(ALSUB_ERR_UNSUPPORTED, "sqrt(3) has no boundary rule (Appendix A omits it)");
     if ((nnz + B) % 2) {
         if (B == 0) return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
         return fail(ALSUB_ERR_INVALID_ARG, "nnz + boundary edges must be even");
@@ -651,7 +651,7 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
         for (int r = 0; r <= F; r++) off[r] = r * order;
     }
     const long long nnz = off[F];
-    if (scheme != ALSUB_CATMULL_CLARK && nnz % 2)
+    if (scheme == ALSUB_SQRT3 && nnz % 2)
         return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
     std::vector<int> used(V, 0), mark(V, -1);
     for (int r = 0; r < F; r++) {
@@ -701,17 +701,18 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
     if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cv, cv.data(), sizeof(int) * 2 * M.K, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cs, cs.data(), sizeof(float) * M.K, cudaMemcpyHostToDevice, s);
     // the host vectors die on return: the copies complete at the stream synchronisation below
-    // (for Catmull-Clark, the boundary scan's, which runs after them on the same stream)
-    if (e == cudaSuccess && scheme != ALSUB_CATMULL_CLARK) e = cudaStreamSynchronize(s);
+    // (for Catmull-Clark and Loop, the boundary scan's, which runs after them on the same stream)
+    if (e == cudaSuccess && scheme == ALSUB_SQRT3) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
         cleanup();
         return cuda_fail(e, "mesh upload");
     }
-    if (scheme == ALSUB_CATMULL_CLARK) {
-        // boundary edges (Sec. 3.2 "Boundaries"): their number sizes every level; the paper gives
-        // no rule for a crease that meets the boundary, so such input is refused
+    if (scheme != ALSUB_SQRT3) {
+        // boundary edges (Sec. 3.2 "Boundaries"; Loop takes the same rules): their number sizes
+        // every level; the paper gives no rule for a crease that meets the boundary, so such input
+        // is refused
         long long B = 0;
         bool crease_at_boundary = false;
         alsub_status st = mesh_boundary_scan(M, s, &B, &crease_at_boundary);

@@ -21,7 +21,7 @@
 // Open meshes (Sec. 3.2 "Boundaries", build and repair): corners without a twin carry twin -1 and
 // the child rules keep it (a boundary edge splits into two boundary halves). The BND variants of
 // the kernels skip every point whose stencil would cross the boundary (boundary edge points,
-// boundary vertices); cc_boundary then writes those from the level's boundary list.
+// boundary vertices); boundary_step then writes those from the level's boundary list.
 #include <algorithm>
 
 #include "common.cuh"
@@ -622,16 +622,18 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     else if (topo && ev) launch<true, false, true>(a, derive, s);
     else if (topo) launch<true, false, false>(a, derive, s);
     else if (ev) launch<false, false, true>(a, derive, s);
-    if (a.bnd) cc_boundary(T, l, topo && l + 1 < T.levels, P, Pn, s);
+    if (a.bnd) boundary_step(T, l, topo && l + 1 < T.levels, P, Pn, s);
 }
 
-void cc_boundary(TopoImpl &T, int l, bool list, const float *P, float *Pn, cudaStream_t s) {
+void boundary_step(TopoImpl &T, int l, bool list, const float *P, float *Pn, cudaStream_t s) {
     const LevelBuf &A = T.L[l];
     if (A.B == 0 || (!list && !P)) return;
     LevelBuf *N = list ? &T.L[l + 1] : nullptr;
+    // the edge point of edge e is |v| + |f| + e (Catmull-Clark) or |v| + e (Loop)
+    const int first_edge_point = (int)(T.scheme == ALSUB_CATMULL_CLARK ? A.V + A.F : A.V);
     k_cc_bnd<<<grid_for(A.B), kBlock, 0, s>>>((int)A.B, l == 0, A.bA, A.bE, A.bS, N ? N->bA : nullptr,
                                              N ? N->bE : nullptr, N ? N->bS : nullptr, (int)A.V, (int)A.E,
-                                             (int)(A.V + A.F), P, Pn, l > 0, l + 1 < T.levels, T.status);
+                                             first_edge_point, P, Pn, l > 0, l + 1 < T.levels, T.status);
     T.launches += 1;
 }
 

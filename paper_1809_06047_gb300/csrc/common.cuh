@@ -199,9 +199,9 @@ struct TriLevel {
         const bool need = j != 3 && i != 1;
         const int t = need ? __ldg(ptw + 3 * R + (i == 0 ? j : jm)) : 0;
         const int s = t / 3, k = t - 3 * s;
-        const int fromParent = i == 0 ? 3 * (4 * s + (k == 2 ? 0 : k + 1)) + 2 : 3 * (4 * s + k);
+        const int fromParent = t < 0 ? -1 : (i == 0 ? 3 * (4 * s + (k == 2 ? 0 : k + 1)) + 2 : 3 * (4 * s + k));
         const int interior = j == 3 ? 3 * (4 * R + (i == 2 ? 0 : i + 1)) + 1 : 3 * (4 * R + 3) + jm;
-        return need ? fromParent : interior;
+        return need ? fromParent : interior;          // -1: the half of a boundary edge
     }
     // Loop only (sqrt(3) has no edge ids); edge_gi takes corner i of triangle g
     __device__ int edge(int x) const;

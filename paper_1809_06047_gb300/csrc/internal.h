@@ -181,10 +181,12 @@ void gather_rows(int n, const int *vmap, const float *P, float *out, cudaStream_
 // new vertex; fills `out` (arrays, maps, counts) on `s`, which it synchronises once per
 // breadth-first level. *levels_out: breadth-first levels over all components.
 alsub_status reorder_mesh(const MeshImpl &M, cudaStream_t s, MeshImpl &out, int *levels_out);
-// Boundary repair of one Catmull-Clark step (Sec. 3.2 "Boundaries", Fig. module_boundary): with
-// positions, overwrite the boundary edge points (midpoints) and boundary vertices (Eq.
-// CC_boundary) of level l + 1; with `list`, write level l + 1's boundary list.
-void cc_boundary(TopoImpl &T, int l, bool list, const float *P, float *Pn, cudaStream_t s);
+// Boundary repair of one Catmull-Clark or Loop step (Sec. 3.2 "Boundaries", Fig.
+// module_boundary; Loop takes the same rules): with positions, overwrite the boundary edge points
+// (midpoints) and boundary vertices (Eq. CC_boundary) of level l + 1; with `list`, write level
+// l + 1's boundary list (the halves' edge ids follow both schemes' rule: the half at the owner
+// corner's start is 2e, where the owner of a boundary half is its one corner on even entries).
+void boundary_step(TopoImpl &T, int l, bool list, const float *P, float *Pn, cudaStream_t s);
 
 // One refinement step from level l to l + 1. topo: emit the child face table; helpers: emit the
 // child's per-corner edge ids and twins; P/Pn: parent/child positions (null = no vertex eval).

@@ -11,7 +11,7 @@
 //    (the upper triangle of E, Eq. CC_E), or when it has no twin (a boundary edge, the entries
 //    of value 1 in E that Sec. 3.2 "Boundaries" identifies); an exclusive scan over the owner
 //    flags numbers the edges deterministically;
-//  * for an open Catmull-Clark mesh, the list of boundary corners with each one's successor
+//  * for an open Catmull-Clark or Loop mesh, the list of boundary corners with each one's successor
 //    along its boundary loop (the input of the boundary repair step, Fig. module_boundary);
 //  * the level-0 crease list (C of Sec. 3.3) sorted by edge id.
 // Non-manifold input is reported through the handle's status word, never by trapping.
@@ -263,7 +263,7 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
                                            reinterpret_cast<unsigned *>(T.vc0));
     k_insert<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, T.status);
     const unsigned nb = grid_for(nnz);
-    const bool open = M.scheme == ALSUB_CATMULL_CLARK;
+    const bool open = M.scheme != ALSUB_SQRT3;          // sqrt(3) has no boundary rule
     k_twin<<<nb, kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, open, L0.tw, T.own0, T.flags, T.status);
     T.launches += 5 + scan_exclusive(T.flags, T.pos, nb, T.e0count, nullptr, T.scan_tmp, s);
     k_eid<<<nb, kBlock, 0, s>>>(nnz, T.own0, T.pos, T.eid);

@@ -589,6 +589,8 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
         return report(ALSUB_ERR_INVALID_ARG, "flags must ask for ALSUB_OP_CHAIN and/or ALSUB_OP_COMPOSE");
     TopoImpl &T = *topology_impl(topo);
     if (!T.built) return report(ALSUB_ERR_INVALID_ARG, "topology not built");
+    if (T.scheme == ALSUB_LOOP && T.mesh->B > 0)
+        return report(ALSUB_ERR_UNSUPPORTED, "operator rows for Loop boundaries are not built");
     cudaStream_t s = (cudaStream_t)stream;
     alsub_status st = ensure_helpers(T, s);
     if (st) return st;

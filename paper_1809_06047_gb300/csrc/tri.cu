@@ -59,7 +59,11 @@ struct TriArgs {
 #define ALSUB_SQRT3_TOPO_SMEM 1
 #endif
 
-template <bool TOPO, bool HELP, bool EVAL>
+// BND: an open mesh (Loop boundaries). Every stencil that would read across a corner without twin
+// (-1) reads this triangle instead: the points it gives are the boundary edge points and boundary
+// vertices, which the boundary step (cc.cu, boundary_step) writes afterwards from the level's
+// boundary list; all other points never meet a boundary.
+template <bool TOPO, bool HELP, bool EVAL, bool BND = false>
 __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
     // with staged face rows every lane of the warp takes part in the stores (a lane past the end
     // works on face 0 and writes nothing); otherwise such a lane leaves at once
@@ -116,10 +120,10 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
             oe[3 * j + 1] = E2 + c + j;
             oe[3 * j + 2] = 2 * ee[jp] + (ow[jp] ? 1 : 0);
             int s = tt[j] / 3, i = tt[j] - 3 * s;
-            ot[3 * j + 0] = 3 * (4 * s + (i == 2 ? 0 : i + 1)) + 2;
+            ot[3 * j + 0] = (BND && tt[j] < 0) ? -1 : 3 * (4 * s + (i == 2 ? 0 : i + 1)) + 2;
             ot[3 * j + 1] = 3 * (4 * r + 3) + (j + 2) % 3;
             int s2 = tt[jp] / 3, i2 = tt[jp] - 3 * s2;
-            ot[3 * j + 2] = 3 * (4 * s2 + i2) + 0;
+            ot[3 * j + 2] = (BND && tt[jp] < 0) ? -1 : 3 * (4 * s2 + i2) + 0;
             oe[9 + j] = E2 + c + (j + 1) % 3;
             ot[9 + j] = 3 * (4 * r + (j + 1) % 3) + 1;
         }
@@ -139,7 +143,7 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
         if (a.l == 0) {
 #pragma unroll
             for (int j = 0; j < 3; j++) {
-                if (!ow[j]) continue;
+                if (!ow[j] || (BND && tt[j] < 0)) continue;      // a boundary edge: the boundary step
                 int d = __ldg(a.fv + tri_prev(tt[j]));
                 float3 ep = 0.375f * (p[j] + p[(j + 1) % 3]) + 0.125f * (p[(j + 2) % 3] + ldpv(P, d, a.in4));
                 stpv(a.Pn, V + ee[j], ep, a.out4);
@@ -154,7 +158,8 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
                     sp += ldpv(P, __ldg(a.fv + tri_next(y)), a.in4);
                     y = a.t.twin(tri_prev(y));
                     n++;
-                } while (y != x && n < kMaxValence);
+                } while (y != x && n < kMaxValence && !(BND && y < 0));
+                if (BND && y < 0) continue;                     // a boundary vertex: the boundary step
                 if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); continue; }
                 float beta = c_loop_beta[n];
                 const float3 pj = j == 0 ? p[0] : (j == 1 ? p[1] : p[2]);   // constant indices: registers
@@ -174,7 +179,8 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
                 // corner-1 edge (E_k E_k-1, inside R). Far vertices: across the half, E'_k2+1 of
                 // the triangle R2 across edge k (twin 3 R2 + k2); across the inner edge, E_k+1.
                 const int k1 = k == 2 ? 0 : k + 1;
-                const int t = __ldg(a.ptw + 3 * R + k);
+                const int t0 = __ldg(a.ptw + 3 * R + k);
+                const int t = (BND && t0 < 0) ? 3 * R + k : t0;    // across a boundary: R itself
                 const int R2 = t / 3, k2 = t - 3 * R2;
                 const int en = a.Vp + __ldg(a.pce + 3 * R + k1);
                 const int ea = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 2 ? 0 : k2 + 1));
@@ -208,7 +214,8 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
                     // on each later level the half at v keeps v as an endpoint, its id doubling
                     // (plus one on the first split when v is not the edge owner's start).
                     const int G = x, c0 = 3 * G + kb;
-                    const int eb = __ldg(a.cel[m - 1] + c0), t = __ldg(a.twl[m - 1] + c0);
+                    const int eb = __ldg(a.cel[m - 1] + c0), t0 = __ldg(a.twl[m - 1] + c0);
+                    const int t = (BND && t0 < 0) ? c0 : t0;       // born on the boundary: G itself
                     const int G2 = t / 3, kb2 = t - 3 * G2, I = 2 * a.El[m - 1];
                     const int id[6] = {2 * eb, 2 * eb + 1, I + 3 * G + kb, I + 3 * G + (kb == 2 ? 0 : kb + 1),
                                        I + 3 * G2 + kb2, I + 3 * G2 + (kb2 == 2 ? 0 : kb2 + 1)};
@@ -230,8 +237,10 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
                         sp += ldpv(P, a.Vp + __ldg(a.pce + y), a.in4);
                         y = __ldg(a.ptw + tri_prev(y));
                         n++;
-                    } while (y != x0 && n < kMaxValence);
-                    if (y != x0) {
+                    } while (y != x0 && n < kMaxValence && !(BND && y < 0));
+                    if (BND && y < 0) {
+                        // a boundary vertex: the boundary step
+                    } else if (y != x0) {
                         set_status(a.status, ALSUB_ERR_UNSUPPORTED);
                     } else {
                         const float beta = c_loop_beta[n];
@@ -429,9 +438,9 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
 #ifndef ALSUB_LOOP_MIN_BLOCKS
 #define ALSUB_LOOP_MIN_BLOCKS 6
 #endif
-template <bool TOPO, bool HELP, bool EVAL>
+template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock, ALSUB_LOOP_MIN_BLOCKS) k_loop(TriArgs a) {
-    loop_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    loop_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 template <bool TOPO, bool HELP, bool EVAL>
 __global__ void __launch_bounds__(kBlock, ALSUB_LOOP_MIN_BLOCKS) k_sqrt3(TriArgs a) {
@@ -531,16 +540,24 @@ void upload_weight_tables() {
     });
 }
 
+template <bool B>
+void launch_loop(const TriArgs &a, bool topo, bool helpers, bool ev, cudaStream_t s) {
+    const unsigned g = grid_for(a.F);
+    if (topo && helpers && ev) k_loop<true, true, true, B><<<g, kBlock, 0, s>>>(a);
+    else if (topo && helpers) k_loop<true, true, false, B><<<g, kBlock, 0, s>>>(a);
+    else if (topo && ev) k_loop<true, false, true, B><<<g, kBlock, 0, s>>>(a);
+    else if (topo) k_loop<true, false, false, B><<<g, kBlock, 0, s>>>(a);
+    else if (ev) k_loop<false, false, true, B><<<g, kBlock, 0, s>>>(a);
+}
+
 void loop_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
     TriArgs a = make_args(T, l, P, Pn);
-    unsigned g = grid_for(a.F);
-    bool ev = P != nullptr;
+    const bool ev = P != nullptr, bnd = T.mesh->B > 0;
     if (topo || ev) T.launches += 1;
-    if (topo && helpers && ev) k_loop<true, true, true><<<g, kBlock, 0, s>>>(a);
-    else if (topo && helpers) k_loop<true, true, false><<<g, kBlock, 0, s>>>(a);
-    else if (topo && ev) k_loop<true, false, true><<<g, kBlock, 0, s>>>(a);
-    else if (topo) k_loop<true, false, false><<<g, kBlock, 0, s>>>(a);
-    else if (ev) k_loop<false, false, true><<<g, kBlock, 0, s>>>(a);
+    if (bnd) launch_loop<true>(a, topo, helpers, ev, s);
+    else launch_loop<false>(a, topo, helpers, ev, s);
+    // open mesh: boundary edge points and vertices, and the next level's boundary list
+    if (bnd) boundary_step(T, l, topo && l + 1 < T.levels, P, Pn, s);
 }
 
 void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {

@@ -413,6 +413,19 @@ def sheet_cc(NX: int = 12, NY: int = 9, split_frac: float = 0.1, jitter: float =
     return _pack(faces, P, np.zeros((0, 2)), np.zeros(0))
 
 
+def triangulate(m: dict) -> dict:
+    """The same mesh with every face of order c > 3 split into the fan of c - 2 triangles from its
+    corner 0 (a quad [a, b, c, d] -> [a, b, c], [a, c, d]); vertices, positions and creases kept."""
+    off, fv = np.asarray(m["off"]), np.asarray(m["fv"])
+    faces = []
+    for r in range(len(off) - 1):
+        f = fv[off[r]:off[r + 1]].tolist()
+        faces += [[f[0], f[k], f[k + 1]] for k in range(1, len(f) - 1)]
+    out = _pack(faces, np.asarray(m["P"]), np.asarray(m.get("crease_verts", np.zeros((0, 2)))).reshape(-1, 2),
+                np.asarray(m.get("crease_sharp", np.zeros(0))).reshape(-1))
+    return out
+
+
 def open_box() -> dict:
     """The unit cube without its z = +1 face: one boundary loop of four valence-3 vertices."""
     m = cube()

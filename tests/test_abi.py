@@ -94,9 +94,9 @@ def test_mesh_validation_on_host():
     with pytest.raises(alsub.AlsubError) as e:           # NaN sharpness
         _create("cc", 8, 6, c["fv"], c["off"], np.array([[0, 1]]), np.array([np.nan]))
     assert e.value.status == 1
-    with pytest.raises(alsub.AlsubError) as e:           # open mesh: odd corner count
+    with pytest.raises(alsub.AlsubError) as e:           # open sqrt(3) mesh: odd corner count
         t = synth.tetrahedron()
-        _create("loop", 4, 3, t["fv"][:9], t["off"][:4])
+        _create("sqrt3", 4, 3, t["fv"][:9], t["off"][:4])
     assert e.value.status in (1, 3)
 
 

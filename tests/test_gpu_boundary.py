@@ -1,7 +1,9 @@
-"""Open Catmull-Clark meshes (Sec. 3.1 and 3.2 "Boundaries") on the CUDA path.
+"""Open Catmull-Clark and Loop meshes (Sec. 3.1 and 3.2 "Boundaries") on the CUDA path.
 
 The boundary edge points are midpoints and the boundary vertices follow Eq. CC_boundary, written
-by the repair step after the smooth eval (build and repair, Fig. module_boundary). Parity with the
+by the repair step after the smooth eval (build and repair, Fig. module_boundary); Loop, for which
+Appendix B gives no boundary rule, takes the same two rules (the oracle's reading, pinned by the
+cubic B-spline boundary curves). Parity with the
 oracle as for closed meshes: topology bit-exact after canonical relabelling, positions within
 2e-6 x bounding-box diagonal at every level; the operator, its transpose, the dynamic and graph
 paths and the server are checked on the same inputs.
@@ -153,12 +155,20 @@ def test_open_mesh_errors():
     assert e.value.status == 3
     o = synth.octahedron()
     open_tri = dict(o, F=6, off=o["off"][:7], fv=o["fv"][:18])
-    for scheme in ("loop", "sqrt3"):               # no boundary rule for the triangle schemes
-        with pytest.raises(alsub.AlsubError) as e:
-            M = alsub.Mesh.from_dict(open_tri, scheme)
-            T = alsub.Topology(M, 1, build=True)
-            T.status()
-        assert e.value.status == 3
+    with pytest.raises(alsub.AlsubError) as e:     # Appendix A omits the sqrt(3) boundary rule
+        M = alsub.Mesh.from_dict(open_tri, "sqrt3")
+        T = alsub.Topology(M, 1, build=True)
+        T.status()
+    assert e.value.status == 3
+    M = alsub.Mesh.from_dict(open_tri, "loop")     # Loop: the rules of Eq. CC_boundary
+    assert M.boundary_edges == 4
+    T = alsub.Topology(M, 1, build=True)
+    T.status()
+    with pytest.raises(alsub.AlsubError) as e:     # no Loop boundary rows in the operator
+        alsub.Operator(T, chain=True)
+    assert e.value.status == 3
+    T.close()
+    M.close()
     # two squares sharing one vertex: two fans there
     bow = dict(V=7, F=2, off=np.array([0, 4, 8], np.int32), fv=np.array([0, 1, 2, 3, 0, 4, 5, 6], np.int32),
                P=np.random.default_rng(1).standard_normal((7, 3)).astype(np.float32),
@@ -204,3 +214,62 @@ def test_open_mesh_served():
         assert r["status"] == 1
     finally:
         S.close()
+
+
+def _triangle():
+    return dict(V=3, F=1, off=np.array([0, 3], np.int32), fv=np.array([0, 1, 2], np.int32),
+                P=np.array([[0, 0, 0], [1, 0, 0.2], [0.3, 1, -0.1]], np.float32),
+                crease_verts=np.zeros((0, 2), np.int32), crease_sharp=np.zeros(0, np.float32))
+
+
+OPEN_LOOP = [
+    ("tube16x9", lambda: synth.triangulate(synth.tube_cc(16, 9, seed=61)), 4),
+    ("tube3x2", lambda: synth.triangulate(synth.tube_cc(3, 2, seed=62)), 4),
+    ("sheet", lambda: synth.triangulate(synth.sheet_cc(12, 9, seed=63)), 4),
+    ("holes_creased", lambda: synth.triangulate(synth.holed_cc_mixed(24, 20, holes=6, seed=64)), 4),
+    ("box", lambda: synth.triangulate(synth.open_box()), 4),
+    ("triangle", _triangle, 4),
+    ("sheet_L1", lambda: synth.triangulate(synth.sheet_cc(6, 5, seed=65)), 1),
+    ("sheet_L0", lambda: synth.triangulate(synth.sheet_cc(6, 5, seed=66)), 0),
+]
+
+
+@pytest.mark.parametrize("name,fn,levels", OPEN_LOOP, ids=[c[0] for c in OPEN_LOOP])
+@pytest.mark.parametrize("mode", ["static", "dynamic"])
+def test_open_loop_parity(name, fn, levels, mode):
+    """Open Loop meshes: every level against the oracle (topology after canonical relabelling,
+    creases, positions within 2e-6 x diagonal), and the boundary count and level counts."""
+    from paper_1809_06047_gb300 import alsub
+    mesh = fn()
+    B = _boundary_edges(mesh)
+    M = alsub.Mesh.from_dict(mesh, "loop")
+    assert M.boundary_edges == B > 0
+    plan = alsub.plan("loop", mesh["V"], mesh["F"], len(mesh["fv"]), levels, boundary=B)
+    M.close()
+    ref = oracle.subdivide(mesh, levels, "loop", keep_all=True)
+    for l in range(levels + 1):
+        assert (ref[l]["V"], ref[l]["F"], ref[l]["E"]) == (int(plan[l][0]), int(plan[l][1]), int(plan[l][3]))
+    gpu = gpu_util.gpu_run(mesh, "loop", levels, mode=mode)
+    gpu_util.compare("loop", gpu, ref)
+
+
+def test_open_loop_repeated_calls_replay_graphs():
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    mesh = synth.triangulate(synth.holed_cc_mixed(20, 16, holes=4, seed=67))
+    M = alsub.Mesh.from_dict(mesh, "loop")
+    T = alsub.Topology(M, 4, build=False)
+    S = alsub.Topology(M, 4, build=True)
+    P0 = torch.from_numpy(np.ascontiguousarray(mesh["P"], dtype=np.float32)).cuda()
+    PL = torch.empty((T.counts[-1]["V"], 3), dtype=torch.float32, device="cuda")
+    outs = []
+    for _ in range(4):
+        T.subdivide(P0, out=PL)
+        torch.cuda.synchronize()
+        outs.append(PL.clone())
+    ref = S.refine_vertices(P0)
+    torch.cuda.synchronize()
+    T.status()
+    S.status()
+    for o in outs:
+        assert torch.equal(o, ref)

@@ -326,6 +326,7 @@ def test_corners_fixed():
     ("cc", synth.pillow(5)),
     ("cc", synth.sheet_cc(3, 3, seed=24)),
     ("loop", synth.torus_tri(5, 5, seed=22)),
+    ("loop", synth.triangulate(synth.sheet_cc(3, 3, seed=25))),
     ("sqrt3", synth.torus_tri(5, 5, seed=23, creases=False)),
 ])
 def test_brute_force_operator(scheme, mesh):
@@ -351,10 +352,10 @@ def test_rejects_invalid_meshes():
     m = synth.cube()
     o = synth.octahedron()
     open_tri = dict(o, F=7, off=o["off"][:8], fv=o["fv"][:21])
-    for scheme in ("loop", "sqrt3"):              # no boundary rule for the triangle schemes
-        with pytest.raises(oracle.OracleError) as ei:
-            oracle.subdivide(open_tri, 1, scheme)
-        assert ei.value.code == 3
+    with pytest.raises(oracle.OracleError) as ei:   # Appendix A omits the sqrt(3) boundary rule
+        oracle.subdivide(open_tri, 1, "sqrt3")
+    assert ei.value.code == 3
+    oracle.subdivide(open_tri, 1, "loop")           # Loop takes the boundary rules of Eq. CC_boundary
     # two squares sharing only vertex 0: two fans at one vertex
     bow = dict(V=7, F=2, off=np.array([0, 4, 8], np.int32),
                fv=np.array([0, 1, 2, 3, 0, 4, 5, 6], np.int32), P=np.zeros((7, 3), np.float32),
@@ -444,17 +445,21 @@ def _refine_closed_polygon(P, c):
     return Q
 
 
-@pytest.mark.parametrize("mesh", [synth.tube_cc(10, 6, jitter=0.2, seed=31), synth.sheet_cc(6, 5, seed=32),
-                                  synth.holed_cc_mixed(16, 14, holes=3, seed=33)],
-                         ids=["tube", "sheet", "holes"])
-def test_boundary_is_cubic_bspline_curve(mesh):
+@pytest.mark.parametrize("scheme,mesh", [
+    ("cc", synth.tube_cc(10, 6, jitter=0.2, seed=31)), ("cc", synth.sheet_cc(6, 5, seed=32)),
+    ("cc", synth.holed_cc_mixed(16, 14, holes=3, seed=33)),
+    ("loop", synth.triangulate(synth.tube_cc(10, 6, jitter=0.2, seed=31))),
+    ("loop", synth.triangulate(synth.sheet_cc(6, 5, seed=32))),
+    ("loop", synth.triangulate(synth.holed_cc_mixed(16, 14, holes=3, seed=33)))],
+    ids=["tube", "sheet", "holes", "loop_tube", "loop_sheet", "loop_holes"])
+def test_boundary_is_cubic_bspline_curve(scheme, mesh):
     """Every boundary loop of the refined mesh is the control polygon of the cubic B-spline curve
     of the level-0 boundary loop, refined l times (Eq. CC_boundary with midpoint edge points;
     the mask comes from the Cox-de Boor basis), whatever the surface inside it."""
     c = _cubic_two_scale_mask()
     np.testing.assert_allclose(c * 8.0, [1, 4, 6, 4, 1], atol=1e-9)   # sanity of the derivation
     levels = 3
-    out = oracle.subdivide(mesh, levels, "cc")
+    out = oracle.subdivide(mesh, levels, scheme)
     loops0 = _boundary_loops(out[0])
     assert len(loops0) >= 1
     expected = []
@@ -469,14 +474,17 @@ def test_boundary_is_cubic_bspline_curve(mesh):
         np.testing.assert_allclose(_as_sorted(got), _as_sorted(np.concatenate(expected)), atol=1e-9)
 
 
-def test_boundary_tube_height_is_linear():
+@pytest.mark.parametrize("scheme", ["cc", "loop"])
+def test_boundary_tube_height_is_linear(scheme):
     """Heights linear in the row index are reproduced exactly by every rule at every level
     (face, edge and vertex points are affine combinations symmetric across the rows, and the
-    boundary rules act along rows), so the refined tube has n 2^l vertices on each of the
-    (M - 1) 2^l + 1 dyadic heights -- a boundary vertex taking the smooth half-ring rule
-    would leave its row."""
+    boundary rules act along rows; for Loop the tube is triangulated along one diagonal
+    direction, whose edge and vertex stencils are symmetric across the rows too), so the refined
+    tube has n 2^l vertices on each of the (M - 1) 2^l + 1 dyadic heights -- a boundary vertex
+    taking the smooth rule would leave its row."""
     N, M, levels, h = 9, 6, 3, 0.25
-    out = oracle.subdivide(synth.tube_cc(N, M, jitter=0.3, z_step=h, seed=34), levels, "cc")
+    tube = synth.tube_cc(N, M, jitter=0.3, z_step=h, seed=34)
+    out = oracle.subdivide(tube if scheme == "cc" else synth.triangulate(tube), levels, scheme)
     for l in range(1, levels + 1):
         z = out[l]["P"][:, 2] / (h / 2 ** l)
         k = np.round(z)
@@ -486,26 +494,31 @@ def test_boundary_tube_height_is_linear():
         assert np.all(counts == N * 2 ** l)
 
 
-def test_boundary_leaves_far_interior_unchanged():
+@pytest.mark.parametrize("scheme", ["cc", "loop"])
+def test_boundary_leaves_far_interior_unchanged(scheme):
     """Cutting a ring of faces out of a closed torus changes nothing at the level-l vertices of
     faces at least three rings away from the cut: the boundary rules only reach about two
-    level-0 rings inwards over any number of levels (the stencils halve in size every level)."""
+    level-0 rings inwards over any number of levels (the stencils halve in size every level).
+    For Loop the torus is triangulated (two triangles per quad, in quad order)."""
     N, M, levels = 12, 8, 3
     closed = synth.torus_cc_plain(N, M, jitter=0.05, seed=35)
     F = closed["F"] - M                              # faces i = N - 1 are the last M
     cut = dict(closed, F=F, off=closed["off"][:F + 1], fv=closed["fv"][:4 * F])
-    a = oracle.subdivide(closed, levels, "cc")[levels]
-    b = oracle.subdivide(cut, levels, "cc")[levels]
-    q = 4 ** levels
+    if scheme == "loop":
+        closed, cut = synth.triangulate(closed), synth.triangulate(cut)
+    a = oracle.subdivide(closed, levels, scheme)[levels]
+    b = oracle.subdivide(cut, levels, scheme)[levels]
+    k = 4 if scheme == "cc" else 3                  # corners of a refined face
+    t = 1 if scheme == "cc" else 2                  # level-0 faces of one quad
+    q = t * 4 ** levels                             # refined faces of one quad
     for i in range(3, N - 4):                       # face columns 3 .. N-5 touch vertex columns <= N-4
         for j in range(M):
             r = i * M + j
-            ca = a["fv"][4 * q * r:4 * q * (r + 1)]
-            cb = b["fv"][4 * q * r:4 * q * (r + 1)]
+            ca = a["fv"][k * q * r:k * q * (r + 1)]
+            cb = b["fv"][k * q * r:k * q * (r + 1)]
             np.testing.assert_array_equal(a["P"][ca], b["P"][cb])
     # and the cut does change the faces next to it
-    r = 0
-    assert not np.array_equal(a["P"][a["fv"][:4 * q]], b["P"][b["fv"][:4 * q]])
+    assert not np.array_equal(a["P"][a["fv"][:k * q]], b["P"][b["fv"][:k * q]])
 
 
 @pytest.mark.parametrize("scheme,mesh", [
