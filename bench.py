@@ -52,6 +52,9 @@ def parse(argv=None):
     p.add_argument("--no-serving", action="store_true", help="skip the serving-loop leg")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the operator, adjoint, batch, boundary, ordering, adaptive and patches legs")
+    p.add_argument("--legs", default="all",
+                   help="comma list of the extra legs to run (operator, adjoint, batch, boundary, ordering, "
+                        "adaptive, patches); default all")
     p.add_argument("--serving-fastest", action="store_true",
                    help="also replay the serving mix with each resident's faster frame path")
     return p.parse_args(argv)
@@ -382,20 +385,16 @@ def batch_leg(w):
             "tuned": best}
 
 
-def boundary_leg(peak):
-    """Open Catmull-Clark mesh at the headline's size (Sec. 3.2 "Boundaries", build and repair): the
-    96 x 96 mixed torus with 64 faces cut out (64 boundary loops), 6 levels through alsub_subdivide,
-    against the closed headline mesh. Reports the refined faces/s, the last step's roofline and the
-    time of the boundary repair kernels."""
+def _open_mesh_run(scheme, m, L, peak):
+    """One open mesh through alsub_subdivide: step time, per-level times, the last step's roofline
+    and the static eval time (which includes one boundary repair kernel per level)."""
     import torch
     from paper_1809_06047_gb300 import alsub
-    m = synth.holed_cc_mixed(96, 96, holes=64, seed=synth.SEED_BASE + 9)
-    L = 6
-    M = alsub.Mesh.from_dict(m, "cc")
+    M = alsub.Mesh.from_dict(m, scheme)
     B = M.boundary_edges
-    counts = [[int(x) for x in row] for row in alsub.plan("cc", m["V"], m["F"], len(m["fv"]), L, boundary=B)]
+    counts = [[int(x) for x in row] for row in alsub.plan(scheme, m["V"], m["F"], len(m["fv"]), L, boundary=B)]
     T = alsub.Topology(M, L, build=False)
-    P0 = torch.from_numpy(m["P"]).cuda()
+    P0 = torch.from_numpy(np.ascontiguousarray(m["P"], dtype=np.float32)).cuda()
     PL = torch.empty((counts[L][0], 3), dtype=torch.float32, device="cuda")
     for _ in range(3):
         T.subdivide(P0, out=PL)
@@ -414,20 +413,38 @@ def boundary_leg(peak):
     last_ms = stage_ms[L] / max(calls, 1)
     alg = level_alg_bytes(counts, L - 1)
     gbs = alg / (last_ms / 1e3) / 1e9
-    # the repair kernels alone: one per level over the boundary lists (2^l B entries)
     S = alsub.Topology(M, L, build=True)
     ev = _events_ms(lambda: S.refine_vertices(P0, out=PL), reps)
-    out = {"workload": f"holed_cc_mixed 96 x 96, 64 holes ({B} boundary edges, {m['F']} control faces), "
-                       f"{L} levels -> {counts[L][1]} quads, {B << (L - 1)} boundary edges on level {L - 1}",
+    shape = "quads" if scheme == "cc" else "triangles"
+    out = {"workload": f"{B} boundary edges, {m['F']} control faces, {L} levels -> {counts[L][1]} {shape}, "
+                       f"{B << (L - 1)} boundary edges on level {L - 1}",
            "ms_per_step": ms, "refined_faces_per_s": counts[L][1] / (ms / 1e3),
            "static_eval_ms": ev,
            "stage_ms": [x / max(calls, 1) for x in stage_ms],
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                        "kernel": "cc level 5->6 fused build+eval step (BND variant) + boundary repair",
-                        "algorithmic_bytes": alg}}
+                        "kernel": f"{scheme} level {L - 1}->{L} fused build+eval step (BND variant) + boundary "
+                                  "repair", "algorithmic_bytes": alg}}
     S.close()
     T.close()
     M.close()
+    return out
+
+
+def boundary_leg(peak):
+    """Open meshes at the headline's size (Sec. 3.2 "Boundaries", build and repair): the 96 x 96
+    mixed torus with 64 faces cut out (64 boundary loops), 6 levels through alsub_subdivide, for
+    Catmull-Clark (against the closed headline mesh) and, triangulated (each n-gon a fan from its
+    first corner), for Loop. Reports the refined faces/s, the last step's roofline and the static
+    eval time."""
+    m = synth.holed_cc_mixed(96, 96, holes=64, seed=synth.SEED_BASE + 9)
+    out = _open_mesh_run("cc", m, 6, peak)
+    out["workload"] = "holed_cc_mixed 96 x 96, 64 holes: " + out["workload"]
+    try:
+        lo = _open_mesh_run("loop", synth.triangulate(m), 6, peak)
+        lo["workload"] = "the same mesh triangulated: " + lo["workload"]
+        out["loop"] = lo
+    except Exception as e:  # noqa: BLE001 -- the Catmull-Clark figures must still print
+        out["loop"] = {"error": f"{type(e).__name__}: {e}"}
     return out
 
 
@@ -783,6 +800,8 @@ def main():
                          ("batch", lambda: batch_leg(mix)), ("boundary", lambda: boundary_leg(peak)),
                          ("ordering", ordering_leg), ("adaptive", adaptive_leg),
                          ("patches", lambda: patches_leg(peak))):
+            if args.legs != "all" and key not in args.legs.split(","):
+                continue
             try:
                 out[key] = leg()
             except Exception as e:  # noqa: BLE001 -- the headline line must still print
