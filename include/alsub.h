@@ -129,8 +129,7 @@ alsub_status alsub_plan_open(alsub_scheme scheme, int64_t num_verts, int64_t num
  * the topology is built), and no crease may touch a boundary vertex (the paper defines no such
  * combination: UNSUPPORTED). Loop meshes may be open too, with the same two boundary rules (Appendix
  * B gives Loop none of its own; these keep its boundary the cubic B-spline curve of the control
- * polygon, as for Catmull-Clark); the Loop operator (alsub_build_operator) refuses them. sqrt(3)
- * meshes must be closed.
+ * polygon, as for Catmull-Clark). sqrt(3) meshes must be closed.
  * Errors: INVALID_ARG, NONMANIFOLD (a repeated directed edge found by the boundary count),
  * UNSUPPORTED (counts beyond int32, odd nnz for sqrt(3), a crease at the boundary), OOM,
  * DEVICE.
@@ -349,7 +348,7 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
  * The operator keeps a pointer to the topology, which must outlive it. Synchronises `stream`
  * (the non-zero counts size the allocations).
  * Errors: INVALID_ARG (topology not built, no flags), UNSUPPORTED (a stencil row of more than 192
- * entries; an open Loop mesh), OOM, DEVICE.
+ * entries), OOM, DEVICE.
  */
 typedef enum { ALSUB_OP_CHAIN = 1, ALSUB_OP_COMPOSE = 2, ALSUB_OP_TRANSPOSE = 4 } alsub_operator_flags;
 

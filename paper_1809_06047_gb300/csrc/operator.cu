@@ -261,9 +261,9 @@ __global__ void k_op_rows(OpLevel L, int *cnt, const long long *rowptr, int *col
     }
 }
 
-// Boundary rows of a Catmull-Clark level (Sec. 3.2 "Boundaries"), one thread per boundary-list
-// entry a -> b with successor b -> c: the midpoint row of edge (a, b) and the row 3/4 b + 1/8
-// (a + c) of vertex b (Eq. CC_boundary).
+// Boundary rows of a Catmull-Clark or Loop level (Sec. 3.2 "Boundaries"; Loop takes the same
+// rules), one thread per boundary-list entry a -> b with successor b -> c: the midpoint row of edge
+// (a, b) and the row 3/4 b + 1/8 (a + c) of vertex b (Eq. CC_boundary).
 template <bool FILL>
 __global__ void k_op_bnd(OpLevel L, int *cnt, const long long *rowptr, int *col, float *w, int *status) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -272,7 +272,7 @@ __global__ void k_op_bnd(OpLevel L, int *cnt, const long long *rowptr, int *col,
     const int a = clampi(__ldg(L.bA + i), L.V), e = clampi(__ldg(L.bE + i), L.E);
     const int s1 = clampi(__ldg(L.bS + i), L.B);
     const int b = clampi(__ldg(L.bA + s1), L.V), c = clampi(__ldg(L.bA + clampi(__ldg(L.bS + s1), L.B)), L.V);
-    const int re = L.V + L.F + e;
+    const int re = (L.scheme == ALSUB_CATMULL_CLARK ? L.V + L.F : L.V) + e;
     const int ce[2] = {min(a, b), max(a, b)};
     int cv[3] = {a, b, c};
     float wv[3] = {0.125f, 0.75f, 0.125f};
@@ -589,8 +589,6 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
         return report(ALSUB_ERR_INVALID_ARG, "flags must ask for ALSUB_OP_CHAIN and/or ALSUB_OP_COMPOSE");
     TopoImpl &T = *topology_impl(topo);
     if (!T.built) return report(ALSUB_ERR_INVALID_ARG, "topology not built");
-    if (T.scheme == ALSUB_LOOP && T.mesh->B > 0)
-        return report(ALSUB_ERR_UNSUPPORTED, "operator rows for Loop boundaries are not built");
     cudaStream_t s = (cudaStream_t)stream;
     alsub_status st = ensure_helpers(T, s);
     if (st) return st;
