@@ -2,8 +2,10 @@
 
 A ctypes wrapper around ``alsub_oracle.c``: a plain, serial FP64 half-edge subdivider written
 from the paper's classical rules (Catmull-Clark Sec. 3.1, creases Sec. 3.3, sqrt(3) Appendix A,
-Loop Appendix B). Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg
-may import this package. It shares no code with the CUDA path and never calls it.
+Loop Appendix B, boundaries Sec. 3.1/3.2), plus plain numpy restatements of selective subdivision
+(Sec. 3.4: extraction, regular patches), hierarchical edits (Sec. 3.5) and mesh reordering
+(Sec. 4.5: reverse Cuthill-McKee). Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s
+CPU-baseline leg may import this package. It shares no code with the CUDA path and never calls it.
 
 Every function follows its passage as cited in the C source. One part is "parity unpinned": the
 crease vertex/edge rule reading (the paper delegates the rules to DeRose et al. 1998 and prints no
