@@ -153,19 +153,21 @@ alsub_status alsub_mesh_info(alsub_mesh_t mesh, int32_t *scheme, int64_t *num_ve
 
 /*
  * Selective subdivision (Sec. 3.4, Fig. module_selective): extract the region around selected
- * vertices of level `level` (0 = the control mesh) of a built Catmull-Clark topology as a new mesh,
+ * vertices of level `level` (0 = the control mesh) of a built Catmull-Clark or Loop topology as a
+ * new mesh,
  * which the ordinary calls then refine (it is open: its cut is refined by the boundary rules, so
  * only faces about two rings inside it match the uniform refinement).
  *   select_dev: uint8[V_level] on the device, 1 = selected; NULL selects the extraordinary vertices
- *               (valence != 4, Eq. vo, among the vertices on no boundary edge) and both ends of every
- *               live crease of the level.
+ *               (valence != 4 for Catmull-Clark, != 6 for Loop, Eq. vo, among the vertices on no
+ *               boundary edge) and both ends of every live crease of the level.
  *   rings >= 1: propagation steps q = M^T x (faces with a selected vertex), x = M q (their vertices);
  *               the mesh keeps the faces of the last q and their vertices, in their original order
  *               (M' = X M X-ring with X, X-ring rows / columns of the identity), and the creases
  *               whose both ends have every face around them kept.
  * The new handle owns its arrays and the maps (alsub_mesh_extract_maps); positions follow with
  * alsub_mesh_gather. Synchronises `stream` (the sizes are read back). Errors: INVALID_ARG (bad
- * level or rings, topology not built, nothing selected), UNSUPPORTED (Loop, sqrt(3)), OOM, DEVICE.
+ * level or rings, topology not built, nothing selected), UNSUPPORTED (sqrt(3): the extracted mesh is
+ * open), OOM, DEVICE.
  */
 alsub_status alsub_topology_extract(alsub_topology_t topo, int32_t level, const uint8_t *select_dev,
                                     int32_t rings, void *stream, alsub_mesh_t *out);

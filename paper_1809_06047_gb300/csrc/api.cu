@@ -750,8 +750,8 @@ alsub_status alsub_topology_extract(alsub_topology_t topo, int32_t level, const 
     TopoImpl &T = topo->t;
     if (level < 0 || level > T.levels) return fail(ALSUB_ERR_INVALID_ARG, "bad level");
     if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
-    if (T.scheme != ALSUB_CATMULL_CLARK)
-        return fail(ALSUB_ERR_UNSUPPORTED, "extraction is for Catmull-Clark (the extracted mesh is open)");
+    if (T.scheme == ALSUB_SQRT3)
+        return fail(ALSUB_ERR_UNSUPPORTED, "extraction gives an open mesh: sqrt(3) has no boundary rule");
     alsub_mesh_s *h = new (std::nothrow) alsub_mesh_s();
     if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
     cudaStream_t s = (cudaStream_t)stream;

@@ -1,10 +1,11 @@
 // Selective subdivision (Sec. 3.4, Fig. module_selective): the extraction matrices X_i (rows of the
 // identity: the kept vertices) and X-ring_i (columns of the identity: the kept faces) built on the
-// device from a level of a topology, and the extracted mesh M' = X_i M X-ring_i with its positions
-// P' = X_i P.
+// device from a level of a Catmull-Clark or Loop topology, and the extracted mesh
+// M' = X_i M X-ring_i with its positions P' = X_i P.
 //
-// Selection: x_0 = the given vertex mask, or the extraordinary vertices (valence != 4, Eq. vo, of
-// vertices on no boundary edge) and the ends of the level's live creases. Propagation, `rings`
+// Selection: x_0 = the given vertex mask, or the extraordinary vertices (valence != 4 for
+// Catmull-Clark, != 6 for Loop, Eq. vo, of vertices on no boundary edge) and the ends of the
+// level's live creases. Propagation, `rings`
 // times: q_i = M^T x_i (faces with a selected vertex), x_{i+1} = M q_i (the vertices of those
 // faces). Where the region touches itself at a vertex only (two fans of kept faces), every face
 // around that vertex is kept too, until no such vertex is left, so the result is a manifold. Kept
@@ -24,6 +25,11 @@ namespace {
 __device__ __forceinline__ void face_range(const int *off, int r, int &s, int &c) {
     if (off) { s = __ldg(off + r); c = __ldg(off + r + 1) - s; }
     else { s = 4 * r; c = 4; }
+}
+
+__global__ void k_x_iota(int n, int step, int *out) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = step * i;
 }
 
 __global__ void k_x_valence(int F, const int *__restrict__ off, const int *__restrict__ fv, int *deg) {
@@ -208,7 +214,8 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
                            MeshImpl &out) {
     const LevelBuf &L = T.L[level];
     const int V = (int)L.V, F = (int)L.F;
-    const int *off = level == 0 ? T.mesh->d_off : nullptr;
+    const int *off = level == 0 ? T.mesh->d_off : nullptr;   // refined Catmull-Clark: quads
+    const bool tri = level > 0 && T.scheme != ALSUB_CATMULL_CLARK;  // refined Loop: offsets 3r
     const int *fv = L.fv;
     // live creases of the level (exported: endpoints and sharpness, count on the device)
     const CreaseList &C = L.cr;
@@ -221,7 +228,7 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
     const size_t nV = (size_t)V, nF = (size_t)F, nC = (size_t)std::max(cap, 1);
     const long long nmax = std::max<long long>({(long long)V, (long long)F, (long long)nC});
     const size_t stmp = scan_tmp_bytes(nmax);
-    const size_t ints = 5 * nV + 4 * nF + 2 * nC + 8;
+    const size_t ints = 5 * nV + 4 * nF + 2 * nC + 8 + (tri ? nF + 1 : 0);
     char *buf = nullptr;
     if (cudaMallocAsync((void **)&buf, 4 * ints + stmp + 256, s) != cudaSuccess) {
         cudaGetLastError();
@@ -229,8 +236,12 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
     }
     int *deg = (int *)buf, *x = deg + nV, *bnd = x + nV, *cnt = bnd + nV, *vpos = cnt + nV;
     int *q = vpos + nV, *ord = q + nF, *fpos = ord + nF, *noff = fpos + nF;
-    int *flag = noff + nF, *cpos = flag + nC, *tot = cpos + nC;
-    void *tmp = (void *)(((uintptr_t)(tot + 8) + 255) & ~(uintptr_t)255);
+    int *flag = noff + nF, *cpos = flag + nC, *tot = cpos + nC, *toff = tot + 8;
+    void *tmp = (void *)(((uintptr_t)(toff + (tri ? nF + 1 : 0)) + 255) & ~(uintptr_t)255);
+    if (tri) {
+        k_x_iota<<<grid_for(F + 1), kBlock, 0, s>>>(F + 1, 3, toff);
+        off = toff;
+    }
     cudaMemsetAsync(deg, 0, 4 * nV, s);
     cudaMemsetAsync(bnd, 0, 4 * nV, s);
     cudaMemsetAsync(cnt, 0, 4 * nV, s);

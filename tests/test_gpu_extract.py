@@ -119,3 +119,73 @@ def test_feature_adaptive_chain():
     a, b = gP[gfv], cur["P"][cur["fv"]]
     diag = float(np.linalg.norm(b.max(0) - b.min(0)))
     assert float(np.abs(a - b).max()) <= gpu_util.POS_TOL * diag
+
+
+def _loop_mesh(seed):
+    return synth.torus_tri(32, 24, flip_frac=0.01, sharp_frac=0.004, seed=seed)
+
+
+@pytest.mark.parametrize("rings", [1, 2])
+def test_extract_loop_control_mesh(rings):
+    """Loop: extraction around the valence != 6 vertices and the crease ends, bit-exact against the
+    oracle; the extracted mesh is open and refines with the boundary rules."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = _loop_mesh(110 + rings)
+    M = alsub.Mesh.from_dict(m, "loop")
+    T = alsub.Topology(M, 1, build=True)
+    sub = T.extract(0, None, rings)
+    got = _gpu_mesh_dict(sub)
+    ref = oracle.extract(m, None, rings, scheme="loop")
+    _same(got, ref)
+    assert sub.boundary_edges > 0
+    P0 = torch.from_numpy(np.ascontiguousarray(m["P"])).cuda()
+    np.testing.assert_array_equal(sub.gather(P0).cpu().numpy(), m["P"][ref["vmap"]])
+
+
+def test_extract_loop_refined_level():
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = _loop_mesh(113)
+    M = alsub.Mesh.from_dict(m, "loop")
+    T = alsub.Topology(M, 2, build=True)
+    T.refine_vertices(torch.from_numpy(np.ascontiguousarray(m["P"])).cuda())
+    torch.cuda.synchronize()
+    T.status()
+    for l in (1, 2):
+        c = T.counts[l]
+        cv, cs = T.creases(l)
+        lvl = dict(V=c["V"], F=c["F"], off=np.arange(c["F"] + 1, dtype=np.int32) * 3, fv=T.faces(l),
+                   crease_verts=cv, crease_sharp=cs)
+        sub = T.extract(l, None, 2)
+        _same(_gpu_mesh_dict(sub), oracle.extract(lvl, None, 2, scheme="loop"))
+
+
+def test_loop_feature_adaptive_chain():
+    """Three rounds of (extract two rings, refine one Loop level) on the device and in the oracle:
+    the same faces, positions within 2e-6 x the bounding-box diagonal corner by corner."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = _loop_mesh(114)
+    M = alsub.Mesh.from_dict(m, "loop")
+    P = torch.from_numpy(np.ascontiguousarray(m["P"])).cuda()
+    T = alsub.Topology(M, 0, build=True)
+    keep, lvl = [M, T], 0
+    for _ in range(3):
+        sub = T.extract(lvl, None, 2)
+        Ps = sub.gather(P)
+        T = alsub.Topology(sub, 1, build=True)
+        P = T.refine_vertices(Ps)
+        torch.cuda.synchronize()
+        T.status()
+        keep += [sub, T]
+        lvl = 1
+    gfv, gP = T.faces(1), P.cpu().numpy()
+    cur = dict(m, P=m["P"].astype(np.float64))
+    for _ in range(3):
+        e = oracle.extract(cur, None, 2, scheme="loop")
+        cur = oracle.subdivide(e, 1, "loop")[1]
+    assert len(gfv) == len(cur["fv"])
+    a, b = gP[gfv], cur["P"][cur["fv"]]
+    diag = float(np.linalg.norm(b.max(0) - b.min(0)))
+    assert float(np.abs(a - b).max()) <= gpu_util.POS_TOL * diag
