@@ -68,6 +68,32 @@ def test_plan_rejects():
     assert e.value.status == 3
 
 
+@pytest.mark.parametrize("scheme,mesh", [
+    ("cc", lambda: synth.holed_cc_mixed(12, 10, holes=3, seed=71)),
+    ("loop", lambda: synth.triangulate(synth.holed_cc_mixed(12, 10, holes=3, seed=72))),
+    ("loop", lambda: synth.triangulate(synth.open_box())),
+])
+def test_plan_open_against_the_oracle(scheme, mesh):
+    """Level counts of open meshes (E0 = (nnz + B) / 2, each boundary edge splitting in two)
+    against the oracle's own counts; sqrt(3) refuses a boundary (no rule in Appendix A)."""
+    m = mesh()
+    off, fv = np.asarray(m["off"]), np.asarray(m["fv"])
+    d = set()
+    for r in range(m["F"]):
+        f = fv[off[r]:off[r + 1]].tolist()
+        d.update((f[j], f[(j + 1) % len(f)]) for j in range(len(f)))
+    B = sum((b, a) not in d for a, b in d)
+    assert B > 0
+    counts = alsub.plan(scheme, m["V"], m["F"], len(fv), 3, boundary=B)
+    ref = oracle.subdivide(m, 3, scheme, keep_all=True)
+    for l, r in enumerate(ref):
+        assert tuple(counts[l]) == (r["V"], r["F"], r["nnz"], r["E"])
+    if scheme == "loop":
+        with pytest.raises(alsub.AlsubError) as e:
+            alsub.plan("sqrt3", m["V"], m["F"], len(fv), 1, boundary=B)
+        assert e.value.status == 3
+
+
 def _create(scheme, V, F, fv, off=None, cv=None, cs=None):
     return alsub.Mesh(scheme, V, F, fv, off, cv, cs, stream=0)
 
