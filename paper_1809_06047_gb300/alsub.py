@@ -43,7 +43,7 @@ def _ptr(a: np.ndarray | None):
 
 def plan(scheme: str, V: int, F: int, nnz: int, levels: int, boundary: int = 0) -> np.ndarray:
     """Closed-form (V, F, nnz, E) per level (host only); ``boundary`` = boundary edges of an open
-    Catmull-Clark mesh (alsub_plan_open)."""
+    Catmull-Clark or Loop mesh (alsub_plan_open)."""
     out = np.zeros(4 * (levels + 1), dtype=np.int64)
     p = out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
     if boundary:

@@ -43,7 +43,7 @@ struct LevelBuf {
     int *tw = nullptr;
     bool helpers = false;  // ce and tw are stored for this level
     CreaseList cr;
-    // boundary list of an open Catmull-Clark mesh (levels below the last): entry i is a boundary
+    // boundary list of an open Catmull-Clark or Loop mesh (levels below the last): entry i is a boundary
     // edge a -> b of this level with a = bA[i], edge id bE[i] and bS[i] = the entry of the next
     // boundary edge b -> c along the loop. Level 0 lists the boundary corners in any order;
     // level l + 1 holds the two halves of entry i at 2i (a -> edge point) and 2i + 1.

@@ -15,7 +15,8 @@ mesh_info_CC, mesh_info_L, mesh_info_S), which are not available:
 * ``torus_tri``       -- triangulated torus with a share of edges flipped (valences 4..8) and a
   share of edges infinitely sharp.
 * ``tube_cc``, ``sheet_cc``, ``holed_cc_mixed`` -- open Catmull-Clark meshes (boundary loops,
-  valence-2 corners, holes cut into the mixed torus) for the boundary rules.
+  valence-2 corners, holes cut into the mixed torus) for the boundary rules; ``triangulate`` turns
+  any of them into a Loop mesh (each n-gon a fan from its first corner).
 
 A mesh is a dict with ``V``, ``F``, ``off`` (int32[F+1]), ``fv`` (int32[nnz], faces in CCW cyclic
 order), ``P`` (float32[V,3]), ``crease_verts`` (int32[K,2]) and ``crease_sharp`` (float32[K]).
