@@ -45,7 +45,26 @@ def _live_creases(m):
     return dict(m, crease_verts=cv[cs > 0], crease_sharp=cs[cs > 0])
 
 
+def _soup(n, seed=9):
+    """n disjoint quads (n components, every vertex of degree 2)."""
+    fv = np.arange(4 * n, dtype=np.int32)
+    P = np.random.default_rng(seed).standard_normal((4 * n, 3)).astype(np.float32)
+    return dict(V=4 * n, F=n, off=np.arange(n + 1, dtype=np.int32) * 4, fv=fv, P=P,
+                crease_verts=np.zeros((0, 2), np.int32), crease_sharp=np.zeros(0, np.float32))
+
+
+def _one(k, seed=10):
+    """A single k-gon."""
+    P = np.random.default_rng(seed).standard_normal((k, 3)).astype(np.float32)
+    return dict(V=k, F=1, off=np.array([0, k], np.int32), fv=np.arange(k, dtype=np.int32), P=P,
+                crease_verts=np.zeros((0, 2), np.int32), crease_sharp=np.zeros(0, np.float32))
+
+
 CASES = [
+    ("single_triangle", "loop", lambda: _one(3)),
+    ("single_quad", "cc", lambda: _one(4)),
+    ("single_heptagon", "cc", lambda: _one(7)),
+    ("seven_components", "cc", lambda: _shuffled(_soup(7), 11)),
     ("cc_mixed_creased", "cc", lambda: _shuffled(synth.torus_cc_mixed(20, 16, merge_frac=0.03, split_frac=0.02,
                                                                       crease_frac=0.05, seed=81), 1)),
     ("cc_holed", "cc", lambda: _shuffled(synth.holed_cc_mixed(20, 16, holes=4, seed=82), 2)),
