@@ -597,7 +597,46 @@ def test_adaptive_refinement_tracks_extraordinary_vertices_exactly():
     np.testing.assert_array_equal(cur["P"][ids], uni["P"][evs])
 
 
-# ---------------------------------------------------------------- hierarchical edits (Sec. 3.4)
+def test_loop_extraction_interior_is_exact():
+    """Loop: one level of an extracted region (its cut refined by the Loop boundary rules) equals
+    the whole mesh's refinement on the triangles around the selected vertices (their children read
+    one ring, well inside the three extracted rings)."""
+    m = synth.torus_tri(24, 20, flip_frac=0.02, sharp_frac=0.0, seed=41)
+    whole = oracle.subdivide(m, 1, "loop")
+    sel = np.zeros(m["V"], bool)
+    sel[[40, 200, 333]] = True
+    e = oracle.extract(m, sel, 3, scheme="loop")
+    assert e["F"] < m["F"]
+    part = oracle.subdivide(e, 1, "loop")
+    inner = oracle.extract(m, sel, 1, scheme="loop")["fmap"]
+    local = np.searchsorted(e["fmap"], inner)
+    assert np.array_equal(e["fmap"][local], inner)
+    for r, q in zip(inner, local):
+        a = whole[1]["fv"][12 * r:12 * (r + 1)]
+        b = part[1]["fv"][12 * q:12 * (q + 1)]
+        np.testing.assert_array_equal(whole[1]["P"][a], part[1]["P"][b])
+
+
+def test_loop_adaptive_refinement_tracks_extraordinary_vertices_exactly():
+    """Loop feature-adaptive refinement (two rings around the valence != 6 vertices, one level,
+    repeat) puts every extraordinary vertex exactly where uniform refinement puts it."""
+    m = synth.torus_tri(20, 16, flip_frac=0.02, sharp_frac=0.0, seed=42)
+    levels = 3
+    uni = oracle.subdivide(m, levels, "loop", keep_all=False)[levels]
+    valence = np.bincount(m["fv"], minlength=m["V"])
+    evs = np.flatnonzero(valence != 6)
+    assert evs.size > 0
+    cur, ids = dict(m, P=m["P"].astype(np.float64)), evs.copy()
+    for _ in range(levels):
+        e = oracle.extract(cur, None, 2, scheme="loop")
+        pos = np.searchsorted(e["vmap"], ids)
+        assert np.array_equal(e["vmap"][pos], ids)
+        assert e["F"] < cur["F"]
+        cur, ids = oracle.subdivide(e, 1, "loop")[1], pos
+    np.testing.assert_array_equal(cur["P"][ids], uni["P"][evs])
+
+
+# ---------------------------------------------------------------- hierarchical edits (Sec. 3.5)
 
 @pytest.mark.parametrize("scheme,mesh", [
     ("cc", synth.torus_cc_mixed(10, 9, crease_frac=0.1, seed=41)),
