@@ -560,6 +560,20 @@ def test_extraction_rings_closed_forms():
         assert sub["V"] - sub["E"] + sub["F"] == 1
 
 
+def test_loop_extraction_rings_closed_forms():
+    """Around one vertex of a regular triangle lattice (every valence 6), r propagation rings keep
+    the hexagon of radius r: 6 r^2 triangles and 3 r (r + 1) + 1 vertices, a disk."""
+    m = synth.torus_tri(16, 16, flip_frac=0.0, sharp_frac=0.0, jitter=0.0)
+    assert set(np.bincount(m["fv"], minlength=m["V"]).tolist()) == {6}
+    sel = np.zeros(m["V"], bool)
+    sel[5 * 16 + 5] = True
+    for r in (1, 2, 3):
+        e = oracle.extract(m, sel, r, scheme="loop")
+        assert (e["F"], e["V"]) == (6 * r * r, 3 * r * (r + 1) + 1)
+        sub = oracle.subdivide(e, 0, "loop")[0]
+        assert sub["V"] - sub["E"] + sub["F"] == 1
+
+
 def test_extraction_interior_is_exact():
     """One level of the extracted region's refinement equals the whole mesh's refinement on the
     faces two rings inside the cut (the region's own cut is refined by the boundary rules)."""
