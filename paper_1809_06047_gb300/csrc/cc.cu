@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(ALSUB_SIB_BLOCK, ALSUB_SIB_MIN_BLOCKS) k_cc_si
 // it also writes the two halves of (a, b) on level l + 1: a -> e at 2i (edge id 2e + 0 when the
 // corner of (a, b) owns its edge, as level 0's boundary corners and levels >= 1's even entries,
 // the corners 0 of their quads, do) and e -> b at 2i + 1, followed by the first half of b -> c.
-__global__ void __launch_bounds__(kBlock) k_bnd_repair(int n, bool lvl0, const int *__restrict__ A,
+__global__ void __launch_bounds__(kBlock) k_cc_bnd(int n, bool lvl0, const int *__restrict__ A,
                                                    const int *__restrict__ E, const int *__restrict__ S,
                                                    int *An, int *En, int *Sn, int V, int El, int VF,
                                                    const float *__restrict__ P, float *Pn, bool in4, bool out4,
@@ -631,7 +631,7 @@ void boundary_step(TopoImpl &T, int l, bool list, const float *P, float *Pn, cud
     LevelBuf *N = list ? &T.L[l + 1] : nullptr;
     // the edge point of edge e is |v| + |f| + e (Catmull-Clark) or |v| + e (Loop)
     const int first_edge_point = (int)(T.scheme == ALSUB_CATMULL_CLARK ? A.V + A.F : A.V);
-    k_bnd_repair<<<grid_for(A.B), kBlock, 0, s>>>((int)A.B, l == 0, A.bA, A.bE, A.bS, N ? N->bA : nullptr,
+    k_cc_bnd<<<grid_for(A.B), kBlock, 0, s>>>((int)A.B, l == 0, A.bA, A.bE, A.bS, N ? N->bA : nullptr,
                                              N ? N->bE : nullptr, N ? N->bS : nullptr, (int)A.V, (int)A.E,
                                              first_edge_point, P, Pn, l > 0, l + 1 < T.levels, T.status);
     T.launches += 1;
