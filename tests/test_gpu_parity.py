@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_1809_06047_gb300 import synth
-from tests import gpu_util
+from tests import crease_cases, gpu_util
 
 pytestmark = pytest.mark.gpu
 
@@ -157,3 +157,18 @@ def test_device_errors_are_latched():
     with pytest.raises(alsub.AlsubError) as e:
         T2.status()
     assert e.value.status == 1
+
+
+CREASE_CASES = [(f, c) for f in ("crease_inheritance.txt", "crease_vertex_sharpness.txt")
+                for c in crease_cases.read_cases(f)]
+
+
+@pytest.mark.parametrize("scheme", ["cc", "loop"])
+@pytest.mark.parametrize("case", [c for _, c in CREASE_CASES], ids=[c["name"] for _, c in CREASE_CASES])
+def test_unequal_crease_sharpness(scheme, case):
+    """The meshes that pin the oracle's Chaikin inheritance and mean vertex sharpness to Sec. 3.3
+    (unequal neighbours, darts, corners, infinite next to finite): crease lists bit-exact and
+    positions within tolerance over four levels, static and dynamic."""
+    m, _ = crease_cases.grid_mesh(scheme, case)
+    for mode in ("static", "dynamic"):
+        _check(m, scheme, 4, mode)

@@ -16,6 +16,7 @@ import pytest
 
 import oracle
 from paper_1809_06047_gb300 import synth
+from tests.crease_cases import GRID, grid_mesh as _grid_mesh, read_cases as _read_crease_cases
 
 GOLD = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -839,3 +840,88 @@ def test_reordering_restores_a_small_bandwidth():
     r = oracle.rcm_reorder(m)
     assert oracle.bandwidth(g) > m["V"] // 2
     assert oracle.bandwidth(oracle.vertex_graph(r)) <= 2 * (24 + 20)
+
+
+# ---- crease inheritance and vertex sharpness with unequal neighbours (Sec. 3.3) --------------
+
+def _neighbours(lvl):
+    """Vertex -> set of vertices sharing a face edge, from a level's face table."""
+    nb = {}
+    off, fv = lvl["off"], lvl["fv"]
+    for r in range(len(off) - 1):
+        f = fv[off[r]:off[r + 1]]
+        for j in range(len(f)):
+            a, b = int(f[j]), int(f[(j + 1) % len(f)])
+            nb.setdefault(a, set()).add(b)
+            nb.setdefault(b, set()).add(a)
+    return nb
+
+
+@pytest.mark.parametrize("scheme", ["cc", "loop"])
+@pytest.mark.parametrize("case", _read_crease_cases("crease_inheritance.txt"), ids=lambda c: c["name"])
+def test_chaikin_inheritance_with_unequal_neighbours(scheme, case):
+    """Level-1 sharpness of every child half equals the paper's two Chaikin equations, hand-derived
+    per half (tests/golden/crease_inheritance.txt); no other crease survives."""
+    m, vid = _grid_mesh(scheme, case)
+    out = oracle.subdivide(m, 1, scheme)
+    nb = _neighbours(out[1])
+    got = {}
+    for (a, b), s in zip(out[1]["crease_verts"], out[1]["crease_sharp"]):
+        got[(min(a, b), max(a, b))] = s
+    expected_live = 0
+    for (i0, j0, i1, j1), end, want in case["halves"]:
+        a, b = vid(i0, j0), vid(i1, j1)
+        x = nb[a] & nb[b]                      # the edge point of (a, b) on level 1
+        assert len(x) == 1
+        x = x.pop()
+        v = a if end == 0 else b
+        key = (min(v, x), max(v, x))
+        if want == 0:
+            assert key not in got, f"half at {v} of ({a},{b}) should have been dropped"
+        else:
+            expected_live += 1
+            assert key in got, f"half at {v} of ({a},{b}) missing"
+            assert got[key] == np.float32(want), (key, got[key], want)
+    assert len(got) == expected_live
+
+
+def _smooth_point(scheme, P, v, nb0):
+    """The smooth level-1 point of a regular vertex from its fixed stencil (regular_stencils.txt)."""
+    p = P[v]
+    if scheme == "cc":
+        # valence 4 on the quad grid: the edge neighbours share an edge; the diagonal ones share a face
+        i, j = divmod(v, GRID)
+        e = [((i + di) % GRID) * GRID + (j + dj) % GRID for di, dj in ((1, 0), (-1, 0), (0, 1), (0, -1))]
+        d = [((i + di) % GRID) * GRID + (j + dj) % GRID for di, dj in ((1, 1), (1, -1), (-1, 1), (-1, -1))]
+        assert set(e) == nb0[v]
+        return (36.0 * p + 6.0 * P[e].sum(axis=0) + P[d].sum(axis=0)) / 64.0
+    ring = sorted(nb0[v])
+    assert len(ring) == 6
+    return (10.0 * p + P[ring].sum(axis=0)) / 16.0
+
+
+@pytest.mark.parametrize("scheme", ["cc", "loop"])
+@pytest.mark.parametrize("case", _read_crease_cases("crease_vertex_sharpness.txt"), ids=lambda c: c["name"])
+def test_vertex_sharpness_is_the_mean_of_unequal_creases(scheme, case):
+    """Crease vertices with unequal incident sharpness (k = 2, k >= 3) and darts (k = 1) at level
+    1 against hand-derived blend weights (tests/golden/crease_vertex_sharpness.txt)."""
+    m, vid = _grid_mesh(scheme, case)
+    out = oracle.subdivide(m, 1, scheme)
+    P = m["P"].astype(np.float64)
+    nb0 = _neighbours(dict(off=m["off"], fv=m["fv"]))
+    creased = {}
+    for (i0, j0, i1, j1), _ in case["creases"]:
+        a, b = vid(i0, j0), vid(i1, j1)
+        creased.setdefault(a, []).append(b)
+        creased.setdefault(b, []).append(a)
+    for (i, j), rule, w in case["vertices"]:
+        v = vid(i, j)
+        smooth = _smooth_point(scheme, P, v, nb0)
+        if rule == "smooth":
+            want = smooth
+        elif rule == "k2":
+            a, b = creased[v]
+            want = w * (P[a] + 6.0 * P[v] + P[b]) / 8.0 + (1.0 - w) * smooth
+        else:
+            want = w * P[v] + (1.0 - w) * smooth
+        np.testing.assert_allclose(out[1]["P"][v], want, rtol=0, atol=1e-15)
