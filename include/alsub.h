@@ -439,17 +439,22 @@ alsub_status alsub_topology_timings(alsub_topology_t topo, double *ms_host, int3
  * code running inside another allocator's callback, or a process that forbids device allocation
  * after start-up) and cannot pass a scratch buffer of their own.
  * It computes exactly what alsub_refine_vertices computes, with the intermediate levels held in a
- * fixed 32 MiB array compiled into the library (every GPU that loads the library keeps it until
- * the process exits) instead of the handle's or the caller's scratch. It calls no cudaMalloc,
- * cudaFree or other allocating routine.
- *   P0_dev: float[3 * V_0]; PL_dev: float[3 * V_levels]; both caller-owned device memory.
- * The first call on a device looks up the array's device address on the current device; make
- * that first call before any stream capture. All calls share the one array and it keeps the last
- * call's contents (nothing in it needs to start at zero): calls that overlap on the GPU race, so
- * serialise them (one stream, or events).
- * Errors: INVALID_ARG (NULL argument), UNSUPPORTED when the topology's intermediate levels need
- * more than 32 MiB (alsub_refine_vertices_scratch_bytes tells the need), DEVICE, and the errors
- * of alsub_refine_vertices.
+ * fixed 32 MiB array compiled into the library instead of the handle's or the caller's scratch,
+ * and with its kernels launched directly on `stream`: it never captures or replays a CUDA graph
+ * and makes no stream or event, so after its set-up it calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *   P0_dev: float[3 * V_0]; PL_dev: float[3 * V_levels]; both caller-owned device memory on the
+ *   current device, which must also be the device the topology was created on.
+ * Set-up: the first call on a device looks up the array's device address with that device
+ * current. That lookup loads the part of the library that holds the array, which reserves its
+ * 32 MiB on the device until the process exits (OOM if it cannot), and the first launch of each
+ * kernel may load that kernel's code. So make the first call at start-up, before any stream
+ * capture and before the point where allocation is forbidden. All calls share the one array and
+ * it keeps the last call's contents (nothing in it needs to start at zero): calls that overlap on
+ * the GPU race, so serialise them (one stream, or events).
+ * Errors: INVALID_ARG (NULL argument, topology not built, topology on another device),
+ * UNSUPPORTED when the topology's intermediate levels need more than 32 MiB
+ * (alsub_refine_vertices_scratch_bytes tells the need), OOM (set-up), DEVICE.
  */
 alsub_status alsub_refine_vertices_static(alsub_topology_t topo, const float *P0_dev, float *PL_dev,
                                           void *stream);

@@ -550,6 +550,13 @@ void alsub::apply_edits(TopoImpl &T, int k, float *out, cudaStream_t s) {
 
 alsub_status alsub::report(alsub_status s, const char *msg) { return fail(s, "%s", msg); }
 
+alsub_status alsub::refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s) {
+    if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
+    refine_body(T, P0, PL, scratch, s);
+    if (T.tcap && T.levels > 0) T.tcalls++;
+    return finish("refine call");
+}
+
 TopoImpl *alsub::topology_impl(alsub_topology_t h) { return &h->t; }
 
 alsub_status alsub::ensure_helpers(TopoImpl &T, cudaStream_t s) {

@@ -238,6 +238,10 @@ void tri_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s);
 struct TriLevel;
 TriLevel tri_level(const TopoImpl &T, int l);
 
+// One vertex refinement of a built topology, its kernels launched directly on `s`: no graph is
+// captured or replayed and no stream or event is made (the graph cache is left as it is).
+alsub_status refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s);
+
 // The implementation behind a topology handle.
 TopoImpl *topology_impl(alsub_topology_t h);
 // Store the per-corner edge ids and twins of every level below the last one (the last
