@@ -542,6 +542,13 @@ typedef struct {
     double host_start_ms_mean;             /* worker time to enqueue a request (validation,
                                               allocation, launches), mean over completed ones */
     double host_finish_ms_mean;            /* worker time to retire one (status, copies, frees) */
+    int64_t peak_in_flight;                /* most requests admitted into slots and not yet
+                                              retired at one time */
+    int64_t device_overlap_peak;           /* most completed requests whose compute intervals on
+                                              the device (CUDA events recorded on each request's
+                                              stream after its input copy and after its kernels)
+                                              were open at one instant: > 1 means the work of
+                                              different requests overlapped on the GPU */
 } alsub_serve_stats;
 
 /* Start a server on the current device. max_slots 1..64 (concurrent requests), budget > 0. The

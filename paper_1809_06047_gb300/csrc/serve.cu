@@ -80,6 +80,7 @@ struct Job {
 struct Slot {
     cudaStream_t stream = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t ev_b = nullptr, ev_c = nullptr;  // timed: the request's compute begins / ends
     Job *job = nullptr;
     float *h_in = nullptr, *h_out = nullptr;   // page-locked staging
     size_t cap_in = 0, cap_out = 0;
@@ -115,6 +116,10 @@ struct alsub_server_s {
     std::condition_variable cv_work, cv_done;
     std::vector<std::thread> workers;
     int running = 0;                 // requests admitted and not yet retired (all workers)
+    int running_peak = 0;            // largest `running` seen
+    cudaEvent_t t0 = nullptr;        // timed reference event, recorded at creation
+    std::vector<std::pair<float, float>> dev_iv;   // completed requests' compute intervals (ms
+                                                   // after t0, from the slot's events)
     bool stop = false, paused = false;
     int device = 0;
     cudaStream_t reg_stream = nullptr;
@@ -159,6 +164,7 @@ alsub_status start(Slot &sl, Job &j) {
     memcpy(sl.h_in, j.P0.data(), 4 * n_in);
     if (cudaMemcpyAsync(d_in, sl.h_in, 4 * n_in, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
         return report(ALSUB_ERR_DEVICE, "server: input copy failed");
+    cudaEventRecord(sl.ev_b, sl.stream);
     if (j.kind == ALSUB_REQ_FRAME) {
         j.by_operator = R->op != nullptr;
         st = R->op ? alsub_apply_operator(R->op, d_in, d_out, sl.stream)
@@ -167,6 +173,7 @@ alsub_status start(Slot &sl, Job &j) {
         st = alsub_subdivide(sl.topo, d_in, d_out, nullptr, sl.stream);
     }
     if (st != ALSUB_OK) return st;
+    cudaEventRecord(sl.ev_c, sl.stream);
     float *dst = direct ? j.user_out : sl.h_out;
     if (cudaMemcpyAsync(dst, d_out, 4 * n_out, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
         cudaEventRecord(sl.ev, sl.stream) != cudaSuccess)
@@ -184,6 +191,10 @@ void finish(alsub_server_s &S, Slot &sl, alsub_status st) {
         if (!j.user_out) j.out.assign(sl.h_out, sl.h_out + n_out);
         else if (!j.user_pinned) memcpy(j.user_out, sl.h_out, 4 * n_out);
     }
+    float tb = -1.f, tc = -1.f;
+    if (st == ALSUB_OK && (cudaEventElapsedTime(&tb, S.t0, sl.ev_b) != cudaSuccess ||
+                           cudaEventElapsedTime(&tc, S.t0, sl.ev_c) != cudaSuccess))
+        tb = tc = -1.f;
     if (sl.d_buf) cudaFreeAsync(sl.d_buf, sl.stream);
     sl.d_buf = nullptr;
     if (sl.topo) alsub_topology_destroy(sl.topo);
@@ -205,6 +216,7 @@ void finish(alsub_server_s &S, Slot &sl, alsub_status st) {
         S.host_finish_sum += j.host_finish;
         S.completed++;
         S.last_done = t;
+        if (tb >= 0.f) S.dev_iv.emplace_back(tb, tc);
         if (j.kind == ALSUB_REQ_MESH) S.meshes++;
         else if (j.by_operator) S.frames_op++;
         else S.frames_eval++;
@@ -261,6 +273,7 @@ void worker_loop(alsub_server_s *Sp, int first, int count) {
                     S.peak = std::max(S.peak, S.used);
                 }
                 S.running++;
+                S.running_peak = std::max(S.running_peak, S.running);
                 j = h;
             }
             progress = true;
@@ -335,11 +348,16 @@ alsub_status alsub_serve_create(size_t budget, int32_t max_slots, alsub_server_t
     bool ok = cudaStreamCreateWithFlags(&S->reg_stream, cudaStreamNonBlocking) == cudaSuccess;
     for (Slot &sl : S->slots)
         ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess;
+             cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreate(&sl.ev_b) == cudaSuccess && cudaEventCreate(&sl.ev_c) == cudaSuccess;
+    ok = ok && cudaEventCreate(&S->t0) == cudaSuccess && cudaEventRecord(S->t0, S->reg_stream) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
+        if (S->t0) cudaEventDestroy(S->t0);
         for (Slot &sl : S->slots) {
             if (sl.ev) cudaEventDestroy(sl.ev);
+            if (sl.ev_b) cudaEventDestroy(sl.ev_b);
+            if (sl.ev_c) cudaEventDestroy(sl.ev_c);
             if (sl.stream) cudaStreamDestroy(sl.stream);
         }
         if (S->reg_stream) cudaStreamDestroy(S->reg_stream);
@@ -619,6 +637,18 @@ alsub_status alsub_serve_stats_get(alsub_server_t S, alsub_serve_stats *st) {
     st->meshes = S->meshes;
     st->host_start_ms_mean = S->completed ? 1e3 * S->host_start_sum / (double)S->completed : 0;
     st->host_finish_ms_mean = S->completed ? 1e3 * S->host_finish_sum / (double)S->completed : 0;
+    st->peak_in_flight = S->running_peak;
+    // most compute intervals open at one instant (an interval's end sorts before a start at the
+    // same time, so touching intervals do not count as overlapping)
+    std::vector<std::pair<float, int>> ev;
+    ev.reserve(2 * S->dev_iv.size());
+    for (const auto &iv : S->dev_iv) {
+        ev.emplace_back(iv.first, 1);
+        ev.emplace_back(iv.second, -1);
+    }
+    std::sort(ev.begin(), ev.end());
+    int64_t open = 0;
+    for (const auto &e : ev) st->device_overlap_peak = std::max(st->device_overlap_peak, open += e.second);
     return ALSUB_OK;
 }
 
@@ -656,8 +686,11 @@ alsub_status alsub_serve_destroy(alsub_server_t S) {
         if (sl.h_in) cudaFreeHost(sl.h_in);
         if (sl.h_out) cudaFreeHost(sl.h_out);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.ev_b) cudaEventDestroy(sl.ev_b);
+        if (sl.ev_c) cudaEventDestroy(sl.ev_c);
         if (sl.stream) cudaStreamDestroy(sl.stream);
     }
+    if (S->t0) cudaEventDestroy(S->t0);
     for (auto &R : S->residents) free_resident(*R);
     if (S->reg_stream) {
         cudaStreamSynchronize(S->reg_stream);

@@ -1,10 +1,13 @@
 """Ragged batches: many topologies of uneven sizes, mixed schemes and level counts, refined with
 one launch per level per kernel class (CUDA graph replay). Every member must equal its own
-alsub_refine_vertices result within the parity tolerance."""
+alsub_refine_vertices result within the parity tolerance, and the oracle: topology from each
+member's handle (bit-exact after relabelling), positions from the batch output."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_1809_06047_gb300 import synth
+from tests import gpu_util
 
 pytestmark = pytest.mark.gpu
 
@@ -23,6 +26,24 @@ def _members():
         ("sqrt3", synth.tetrahedron(), 2),
         ("cc", synth.torus_cc_mixed(12, 12, seed=86), 0),
     ]
+
+
+def _oracle_refs():
+    return [oracle.subdivide(m, lv, scheme, keep_all=True) for scheme, m, lv in _members()]
+
+
+def _check_oracle(topos, outs, refs):
+    """Each member's face tables and creases from its own handle, its last level's positions from
+    the batch output, against the oracle."""
+    for (scheme, m, lv), T, got, ref in zip(_members(), topos, outs, refs):
+        gpu = []
+        for l in range(lv + 1):
+            d = dict(T.counts[l])
+            d["fv"] = T.faces(l)
+            d["crease_verts"], d["crease_sharp"] = T.creases(l)
+            gpu.append(d)
+        gpu[-1]["P"] = got.cpu().numpy()
+        gpu_util.compare(scheme, gpu, ref, pos_levels={lv})
 
 
 def _build():
@@ -58,6 +79,9 @@ def test_batch_matches_members_and_replays():
     for a, b in zip(first, second):
         assert torch.equal(a, b)
     _check(topos, P0s, first)
+    refs = _oracle_refs()
+    _check_oracle(topos, first, refs)
+    _check_oracle(topos, second, refs)
     # new positions written into the bound inputs are picked up by the replay
     for P in P0s:
         P.mul_(1.5).add_(0.25)
@@ -83,6 +107,7 @@ def test_batch_autotune_keeps_results():
     torch.cuda.synchronize()
     assert best["block"] in (128, 256, 512) and best["ms"] > 0
     _check(topos, P0s, outs)
+    _check_oracle(topos, outs, _oracle_refs())
     B.configure(128, 0)
     outs = [x.clone() for x in B.refine()]
     torch.cuda.synchronize()
