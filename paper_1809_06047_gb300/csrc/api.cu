@@ -175,6 +175,7 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     AL(L0.tw, nnz);
     AL(T.cf0, nnz); AL(T.nx0, nnz); AL(T.pv0, nnz); AL(T.own0, nnz); AL(T.rn0, nnz); AL(T.eid, nnz);
     AL(T.vc0, V); AL(T.deg, V);
+    if (M.scheme == ALSUB_CATMULL_CLARK) AL(T.rec0, (size_t)kRecInts * nnz);
     {
         int k = 4;                                   // directed-edge table: load factor <= 1/2
         while ((1LL << k) < 2LL * nnz) k++;
@@ -322,7 +323,7 @@ alsub_status run_call(TopoImpl &T, int kind, const float *P0, float *PL, void *s
         }
         G = lru;
         drop_graph(*G);
-        if (kind == 1) ensure_side(T);      // the crease branch, for the graph of a repeated call
+        ensure_side(T);      // the crease branch and the ring stream, for the graph of a repeated call
         bool ok = T.cap || cudaStreamCreateWithFlags(&T.cap, cudaStreamNonBlocking) == cudaSuccess;
         const long long before = T.launches;
         cudaGraph_t g = nullptr;
@@ -397,6 +398,13 @@ void free_side(TopoImpl &T) {
     for (cudaEvent_t e : T.join_ev) if (e) cudaEventDestroy(e);
     T.fork_ev.clear();
     T.join_ev.clear();
+    if (T.ring_ev) cudaEventDestroy(T.ring_ev);
+    T.ring_ev = nullptr;
+    if (T.rfork) cudaEventDestroy(T.rfork);
+    if (T.rjoin) cudaEventDestroy(T.rjoin);
+    if (T.rside) cudaStreamDestroy(T.rside);
+    T.rfork = T.rjoin = nullptr;
+    T.rside = nullptr;
     if (T.side) cudaStreamDestroy(T.side);
     T.side = nullptr;
 }
@@ -412,6 +420,11 @@ void ensure_side(TopoImpl &T) {
     for (int l = 0; ok && l <= T.levels; l++)
         ok = cudaEventCreateWithFlags(&T.fork_ev[l], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&T.join_ev[l], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&T.ring_ev, cudaEventDisableTiming) == cudaSuccess;
+    if (ok && T.scheme == ALSUB_CATMULL_CLARK)
+        ok = cudaStreamCreateWithFlags(&T.rside, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&T.rfork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&T.rjoin, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         free_side(T);
@@ -492,7 +505,8 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
             cudaStreamWaitEvent(z, T.fork_ev[0], 0);
         }
     }
-    level0_validate(T, z);
+    level0_validate(T, z);                  // also writes the ring records the steps >= 2 read
+    if (z != s) cudaEventRecord(T.ring_ev, z);
     mark(T, 1, s);
     auto join_all = [&] {                   // everything on the side branch, before the call ends
         if (z == s) return;
@@ -508,6 +522,7 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
         const float *in;
         float *out;
         level_buffers(T, P0, PL, scratch, l, &in, &out);
+        if (l == 2 && z != s) cudaStreamWaitEvent(s, T.ring_ev, 0);
         step(T, l, true, T.L[l + 1].helpers, in, out, s);
         if (l + 1 < T.levels) {
             if (crease_alive(T, l + 1)) analyse_beside(l + 1, false);

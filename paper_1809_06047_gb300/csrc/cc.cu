@@ -275,7 +275,7 @@ __device__ __forceinline__ void prefetch_rows(const int *rows, long long f0, lon
     l2_prefetch(rows + 4 * f0, (unsigned)(16 * n));
 }
 
-template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND>
+template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND, bool RINGS>
 __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
     if (ALSUB_SIB_PREFETCH > 0 && threadIdx.x == 0) {
         const long long f0 = ((long long)blockIdx.x + ALSUB_SIB_PREFETCH) * blockDim.x;
@@ -394,53 +394,69 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
                 stpv(a.Pn, v.y, 0.5625f * pb + 0.09375f * (pc + pa + pz + pan) + 0.015625f * (pd + py + pw + pbn),
                      a.out4);
             if (fk > 0) stpv(a.Pn, v.x, vp_old, a.out4);
-            if (fk < 0 && b.k != 3) {
-                // created on level 0 or 1: designation and ring need the level-0 arrays
-                bool des;
-                if (b.m == 0) des = __ldg(z.vc + __ldg(z.fv + b.c)) == b.c;
-                else if (b.k == 1) des = __ldg(z.own + b.c) != 0;
-                else des = b.c == __ldg(z.off + __ldg(z.cf + b.c));
-                if (des) {
-                    const int sh = 2 * (a.l - b.m - 1);
-                    float3 sn = f3(0.f, 0.f, 0.f), so = sn;
-                    int n = 0;
-                    auto visit = [&](int y) {
+            if (RINGS && fk < 0 && b.k != 3) {
+                // created on level 0 or 1: designation and ring come from the level-0 record. Its
+                // ring faces on level l are the descendants (index << sh) of the faces y listed
+                // one level below the birth level, the vertex at their corner 0.
+                const int sh = 2 * (a.l - b.m - 1);
+                const int4 *rp = reinterpret_cast<const int4 *>(z.rec) + (size_t)(kRecInts / 4) * b.c;
+                const int4 rh = __ldg(rp + ((b.m == 1 && b.k == 2) ? kRecFace / 4 : 0));
+                float3 sn = f3(0.f, 0.f, 0.f), so = sn;
+                int n = 0;
+                bool walk = false, ok = true;
+                int4 ra = make_int4(0, 0, 0, 0), rb = ra;
+                if (b.m == 0) {
+                    if (rh.x > 0) {                          // designated, closed ring of rh.x faces
+                        n = rh.x;
+                        ra = __ldg(rp + kRecRing / 4);
+                        if (n > 4) rb = __ldg(rp + kRecRing / 4 + 1);
+                    }
+                    walk = rh.x == kRecLong;
+                } else if (b.k == 1) {
+                    if (rh.y >= 0) {                         // the owned edge's four ring faces
+                        n = 4;
+                        ra = make_int4(4 * b.c + 1, 4 * rh.z + 3, 4 * rh.y + 1, 4 * rh.w + 3);
+                    }
+                } else {
+                    n = rh.x;                                // the first corner's face: its order
+                }
+                if (walk) {                                  // a long ring: walked
+                    int y = b.c;
+                    do {
                         const int4 q = ld4(fv + 4 * ((size_t)y << sh));
                         sn += ldpv(P, q.y, true);
                         so += ldpv(P, q.z, true);
+                        y = __ldg(z.rn + y);
                         n++;
-                    };
-                    bool ok = true, open = false;     // open: a boundary vertex, repaired
-                    if (b.m == 0) {
-                        int y = b.c;
-                        do {
-                            visit(y);
-                            y = __ldg(z.rn + y);
-                        } while ((!BND || y >= 0) && y != b.c && n < kMaxValence);
-                        open = BND && y < 0;
-                        ok = y == b.c;
-                    } else if (b.k == 1) {
-                        const int t0 = __ldg(z.tw + b.c);
-                        if (BND && t0 < 0) {
-                            open = true;
-                        } else {
-                            visit(4 * b.c + 1);
-                            visit(4 * __ldg(z.nx + t0) + 3);
-                            visit(4 * t0 + 1);
-                            visit(4 * __ldg(z.nx + b.c) + 3);
+                    } while ((!BND || y >= 0) && y != b.c && n < kMaxValence);
+                    ok = y == b.c;
+                    if (BND && y < 0) n = 0;                 // a boundary vertex: repaired
+                } else {
+                    // four ring faces per round: their rows, then their positions
+                    for (int i0 = 0; i0 < n; i0 += 4) {
+                        int4 q[4];
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            const int i = i0 + u;
+                            const int y = (b.m == 1 && b.k == 2) ? 4 * (b.c + i) + 2
+                                                                 : (i < 4 ? comp(ra, i) : comp(rb, i - 4));
+                            if (i < n) q[u] = ld4(fv + 4 * ((size_t)y << sh));
                         }
-                    } else {
-                        const int Q = __ldg(z.cf + b.c), s0 = __ldg(z.off + Q), c = __ldg(z.off + Q + 1) - s0;
-                        for (int i = 0; i < c; i++) visit(4 * (s0 + i) + 2);
+#pragma unroll
+                        for (int u = 0; u < 4; u++) {
+                            if (i0 + u < n) {
+                                sn += ldpv(P, q[u].y, true);
+                                so += ldpv(P, q[u].z, true);
+                            }
+                        }
                     }
-                    if (open) {
-                    } else if (!ok) {
-                        set_status(a.status, ALSUB_ERR_UNSUPPORTED);
-                    } else {
-                        const float inv = 1.0f / (float)n;
-                        stpv(a.Pn, v.x, (1.0f - 1.75f * inv) * pa + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so,
-                             a.out4);
-                    }
+                }
+                if (!ok) {
+                    set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+                } else if (n > 0) {
+                    const float inv = 1.0f / (float)n;
+                    stpv(a.Pn, v.x, (1.0f - 1.75f * inv) * pa + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so,
+                         a.out4);
                 }
             }
         }
@@ -493,9 +509,84 @@ template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
     cc_quad_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
+// Vertices born on levels 0 and 1 are left to k_cc_ring01, which runs beside this kernel.
 template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND>
 __global__ void __launch_bounds__(ALSUB_SIB_BLOCK, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
-    cc_sib_body<TOPO, HELP, EVAL, DERIVE, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    cc_sib_body<TOPO, HELP, EVAL, DERIVE, BND, false>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+
+// Vertex point, on a level l >= 2, of a vertex born on level m <= 1 whose ring faces on level l are
+// the descendants (y << sh) of the faces y(i), i < n (the vertex at their corner 0, so the first
+// row names it): (1 - 7/(4n)) p + 3/(2n^2) sum next + 1/(4n^2) sum opposite (Eq. pos_update on
+// quads). Four ring faces per round trip pair (their rows, then their positions).
+template <class Y>
+__device__ __forceinline__ void ring_vertex(const CCArgs &a, int n, int sh, Y y) {
+    const int *__restrict__ fv = a.fv;
+    const float *__restrict__ P = a.P;
+    float3 sn = f3(0.f, 0.f, 0.f), so = sn, p = sn;
+    int vid = 0;
+    for (int i0 = 0; i0 < n; i0 += 4) {
+        int4 q[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++)
+            if (i0 + u < n) q[u] = ld4(fv + 4 * ((size_t)y(i0 + u) << sh));
+        if (i0 == 0) {
+            vid = q[0].x;
+            p = ldpv(P, vid, true);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (i0 + u < n) {
+                sn += ldpv(P, q[u].y, true);
+                so += ldpv(P, q[u].z, true);
+            }
+        }
+    }
+    const float inv = 1.0f / (float)n;
+    stpv(a.Pn, vid, (1.0f - 1.75f * inv) * p + (1.5f * inv * inv) * sn + (0.25f * inv * inv) * so, a.out4);
+}
+
+// Level l >= 2 step, the vertices the sibling kernel leaves out: those born on levels 0 and 1,
+// one level-0 corner c per thread, from its ring record (Level0::rec): the control vertex c
+// designates, the level-1 edge point of the edge c owns, the level-1 face point of the face whose
+// first corner c is. Boundary vertices are skipped (the boundary repair writes them).
+template <bool BND>
+__global__ void __launch_bounds__(kBlock) k_cc_ring01(CCArgs a, int nnz0) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= nnz0 || failed(a.status)) return;
+    const int4 *rp = reinterpret_cast<const int4 *>(a.z.rec) + (size_t)(kRecInts / 4) * c;
+    const int4 h0 = __ldg(rp), h1 = __ldg(rp + kRecFace / 4);
+    const int sh1 = 2 * (a.l - 1), sh2 = 2 * (a.l - 2);
+    if (h0.x > 0) {                                   // the control vertex: its ring corners
+        const int4 ra = __ldg(rp + kRecRing / 4);
+        const int4 rb = h0.x > 4 ? __ldg(rp + kRecRing / 4 + 1) : ra;
+        ring_vertex(a, h0.x, sh1, [&](int i) { return i < 4 ? comp(ra, i) : comp(rb, i - 4); });
+    } else if (h0.x == kRecLong) {                    // a longer ring: walked
+        const int *__restrict__ fv = a.fv;
+        float3 sn = f3(0.f, 0.f, 0.f), so = sn;
+        int y = c, n = 0, vid = 0;
+        do {
+            const int4 q = ld4(fv + 4 * ((size_t)y << sh1));
+            vid = q.x;
+            sn += ldpv(a.P, q.y, true);
+            so += ldpv(a.P, q.z, true);
+            y = __ldg(a.z.rn + y);
+            n++;
+        } while (y >= 0 && y != c && n < kMaxValence);
+        if (y != c) {
+            if (!BND || y >= 0) set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+        } else {
+            const float inv = 1.0f / (float)n;
+            stpv(a.Pn, vid, (1.0f - 1.75f * inv) * ldpv(a.P, vid, true) + (1.5f * inv * inv) * sn +
+                                (0.25f * inv * inv) * so, a.out4);
+        }
+    }
+    if (h0.y >= 0) {                                  // the owned edge's four ring faces
+        const int4 ra = make_int4(4 * c + 1, 4 * h0.z + 3, 4 * h0.y + 1, 4 * h0.w + 3);
+        ring_vertex(a, 4, sh2, [&](int i) { return comp(ra, i); });
+    }
+    if (h1.x > 0)                                     // the face's order
+        ring_vertex(a, h1.x, sh2, [&](int i) { return 4 * (c + i) + 2; });
 }
 
 // Boundary repair of step l (Sec. 3.2 "Boundaries"): entry i of level l's boundary list is the
@@ -556,9 +647,9 @@ __global__ void __launch_bounds__(512, 2) k_cc_batch(const CCArgs *__restrict__ 
         const CCArgs &a = items[i];          // read in place: a copy would not fit in registers
         if (KIND == 0) cc_l0_body<false, false, true, false>(a, r);
         else if (KIND == 1) cc_quad_body<false, false, true, false>(a, r);
-        else if (KIND == 2) cc_sib_body<false, false, true, 0, false>(a, r);
-        else if (KIND == 3) cc_sib_body<false, false, true, 1, false>(a, r);
-        else cc_sib_body<false, false, true, 2, false>(a, r);
+        else if (KIND == 2) cc_sib_body<false, false, true, 0, false, true>(a, r);
+        else if (KIND == 3) cc_sib_body<false, false, true, 1, false, true>(a, r);
+        else cc_sib_body<false, false, true, 2, false, true>(a, r);
     }
 }
 
@@ -587,7 +678,8 @@ CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, int *derive_out)
     a.l = l;
     a.V = (int)A.V; a.F = (int)A.F; a.E = (int)A.E;
     a.fv = A.fv; a.ce = A.ce; a.tw = A.tw;
-    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
+    a.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0,
+                 T.rec0};
     a.P = P; a.Pn = Pn;
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
@@ -617,11 +709,30 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     CCArgs a = make_args(T, l, P, Pn, &derive);
     bool ev = P != nullptr;
     if (topo || ev) T.launches += 1;
+    // levels >= 2: the vertices born on levels 0 and 1 go to k_cc_ring01, launched first on the
+    // handle's ring stream beside the sibling kernel when it has one (forked and joined here, so
+    // that its few blocks take SMs before the sibling kernel's grid fills them), else after it
+    const bool rings = ev && l >= 2;
+    const int nnz0 = T.mesh->nnz;
+    auto launch_rings = [&](cudaStream_t rs) {
+        if (a.bnd) k_cc_ring01<true><<<grid_for(nnz0), kBlock, 0, rs>>>(a, nnz0);
+        else k_cc_ring01<false><<<grid_for(nnz0), kBlock, 0, rs>>>(a, nnz0);
+        T.launches += 1;
+    };
+    const bool beside = rings && T.rside;
+    if (beside) {
+        cudaEventRecord(T.rfork, s);
+        cudaStreamWaitEvent(T.rside, T.rfork, 0);
+        launch_rings(T.rside);
+        cudaEventRecord(T.rjoin, T.rside);
+    }
     if (topo && helpers && ev) launch<true, true, true>(a, derive, s);
     else if (topo && helpers) launch<true, true, false>(a, derive, s);
     else if (topo && ev) launch<true, false, true>(a, derive, s);
     else if (topo) launch<true, false, false>(a, derive, s);
     else if (ev) launch<false, false, true>(a, derive, s);
+    if (beside) cudaStreamWaitEvent(s, T.rjoin, 0);
+    else if (rings) launch_rings(s);
     if (a.bnd) boundary_step(T, l, topo && l + 1 < T.levels, P, Pn, s);
 }
 

@@ -82,7 +82,20 @@ struct Level0 {
     const int *own;   // 1 if the corner owns its edge (start vertex < end vertex)
     const int *vc;    // designated (smallest) outgoing corner of each vertex
     const int *rn;    // ring step twin(prev(x)): the next outgoing corner around the start vertex
+    const int *rec = nullptr;   // Catmull-Clark ring records of level 0 (kRec* below), or null
 };
+
+// Ring record of level-0 corner c (16 ints at rec + 16 c) for the vertices that refined levels
+// >= 2 cannot classify by index arithmetic alone (those born on levels 0 and 1):
+//   [kRecVertex]  the vertex fv[c] when c is its designated corner: its valence n (1 .. 8, the
+//                 ring's corners in walk order x <- twin(prev(x)) at [8, 8 + n)), kRecOpen on the
+//                 boundary, kRecLong for a longer ring (walked instead); 0 elsewhere
+//   [kRecEdge]    the edge point of c's edge when c owns it: the twin t of c (kRecOpen for a
+//                 boundary edge), with [2] = next(t) and [3] = next(c); -1 when c does not own it
+//   [4]           the face point of c's face when c is its first corner: the face's order; else 0
+constexpr int kRecInts = 16;
+constexpr int kRecVertex = 0, kRecEdge = 1, kRecFace = 4, kRecRing = 8, kRecMaxRing = 8;
+constexpr int kRecOpen = -2, kRecLong = -3;
 
 // Corner accessors used by the ring walks of the crease kernels. Each gives next / prev corner
 // in the face, the ring step twin(prev), twin, edge id and start vertex of a corner.

@@ -91,6 +91,9 @@ struct TopoImpl {
     // level-0 adjacency
     int *cf0 = nullptr, *nx0 = nullptr, *pv0 = nullptr, *own0 = nullptr, *vc0 = nullptr;
     int *eo0 = nullptr, *deg = nullptr, *rn0 = nullptr;   // rn0: twin(prev(x)), the ring step
+    // Catmull-Clark: the rings of the vertices born on levels 0 and 1, per level-0 corner c, 16
+    // ints (see kRec* in common.cuh), read by the steps of levels >= 2 instead of walking them
+    int *rec0 = nullptr;
     DirTable dir;
     int *eid = nullptr, *e0count = nullptr;
     int *bcount = nullptr;       // boundary corners found on level 0
@@ -127,6 +130,11 @@ struct TopoImpl {
     // build + eval step (fork after the step that built level l, join before the crease fix)
     cudaStream_t side = nullptr;
     std::vector<cudaEvent_t> fork_ev, join_ev;   // levels + 1 each
+    cudaEvent_t ring_ev = nullptr;               // the ring records of level 0 are written
+    // Catmull-Clark levels >= 2: the stream the vertices born on levels 0 and 1 are refined on,
+    // beside the step's main kernel (fork and join events reused level after level)
+    cudaStream_t rside = nullptr;
+    cudaEvent_t rfork = nullptr, rjoin = nullptr;
     // hierarchical edits (alsub_topology_set_edits): per level, offsets added to its vertices after
     // the level has been refined
     struct LevelEdits {

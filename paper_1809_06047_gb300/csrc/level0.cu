@@ -132,9 +132,11 @@ __global__ void __launch_bounds__(kBlock) k_eid(int nnz, const int *__restrict__
 // exactly deg(v) steps. Boundary vertex (the walk meets a corner without twin): the walk forward
 // from the start to the fan's end plus the walk backward x <- next(twin(x)) to its beginning
 // visit deg(v) corners (a second fan would be missed by both).
+// With `rec` (Catmull-Clark), the walk also fills the ring record of the designated corner (the
+// corners in walk order, for the steps of levels >= 2 that read the vertex's ring).
 __global__ void k_vertex(int V, const int *__restrict__ deg, const unsigned *__restrict__ vc,
                          const int *__restrict__ rn, const int *__restrict__ tw, const int *__restrict__ nx,
-                         int *status) {
+                         int *rec, int *status) {
     int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const int d = deg[v];
@@ -142,13 +144,20 @@ __global__ void k_vertex(int V, const int *__restrict__ deg, const unsigned *__r
     if (d > kMaxValence) { set_status(status, ALSUB_ERR_UNSUPPORTED); return; }
     if (failed(status)) return;
     const int m = (int)vc[v];
+    int *r = rec ? rec + (size_t)kRecInts * m : nullptr;
     int x = m, steps = 0;
-    do { x = rn[x]; steps++; } while (x >= 0 && x != m && steps <= d);
+    do {
+        if (r && steps < kRecMaxRing) r[kRecRing + steps] = x;
+        x = rn[x];
+        steps++;
+    } while (x >= 0 && x != m && steps <= d);
+    const bool closed = x == m;
     if (x < 0) {
         int y = m;
         while (tw[y] >= 0 && steps <= d) { y = nx[tw[y]]; steps++; }
     }
     if (steps != d) set_status(status, ALSUB_ERR_NONMANIFOLD);
+    if (r) r[kRecVertex] = !closed ? kRecOpen : (steps <= kRecMaxRing && steps == d ? steps : kRecLong);
 }
 
 // Boundary corners of an open mesh (twin -1), appended in any order: entry i holds the corner's
@@ -211,17 +220,27 @@ __global__ void k_mb_crease(int K, const int *__restrict__ cv, const int *__rest
 
 // Edge ids (an owner's own, else its twin's), owner corner of each edge, and the ring step
 // twin(prev(x)).
+// With `rec` (Catmull-Clark), also the edge and face parts of the corner's ring record (its
+// vertex part is set to 0 here and filled by k_vertex at the designated corners).
 __global__ void k_edges(int nnz, const int *__restrict__ own, const int *__restrict__ eid,
-                        const int *__restrict__ tw, const int *__restrict__ pv, const int *e0count, int E0,
-                        int *ce, int *eo, int *rn, int *status) {
+                        const int *__restrict__ tw, const int *__restrict__ pv, const int *__restrict__ nx,
+                        const int *__restrict__ off, const int *__restrict__ cf, const int *e0count, int E0,
+                        int *ce, int *eo, int *rn, int *rec, int *status) {
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x == 0 && *e0count != E0) set_status(status, ALSUB_ERR_NONMANIFOLD);
     if (x >= nnz) return;
-    int e = own[x] ? eid[x] : eid[tw[x]];
+    const int o = own[x], t = tw[x];
+    int e = o ? eid[x] : eid[t];
     e = min(max(e, 0), E0 - 1);
     ce[x] = e;
-    if (own[x]) eo[e] = x;
+    if (o) eo[e] = x;
     rn[x] = tw[pv[x]];
+    if (rec) {
+        const int f = cf[x], s = off[f];
+        int4 *r = reinterpret_cast<int4 *>(rec + (size_t)kRecInts * x);
+        r[0] = make_int4(0, !o ? -1 : (t < 0 ? kRecOpen : t), (o && t >= 0) ? nx[t] : 0, nx[x]);
+        r[1] = make_int4(x == s ? off[f + 1] - s : 0, 0, 0, 0);
+    }
 }
 
 // Level-0 crease list, in input order (the crease matrix C of Sec. 3.3): each input crease
@@ -267,8 +286,8 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     k_twin<<<nb, kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, open, L0.tw, T.own0, T.flags, T.status);
     T.launches += 5 + scan_exclusive(T.flags, T.pos, nb, T.e0count, nullptr, T.scan_tmp, s);
     k_eid<<<nb, kBlock, 0, s>>>(nnz, T.own0, T.pos, T.eid);
-    k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.pv0, T.e0count, E0, L0.ce, T.eo0,
-                                             T.rn0, T.status);
+    k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.pv0, T.nx0, M.d_off, T.cf0, T.e0count,
+                                             E0, L0.ce, T.eo0, T.rn0, T.rec0, T.status);
     if (L0.B > 0) {
         // (the list exists when a step follows: levels >= 1.) The per-corner edge-id temporaries
         // are dead: they map boundary corners to entries
@@ -341,7 +360,7 @@ alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool 
 
 void level0_validate(TopoImpl &T, cudaStream_t s) {
     k_vertex<<<grid_for(T.mesh->V), kBlock, 0, s>>>(T.mesh->V, T.deg, reinterpret_cast<unsigned *>(T.vc0),
-                                                    T.rn0, T.L[0].tw, T.nx0, T.status);
+                                                    T.rn0, T.L[0].tw, T.nx0, T.rec0, T.status);
     T.launches += 1;
 }
 
