@@ -503,15 +503,21 @@ __device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
 
 template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
+    pdl_wait();
+    pdl_trigger();
     cc_l0_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
+    pdl_wait();
+    pdl_trigger();
     cc_quad_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 // Vertices born on levels 0 and 1 are left to k_cc_ring01, which runs beside this kernel.
 template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND>
 __global__ void __launch_bounds__(ALSUB_SIB_BLOCK, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
+    pdl_wait();
+    pdl_trigger();
     cc_sib_body<TOPO, HELP, EVAL, DERIVE, BND, false>(a, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
@@ -601,6 +607,8 @@ __global__ void __launch_bounds__(kBlock) k_cc_bnd(int n, bool lvl0, const int *
                                                    int *An, int *En, int *Sn, int V, int El, int VF,
                                                    const float *__restrict__ P, float *Pn, bool in4, bool out4,
                                                    int *status) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n || failed(status)) return;
     auto clampi = [](int x, int hi) { return min(max(x, 0), hi - 1); };
@@ -656,11 +664,11 @@ __global__ void __launch_bounds__(512, 2) k_cc_batch(const CCArgs *__restrict__ 
 template <bool T, bool H, bool E, bool B>
 void launch_b(const CCArgs &a, int derive, cudaStream_t s) {
     const unsigned g = grid_for(a.F, ALSUB_SIB_BLOCK);
-    if (a.l == 0) k_cc_l0<T, H, E, B><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else if (a.l == 1) k_cc_quad<T, H, E, B><<<grid_for(a.F), kBlock, 0, s>>>(a);
-    else if (derive == 2) k_cc_sib<T, false, E, 2, B><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
-    else if (derive == 1) k_cc_sib<T, false, E, 1, B><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
-    else k_cc_sib<T, H, E, 0, B><<<g, ALSUB_SIB_BLOCK, 0, s>>>(a);
+    if (a.l == 0) launch_pdl(k_cc_l0<T, H, E, B>, grid_for(a.F), kBlock, s, a);
+    else if (a.l == 1) launch_pdl(k_cc_quad<T, H, E, B>, grid_for(a.F), kBlock, s, a);
+    else if (derive == 2) launch_pdl(k_cc_sib<T, false, E, 2, B>, g, ALSUB_SIB_BLOCK, s, a);
+    else if (derive == 1) launch_pdl(k_cc_sib<T, false, E, 1, B>, g, ALSUB_SIB_BLOCK, s, a);
+    else launch_pdl(k_cc_sib<T, H, E, 0, B>, g, ALSUB_SIB_BLOCK, s, a);
 }
 template <bool T, bool H, bool E>
 void launch(const CCArgs &a, int derive, cudaStream_t s) {
@@ -742,9 +750,9 @@ void boundary_step(TopoImpl &T, int l, bool list, const float *P, float *Pn, cud
     LevelBuf *N = list ? &T.L[l + 1] : nullptr;
     // the edge point of edge e is |v| + |f| + e (Catmull-Clark) or |v| + e (Loop)
     const int first_edge_point = (int)(T.scheme == ALSUB_CATMULL_CLARK ? A.V + A.F : A.V);
-    k_cc_bnd<<<grid_for(A.B), kBlock, 0, s>>>((int)A.B, l == 0, A.bA, A.bE, A.bS, N ? N->bA : nullptr,
-                                             N ? N->bE : nullptr, N ? N->bS : nullptr, (int)A.V, (int)A.E,
-                                             first_edge_point, P, Pn, l > 0, l + 1 < T.levels, T.status);
+    launch_pdl(k_cc_bnd, grid_for(A.B), kBlock, s, (int)A.B, l == 0, (const int *)A.bA, (const int *)A.bE,
+               (const int *)A.bS, N ? N->bA : (int *)nullptr, N ? N->bE : (int *)nullptr, N ? N->bS : (int *)nullptr,
+               (int)A.V, (int)A.E, first_edge_point, P, Pn, l > 0, l + 1 < T.levels, T.status);
     T.launches += 1;
 }
 

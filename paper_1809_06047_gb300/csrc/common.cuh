@@ -307,4 +307,28 @@ inline unsigned grid_for(long long n, int block = kBlock) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+// Programmatic dependent launch. A kernel launched by launch_pdl may be scheduled while the kernel
+// before it in the stream is still draining (its blocks take the SMs that free up), so its start
+// is not a launch gap behind the previous kernel's last block. Such a kernel calls pdl_wait()
+// before its first memory access: it returns once the previous grid has completed and its
+// writes are visible (and at once when there is no such dependency). pdl_trigger() lets the next
+// kernel launch as soon as every block of this grid has started.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <class... KArgs, class... Args>
+inline void launch_pdl(void (*kernel)(KArgs...), unsigned grid, unsigned block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 }  // namespace alsub

@@ -179,6 +179,8 @@ __global__ void __launch_bounds__(kBlock) k_crease_analyse(Acc A, CreaseArgs a, 
 // Fix of one crease entry from its stored analysis: the crease edge point, and each end vertex the
 // entry designates (exactly one crease per crease vertex does).
 __global__ void __launch_bounds__(kBlock) k_crease_fix(CreaseArgs a, int cap) {
+    pdl_wait();
+    pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= cap) return;
     const int e = a.in.edge[i];
@@ -289,7 +291,7 @@ void crease_fix(TopoImpl &T, int l, const float *P, float *Pn, cudaStream_t s) {
     a.P = P;
     a.Pn = Pn;
     const int cap = (int)T.L[l].cr.cap;
-    k_crease_fix<<<grid_for(cap), kBlock, 0, s>>>(a, cap);
+    launch_pdl(k_crease_fix, grid_for(cap), kBlock, s, a, cap);
     T.launches += 1;
 }
 

@@ -15,6 +15,8 @@
 //    along its boundary loop (the input of the boundary repair step, Fig. module_boundary);
 //  * the level-0 crease list (C of Sec. 3.3) sorted by edge id.
 // Non-manifold input is reported through the handle's status word, never by trapping.
+#include <algorithm>
+
 #include "common.cuh"
 #include "internal.h"
 
@@ -60,28 +62,44 @@ __device__ int dir_find(const DirTable &t, int a, int b) {
     return -1;
 }
 
-// Corner maps, vertex degrees (M 1) and each vertex's smallest outgoing corner.
+// Start of a level-0 build: the status word, the vertex degrees and designated corners, and the
+// directed-edge table cleared in one pass.
+__global__ void k_clear0(int V, DirTable tab, int *status, int *deg, unsigned *vc) {
+    pdl_wait();
+    pdl_trigger();
+    const long long n = (long long)tab.mask + 1;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n || i < V; i += stride) {
+        if (i < n) tab.key[i] = kEmptyKey;
+        if (i < V) {
+            deg[i] = 0;
+            vc[i] = ~0u;
+        }
+        if (i == 0) *status = 0;
+    }
+}
+
+// Corner maps, vertex degrees (M 1), each vertex's smallest outgoing corner, and the directed
+// edge of every corner into the table.
 __global__ void k_faces(int F, const int *__restrict__ off, const int *__restrict__ fv, int *cf,
-                        int *nx, int *pv, int *deg, unsigned *vc) {
+                        int *nx, int *pv, int *deg, unsigned *vc, DirTable tab, int *status) {
+    pdl_wait();
+    pdl_trigger();
     int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= F) return;
     const int s = off[r], c = off[r + 1] - s;
+    int v = fv[s];
+    const int v0 = v;
     for (int j = 0; j < c; j++) {
-        const int x = s + j, v = fv[x];
+        const int x = s + j, w = j + 1 == c ? v0 : fv[x + 1];
         cf[x] = r;
         nx[x] = s + (j + 1 == c ? 0 : j + 1);
         pv[x] = s + (j == 0 ? c - 1 : j - 1);
         atomicAdd(deg + v, 1);
         atomicMin(vc + v, (unsigned)x);
+        if (!dir_insert(tab, v, w, x)) set_status(status, ALSUB_ERR_NONMANIFOLD);  // a duplicate
+        v = w;
     }
-}
-
-// The directed edge of every corner into the table, one corner per thread.
-__global__ void k_insert(int nnz, const int *__restrict__ fv, const int *__restrict__ nx, DirTable tab,
-                         int *status) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= nnz) return;
-    if (!dir_insert(tab, fv[x], fv[nx[x]], x)) set_status(status, ALSUB_ERR_NONMANIFOLD);  // duplicate
 }
 
 // Twin of a -> b: the corner of b -> a (none: an open edge, i.e. a boundary: twin -1 when the
@@ -91,6 +109,8 @@ __global__ void __launch_bounds__(kBlock) k_twin(int nnz, const int *__restrict_
                                                  DirTable tab, bool open, int *tw, int *own, int *bcount,
                                                  int *status) {
     __shared__ int wsum[kBlock / 32];
+    pdl_wait();
+    pdl_trigger();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     int o = 0;
     if (x < nnz) {
@@ -116,6 +136,8 @@ __global__ void __launch_bounds__(kBlock) k_twin(int nnz, const int *__restrict_
 __global__ void __launch_bounds__(kBlock) k_eid(int nnz, const int *__restrict__ own, const int *__restrict__ boff,
                                                 int *eid) {
     __shared__ int wpre[kBlock / 32];
+    pdl_wait();
+    pdl_trigger();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int o = x < nnz ? own[x] : 0;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -226,6 +248,8 @@ __global__ void k_edges(int nnz, const int *__restrict__ own, const int *__restr
                         const int *__restrict__ tw, const int *__restrict__ pv, const int *__restrict__ nx,
                         const int *__restrict__ off, const int *__restrict__ cf, const int *e0count, int E0,
                         int *ce, int *eo, int *rn, int *rec, int *status) {
+    pdl_wait();
+    pdl_trigger();
     int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x == 0 && *e0count != E0) set_status(status, ALSUB_ERR_NONMANIFOLD);
     if (x >= nnz) return;
@@ -274,20 +298,20 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     MeshImpl &M = *T.mesh;
     LevelBuf &L0 = T.L[0];
     const int V = M.V, F = M.F, nnz = M.nnz, E0 = (int)L0.E;
-    cudaMemsetAsync(T.status, 0, sizeof(int), s);
-    cudaMemsetAsync(T.deg, 0, sizeof(int) * (size_t)V, s);
-    cudaMemsetAsync(T.vc0, 0xff, sizeof(int) * (size_t)V, s);
-    cudaMemsetAsync(T.dir.key, 0xff, sizeof(unsigned long long) * ((size_t)T.dir.mask + 1), s);
-    k_faces<<<grid_for(F), kBlock, 0, s>>>(F, M.d_off, M.d_fv, T.cf0, T.nx0, T.pv0, T.deg,
-                                           reinterpret_cast<unsigned *>(T.vc0));
-    k_insert<<<grid_for(nnz), kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, T.status);
+    const long long slots = (long long)T.dir.mask + 1;
+    launch_pdl(k_clear0, std::min<unsigned>(grid_for(std::max<long long>(slots, V)), 1024u), kBlock, s, V, T.dir,
+               T.status, T.deg, reinterpret_cast<unsigned *>(T.vc0));
+    launch_pdl(k_faces, grid_for(F), kBlock, s, F, (const int *)M.d_off, (const int *)M.d_fv, T.cf0, T.nx0, T.pv0,
+               T.deg, reinterpret_cast<unsigned *>(T.vc0), T.dir, T.status);
     const unsigned nb = grid_for(nnz);
     const bool open = M.scheme != ALSUB_SQRT3;          // sqrt(3) has no boundary rule
-    k_twin<<<nb, kBlock, 0, s>>>(nnz, M.d_fv, T.nx0, T.dir, open, L0.tw, T.own0, T.flags, T.status);
+    launch_pdl(k_twin, nb, kBlock, s, nnz, (const int *)M.d_fv, (const int *)T.nx0, T.dir, open, L0.tw, T.own0,
+               T.flags, T.status);
     T.launches += 5 + scan_exclusive(T.flags, T.pos, nb, T.e0count, nullptr, T.scan_tmp, s);
-    k_eid<<<nb, kBlock, 0, s>>>(nnz, T.own0, T.pos, T.eid);
-    k_edges<<<grid_for(nnz), kBlock, 0, s>>>(nnz, T.own0, T.eid, L0.tw, T.pv0, T.nx0, M.d_off, T.cf0, T.e0count,
-                                             E0, L0.ce, T.eo0, T.rn0, T.rec0, T.status);
+    launch_pdl(k_eid, nb, kBlock, s, nnz, (const int *)T.own0, (const int *)T.pos, T.eid);
+    launch_pdl(k_edges, grid_for(nnz), kBlock, s, nnz, (const int *)T.own0, (const int *)T.eid, (const int *)L0.tw,
+               (const int *)T.pv0, (const int *)T.nx0, (const int *)M.d_off, (const int *)T.cf0,
+               (const int *)T.e0count, E0, L0.ce, T.eo0, T.rn0, T.rec0, T.status);
     if (L0.B > 0) {
         // (the list exists when a step follows: levels >= 1.) The per-corner edge-id temporaries
         // are dead: they map boundary corners to entries

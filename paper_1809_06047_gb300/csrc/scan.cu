@@ -53,6 +53,8 @@ __device__ __forceinline__ long long limit_of(long long n, const int *n_dev) {
 
 template <class T>
 __global__ void k_tile_sums(const int *__restrict__ in, long long n, const int *n_dev, T *sums) {
+    pdl_wait();
+    pdl_trigger();
     long long lim = limit_of(n, n_dev);
     long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kItems;
     T s = 0;
@@ -66,6 +68,8 @@ __global__ void k_tile_sums(const int *__restrict__ in, long long n, const int *
 // One CTA scans the tile sums in place (any count, looping over chunks).
 template <class T>
 __global__ void k_scan_sums(T *sums, int nt, T *total) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ T carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
@@ -85,6 +89,8 @@ __global__ void k_scan_sums(T *sums, int nt, T *total) {
 template <class T>
 __global__ void k_scan_tiles(const int *__restrict__ in, T *out, long long n, const int *n_dev,
                              const T *sums) {
+    pdl_wait();
+    pdl_trigger();
     long long lim = limit_of(n, n_dev);
     long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kItems;
     T v[kItems];
@@ -112,6 +118,8 @@ constexpr long long kBlockScanMax = 1 << 16;
 template <class T>
 __global__ void __launch_bounds__(kBlockScanThreads) k_scan_block(const int *__restrict__ in, T *out,
                                                                   long long n, const int *n_dev, T *total) {
+    pdl_wait();
+    pdl_trigger();
     __shared__ T wsum[kBlockScanThreads / 32 + 1];
     const long long lim = limit_of(n, n_dev);
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -150,14 +158,14 @@ int scan_impl(const int *in, T *out, long long n, T *total, const int *n_dev, vo
         return 0;
     }
     if (n <= kBlockScanMax) {
-        k_scan_block<T><<<1, kBlockScanThreads, 0, s>>>(in, out, n, n_dev, total);
+        launch_pdl(k_scan_block<T>, 1, kBlockScanThreads, s, in, out, n, n_dev, total);
         return 1;
     }
     int nt = (int)((n + kTile - 1) / kTile);
     T *sums = (T *)tmp;
-    k_tile_sums<T><<<nt, kScanThreads, 0, s>>>(in, n, n_dev, sums);
-    k_scan_sums<T><<<1, kScanThreads, 0, s>>>(sums, nt, total);
-    k_scan_tiles<T><<<nt, kScanThreads, 0, s>>>(in, out, n, n_dev, sums);
+    launch_pdl(k_tile_sums<T>, nt, kScanThreads, s, in, n, n_dev, sums);
+    launch_pdl(k_scan_sums<T>, 1, kScanThreads, s, sums, nt, total);
+    launch_pdl(k_scan_tiles<T>, nt, kScanThreads, s, in, out, n, n_dev, sums);
     return 3;
 }
 
