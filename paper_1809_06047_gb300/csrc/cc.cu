@@ -68,6 +68,7 @@ struct CCArgs {
     bool in4, out4;               // parent / child positions in padded float4 rows
     int *status;
     bool bnd;                     // the mesh is open (twins may be -1)
+    bool rev;                     // sibling kernel: blocks take the faces from the end backwards
 };
 
 // Child twins across the halves of a parent edge (corner 0 and corner 3 of the children), or -1
@@ -270,15 +271,18 @@ __device__ __forceinline__ void l2_prefetch(const void *p, unsigned bytes) {
 
 // Face rows [f0, f0 + n) of a level with 4-int rows, clipped to its F faces (16-byte granules).
 __device__ __forceinline__ void prefetch_rows(const int *rows, long long f0, long long n, long long F) {
-    if (f0 >= F) return;
+    if (f0 < 0 || f0 >= F) return;
     if (f0 + n > F) n = F - f0;
     l2_prefetch(rows + 4 * f0, (unsigned)(16 * n));
 }
 
+// blk: the block's place in the order the blocks take the faces; its rows are prefetched that
+// many blocks ahead in the same direction
 template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND, bool RINGS>
-__device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r) {
+__device__ __forceinline__ void cc_sib_body(const CCArgs &a, int r, int blk) {
     if (ALSUB_SIB_PREFETCH > 0 && threadIdx.x == 0) {
-        const long long f0 = ((long long)blockIdx.x + ALSUB_SIB_PREFETCH) * blockDim.x;
+        const long long f0 = a.rev ? ((long long)blk - ALSUB_SIB_PREFETCH) * blockDim.x
+                                   : ((long long)blk + ALSUB_SIB_PREFETCH) * blockDim.x;
         prefetch_rows(a.fv, f0, blockDim.x, a.F);
         if (DERIVE) {
             const int sh = 2 * DERIVE;        // ancestor rows: one per 4^DERIVE faces
@@ -518,7 +522,8 @@ template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND>
 __global__ void __launch_bounds__(ALSUB_SIB_BLOCK, ALSUB_SIB_MIN_BLOCKS) k_cc_sib(CCArgs a) {
     pdl_wait();
     pdl_trigger();
-    cc_sib_body<TOPO, HELP, EVAL, DERIVE, BND, false>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    const int blk = a.rev ? (int)(gridDim.x - 1 - blockIdx.x) : (int)blockIdx.x;
+    cc_sib_body<TOPO, HELP, EVAL, DERIVE, BND, false>(a, blk * blockDim.x + threadIdx.x, blk);
 }
 
 // Vertex point, on a level l >= 2, of a vertex born on level m <= 1 whose ring faces on level l are
@@ -655,9 +660,9 @@ __global__ void __launch_bounds__(512, 2) k_cc_batch(const CCArgs *__restrict__ 
         const CCArgs &a = items[i];          // read in place: a copy would not fit in registers
         if (KIND == 0) cc_l0_body<false, false, true, false>(a, r);
         else if (KIND == 1) cc_quad_body<false, false, true, false>(a, r);
-        else if (KIND == 2) cc_sib_body<false, false, true, 0, false, true>(a, r);
-        else if (KIND == 3) cc_sib_body<false, false, true, 1, false, true>(a, r);
-        else cc_sib_body<false, false, true, 2, false, true>(a, r);
+        else if (KIND == 2) cc_sib_body<false, false, true, 0, false, true>(a, r, blockIdx.x);
+        else if (KIND == 3) cc_sib_body<false, false, true, 1, false, true>(a, r, blockIdx.x);
+        else cc_sib_body<false, false, true, 2, false, true>(a, r, blockIdx.x);
     }
 }
 
@@ -692,6 +697,9 @@ CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, int *derive_out)
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
     a.bnd = T.mesh->B > 0;
+    // consecutive steps take their faces in opposite orders, the last step from the end: a step
+    // starts on the rows and positions its predecessor wrote last, which are still in L2
+    a.rev = ((T.levels - 1 - l) & 1) == 0;
     a.in4 = l > 0;                     // only the caller's input level is packed xyz
     a.out4 = l + 1 < T.levels;         // and the caller's output level
     // a level >= 2 without stored edge ids / twins derives them from its parent level, or (level
@@ -762,6 +770,7 @@ std::vector<BatchClass> cc_batch_plan(const std::vector<EvalItem> &items, int bl
     for (const EvalItem &it : items) {
         int derive = 0;
         CCArgs a = make_args(*it.T, it.l, it.P, it.Pn, &derive);
+        a.rev = false;                      // the batch kernel walks its own tile list
         const int kind = it.l == 0 ? 0 : (it.l == 1 ? 1 : 2 + derive);
         if (tiles[kind].empty()) tiles[kind].push_back(0);
         args[kind].push_back(a);
