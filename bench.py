@@ -234,7 +234,8 @@ def serving_leg(w, n_slots: int = 16, budget: float = 40e9, fastest: bool = Fals
                  register_s=register_s, hbm_peak_gb=st["hbm_peak"] / 1e9,
                  frames_operator=st["frames_operator"] - base["frames_operator"],
                  frames_eval=st["frames_eval"] - base["frames_eval"], meshes=st["meshes"] - base["meshes"],
-                 host_start_ms_mean=st["host_start_ms_mean"], host_finish_ms_mean=st["host_finish_ms_mean"])
+                 host_start_ms_mean=st["host_start_ms_mean"], host_finish_ms_mean=st["host_finish_ms_mean"],
+                 peak_in_flight=st["peak_in_flight"], device_overlap_peak=st["device_overlap_peak"])
         return d
 
     out_served = served("operator")
@@ -608,16 +609,21 @@ def traffic_for(kernel_key):
 
 
 def cpu_baseline(m, budget_levels):
-    """The oracle (serial FP64, as it stands) on a bounded sample of the same workload."""
+    """The oracle (serial FP64, as it stands) on a bounded sample of the same workload: one
+    warm-up run, then the median of three."""
     import oracle
     oracle.build()
-    t0 = time.perf_counter()
-    out = oracle.subdivide(m, budget_levels, m["scheme"], keep_all=False)
-    dt = time.perf_counter() - t0
+    oracle.subdivide(m, budget_levels, m["scheme"], keep_all=False)
+    times = []
+    for _ in range(3):
+        t0 = time.perf_counter()
+        out = oracle.subdivide(m, budget_levels, m["scheme"], keep_all=False)
+        times.append(time.perf_counter() - t0)
+    dt = statistics.median(times)
     F = out[-1]["F"]
     return {"value": F / dt, "unit": "refined faces/s", "cores": 1, "kind": "oracle",
-            "sample": f"{m['name']} refined to level {budget_levels} ({F} faces) once, "
-                      f"{dt:.1f} s on one host core"}
+            "sample": f"{m['name']} refined to level {budget_levels} ({F} faces): 1 warm-up, median of 3 "
+                      f"runs = {dt:.2f} s on one host core ({os.cpu_count()} on the host)"}
 
 
 def sample_levels(name):
@@ -653,6 +659,45 @@ def run_reference(args):
                          "sample": sample},
         "e2e": {"value": value, "unit": "refined faces/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0}}))
+
+
+def summary_of(out):
+    """The headline and every leg's main numbers, rounded, in a few hundred characters (the end
+    of the JSON line, so that a reader of its tail sees all of them)."""
+    def r(x, n=4):
+        return None if x is None else float(f"{x:.{n}g}")
+
+    def get(d, *path):
+        for k in path:
+            if not isinstance(d, dict) or k not in d:
+                return None
+            d = d[k]
+        return d
+    s = {"ms_per_step": r(out["ms_per_step"]), "frac_last": r(out["roofline"]["frac"]),
+         "frac_step": r(out["pipeline"]["frac"]),
+         "stage_ms": [r(x, 3) for x in out["pipeline"]["stage_ms"]],
+         "stage_frac": [r(x, 3) for x in out["pipeline"].get("stage_frac", [])],
+         "e2e_ms": r(out["e2e"]["ms_per_step"])}
+    legs = {
+        "operator": [("apply_ms", "apply_ms"), ("eval_ms", "eval_kernels_ms"), ("frac", "roofline", "frac")],
+        "adjoint": [("fwd_bwd_ms", "forward_backward_ms"), ("bwd_ms", "backward_ms"), ("frac", "roofline", "frac")],
+        "batch": [("batch_ms", "batch_ms"), ("alone_ms", "one_at_a_time_ms")],
+        "boundary": [("ms", "ms_per_step"), ("frac", "roofline", "frac"), ("loop_ms", "loop", "ms_per_step")],
+        "ordering": [("ordered_ms", "ordered", "ms_per_step"), ("shuffled_ms", "shuffled", "ms_per_step"),
+                     ("rcm_ms", "rcm", "ms_per_step"), ("reorder_ms", "reorder_ms")],
+        "adaptive": [("ms", "adaptive_ms_per_pass"), ("uniform_ms", "uniform_ms")],
+        "patches": [("ms", "eval_ms"), ("frac", "roofline", "frac")],
+        "serving": [("p50", "served", "p50_ms"), ("p99", "served", "p99_ms"), ("rps", "served", "throughput_rps"),
+                    ("overlap", "served", "device_overlap_peak"), ("host_start", "served", "host_start_ms_mean"),
+                    ("plain_p50", "plain", "p50_ms"), ("plain_p99", "plain", "p99_ms"),
+                    ("plain_rps", "plain", "throughput_rps")],
+    }
+    for leg, fields in legs.items():
+        if leg in out:
+            s[leg] = {name: r(get(out[leg], *path)) for name, *path in fields}
+            if "error" in out[leg]:
+                s[leg] = {"error": str(out[leg]["error"])[:80]}
+    return s
 
 
 def main():
@@ -783,7 +828,10 @@ def main():
                      "frac": pipe_bytes / (ms_step / 1e3) / 1e9 / peak,
                      "alg_bytes_with_ids_per_step": pipe_ids,
                      "equivalent_frac_with_ids": pipe_ids / (ms_step / 1e3) / 1e9 / peak,
-                     "stage_ms": [s / max(calls, 1) for s in stage_ms]},
+                     "stage_ms": [s / max(calls, 1) for s in stage_ms],
+                     # per step l -> l + 1 (entry 1 + l of stage_ms; entry 0 is the level-0 build)
+                     "stage_frac": [None] + [level_alg_bytes(counts, l) / (stage_ms[1 + l] / max(calls, 1) / 1e3)
+                                             / 1e9 / peak if stage_ms[1 + l] > 0 else None for l in range(L)]},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "clocks": clk,
@@ -812,6 +860,7 @@ def main():
         except Exception as e:  # noqa: BLE001 -- the headline line must still print
             out["serving"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
+        out["summary"] = summary_of(out)          # last: the compact numbers of every leg
         print(json.dumps(out, default=lambda o: o.item() if hasattr(o, "item") else str(o)))
     if dist is not None:
         dist.destroy_process_group()
