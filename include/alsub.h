@@ -140,6 +140,37 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t num_verts, int32_t n
                                const float *crease_sharpness_host, void *stream,
                                alsub_mesh_t *out);
 
+/*
+ * Device memory supplied by the caller (the boundary's allocator callback: a caller that manages
+ * device memory itself, e.g. through PyTorch's caching allocator or a fixed arena, keeps every
+ * array of the library inside it). alloc returns `bytes` of device memory usable in stream order
+ * on `stream` (16-byte aligned; a misaligned block is handed back and the call fails with OOM),
+ * or NULL when it has none (the library call then fails with OOM); free takes back a block once
+ * the work that the library enqueued on `stream` before the call no longer needs it (stream
+ * ordered, like cudaFreeAsync). ctx is passed through. Both callbacks must be thread-safe if the
+ * caller uses the library from several threads, and must not call back into the library.
+ */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx, void *stream);
+    void (*free)(void *ptr, void *ctx, void *stream);
+    void *ctx;
+} alsub_allocator;
+
+/*
+ * alsub_mesh_create with the caller's allocator (NULL: CUDA's stream-ordered allocator, as
+ * alsub_mesh_create). The mesh and every handle made from it (topologies and their host-buffer
+ * staging, operators, hierarchical edits, extracted and reordered meshes, which inherit the
+ * allocator) take all of their device memory, temporaries included, from `allocator`; the
+ * allocator struct is copied, and its callbacks and ctx must stay valid until the last of those
+ * handles is destroyed. Batches and servers keep using their own allocations. Errors: those of
+ * alsub_mesh_create, INVALID_ARG when alloc or free is NULL.
+ */
+alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t num_verts, int32_t num_faces,
+                                  const int32_t *face_offsets_host, const int32_t *face_verts_host,
+                                  int32_t num_creases, const int32_t *crease_verts_host,
+                                  const float *crease_sharpness_host, const alsub_allocator *allocator,
+                                  void *stream, alsub_mesh_t *out);
+
 alsub_status alsub_mesh_destroy(alsub_mesh_t mesh);
 
 /* Number of boundary edges (edges of one face) of a mesh; 0 for a closed mesh and for sqrt(3)

@@ -13,6 +13,15 @@ H = c_void_p  # opaque handles and raw pointers
 
 
 
+ALLOC_FN = ctypes.CFUNCTYPE(c_void_p, c_size_t, c_void_p, c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, c_void_p, c_void_p, c_void_p)
+
+
+class Allocator(ctypes.Structure):
+    """alsub_allocator."""
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", c_void_p)]
+
+
 class Request(ctypes.Structure):
     """alsub_request."""
     _fields_ = [("kind", c_int32), ("resident", c_int32), ("scheme", c_int32), ("levels", c_int32),
@@ -59,6 +68,8 @@ SIGNATURES = {
     "alsub_mesh_gather": [c_void_p, c_void_p, c_void_p, c_void_p],
     "alsub_mesh_create": [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
                           c_void_p, P(H)],
+    "alsub_mesh_create_ex": [c_int32, c_int32, c_int32, c_void_p, c_void_p, c_int32, c_void_p, c_void_p,
+                             P(Allocator), c_void_p, P(H)],
     "alsub_mesh_destroy": [H],
     "alsub_topology_create": [H, c_int32, c_void_p, P(H)],
     "alsub_refine_topology": [H, c_int32, c_void_p, P(H)],

@@ -70,11 +70,38 @@ def copy_to_host(ptr: int, nbytes: int, dtype, count: int, stream=None) -> np.nd
     return out
 
 
+class DeviceAllocator:
+    """An alsub_allocator backed by PyTorch's caching allocator (blocks come from and go back to
+    torch's pool on the stream the library names). Keeps count of the blocks it holds; it must
+    outlive every handle made with it (the handles keep a reference)."""
+
+    def __init__(self, fail: bool = False):
+        self.live, self.allocs, self.frees, self.bytes_live, self.fail = {}, 0, 0, 0, fail
+
+        def _alloc(nbytes, ctx, stream):
+            if self.fail:
+                return None
+            s = torch.cuda.ExternalStream(stream) if stream else torch.cuda.default_stream()
+            p = torch.cuda.caching_allocator_alloc(int(nbytes), stream=s)
+            self.live[p] = int(nbytes)
+            self.allocs += 1
+            self.bytes_live += int(nbytes)
+            return p
+
+        def _free(ptr, ctx, stream):
+            self.bytes_live -= self.live.pop(ptr)
+            self.frees += 1
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_fn, self._free_fn = _lib.ALLOC_FN(_alloc), _lib.FREE_FN(_free)
+        self.struct = _lib.Allocator(self._alloc_fn, self._free_fn, None)
+
+
 class Mesh:
-    """alsub_mesh_create / alsub_mesh_destroy."""
+    """alsub_mesh_create / alsub_mesh_create_ex / alsub_mesh_destroy."""
 
     def __init__(self, scheme: str, V: int, F: int, fv, off=None, crease_verts=None,
-                 crease_sharp=None, stream=None):
+                 crease_sharp=None, stream=None, allocator: DeviceAllocator | None = None):
         self.scheme = scheme
         fv = np.ascontiguousarray(fv, dtype=np.int32)
         off = None if off is None else np.ascontiguousarray(off, dtype=np.int32)
@@ -84,19 +111,22 @@ class Mesh:
                                   dtype=np.float32).reshape(-1)
         self.V, self.F, self.nnz = int(V), int(F), int(fv.size)
         self._h = ctypes.c_void_p()
-        _check(lib().alsub_mesh_create(SCHEMES[scheme], self.V, self.F, _ptr(off), _ptr(fv),
-                                       int(cs.size), _ptr(cv) if cs.size else None,
-                                       _ptr(cs) if cs.size else None,
-                                       ctypes.c_void_p(_stream(stream)), ctypes.byref(self._h)))
+        self._allocator = allocator
+        _check(lib().alsub_mesh_create_ex(SCHEMES[scheme], self.V, self.F, _ptr(off), _ptr(fv),
+                                          int(cs.size), _ptr(cv) if cs.size else None,
+                                          _ptr(cs) if cs.size else None,
+                                          ctypes.byref(allocator.struct) if allocator else None,
+                                          ctypes.c_void_p(_stream(stream)), ctypes.byref(self._h)))
         b = ctypes.c_int64()
         _check(lib().alsub_mesh_boundary_edges(self._h, ctypes.byref(b)))
         self.boundary_edges = int(b.value)
 
     @classmethod
-    def _wrap(cls, h: ctypes.c_void_p) -> "Mesh":
+    def _wrap(cls, h: ctypes.c_void_p, allocator=None) -> "Mesh":
         """A Mesh object around a handle the library made (an extracted or reordered mesh)."""
         self = cls.__new__(cls)
         self._h = h
+        self._allocator = allocator
         sch, V, F, nnz, K = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(lib().alsub_mesh_info(h, ctypes.byref(sch), ctypes.byref(V), ctypes.byref(F), ctypes.byref(nnz),
                                      ctypes.byref(K)))
@@ -113,7 +143,7 @@ class Mesh:
         one. The breadth-first levels it took are in `.rcm_levels`."""
         h, lv = ctypes.c_void_p(), ctypes.c_int32()
         _check(lib().alsub_mesh_reorder(self._h, ctypes.c_void_p(_stream(stream)), ctypes.byref(h), ctypes.byref(lv)))
-        out = Mesh._wrap(h)
+        out = Mesh._wrap(h, self._allocator)
         out.rcm_levels = int(lv.value)
         return out
 
@@ -148,9 +178,9 @@ class Mesh:
         return out
 
     @classmethod
-    def from_dict(cls, m: dict, scheme: str | None = None, stream=None) -> "Mesh":
+    def from_dict(cls, m: dict, scheme: str | None = None, stream=None, allocator=None) -> "Mesh":
         return cls(scheme or m.get("scheme", "cc"), m["V"], m["F"], m["fv"], m["off"],
-                   m.get("crease_verts"), m.get("crease_sharp"), stream)
+                   m.get("crease_verts"), m.get("crease_sharp"), stream, allocator)
 
     @property
     def handle(self):
@@ -292,7 +322,7 @@ class Topology:
             assert select.is_cuda and select.dtype == torch.uint8 and select.numel() == self.counts[level]["V"]
         _check(lib().alsub_topology_extract(self._h, int(level), sel, int(rings), ctypes.c_void_p(_stream(stream)),
                                             ctypes.byref(h)))
-        return Mesh._wrap(h)
+        return Mesh._wrap(h, getattr(self.mesh, "_allocator", None))
 
     def regular_faces(self, level: int = 0, stream=None) -> torch.Tensor:
         """alsub_topology_regular_faces: uint8 device mask of the level's regular (bicubic) faces."""

@@ -80,7 +80,7 @@ alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
         return ALSUB_OK;
     }
     void *q = nullptr;
-    cudaError_t e = cudaMallocAsync(&q, n * sizeof(T), s);
+    cudaError_t e = dev_malloc(T_.mesh->alloc, &q, n * sizeof(T), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ALSUB_ERR_OOM, "device allocation of %zu bytes failed", n * sizeof(T));
@@ -97,7 +97,7 @@ alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
     } while (0)
 
 void free_topo(TopoImpl &T) {
-    for (void *p : T.allocs) cudaFreeAsync(p, T.stream);
+    for (void *p : T.allocs) dev_free(T.mesh->alloc, p, T.stream);
     T.allocs.clear();
     T.bytes = 0;
     T.arena = nullptr;
@@ -138,7 +138,8 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     alsub_status st = topo_layout(D, M, levels, s);
     if (st != ALSUB_OK) return st;
     void *q = nullptr;
-    if (cudaMallocAsync(&q, D.bytes, s) != cudaSuccess) {
+    T.mesh = &M;
+    if (dev_malloc(M.alloc, &q, D.bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return fail(ALSUB_ERR_OOM, "device allocation of %zu bytes failed", D.bytes);
     }
@@ -437,12 +438,12 @@ void free_hostio(TopoImpl &T) {
     if (io.cs) cudaStreamSynchronize(io.cs);
     if (io.ds) cudaStreamSynchronize(io.ds);
     for (int b = 0; b < 2; b++) {
-        if (io.dPL[b]) cudaFree(io.dPL[b]);
+        if (io.dPL[b]) dev_free(T.mesh->alloc, io.dPL[b], T.stream);
         if (io.hP0[b]) cudaFreeHost(io.hP0[b]);
         for (cudaEvent_t e : {io.up[b], io.done[b], io.copied[b]})
             if (e) cudaEventDestroy(e);
     }
-    if (io.dP0) cudaFree(io.dP0);
+    if (io.dP0) dev_free(T.mesh->alloc, io.dP0, T.stream);
     if (io.cs) cudaStreamDestroy(io.cs);
     if (io.ds) cudaStreamDestroy(io.ds);
     io = TopoImpl::HostIO();
@@ -456,9 +457,10 @@ alsub_status ensure_hostio(TopoImpl &T) {
     const size_t n0 = 12 * (size_t)T.L[0].V, nl = 12 * (size_t)T.L[T.levels].V;
     bool ok = cudaStreamCreateWithFlags(&io.cs, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&io.ds, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaMalloc(&io.dP0, n0) == cudaSuccess;
+              dev_malloc(T.mesh->alloc, &io.dP0, n0, io.cs) == cudaSuccess;
     for (int b = 0; ok && b < 2; b++)
-        ok = cudaMalloc(&io.dPL[b], nl) == cudaSuccess && cudaMallocHost(&io.hP0[b], n0) == cudaSuccess &&
+        ok = dev_malloc(T.mesh->alloc, &io.dPL[b], nl, io.cs) == cudaSuccess &&
+             cudaMallocHost(&io.hP0[b], n0) == cudaSuccess &&
              cudaEventCreateWithFlags(&io.up[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&io.done[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&io.copied[b], cudaEventDisableTiming) == cudaSuccess;
@@ -565,6 +567,33 @@ void alsub::apply_edits(TopoImpl &T, int k, float *out, cudaStream_t s) {
 
 alsub_status alsub::report(alsub_status s, const char *msg) { return fail(s, "%s", msg); }
 
+cudaError_t alsub::dev_malloc(const DevAlloc &A, void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 1;
+    if (A.alloc) {
+        *p = A.alloc(bytes, A.ctx, (void *)s);
+        // the arrays carved from an allocation need 16-byte alignment (vector and bulk accesses)
+        if (*p && (reinterpret_cast<uintptr_t>(*p) & 15)) {
+            A.free(*p, A.ctx, (void *)s);
+            *p = nullptr;
+        }
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    const cudaError_t e = cudaMallocAsync(p, bytes, s);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaSuccess;
+}
+
+void alsub::dev_free(const DevAlloc &A, void *p, cudaStream_t s) {
+    if (!p) return;
+    if (A.free) A.free(p, A.ctx, (void *)s);
+    else cudaFreeAsync(p, s);
+}
+
 alsub_status alsub::refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s) {
     if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
     refine_body(T, P0, PL, scratch, s);
@@ -652,7 +681,16 @@ alsub_status alsub_plan_open(alsub_scheme scheme, int64_t V, int64_t F, int64_t 
 alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const int32_t *off_h,
                                const int32_t *fv_h, int32_t K, const int32_t *cv_h,
                                const float *cs_h, void *stream, alsub_mesh_t *out) {
+    return alsub_mesh_create_ex(scheme, V, F, off_h, fv_h, K, cv_h, cs_h, nullptr, stream, out);
+}
+
+alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t V, int32_t F, const int32_t *off_h,
+                                  const int32_t *fv_h, int32_t K, const int32_t *cv_h, const float *cs_h,
+                                  const alsub_allocator *allocator, void *stream, alsub_mesh_t *out) {
     if (!out) return fail(ALSUB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (allocator && (!allocator->alloc || !allocator->free))
+        return fail(ALSUB_ERR_INVALID_ARG, "allocator: both alloc and free are needed");
     *out = nullptr;
     if (scheme < ALSUB_CATMULL_CLARK || scheme > ALSUB_SQRT3) return fail(ALSUB_ERR_INVALID_ARG, "bad scheme");
     if (V <= 0 || F <= 0 || !fv_h || K < 0 || (K > 0 && (!cv_h || !cs_h)))
@@ -703,21 +741,27 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
     alsub_mesh_s *h = new (std::nothrow) alsub_mesh_s();
     if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
     MeshImpl &M = h->m;
+    if (allocator) {
+        M.alloc.alloc = allocator->alloc;
+        M.alloc.free = allocator->free;
+        M.alloc.ctx = allocator->ctx;
+    }
     M.scheme = scheme; M.V = V; M.F = F; M.nnz = (int)nnz; M.K = scheme == ALSUB_SQRT3 ? 0 : (int)cs.size();
     M.sigma_max = smax;
     M.stream = (cudaStream_t)stream;
     cudaStream_t s = M.stream;
     upload_weight_tables();
     auto cleanup = [&]() {
-        cudaFreeAsync(M.d_off, s); cudaFreeAsync(M.d_fv, s);
-        if (M.d_cv) cudaFreeAsync(M.d_cv, s);
-        if (M.d_cs) cudaFreeAsync(M.d_cs, s);
+        if (M.d_off) dev_free(M.alloc, M.d_off, s);
+        if (M.d_fv) dev_free(M.alloc, M.d_fv, s);
+        if (M.d_cv) dev_free(M.alloc, M.d_cv, s);
+        if (M.d_cs) dev_free(M.alloc, M.d_cs, s);
         delete h;
     };
-    cudaError_t e = cudaMallocAsync(&M.d_off, sizeof(int) * (F + 1), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&M.d_fv, sizeof(int) * nnz, s);
-    if (e == cudaSuccess && M.K) e = cudaMallocAsync(&M.d_cv, sizeof(int) * 2 * M.K, s);
-    if (e == cudaSuccess && M.K) e = cudaMallocAsync(&M.d_cs, sizeof(float) * M.K, s);
+    cudaError_t e = dev_malloc(M.alloc, &M.d_off, sizeof(int) * (F + 1), s);
+    if (e == cudaSuccess) e = dev_malloc(M.alloc, &M.d_fv, sizeof(int) * nnz, s);
+    if (e == cudaSuccess && M.K) e = dev_malloc(M.alloc, &M.d_cv, sizeof(int) * 2 * M.K, s);
+    if (e == cudaSuccess && M.K) e = dev_malloc(M.alloc, &M.d_cs, sizeof(float) * M.K, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_off, off.data(), sizeof(int) * (F + 1), cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_fv, fv_h, sizeof(int) * nnz, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cv, cv.data(), sizeof(int) * 2 * M.K, cudaMemcpyHostToDevice, s);
@@ -729,6 +773,7 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
         cudaStreamSynchronize(s);
         cudaGetLastError();
         cleanup();
+        if (e == cudaErrorMemoryAllocation) return fail(ALSUB_ERR_OOM, "mesh upload: out of device memory");
         return cuda_fail(e, "mesh upload");
     }
     if (scheme != ALSUB_SQRT3) {
@@ -842,12 +887,9 @@ alsub_status alsub_mesh_boundary_edges(alsub_mesh_t h, int64_t *boundary_edges) 
 alsub_status alsub_mesh_destroy(alsub_mesh_t h) {
     if (!h) return ALSUB_OK;
     MeshImpl &M = h->m;
-    if (M.d_off) cudaFreeAsync(M.d_off, M.stream);
-    if (M.d_fv) cudaFreeAsync(M.d_fv, M.stream);
-    if (M.d_cv) cudaFreeAsync(M.d_cv, M.stream);
-    if (M.d_cs) cudaFreeAsync(M.d_cs, M.stream);
-    if (M.d_vmap) cudaFreeAsync(M.d_vmap, M.stream);
-    if (M.d_fmap) cudaFreeAsync(M.d_fmap, M.stream);
+    for (void *p : {(void *)M.d_off, (void *)M.d_fv, (void *)M.d_cv, (void *)M.d_cs, (void *)M.d_vmap,
+                    (void *)M.d_fmap})
+        if (p) dev_free(M.alloc, p, M.stream);
     delete h;
     return finish("alsub_mesh_destroy");
 }
@@ -985,13 +1027,13 @@ alsub_status alsub_topology_set_edits(alsub_topology_t h, int32_t level, int32_t
     TopoImpl::LevelEdits &e = T.edits[level];
     CK(cudaStreamSynchronize(T.stream));          // calls in flight may still read the old edits
     CK(cudaStreamSynchronize(s));
-    if (e.vid) cudaFreeAsync(e.vid, s);
-    if (e.off) cudaFreeAsync(e.off, s);
+    if (e.vid) dev_free(T.mesh->alloc, e.vid, s);
+    if (e.off) dev_free(T.mesh->alloc, e.off, s);
     e = TopoImpl::LevelEdits();
     drop_graphs(T);                               // captured calls hold the old edit launches
     if (n == 0) return finish("alsub_topology_set_edits");
-    CK(cudaMallocAsync(&e.vid, sizeof(int) * (size_t)n, s));
-    CK(cudaMallocAsync(&e.off, sizeof(float) * 3 * (size_t)n, s));
+    CK(dev_malloc(T.mesh->alloc, &e.vid, sizeof(int) * (size_t)n, s));
+    CK(dev_malloc(T.mesh->alloc, &e.off, sizeof(float) * 3 * (size_t)n, s));
     CK(cudaMemcpyAsync(e.vid, vid_dev, sizeof(int) * (size_t)n, cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(e.off, off_dev, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, s));
     e.n = n;
@@ -1001,8 +1043,8 @@ alsub_status alsub_topology_set_edits(alsub_topology_t h, int32_t level, int32_t
 alsub_status alsub_topology_destroy(alsub_topology_t h) {
     if (!h) return ALSUB_OK;
     for (TopoImpl::LevelEdits &e : h->t.edits) {
-        if (e.vid) cudaFreeAsync(e.vid, h->t.stream);
-        if (e.off) cudaFreeAsync(e.off, h->t.stream);
+        if (e.vid) dev_free(h->t.mesh->alloc, e.vid, h->t.stream);
+        if (e.off) dev_free(h->t.mesh->alloc, e.off, h->t.stream);
     }
     free_hostio(h->t);
     free_events(h->t);

@@ -230,8 +230,9 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
     const size_t stmp = scan_tmp_bytes(nmax);
     const size_t ints = 5 * nV + 4 * nF + 2 * nC + 8 + (tri ? nF + 1 : 0);
     char *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, 4 * ints + stmp + 256, s) != cudaSuccess) {
-        cudaGetLastError();
+    const DevAlloc &DA = T.mesh->alloc;       // the extracted mesh takes the source mesh's allocator
+    out.alloc = DA;
+    if (dev_malloc(DA, &buf, 4 * ints + stmp + 256, s) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "extraction: device allocation failed");
     }
     int *deg = (int *)buf, *x = deg + nV, *bnd = x + nV, *cnt = bnd + nV, *vpos = cnt + nV;
@@ -250,9 +251,9 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
     if (mask) {
         k_x_select_mask<<<grid_for(V), kBlock, 0, s>>>(V, mask, x);
     } else {
-        alsub_status st = level_boundary_flags(V, F, L.nnz, off, fv, bnd, s);
+        alsub_status st = level_boundary_flags(V, F, L.nnz, off, fv, bnd, DA, s);
         if (st != ALSUB_OK) {
-            cudaFreeAsync(buf, s);
+            dev_free(DA, buf, s);
             return st;
         }
         k_x_select<<<grid_for(V), kBlock, 0, s>>>(V, deg, bnd, T.scheme == ALSUB_CATMULL_CLARK ? 4 : 6, x);
@@ -271,9 +272,8 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
         while ((1LL << k) < 2 * L.nnz) k++;
         const size_t slots = (size_t)1 << k;
         unsigned long long *key = nullptr;
-        if (cudaMallocAsync((void **)&key, slots * sizeof(unsigned long long), s) != cudaSuccess) {
-            cudaGetLastError();
-            cudaFreeAsync(buf, s);
+        if (dev_malloc(DA, &key, slots * sizeof(unsigned long long), s) != cudaSuccess) {
+            dev_free(DA, buf, s);
             return report(ALSUB_ERR_OOM, "extraction: device allocation failed");
         }
         bool clean = false;
@@ -289,16 +289,16 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
             if (e == cudaSuccess) e = cudaStreamSynchronize(s);
             if (e != cudaSuccess) {
                 cudaGetLastError();
-                cudaFreeAsync(key, s);
-                cudaFreeAsync(buf, s);
+                dev_free(DA, key, s);
+                dev_free(DA, buf, s);
                 return report(ALSUB_ERR_DEVICE, "extraction failed");
             }
             clean = pinches == 0;
             if (!clean) k_x_faces_or<<<grid_for(F), kBlock, 0, s>>>(F, off, fv, x, q);
         }
-        cudaFreeAsync(key, s);
+        dev_free(DA, key, s);
         if (!clean) {
-            cudaFreeAsync(buf, s);
+            dev_free(DA, buf, s);
             return report(ALSUB_ERR_UNSUPPORTED, "extraction: the region still touches itself after 64 rounds");
         }
     }
@@ -317,7 +317,7 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
     cudaError_t e = cudaMemcpyAsync(h, tot, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
-        cudaFreeAsync(buf, s);
+        dev_free(DA, buf, s);
         cudaGetLastError();
         return report(ALSUB_ERR_DEVICE, "extraction failed");
     }
@@ -327,25 +327,25 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
     out.sigma_max = T.mesh->sigma_max;
     out.stream = s;
     if (Fo == 0) {                            // nothing selected: an empty mesh is not a mesh
-        cudaFreeAsync(buf, s);
+        dev_free(DA, buf, s);
         return report(ALSUB_ERR_INVALID_ARG, "extraction selected no face");
     }
-    e = cudaMallocAsync(&out.d_off, sizeof(int) * (Fo + 1), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out.d_fv, sizeof(int) * (size_t)nnzo, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out.d_vmap, sizeof(int) * (size_t)Vo, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out.d_fmap, sizeof(int) * (size_t)Fo, s);
-    if (e == cudaSuccess && Ko) e = cudaMallocAsync(&out.d_cv, sizeof(int) * 2 * (size_t)Ko, s);
-    if (e == cudaSuccess && Ko) e = cudaMallocAsync(&out.d_cs, sizeof(float) * (size_t)Ko, s);
+    e = dev_malloc(DA, &out.d_off, sizeof(int) * (Fo + 1), s);
+    if (e == cudaSuccess) e = dev_malloc(DA, &out.d_fv, sizeof(int) * (size_t)nnzo, s);
+    if (e == cudaSuccess) e = dev_malloc(DA, &out.d_vmap, sizeof(int) * (size_t)Vo, s);
+    if (e == cudaSuccess) e = dev_malloc(DA, &out.d_fmap, sizeof(int) * (size_t)Fo, s);
+    if (e == cudaSuccess && Ko) e = dev_malloc(DA, &out.d_cv, sizeof(int) * 2 * (size_t)Ko, s);
+    if (e == cudaSuccess && Ko) e = dev_malloc(DA, &out.d_cs, sizeof(float) * (size_t)Ko, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFreeAsync(buf, s);
+        dev_free(DA, buf, s);
         return report(ALSUB_ERR_OOM, "extraction: device allocation failed");
     }
     k_x_fill_faces<<<grid_for(F), kBlock, 0, s>>>(F, off, fv, q, fpos, noff, vpos, out.d_off, out.d_fv, out.d_fmap);
     cudaMemcpyAsync(out.d_off + Fo, tot + 1, sizeof(int), cudaMemcpyDeviceToDevice, s);
     k_x_fill_verts<<<grid_for(V), kBlock, 0, s>>>(V, x, vpos, out.d_vmap);
     if (Ko) k_x_fill_creases<<<grid_for(cap), kBlock, 0, s>>>(cap, flag, cpos, C.xverts, C.xsig, vpos, out.d_cv, out.d_cs);
-    cudaFreeAsync(buf, s);
+    dev_free(DA, buf, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return report(ALSUB_ERR_DEVICE, cudaGetErrorString(e));
     return ALSUB_OK;

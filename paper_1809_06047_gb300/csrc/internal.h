@@ -51,6 +51,22 @@ struct LevelBuf {
     int *bA = nullptr, *bE = nullptr, *bS = nullptr;
 };
 
+// Where the device memory of a mesh, and of every handle made from it, comes from: the caller's
+// allocator (alsub_mesh_create_ex) or, when `alloc` is null, CUDA's stream-ordered allocator.
+struct DevAlloc {
+    void *(*alloc)(size_t bytes, void *ctx, void *stream) = nullptr;
+    void (*free)(void *ptr, void *ctx, void *stream) = nullptr;
+    void *ctx = nullptr;
+};
+// Stream-ordered allocation of `bytes` on `s` (cudaSuccess, or cudaErrorMemoryAllocation with *p
+// null; no CUDA error is left pending) and its release after the work enqueued on `s`.
+cudaError_t dev_malloc(const DevAlloc &A, void **p, size_t bytes, cudaStream_t s);
+void dev_free(const DevAlloc &A, void *p, cudaStream_t s);
+template <class T>
+cudaError_t dev_malloc(const DevAlloc &A, T **p, size_t bytes, cudaStream_t s) {
+    return dev_malloc(A, reinterpret_cast<void **>(p), bytes, s);
+}
+
 struct MeshImpl {
     alsub_scheme scheme;
     int V = 0, F = 0, nnz = 0, K = 0;
@@ -63,6 +79,7 @@ struct MeshImpl {
     int *d_vmap = nullptr;     // extracted meshes (selective subdivision): kept vertex -> source vertex
     int *d_fmap = nullptr;     //                                           kept face -> source face
     cudaStream_t stream = nullptr;
+    DevAlloc alloc;            // every device array of the mesh and of its handles
 };
 
 // A captured refine call: replayed while its pointers (and timing mode) stay the same.
@@ -176,7 +193,7 @@ void level0_creases(TopoImpl &T, cudaStream_t s);
 alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary);
 // Vertices on a boundary edge (flag 1) of a face table (off == nullptr: uniform quads).
 alsub_status level_boundary_flags(int V, int F, long long nnz, const int *off, const int *fv, int *flag,
-                                  cudaStream_t s);
+                                  const DevAlloc &A, cudaStream_t s);
 // Extraction of selective subdivision (Sec. 3.4) from level `level` of a built topology into a new
 // mesh (device arrays, maps, creases; B not yet set); synchronises `s`.
 alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, int rings, cudaStream_t s,

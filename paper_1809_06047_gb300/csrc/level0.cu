@@ -324,13 +324,12 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
 }
 
 alsub_status level_boundary_flags(int V, int F, long long n, const int *off, const int *fv, int *flag,
-                                  cudaStream_t s) {
+                                  const DevAlloc &A, cudaStream_t s) {
     int k = 4;
     while ((1LL << k) < 2 * n) k++;
     const size_t slots = (size_t)1 << k;
     char *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, slots * (sizeof(unsigned long long) + sizeof(int)) + 16, s) != cudaSuccess) {
-        cudaGetLastError();
+    if (dev_malloc(A, &buf, slots * (sizeof(unsigned long long) + sizeof(int)) + 16, s) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "boundary flags: device allocation failed");
     }
     DirTable tab;
@@ -343,7 +342,7 @@ alsub_status level_boundary_flags(int V, int F, long long n, const int *off, con
     cudaMemsetAsync(flag, 0, sizeof(int) * (size_t)V, s);
     k_mb_insert<<<grid_for(F), kBlock, 0, s>>>(F, off, fv, tab);
     k_mb_count<<<grid_for(F), kBlock, 0, s>>>(F, off, fv, tab, flag, count);
-    cudaFreeAsync(buf, s);
+    dev_free(A, buf, s);
     return ALSUB_OK;
 }
 
@@ -355,8 +354,7 @@ alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool 
     const size_t slots = (size_t)1 << k;
     char *buf = nullptr;
     const size_t bytes = slots * (sizeof(unsigned long long) + sizeof(int)) + sizeof(int) * ((size_t)M.V + 2);
-    if (cudaMallocAsync((void **)&buf, bytes, s) != cudaSuccess) {
-        cudaGetLastError();
+    if (dev_malloc(M.alloc, &buf, bytes, s) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "mesh boundary scan: device allocation failed");
     }
     DirTable tab;
@@ -372,7 +370,7 @@ alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool 
     int h[2] = {0, 0};
     cudaError_t e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    cudaFreeAsync(buf, s);
+    dev_free(M.alloc, buf, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return report(ALSUB_ERR_DEVICE, "mesh boundary scan failed");

@@ -425,8 +425,7 @@ alsub_status oalloc(alsub_operator_s &O, T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
     void *q = nullptr;
-    if (cudaMallocAsync(&q, n * sizeof(T), O.stream) != cudaSuccess) {
-        cudaGetLastError();
+    if (dev_malloc(O.T->mesh->alloc, &q, n * sizeof(T), O.stream) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "operator: device allocation failed");
     }
     O.allocs.push_back({q, n * sizeof(T)});
@@ -559,7 +558,7 @@ void spmv(alsub_operator_s &O, const Csr &M, const float *x, float *y, cudaStrea
 }
 
 void free_op(alsub_operator_s *O) {
-    for (auto &a : O->allocs) cudaFreeAsync(a.first, O->stream);
+    for (auto &a : O->allocs) dev_free(O->T->mesh->alloc, a.first, O->stream);
     O->allocs.clear();
     O->bytes = 0;
 }
@@ -569,7 +568,7 @@ void release(alsub_operator_s &O, Csr &M) {
     for (void *p : {(void *)M.rowptr, (void *)M.col, (void *)M.w}) {
         for (size_t i = 0; i < O.allocs.size(); i++) {
             if (O.allocs[i].first != p) continue;
-            cudaFreeAsync(p, O.stream);
+            dev_free(O.T->mesh->alloc, p, O.stream);
             O.bytes -= O.allocs[i].second;
             O.allocs.erase(O.allocs.begin() + i);
             break;

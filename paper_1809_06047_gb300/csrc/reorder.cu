@@ -241,8 +241,9 @@ alsub_status reorder_mesh(const MeshImpl &M, cudaStream_t s, MeshImpl &out, int 
     const size_t stmp = scan_tmp_bytes(nmax);
     const size_t ints = 10 * nV + 2 * (size_t)nnz + 2 * nF + 8;
     char *buf = nullptr;
-    if (cudaMallocAsync((void **)&buf, 4 * ints + stmp + 512, s) != cudaSuccess) {
-        cudaGetLastError();
+    const DevAlloc &DA = M.alloc;             // the reordered mesh takes the source mesh's allocator
+    out.alloc = DA;
+    if (dev_malloc(DA, &buf, 4 * ints + stmp + 512, s) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "reorder: device allocation failed");
     }
     int *aoff = (int *)buf, *afill = aoff + nV, *deg = afill + nV, *label = deg + nV, *parent = label + nV;
@@ -253,7 +254,7 @@ alsub_status reorder_mesh(const MeshImpl &M, cudaStream_t s, MeshImpl &out, int 
     auto bail = [&](alsub_status st, const char *what) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
-        cudaFreeAsync(buf, s);
+        dev_free(DA, buf, s);
         return report(st, what);
     };
 
@@ -304,12 +305,12 @@ alsub_status reorder_mesh(const MeshImpl &M, cudaStream_t s, MeshImpl &out, int 
     out.V = V; out.F = F; out.nnz = (int)nnz; out.K = M.K; out.B = M.B;
     out.sigma_max = M.sigma_max;
     out.stream = s;
-    e = cudaMallocAsync(&out.d_off, sizeof(int) * (size_t)(F + 1), s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out.d_fv, sizeof(int) * (size_t)nnz, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out.d_vmap, sizeof(int) * (size_t)V, s);
-    if (e == cudaSuccess) e = cudaMallocAsync(&out.d_fmap, sizeof(int) * (size_t)F, s);
-    if (e == cudaSuccess && M.K) e = cudaMallocAsync(&out.d_cv, sizeof(int) * 2 * (size_t)M.K, s);
-    if (e == cudaSuccess && M.K) e = cudaMallocAsync(&out.d_cs, sizeof(float) * (size_t)M.K, s);
+    e = dev_malloc(DA, &out.d_off, sizeof(int) * (size_t)(F + 1), s);
+    if (e == cudaSuccess) e = dev_malloc(DA, &out.d_fv, sizeof(int) * (size_t)nnz, s);
+    if (e == cudaSuccess) e = dev_malloc(DA, &out.d_vmap, sizeof(int) * (size_t)V, s);
+    if (e == cudaSuccess) e = dev_malloc(DA, &out.d_fmap, sizeof(int) * (size_t)F, s);
+    if (e == cudaSuccess && M.K) e = dev_malloc(DA, &out.d_cv, sizeof(int) * 2 * (size_t)M.K, s);
+    if (e == cudaSuccess && M.K) e = dev_malloc(DA, &out.d_cs, sizeof(float) * (size_t)M.K, s);
     if (e != cudaSuccess) return bail(ALSUB_ERR_OOM, "reorder: device allocation failed");
     k_rcm_vmap<<<grid_for(V), kBlock, 0, s>>>(V, order, newid, out.d_vmap);
     cudaMemsetAsync(cnt, 0, 4 * nV, s);
@@ -323,7 +324,7 @@ alsub_status reorder_mesh(const MeshImpl &M, cudaStream_t s, MeshImpl &out, int 
         k_rcm_creases<<<grid_for(2 * M.K), kBlock, 0, s>>>(M.K, M.d_cv, newid, out.d_cv);
         cudaMemcpyAsync(out.d_cs, M.d_cs, sizeof(float) * (size_t)M.K, cudaMemcpyDeviceToDevice, s);
     }
-    cudaFreeAsync(buf, s);
+    dev_free(DA, buf, s);
     e = cudaGetLastError();
     if (e != cudaSuccess) return report(ALSUB_ERR_DEVICE, cudaGetErrorString(e));
     return ALSUB_OK;

@@ -153,3 +153,16 @@ def test_plan_bytes_host_only():
             alsub.plan_bytes("cc", m["V"], m["F"], bad.get("nnz", nnz), bad.get("levels", 2))
     with pytest.raises(alsub.AlsubError):
         alsub.plan_bytes("cc", m["V"], m["F"], nnz, 2, 3, -1.0)
+
+
+def test_allocator_needs_both_callbacks():
+    """alsub_mesh_create_ex refuses an allocator without a free callback before any device work."""
+    lib = _lib.load()
+    c = synth.cube()
+    fv = np.ascontiguousarray(c["fv"], dtype=np.int32)
+    a = _lib.Allocator(_lib.ALLOC_FN(lambda n, ctx, s: None), _lib.FREE_FN(), None)
+    h = ctypes.c_void_p()
+    st = lib.alsub_mesh_create_ex(0, 8, 6, None, fv.ctypes.data_as(ctypes.c_void_p), 0, None, None,
+                                  ctypes.byref(a), None, ctypes.byref(h))
+    assert st == 1 and not h.value
+    assert b"alloc and free" in lib.alsub_last_error()
