@@ -43,6 +43,7 @@ struct TriArgs {
     float *Pn;
     int *fvn, *cen, *twn;
     bool in4, out4;               // parent / child positions in padded float4 rows
+    bool rev = false;             // blocks take the triangles from the end backwards
     int *status;
 };
 
@@ -430,6 +431,9 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
     a.status = T.status;
     a.in4 = l > 0;
     a.out4 = l + 1 < T.levels;
+    // consecutive steps take their triangles in opposite orders, the last step from the end: a
+    // step starts on what its predecessor wrote last, still in L2
+    a.rev = ((T.levels - 1 - l) & 1) == 0;
     return a;
 }
 
@@ -440,11 +444,13 @@ TriArgs make_args(TopoImpl &T, int l, const float *P, float *Pn) {
 #endif
 template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock, ALSUB_LOOP_MIN_BLOCKS) k_loop(TriArgs a) {
-    loop_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    const unsigned blk = a.rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    loop_body<TOPO, HELP, EVAL, BND>(a, blk * blockDim.x + threadIdx.x);
 }
 template <bool TOPO, bool HELP, bool EVAL>
 __global__ void __launch_bounds__(kBlock, ALSUB_LOOP_MIN_BLOCKS) k_sqrt3(TriArgs a) {
-    sqrt3_body<TOPO, HELP, EVAL>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    const unsigned blk = a.rev ? gridDim.x - 1 - blockIdx.x : blockIdx.x;
+    sqrt3_body<TOPO, HELP, EVAL>(a, blk * blockDim.x + threadIdx.x);
 }
 
 // Ragged batches (see the Catmull-Clark batch kernel): eval of many topologies at one level,
@@ -492,6 +498,7 @@ std::vector<BatchClass> tri_batch_plan(const std::vector<EvalItem> &items, int b
     std::vector<int> tiles[2];
     for (const EvalItem &it : items) {
         TriArgs a = make_args(*it.T, it.l, it.P, it.Pn);
+        a.rev = false;                      // the batch kernel walks its own tile list
         const int kind = it.T->scheme == ALSUB_LOOP ? 0 : 1;
         if (tiles[kind].empty()) tiles[kind].push_back(0);
         args[kind].push_back(a);

@@ -4,9 +4,10 @@ alsub_subdivide call on the dynamic path), on sampled outputs.
 The oracle cannot refine the full meshes, but it can compute any child point from a patch of the
 level above (tests/patch.py: two rings around the sampled faces, oracle patch mode). For the
 Catmull-Clark workload the level above is the oracle's own level 5 (so the check covers all six
-levels end to end); for Loop level 6 and sqrt(3) level 8 it is the CUDA path's level L-1 (the
-earlier levels are checked whole at smaller sizes), so the check covers the timed last step. Every
-child point of 4096 sampled faces must agree within 2e-6 x the bounding-box diagonal.
+levels end to end); for Loop and sqrt(3) it is the CUDA path's level L-1, for the timed last step
+(Loop level 6, sqrt(3) level 8) and for every level between it and the largest level the oracle
+refines whole (Loop 5, sqrt(3) 6 and 7). Every child point of 4096 sampled faces must agree within
+2e-6 x the bounding-box diagonal.
 """
 import numpy as np
 import pytest
@@ -60,10 +61,22 @@ def test_cc_creased_torus96_L6_sampled():
 def test_triangle_schemes_last_step_sampled(name, scheme):
     """Loop level 6 (134.2 M triangles) and sqrt(3) level 8 (215.0 M triangles): the timed last
     step, from the CUDA path's level L-1, against one oracle patch step."""
+    _triangle_step_sampled(name, scheme, synth.workload(name)["levels"])
+
+
+@pytest.mark.parametrize("name,scheme,L", [("loop_tri_torus128_L6", "loop", 5),
+                                           ("sqrt3_tri_torus128_L8", "sqrt3", 6),
+                                           ("sqrt3_tri_torus128_L8", "sqrt3", 7)])
+def test_triangle_schemes_middle_levels_sampled(name, scheme, L):
+    """The levels between the oracle's whole-mesh limit (Loop 4, sqrt(3) 5) and the last one, at the
+    benchmark's full size: level L from the CUDA path's level L - 1 against one oracle patch step."""
+    _triangle_step_sampled(name, scheme, L)
+
+
+def _triangle_step_sampled(name, scheme, L):
     import torch
     from paper_1809_06047_gb300 import alsub
     m = synth.workload(name)
-    L = m["levels"]
     M = alsub.Mesh.from_dict(m, scheme)
     P0 = torch.from_numpy(np.ascontiguousarray(m["P"], dtype=np.float32)).cuda()
     T = alsub.Topology(M, L - 1, build=True)
