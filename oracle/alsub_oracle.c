@@ -25,7 +25,9 @@
  *                  == 2 and it is finite, else the crease's own sharpness. The inherited value
  *                  is evaluated in FP32, in the fixed order t = 3*s; u = s_o + t; w = u * 0.25;
  *                  y = w - 1; max(y, 0) (compile with -ffp-contract=off).
- *                  sqrt(3) ignores sharpness (the paper gives it no crease treatment).
+ *                  sqrt(3) (no crease treatment in the paper) keeps the infinitely sharp creases
+ *                  as feature edges, handled as its boundaries are (below); finite sharpness is
+ *                  ignored.
  *   Boundaries     Catmull-Clark (Sec. 3.1 "Boundaries", Eq. CC_boundary): an edge with one
  *                  face is a boundary edge; its edge point is its midpoint, and a boundary vertex
  *                  becomes 3/4 p + 1/8 (p_prev + p_next) with its two boundary neighbours. Every
@@ -33,8 +35,11 @@
  *                  edges (several fans) is non-manifold; a crease that touches a boundary vertex
  *                  is refused (the paper defines no combination). Loop (Appendix B gives no
  *                  boundary rule) takes the same two rules on its boundary, so that the boundary
- *                  is again the cubic B-spline curve of its control polygon; sqrt(3) refuses open
- *                  meshes (Appendix A omits its boundary treatment).
+ *                  is again the cubic B-spline curve of its control polygon. sqrt(3) (Appendix A
+ *                  omits boundaries) follows Kobbelt 2000: feature edges (boundary edges and
+ *                  infinitely sharp creases) are not flipped on the first step of each pair of
+ *                  steps and are split into three on the second, their curves refined by the
+ *                  ternary cubic B-spline masks (see sqrt3_level).
  * Edge numbering follows Sec. 3.2: edges are numbered in the order of the non-zeros of the upper
  * triangle of E, i.e. lexicographically by (min vertex, max vertex).
  * Child faces: face r with corners j = 0..c-1 is replaced by its children in corner order; the
@@ -654,52 +659,204 @@ static int loop_level(const hedge *h, const creases *cr, const double *P, onext 
 
 static double sqrt3_alpha(int n) { return (4.0 - 2.0 * cos(2.0 * M_PI / n)) / 9.0; }
 
-/* sqrt(3), Appendix A (no creases). */
-static int sqrt3_level(const hedge *h, const double *P, onext *o, coo *R) {
-    int V = h->V, F = h->F;
-    int st = alloc_next(o, V + F, 3 * F, 9 * F, 0);
-    if (st) return st;
-    double *Pn = o->P, *fp = Pn + 3 * (size_t)V;
+/* sqrt(3), Appendix A, with feature edges: the boundary edges and the infinitely sharp creases
+ * (the paper omits both; the treatment follows Kobbelt 2000, Sec. 4 "Boundaries"). Refinement
+ * alternates between two kinds of step:
+ *   first step of a pair (odd, from an even level): a face point f_i for every triangle; every
+ *     edge but the feature edges is flipped, so corner k of triangle i = (k, l, m) gives
+ *     (p_k, f_{F(l,k)}, f_i), or (p_k, p_l, f_i) when k -> l is a feature edge; vertices on
+ *     feature curves (two feature edges) and corners (three or more) keep their positions;
+ *   second step (even, from an odd level): every triangle with a feature edge a -> b (exactly one,
+ *     by construction of the first step) gets no face point; the edge is split into three by two
+ *     new points q1 (near a) and q2 (near b), and the triangle (a, b, c) into (a, q1, c),
+ *     (q1, q2, c), (q2, b, c); an edge flips only between two triangles with face points; the
+ *     feature curve is refined by the ternary cubic B-spline masks (1, 16, 10)/27, (10, 16, 1)/27
+ *     for q1, q2 and (4, 19, 4)/27 for its vertices, a curve end (a corner or a dart) being
+ *     mirrored (its neighbour beyond it read as 2 p - p_next, which makes the points next to it
+ *     the linear thirds); corners stay fixed.
+ * Every other vertex takes the smooth rule (Eq. sqrt2), darts (one feature edge) included.
+ * Numbering: old vertices, then slot |v| + i of triangle i (its face point, or the point of its
+ * feature edge nearer the edge's start), then |v| + |f| + b for the second point of the b-th
+ * boundary edge (in edge order). feat: per edge, 1 for a feature edge; ff: per vertex, its feature
+ * valency and its feature neighbours (the two first found). */
+typedef struct { int k, n1, n2; } fvert;
+
+static void fvert_add(fvert *fvx, int v, int o) {
+    if (fvx[v].k == 0) fvx[v].n1 = o;
+    else if (fvx[v].k == 1) fvx[v].n2 = o;
+    fvx[v].k++;
+}
+
+static int sqrt3_level(const hedge *h, const creases *cr, const double *P, int odd, onext *o, coo *R) {
+    int V = h->V, F = h->F, E = h->E;
+    int *feat = calloc((size_t)E, sizeof(int)), *brank = malloc(sizeof(int) * (size_t)E);
+    fvert *fx = calloc((size_t)V, sizeof(fvert));
+    int *fcorner = malloc(sizeof(int) * (size_t)F);          /* the triangle's feature corner, or -1 */
+    if (!feat || !brank || !fx || !fcorner) { free(feat); free(brank); free(fx); free(fcorner); return OR_ERR_OOM; }
+    int nb = 0, nfeat = 0;
+    /* boundary edges ranked in corner order (a boundary edge has one corner); in patch mode the cut
+     * is no feature: what lies across it is unknown (-1, NaN) */
+    for (int e = 0; e < E; e++) brank[e] = -1;
+    for (int x = 0; x < h->nnz; x++)
+        if (h->tw[x] < 0 && !h->patch) brank[h->eid[x]] = nb++;
+    for (int e = 0; e < E; e++) {
+        int boundary = h->tw[h->eo[e]] < 0 && !h->patch;
+        int crease = cr && cr->es && isinf(cr->es[e]);
+        if (boundary || crease) {
+            feat[e] = 1;
+            nfeat++;
+            fvert_add(fx, h->ea[e], h->eb[e]);
+            fvert_add(fx, h->eb[e], h->ea[e]);
+        }
+    }
+    int st = OR_OK;
+    for (int r = 0; r < F && !st; r++) {
+        fcorner[r] = -1;
+        for (int j = 0; j < 3; j++) {
+            int x = h->off[r] + j;
+            if (!feat[h->eid[x]]) continue;
+            if (!odd && fcorner[r] >= 0) st = OR_ERR_ARG;      /* cannot follow a first step */
+            fcorner[r] = x;
+        }
+    }
+    if (!st) st = alloc_next(o, V + F + (odd ? 0 : nb), 3 * F, 9 * F, odd ? nfeat : 3 * nfeat);
+    if (st) { free(feat); free(brank); free(fx); free(fcorner); return st; }
+    double *Pn = o->P;
+    /* the neighbour of feature vertex v beyond it, seen from its feature neighbour w */
+    /* face points (every triangle on a first step, the triangles without a feature edge on a
+     * second one) */
     for (int r = 0; r < F; r++) {
+        if (!odd && fcorner[r] >= 0) continue;
         int s = h->off[r];
         for (int d = 0; d < 3; d++)
-            fp[3 * r + d] = (P[3 * h->fv[s] + d] + P[3 * h->fv[s + 1] + d] + P[3 * h->fv[s + 2] + d]) / 3.0;
+            Pn[3 * (V + r) + d] = (P[3 * h->fv[s] + d] + P[3 * h->fv[s + 1] + d] + P[3 * h->fv[s + 2] + d]) / 3.0;
     }
-    /* S(p) = (1 - alpha) p + alpha / n sum p_j (Eq. sqrt2, alpha from Eq. alpha) */
+    /* vertex points */
     for (int v = 0; v < V; v++) {
-        int nv = h->vo[v + 1] - h->vo[v];
-        double al = sqrt3_alpha(nv), sm[3] = {0, 0, 0};
-        for (int q = h->vo[v]; q < h->vo[v + 1]; q++) {
-            int pj = h->fv[h->nx[h->vb[q]]];
-            for (int d = 0; d < 3; d++) sm[d] += P[3 * pj + d];
+        const double *p = P + 3 * v;
+        double *q = Pn + 3 * v;
+        int k = fx[v].k;
+        if (k >= 3 || (odd && k == 2)) {                    /* corner, or a curve on a first step */
+            for (int d = 0; d < 3; d++) q[d] = p[d];
+        } else if (k == 2) {                                 /* curve vertex, second step */
+            const double *a = P + 3 * fx[v].n1, *b = P + 3 * fx[v].n2;
+            for (int d = 0; d < 3; d++) q[d] = (4.0 * a[d] + 19.0 * p[d] + 4.0 * b[d]) / 27.0;
+        } else {                                             /* S(p) = (1 - alpha) p + alpha / n sum p_j */
+            int nv = h->vo[v + 1] - h->vo[v];
+            double al = sqrt3_alpha(nv), sm[3] = {0, 0, 0};
+            for (int qq = h->vo[v]; qq < h->vo[v + 1]; qq++) {
+                int pj = h->fv[h->nx[h->vb[qq]]];
+                for (int d = 0; d < 3; d++) sm[d] += P[3 * pj + d];
+            }
+            for (int d = 0; d < 3; d++) q[d] = (1.0 - al) * p[d] + al / nv * sm[d];
         }
-        for (int d = 0; d < 3; d++) Pn[3 * v + d] = (1.0 - al) * P[3 * v + d] + al / nv * sm[d];
-        if (h->bo[v] >= 0) for (int d = 0; d < 3; d++) Pn[3 * v + d] = NAN;   /* patch mode only */
+        if (h->patch && h->bo[v] >= 0) for (int d = 0; d < 3; d++) q[d] = NAN;
     }
-    /* corner k of triangle i = (k, l, m) -> (p_k, f_{F(l,k)}, f_i) */
+    /* second step: the two points of every feature edge */
+    if (!odd) {
+        for (int e = 0; e < E; e++) {
+            if (!feat[e]) continue;
+            int x = h->eo[e], a = h->fv[x], b = h->fv[h->nx[x]];
+            int sa = V + h->cf[x];                                          /* near a */
+            int sb = h->tw[x] < 0 ? V + F + brank[e] : V + h->cf[h->tw[x]]; /* near b */
+            double pa_beyond[3], pb_beyond[3];
+            for (int d = 0; d < 3; d++) {
+                int wa = fx[a].k == 2 ? (fx[a].n1 == b ? fx[a].n2 : fx[a].n1) : -1;
+                int wb = fx[b].k == 2 ? (fx[b].n1 == a ? fx[b].n2 : fx[b].n1) : -1;
+                pa_beyond[d] = wa >= 0 ? P[3 * wa + d] : 2.0 * P[3 * a + d] - P[3 * b + d];
+                pb_beyond[d] = wb >= 0 ? P[3 * wb + d] : 2.0 * P[3 * b + d] - P[3 * a + d];
+            }
+            for (int d = 0; d < 3; d++) {
+                Pn[3 * sa + d] = (pa_beyond[d] + 16.0 * P[3 * a + d] + 10.0 * P[3 * b + d]) / 27.0;
+                Pn[3 * sb + d] = (10.0 * P[3 * a + d] + 16.0 * P[3 * b + d] + pb_beyond[d]) / 27.0;
+            }
+        }
+    }
+    /* children */
     for (int r = 0; r <= 3 * F; r++) o->off[r] = 3 * r;
-    for (int x = 0; x < h->nnz; x++) {
-        o->fv[3 * x + 0] = h->fv[x];
-        o->fv[3 * x + 1] = h->tw[x] < 0 ? -1 : V + h->cf[h->tw[x]];
-        o->fv[3 * x + 2] = V + h->cf[x];
+    for (int r = 0; r < F; r++) {
+        int s = h->off[r];
+        if (!odd && fcorner[r] >= 0) {
+            int x = fcorner[r], e = h->eid[x];
+            int a = h->fv[x], b = h->fv[h->nx[x]], c = h->fv[h->pv[x]];
+            int q1 = V + r, q2 = h->tw[x] < 0 ? V + F + brank[e] : V + h->cf[h->tw[x]];
+            int ch[9] = {a, q1, c, q1, q2, c, q2, b, c};
+            memcpy(o->fv + 9 * r, ch, sizeof(ch));
+            continue;
+        }
+        for (int j = 0; j < 3; j++) {
+            int x = s + j, t = h->tw[x];
+            /* flipped when neither side is a feature: the edge is no feature and, on a second
+             * step, the triangle across it has a face point */
+            if (t < 0 && !feat[h->eid[x]]) {                 /* patch mode: across the cut */
+                o->fv[3 * x + 0] = h->fv[x];
+                o->fv[3 * x + 1] = -1;
+                o->fv[3 * x + 2] = V + r;
+                continue;
+            }
+            int flip = !feat[h->eid[x]] && (odd || fcorner[h->cf[t]] < 0);
+            o->fv[3 * x + 0] = h->fv[x];
+            o->fv[3 * x + 1] = flip ? V + h->cf[t] : h->fv[h->nx[x]];
+            o->fv[3 * x + 2] = V + r;
+        }
+    }
+    /* crease edges of the next level (boundaries need no list) */
+    for (int e = 0; e < E; e++) {
+        if (!feat[e] || h->tw[h->eo[e]] < 0) continue;
+        int x = h->eo[e], a = h->fv[x], b = h->fv[h->nx[x]];
+        if (odd) {
+            push_crease(o, a, b, INFINITY);
+        } else {
+            int q1 = V + h->cf[x], q2 = V + h->cf[h->tw[x]];
+            push_crease(o, a, q1, INFINITY);
+            push_crease(o, q1, q2, INFINITY);
+            push_crease(o, q2, b, INFINITY);
+        }
     }
     if (R) {
         row rw = {0, 0, NULL, NULL};
         for (int v = 0; v < V && !st; v++) {
-            int nv = h->vo[v + 1] - h->vo[v];
-            double al = sqrt3_alpha(nv);
-            st = row_add(&rw, v, 1.0 - al);
-            for (int q = h->vo[v]; q < h->vo[v + 1] && !st; q++)
-                st = row_add(&rw, h->fv[h->nx[h->vb[q]]], al / nv);
+            int k = fx[v].k;
+            if (k >= 3 || (odd && k == 2)) {
+                st = row_add(&rw, v, 1.0);
+            } else if (k == 2) {
+                st = row_add(&rw, fx[v].n1, 4.0 / 27.0);
+                if (!st) st = row_add(&rw, v, 19.0 / 27.0);
+                if (!st) st = row_add(&rw, fx[v].n2, 4.0 / 27.0);
+            } else {
+                int nv = h->vo[v + 1] - h->vo[v];
+                double al = sqrt3_alpha(nv);
+                st = row_add(&rw, v, 1.0 - al);
+                for (int qq = h->vo[v]; qq < h->vo[v + 1] && !st; qq++)
+                    st = row_add(&rw, h->fv[h->nx[h->vb[qq]]], al / nv);
+            }
             if (!st) st = coo_push_row(R, v, &rw);
         }
         for (int r = 0; r < F && !st; r++) {
+            if (!odd && fcorner[r] >= 0) continue;
             int s = h->off[r];
             for (int j = 0; j < 3 && !st; j++) st = row_add(&rw, h->fv[s + j], 1.0 / 3.0);
             if (!st) st = coo_push_row(R, V + r, &rw);
         }
+        for (int e = 0; e < E && !st && !odd; e++) {
+            if (!feat[e]) continue;
+            int x = h->eo[e], a = h->fv[x], b = h->fv[h->nx[x]];
+            int sa = V + h->cf[x];
+            int sb = h->tw[x] < 0 ? V + F + brank[e] : V + h->cf[h->tw[x]];
+            int wa = fx[a].k == 2 ? (fx[a].n1 == b ? fx[a].n2 : fx[a].n1) : -1;
+            int wb = fx[b].k == 2 ? (fx[b].n1 == a ? fx[b].n2 : fx[b].n1) : -1;
+            /* q1 = (beyond_a + 16 a + 10 b) / 27 with beyond_a = 2 a - b at a curve end */
+            if (wa >= 0) { st = row_add(&rw, wa, 1.0 / 27.0); if (!st) st = row_add(&rw, a, 16.0 / 27.0); if (!st) st = row_add(&rw, b, 10.0 / 27.0); }
+            else { st = row_add(&rw, a, 18.0 / 27.0); if (!st) st = row_add(&rw, b, 9.0 / 27.0); }
+            if (!st) st = coo_push_row(R, sa, &rw);
+            if (st) break;
+            if (wb >= 0) { st = row_add(&rw, a, 10.0 / 27.0); if (!st) st = row_add(&rw, b, 16.0 / 27.0); if (!st) st = row_add(&rw, wb, 1.0 / 27.0); }
+            else { st = row_add(&rw, a, 9.0 / 27.0); if (!st) st = row_add(&rw, b, 18.0 / 27.0); }
+            if (!st) st = coo_push_row(R, sb, &rw);
+        }
         free(rw.c); free(rw.w);
     }
+    free(feat); free(brank); free(fx); free(fcorner);
     return st;
 }
 
@@ -749,10 +906,11 @@ int or_run(int scheme, int levels, int keep_all, int want_operator, int patch,
     memcpy(cur->fv, fv, sizeof(int) * (size_t)off[F]);
     memcpy(cur->P, P0, sizeof(double) * 3 * (size_t)V);
     cur->K = 0;
-    if (scheme != OR_SQRT3) {
+    {
         for (int i = 0; i < K; i++) {
             if (!(cs[i] >= 0.0f)) { or_free(res); return OR_ERR_CREASE; }
-            if (cs[i] > 0.0f) {
+            /* sqrt(3) keeps the infinitely sharp creases only (feature edges) */
+            if (cs[i] > 0.0f && (scheme != OR_SQRT3 || isinf(cs[i]))) {
                 cur->cv[2 * cur->K] = cv[2 * i]; cur->cv[2 * cur->K + 1] = cv[2 * i + 1];
                 cur->cs[cur->K] = cs[i]; cur->K++;
             }
@@ -764,13 +922,13 @@ int or_run(int scheme, int levels, int keep_all, int want_operator, int patch,
         olevel *L = &res->L[last];
         if (patch && l == levels) break;          /* a patch's child may reference the cut (-1) */
         hedge h;
-        st = hedge_build(&h, L->V, L->F, L->off, L->fv, patch ? 2 : scheme != OR_SQRT3);
+        st = hedge_build(&h, L->V, L->F, L->off, L->fv, patch ? 2 : 1);
         h.patch = patch;
         if (st) { hedge_free(&h); break; }
         L->E = h.E;
         creases cr;
         memset(&cr, 0, sizeof(cr));
-        int use_cr = (scheme != OR_SQRT3) && L->K > 0;
+        int use_cr = L->K > 0;
         if (use_cr) st = creases_build(&cr, &h, L->K, L->cv, L->cs);
         if (st || l == levels) { creases_free(&cr); hedge_free(&h); break; }
         onext o;
@@ -779,7 +937,7 @@ int or_run(int scheme, int levels, int keep_all, int want_operator, int patch,
         coo *Rp = want_operator ? &R : NULL;
         if (scheme == OR_CC) st = cc_level(&h, use_cr ? &cr : NULL, L->P, &o, Rp);
         else if (scheme == OR_LOOP) st = loop_level(&h, use_cr ? &cr : NULL, L->P, &o, Rp);
-        else st = sqrt3_level(&h, L->P, &o, Rp);
+        else st = sqrt3_level(&h, use_cr ? &cr : NULL, L->P, (l & 1) == 0, &o, Rp);
         creases_free(&cr);
         hedge_free(&h);
         if (Rp) { L->rnnz = R.n; L->rr = R.r; L->rc = R.c; L->rw = R.w; }

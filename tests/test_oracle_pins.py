@@ -80,7 +80,22 @@ def _meshes():
         ("loop", synth.torus_tri(10, 10, seed=12)),
         ("sqrt3", synth.tetrahedron()),
         ("sqrt3", synth.torus_tri(10, 10, seed=13, creases=False)),
+        ("sqrt3", synth.triangulate(synth.sheet_cc(5, 4, seed=15))),
+        ("sqrt3", synth.triangulate(synth.holed_cc_mixed(12, 12, holes=3, seed=16))),
+        ("sqrt3", synth.torus_tri(10, 10, seed=17)),                  # infinitely sharp creases
+        ("sqrt3", synth.polygon(3)),
     ]
+
+
+def _boundary_edge_count(level):
+    """Directed edges of a face table without the reverse edge (the boundary edges)."""
+    off, fv = level["off"], level["fv"]
+    d = set()
+    for r in range(level["F"]):
+        f = fv[off[r]:off[r + 1]]
+        for j in range(len(f)):
+            d.add((int(f[j]), int(f[(j + 1) % len(f)])))
+    return sum(1 for a, b in d if (b, a) not in d)
 
 
 @pytest.mark.parametrize("scheme,mesh", _meshes())
@@ -97,7 +112,10 @@ def test_counts_and_euler(scheme, mesh):
         elif scheme == "loop":
             exp = (a["V"] + a["E"], 4 * a["F"], 2 * a["E"] + 3 * a["F"])
         else:
-            exp = (a["V"] + a["F"], 3 * a["F"], 9 * a["F"] // 2)
+            # sqrt(3) with feature edges (Kobbelt 2000): the second step of each pair adds two
+            # points per boundary edge, one in the slot of the triangle beside it, one more
+            B = _boundary_edge_count(a) if l % 2 == 1 else 0
+            exp = (a["V"] + a["F"] + B, 3 * a["F"], a["E"] + 3 * a["F"] + B)
         assert (b["V"], b["F"], b["E"]) == exp
         assert b["V"] - b["E"] + b["F"] == chi
 
@@ -329,6 +347,8 @@ def test_corners_fixed():
     ("loop", synth.torus_tri(5, 5, seed=22)),
     ("loop", synth.triangulate(synth.sheet_cc(3, 3, seed=25))),
     ("sqrt3", synth.torus_tri(5, 5, seed=23, creases=False)),
+    ("sqrt3", synth.triangulate(synth.sheet_cc(3, 3, seed=26))),
+    ("sqrt3", synth.torus_tri(5, 5, seed=27, sharp_frac=0.1)),
 ])
 def test_brute_force_operator(scheme, mesh):
     """Dense R_l from unit impulses equals the oracle's sparse operator, and the composed
@@ -353,10 +373,15 @@ def test_rejects_invalid_meshes():
     m = synth.cube()
     o = synth.octahedron()
     open_tri = dict(o, F=7, off=o["off"][:8], fv=o["fv"][:21])
-    with pytest.raises(oracle.OracleError) as ei:   # Appendix A omits the sqrt(3) boundary rule
-        oracle.subdivide(open_tri, 1, "sqrt3")
-    assert ei.value.code == 3
+    oracle.subdivide(open_tri, 2, "sqrt3")          # sqrt(3) takes Kobbelt's boundary treatment
     oracle.subdivide(open_tri, 1, "loop")           # Loop takes the boundary rules of Eq. CC_boundary
+    # an infinitely sharp sqrt(3) crease touching a boundary vertex
+    t = synth.triangulate(dict(m, F=5, off=m["off"][:6], fv=m["fv"][:20]))
+    f5 = m["fv"][20:24]
+    with pytest.raises(oracle.OracleError) as ei:
+        oracle.subdivide(dict(t, crease_verts=np.array([[f5[0], f5[1]]], np.int32),
+                              crease_sharp=np.array([np.inf], np.float32)), 1, "sqrt3")
+    assert ei.value.code == 3
     # two squares sharing only vertex 0: two fans at one vertex
     bow = dict(V=7, F=2, off=np.array([0, 4, 8], np.int32),
                fv=np.array([0, 1, 2, 3, 0, 4, 5, 6], np.int32), P=np.zeros((7, 3), np.float32),
@@ -925,3 +950,112 @@ def test_vertex_sharpness_is_the_mean_of_unequal_creases(scheme, case):
         else:
             want = w * P[v] + (1.0 - w) * smooth
         np.testing.assert_allclose(out[1]["P"][v], want, rtol=0, atol=1e-15)
+
+
+# ---- sqrt(3) feature edges: boundaries and infinitely sharp creases (Kobbelt 2000) ---------------
+
+def _ternary_cubic_mask():
+    """The coefficients c_k of N(t) = sum_k c_k N(3t - k) for the uniform cubic B-spline N,
+    found by least squares on samples of the Cox-de Boor basis (not typed in)."""
+    t = np.linspace(0.0, 4.0, 1201)[:-1]
+    A = np.stack([_cox_de_boor(3 * t - k, 0, 4) for k in range(10)], axis=1)
+    c, *_ = np.linalg.lstsq(A, _cox_de_boor(t, 0, 4), rcond=None)
+    return c
+
+
+def _refine_closed_polygon_3(P, c):
+    """Control polygon of the same closed cubic B-spline on a third of the knot spacing:
+    Q_m = sum_j c_{m - 3j} P_j (indices cyclic), rolled so that entry 3i is the point at P_i (the
+    mask's centre is c_4, so Q_{3i+4} sits at P_i)."""
+    n = len(P)
+    Q = np.zeros((3 * n, 3))
+    for m in range(3 * n):
+        for j in range(n):
+            k = (m - 3 * j) % (3 * n)
+            if k < len(c):
+                Q[m] += c[k] * P[j]
+    return np.roll(Q, -4, axis=0)
+
+
+@pytest.mark.parametrize("mesh", [synth.triangulate(synth.tube_cc(10, 6, jitter=0.2, seed=41)),
+                                  synth.triangulate(synth.sheet_cc(6, 5, seed=42)),
+                                  synth.triangulate(synth.holed_cc_mixed(16, 14, holes=3, seed=43)),
+                                  synth.polygon(3)],
+                         ids=["tube", "sheet", "holes", "triangle"])
+def test_sqrt3_boundary_is_ternary_cubic_bspline_curve(mesh):
+    """sqrt(3) boundaries: every second step refines each boundary loop as the cubic B-spline
+    curve of the level-0 loop on a third of the knot spacing (the mask comes from the Cox-de Boor
+    basis), and every first step leaves the boundary points where they are."""
+    c = _ternary_cubic_mask()
+    np.testing.assert_allclose(c * 27.0, [1, 4, 10, 16, 19, 16, 10, 4, 1, 0], atol=1e-9)
+    out = oracle.subdivide(mesh, 4, "sqrt3")
+    expected = [out[0]["P"][loop].astype(np.float64) for loop in _boundary_loops(out[0])]
+    for l in range(1, 5):
+        if l % 2 == 0:
+            expected = [_refine_closed_polygon_3(poly, c) for poly in expected]
+        loops = _boundary_loops(out[l])
+        assert sorted(len(x) for x in loops) == sorted(len(x) for x in expected)
+        got = np.concatenate([out[l]["P"][x] for x in loops])
+        np.testing.assert_allclose(_as_sorted(got), _as_sorted(np.concatenate(expected)), atol=1e-12)
+
+
+def test_sqrt3_sharp_crease_is_ternary_cubic_bspline_curve():
+    """An infinitely sharp crease loop on a sqrt(3) torus refines as the ternary cubic B-spline
+    curve of its polygon, whatever the surface on either side, and keeps still on first steps."""
+    N = M = 9
+    m = synth.torus_tri(N, M, flip_frac=0.0, creases=False, jitter=0.05, seed=44)
+    m["crease_verts"], m["crease_sharp"] = _loop_creases(N, M, np.inf)
+    c = _ternary_cubic_mask()
+    out = oracle.subdivide(m, 4, "sqrt3")
+    poly = m["P"][[i * M for i in range(N)]].astype(np.float64)
+    for l in range(1, 5):
+        if l % 2 == 0:
+            poly = _refine_closed_polygon_3(poly, c)
+        seq = _ordered_loop(out[l], 0)
+        got = out[l]["P"][seq]
+        if not np.allclose(got[1], poly[1], atol=1e-12):
+            got = got[[0] + list(range(len(seq) - 1, 0, -1))]
+        assert len(seq) == len(poly)
+        np.testing.assert_allclose(got, poly, atol=1e-12)
+        assert np.all(np.isinf(out[l]["crease_sharp"]))
+
+
+def test_sqrt3_finite_sharpness_is_ignored_and_corners_fixed():
+    """Finite sharpness has no sqrt(3) form (the paper and Kobbelt 2000 give none): it changes
+    nothing. Three infinitely sharp creases meeting at a vertex (a corner) keep it fixed."""
+    N = M = 8
+    base = synth.torus_tri(N, M, flip_frac=0.0, creases=False, jitter=0.04, seed=45)
+    plain = oracle.subdivide(base, 3, "sqrt3")
+    fin = dict(base, crease_verts=np.array([[0, M], [M, 2 * M]], np.int32),
+               crease_sharp=np.array([2.5, 0.5], np.float32))
+    out = oracle.subdivide(fin, 3, "sqrt3")
+    for l in range(4):
+        np.testing.assert_array_equal(out[l]["fv"], plain[l]["fv"])
+        np.testing.assert_array_equal(out[l]["P"], plain[l]["P"])
+    v = 3 * M + 3
+    corner = dict(base, crease_verts=np.array([[v, v + M], [v, v + 1], [v, v - M]], np.int32),
+                  crease_sharp=np.full(3, np.inf, np.float32))
+    out = oracle.subdivide(corner, 4, "sqrt3")
+    for l in range(1, 5):
+        np.testing.assert_array_equal(out[l]["P"][v], base["P"][v].astype(np.float64))
+
+
+def test_sqrt3_boundary_leaves_far_interior_unchanged():
+    """Cutting a ring of quads (two triangles each) out of a sqrt(3) torus leaves the level-2 and
+    level-4 children of triangles far from the cut exactly as on the closed torus."""
+    N, M = 14, 8
+    closed = synth.torus_cc_plain(N, M, jitter=0.05, seed=46)
+    F = closed["F"] - M
+    cut = dict(closed, F=F, off=closed["off"][:F + 1], fv=closed["fv"][:4 * F])
+    closed, cut = synth.triangulate(closed), synth.triangulate(cut)
+    for levels in (2, 4):
+        a = oracle.subdivide(closed, levels, "sqrt3")[levels]
+        b = oracle.subdivide(cut, levels, "sqrt3")[levels]
+        q = 2 * 3 ** levels                          # refined triangles of one quad
+        for i in range(4, N - 5):
+            for j in range(M):
+                r = i * M + j
+                ca = a["fv"][3 * q * r:3 * q * (r + 1)]
+                cb = b["fv"][3 * q * r:3 * q * (r + 1)]
+                np.testing.assert_array_equal(a["P"][ca], b["P"][cb])
+        assert not np.array_equal(a["P"][a["fv"][:3 * q]], b["P"][b["fv"][:3 * q]])
