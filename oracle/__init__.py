@@ -57,7 +57,7 @@ def _load():
             i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
             f32p = np.ctypeslib.ndpointer(np.float32, flags="C")
             f64p = np.ctypeslib.ndpointer(np.float64, flags="C")
-            lib.or_run.argtypes = [ctypes.c_int] * 5 + [ctypes.c_int, ctypes.c_int, i32p, i32p, f64p,
+            lib.or_run.argtypes = [ctypes.c_int] * 6 + [ctypes.c_int, ctypes.c_int, i32p, i32p, f64p,
                                                         ctypes.c_int, i32p, f32p,
                                                         ctypes.POINTER(ctypes.c_void_p)]
             lib.or_counts.argtypes = [ctypes.c_void_p, ctypes.c_int, np.ctypeslib.ndpointer(np.int64)]
@@ -74,7 +74,7 @@ def _load():
 
 
 def subdivide(mesh: dict, levels: int, scheme: str | None = None, keep_all: bool = True,
-              operator: bool = False, P0=None, patch: bool = False) -> list[dict | None]:
+              operator: bool = False, P0=None, patch: bool = False, start_level: int = 0) -> list[dict | None]:
     """Refine ``mesh`` ``levels`` times; returns one dict per level (None for levels not kept).
 
     Each dict holds V, F, nnz, E, K, off, fv, P (float64[V,3]), crease_verts, crease_sharp and,
@@ -84,6 +84,9 @@ def subdivide(mesh: dict, levels: int, scheme: str | None = None, keep_all: bool
     ``patch``: the mesh is a patch cut out of a larger closed mesh (one level, any scheme); points
     whose rule reaches beyond the cut are NaN, every other point is the closed mesh's (the last
     level's E is not computed).
+
+    ``start_level``: the level the input mesh is at (sqrt(3) alternates two kinds of step, the
+    first of a pair from an even level).
     """
     lib = _load()
     scheme = scheme or mesh.get("scheme", "cc")
@@ -99,7 +102,8 @@ def subdivide(mesh: dict, levels: int, scheme: str | None = None, keep_all: bool
     else:
         cs_n = cs.size
     h = ctypes.c_void_p()
-    st = lib.or_run(SCHEMES[scheme], int(levels), int(keep_all), int(operator), int(patch), int(mesh["V"]),
+    st = lib.or_run(SCHEMES[scheme], int(levels), int(keep_all), int(operator), int(patch), int(start_level),
+                    int(mesh["V"]),
                     int(mesh["F"]), off, fv, P, cs_n, cv, cs, ctypes.byref(h))
     if st:
         raise OracleError(st)

@@ -877,9 +877,10 @@ void or_free(oresult *r) {
 
 /*
  * Refine `levels` times. keep_all = 0 keeps only the last level; want_operator = 1 stores the
- * operator R_l of every kept level l < levels (COO, FP64).
+ * operator R_l of every kept level l < levels (COO, FP64). start_level: the level the input is at
+ * (it decides which kind of sqrt(3) step comes first).
  */
-int or_run(int scheme, int levels, int keep_all, int want_operator, int patch,
+int or_run(int scheme, int levels, int keep_all, int want_operator, int patch, int start_level,
            int V, int F, const int *off, const int *fv, const double *P0,
            int K, const int *cv, const float *cs, oresult **out) {
     *out = NULL;
@@ -937,7 +938,7 @@ int or_run(int scheme, int levels, int keep_all, int want_operator, int patch,
         coo *Rp = want_operator ? &R : NULL;
         if (scheme == OR_CC) st = cc_level(&h, use_cr ? &cr : NULL, L->P, &o, Rp);
         else if (scheme == OR_LOOP) st = loop_level(&h, use_cr ? &cr : NULL, L->P, &o, Rp);
-        else st = sqrt3_level(&h, use_cr ? &cr : NULL, L->P, (l & 1) == 0, &o, Rp);
+        else st = sqrt3_level(&h, use_cr ? &cr : NULL, L->P, ((l + start_level) & 1) == 0, &o, Rp);
         creases_free(&cr);
         hedge_free(&h);
         if (Rp) { L->rnnz = R.n; L->rr = R.r; L->rc = R.c; L->rw = R.w; }

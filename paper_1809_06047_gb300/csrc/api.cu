@@ -54,13 +54,20 @@ alsub_status cuda_fail(cudaError_t e, const char *what) {
 
 const long long kI32 = 2147483647LL;
 
-// Closed-form counts of one refinement step (Sec. 3.1 step 4, Appendix A, B).
-bool next_counts(alsub_scheme s, long long V, long long F, long long nnz, long long E,
+// Closed-form counts of one refinement step from level l (Sec. 3.1 step 4, Appendix A, B): o =
+// V, F, nnz, E and B (boundary edges) of level l + 1. Catmull-Clark and Loop split every boundary
+// edge in two. sqrt(3) with feature edges (Kobbelt 2000): the first step of a pair (l even) keeps
+// them; the second (l odd) splits them in three, which adds one vertex and one edge per boundary
+// edge beyond the triangle slots (with B = 0, E + 3F is the closed mesh's 9F / 2).
+bool next_counts(alsub_scheme s, int l, long long V, long long F, long long nnz, long long E, long long B,
                  long long *o) {
-    if (s == ALSUB_CATMULL_CLARK) { o[0] = V + F + E; o[1] = nnz; o[2] = 4 * nnz; o[3] = 2 * E + nnz; }
-    else if (s == ALSUB_LOOP) { o[0] = V + E; o[1] = 4 * F; o[2] = 12 * F; o[3] = 2 * E + 3 * F; }
-    else { o[0] = V + F; o[1] = 3 * F; o[2] = 9 * F; o[3] = 9 * F / 2; }
-    for (int i = 0; i < 4; i++)
+    if (s == ALSUB_CATMULL_CLARK) { o[0] = V + F + E; o[1] = nnz; o[2] = 4 * nnz; o[3] = 2 * E + nnz; o[4] = 2 * B; }
+    else if (s == ALSUB_LOOP) { o[0] = V + E; o[1] = 4 * F; o[2] = 12 * F; o[3] = 2 * E + 3 * F; o[4] = 2 * B; }
+    else {
+        const long long b = (l & 1) ? B : 0;
+        o[0] = V + F + b; o[1] = 3 * F; o[2] = 9 * F; o[3] = E + 3 * F + b; o[4] = (l & 1) ? 3 * B : B;
+    }
+    for (int i = 0; i < 5; i++)
         if (o[i] > kI32) return false;
     return true;
 }
@@ -161,15 +168,17 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     T.L.assign(levels + 1, LevelBuf());
     LevelBuf &L0 = T.L[0];
     // every edge has two corners except the B boundary edges (one each)
-    L0.V = M.V; L0.F = M.F; L0.nnz = M.nnz; L0.E = (M.nnz + M.B) / 2;
+    L0.V = M.V; L0.F = M.F; L0.nnz = M.nnz; L0.E = (M.nnz + M.B) / 2; L0.B = M.B;
     for (int l = 0; l < levels; l++) {
-        long long o[4];
+        long long o[5];
         LevelBuf &A = T.L[l];
-        if (!next_counts(M.scheme, A.V, A.F, A.nnz, A.E, o))
+        if (!next_counts(M.scheme, l, A.V, A.F, A.nnz, A.E, A.B, o))
             return fail(ALSUB_ERR_UNSUPPORTED, "level %d exceeds int32 counts", l + 1);
         LevelBuf &B = T.L[l + 1];
-        B.V = o[0]; B.F = o[1]; B.nnz = o[2]; B.E = o[3];
+        B.V = o[0]; B.F = o[1]; B.nnz = o[2]; B.E = o[3]; B.B = o[4];
     }
+    // sqrt(3) with feature edges takes the general path of sqrt3f.cu
+    T.s3f = M.scheme == ALSUB_SQRT3 && (M.B > 0 || M.K > 0);
     const int V = M.V, nnz = M.nnz, E0 = (int)L0.E;
     L0.fv = M.d_fv;
     AL(L0.ce, nnz);
@@ -188,12 +197,10 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     AL(T.e0count, 1); AL(T.status, 1);
     // boundary lists of an open mesh, levels 0 .. levels - 1: the B_l = 2^l B boundary edges of
     // level l (each boundary edge splits into two, Sec. 3.2 "Boundaries")
-    if (M.B > 0) {
+    if (M.B > 0 && M.scheme != ALSUB_SQRT3) {
         AL(T.bcount, 1);
         for (int l = 0; l < levels; l++) {
             LevelBuf &A = T.L[l];
-            A.B = M.B << l;
-            if (A.B > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "level %d exceeds int32 counts", l);
             AL(A.bA, A.B); AL(A.bE, A.B); AL(A.bS, A.B);
         }
     }
@@ -208,6 +215,26 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
         alsub_status st = alloc_crease(T, T.L[l].cr, cap, true, s);
         if (st) return st;
         maxcap = std::max(maxcap, cap);
+    }
+    if (T.s3f) {
+        // sqrt(3) feature path: every level's feature flags and twins, the export list of its
+        // crease edges (K_l: the first step of a pair keeps them, the second splits them in three),
+        // and the per-vertex scratch of the steps
+        long long K = M.K, vmax3 = 1;
+        for (int l = 0; l <= levels; l++) {
+            LevelBuf &A = T.L[l];
+            AL(A.fe, A.nnz);
+            A.cr.cap = K;
+            if (K > 0) {
+                AL(A.cr.xverts, 2 * K);
+                AL(A.cr.xsig, K);
+                AL(A.cr.xcount, 1);
+            }
+            if (l < levels) vmax3 = std::max(vmax3, A.V);
+            K = (l & 1) ? 3 * K : K;
+        }
+        AL(T.s3_vc, vmax3);
+        AL(T.s3_vi, vmax3);
     }
     long long nflags = std::max<long long>({(long long)nnz, (long long)E0, 2 * maxcap, 1});
     AL(T.flags, nflags);
@@ -232,6 +259,7 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
         // Loop and sqrt(3): the last step derives its level's edge ids and twins from the parent
         // level (crease analysis included); its vertex rings are read from the parent level.
         if (!cc && l == levels - 1 && l >= 1) B.helpers = false;
+        if (T.s3f) B.helpers = true;       // the general sqrt(3) path stores every level's twins
         if (B.helpers) {
             if (M.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);
             AL(B.tw, B.nnz);
@@ -496,6 +524,7 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
     };
     mark(T, 0, s);
     level0_build(T, s);
+    if (T.s3f) s3f_level0(T, s);
     // the side branch: the level-0 crease list and analysis, then the level-0 vertex checks (they
     // only set the status word, so nothing waits for them before the end of the call)
     if (crease_alive(T, 0)) {
@@ -659,19 +688,17 @@ alsub_status alsub_plan_open(alsub_scheme scheme, int64_t V, int64_t F, int64_t 
         return fail(ALSUB_ERR_INVALID_ARG, "bad counts");
     if (scheme != ALSUB_CATMULL_CLARK && nnz != 3 * F)
         return fail(ALSUB_ERR_INVALID_ARG, "Loop and sqrt(3) need a triangle mesh");
-    if (B > 0 && scheme == ALSUB_SQRT3)
-        return fail(ALSUB_ERR_UNSUPPORTED, "sqrt(3) has no boundary rule (Appendix A omits it)");
     if ((nnz + B) % 2) {
         if (B == 0) return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
         return fail(ALSUB_ERR_INVALID_ARG, "nnz + boundary edges must be even");
     }
     if (V > kI32 || F > kI32 || nnz > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "counts exceed int32");
-    long long c[4] = {V, F, nnz, (nnz + B) / 2};
+    long long c[5] = {V, F, nnz, (nnz + B) / 2, B};
     for (int l = 0; l <= levels; l++) {
         for (int i = 0; i < 4; i++) counts[4 * l + i] = c[i];
         if (l == levels) break;
-        long long o[4];
-        if (!next_counts(scheme, c[0], c[1], c[2], c[3], o))
+        long long o[5];
+        if (!next_counts(scheme, l, c[0], c[1], c[2], c[3], c[4], o))
             return fail(ALSUB_ERR_UNSUPPORTED, "level %d exceeds int32 counts", l + 1);
         memcpy(c, o, sizeof(c));
     }
@@ -711,8 +738,6 @@ alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t V, int32_t F, con
         for (int r = 0; r <= F; r++) off[r] = r * order;
     }
     const long long nnz = off[F];
-    if (scheme == ALSUB_SQRT3 && nnz % 2)
-        return fail(ALSUB_ERR_UNSUPPORTED, "odd corner count: the mesh is not closed");
     std::vector<int> used(V, 0), mark(V, -1);
     for (int r = 0; r < F; r++) {
         for (int x = off[r]; x < off[r + 1]; x++) {
@@ -734,7 +759,9 @@ alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t V, int32_t F, con
         if (a < 0 || a >= V || b < 0 || b >= V || a == b)
             return fail(ALSUB_ERR_INVALID_ARG, "crease %d: bad endpoints (%d, %d)", i, a, b);
         if (!(sg >= 0.f)) return fail(ALSUB_ERR_INVALID_ARG, "crease %d: sharpness must be >= 0", i);
-        if (sg == 0.f) continue;
+        // sqrt(3) keeps the infinitely sharp creases (feature edges); finite sharpness has no
+        // sqrt(3) rule
+        if (sg == 0.f || (scheme == ALSUB_SQRT3 && !isinf(sg))) continue;
         cv.push_back(a); cv.push_back(b); cs.push_back(sg);
         smax = std::max(smax, sg);
     }
@@ -746,7 +773,7 @@ alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t V, int32_t F, con
         M.alloc.free = allocator->free;
         M.alloc.ctx = allocator->ctx;
     }
-    M.scheme = scheme; M.V = V; M.F = F; M.nnz = (int)nnz; M.K = scheme == ALSUB_SQRT3 ? 0 : (int)cs.size();
+    M.scheme = scheme; M.V = V; M.F = F; M.nnz = (int)nnz; M.K = (int)cs.size();
     M.sigma_max = smax;
     M.stream = (cudaStream_t)stream;
     cudaStream_t s = M.stream;
@@ -767,8 +794,7 @@ alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t V, int32_t F, con
     if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cv, cv.data(), sizeof(int) * 2 * M.K, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cs, cs.data(), sizeof(float) * M.K, cudaMemcpyHostToDevice, s);
     // the host vectors die on return: the copies complete at the stream synchronisation below
-    // (for Catmull-Clark and Loop, the boundary scan's, which runs after them on the same stream)
-    if (e == cudaSuccess && scheme == ALSUB_SQRT3) e = cudaStreamSynchronize(s);
+    // (the boundary scan's, which runs after them on the same stream)
     if (e != cudaSuccess) {
         cudaStreamSynchronize(s);
         cudaGetLastError();
@@ -776,10 +802,10 @@ alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t V, int32_t F, con
         if (e == cudaErrorMemoryAllocation) return fail(ALSUB_ERR_OOM, "mesh upload: out of device memory");
         return cuda_fail(e, "mesh upload");
     }
-    if (scheme != ALSUB_SQRT3) {
-        // boundary edges (Sec. 3.2 "Boundaries"; Loop takes the same rules): their number sizes
-        // every level; the paper gives no rule for a crease that meets the boundary, so such input
-        // is refused
+    {
+        // boundary edges (Sec. 3.2 "Boundaries"; Loop takes the same rules, sqrt(3) Kobbelt's):
+        // their number sizes every level; the paper gives no rule for a crease that meets the
+        // boundary, so such input is refused
         long long B = 0;
         bool crease_at_boundary = false;
         alsub_status st = mesh_boundary_scan(M, s, &B, &crease_at_boundary);
@@ -921,6 +947,7 @@ alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stre
     TopoImpl &T = (*out)->t;
     cudaStream_t s = (cudaStream_t)stream;
     level0_build(T, s);
+    if (T.s3f) s3f_level0(T, s);
     level0_validate(T, s);
     level0_creases(T, s);
     for (int l = 0; l < levels; l++) {
@@ -1070,7 +1097,8 @@ alsub_status alsub_plan_bytes(alsub_scheme scheme, int32_t V, int32_t F, int32_t
     if (st != ALSUB_OK) return st;
     MeshImpl M;
     M.scheme = scheme; M.V = V; M.F = F; M.nnz = nnz; M.B = B;
-    M.K = scheme == ALSUB_SQRT3 ? 0 : K;
+    // sqrt(3) keeps infinitely sharp creases only: num_creases counts those
+    M.K = scheme == ALSUB_SQRT3 ? (isinf(sigma_max) ? K : 0) : K;
     M.sigma_max = M.K ? sigma_max : 0.f;
     TopoImpl T;
     T.dry = true;

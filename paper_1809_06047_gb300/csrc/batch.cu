@@ -157,6 +157,11 @@ alsub_status alsub_batch_create(int32_t n, const alsub_topology_t *topos, const 
             delete B;
             return report(ALSUB_ERR_UNSUPPORTED, "batch members must be closed meshes (no boundary repair)");
         }
+        if (T->s3f) {
+            delete B;
+            return report(ALSUB_ERR_UNSUPPORTED, "batch members: a sqrt(3) mesh with infinitely sharp creases takes "
+                                                 "the general feature path, which is not batched");
+        }
         for (TopoImpl *U : B->T)
             if (U == T) { delete B; return report(ALSUB_ERR_INVALID_ARG, "a topology appears twice in the batch"); }
         B->T.push_back(T);

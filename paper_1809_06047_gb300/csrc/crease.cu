@@ -296,6 +296,7 @@ void crease_fix(TopoImpl &T, int l, const float *P, float *Pn, cudaStream_t s) {
 }
 
 int crease_export(TopoImpl &T, int l, cudaStream_t s) {
+    if (T.s3f) return s3f_export(T, l, s);
     CreaseList &C = T.L[l].cr;
     if (C.cap == 0) return 0;
     const long long n = C.cap;

@@ -292,6 +292,40 @@ __global__ void k_crease0(int K, const int *__restrict__ cv, const float *__rest
     out.verts[2 * i + 1] = fv[tw[o]];
 }
 
+// sqrt(3) with feature edges, level 0 (the general path of sqrt3f.cu): the boundary corners (twin
+// -1) are ranked in corner order by a scan of their flags; their twins become -1 - rank and every
+// corner's feature flag is set: boundary corners, then both corners of every infinitely sharp
+// crease (a crease that is not an edge is an input error).
+__global__ void k_s3f_flags0(int nnz, const int *__restrict__ tw, int *flag) {
+    pdl_wait();
+    pdl_trigger();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < nnz) flag[x] = tw[x] < 0;
+}
+
+__global__ void k_s3f_rank0(int nnz, const int *__restrict__ pos, int *tw, int *fe) {
+    pdl_wait();
+    pdl_trigger();
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nnz) return;
+    const int t = tw[x];
+    if (t < 0) tw[x] = -1 - pos[x];
+    fe[x] = t < 0;
+}
+
+__global__ void k_s3f_crease0(int K, const int *__restrict__ cv, const float *__restrict__ cs, DirTable tab,
+                              const int *__restrict__ tw, int *fe, int *status) {
+    pdl_wait();
+    pdl_trigger();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K || !isinf(cs[i])) return;
+    const int x = dir_find(tab, cv[2 * i], cv[2 * i + 1]);
+    if (x < 0) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
+    fe[x] = 1;
+    const int t = tw[x];
+    if (t >= 0) fe[t] = 1;
+}
+
 }  // namespace
 
 void level0_build(TopoImpl &T, cudaStream_t s) {
@@ -304,7 +338,7 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     launch_pdl(k_faces, grid_for(F), kBlock, s, F, (const int *)M.d_off, (const int *)M.d_fv, T.cf0, T.nx0, T.pv0,
                T.deg, reinterpret_cast<unsigned *>(T.vc0), T.dir, T.status);
     const unsigned nb = grid_for(nnz);
-    const bool open = M.scheme != ALSUB_SQRT3;          // sqrt(3) has no boundary rule
+    const bool open = M.scheme != ALSUB_SQRT3 || M.B > 0;  // closed sqrt(3) meshes are checked closed
     launch_pdl(k_twin, nb, kBlock, s, nnz, (const int *)M.d_fv, (const int *)T.nx0, T.dir, open, L0.tw, T.own0,
                T.flags, T.status);
     T.launches += 5 + scan_exclusive(T.flags, T.pos, nb, T.e0count, nullptr, T.scan_tmp, s);
@@ -312,7 +346,7 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     launch_pdl(k_edges, grid_for(nnz), kBlock, s, nnz, (const int *)T.own0, (const int *)T.eid, (const int *)L0.tw,
                (const int *)T.pv0, (const int *)T.nx0, (const int *)M.d_off, (const int *)T.cf0,
                (const int *)T.e0count, E0, L0.ce, T.eo0, T.rn0, T.rec0, T.status);
-    if (L0.B > 0) {
+    if (L0.B > 0 && T.levels > 0 && M.scheme != ALSUB_SQRT3) {
         // (the list exists when a step follows: levels >= 1.) The per-corner edge-id temporaries
         // are dead: they map boundary corners to entries
         cudaMemsetAsync(T.bcount, 0, sizeof(int), s);
@@ -387,6 +421,7 @@ void level0_validate(TopoImpl &T, cudaStream_t s) {
 }
 
 void level0_creases(TopoImpl &T, cudaStream_t s) {
+    if (T.scheme == ALSUB_SQRT3) return;     // sqrt(3) creases are feature flags (s3f_level0)
     MeshImpl &M = *T.mesh;
     LevelBuf &L0 = T.L[0];
     CreaseList &C = L0.cr;
@@ -397,6 +432,20 @@ void level0_creases(TopoImpl &T, cudaStream_t s) {
         T.launches += 1;
     } else if (C.count) {
         cudaMemsetAsync(C.count, 0, sizeof(int), s);
+    }
+}
+
+void s3f_level0(TopoImpl &T, cudaStream_t s) {
+    MeshImpl &M = *T.mesh;
+    LevelBuf &L0 = T.L[0];
+    const int nnz = M.nnz;
+    launch_pdl(k_s3f_flags0, grid_for(nnz), kBlock, s, nnz, (const int *)L0.tw, T.flags);
+    T.launches += 2 + scan_exclusive(T.flags, T.pos, nnz, nullptr, nullptr, T.scan_tmp, s);
+    launch_pdl(k_s3f_rank0, grid_for(nnz), kBlock, s, nnz, (const int *)T.pos, L0.tw, L0.fe);
+    if (M.K > 0) {
+        launch_pdl(k_s3f_crease0, grid_for(M.K), kBlock, s, M.K, (const int *)M.d_cv, (const float *)M.d_cs, T.dir,
+                   (const int *)L0.tw, L0.fe, T.status);
+        T.launches += 1;
     }
 }
 

@@ -588,6 +588,9 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
         return report(ALSUB_ERR_INVALID_ARG, "flags must ask for ALSUB_OP_CHAIN and/or ALSUB_OP_COMPOSE");
     TopoImpl &T = *topology_impl(topo);
     if (!T.built) return report(ALSUB_ERR_INVALID_ARG, "topology not built");
+    if (T.s3f)
+        return report(ALSUB_ERR_UNSUPPORTED, "operator: sqrt(3) meshes with boundaries or infinitely sharp creases "
+                                             "are refined by the eval kernels only");
     cudaStream_t s = (cudaStream_t)stream;
     alsub_status st = ensure_helpers(T, s);
     if (st) return st;

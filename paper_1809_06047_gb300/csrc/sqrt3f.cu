@@ -1,0 +1,273 @@
+// sqrt(3) refinement with feature edges: boundaries and infinitely sharp creases (Appendix A gives
+// neither; the treatment follows Kobbelt 2000, Sec. 4). The closed-mesh kernels of tri.cu derive
+// every index from closed-form rules that assume every edge flips; a feature edge never flips, so
+// meshes with features take this general path, one step at a time with every level's arrays
+// stored:
+//   fv  triangle rows (3 ints), tw  per-corner twin (a boundary corner holds -1 - its rank among the
+//   level's boundary corners in corner order), fe  per-corner flag: the corner's edge is a feature.
+// Steps alternate, by the level they start from:
+//   first step of a pair (even level l): a face point at |v| + i for every triangle i; corner k of
+//     (k, l, m) gives (p_k, f_{F(l,k)}, f_i), or (p_k, p_l, f_i) when k -> l is a feature edge;
+//   second step (odd level l): a triangle with a feature edge a -> b (one at most, by construction)
+//     gets no face point; the edge splits into three at q1 (near a, in the triangle's slot |v| + i)
+//     and q2 (near b: the slot of the triangle across a crease, or |v| + |f| + rank for a boundary
+//     edge), and the triangle into (a, q1, c), (q1, q2, c), (q2, b, c); an edge flips only between
+//     two triangles with face points.
+// Positions: face points are barycenters; curve vertices (two feature edges) stay on the first step
+// and take (4, 19, 4) / 27 on the second, corners (three or more) stay, every other vertex takes Eq.
+// sqrt2; q1, q2 take the ternary cubic B-spline masks (1, 16, 10) / 27 and (10, 16, 1) / 27, the
+// neighbour beyond a curve end (a corner or a dart) read as its mirror 2 p_end - p_next.
+#include <math.h>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace alsub {
+
+namespace {
+
+struct S3Args {
+    int l, V, F;
+    bool odd;                        // first step of a pair (from an even level)
+    const int *fv, *tw, *fe;         // level l
+    int *vc;                         // per vertex of level l: its smallest outgoing corner
+    int4 *vi;                        // per vertex of level l: feature valency, feature neighbours
+    const float *P;
+    float *Pn;
+    bool in4, out4;
+    int *fvn, *twn, *fen;            // level l + 1
+    int *status;
+};
+
+__device__ __forceinline__ int t_next(int x) { const int q = x / 3; return 3 * q + (x - 3 * q == 2 ? 0 : x - 3 * q + 1); }
+__device__ __forceinline__ int t_prev(int x) { const int q = x / 3; return 3 * q + (x - 3 * q == 0 ? 2 : x - 3 * q - 1); }
+
+__global__ void __launch_bounds__(kBlock) k_s3f_desig(int nnz, const int *__restrict__ fv, int *vc) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x < nnz) atomicMin(vc + __ldg(fv + x), x);
+}
+
+// One vertex per designated corner: its ring (an open fan of a boundary vertex walked both ways),
+// its feature edges, and with EVAL its refined position.
+template <bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a, int nnz) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nnz || failed(a.status)) return;
+    const int v = __ldg(a.fv + x);
+    if (a.vc[v] != x) return;
+    int k = 0, n1 = -1, n2 = -1, n = 0;
+    float3 sum = f3(0.f, 0.f, 0.f);
+    auto neighbour = [&](int w, bool feature) {
+        if (EVAL) sum += ldpv(a.P, w, a.in4);
+        n++;
+        if (feature) {
+            if (k == 0) n1 = w;
+            else if (k == 1) n2 = w;
+            k++;
+        }
+    };
+    int y = x;
+    bool open = false;
+    do {
+        neighbour(__ldg(a.fv + t_next(y)), __ldg(a.fe + y) != 0);
+        const int t = __ldg(a.tw + t_prev(y));
+        if (t < 0) {
+            open = true;
+            break;
+        }
+        y = t;
+    } while (y != x && n < kMaxValence);
+    if (open) {
+        // the fan ends at an incoming boundary edge u -> v; then the corners before x
+        neighbour(__ldg(a.fv + t_prev(y)), true);
+        y = x;
+        while (n < kMaxValence) {
+            const int t = __ldg(a.tw + y);
+            if (t < 0) break;
+            y = t_next(t);
+            neighbour(__ldg(a.fv + t_next(y)), __ldg(a.fe + y) != 0);
+        }
+    }
+    if (n >= kMaxValence) {
+        set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+        return;
+    }
+    a.vi[v] = make_int4(k, n1, n2, 0);
+    if (!EVAL) return;
+    const float3 p = ldpv(a.P, v, a.in4);
+    float3 q;
+    if (k >= 3 || (a.odd && k == 2)) {
+        q = p;                                         // a corner; a curve vertex on a first step
+    } else if (k == 2) {
+        q = (4.0f / 27.0f) * (ldpv(a.P, n1, a.in4) + ldpv(a.P, n2, a.in4)) + (19.0f / 27.0f) * p;
+    } else {
+        const float al = (float)((4.0 - 2.0 * cos(2.0 * M_PI / (double)n)) / 9.0);
+        q = (1.0f - al) * p + (al / (float)n) * sum;
+    }
+    stpv(a.Pn, v, q, a.out4);
+}
+
+// Local index of the feature corner of triangle q on a second step, or -1 (then it has a face
+// point; on a first step every triangle has one).
+__device__ __forceinline__ int feature_corner(const S3Args &a, int q) {
+    if (a.odd) return -1;
+    const int f0 = __ldg(a.fe + 3 * q), f1 = __ldg(a.fe + 3 * q + 1), f2 = __ldg(a.fe + 3 * q + 2);
+    return f0 ? 0 : (f1 ? 1 : (f2 ? 2 : -1));
+}
+
+// The child corner that carries, on its own side, the unflipped edge of parent corner t (t >= 0):
+// corner 0 of the child of t when t's triangle has a face point; else corner 1 of the last child
+// (the edge b -> c) or corner 2 of the first (the edge c -> a) of its three-way split.
+__device__ __forceinline__ int carry(const S3Args &a, int t) {
+    const int q = t / 3, i = t - 3 * q, jq = feature_corner(a, q);
+    if (jq < 0) return 3 * t;
+    return i == (jq == 2 ? 0 : jq + 1) ? 3 * (3 * q + 2) + 1 : 3 * (3 * q) + 2;
+}
+
+// ternary cubic B-spline point of the feature edge a -> b nearer a: (beyond + 16 a + 10 b) / 27,
+// beyond = the feature neighbour of a other than b, or the mirror 2 a - b at a curve end
+__device__ __forceinline__ float3 third_point(const S3Args &a, int va, int vb, float3 pa, float3 pb) {
+    const int4 ia = a.vi[va];
+    float3 beyond;
+    if (ia.x == 2) beyond = ldpv(a.P, ia.y == vb ? ia.z : ia.y, a.in4);
+    else beyond = 2.0f * pa - pb;
+    return (1.0f / 27.0f) * beyond + (16.0f / 27.0f) * pa + (10.0f / 27.0f) * pb;
+}
+
+template <bool TOPO, bool EVAL>
+__global__ void __launch_bounds__(kBlock) k_s3f_tri(S3Args a) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.F || failed(a.status)) return;
+    const int c = 3 * r, V = a.V;
+    int vv[3], tt[3], ff[3];
+#pragma unroll
+    for (int j = 0; j < 3; j++) {
+        vv[j] = __ldg(a.fv + c + j);
+        tt[j] = __ldg(a.tw + c + j);
+        ff[j] = __ldg(a.fe + c + j);
+    }
+    const int jf = a.odd ? -1 : (ff[0] ? 0 : (ff[1] ? 1 : (ff[2] ? 2 : -1)));
+    if (jf < 0) {
+        // a face point: every corner's child, its edge flipped unless a feature or (second
+        // step) the triangle across has no face point
+        bool flip[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) flip[j] = !ff[j] && (a.odd || feature_corner(a, tt[j] / 3) < 0);
+        if (TOPO) {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                const int jn = j == 2 ? 0 : j + 1, jp = j == 0 ? 2 : j - 1, t = tt[j];
+                int *o = a.fvn + 3 * (size_t)(c + j);
+                o[0] = vv[j];
+                o[1] = flip[j] ? V + t / 3 : vv[jn];
+                o[2] = V + r;
+                int *w = a.twn + 3 * (size_t)(c + j);
+                w[0] = flip[j] ? 3 * t_next(t) + 2 : (t < 0 ? t : carry(a, t));
+                w[1] = flip[j] ? 3 * t + 1 : 3 * (c + jn) + 2;
+                w[2] = flip[jp] ? 3 * tt[jp] : 3 * (c + jp) + 1;
+                int *e = a.fen + 3 * (size_t)(c + j);
+                e[0] = ff[j];
+                e[1] = 0;
+                e[2] = 0;
+            }
+        }
+        if (EVAL) {
+            const float3 p0 = ldpv(a.P, vv[0], a.in4), p1 = ldpv(a.P, vv[1], a.in4), p2 = ldpv(a.P, vv[2], a.in4);
+            stpv(a.Pn, V + r, (1.0f / 3.0f) * (p0 + p1 + p2), a.out4);
+        }
+        return;
+    }
+    // second step, feature edge a -> b at corner jf, third vertex cc: split in three
+    const int jb = jf == 2 ? 0 : jf + 1, jc = jf == 0 ? 2 : jf - 1;
+    const int va = vv[jf], vb = vv[jb], vcc = vv[jc], tf = tt[jf];
+    const int rank = -1 - tf;                                  // a boundary edge's rank
+    const int q1 = V + r, q2 = tf >= 0 ? V + tf / 3 : V + a.F + rank;
+    if (TOPO) {
+        const int rows[9] = {va, q1, vcc, q1, q2, vcc, q2, vb, vcc};
+        int *o = a.fvn + 3 * (size_t)c;
+#pragma unroll
+        for (int i = 0; i < 9; i++) o[i] = rows[i];
+        const int rf = tf / 3;
+        const int tw0[3] = {tf >= 0 ? 3 * (3 * rf + 2) : -1 - 3 * rank, tf >= 0 ? 3 * (3 * rf + 1) : -2 - 3 * rank,
+                            tf >= 0 ? 3 * (3 * rf) : -3 - 3 * rank};
+        int *w = a.twn + 3 * (size_t)c;
+        w[0] = tw0[0]; w[1] = 3 * (c + 1) + 2; w[2] = carry(a, tt[jc]);
+        w[3] = tw0[1]; w[4] = 3 * (c + 2) + 2; w[5] = 3 * c + 1;
+        w[6] = tw0[2]; w[7] = carry(a, tt[jb]); w[8] = 3 * (c + 1) + 1;
+        int *e = a.fen + 3 * (size_t)c;
+#pragma unroll
+        for (int i = 0; i < 9; i++) e[i] = i % 3 == 0;
+    }
+    if (EVAL) {
+        const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
+        stpv(a.Pn, q1, third_point(a, va, vb, pa, pb), a.out4);
+        if (tf < 0) stpv(a.Pn, q2, third_point(a, vb, va, pb, pa), a.out4);
+    }
+}
+
+// The crease edges of a level (feature edges that are not boundary edges), once each from the
+// smaller of their two corners, appended to the level's export list (any order).
+__global__ void __launch_bounds__(kBlock) k_s3f_export(int nnz, const int *__restrict__ fv, const int *__restrict__ tw,
+                                                      const int *__restrict__ fe, int cap, int *count, int *verts,
+                                                      float *sig) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nnz) return;
+    const int t = __ldg(tw + x);
+    if (!__ldg(fe + x) || t < 0 || t < x) return;
+    const int i = atomicAdd(count, 1);
+    if (i >= cap) return;
+    verts[2 * i] = __ldg(fv + x);
+    verts[2 * i + 1] = __ldg(fv + t_next(x));
+    sig[i] = INFINITY;
+}
+
+}  // namespace
+
+}  // namespace alsub
+
+namespace alsub {
+
+void s3f_step(TopoImpl &T, int l, bool topo, const float *P, float *Pn, cudaStream_t s) {
+    const LevelBuf &A = T.L[l];
+    LevelBuf &B = T.L[l + 1];
+    const bool ev = P != nullptr;
+    if (!topo && !ev) return;
+    S3Args a;
+    a.l = l;
+    a.V = (int)A.V;
+    a.F = (int)A.F;
+    a.odd = (l & 1) == 0;
+    a.fv = A.fv; a.tw = A.tw; a.fe = A.fe;
+    a.vc = T.s3_vc;
+    a.vi = T.s3_vi;
+    a.P = P; a.Pn = Pn;
+    a.in4 = l > 0;
+    a.out4 = l + 1 < T.levels;
+    a.fvn = B.fv; a.twn = B.tw; a.fen = B.fe;
+    a.status = T.status;
+    const int nnz = (int)A.nnz;
+    if (ev) {
+        // designated corners, then the vertices (their positions and feature neighbours)
+        cudaMemsetAsync(T.s3_vc, 0x7f, sizeof(int) * (size_t)A.V, s);
+        k_s3f_desig<<<grid_for(nnz), kBlock, 0, s>>>(nnz, A.fv, T.s3_vc);
+        k_s3f_vert<true><<<grid_for(nnz), kBlock, 0, s>>>(a, nnz);
+        T.launches += 2;
+    }
+    const unsigned g = grid_for(a.F);
+    if (topo && ev) k_s3f_tri<true, true><<<g, kBlock, 0, s>>>(a);
+    else if (topo) k_s3f_tri<true, false><<<g, kBlock, 0, s>>>(a);
+    else k_s3f_tri<false, true><<<g, kBlock, 0, s>>>(a);
+    T.launches += 1;
+}
+
+int s3f_export(TopoImpl &T, int l, cudaStream_t s) {
+    CreaseList &C = T.L[l].cr;
+    if (C.cap == 0) return 0;
+    const LevelBuf &A = T.L[l];
+    cudaMemsetAsync(C.xcount, 0, sizeof(int), s);
+    k_s3f_export<<<grid_for(A.nnz), kBlock, 0, s>>>((int)A.nnz, A.fv, A.tw, A.fe, (int)C.cap, C.xcount, C.xverts,
+                                                   C.xsig);
+    return 1;
+}
+
+}  // namespace alsub

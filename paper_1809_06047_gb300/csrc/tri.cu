@@ -568,6 +568,10 @@ void loop_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, floa
 }
 
 void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float *Pn, cudaStream_t s) {
+    if (T.s3f) {
+        s3f_step(T, l, topo, P, Pn, s);
+        return;
+    }
     TriArgs a = make_args(T, l, P, Pn);
     unsigned g = grid_for(a.F);
     bool ev = P != nullptr;

@@ -63,7 +63,9 @@ def vertex_maps(scheme: str, faces_a: list, faces_b: list, counts: list) -> list
         else:
             base, emap = None, None
         if scheme == "sqrt3":
-            nxt = np.concatenate([pi[l], np.arange(V, V + F)])
+            # face points (and the feature-edge points in the triangles' slots), then the second
+            # points of boundary edges split on a second step (ranked alike on both sides)
+            nxt = np.concatenate([pi[l], np.arange(V, counts[l + 1]["V"])])
         elif scheme == "cc":
             nxt = np.concatenate([pi[l], np.arange(V, V + F), base + emap])
         else:
@@ -129,7 +131,7 @@ def relabel(scheme: str, levels: list, seed: int) -> list:
         elif scheme == "loop":
             nperm = np.concatenate([perm, V + ep])
         else:
-            nperm = np.concatenate([perm, np.arange(V, V + F)])
+            nperm = np.concatenate([perm, np.arange(V, b["V"])])
         d = dict(b)
         d["fv"] = nperm[np.asarray(b["fv"], dtype=np.int64)].astype(np.int32)
         P = np.empty_like(b["P"])

@@ -75,7 +75,7 @@ def test_plan_rejects():
 ])
 def test_plan_open_against_the_oracle(scheme, mesh):
     """Level counts of open meshes (E0 = (nnz + B) / 2, each boundary edge splitting in two)
-    against the oracle's own counts; sqrt(3) refuses a boundary (no rule in Appendix A)."""
+    against the oracle's own counts, for sqrt(3) too (two kinds of step, Kobbelt 2000)."""
     m = mesh()
     off, fv = np.asarray(m["off"]), np.asarray(m["fv"])
     d = set()
@@ -89,9 +89,12 @@ def test_plan_open_against_the_oracle(scheme, mesh):
     for l, r in enumerate(ref):
         assert tuple(counts[l]) == (r["V"], r["F"], r["nnz"], r["E"])
     if scheme == "loop":
-        with pytest.raises(alsub.AlsubError) as e:
-            alsub.plan("sqrt3", m["V"], m["F"], len(fv), 1, boundary=B)
-        assert e.value.status == 3
+        # sqrt(3) (Kobbelt's boundary treatment): its own counts against the oracle's, over two
+        # pairs of steps
+        counts = alsub.plan("sqrt3", m["V"], m["F"], len(fv), 4, boundary=B)
+        ref = oracle.subdivide(m, 4, "sqrt3", keep_all=True)
+        for l, r in enumerate(ref):
+            assert tuple(counts[l]) == (r["V"], r["F"], r["nnz"], r["E"])
 
 
 def _create(scheme, V, F, fv, off=None, cv=None, cs=None):
@@ -120,10 +123,9 @@ def test_mesh_validation_on_host():
     with pytest.raises(alsub.AlsubError) as e:           # NaN sharpness
         _create("cc", 8, 6, c["fv"], c["off"], np.array([[0, 1]]), np.array([np.nan]))
     assert e.value.status == 1
-    with pytest.raises(alsub.AlsubError) as e:           # open sqrt(3) mesh: odd corner count
-        t = synth.tetrahedron()
-        _create("sqrt3", 4, 3, t["fv"][:9], t["off"][:4])
-    assert e.value.status in (1, 3)
+    with pytest.raises(alsub.AlsubError) as e:           # a sqrt(3) face that is not a triangle
+        _create("sqrt3", 8, 6, c["fv"], c["off"])
+    assert e.value.status == 1
 
 
 def test_last_error_message():
@@ -144,10 +146,12 @@ def test_plan_bytes_host_only():
     K = len(m["crease_sharp"])
     with_creases = alsub.plan_bytes("cc", m["V"], m["F"], nnz, 3, K, float(m["crease_sharp"].max()))
     assert with_creases > sizes[3]
-    # sqrt(3) has no crease rules: creases cost nothing
+    # sqrt(3) keeps infinitely sharp creases only (the feature path stores every level): finite
+    # sharpness costs nothing, infinite sharpness takes the feature path's arrays
     t = synth.torus_tri(10, 10, seed=6)
-    assert (alsub.plan_bytes("sqrt3", t["V"], t["F"], len(t["fv"]), 3, 50, float("inf"))
-            == alsub.plan_bytes("sqrt3", t["V"], t["F"], len(t["fv"]), 3))
+    plain = alsub.plan_bytes("sqrt3", t["V"], t["F"], len(t["fv"]), 3)
+    assert alsub.plan_bytes("sqrt3", t["V"], t["F"], len(t["fv"]), 3, 50, 3.5) == plain
+    assert alsub.plan_bytes("sqrt3", t["V"], t["F"], len(t["fv"]), 3, 50, float("inf")) > plain
     for bad in [dict(nnz=nnz + 1), dict(levels=-1)]:
         with pytest.raises(alsub.AlsubError):
             alsub.plan_bytes("cc", m["V"], m["F"], bad.get("nnz", nnz), bad.get("levels", 2))

@@ -158,10 +158,15 @@ def test_open_mesh_errors():
     assert e.value.status == 3
     o = synth.octahedron()
     open_tri = dict(o, F=6, off=o["off"][:7], fv=o["fv"][:18])
-    with pytest.raises(alsub.AlsubError) as e:     # Appendix A omits the sqrt(3) boundary rule
-        M = alsub.Mesh.from_dict(open_tri, "sqrt3")
-        T = alsub.Topology(M, 1, build=True)
-        T.status()
+    # sqrt(3): Kobbelt's boundary treatment (the feature path); a sharp crease at its boundary is
+    # refused as for the other schemes
+    M = alsub.Mesh.from_dict(open_tri, "sqrt3")
+    assert M.boundary_edges == 4
+    M.close()
+    t = synth.triangulate(box)
+    with pytest.raises(alsub.AlsubError) as e:
+        alsub.Mesh.from_dict(dict(t, crease_verts=np.array([[rim[0], rim[1]]], np.int32),
+                                  crease_sharp=np.array([np.inf], np.float32)), "sqrt3")
     assert e.value.status == 3
     M = alsub.Mesh.from_dict(open_tri, "loop")     # Loop: the rules of Eq. CC_boundary
     assert M.boundary_edges == 4

@@ -21,9 +21,9 @@ pytestmark = pytest.mark.gpu
 N_SAMPLES = 4096
 
 
-def _compare(scheme, parent, child, faces):
+def _compare(scheme, parent, child, faces, level=0):
     pm, local = patch.extract(parent, faces)
-    part = oracle.subdivide(pm, 1, scheme, patch=True)[1]
+    part = oracle.subdivide(pm, 1, scheme, patch=True, start_level=level)[1]
     diag = float(np.linalg.norm(child["P"].max(0) - child["P"].min(0)))
     worst = 0.0
     for r, q in zip(faces, local):
@@ -86,8 +86,8 @@ def _triangle_step_sampled(name, scheme, L):
     c = T.counts[-1]
     parent = dict(V=c["V"], F=c["F"], fv=T.faces(L - 1), off=np.arange(c["F"] + 1, dtype=np.int64) * 3,
                   P=P.cpu().numpy().astype(np.float64))
-    if scheme == "loop":
-        parent["crease_verts"], parent["crease_sharp"] = T.creases(L - 1)
+    # Loop creases, and sqrt(3)'s infinitely sharp ones (feature edges)
+    parent["crease_verts"], parent["crease_sharp"] = T.creases(L - 1)
     T.close()
     del P
     T = alsub.Topology(M, L, build=False)
@@ -98,4 +98,4 @@ def _triangle_step_sampled(name, scheme, L):
     child = dict(fv=T.faces(L), P=PL.cpu().numpy().astype(np.float64))
     T.close()
     faces = patch.sample_faces(parent["F"], N_SAMPLES, seed=72)
-    _compare(scheme, parent, child, faces)
+    _compare(scheme, parent, child, faces, level=L - 1)
