@@ -223,7 +223,10 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
         long long K = M.K, vmax3 = 1;
         for (int l = 0; l <= levels; l++) {
             LevelBuf &A = T.L[l];
-            AL(A.fe, A.nnz);
+            if (l < levels) {
+                AL(A.fm, A.F);
+                if (l > 0) AL(A.vc, A.V);
+            }
             A.cr.cap = K;
             if (K > 0) {
                 AL(A.cr.xverts, 2 * K);
@@ -233,7 +236,6 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
             if (l < levels) vmax3 = std::max(vmax3, A.V);
             K = (l & 1) ? 3 * K : K;
         }
-        AL(T.s3_vc, vmax3);
         AL(T.s3_vi, vmax3);
     }
     long long nflags = std::max<long long>({(long long)nnz, (long long)E0, 2 * maxcap, 1});
@@ -259,7 +261,7 @@ alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
         // Loop and sqrt(3): the last step derives its level's edge ids and twins from the parent
         // level (crease analysis included); its vertex rings are read from the parent level.
         if (!cc && l == levels - 1 && l >= 1) B.helpers = false;
-        if (T.s3f) B.helpers = true;       // the general sqrt(3) path stores every level's twins
+        if (T.s3f) B.helpers = l < levels; // the general sqrt(3) path stores the twins below the last
         if (B.helpers) {
             if (M.scheme != ALSUB_SQRT3) AL(B.ce, B.nnz);
             AL(B.tw, B.nnz);

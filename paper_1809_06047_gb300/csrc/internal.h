@@ -42,7 +42,10 @@ struct LevelBuf {
     int *ce = nullptr;
     int *tw = nullptr;
     bool helpers = false;  // ce and tw are stored for this level
-    int *fe = nullptr;     // sqrt(3) with feature edges: 1 where the corner's edge is a feature edge
+    // sqrt(3) with feature edges, levels below the last: per triangle, bit j set when corner j's
+    // edge is a feature edge; per vertex, one of its outgoing corners (level 0: TopoImpl::vc0)
+    unsigned char *fm = nullptr;
+    int *vc = nullptr;
     CreaseList cr;
     // boundary list of an open Catmull-Clark or Loop mesh (levels below the last): entry i is a boundary
     // edge a -> b of this level with a = bA[i], edge id bE[i] and bS[i] = the entry of the next
@@ -115,7 +118,6 @@ struct TopoImpl {
     // sqrt(3) with feature edges (boundary edges, infinitely sharp creases): the general path of
     // sqrt3f.cu, with per-vertex scratch for the largest level a step starts from
     bool s3f = false;
-    int *s3_vc = nullptr;        // designated corner of every vertex
     int4 *s3_vi = nullptr;       // feature valency and feature neighbours of every vertex
     DirTable dir;
     int *eid = nullptr, *e0count = nullptr;
@@ -227,8 +229,9 @@ void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, flo
 
 // sqrt(3) with feature edges (sqrt3f.cu). s3f_level0: after level0_build, the boundary corners'
 // twins become -1 - rank (rank in corner order) and the per-corner feature flags of level 0 are set
-// (boundary edges, infinitely sharp creases). s3f_step: one step l -> l + 1 (topology and/or
-// positions). s3f_export: level l's crease edges into its export list (returns the launches).
+// and crease list (boundary edges, infinitely sharp creases). s3f_step: one step l -> l + 1
+// (topology and/or positions). s3f_export: nothing to do (the steps keep every level's crease list
+// current; returns the launches).
 void s3f_level0(TopoImpl &T, cudaStream_t s);
 void s3f_step(TopoImpl &T, int l, bool topo, const float *P, float *Pn, cudaStream_t s);
 int s3f_export(TopoImpl &T, int l, cudaStream_t s);

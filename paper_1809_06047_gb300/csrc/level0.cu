@@ -293,9 +293,10 @@ __global__ void k_crease0(int K, const int *__restrict__ cv, const float *__rest
 }
 
 // sqrt(3) with feature edges, level 0 (the general path of sqrt3f.cu): the boundary corners (twin
-// -1) are ranked in corner order by a scan of their flags; their twins become -1 - rank and every
-// corner's feature flag is set: boundary corners, then both corners of every infinitely sharp
-// crease (a crease that is not an edge is an input error).
+// -1) are ranked in corner order by a scan of their flags and their twins become -1 - rank; the
+// flags then also mark both corners of every infinitely sharp crease (a crease that is not an edge
+// is an input error), which also enter the level's crease list; each triangle's flags become its
+// feature bits.
 __global__ void k_s3f_flags0(int nnz, const int *__restrict__ tw, int *flag) {
     pdl_wait();
     pdl_trigger();
@@ -303,27 +304,39 @@ __global__ void k_s3f_flags0(int nnz, const int *__restrict__ tw, int *flag) {
     if (x < nnz) flag[x] = tw[x] < 0;
 }
 
-__global__ void k_s3f_rank0(int nnz, const int *__restrict__ pos, int *tw, int *fe) {
+__global__ void k_s3f_rank0(int nnz, const int *__restrict__ pos, int *tw) {
     pdl_wait();
     pdl_trigger();
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nnz) return;
     const int t = tw[x];
     if (t < 0) tw[x] = -1 - pos[x];
-    fe[x] = t < 0;
 }
 
 __global__ void k_s3f_crease0(int K, const int *__restrict__ cv, const float *__restrict__ cs, DirTable tab,
-                              const int *__restrict__ tw, int *fe, int *status) {
+                              const int *__restrict__ tw, int *flag, int *xcount, int *xverts, float *xsig,
+                              int *status) {
     pdl_wait();
     pdl_trigger();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= K || !isinf(cs[i])) return;
-    const int x = dir_find(tab, cv[2 * i], cv[2 * i + 1]);
+    if (i == 0) *xcount = K;
+    if (i >= K) return;
+    const int a = cv[2 * i], b = cv[2 * i + 1];
+    xverts[2 * i] = a;
+    xverts[2 * i + 1] = b;
+    xsig[i] = cs[i];
+    const int x = dir_find(tab, a, b);
     if (x < 0) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
-    fe[x] = 1;
+    flag[x] = 1;
     const int t = tw[x];
-    if (t >= 0) fe[t] = 1;
+    if (t >= 0) flag[t] = 1;
+}
+
+__global__ void k_s3f_mask0(int F, const int *__restrict__ flag, unsigned char *fm) {
+    pdl_wait();
+    pdl_trigger();
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < F) fm[q] = (unsigned char)(flag[3 * q] | flag[3 * q + 1] << 1 | flag[3 * q + 2] << 2);
 }
 
 }  // namespace
@@ -440,13 +453,14 @@ void s3f_level0(TopoImpl &T, cudaStream_t s) {
     LevelBuf &L0 = T.L[0];
     const int nnz = M.nnz;
     launch_pdl(k_s3f_flags0, grid_for(nnz), kBlock, s, nnz, (const int *)L0.tw, T.flags);
-    T.launches += 2 + scan_exclusive(T.flags, T.pos, nnz, nullptr, nullptr, T.scan_tmp, s);
-    launch_pdl(k_s3f_rank0, grid_for(nnz), kBlock, s, nnz, (const int *)T.pos, L0.tw, L0.fe);
+    T.launches += 3 + scan_exclusive(T.flags, T.pos, nnz, nullptr, nullptr, T.scan_tmp, s);
+    launch_pdl(k_s3f_rank0, grid_for(nnz), kBlock, s, nnz, (const int *)T.pos, L0.tw);
     if (M.K > 0) {
         launch_pdl(k_s3f_crease0, grid_for(M.K), kBlock, s, M.K, (const int *)M.d_cv, (const float *)M.d_cs, T.dir,
-                   (const int *)L0.tw, L0.fe, T.status);
+                   (const int *)L0.tw, T.flags, L0.cr.xcount, L0.cr.xverts, L0.cr.xsig, T.status);
         T.launches += 1;
     }
+    if (L0.fm) launch_pdl(k_s3f_mask0, grid_for(M.F), kBlock, s, M.F, (const int *)T.flags, L0.fm);
 }
 
 }  // namespace alsub

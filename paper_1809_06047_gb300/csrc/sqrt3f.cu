@@ -1,10 +1,13 @@
 // sqrt(3) refinement with feature edges: boundaries and infinitely sharp creases (Appendix A gives
 // neither; the treatment follows Kobbelt 2000, Sec. 4). The closed-mesh kernels of tri.cu derive
 // every index from closed-form rules that assume every edge flips; a feature edge never flips, so
-// meshes with features take this general path, one step at a time with every level's arrays
-// stored:
-//   fv  triangle rows (3 ints), tw  per-corner twin (a boundary corner holds -1 - its rank among the
-//   level's boundary corners in corner order), fe  per-corner flag: the corner's edge is a feature.
+// meshes with features take this general path, one step at a time with the arrays of every level
+// below the last stored:
+//   fv  triangle rows (3 ints); tw  per-corner twin (a boundary corner holds -1 - its rank among the
+//   level's boundary corners in corner order); fm  per-triangle byte, bit j set when corner j's
+//   edge is a feature edge; vc  per vertex, one of its outgoing corners (the level-0 designated
+//   corner, then carried to the child that keeps the vertex, so no search is needed); and the
+//   level's crease edges as a list (appended by the step that makes the level).
 // Steps alternate, by the level they start from:
 //   first step of a pair (even level l): a face point at |v| + i for every triangle i; corner k of
 //     (k, l, m) gives (p_k, f_{F(l,k)}, f_i), or (p_k, p_l, f_i) when k -> l is a feature edge;
@@ -17,6 +20,9 @@
 // and take (4, 19, 4) / 27 on the second, corners (three or more) stay, every other vertex takes Eq.
 // sqrt2; q1, q2 take the ternary cubic B-spline masks (1, 16, 10) / 27 and (10, 16, 1) / 27, the
 // neighbour beyond a curve end (a corner or a dart) read as its mirror 2 p_end - p_next.
+// Per step: a vertex pass (one thread per vertex: its ring from its corner, its feature neighbours,
+// its position) and a triangle pass (one thread per triangle: children, their twins, flags and
+// corners, the level's crease list, face points and feature-edge points).
 #include <math.h>
 
 #include "common.cuh"
@@ -29,32 +35,34 @@ namespace {
 struct S3Args {
     int l, V, F;
     bool odd;                        // first step of a pair (from an even level)
-    const int *fv, *tw, *fe;         // level l
-    int *vc;                         // per vertex of level l: its smallest outgoing corner
+    const int *fv, *tw, *vc;         // level l
+    const unsigned char *fm;
     int4 *vi;                        // per vertex of level l: feature valency, feature neighbours
     const float *P;
     float *Pn;
     bool in4, out4;
-    int *fvn, *twn, *fen;            // level l + 1
+    int *fvn, *twn, *vcn;            // level l + 1 (twn, fmn, vcn null when it is the last level)
+    unsigned char *fmn;
+    int *ccount, *cverts;            // level l + 1's crease list
+    float *csig;
+    int ccap;
     int *status;
 };
 
 __device__ __forceinline__ int t_next(int x) { const int q = x / 3; return 3 * q + (x - 3 * q == 2 ? 0 : x - 3 * q + 1); }
 __device__ __forceinline__ int t_prev(int x) { const int q = x / 3; return 3 * q + (x - 3 * q == 0 ? 2 : x - 3 * q - 1); }
-
-__global__ void __launch_bounds__(kBlock) k_s3f_desig(int nnz, const int *__restrict__ fv, int *vc) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < nnz) atomicMin(vc + __ldg(fv + x), x);
+__device__ __forceinline__ bool feat(const unsigned char *fm, int x) {
+    const int q = x / 3;
+    return (__ldg(fm + q) >> (x - 3 * q)) & 1;
 }
 
-// One vertex per designated corner: its ring (an open fan of a boundary vertex walked both ways),
-// its feature edges, and with EVAL its refined position.
+// One vertex per thread: its ring from its corner (the open fan of a boundary vertex walked both
+// ways), its feature edges, and with EVAL its refined position.
 template <bool EVAL>
-__global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a, int nnz) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= nnz || failed(a.status)) return;
-    const int v = __ldg(a.fv + x);
-    if (a.vc[v] != x) return;
+__global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a) {
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.V || failed(a.status)) return;
+    const int x = __ldg(a.vc + v);
     int k = 0, n1 = -1, n2 = -1, n = 0;
     float3 sum = f3(0.f, 0.f, 0.f);
     auto neighbour = [&](int w, bool feature) {
@@ -69,7 +77,7 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a, int nnz) {
     int y = x;
     bool open = false;
     do {
-        neighbour(__ldg(a.fv + t_next(y)), __ldg(a.fe + y) != 0);
+        neighbour(__ldg(a.fv + t_next(y)), feat(a.fm, y));
         const int t = __ldg(a.tw + t_prev(y));
         if (t < 0) {
             open = true;
@@ -85,7 +93,7 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a, int nnz) {
             const int t = __ldg(a.tw + y);
             if (t < 0) break;
             y = t_next(t);
-            neighbour(__ldg(a.fv + t_next(y)), __ldg(a.fe + y) != 0);
+            neighbour(__ldg(a.fv + t_next(y)), feat(a.fm, y));
         }
     }
     if (n >= kMaxValence) {
@@ -111,8 +119,8 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a, int nnz) {
 // point; on a first step every triangle has one).
 __device__ __forceinline__ int feature_corner(const S3Args &a, int q) {
     if (a.odd) return -1;
-    const int f0 = __ldg(a.fe + 3 * q), f1 = __ldg(a.fe + 3 * q + 1), f2 = __ldg(a.fe + 3 * q + 2);
-    return f0 ? 0 : (f1 ? 1 : (f2 ? 2 : -1));
+    const int m = __ldg(a.fm + q);
+    return m & 1 ? 0 : (m & 2 ? 1 : (m & 4 ? 2 : -1));
 }
 
 // The child corner that carries, on its own side, the unflipped edge of parent corner t (t >= 0):
@@ -134,42 +142,53 @@ __device__ __forceinline__ float3 third_point(const S3Args &a, int va, int vb, f
     return (1.0f / 27.0f) * beyond + (16.0f / 27.0f) * pa + (10.0f / 27.0f) * pb;
 }
 
+__device__ __forceinline__ void push_crease(const S3Args &a, int u, int w) {
+    const int i = atomicAdd(a.ccount, 1);
+    if (i >= a.ccap) return;
+    a.cverts[2 * i] = u;
+    a.cverts[2 * i + 1] = w;
+    a.csig[i] = INFINITY;
+}
+
 template <bool TOPO, bool EVAL>
 __global__ void __launch_bounds__(kBlock) k_s3f_tri(S3Args a) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.F || failed(a.status)) return;
     const int c = 3 * r, V = a.V;
-    int vv[3], tt[3], ff[3];
+    const int mask = __ldg(a.fm + r);
+    int vv[3], tt[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         vv[j] = __ldg(a.fv + c + j);
         tt[j] = __ldg(a.tw + c + j);
-        ff[j] = __ldg(a.fe + c + j);
     }
-    const int jf = a.odd ? -1 : (ff[0] ? 0 : (ff[1] ? 1 : (ff[2] ? 2 : -1)));
+    const bool helpers = TOPO && a.twn;        // the child level is not the last one
+    const int jf = a.odd ? -1 : (mask & 1 ? 0 : (mask & 2 ? 1 : (mask & 4 ? 2 : -1)));
     if (jf < 0) {
         // a face point: every corner's child, its edge flipped unless a feature or (second
         // step) the triangle across has no face point
         bool flip[3];
 #pragma unroll
-        for (int j = 0; j < 3; j++) flip[j] = !ff[j] && (a.odd || feature_corner(a, tt[j] / 3) < 0);
+        for (int j = 0; j < 3; j++) flip[j] = !((mask >> j) & 1) && (a.odd || feature_corner(a, tt[j] / 3) < 0);
         if (TOPO) {
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 const int jn = j == 2 ? 0 : j + 1, jp = j == 0 ? 2 : j - 1, t = tt[j];
+                const bool fj = (mask >> j) & 1;
                 int *o = a.fvn + 3 * (size_t)(c + j);
                 o[0] = vv[j];
                 o[1] = flip[j] ? V + t / 3 : vv[jn];
                 o[2] = V + r;
+                if (fj && t >= 0 && c + j < t) push_crease(a, vv[j], vv[jn]);   // a kept crease edge
+                if (!helpers) continue;
                 int *w = a.twn + 3 * (size_t)(c + j);
                 w[0] = flip[j] ? 3 * t_next(t) + 2 : (t < 0 ? t : carry(a, t));
                 w[1] = flip[j] ? 3 * t + 1 : 3 * (c + jn) + 2;
                 w[2] = flip[jp] ? 3 * tt[jp] : 3 * (c + jp) + 1;
-                int *e = a.fen + 3 * (size_t)(c + j);
-                e[0] = ff[j];
-                e[1] = 0;
-                e[2] = 0;
+                a.fmn[c + j] = fj ? 1 : 0;
+                if (__ldg(a.vc + vv[j]) == c + j) a.vcn[vv[j]] = 3 * (c + j);
             }
+            if (helpers) a.vcn[V + r] = 3 * c + 2;               // the face point: child 0, corner 2
         }
         if (EVAL) {
             const float3 p0 = ldpv(a.P, vv[0], a.in4), p1 = ldpv(a.P, vv[1], a.in4), p2 = ldpv(a.P, vv[2], a.in4);
@@ -187,38 +206,33 @@ __global__ void __launch_bounds__(kBlock) k_s3f_tri(S3Args a) {
         int *o = a.fvn + 3 * (size_t)c;
 #pragma unroll
         for (int i = 0; i < 9; i++) o[i] = rows[i];
-        const int rf = tf / 3;
-        const int tw0[3] = {tf >= 0 ? 3 * (3 * rf + 2) : -1 - 3 * rank, tf >= 0 ? 3 * (3 * rf + 1) : -2 - 3 * rank,
-                            tf >= 0 ? 3 * (3 * rf) : -3 - 3 * rank};
-        int *w = a.twn + 3 * (size_t)c;
-        w[0] = tw0[0]; w[1] = 3 * (c + 1) + 2; w[2] = carry(a, tt[jc]);
-        w[3] = tw0[1]; w[4] = 3 * (c + 2) + 2; w[5] = 3 * c + 1;
-        w[6] = tw0[2]; w[7] = carry(a, tt[jb]); w[8] = 3 * (c + 1) + 1;
-        int *e = a.fen + 3 * (size_t)c;
-#pragma unroll
-        for (int i = 0; i < 9; i++) e[i] = i % 3 == 0;
+        if (tf >= 0 && c + jf < tf) {                          // the crease edge's three pieces
+            push_crease(a, va, q1);
+            push_crease(a, q1, q2);
+            push_crease(a, q2, vb);
+        }
+        if (helpers) {
+            const int rf = tf / 3;
+            const int tw0[3] = {tf >= 0 ? 3 * (3 * rf + 2) : -1 - 3 * rank, tf >= 0 ? 3 * (3 * rf + 1) : -2 - 3 * rank,
+                                tf >= 0 ? 3 * (3 * rf) : -3 - 3 * rank};
+            int *w = a.twn + 3 * (size_t)c;
+            w[0] = tw0[0]; w[1] = 3 * (c + 1) + 2; w[2] = carry(a, tt[jc]);
+            w[3] = tw0[1]; w[4] = 3 * (c + 2) + 2; w[5] = 3 * c + 1;
+            w[6] = tw0[2]; w[7] = carry(a, tt[jb]); w[8] = 3 * (c + 1) + 1;
+            a.fmn[c] = 1; a.fmn[c + 1] = 1; a.fmn[c + 2] = 1;
+            // carried corners: a at child 0 corner 0, b at child 2 corner 1, cc at child 0 corner 2
+            if (__ldg(a.vc + va) == c + jf) a.vcn[va] = 3 * c;
+            if (__ldg(a.vc + vb) == c + jb) a.vcn[vb] = 3 * (c + 2) + 1;
+            if (__ldg(a.vc + vcc) == c + jc) a.vcn[vcc] = 3 * c + 2;
+            a.vcn[q1] = 3 * c + 1;                             // q1: child 0, corner 1
+            if (tf < 0) a.vcn[q2] = 3 * (c + 1) + 1;           // a boundary q2: child 1, corner 1
+        }
     }
     if (EVAL) {
         const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
         stpv(a.Pn, q1, third_point(a, va, vb, pa, pb), a.out4);
         if (tf < 0) stpv(a.Pn, q2, third_point(a, vb, va, pb, pa), a.out4);
     }
-}
-
-// The crease edges of a level (feature edges that are not boundary edges), once each from the
-// smaller of their two corners, appended to the level's export list (any order).
-__global__ void __launch_bounds__(kBlock) k_s3f_export(int nnz, const int *__restrict__ fv, const int *__restrict__ tw,
-                                                      const int *__restrict__ fe, int cap, int *count, int *verts,
-                                                      float *sig) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= nnz) return;
-    const int t = __ldg(tw + x);
-    if (!__ldg(fe + x) || t < 0 || t < x) return;
-    const int i = atomicAdd(count, 1);
-    if (i >= cap) return;
-    verts[2 * i] = __ldg(fv + x);
-    verts[2 * i + 1] = __ldg(fv + t_next(x));
-    sig[i] = INFINITY;
 }
 
 }  // namespace
@@ -232,26 +246,29 @@ void s3f_step(TopoImpl &T, int l, bool topo, const float *P, float *Pn, cudaStre
     LevelBuf &B = T.L[l + 1];
     const bool ev = P != nullptr;
     if (!topo && !ev) return;
+    const bool last = l + 1 == T.levels;
     S3Args a;
     a.l = l;
     a.V = (int)A.V;
     a.F = (int)A.F;
     a.odd = (l & 1) == 0;
-    a.fv = A.fv; a.tw = A.tw; a.fe = A.fe;
-    a.vc = T.s3_vc;
+    a.fv = A.fv; a.tw = A.tw; a.fm = A.fm;
+    a.vc = l == 0 ? T.vc0 : A.vc;
     a.vi = T.s3_vi;
     a.P = P; a.Pn = Pn;
     a.in4 = l > 0;
-    a.out4 = l + 1 < T.levels;
-    a.fvn = B.fv; a.twn = B.tw; a.fen = B.fe;
+    a.out4 = !last;
+    a.fvn = B.fv;
+    a.twn = last ? nullptr : B.tw;
+    a.fmn = last ? nullptr : B.fm;
+    a.vcn = last ? nullptr : B.vc;
+    a.ccount = B.cr.xcount; a.cverts = B.cr.xverts; a.csig = B.cr.xsig;
+    a.ccap = (int)B.cr.cap;
     a.status = T.status;
-    const int nnz = (int)A.nnz;
+    if (topo && B.cr.cap > 0) cudaMemsetAsync(B.cr.xcount, 0, sizeof(int), s);
     if (ev) {
-        // designated corners, then the vertices (their positions and feature neighbours)
-        cudaMemsetAsync(T.s3_vc, 0x7f, sizeof(int) * (size_t)A.V, s);
-        k_s3f_desig<<<grid_for(nnz), kBlock, 0, s>>>(nnz, A.fv, T.s3_vc);
-        k_s3f_vert<true><<<grid_for(nnz), kBlock, 0, s>>>(a, nnz);
-        T.launches += 2;
+        k_s3f_vert<true><<<grid_for(a.V), kBlock, 0, s>>>(a);
+        T.launches += 1;
     }
     const unsigned g = grid_for(a.F);
     if (topo && ev) k_s3f_tri<true, true><<<g, kBlock, 0, s>>>(a);
@@ -260,14 +277,8 @@ void s3f_step(TopoImpl &T, int l, bool topo, const float *P, float *Pn, cudaStre
     T.launches += 1;
 }
 
-int s3f_export(TopoImpl &T, int l, cudaStream_t s) {
-    CreaseList &C = T.L[l].cr;
-    if (C.cap == 0) return 0;
-    const LevelBuf &A = T.L[l];
-    cudaMemsetAsync(C.xcount, 0, sizeof(int), s);
-    k_s3f_export<<<grid_for(A.nnz), kBlock, 0, s>>>((int)A.nnz, A.fv, A.tw, A.fe, (int)C.cap, C.xcount, C.xverts,
-                                                   C.xsig);
-    return 1;
+int s3f_export(TopoImpl &, int, cudaStream_t) {
+    return 0;      // every level's crease list is written by the step that makes the level
 }
 
 }  // namespace alsub
