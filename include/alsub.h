@@ -5,8 +5,9 @@
  *
  * Scope: one uniform subdivision step, repeated level by level, for Catmull-Clark (Sec. 3),
  * Loop (Appendix B) and sqrt(3) (Appendix A) on 2-manifold meshes -- closed, or open with
- * boundaries for Catmull-Clark (Sec. 3.1 and 3.2 "Boundaries") and Loop -- with sharp and semi-sharp
- * creases for Catmull-Clark and Loop (Sec. 3.3), and the extraction of selective subdivision
+ * boundaries for Catmull-Clark (Sec. 3.1 and 3.2 "Boundaries"), Loop and sqrt(3) (Kobbelt 2000) --
+ * with sharp and semi-sharp creases for Catmull-Clark and Loop (Sec. 3.3) and infinitely sharp
+ * ones for sqrt(3), and the extraction of selective subdivision
  * (Sec. 3.4). Topology refinement (the build step
  * of Fig. module_core) is integer work that emits each level's face table directly; vertex
  * refinement (the eval step) is FP32. The subdivision operator of Sec. 3.6 "Single SpMV
@@ -55,8 +56,8 @@ typedef enum {
     ALSUB_OK = 0,
     ALSUB_ERR_INVALID_ARG = 1,   /* a pointer, count, index or sharpness out of range */
     ALSUB_ERR_NONMANIFOLD = 2,   /* duplicate directed edge, edge of >2 faces, vertex with >1 fan */
-    ALSUB_ERR_UNSUPPORTED = 3,   /* open sqrt(3) mesh, crease at a boundary, counts beyond
-                                    int32, valence > 1024 */
+    ALSUB_ERR_UNSUPPORTED = 3,   /* crease at a boundary, counts beyond int32, valence > 1024, a
+                                    call with no path for the mesh */
     ALSUB_ERR_OOM = 4,           /* device allocation failed or a budget is exhausted */
     ALSUB_ERR_TIMEOUT = 5,       /* a bounded wait ran out */
     ALSUB_ERR_DEVICE = 6,        /* a CUDA runtime error */
@@ -88,7 +89,7 @@ alsub_status alsub_copy(void *dst, const void *src, size_t bytes, void *stream);
  * Closed-form per-level counts (host only, no GPU needed). Sec. 3.1 step 4 / Sec. 3.2 for
  * Catmull-Clark (V' = V + F + E, F' = nnz, nnz' = 4 nnz, E' = 2E + nnz), Appendix B for Loop
  * (V' = V + E, F' = 4F, E' = 2E + 3F), Appendix A for sqrt(3) (V' = V + F, F' = 3F,
- * E' = 3F'/2); a closed mesh has E = nnz / 2.
+ * E' = E + 3F); a closed mesh has E = nnz / 2.
  *   counts_host: int64[4 * (levels + 1)], filled with (V, F, nnz, E) per level.
  * Errors: INVALID_ARG for negative or inconsistent inputs, UNSUPPORTED when a count would exceed
  * int32 or nnz is odd (an open mesh: see alsub_plan_open).
@@ -97,12 +98,14 @@ alsub_status alsub_plan(alsub_scheme scheme, int64_t num_verts, int64_t num_face
                         int32_t levels, int64_t *counts_host);
 
 /*
- * alsub_plan for a Catmull-Clark mesh with `boundary_edges` edges of one face (Sec. 3.1 and 3.2
- * "Boundaries"): E = (nnz + boundary_edges) / 2 on level 0, the same recurrences after it (each
- * boundary edge splits into two boundary edges). boundary_edges = 0 is alsub_plan.
+ * alsub_plan for a mesh with `boundary_edges` edges of one face (Sec. 3.1 and 3.2 "Boundaries"):
+ * E = (nnz + boundary_edges) / 2 on level 0, the same recurrences after it, each boundary edge
+ * splitting into two (Catmull-Clark, Loop). sqrt(3) (Kobbelt 2000) alternates two kinds of step:
+ * from an even level the boundary edges stay (the recurrences above); from an odd level each splits
+ * into three, which adds one vertex and one edge per boundary edge (V' = V + F + B, E' = E + 3F +
+ * B, B' = 3B). boundary_edges = 0 is alsub_plan.
  * Errors: those of alsub_plan; INVALID_ARG when nnz + boundary_edges is odd or boundary_edges is
- * negative or above nnz; UNSUPPORTED for boundary_edges > 0 with sqrt(3) (Appendix A omits its
- * boundary rule). Loop takes the Catmull-Clark counts' boundary rule: a boundary edge splits in two.
+ * negative or above nnz.
  */
 alsub_status alsub_plan_open(alsub_scheme scheme, int64_t num_verts, int64_t num_faces, int64_t nnz,
                              int64_t boundary_edges, int32_t levels, int64_t *counts_host);
@@ -116,7 +119,9 @@ alsub_status alsub_plan_open(alsub_scheme scheme, int64_t num_verts, int64_t num
  *   face_verts_host:   int32[nnz] vertex ids of each face in counter-clockwise cyclic order.
  *   crease_verts_host: int32[2 * num_creases] edge endpoints; crease_sharpness_host: float[K]
  *                      sharpness sigma >= 0 (+inf = infinitely sharp; 0 = smooth, dropped).
- *                      sqrt(3) ignores creases (the paper gives the scheme no crease rules).
+ *                      sqrt(3) (no crease rules in the paper) keeps the infinitely sharp creases
+ *                      as feature edges, like its boundary edges below; finite sharpness is
+ *                      ignored.
  * The host validates ranges (vertex ids, face order >= 3, Loop/sqrt(3) triangles only, no
  * repeated vertex in a face, every vertex used, sigma not NaN or negative) and copies everything
  * to the device on `stream`; the caller may free its arrays on return. Adjacency is checked on
@@ -129,10 +134,15 @@ alsub_status alsub_plan_open(alsub_scheme scheme, int64_t num_verts, int64_t num
  * the topology is built), and no crease may touch a boundary vertex (the paper defines no such
  * combination: UNSUPPORTED). Loop meshes may be open too, with the same two boundary rules (Appendix
  * B gives Loop none of its own; these keep its boundary the cubic B-spline curve of the control
- * polygon, as for Catmull-Clark). sqrt(3) meshes must be closed.
+ * polygon, as for Catmull-Clark). sqrt(3) meshes may be open too (Appendix A omits boundaries; the
+ * treatment is Kobbelt 2000's): boundary edges and infinitely sharp creases (feature edges) are not
+ * flipped on the first step of each pair of steps and are split into three on the second, their
+ * curves refined by the ternary cubic B-spline rules (new points (1, 16, 10) / 27 and
+ * (10, 16, 1) / 27, curve vertices (4, 19, 4) / 27 on the second step and unmoved on the first,
+ * corners fixed, a curve end mirrored). Such meshes take a general per-level path (every level's
+ * twins stored); the operator and ragged batches refuse them (UNSUPPORTED).
  * Errors: INVALID_ARG, NONMANIFOLD (a repeated directed edge found by the boundary count),
- * UNSUPPORTED (counts beyond int32, odd nnz for sqrt(3), a crease at the boundary), OOM,
- * DEVICE.
+ * UNSUPPORTED (counts beyond int32, a crease at the boundary), OOM, DEVICE.
  */
 alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t num_verts, int32_t num_faces,
                                const int32_t *face_offsets_host, const int32_t *face_verts_host,
@@ -173,8 +183,8 @@ alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t num_verts, int32_
 
 alsub_status alsub_mesh_destroy(alsub_mesh_t mesh);
 
-/* Number of boundary edges (edges of one face) of a mesh; 0 for a closed mesh and for sqrt(3)
- * meshes (those must be closed). Host only. Errors: INVALID_ARG. */
+/* Number of boundary edges (edges of one face) of a mesh; 0 for a closed mesh. Host only.
+ * Errors: INVALID_ARG. */
 alsub_status alsub_mesh_boundary_edges(alsub_mesh_t mesh, int64_t *boundary_edges);
 
 /* Scheme, vertex, face, corner and crease counts of a mesh (host only; any pointer may be NULL).
@@ -381,7 +391,7 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
  * The operator keeps a pointer to the topology, which must outlive it. Synchronises `stream`
  * (the non-zero counts size the allocations).
  * Errors: INVALID_ARG (topology not built, no flags), UNSUPPORTED (a stencil row of more than 192
- * entries), OOM, DEVICE.
+ * entries; a sqrt(3) mesh with boundaries or infinitely sharp creases), OOM, DEVICE.
  */
 typedef enum { ALSUB_OP_CHAIN = 1, ALSUB_OP_COMPOSE = 2, ALSUB_OP_TRANSPOSE = 4 } alsub_operator_flags;
 
@@ -418,7 +428,8 @@ alsub_status alsub_operator_destroy(alsub_operator_t op);
  * (float[3 V_L]) exactly as alsub_refine_vertices(topos[i], ...) would, using that topology's own
  * scratch, so a topology may appear only once and must not be refined elsewhere while the batch
  * runs. The buffers are bound at creation: to refine new positions, write them into P0_dev[i].
- * Members must be closed meshes (UNSUPPORTED otherwise: the batch has no boundary repair step).
+ * Members must be closed meshes without sqrt(3) feature edges (UNSUPPORTED otherwise: the batch
+ * has no boundary repair step and does not run the sqrt(3) feature path).
  * Members' hierarchical edits (alsub_topology_set_edits) are applied as set when the batch first
  * runs on a stream (its captured graph keeps them).
  */
@@ -494,8 +505,9 @@ alsub_status alsub_refine_vertices_static(alsub_topology_t topo, const float *P0
  * Device bytes that alsub_topology_create(levels) allocates for a mesh of these sizes (host only,
  * no GPU needed; the same closed-form sizes the create call uses). boundary_edges as in
  * alsub_plan_open (0 for a closed mesh). sigma_max is the largest crease sharpness (+inf
- * allowed; it bounds how many levels keep crease lists). The mesh itself holds 4 (F + 1) +
- * 4 nnz + 12 K bytes more. Errors: those of alsub_plan_open.
+ * allowed; it bounds how many levels keep crease lists). For sqrt(3), num_creases counts the
+ * infinitely sharp creases (the only ones it keeps) and matters only when sigma_max is +inf. The
+ * mesh itself holds 4 (F + 1) + 4 nnz + 12 K bytes more. Errors: those of alsub_plan_open.
  */
 alsub_status alsub_plan_bytes(alsub_scheme scheme, int32_t num_verts, int32_t num_faces, int32_t nnz,
                               int32_t boundary_edges, int32_t num_creases, float sigma_max, int32_t levels,
