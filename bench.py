@@ -633,7 +633,8 @@ def cpu_baseline(m, budget_levels):
 def sample_levels(name):
     # level whose serial FP64 refinement takes roughly 2-10 s on one core
     return {"cc_torus16_L3": 3, "cc_creased_torus96_L6": 5, "loop_tri_torus128_L6": 4,
-            "sqrt3_tri_torus128_L8": 5, "cc_creased_torus144_L4": 4}.get(name, 3)
+            "sqrt3_tri_torus128_L8": 5, "sqrt3_tri_torus128_L8_smooth": 5,
+            "cc_creased_torus144_L4": 4}.get(name, 3)
 
 
 def run_reference(args):

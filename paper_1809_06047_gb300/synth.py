@@ -311,6 +311,11 @@ def workload(name: str) -> dict:
     elif name == "sqrt3_tri_torus128_L8":
         m = torus_tri(128, 128, seed=SEED_BASE + 3)
         m.update(scheme="sqrt3", levels=8)
+    elif name == "sqrt3_tri_torus128_L8_smooth":
+        # the same mesh without its sharp edges: the closed-mesh sqrt(3) kernels
+        m = torus_tri(128, 128, seed=SEED_BASE + 3)
+        m.update(scheme="sqrt3", levels=8, crease_verts=np.zeros((0, 2), np.int32),
+                 crease_sharp=np.zeros(0, np.float32))
     elif name == "cc_creased_torus144_L4":
         m = torus_cc_mixed(144, 144, seed=SEED_BASE + 5)
         m.update(scheme="cc", levels=4)
