@@ -238,7 +238,7 @@ def serving_leg(w, n_slots: int = 16, budget: float = 40e9, fastest: bool = Fals
                  peak_in_flight=st["peak_in_flight"], device_overlap_peak=st["device_overlap_peak"])
         return d
 
-    out_served = served("operator")
+    out_served = served("operator_mf")
     out_fastest = served("fastest") if fastest else None
 
     def plain_one(i, q, due):
@@ -293,8 +293,9 @@ def spmv_bytes(rows, cols, nnz):
 
 def operator_leg(peak):
     """The subdivision operator of Sec. 3.6 on the headline workload: composite R = R_5 ... R_0 built
-    in the paper's two stages, then one SpMV per frame, against the fused eval kernels on the same
-    cached topology."""
+    in the paper's two stages, then one SpMV per frame; the matrix-free operator (the same rows
+    evaluated as stencils by the eval kernels behind alsub_apply_operator); and the fused eval
+    kernels on the same cached topology."""
     import torch
     from paper_1809_06047_gb300 import alsub
     m = synth.workload(DEFAULT_WORKLOAD)
@@ -311,6 +312,10 @@ def operator_leg(peak):
     PL = torch.empty((info["rows"], 3), dtype=torch.float32, device="cuda")
     ms_spmv = _events_ms(lambda: O.apply(P0, out=PL), 10)
     ms_eval = _events_ms(lambda: T.refine_vertices(P0, out=PL), 10)
+    mf = alsub.Operator(T, chain=False, matrix_free=True)
+    ms_mf = _events_ms(lambda: mf.apply(P0, out=PL), 10)
+    mf_bytes = mf.bytes()
+    mf.close()
     b = spmv_bytes(info["rows"], info["cols"], info["nnz"])
     gbs = b / (ms_spmv / 1e3) / 1e9
     out = {"workload": f"{DEFAULT_WORKLOAD}: composite operator R, {info['rows']} x {info['cols']}, "
@@ -318,6 +323,8 @@ def operator_leg(peak):
            "build_s": build_s, "bytes_held": O.bytes(), "apply_ms": ms_spmv,
            "apply_refined_verts_per_s": info["rows"] / (ms_spmv / 1e3),
            "eval_kernels_ms": ms_eval,
+           "matrix_free": {"apply_ms": ms_mf, "bytes_held": mf_bytes,
+                           "apply_refined_verts_per_s": info["rows"] / (ms_mf / 1e3)},
            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                         "kernel": "k_spmv (one CSR SpMV, xyz rows)", "algorithmic_bytes": b}}
     O.close()
@@ -684,7 +691,8 @@ def summary_of(out):
          "stage_frac": [r(x, 3) for x in out["pipeline"].get("stage_frac", [])],
          "e2e_ms": r(out["e2e"]["ms_per_step"])}
     legs = {
-        "operator": [("apply_ms", "apply_ms"), ("eval_ms", "eval_kernels_ms"), ("frac", "roofline", "frac")],
+        "operator": [("apply_ms", "apply_ms"), ("mf_ms", "matrix_free", "apply_ms"), ("eval_ms", "eval_kernels_ms"),
+                     ("frac", "roofline", "frac")],
         "adjoint": [("fwd_bwd_ms", "forward_backward_ms"), ("bwd_ms", "backward_ms"), ("frac", "roofline", "frac")],
         "batch": [("batch_ms", "batch_ms"), ("alone_ms", "one_at_a_time_ms")],
         "boundary": [("ms", "ms_per_step"), ("frac", "roofline", "frac"), ("loop_ms", "loop", "ms_per_step")],

@@ -286,7 +286,9 @@ alsub_status alsub_refine_topology(alsub_mesh_t mesh, int32_t levels, void *stre
 /*
  * Allocate a topology handle for `levels` steps of `mesh` without computing anything (sizes are
  * closed-form). alsub_subdivide fills it; alsub_refine_topology is alsub_topology_create plus the
- * build. The handle keeps a reference to `mesh`, which must outlive it.
+ * build. The handle keeps a reference to `mesh`, which must outlive every call on it but
+ * alsub_topology_destroy (the release reads nothing of the mesh: the two may be destroyed in
+ * either order).
  * Errors: INVALID_ARG, UNSUPPORTED (a level beyond int32 counts), OOM, DEVICE.
  */
 alsub_status alsub_topology_create(alsub_mesh_t mesh, int32_t levels, void *stream,
@@ -383,17 +385,30 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
  * of every row, then fill column indices and FP32 weights); rows are sorted by column.
  *   flags: ALSUB_OP_CHAIN keeps every R_l (apply = L SpMVs); ALSUB_OP_COMPOSE forms R by row-wise
  *          sparse products (apply = one SpMV; memory ~ rows x support); ALSUB_OP_TRANSPOSE also
- *          builds the transposes for alsub_apply_operator_transpose (the adjoint g_0 = R^T g_L).
+ *          builds the transposes for alsub_apply_operator_transpose (the adjoint g_0 = R^T g_L);
+ *          ALSUB_OP_MATRIX_FREE applies R without storing it: its rows are the stencils the eval
+ *          kernels evaluate from the cached topology (apply = alsub_refine_vertices' kernels, in
+ *          the operator's own scratch, a repeated apply replaying a captured graph), which moves the
+ *          face tables of the levels and their positions instead of ~16 column indices and weights
+ *          per refined vertex; with ALSUB_OP_TRANSPOSE (and no other flag) only the transposes of
+ *          the R_l are stored. When combined with CHAIN or COMPOSE, apply takes the matrix-free
+ *          form and alsub_operator_info the stored matrices.
  * Weights: Catmull-Clark face row 1/c; edge row 1/4 on the endpoints and 1/(4c) on every vertex of
  * both faces (Eq. 2 with Eq. 1 expanded); vertex row (1 - 2/n) on the vertex, 1/n^2 on each
  * neighbour and 1/(n^2 c) on every vertex of each incident face (Eq. pos_update); Loop and sqrt(3)
  * per Appendices B and A; crease rows blended as in alsub_refine_vertices.
- * The operator keeps a pointer to the topology, which must outlive it. Synchronises `stream`
+ * The operator keeps a pointer to the topology, which must outlive every call on it but
+ * alsub_operator_destroy (which reads nothing of the topology). Synchronises `stream`
  * (the non-zero counts size the allocations).
  * Errors: INVALID_ARG (topology not built, no flags), UNSUPPORTED (a stencil row of more than 192
  * entries; a sqrt(3) mesh with boundaries or infinitely sharp creases), OOM, DEVICE.
  */
-typedef enum { ALSUB_OP_CHAIN = 1, ALSUB_OP_COMPOSE = 2, ALSUB_OP_TRANSPOSE = 4 } alsub_operator_flags;
+typedef enum {
+    ALSUB_OP_CHAIN = 1,
+    ALSUB_OP_COMPOSE = 2,
+    ALSUB_OP_TRANSPOSE = 4,
+    ALSUB_OP_MATRIX_FREE = 8
+} alsub_operator_flags;
 
 alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *stream,
                                   alsub_operator_t *out);
@@ -407,9 +422,12 @@ alsub_status alsub_operator_info(alsub_operator_t op, int32_t level, int64_t *ro
                                  int64_t *nnz, const int64_t **rowptr_dev, const int32_t **col_dev,
                                  const float **w_dev);
 
-/* P_L = R P_0 on `stream` (one SpMV with the composite, else the chain of R_l). P0_dev:
- * float[3 V_0], PL_dev: float[3 V_L] (packed xyz). Calls on one operator must not overlap when
- * the chain is used (it keeps intermediate levels in the operator). */
+/* P_L = R P_0 on `stream` (matrix-free: the eval kernels; else one SpMV with the composite, else
+ * the chain of R_l). P0_dev: float[3 V_0], PL_dev: float[3 V_L] (packed xyz). A matrix-free
+ * operator keeps its intermediate levels in its own scratch: its applies are taken one at a time
+ * on the host and ordered on the device (each waits on the stream for the previous one), and the
+ * result is bitwise that of alsub_refine_vertices on the same topology. Calls on one chain
+ * operator must not overlap (it keeps intermediate levels in the operator). */
 alsub_status alsub_apply_operator(alsub_operator_t op, const float *P0_dev, float *PL_dev, void *stream);
 
 /* g_0 = R^T g_L (the adjoint of vertex refinement: vertex refinement is linear in P, so this is
@@ -606,12 +624,22 @@ alsub_status alsub_serve_create(size_t hbm_budget_bytes, int32_t max_slots, alsu
  *   ALSUB_FRAMES_EVAL      the eval kernels on the cached topology (no operator is built);
  *   ALSUB_FRAMES_OPERATOR  one SpMV with the cached composite operator R (Sec. 3.6 "Single SpMV
  *                          evaluation"); falls back to EVAL when R does not fit the budget;
- *   ALSUB_FRAMES_FASTEST   build R, time one frame by each path and keep the faster.
+ *   ALSUB_FRAMES_FASTEST   build R, time one frame by each path and keep the faster;
+ *   ALSUB_FRAMES_OPERATOR_MATRIX_FREE  alsub_apply_operator on a matrix-free operator
+ *                          (ALSUB_OP_MATRIX_FREE): R's rows are the stencils the eval kernels
+ *                          evaluate, so a frame costs what an EVAL frame costs and nothing but the
+ *                          operator's scratch is stored; frames of one resident run one after
+ *                          another on the device (they share that scratch).
  * Mesh arguments as alsub_mesh_create. *resident receives the id FRAME requests name.
  * Errors: those of the mesh, topology and operator calls, INVALID_ARG for an unknown mode, OOM when
  * the topology does not fit the budget.
  */
-typedef enum { ALSUB_FRAMES_EVAL = 0, ALSUB_FRAMES_OPERATOR = 1, ALSUB_FRAMES_FASTEST = 2 } alsub_frame_path;
+typedef enum {
+    ALSUB_FRAMES_EVAL = 0,
+    ALSUB_FRAMES_OPERATOR = 1,
+    ALSUB_FRAMES_FASTEST = 2,
+    ALSUB_FRAMES_OPERATOR_MATRIX_FREE = 3
+} alsub_frame_path;
 
 alsub_status alsub_serve_register(alsub_server_t server, alsub_scheme scheme, int32_t num_verts,
                                   int32_t num_faces, const int32_t *face_offsets_host,

@@ -394,13 +394,13 @@ class Topology:
 class Operator:
     """alsub_build_operator and friends: R_l per level and/or the composite R = R_{L-1}...R_0."""
 
-    CHAIN, COMPOSE, TRANSPOSE = 1, 2, 4
+    CHAIN, COMPOSE, TRANSPOSE, MATRIX_FREE = 1, 2, 4, 8
 
     def __init__(self, topo: Topology, chain: bool = True, compose: bool = False,
-                 transpose: bool = False, stream=None):
+                 transpose: bool = False, matrix_free: bool = False, stream=None):
         self.topo = topo          # the topology must outlive the operator
         flags = (self.CHAIN if chain else 0) | (self.COMPOSE if compose else 0) | \
-            (self.TRANSPOSE if transpose else 0)
+            (self.TRANSPOSE if transpose else 0) | (self.MATRIX_FREE if matrix_free else 0)
         self._h = ctypes.c_void_p()
         _check(lib().alsub_build_operator(topo.handle, flags, ctypes.c_void_p(_stream(stream)),
                                           ctypes.byref(self._h)))
@@ -534,11 +534,13 @@ class Server:
         self._keep = {}
         _check(lib().alsub_serve_create(int(budget_bytes), int(max_slots), ctypes.byref(self._h)))
 
-    FRAMES = {"eval": 0, "operator": 1, "fastest": 2}
+    FRAMES = {"eval": 0, "operator": 1, "fastest": 2, "operator_mf": 3}
 
-    def register(self, m: dict, scheme: str, levels: int, frames: str = "operator") -> int:
+    def register(self, m: dict, scheme: str, levels: int, frames: str = "operator_mf") -> int:
         """alsub_serve_register: make `m` a resident topology of `levels` steps whose frames are
-        served by the eval kernels, the cached composite operator, or the faster of the two."""
+        served by the eval kernels ("eval"), the cached composite operator ("operator"), the faster
+        of those two ("fastest") or a matrix-free operator ("operator_mf", the stencils of the eval
+        kernels behind alsub_apply_operator)."""
         fv, off, cv, cs = _mesh_arrays(m)
         rid = ctypes.c_int32()
         _check(lib().alsub_serve_register(self._h, SCHEMES[scheme], int(m["V"]), int(m["F"]), _ptr(off),

@@ -87,7 +87,7 @@ alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
         return ALSUB_OK;
     }
     void *q = nullptr;
-    cudaError_t e = dev_malloc(T_.mesh->alloc, &q, n * sizeof(T), s);
+    cudaError_t e = dev_malloc(T_.alloc, &q, n * sizeof(T), s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(ALSUB_ERR_OOM, "device allocation of %zu bytes failed", n * sizeof(T));
@@ -104,7 +104,7 @@ alsub_status dalloc(TopoImpl &T_, T **p, size_t n, cudaStream_t s) {
     } while (0)
 
 void free_topo(TopoImpl &T) {
-    for (void *p : T.allocs) dev_free(T.mesh->alloc, p, T.stream);
+    for (void *p : T.allocs) dev_free(T.alloc, p, T.stream);
     T.allocs.clear();
     T.bytes = 0;
     T.arena = nullptr;
@@ -146,6 +146,7 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     if (st != ALSUB_OK) return st;
     void *q = nullptr;
     T.mesh = &M;
+    T.alloc = M.alloc;
     if (dev_malloc(M.alloc, &q, D.bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return fail(ALSUB_ERR_OOM, "device allocation of %zu bytes failed", D.bytes);
@@ -161,6 +162,7 @@ alsub_status topo_alloc(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
 
 alsub_status topo_layout(TopoImpl &T, MeshImpl &M, int levels, cudaStream_t s) {
     T.mesh = &M;
+    T.alloc = M.alloc;
     T.scheme = M.scheme;
     T.levels = levels;
     T.stream = s;
@@ -468,12 +470,12 @@ void free_hostio(TopoImpl &T) {
     if (io.cs) cudaStreamSynchronize(io.cs);
     if (io.ds) cudaStreamSynchronize(io.ds);
     for (int b = 0; b < 2; b++) {
-        if (io.dPL[b]) dev_free(T.mesh->alloc, io.dPL[b], T.stream);
+        if (io.dPL[b]) dev_free(T.alloc, io.dPL[b], T.stream);
         if (io.hP0[b]) cudaFreeHost(io.hP0[b]);
         for (cudaEvent_t e : {io.up[b], io.done[b], io.copied[b]})
             if (e) cudaEventDestroy(e);
     }
-    if (io.dP0) dev_free(T.mesh->alloc, io.dP0, T.stream);
+    if (io.dP0) dev_free(T.alloc, io.dP0, T.stream);
     if (io.cs) cudaStreamDestroy(io.cs);
     if (io.ds) cudaStreamDestroy(io.ds);
     io = TopoImpl::HostIO();
@@ -487,9 +489,9 @@ alsub_status ensure_hostio(TopoImpl &T) {
     const size_t n0 = 12 * (size_t)T.L[0].V, nl = 12 * (size_t)T.L[T.levels].V;
     bool ok = cudaStreamCreateWithFlags(&io.cs, cudaStreamNonBlocking) == cudaSuccess &&
               cudaStreamCreateWithFlags(&io.ds, cudaStreamNonBlocking) == cudaSuccess &&
-              dev_malloc(T.mesh->alloc, &io.dP0, n0, io.cs) == cudaSuccess;
+              dev_malloc(T.alloc, &io.dP0, n0, io.cs) == cudaSuccess;
     for (int b = 0; ok && b < 2; b++)
-        ok = dev_malloc(T.mesh->alloc, &io.dPL[b], nl, io.cs) == cudaSuccess &&
+        ok = dev_malloc(T.alloc, &io.dPL[b], nl, io.cs) == cudaSuccess &&
              cudaMallocHost(&io.hP0[b], n0) == cudaSuccess &&
              cudaEventCreateWithFlags(&io.up[b], cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&io.done[b], cudaEventDisableTiming) == cudaSuccess &&
@@ -623,6 +625,13 @@ void alsub::dev_free(const DevAlloc &A, void *p, cudaStream_t s) {
     if (!p) return;
     if (A.free) A.free(p, A.ctx, (void *)s);
     else cudaFreeAsync(p, s);
+}
+
+alsub_status alsub::refine_call(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s) {
+    if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
+    alsub_status st = run_call(T, 0, P0, PL, scratch, s, refine_body);
+    if (T.tcap && T.levels > 0) T.tcalls++;
+    return st;
 }
 
 alsub_status alsub::refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s) {
@@ -1056,13 +1065,13 @@ alsub_status alsub_topology_set_edits(alsub_topology_t h, int32_t level, int32_t
     TopoImpl::LevelEdits &e = T.edits[level];
     CK(cudaStreamSynchronize(T.stream));          // calls in flight may still read the old edits
     CK(cudaStreamSynchronize(s));
-    if (e.vid) dev_free(T.mesh->alloc, e.vid, s);
-    if (e.off) dev_free(T.mesh->alloc, e.off, s);
+    if (e.vid) dev_free(T.alloc, e.vid, s);
+    if (e.off) dev_free(T.alloc, e.off, s);
     e = TopoImpl::LevelEdits();
     drop_graphs(T);                               // captured calls hold the old edit launches
     if (n == 0) return finish("alsub_topology_set_edits");
-    CK(dev_malloc(T.mesh->alloc, &e.vid, sizeof(int) * (size_t)n, s));
-    CK(dev_malloc(T.mesh->alloc, &e.off, sizeof(float) * 3 * (size_t)n, s));
+    CK(dev_malloc(T.alloc, &e.vid, sizeof(int) * (size_t)n, s));
+    CK(dev_malloc(T.alloc, &e.off, sizeof(float) * 3 * (size_t)n, s));
     CK(cudaMemcpyAsync(e.vid, vid_dev, sizeof(int) * (size_t)n, cudaMemcpyDefault, s));
     CK(cudaMemcpyAsync(e.off, off_dev, sizeof(float) * 3 * (size_t)n, cudaMemcpyDefault, s));
     e.n = n;
@@ -1072,8 +1081,8 @@ alsub_status alsub_topology_set_edits(alsub_topology_t h, int32_t level, int32_t
 alsub_status alsub_topology_destroy(alsub_topology_t h) {
     if (!h) return ALSUB_OK;
     for (TopoImpl::LevelEdits &e : h->t.edits) {
-        if (e.vid) dev_free(h->t.mesh->alloc, e.vid, h->t.stream);
-        if (e.off) dev_free(h->t.mesh->alloc, e.off, h->t.stream);
+        if (e.vid) dev_free(h->t.alloc, e.vid, h->t.stream);
+        if (e.off) dev_free(h->t.alloc, e.off, h->t.stream);
     }
     free_hostio(h->t);
     free_events(h->t);
@@ -1119,11 +1128,7 @@ alsub_status alsub_topology_bytes(alsub_topology_t h, size_t *bytes) {
 alsub_status alsub_refine_vertices(alsub_topology_t h, const float *P0, float *PL, void *scratch,
                                    void *stream) {
     if (!h || !P0 || !PL) return fail(ALSUB_ERR_INVALID_ARG, "bad arguments");
-    TopoImpl &T = h->t;
-    if (!T.built) return fail(ALSUB_ERR_INVALID_ARG, "topology not built");
-    alsub_status st = run_call(T, 0, P0, PL, scratch, (cudaStream_t)stream, refine_body);
-    if (T.tcap && T.levels > 0) T.tcalls++;
-    return st;
+    return refine_call(h->t, P0, PL, scratch, (cudaStream_t)stream);
 }
 
 alsub_status alsub_subdivide_host(alsub_topology_t h, const float *P0_host, float *PL_host, void *stream) {

@@ -230,7 +230,7 @@ alsub_status extract_level(TopoImpl &T, int level, const unsigned char *mask, in
     const size_t stmp = scan_tmp_bytes(nmax);
     const size_t ints = 5 * nV + 4 * nF + 2 * nC + 8 + (tri ? nF + 1 : 0);
     char *buf = nullptr;
-    const DevAlloc &DA = T.mesh->alloc;       // the extracted mesh takes the source mesh's allocator
+    const DevAlloc &DA = T.alloc;       // the extracted mesh takes the source mesh's allocator
     out.alloc = DA;
     if (dev_malloc(DA, &buf, 4 * ints + stmp + 256, s) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "extraction: device allocation failed");

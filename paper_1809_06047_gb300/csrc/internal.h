@@ -106,6 +106,8 @@ struct DirTable {
 
 struct TopoImpl {
     MeshImpl *mesh = nullptr;
+    DevAlloc alloc;              // the mesh's allocator, copied: the arrays are released with it
+                                 // even when the mesh is destroyed first
     alsub_scheme scheme;
     int levels = 0;
     std::vector<LevelBuf> L;     // levels + 1
@@ -280,6 +282,9 @@ void tri_batch_launch(const BatchClass &c, int block, int grid, cudaStream_t s);
 struct TriLevel;
 TriLevel tri_level(const TopoImpl &T, int l);
 
+// One vertex refinement of a built topology as alsub_refine_vertices makes it (a repeated call
+// replays a captured graph); `scratch` holds the intermediate levels (null: the handle's own).
+alsub_status refine_call(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s);
 // One vertex refinement of a built topology, its kernels launched directly on `s`: no graph is
 // captured or replayed and no stream or event is made (the graph cache is left as it is).
 alsub_status refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s);

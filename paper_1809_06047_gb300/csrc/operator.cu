@@ -12,6 +12,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -408,6 +409,13 @@ struct alsub_operator_s {
     std::vector<Csr> R, RT;        // per level (ALSUB_OP_CHAIN), and transposes
     Csr C, CT;                     // composite and its transpose (ALSUB_OP_COMPOSE)
     bool has_chain = false, has_comp = false, has_t = false;
+    DevAlloc alloc;                // the topology's allocator, copied for the release
+    bool matrix_free = false;      // ALSUB_OP_MATRIX_FREE: apply = the stencil kernels on the topology
+    float *mf_scratch = nullptr;   // their intermediate levels (the operator's own)
+    // applies of a matrix-free operator share its scratch and the topology's launch state: one at a
+    // time on the host (mf_lock) and, through mf_done, in order on the device
+    std::mutex mf_lock;
+    cudaEvent_t mf_done = nullptr;
     float *buf = nullptr;          // two intermediate levels of packed xyz for chain applies
     size_t buf_floats = 0;
     int *cnt = nullptr;            // scratch counts
@@ -425,7 +433,7 @@ alsub_status oalloc(alsub_operator_s &O, T **p, size_t n) {
     *p = nullptr;
     if (n == 0) n = 1;
     void *q = nullptr;
-    if (dev_malloc(O.T->mesh->alloc, &q, n * sizeof(T), O.stream) != cudaSuccess) {
+    if (dev_malloc(O.alloc, &q, n * sizeof(T), O.stream) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "operator: device allocation failed");
     }
     O.allocs.push_back({q, n * sizeof(T)});
@@ -558,7 +566,12 @@ void spmv(alsub_operator_s &O, const Csr &M, const float *x, float *y, cudaStrea
 }
 
 void free_op(alsub_operator_s *O) {
-    for (auto &a : O->allocs) dev_free(O->T->mesh->alloc, a.first, O->stream);
+    if (O->mf_done) {
+        cudaEventSynchronize(O->mf_done);
+        cudaEventDestroy(O->mf_done);
+        O->mf_done = nullptr;
+    }
+    for (auto &a : O->allocs) dev_free(O->alloc, a.first, O->stream);
     O->allocs.clear();
     O->bytes = 0;
 }
@@ -568,7 +581,7 @@ void release(alsub_operator_s &O, Csr &M) {
     for (void *p : {(void *)M.rowptr, (void *)M.col, (void *)M.w}) {
         for (size_t i = 0; i < O.allocs.size(); i++) {
             if (O.allocs[i].first != p) continue;
-            dev_free(O.T->mesh->alloc, p, O.stream);
+            dev_free(O.alloc, p, O.stream);
             O.bytes -= O.allocs[i].second;
             O.allocs.erase(O.allocs.begin() + i);
             break;
@@ -584,19 +597,25 @@ extern "C" {
 alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *stream, alsub_operator_t *out) {
     if (!topo || !out) return report(ALSUB_ERR_INVALID_ARG, "bad operator arguments");
     *out = nullptr;
-    if (!(flags & (ALSUB_OP_CHAIN | ALSUB_OP_COMPOSE)))
-        return report(ALSUB_ERR_INVALID_ARG, "flags must ask for ALSUB_OP_CHAIN and/or ALSUB_OP_COMPOSE");
+    if (!(flags & (ALSUB_OP_CHAIN | ALSUB_OP_COMPOSE | ALSUB_OP_MATRIX_FREE)))
+        return report(ALSUB_ERR_INVALID_ARG,
+                      "flags must ask for ALSUB_OP_CHAIN, ALSUB_OP_COMPOSE and/or ALSUB_OP_MATRIX_FREE");
     TopoImpl &T = *topology_impl(topo);
     if (!T.built) return report(ALSUB_ERR_INVALID_ARG, "topology not built");
-    if (T.s3f)
-        return report(ALSUB_ERR_UNSUPPORTED, "operator: sqrt(3) meshes with boundaries or infinitely sharp creases "
-                                             "are refined by the eval kernels only");
     cudaStream_t s = (cudaStream_t)stream;
-    alsub_status st = ensure_helpers(T, s);
+    const bool want_t = flags & ALSUB_OP_TRANSPOSE;
+    // the CSR matrices: per level when a chain, a composite or (for a matrix-free operator) the
+    // transposes are asked for
+    const bool need_rows = (flags & (ALSUB_OP_CHAIN | ALSUB_OP_COMPOSE)) || want_t;
+    if (T.s3f && need_rows)
+        return report(ALSUB_ERR_UNSUPPORTED, "operator: the rows of sqrt(3) meshes with boundaries or infinitely "
+                                             "sharp creases are evaluated matrix-free only");
+    alsub_status st = need_rows ? ensure_helpers(T, s) : ALSUB_OK;
     if (st) return st;
     alsub_operator_s *O = new (std::nothrow) alsub_operator_s();
     if (!O) return report(ALSUB_ERR_OOM, "host allocation failed");
     O->T = &T;
+    O->alloc = T.alloc;
     O->stream = s;
     O->flags = flags;
     {
@@ -607,15 +626,26 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
     auto bail = [&](alsub_status e) { cudaStreamSynchronize(s); free_op(O); delete O; return e; };
     long long vmax = 1;
     for (int l = 0; l <= T.levels; l++) vmax = std::max(vmax, T.L[l].V);
-    if ((st = oalloc(*O, &O->cnt, (size_t)vmax))) return bail(st);
-    if ((st = oalloc(*O, (char **)&O->scan_tmp, scan_tmp_bytes(vmax)))) return bail(st);
-    if ((st = oalloc(*O, &O->status, 1))) return bail(st);
-    cudaMemsetAsync(O->status, 0, sizeof(int), s);
-    const bool want_t = flags & ALSUB_OP_TRANSPOSE;
-    std::vector<Csr> R(T.levels);
-    for (int l = 0; l < T.levels; l++)
+    if (need_rows) {
+        if ((st = oalloc(*O, &O->cnt, (size_t)vmax))) return bail(st);
+        if ((st = oalloc(*O, (char **)&O->scan_tmp, scan_tmp_bytes(vmax)))) return bail(st);
+        if ((st = oalloc(*O, &O->status, 1))) return bail(st);
+        cudaMemsetAsync(O->status, 0, sizeof(int), s);
+    }
+    if (flags & ALSUB_OP_MATRIX_FREE) {
+        // the operator applied matrix-free: its rows are the stencils the eval kernels evaluate
+        // from the cached topology, so nothing but their scratch is stored
+        O->matrix_free = true;
+        if (T.scratch_bytes && (st = oalloc(*O, (char **)&O->mf_scratch, T.scratch_bytes))) return bail(st);
+        if (cudaEventCreateWithFlags(&O->mf_done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(report(ALSUB_ERR_DEVICE, "operator: event creation failed"));
+        }
+    }
+    std::vector<Csr> R(need_rows ? T.levels : 0);
+    for (int l = 0; l < (int)R.size(); l++)
         if ((st = build_level(*O, l, R[l]))) return bail(st);
-    if (flags & ALSUB_OP_CHAIN) {
+    if ((flags & ALSUB_OP_CHAIN) || (want_t && !(flags & ALSUB_OP_COMPOSE) && O->matrix_free)) {
         O->R = R;
         O->has_chain = true;
         long long vmid = 1;
@@ -627,6 +657,11 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
             for (int l = 0; l < T.levels; l++)
                 if ((st = build_transpose(*O, R[l], O->RT[l]))) return bail(st);
             O->has_t = true;
+        }
+        if (!(flags & ALSUB_OP_CHAIN)) {        // matrix-free forward: keep the transposes only
+            for (Csr &M : O->R) release(*O, M);
+            O->R.clear();
+            O->has_chain = false;
         }
     }
     if (flags & ALSUB_OP_COMPOSE) {
@@ -647,7 +682,11 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
             O->has_t = true;
         }
     }
-    if ((st = check_status(*O))) return bail(st);
+    if (need_rows && (st = check_status(*O))) return bail(st);
+    if (!need_rows && cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(report(ALSUB_ERR_DEVICE, "operator: build failed"));
+    }
     *out = O;
     return ALSUB_OK;
 }
@@ -672,6 +711,13 @@ alsub_status alsub_operator_info(alsub_operator_t op, int32_t level, int64_t *ro
 alsub_status alsub_apply_operator(alsub_operator_t op, const float *P0, float *PL, void *stream) {
     if (!op || !P0 || !PL) return report(ALSUB_ERR_INVALID_ARG, "bad arguments");
     cudaStream_t s = (cudaStream_t)stream;
+    if (op->matrix_free) {
+        std::lock_guard<std::mutex> g(op->mf_lock);
+        cudaStreamWaitEvent(s, op->mf_done, 0);        // the previous apply's scratch use is done
+        alsub_status st = refine_call(*op->T, P0, PL, op->mf_scratch, s);
+        cudaEventRecord(op->mf_done, s);
+        return st;
+    }
     if (op->has_comp) {
         spmv(*op, op->C, P0, PL, s);
     } else {

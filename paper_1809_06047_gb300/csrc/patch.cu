@@ -246,14 +246,14 @@ alsub_status alsub_topology_regular_faces(alsub_topology_t topo, int32_t level, 
     if (st != ALSUB_OK) return st;
     const LevelBuf &L = T->L[level];
     char *buf = nullptr;
-    if (dev_malloc(T->mesh->alloc, &buf, (size_t)L.V + 64, s) != cudaSuccess) {
+    if (dev_malloc(T->alloc, &buf, (size_t)L.V + 64, s) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "patches: device allocation failed");
     }
     unsigned long long *cnt = (unsigned long long *)buf;
     unsigned char *crease_v = (unsigned char *)buf + 64;
     PatchAcc A;
     if (!patch_setup(*T, level, s, &A, crease_v)) {
-        dev_free(T->mesh->alloc, buf, s);
+        dev_free(T->alloc, buf, s);
         return report(ALSUB_ERR_INVALID_ARG, "the level keeps no twins");
     }
     cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), s);
@@ -266,7 +266,7 @@ alsub_status alsub_topology_regular_faces(alsub_topology_t topo, int32_t level, 
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         *count = (int64_t)h;
     }
-    dev_free(T->mesh->alloc, buf, s);
+    dev_free(T->alloc, buf, s);
     if (e != cudaSuccess) return report(ALSUB_ERR_DEVICE, cudaGetErrorString(e));
     e = cudaGetLastError();
     return e == cudaSuccess ? ALSUB_OK : report(ALSUB_ERR_DEVICE, cudaGetErrorString(e));
@@ -283,14 +283,14 @@ alsub_status alsub_topology_eval_patches(alsub_topology_t topo, int32_t level, i
     const LevelBuf &L = T->L[level];
     char *buf = nullptr;
     const size_t net_bytes = 64 * (size_t)n;
-    if (dev_malloc(T->mesh->alloc, &buf, net_bytes + (size_t)L.V + 16, s) != cudaSuccess) {
+    if (dev_malloc(T->alloc, &buf, net_bytes + (size_t)L.V + 16, s) != cudaSuccess) {
         return report(ALSUB_ERR_OOM, "patches: device allocation failed");
     }
     int *nets = (int *)buf;
     unsigned char *crease_v = (unsigned char *)buf + net_bytes;
     PatchAcc A;
     if (!patch_setup(*T, level, s, &A, crease_v)) {
-        dev_free(T->mesh->alloc, buf, s);
+        dev_free(T->alloc, buf, s);
         return report(ALSUB_ERR_INVALID_ARG, "the level keeps no twins");
     }
     k_patch_nets<<<grid_for(n), kBlock, 0, s>>>(A, n, faces_dev, (int)L.F, crease_v, nets);
@@ -305,7 +305,7 @@ alsub_status alsub_topology_eval_patches(alsub_topology_t topo, int32_t level, i
         k_patch_eval<<<(unsigned)((total + kBlock - 1) / kBlock), kBlock, 0, s>>>(total, samples, nets, P_dev, out_dev);
     }
     T->launches += 2;
-    dev_free(T->mesh->alloc, buf, s);
+    dev_free(T->alloc, buf, s);
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? ALSUB_OK : report(ALSUB_ERR_DEVICE, cudaGetErrorString(e));
 }

@@ -54,6 +54,9 @@ struct Resident {
     int64_t V0 = 0, VL = 0;
     size_t bytes = 0;                // topology + mesh + operator
     size_t scratch = 0;              // eval scratch a frame needs when served without the operator
+    // the topology's launch state (its graph cache, the fork and join events of its side streams)
+    // is shared by every frame of this resident: one worker enqueues at a time
+    std::mutex launch;
 };
 
 struct Job {
@@ -150,7 +153,7 @@ alsub_status start(Slot &sl, Job &j) {
         if (st == ALSUB_OK) st = alsub_topology_create(sl.mesh, j.levels, sl.stream, &sl.topo);
         if (st != ALSUB_OK) return st;
     }
-    const Resident *R = j.res;
+    Resident *R = j.res;
     const size_t scratch = (j.kind == ALSUB_REQ_FRAME && !R->op) ? R->scratch : 0;
     const size_t b_in = align256(4 * n_in), b_out = align256(4 * n_out);
     if (cudaMallocAsync(&sl.d_buf, b_in + b_out + scratch, sl.stream) != cudaSuccess) {
@@ -167,6 +170,7 @@ alsub_status start(Slot &sl, Job &j) {
     cudaEventRecord(sl.ev_b, sl.stream);
     if (j.kind == ALSUB_REQ_FRAME) {
         j.by_operator = R->op != nullptr;
+        std::lock_guard<std::mutex> g(j.res->launch);
         st = R->op ? alsub_apply_operator(R->op, d_in, d_out, sl.stream)
                    : alsub_refine_vertices(R->topo, d_in, d_out, d_scratch, sl.stream);
     } else {
@@ -391,7 +395,8 @@ alsub_status alsub_serve_create(size_t budget, int32_t max_slots, alsub_server_t
 alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t V, int32_t F,
                                   const int32_t *off, const int32_t *fv, int32_t K, const int32_t *cv,
                                   const float *cs, int32_t levels, int32_t frame_path, int32_t *resident) {
-    if (!S || !resident || frame_path < ALSUB_FRAMES_EVAL || frame_path > ALSUB_FRAMES_FASTEST)
+    if (!S || !resident || frame_path < ALSUB_FRAMES_EVAL ||
+        frame_path > ALSUB_FRAMES_OPERATOR_MATRIX_FREE)
         return report(ALSUB_ERR_INVALID_ARG, "bad arguments");
     cudaSetDevice(S->device);
     cudaStream_t s = S->reg_stream;
@@ -428,7 +433,21 @@ alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t
     size_t tbytes = 0;
     alsub_topology_bytes(R->topo, &tbytes);
     R->bytes = tbytes + mb;
-    if (frame_path != ALSUB_FRAMES_EVAL && levels > 0) {
+    if (frame_path == ALSUB_FRAMES_OPERATOR_MATRIX_FREE && levels > 0) {
+        // the stencil kernels on the cached topology behind alsub_apply_operator: no matrix, only
+        // the operator's own scratch (the intermediate levels)
+        alsub_operator_t op = nullptr;
+        st = alsub_build_operator(R->topo, ALSUB_OP_MATRIX_FREE, s, &op);
+        if (st != ALSUB_OK) {
+            cudaStreamSynchronize(s);
+            free_resident(*R);
+            return st;
+        }
+        size_t ob = 0;
+        alsub_operator_bytes(op, &ob);
+        R->op = op;
+        R->bytes = tbytes + mb + ob;
+    } else if (frame_path != ALSUB_FRAMES_EVAL && levels > 0) {
         alsub_operator_t op = nullptr;
         if (alsub_build_operator(R->topo, ALSUB_OP_COMPOSE, s, &op) == ALSUB_OK) {
             size_t ob = 0;

@@ -80,6 +80,29 @@ def test_caller_allocator_holds_everything_and_matches(scheme, mesh, levels):
     assert A.bytes_live == 0 and not A.live and A.frees == A.allocs
 
 
+def test_handles_released_parent_first():
+    """A handle's release reads nothing of the handle it was made from, so the mesh, then the
+    topology, then its operators (matrix-free, chain and transposes) may be destroyed in that
+    order, as Python's cycle collector may do; every byte goes back to the caller's allocator."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    A = alsub.DeviceAllocator()
+    m = synth.torus_cc_mixed(12, 10, crease_frac=0.1, seed=65)
+    M = alsub.Mesh.from_dict(m, "cc", allocator=A)
+    T = alsub.Topology(M, 3)
+    P0 = torch.from_numpy(np.ascontiguousarray(m["P"], dtype=np.float32)).cuda()
+    ops = [alsub.Operator(T, chain=False, matrix_free=True), alsub.Operator(T, chain=True, transpose=True)]
+    want = T.refine_vertices(P0)
+    assert torch.equal(ops[0].apply(P0), want)
+    torch.cuda.synchronize()
+    M.close()
+    T.close()
+    for o in ops:
+        o.close()
+    torch.cuda.synchronize()
+    assert A.bytes_live == 0 and not A.live and A.frees == A.allocs
+
+
 def test_allocator_without_memory_is_oom():
     from paper_1809_06047_gb300 import alsub
     A = alsub.DeviceAllocator(fail=True)

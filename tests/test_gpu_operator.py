@@ -106,6 +106,60 @@ def test_apply_chain_composite_transpose(scheme, fn, levels):
         np.testing.assert_allclose(g0, want, atol=1e-4 * np.abs(want).max())
 
 
+@pytest.mark.parametrize("scheme,fn,levels", CASES)
+def test_matrix_free_apply_and_transpose(scheme, fn, levels):
+    """ALSUB_OP_MATRIX_FREE: apply is the eval kernels' result bit for bit (and so within the
+    tolerance of the oracle); with ALSUB_OP_TRANSPOSE the stored transposes give the chain's
+    adjoint bit for bit; no forward matrix is stored."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    mesh = fn()
+    ref = oracle.subdivide(mesh, levels, scheme, keep_all=True)
+    M, T, P0 = _setup(mesh, scheme, levels)
+    pi = _maps(scheme, T, ref)
+    ev = T.refine_vertices(P0).cpu().numpy()
+    mf = alsub.Operator(T, chain=False, matrix_free=True, transpose=True)
+    chain = alsub.Operator(T, chain=True, transpose=True)
+    got = [mf.apply(P0).cpu().numpy() for _ in range(3)]   # a one-off call, then a graph replay
+    T.status()
+    for g in got:
+        assert np.array_equal(g, ev)
+    err, diag = canon.position_error(pi[levels], got[0], ref[levels]["P"])
+    assert err <= gpu_util.POS_TOL * diag
+    gL = torch.from_numpy(np.random.default_rng(5).standard_normal((ev.shape[0], 3)).astype(np.float32)).cuda()
+    assert torch.equal(mf.apply_transpose(gL), chain.apply_transpose(gL))
+    with pytest.raises(alsub.AlsubError) as e:
+        mf.info(0)
+    assert e.value.status == 1
+    only = alsub.Operator(T, chain=False, matrix_free=True)
+    assert only.bytes() < mf.bytes()
+    with pytest.raises(alsub.AlsubError) as e:
+        only.apply_transpose(gL)
+    assert e.value.status == 1
+
+
+def test_matrix_free_applies_on_many_streams():
+    """Applies of one matrix-free operator issued on several streams share its scratch: each one
+    waits for the previous, so every result equals the eval kernels' for its own input."""
+    import torch
+    from paper_1809_06047_gb300 import alsub
+    m = synth.torus_cc_mixed(24, 20, crease_frac=0.1, seed=66)
+    M, T, P0 = _setup(m, "cc", 4)
+    op = alsub.Operator(T, chain=False, matrix_free=True)
+    streams = [torch.cuda.Stream() for _ in range(4)]
+    ins = [P0 * (1.0 + 0.25 * k) + k for k in range(8)]
+    torch.cuda.synchronize()
+    outs = []
+    for k, x in enumerate(ins):
+        s = streams[k % 4]
+        with torch.cuda.stream(s):
+            outs.append(op.apply(x, stream=s))
+    torch.cuda.synchronize()
+    for x, y in zip(ins, outs):
+        assert torch.equal(y, T.refine_vertices(x))
+    T.status()
+
+
 def test_operator_matches_refine_vertices_and_is_deterministic():
     """Config-2 mesh at level 4: R P0 (composite) equals the fused eval within tolerance; two
     builds give identical bits."""

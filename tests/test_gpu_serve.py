@@ -72,7 +72,8 @@ def test_mix_equals_alone():
     w = synth.serving_requests(n_requests=40, n_resident=4, fmin=200, fmax=3000, rate_hz=1e5, seed=777)
     S = alsub.Server(budget_bytes=8 << 30, max_slots=6)
     try:
-        rids = [S.register(m, m["scheme"], m["levels"], frames=("operator", "eval", "fastest")[i % 3])
+        rids = [S.register(m, m["scheme"], m["levels"],
+                           frames=("operator", "eval", "fastest", "operator_mf")[i % 4])
                 for i, m in enumerate(w["resident"])]
         tickets = []
         for q in w["requests"]:
@@ -133,6 +134,32 @@ def test_frame_against_oracle_and_pinned_output():
     gpu[-1]["P"] = out
     gpu_util.compare("cc", gpu, ref, pos_levels={3})
     assert np.array_equal(r2["P"], out)      # same path, same bits
+
+
+@pytest.mark.parametrize("frames", ["operator_mf", "eval"])
+def test_frames_of_one_resident_in_flight_together(frames):
+    """Many frames of one resident admitted side by side (six slots, three workers): each result is
+    bit for bit the plain eval call's on its own input. Matrix-free operator frames share the
+    operator's scratch and run one after another on the device; eval frames use their own."""
+    from paper_1809_06047_gb300 import alsub
+    m = synth.torus_cc_mixed(30, 24, crease_frac=0.1, seed=88)
+    rng = np.random.default_rng(89)
+    Ps = [(m["P"] + 0.05 * rng.standard_normal(m["P"].shape)).astype(np.float32) for _ in range(24)]
+    S = alsub.Server(budget_bytes=4 << 30, max_slots=6)
+    try:
+        rid = S.register(m, "cc", 4, frames=frames)
+        tickets = [S.submit_frame(rid, P) for P in Ps]
+        results = [S.poll(t, timeout_us=60_000_000) for t in tickets]
+        st = S.stats()
+    finally:
+        S.close()
+    assert st["completed"] == len(Ps) and st["failed"] == 0
+    assert st["frames_operator" if frames == "operator_mf" else "frames_eval"] == len(Ps)
+    assert st["peak_in_flight"] > 1, st
+    for P, r in zip(Ps, results):
+        assert r["status"] == 0
+        assert np.array_equal(r["P"], _alone(m, "cc", 4, P))
+    _vs_oracle(m, "cc", 4, Ps[-1], results[-1]["P"])
 
 
 def test_timeout_pause_and_resume():

@@ -92,5 +92,13 @@ def test_sqrt3_features_refused_where_no_path():
         alsub.Operator(T, chain=True)
     assert e.value.status == 3
     with pytest.raises(alsub.AlsubError) as e:
+        alsub.Operator(T, chain=False, matrix_free=True, transpose=True)
+    assert e.value.status == 3
+    # the matrix-free operator needs no rows: it is the feature path's eval kernels
+    op = alsub.Operator(T, chain=False, matrix_free=True)
+    P0 = torch.from_numpy(np.ascontiguousarray(m["P"], np.float32)).cuda()
+    assert torch.equal(op.apply(P0), T.refine_vertices(P0))
+    T.status()
+    with pytest.raises(alsub.AlsubError) as e:
         alsub.Batch([T], [torch.from_numpy(m["P"]).cuda()])
     assert e.value.status == 3
