@@ -235,6 +235,8 @@ def serving_leg(w, n_slots: int = 16, budget: float = 40e9, fastest: bool = Fals
                  frames_operator=st["frames_operator"] - base["frames_operator"],
                  frames_eval=st["frames_eval"] - base["frames_eval"], meshes=st["meshes"] - base["meshes"],
                  host_start_ms_mean=st["host_start_ms_mean"], host_finish_ms_mean=st["host_finish_ms_mean"],
+                 host_start_frame_ms_mean=st["host_start_frame_ms_mean"],
+                 host_start_mesh_ms_mean=st["host_start_mesh_ms_mean"],
                  peak_in_flight=st["peak_in_flight"], device_overlap_peak=st["device_overlap_peak"])
         return d
 
@@ -702,6 +704,8 @@ def summary_of(out):
         "patches": [("ms", "eval_ms"), ("frac", "roofline", "frac")],
         "serving": [("p50", "served", "p50_ms"), ("p99", "served", "p99_ms"), ("rps", "served", "throughput_rps"),
                     ("overlap", "served", "device_overlap_peak"), ("host_start", "served", "host_start_ms_mean"),
+                    ("host_frame", "served", "host_start_frame_ms_mean"),
+                    ("host_mesh", "served", "host_start_mesh_ms_mean"),
                     ("plain_p50", "plain", "p50_ms"), ("plain_p99", "plain", "p99_ms"),
                     ("plain_rps", "plain", "throughput_rps")],
     }

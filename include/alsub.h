@@ -610,6 +610,8 @@ typedef struct {
                                               stream after its input copy and after its kernels)
                                               were open at one instant: > 1 means the work of
                                               different requests overlapped on the GPU */
+    double host_start_frame_ms_mean;       /* host_start_ms_mean over the FRAME requests */
+    double host_start_mesh_ms_mean;        /* host_start_ms_mean over the MESH requests */
 } alsub_serve_stats;
 
 /* Start a server on the current device. max_slots 1..64 (concurrent requests), budget > 0. The
@@ -628,8 +630,12 @@ alsub_status alsub_serve_create(size_t hbm_budget_bytes, int32_t max_slots, alsu
  *   ALSUB_FRAMES_OPERATOR_MATRIX_FREE  alsub_apply_operator on a matrix-free operator
  *                          (ALSUB_OP_MATRIX_FREE): R's rows are the stencils the eval kernels
  *                          evaluate, so a frame costs what an EVAL frame costs and nothing but the
- *                          operator's scratch is stored; frames of one resident run one after
- *                          another on the device (they share that scratch).
+ *                          operator's scratch is stored.
+ * Every resident also holds its frames' device input and output (12 V_0 + 12 V_L bytes, counted in
+ * the budget): a frame copies its positions into them, runs there (a repeated frame replays the
+ * topology's captured graph: one launch) and is copied out, so the frames of one resident run one
+ * after another on the device while those of different residents overlap; a FRAME request itself
+ * takes no device memory at admission.
  * Mesh arguments as alsub_mesh_create. *resident receives the id FRAME requests name.
  * Errors: those of the mesh, topology and operator calls, INVALID_ARG for an unknown mode, OOM when
  * the topology does not fit the budget.

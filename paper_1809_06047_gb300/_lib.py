@@ -45,7 +45,8 @@ class ServeStats(ctypes.Structure):
                 ("hbm_budget", ctypes.c_uint64), ("hbm_in_use", ctypes.c_uint64), ("hbm_peak", ctypes.c_uint64),
                 ("frames_operator", c_int64), ("frames_eval", c_int64), ("meshes", c_int64),
                 ("host_start_ms_mean", ctypes.c_double), ("host_finish_ms_mean", ctypes.c_double),
-                ("peak_in_flight", c_int64), ("device_overlap_peak", c_int64)]
+                ("peak_in_flight", c_int64), ("device_overlap_peak", c_int64),
+                ("host_start_frame_ms_mean", ctypes.c_double), ("host_start_mesh_ms_mean", ctypes.c_double)]
 
 
 # name -> argtypes; every function returns alsub_status (int32) unless listed in _RESTYPE

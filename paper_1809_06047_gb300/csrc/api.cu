@@ -659,6 +659,138 @@ alsub_status alsub::ensure_helpers(TopoImpl &T, cudaStream_t s) {
     return finish("ensure_helpers");
 }
 
+alsub_status alsub::create_mesh(alsub_scheme scheme, int32_t V, int32_t F, const int32_t *off_h,
+                                const int32_t *fv_h, int32_t K, const int32_t *cv_h, const float *cs_h,
+                                const alsub_allocator *allocator, const long long *B_stated, void *stream,
+                                alsub_mesh_t *out) {
+    if (!out) return fail(ALSUB_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (allocator && (!allocator->alloc || !allocator->free))
+        return fail(ALSUB_ERR_INVALID_ARG, "allocator: both alloc and free are needed");
+    *out = nullptr;
+    if (scheme < ALSUB_CATMULL_CLARK || scheme > ALSUB_SQRT3) return fail(ALSUB_ERR_INVALID_ARG, "bad scheme");
+    if (V <= 0 || F <= 0 || !fv_h || K < 0 || (K > 0 && (!cv_h || !cs_h)))
+        return fail(ALSUB_ERR_INVALID_ARG, "bad mesh arguments");
+    const int order = scheme == ALSUB_CATMULL_CLARK ? 4 : 3;
+    std::vector<int32_t> off(F + 1);
+    if (off_h) {
+        if (off_h[0] != 0) return fail(ALSUB_ERR_INVALID_ARG, "face_offsets[0] must be 0");
+        for (int r = 0; r < F; r++) {
+            long long c = (long long)off_h[r + 1] - off_h[r];
+            if (c < 3) return fail(ALSUB_ERR_INVALID_ARG, "face %d has order %lld < 3", r, c);
+            if (scheme != ALSUB_CATMULL_CLARK && c != 3)
+                return fail(ALSUB_ERR_INVALID_ARG, "face %d is not a triangle", r);
+        }
+        memcpy(off.data(), off_h, sizeof(int32_t) * (F + 1));
+    } else {
+        if ((long long)F * order > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "counts exceed int32");
+        for (int r = 0; r <= F; r++) off[r] = r * order;
+    }
+    const long long nnz = off[F];
+    std::vector<int> used(V, 0), mark(V, -1);
+    for (int r = 0; r < F; r++) {
+        for (int x = off[r]; x < off[r + 1]; x++) {
+            int v = fv_h[x];
+            if (v < 0 || v >= V) return fail(ALSUB_ERR_INVALID_ARG, "face %d: vertex id %d out of range", r, v);
+            if (mark[v] == r) return fail(ALSUB_ERR_INVALID_ARG, "face %d repeats vertex %d", r, v);
+            mark[v] = r;
+            used[v] = 1;
+        }
+    }
+    for (int v = 0; v < V; v++)
+        if (!used[v]) return fail(ALSUB_ERR_INVALID_ARG, "vertex %d is in no face", v);
+    std::vector<int32_t> cv;
+    std::vector<float> cs;
+    float smax = 0.f;
+    for (int i = 0; i < K; i++) {
+        int a = cv_h[2 * i], b = cv_h[2 * i + 1];
+        float sg = cs_h[i];
+        if (a < 0 || a >= V || b < 0 || b >= V || a == b)
+            return fail(ALSUB_ERR_INVALID_ARG, "crease %d: bad endpoints (%d, %d)", i, a, b);
+        if (!(sg >= 0.f)) return fail(ALSUB_ERR_INVALID_ARG, "crease %d: sharpness must be >= 0", i);
+        // sqrt(3) keeps the infinitely sharp creases (feature edges); finite sharpness has no
+        // sqrt(3) rule
+        if (sg == 0.f || (scheme == ALSUB_SQRT3 && !isinf(sg))) continue;
+        cv.push_back(a); cv.push_back(b); cs.push_back(sg);
+        smax = std::max(smax, sg);
+    }
+    alsub_mesh_s *h = new (std::nothrow) alsub_mesh_s();
+    if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
+    MeshImpl &M = h->m;
+    if (allocator) {
+        M.alloc.alloc = allocator->alloc;
+        M.alloc.free = allocator->free;
+        M.alloc.ctx = allocator->ctx;
+    }
+    M.scheme = scheme; M.V = V; M.F = F; M.nnz = (int)nnz; M.K = (int)cs.size();
+    M.sigma_max = smax;
+    M.stream = (cudaStream_t)stream;
+    cudaStream_t s = M.stream;
+    upload_weight_tables();
+    auto cleanup = [&]() {
+        if (M.d_block) dev_free(M.alloc, M.d_block, s);
+        delete h;
+    };
+    // one allocation: face offsets, corners, crease pairs and sharpness, the status word
+    const size_t b_off = align256(sizeof(int) * ((size_t)F + 1)), b_fv = align256(sizeof(int) * (size_t)nnz);
+    const size_t b_cv = align256(sizeof(int) * 2 * (size_t)M.K), b_cs = align256(sizeof(float) * (size_t)M.K);
+    cudaError_t e = dev_malloc(M.alloc, &M.d_block, b_off + b_fv + b_cv + b_cs + 256, s);
+    if (e == cudaSuccess) {
+        char *p = (char *)M.d_block;
+        M.d_off = (int *)p;
+        M.d_fv = (int *)(p + b_off);
+        M.d_cv = M.K ? (int *)(p + b_off + b_fv) : nullptr;
+        M.d_cs = M.K ? (float *)(p + b_off + b_fv + b_cv) : nullptr;
+        M.d_status = (int *)(p + b_off + b_fv + b_cv + b_cs);
+        e = cudaMemsetAsync(M.d_status, 0, sizeof(int), s);
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_off, off.data(), sizeof(int) * (F + 1), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_fv, fv_h, sizeof(int) * nnz, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cv, cv.data(), sizeof(int) * 2 * M.K, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cs, cs.data(), sizeof(float) * M.K, cudaMemcpyHostToDevice, s);
+    // the host vectors (off, cv, cs) die on return: the copies complete at the stream
+    // synchronisation below (the boundary scan's, which runs after them on the same stream)
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        cleanup();
+        if (e == cudaErrorMemoryAllocation) return fail(ALSUB_ERR_OOM, "mesh upload: out of device memory");
+        return cuda_fail(e, "mesh upload");
+    }
+    if (B_stated) {
+        // the caller's count, checked on the device: a different one fails the builds that follow
+        alsub_status st = mesh_boundary_check(M, s, *B_stated);
+        if (st != ALSUB_OK) {
+            cudaStreamSynchronize(s);          // the uploads read the host vectors
+            cudaGetLastError();
+            cleanup();
+            return st;
+        }
+        // (copies from pageable host memory have been staged when cudaMemcpyAsync returns, so the
+        // local vectors may die on return)
+    } else {
+        // boundary edges (Sec. 3.2 "Boundaries"; Loop takes the same rules, sqrt(3) Kobbelt's):
+        // their number sizes every level; the paper gives no rule for a crease that meets the
+        // boundary, so such input is refused
+        long long B = 0;
+        bool crease_at_boundary = false;
+        alsub_status st = mesh_boundary_scan(M, s, &B, &crease_at_boundary);
+        if (st == ALSUB_OK && crease_at_boundary)
+            st = fail(ALSUB_ERR_UNSUPPORTED, "a crease touches a boundary vertex");
+        if (st == ALSUB_OK && ((nnz + B) % 2 || B > kI32))
+            st = fail(ALSUB_ERR_NONMANIFOLD, "inconsistent boundary (a directed edge repeats)");
+        if (st != ALSUB_OK) {
+            cudaStreamSynchronize(s);          // the uploads read the host vectors
+            cudaGetLastError();
+            cleanup();
+            return st;
+        }
+        M.B = (int)B;
+    }
+    *out = h;
+    return ALSUB_OK;
+}
+
 extern "C" {
 
 const char *alsub_last_error(void) { return g_err.c_str(); }
@@ -725,115 +857,7 @@ alsub_status alsub_mesh_create(alsub_scheme scheme, int32_t V, int32_t F, const 
 alsub_status alsub_mesh_create_ex(alsub_scheme scheme, int32_t V, int32_t F, const int32_t *off_h,
                                   const int32_t *fv_h, int32_t K, const int32_t *cv_h, const float *cs_h,
                                   const alsub_allocator *allocator, void *stream, alsub_mesh_t *out) {
-    if (!out) return fail(ALSUB_ERR_INVALID_ARG, "out is NULL");
-    *out = nullptr;
-    if (allocator && (!allocator->alloc || !allocator->free))
-        return fail(ALSUB_ERR_INVALID_ARG, "allocator: both alloc and free are needed");
-    *out = nullptr;
-    if (scheme < ALSUB_CATMULL_CLARK || scheme > ALSUB_SQRT3) return fail(ALSUB_ERR_INVALID_ARG, "bad scheme");
-    if (V <= 0 || F <= 0 || !fv_h || K < 0 || (K > 0 && (!cv_h || !cs_h)))
-        return fail(ALSUB_ERR_INVALID_ARG, "bad mesh arguments");
-    const int order = scheme == ALSUB_CATMULL_CLARK ? 4 : 3;
-    std::vector<int32_t> off(F + 1);
-    if (off_h) {
-        if (off_h[0] != 0) return fail(ALSUB_ERR_INVALID_ARG, "face_offsets[0] must be 0");
-        for (int r = 0; r < F; r++) {
-            long long c = (long long)off_h[r + 1] - off_h[r];
-            if (c < 3) return fail(ALSUB_ERR_INVALID_ARG, "face %d has order %lld < 3", r, c);
-            if (scheme != ALSUB_CATMULL_CLARK && c != 3)
-                return fail(ALSUB_ERR_INVALID_ARG, "face %d is not a triangle", r);
-        }
-        memcpy(off.data(), off_h, sizeof(int32_t) * (F + 1));
-    } else {
-        if ((long long)F * order > kI32) return fail(ALSUB_ERR_UNSUPPORTED, "counts exceed int32");
-        for (int r = 0; r <= F; r++) off[r] = r * order;
-    }
-    const long long nnz = off[F];
-    std::vector<int> used(V, 0), mark(V, -1);
-    for (int r = 0; r < F; r++) {
-        for (int x = off[r]; x < off[r + 1]; x++) {
-            int v = fv_h[x];
-            if (v < 0 || v >= V) return fail(ALSUB_ERR_INVALID_ARG, "face %d: vertex id %d out of range", r, v);
-            if (mark[v] == r) return fail(ALSUB_ERR_INVALID_ARG, "face %d repeats vertex %d", r, v);
-            mark[v] = r;
-            used[v] = 1;
-        }
-    }
-    for (int v = 0; v < V; v++)
-        if (!used[v]) return fail(ALSUB_ERR_INVALID_ARG, "vertex %d is in no face", v);
-    std::vector<int32_t> cv;
-    std::vector<float> cs;
-    float smax = 0.f;
-    for (int i = 0; i < K; i++) {
-        int a = cv_h[2 * i], b = cv_h[2 * i + 1];
-        float sg = cs_h[i];
-        if (a < 0 || a >= V || b < 0 || b >= V || a == b)
-            return fail(ALSUB_ERR_INVALID_ARG, "crease %d: bad endpoints (%d, %d)", i, a, b);
-        if (!(sg >= 0.f)) return fail(ALSUB_ERR_INVALID_ARG, "crease %d: sharpness must be >= 0", i);
-        // sqrt(3) keeps the infinitely sharp creases (feature edges); finite sharpness has no
-        // sqrt(3) rule
-        if (sg == 0.f || (scheme == ALSUB_SQRT3 && !isinf(sg))) continue;
-        cv.push_back(a); cv.push_back(b); cs.push_back(sg);
-        smax = std::max(smax, sg);
-    }
-    alsub_mesh_s *h = new (std::nothrow) alsub_mesh_s();
-    if (!h) return fail(ALSUB_ERR_OOM, "host allocation failed");
-    MeshImpl &M = h->m;
-    if (allocator) {
-        M.alloc.alloc = allocator->alloc;
-        M.alloc.free = allocator->free;
-        M.alloc.ctx = allocator->ctx;
-    }
-    M.scheme = scheme; M.V = V; M.F = F; M.nnz = (int)nnz; M.K = (int)cs.size();
-    M.sigma_max = smax;
-    M.stream = (cudaStream_t)stream;
-    cudaStream_t s = M.stream;
-    upload_weight_tables();
-    auto cleanup = [&]() {
-        if (M.d_off) dev_free(M.alloc, M.d_off, s);
-        if (M.d_fv) dev_free(M.alloc, M.d_fv, s);
-        if (M.d_cv) dev_free(M.alloc, M.d_cv, s);
-        if (M.d_cs) dev_free(M.alloc, M.d_cs, s);
-        delete h;
-    };
-    cudaError_t e = dev_malloc(M.alloc, &M.d_off, sizeof(int) * (F + 1), s);
-    if (e == cudaSuccess) e = dev_malloc(M.alloc, &M.d_fv, sizeof(int) * nnz, s);
-    if (e == cudaSuccess && M.K) e = dev_malloc(M.alloc, &M.d_cv, sizeof(int) * 2 * M.K, s);
-    if (e == cudaSuccess && M.K) e = dev_malloc(M.alloc, &M.d_cs, sizeof(float) * M.K, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_off, off.data(), sizeof(int) * (F + 1), cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(M.d_fv, fv_h, sizeof(int) * nnz, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cv, cv.data(), sizeof(int) * 2 * M.K, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && M.K) e = cudaMemcpyAsync(M.d_cs, cs.data(), sizeof(float) * M.K, cudaMemcpyHostToDevice, s);
-    // the host vectors die on return: the copies complete at the stream synchronisation below
-    // (the boundary scan's, which runs after them on the same stream)
-    if (e != cudaSuccess) {
-        cudaStreamSynchronize(s);
-        cudaGetLastError();
-        cleanup();
-        if (e == cudaErrorMemoryAllocation) return fail(ALSUB_ERR_OOM, "mesh upload: out of device memory");
-        return cuda_fail(e, "mesh upload");
-    }
-    {
-        // boundary edges (Sec. 3.2 "Boundaries"; Loop takes the same rules, sqrt(3) Kobbelt's):
-        // their number sizes every level; the paper gives no rule for a crease that meets the
-        // boundary, so such input is refused
-        long long B = 0;
-        bool crease_at_boundary = false;
-        alsub_status st = mesh_boundary_scan(M, s, &B, &crease_at_boundary);
-        if (st == ALSUB_OK && crease_at_boundary)
-            st = fail(ALSUB_ERR_UNSUPPORTED, "a crease touches a boundary vertex");
-        if (st == ALSUB_OK && ((nnz + B) % 2 || B > kI32))
-            st = fail(ALSUB_ERR_NONMANIFOLD, "inconsistent boundary (a directed edge repeats)");
-        if (st != ALSUB_OK) {
-            cudaStreamSynchronize(s);          // the uploads read the host vectors
-            cudaGetLastError();
-            cleanup();
-            return st;
-        }
-        M.B = (int)B;
-    }
-    *out = h;
-    return ALSUB_OK;
+    return alsub::create_mesh(scheme, V, F, off_h, fv_h, K, cv_h, cs_h, allocator, nullptr, stream, out);
 }
 
 alsub_status alsub_mesh_info(alsub_mesh_t h, int32_t *scheme, int64_t *V, int64_t *F, int64_t *nnz,
@@ -924,6 +948,11 @@ alsub_status alsub_mesh_boundary_edges(alsub_mesh_t h, int64_t *boundary_edges) 
 alsub_status alsub_mesh_destroy(alsub_mesh_t h) {
     if (!h) return ALSUB_OK;
     MeshImpl &M = h->m;
+    if (M.d_block) {
+        dev_free(M.alloc, M.d_block, M.stream);
+        M.d_off = M.d_fv = M.d_cv = nullptr;
+        M.d_cs = nullptr;
+    }
     for (void *p : {(void *)M.d_off, (void *)M.d_fv, (void *)M.d_cv, (void *)M.d_cs, (void *)M.d_vmap,
                     (void *)M.d_fmap})
         if (p) dev_free(M.alloc, p, M.stream);

@@ -10,6 +10,9 @@
 
 namespace alsub {
 
+// Sizes of carved sub-allocations, rounded up to 256 bytes.
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
 // The crease matrix C_l of one level (Sec. 3.3) as a list of tagged edges. Level 0 keeps the
 // input order; level l + 1 holds the two halves of entry i at 2i and 2i + 1, so entries whose
 // sharpness decayed to 0 stay in the list as inert entries.
@@ -82,6 +85,10 @@ struct MeshImpl {
     int B = 0;                 // boundary edges (Catmull-Clark open meshes)
     int *d_vmap = nullptr;     // extracted meshes (selective subdivision): kept vertex -> source vertex
     int *d_fmap = nullptr;     //                                           kept face -> source face
+    void *d_block = nullptr;   // one allocation holding d_off, d_fv, d_cv, d_cs and d_status (or
+                               // null: those are allocated one by one)
+    int *d_status = nullptr;   // checks of the mesh that run on the device (the boundary edge count
+                               // a caller stated): 0, or the error each level-0 build starts from
     cudaStream_t stream = nullptr;
     DevAlloc alloc;            // every device array of the mesh and of its handles
 };
@@ -201,6 +208,10 @@ void level0_creases(TopoImpl &T, cudaStream_t s);
 // Boundary edges of a Catmull-Clark control mesh (corners whose reverse edge is in no face) and
 // whether a crease touches a boundary vertex; synchronises `s`.
 alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary);
+// The same scan with the count a caller stated (M.B = B_stated) checked on the device instead of
+// read back: M.d_status becomes UNSUPPORTED (a crease touches a boundary vertex), NONMANIFOLD
+// (nnz + B odd) or INVALID_ARG (another count than B_stated). Nothing is synchronised.
+alsub_status mesh_boundary_check(MeshImpl &M, cudaStream_t s, long long B_stated);
 // Vertices on a boundary edge (flag 1) of a face table (off == nullptr: uniform quads).
 alsub_status level_boundary_flags(int V, int F, long long nnz, const int *off, const int *fv, int *flag,
                                   const DevAlloc &A, cudaStream_t s);
@@ -288,6 +299,12 @@ alsub_status refine_call(TopoImpl &T, const float *P0, float *PL, void *scratch,
 // One vertex refinement of a built topology, its kernels launched directly on `s`: no graph is
 // captured or replayed and no stream or event is made (the graph cache is left as it is).
 alsub_status refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s);
+// alsub_mesh_create_ex behind the C ABI. B_stated null: the boundary edges are counted on the
+// device and read back (the call synchronises `stream`); else the caller states their number and
+// the count is checked on the device (mesh_boundary_check), so nothing waits for the device.
+alsub_status create_mesh(alsub_scheme scheme, int32_t V, int32_t F, const int32_t *off_h, const int32_t *fv_h,
+                         int32_t K, const int32_t *cv_h, const float *cs_h, const alsub_allocator *allocator,
+                         const long long *B_stated, void *stream, alsub_mesh_t *out);
 
 // The implementation behind a topology handle.
 TopoImpl *topology_impl(alsub_topology_t h);

@@ -62,9 +62,9 @@ __device__ int dir_find(const DirTable &t, int a, int b) {
     return -1;
 }
 
-// Start of a level-0 build: the status word, the vertex degrees and designated corners, and the
-// directed-edge table cleared in one pass.
-__global__ void k_clear0(int V, DirTable tab, int *status, int *deg, unsigned *vc) {
+// Start of a level-0 build: the status word (from the mesh's device checks), the vertex degrees
+// and designated corners, and the directed-edge table cleared in one pass.
+__global__ void k_clear0(int V, DirTable tab, int *status, const int *mstatus, int *deg, unsigned *vc) {
     pdl_wait();
     pdl_trigger();
     const long long n = (long long)tab.mask + 1;
@@ -75,7 +75,7 @@ __global__ void k_clear0(int V, DirTable tab, int *status, int *deg, unsigned *v
             deg[i] = 0;
             vc[i] = ~0u;
         }
-        if (i == 0) *status = 0;
+        if (i == 0) *status = mstatus ? *mstatus : 0;    // the mesh's own device checks
     }
 }
 
@@ -239,6 +239,15 @@ __global__ void k_mb_crease(int K, const int *__restrict__ cv, const int *__rest
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < K && (bv[cv[2 * i]] || bv[cv[2 * i + 1]])) out[1] = 1;
 }
+// The scan's verdict against the boundary edge count a caller stated, into the mesh's status word.
+__global__ void k_mb_check(const int *__restrict__ out, long long nnz, long long B, int *mstatus) {
+    const long long b = out[0];
+    int st = 0;
+    if (out[1]) st = ALSUB_ERR_UNSUPPORTED;                  // a crease touches a boundary vertex
+    else if ((nnz + b) % 2) st = ALSUB_ERR_NONMANIFOLD;      // a directed edge repeats
+    else if (b != B) st = ALSUB_ERR_INVALID_ARG;             // not the stated count
+    *mstatus = st;
+}
 
 // Edge ids (an owner's own, else its twin's), owner corner of each edge, and the ring step
 // twin(prev(x)).
@@ -347,7 +356,7 @@ void level0_build(TopoImpl &T, cudaStream_t s) {
     const int V = M.V, F = M.F, nnz = M.nnz, E0 = (int)L0.E;
     const long long slots = (long long)T.dir.mask + 1;
     launch_pdl(k_clear0, std::min<unsigned>(grid_for(std::max<long long>(slots, V)), 1024u), kBlock, s, V, T.dir,
-               T.status, T.deg, reinterpret_cast<unsigned *>(T.vc0));
+               T.status, (const int *)M.d_status, T.deg, reinterpret_cast<unsigned *>(T.vc0));
     launch_pdl(k_faces, grid_for(F), kBlock, s, F, (const int *)M.d_off, (const int *)M.d_fv, T.cf0, T.nx0, T.pv0,
                T.deg, reinterpret_cast<unsigned *>(T.vc0), T.dir, T.status);
     const unsigned nb = grid_for(nnz);
@@ -393,9 +402,11 @@ alsub_status level_boundary_flags(int V, int F, long long n, const int *off, con
     return ALSUB_OK;
 }
 
-alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary) {
-    *B = 0;
-    *crease_at_boundary = false;
+namespace {
+
+// The scan's kernels into a temporary buffer (released after them, stream-ordered); *out gets
+// the device address of [boundary edges, crease at a boundary].
+alsub_status boundary_scan_kernels(MeshImpl &M, cudaStream_t s, char **buf_out, int **out_dev) {
     int k = 4;
     while ((1LL << k) < 2LL * M.nnz) k++;
     const size_t slots = (size_t)1 << k;
@@ -414,6 +425,32 @@ alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool 
     k_mb_insert<<<grid_for(M.F), kBlock, 0, s>>>(M.F, M.d_off, M.d_fv, tab);
     k_mb_count<<<grid_for(M.F), kBlock, 0, s>>>(M.F, M.d_off, M.d_fv, tab, bv, out);
     if (M.K > 0) k_mb_crease<<<grid_for(M.K), kBlock, 0, s>>>(M.K, M.d_cv, bv, out);
+    *buf_out = buf;
+    *out_dev = out;
+    return ALSUB_OK;
+}
+
+}  // namespace
+
+alsub_status mesh_boundary_check(MeshImpl &M, cudaStream_t s, long long B_stated) {
+    char *buf = nullptr;
+    int *out = nullptr;
+    alsub_status st = boundary_scan_kernels(M, s, &buf, &out);
+    if (st != ALSUB_OK) return st;
+    k_mb_check<<<1, 1, 0, s>>>(out, (long long)M.nnz, B_stated, M.d_status);
+    dev_free(M.alloc, buf, s);
+    M.B = (int)B_stated;
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? ALSUB_OK : report(ALSUB_ERR_DEVICE, "mesh boundary check failed");
+}
+
+alsub_status mesh_boundary_scan(MeshImpl &M, cudaStream_t s, long long *B, bool *crease_at_boundary) {
+    *B = 0;
+    *crease_at_boundary = false;
+    char *buf = nullptr;
+    int *out = nullptr;
+    alsub_status st = boundary_scan_kernels(M, s, &buf, &out);
+    if (st != ALSUB_OK) return st;
     int h[2] = {0, 0};
     cudaError_t e = cudaMemcpyAsync(h, out, sizeof(h), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -45,17 +45,21 @@ size_t mesh_bytes(long long F, long long nnz, long long K) {
     return 4 * (size_t)(F + 1) + 4 * (size_t)nnz + 12 * (size_t)K;
 }
 
-size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Resident {
     alsub_mesh_t mesh = nullptr;
     alsub_topology_t topo = nullptr;
-    alsub_operator_t op = nullptr;   // kept only when its SpMV beat the eval kernels
+    alsub_operator_t op = nullptr;   // the composite (or matrix-free) operator frames run on
     int64_t V0 = 0, VL = 0;
-    size_t bytes = 0;                // topology + mesh + operator
-    size_t scratch = 0;              // eval scratch a frame needs when served without the operator
+    size_t bytes = 0;                // topology + mesh + operator + frame buffers
+    // The frames' device buffers, the resident's own: with the same input and output every frame,
+    // a repeated frame replays the topology's captured graph. Frames of the resident therefore run
+    // one after another on the device: a frame's input copy waits for in_free (the previous frame's
+    // kernels have read d_in) and its kernels for out_free (the previous output copy has read d_out).
+    float *d_in = nullptr, *d_out = nullptr;
+    cudaEvent_t in_free = nullptr, out_free = nullptr;
     // the topology's launch state (its graph cache, the fork and join events of its side streams)
-    // is shared by every frame of this resident: one worker enqueues at a time
+    // and the two events are shared by every frame of this resident: one worker enqueues at a time
     std::mutex launch;
 };
 
@@ -130,6 +134,7 @@ struct alsub_server_s {
     uint64_t old_threshold = 0;
     std::vector<double> lat;         // latencies of completed requests (s)
     double host_start_sum = 0, host_finish_sum = 0;
+    double host_start_frames = 0, host_start_meshes = 0;   // host_start_sum split by kind
     int64_t completed = 0, failed = 0, frames_op = 0, frames_eval = 0, meshes = 0;
     double first_submit = -1, last_done = 0;
 };
@@ -142,43 +147,54 @@ alsub_status start(Slot &sl, Job &j) {
     const bool direct = j.user_out && j.user_pinned;    // D2H straight into the caller's buffer
     if (!grow_host(&sl.h_in, &sl.cap_in, n_in) || (!direct && !grow_host(&sl.h_out, &sl.cap_out, n_out)))
         return report(ALSUB_ERR_OOM, "server: page-locked staging allocation failed");
+    memcpy(sl.h_in, j.P0.data(), 4 * n_in);
+    float *dst = direct ? j.user_out : sl.h_out;
+    if (j.kind == ALSUB_REQ_FRAME) {
+        // the resident's own buffers, so a repeated frame replays one captured graph
+        Resident *R = j.res;
+        j.by_operator = R->op != nullptr;
+        std::lock_guard<std::mutex> g(R->launch);
+        cudaStreamWaitEvent(sl.stream, R->in_free, 0);
+        if (cudaMemcpyAsync(R->d_in, sl.h_in, 4 * n_in, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
+            return report(ALSUB_ERR_DEVICE, "server: input copy failed");
+        cudaStreamWaitEvent(sl.stream, R->out_free, 0);
+        cudaEventRecord(sl.ev_b, sl.stream);
+        const alsub_status fs = R->op ? alsub_apply_operator(R->op, R->d_in, R->d_out, sl.stream)
+                                      : alsub_refine_vertices(R->topo, R->d_in, R->d_out, nullptr, sl.stream);
+        if (fs != ALSUB_OK) return fs;
+        cudaEventRecord(R->in_free, sl.stream);
+        cudaEventRecord(sl.ev_c, sl.stream);
+        if (cudaMemcpyAsync(dst, R->d_out, 4 * n_out, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
+            cudaEventRecord(R->out_free, sl.stream) != cudaSuccess ||
+            cudaEventRecord(sl.ev, sl.stream) != cudaSuccess)
+            return report(ALSUB_ERR_DEVICE, "server: output copy failed");
+        return ALSUB_OK;
+    }
     alsub_status st = ALSUB_OK;
-    if (j.kind == ALSUB_REQ_MESH) {
-        st = alsub_mesh_create(j.scheme, j.V, j.F, j.off.data(), j.fv.data(), j.K,
-                               j.K ? j.cv.data() : nullptr, j.K ? j.cs.data() : nullptr, sl.stream, &sl.mesh);
-        int64_t B = 0;
-        if (st == ALSUB_OK) alsub_mesh_boundary_edges(sl.mesh, &B);
-        if (st == ALSUB_OK && B != j.B)
-            st = report(ALSUB_ERR_INVALID_ARG, "server: the mesh's boundary edge count differs from the request's");
+    {
+        // the stated boundary edge count is checked on the device (a different one is reported in
+        // the request's status when it is retired): nothing here waits for the device
+        const long long B = j.B;
+        st = alsub::create_mesh(j.scheme, j.V, j.F, j.off.empty() ? nullptr : j.off.data(), j.fv.data(), j.K,
+                                j.K ? j.cv.data() : nullptr, j.K ? j.cs.data() : nullptr, nullptr, &B, sl.stream,
+                                &sl.mesh);
         if (st == ALSUB_OK) st = alsub_topology_create(sl.mesh, j.levels, sl.stream, &sl.topo);
         if (st != ALSUB_OK) return st;
     }
-    Resident *R = j.res;
-    const size_t scratch = (j.kind == ALSUB_REQ_FRAME && !R->op) ? R->scratch : 0;
     const size_t b_in = align256(4 * n_in), b_out = align256(4 * n_out);
-    if (cudaMallocAsync(&sl.d_buf, b_in + b_out + scratch, sl.stream) != cudaSuccess) {
+    if (cudaMallocAsync(&sl.d_buf, b_in + b_out, sl.stream) != cudaSuccess) {
         cudaGetLastError();
         sl.d_buf = nullptr;
         return report(ALSUB_ERR_OOM, "server: device allocation failed");
     }
     float *d_in = (float *)sl.d_buf;
     float *d_out = (float *)((char *)sl.d_buf + b_in);
-    void *d_scratch = scratch ? (char *)sl.d_buf + b_in + b_out : nullptr;
-    memcpy(sl.h_in, j.P0.data(), 4 * n_in);
     if (cudaMemcpyAsync(d_in, sl.h_in, 4 * n_in, cudaMemcpyHostToDevice, sl.stream) != cudaSuccess)
         return report(ALSUB_ERR_DEVICE, "server: input copy failed");
     cudaEventRecord(sl.ev_b, sl.stream);
-    if (j.kind == ALSUB_REQ_FRAME) {
-        j.by_operator = R->op != nullptr;
-        std::lock_guard<std::mutex> g(j.res->launch);
-        st = R->op ? alsub_apply_operator(R->op, d_in, d_out, sl.stream)
-                   : alsub_refine_vertices(R->topo, d_in, d_out, d_scratch, sl.stream);
-    } else {
-        st = alsub_subdivide(sl.topo, d_in, d_out, nullptr, sl.stream);
-    }
+    st = alsub_subdivide(sl.topo, d_in, d_out, nullptr, sl.stream);
     if (st != ALSUB_OK) return st;
     cudaEventRecord(sl.ev_c, sl.stream);
-    float *dst = direct ? j.user_out : sl.h_out;
     if (cudaMemcpyAsync(dst, d_out, 4 * n_out, cudaMemcpyDeviceToHost, sl.stream) != cudaSuccess ||
         cudaEventRecord(sl.ev, sl.stream) != cudaSuccess)
         return report(ALSUB_ERR_DEVICE, "server: output copy failed");
@@ -217,6 +233,7 @@ void finish(alsub_server_s &S, Slot &sl, alsub_status st) {
     if (st == ALSUB_OK) {
         S.lat.push_back(t - j.t_submit);
         S.host_start_sum += j.host_start;
+        (j.kind == ALSUB_REQ_MESH ? S.host_start_meshes : S.host_start_frames) += j.host_start;
         S.host_finish_sum += j.host_finish;
         S.completed++;
         S.last_done = t;
@@ -306,6 +323,14 @@ void worker_loop(alsub_server_s *Sp, int first, int count) {
 }
 
 void free_resident(Resident &R) {
+    if (R.in_free) cudaEventSynchronize(R.in_free);
+    if (R.out_free) cudaEventSynchronize(R.out_free);
+    if (R.d_in) cudaFree(R.d_in);
+    if (R.d_out) cudaFree(R.d_out);
+    if (R.in_free) cudaEventDestroy(R.in_free);
+    if (R.out_free) cudaEventDestroy(R.out_free);
+    R.d_in = R.d_out = nullptr;
+    R.in_free = R.out_free = nullptr;
     if (R.op) alsub_operator_destroy(R.op);
     if (R.topo) alsub_topology_destroy(R.topo);
     if (R.mesh) alsub_mesh_destroy(R.mesh);
@@ -429,7 +454,6 @@ alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t
     const size_t mb = mesh_bytes(P->mesh->F, P->mesh->nnz, P->mesh->K);
     R->V0 = V;
     R->VL = P->L[levels].V;
-    alsub_refine_vertices_scratch_bytes(R->topo, &R->scratch);
     size_t tbytes = 0;
     alsub_topology_bytes(R->topo, &tbytes);
     R->bytes = tbytes + mb;
@@ -465,13 +489,12 @@ alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t
                 // trial: frames by each path on zero positions (the values do not change the time)
                 void *buf = nullptr;
                 const size_t n0 = align256(12 * (size_t)R->V0), nl = align256(12 * (size_t)R->VL);
-                if (cudaMallocAsync(&buf, n0 + nl + R->scratch, s) == cudaSuccess) {
+                if (cudaMallocAsync(&buf, n0 + nl, s) == cudaSuccess) {
                     cudaMemsetAsync(buf, 0, n0, s);
                     const float *p0 = (const float *)buf;
                     float *pl = (float *)((char *)buf + n0);
-                    void *scr = R->scratch ? (char *)buf + n0 + nl : nullptr;
                     t_op = time_ms(s, 3, [&] { alsub_apply_operator(op, p0, pl, s); });
-                    t_eval = time_ms(s, 3, [&] { alsub_refine_vertices(R->topo, p0, pl, scr, s); });
+                    t_eval = time_ms(s, 3, [&] { alsub_refine_vertices(R->topo, p0, pl, nullptr, s); });
                     cudaFreeAsync(buf, s);
                 }
                 cudaGetLastError();
@@ -485,6 +508,27 @@ alsub_status alsub_serve_register(alsub_server_t S, alsub_scheme scheme, int32_t
             }
         }
         cudaGetLastError();
+    }
+    {
+        // the frames' buffers and the events that order the frames on the device
+        const size_t io = align256(12 * (size_t)R->V0) + align256(12 * (size_t)R->VL);
+        bool ok = cudaMalloc(&R->d_in, align256(12 * (size_t)R->V0)) == cudaSuccess &&
+                  cudaMalloc(&R->d_out, align256(12 * (size_t)R->VL)) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            cudaStreamSynchronize(s);
+            free_resident(*R);
+            return report(ALSUB_ERR_OOM, "server: frame buffer allocation failed");
+        }
+        ok = cudaEventCreateWithFlags(&R->in_free, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&R->out_free, cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) {
+            cudaGetLastError();
+            cudaStreamSynchronize(s);
+            free_resident(*R);
+            return report(ALSUB_ERR_DEVICE, "server: event creation failed");
+        }
+        R->bytes += io;
     }
     if (cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
@@ -518,7 +562,7 @@ alsub_status alsub_serve_submit(alsub_server_t S, const alsub_request *r, uint64
         j->res = R;
         j->V = (int)R->V0;
         j->VL = R->VL;
-        j->need = align256(12 * (size_t)R->V0) + align256(12 * (size_t)R->VL) + (R->op ? 0 : R->scratch);
+        j->need = 0;                 // a frame runs in its resident's buffers
     } else if (r->kind == ALSUB_REQ_MESH) {
         if (r->num_verts <= 0 || r->num_faces <= 0 || !r->face_verts_host || r->levels < 0 ||
             r->scheme < ALSUB_CATMULL_CLARK || r->scheme > ALSUB_SQRT3 || r->num_creases < 0 ||
@@ -656,6 +700,9 @@ alsub_status alsub_serve_stats_get(alsub_server_t S, alsub_serve_stats *st) {
     st->meshes = S->meshes;
     st->host_start_ms_mean = S->completed ? 1e3 * S->host_start_sum / (double)S->completed : 0;
     st->host_finish_ms_mean = S->completed ? 1e3 * S->host_finish_sum / (double)S->completed : 0;
+    const int64_t nf = S->frames_op + S->frames_eval;
+    st->host_start_frame_ms_mean = nf ? 1e3 * S->host_start_frames / (double)nf : 0;
+    st->host_start_mesh_ms_mean = S->meshes ? 1e3 * S->host_start_meshes / (double)S->meshes : 0;
     st->peak_in_flight = S->running_peak;
     // most compute intervals open at one instant (an interval's end sorts before a start at the
     // same time, so touching intervals do not count as overlapping)
