@@ -390,8 +390,13 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
  *          kernels evaluate from the cached topology (apply = alsub_refine_vertices' kernels, in
  *          the operator's own scratch, a repeated apply replaying a captured graph), which moves the
  *          face tables of the levels and their positions instead of ~16 column indices and weights
- *          per refined vertex; with ALSUB_OP_TRANSPOSE (and no other flag) only the transposes of
- *          the R_l are stored. When combined with CHAIN or COMPOSE, apply takes the matrix-free
+ *          per refined vertex. Its transpose, on a closed Catmull-Clark mesh, is matrix-free too:
+ *          g_l = R_l^T g_{l+1} gathered per coarse vertex (its face points, the edge points around
+ *          and across its faces, its own and its neighbours' vertex points, with the crease rules),
+ *          no atomics, from per-vertex coefficients computed once here (16 bytes per vertex of
+ *          every level below the last; the levels' edge ids and twins are stored). With
+ *          ALSUB_OP_TRANSPOSE (and no other flag) the transposes of the R_l are stored and applied
+ *          instead (any scheme). When combined with CHAIN or COMPOSE, apply takes the matrix-free
  *          form and alsub_operator_info the stored matrices.
  * Weights: Catmull-Clark face row 1/c; edge row 1/4 on the endpoints and 1/(4c) on every vertex of
  * both faces (Eq. 2 with Eq. 1 expanded); vertex row (1 - 2/n) on the vertex, 1/n^2 on each
@@ -432,7 +437,10 @@ alsub_status alsub_apply_operator(alsub_operator_t op, const float *P0_dev, floa
 
 /* g_0 = R^T g_L (the adjoint of vertex refinement: vertex refinement is linear in P, so this is
  * the exact gradient of any loss of P_L with respect to P_0 given g_L = dLoss/dP_L). Needs
- * ALSUB_OP_TRANSPOSE. gL_dev: float[3 V_L], g0_dev: float[3 V_0]. */
+ * ALSUB_OP_TRANSPOSE (the stored transposes), or ALSUB_OP_MATRIX_FREE on a closed Catmull-Clark
+ * mesh (the per-vertex gather; its applies, like the forward ones, run one at a time and in
+ * order on the device). gL_dev: float[3 V_L], g0_dev: float[3 V_0]. Errors: INVALID_ARG when the
+ * operator has neither. */
 alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL_dev, float *g0_dev,
                                             void *stream);
 

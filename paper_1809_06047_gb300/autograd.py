@@ -3,8 +3,10 @@
 Vertex refinement is linear in the control positions (P_L = R P_0, Sec. 3.6 Eq. singleSpMV), so
 the gradient of any loss of P_L is g_0 = R^T g_L. Forward runs the fused eval kernels
 (alsub_refine_vertices); backward applies the transposed per-level operators
-g_l = R_l^T g_{l+1} (alsub_apply_operator_transpose on an ALSUB_OP_CHAIN operator), which depend
-on the topology only: no intermediate positions are kept for the backward pass.
+g_l = R_l^T g_{l+1} (alsub_apply_operator_transpose), which depend on the topology only: no
+intermediate positions are kept for the backward pass. A closed Catmull-Clark mesh applies them
+matrix-free, gathered per coarse vertex (ALSUB_OP_MATRIX_FREE); other meshes through their stored
+transposes (ALSUB_OP_TRANSPOSE).
 """
 from __future__ import annotations
 
@@ -32,7 +34,8 @@ class Subdivider:
     def __init__(self, mesh: dict, levels: int | None = None, scheme: str | None = None):
         self.mesh = alsub.Mesh.from_dict(mesh, scheme)
         self.topo = alsub.Topology(self.mesh, levels if levels is not None else mesh["levels"])
-        self.op = alsub.Operator(self.topo, chain=True, transpose=True)
+        gather = self.mesh.scheme == "cc" and self.mesh.boundary_edges == 0
+        self.op = alsub.Operator(self.topo, chain=False, matrix_free=True, transpose=not gather)
 
     def __call__(self, P0: torch.Tensor) -> torch.Tensor:
         return Refine.apply(P0, self.topo, self.op)

@@ -13,7 +13,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libalsub.so")
 SOURCES = ["scan.cu", "level0.cu", "cc.cu", "tri.cu", "crease.cu", "api.cu", "operator.cu", "batch.cu", "noalloc.cu",
-           "serve.cu", "extract.cu", "patch.cu", "reorder.cu", "sqrt3f.cu"]
+           "serve.cu", "extract.cu", "patch.cu", "reorder.cu", "sqrt3f.cu", "adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                      "-I", CSRC, "--expt-relaxed-constexpr"]

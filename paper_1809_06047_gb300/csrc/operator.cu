@@ -416,6 +416,12 @@ struct alsub_operator_s {
     // time on the host (mf_lock) and, through mf_done, in order on the device
     std::mutex mf_lock;
     cudaEvent_t mf_done = nullptr;
+    // matrix-free transpose (Catmull-Clark, closed meshes): per-vertex coefficients of every level
+    // below the last and two intermediate levels of gradients (float4 rows)
+    bool mf_t = false;
+    std::vector<AdjLevel> adj;
+    float *adj_buf = nullptr;
+    size_t adj_half = 0;           // floats per intermediate level
     float *buf = nullptr;          // two intermediate levels of packed xyz for chain applies
     size_t buf_floats = 0;
     int *cnt = nullptr;            // scratch counts
@@ -641,6 +647,25 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
             cudaGetLastError();
             return bail(report(ALSUB_ERR_DEVICE, "operator: event creation failed"));
         }
+        if (!want_t && adjoint_supported(T)) {
+            // the transpose as a gather per coarse vertex: the levels' edge ids and twins, and
+            // each level's per-vertex coefficients (topology only, computed here once)
+            if ((st = ensure_helpers(T, s))) return bail(st);
+            O->adj.assign(T.levels, AdjLevel());
+            long long vmid = 1;
+            for (int l = 0; l < T.levels; l++) {
+                AdjLevel &P = O->adj[l];
+                if ((st = oalloc(*O, (char **)&P.coef, sizeof(float4) * (size_t)T.L[l].V))) return bail(st);
+                if ((st = oalloc(*O, &P.corner, (size_t)T.L[l].V))) return bail(st);
+                if (l >= 1 && (st = oalloc(*O, (char **)&P.ring, sizeof(int4) * (size_t)T.L[l].V))) return bail(st);
+                if (adjoint_level_creased(T, l) && (st = oalloc(*O, &P.sh, (size_t)T.L[l].E))) return bail(st);
+                adjoint_prepare(T, l, P, s);
+                if (l >= 1) vmid = std::max(vmid, T.L[l].V);
+            }
+            O->adj_half = 4 * (size_t)vmid;
+            if ((st = oalloc(*O, &O->adj_buf, 2 * O->adj_half))) return bail(st);
+            O->mf_t = true;
+        }
     }
     std::vector<Csr> R(need_rows ? T.levels : 0);
     for (int l = 0; l < (int)R.size(); l++)
@@ -686,6 +711,16 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
     if (!need_rows && cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();
         return bail(report(ALSUB_ERR_DEVICE, "operator: build failed"));
+    }
+    if (O->mf_t) {
+        // the coefficient kernels check every ring (closed, valence) into the topology's status
+        int dst = 0;
+        if (cudaMemcpyAsync(&dst, T.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(report(ALSUB_ERR_DEVICE, "operator: build failed"));
+        }
+        if (dst) return bail(report((alsub_status)dst, "operator: the topology reports an error"));
     }
     *out = O;
     return ALSUB_OK;
@@ -735,8 +770,23 @@ alsub_status alsub_apply_operator(alsub_operator_t op, const float *P0, float *P
 
 alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL, float *g0, void *stream) {
     if (!op || !gL || !g0) return report(ALSUB_ERR_INVALID_ARG, "bad arguments");
-    if (!op->has_t) return report(ALSUB_ERR_INVALID_ARG, "operator built without ALSUB_OP_TRANSPOSE");
     cudaStream_t s = (cudaStream_t)stream;
+    if (!op->has_t && op->mf_t) {
+        // g_l = R_l^T g_{l+1} gathered per coarse vertex, level by level from the last
+        std::lock_guard<std::mutex> g(op->mf_lock);
+        cudaStreamWaitEvent(s, op->mf_done, 0);        // the previous apply's buffers are free
+        TopoImpl &T = *op->T;
+        const int L = T.levels;
+        for (int l = L - 1; l >= 0; l--) {
+            const float *G = l == L - 1 ? gL : op->adj_buf + op->adj_half * ((l + 1) & 1);
+            float *gl = l == 0 ? g0 : op->adj_buf + op->adj_half * (l & 1);
+            adjoint_step(T, l, G, l + 1 < L, gl, l > 0, op->adj[l], s);
+        }
+        cudaEventRecord(op->mf_done, s);
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? ALSUB_OK : report(ALSUB_ERR_DEVICE, cudaGetErrorString(e));
+    }
+    if (!op->has_t) return report(ALSUB_ERR_INVALID_ARG, "operator built without ALSUB_OP_TRANSPOSE");
     if (op->has_comp) {
         spmv(*op, op->CT, gL, g0, s);
     } else {

@@ -110,11 +110,14 @@ def test_apply_chain_composite_transpose(scheme, fn, levels):
 def test_matrix_free_apply_and_transpose(scheme, fn, levels):
     """ALSUB_OP_MATRIX_FREE: apply is the eval kernels' result bit for bit (and so within the
     tolerance of the oracle); with ALSUB_OP_TRANSPOSE the stored transposes give the chain's
-    adjoint bit for bit; no forward matrix is stored."""
+    adjoint bit for bit; no forward matrix is stored. Without ALSUB_OP_TRANSPOSE a closed
+    Catmull-Clark mesh applies R^T as a gather per coarse vertex: against the oracle's R_l^T chain
+    (scipy, FP64); the other schemes refuse."""
+    import scipy.sparse as sp
     import torch
     from paper_1809_06047_gb300 import alsub
     mesh = fn()
-    ref = oracle.subdivide(mesh, levels, scheme, keep_all=True)
+    ref = oracle.subdivide(mesh, levels, scheme, keep_all=True, operator=True)
     M, T, P0 = _setup(mesh, scheme, levels)
     pi = _maps(scheme, T, ref)
     ev = T.refine_vertices(P0).cpu().numpy()
@@ -133,9 +136,21 @@ def test_matrix_free_apply_and_transpose(scheme, fn, levels):
     assert e.value.status == 1
     only = alsub.Operator(T, chain=False, matrix_free=True)
     assert only.bytes() < mf.bytes()
-    with pytest.raises(alsub.AlsubError) as e:
-        only.apply_transpose(gL)
-    assert e.value.status == 1
+    if scheme != "cc":
+        with pytest.raises(alsub.AlsubError) as e:
+            only.apply_transpose(gL)
+        assert e.value.status == 1
+        return
+    Rs = [sp.csr_matrix((ref[l]["R_w"], (ref[l]["R_rows"], ref[l]["R_cols"])),
+                        shape=(ref[l + 1]["V"], ref[l]["V"])) for l in range(levels)]
+    gl = gL.double().cpu().numpy()[np.argsort(pi[levels])]      # into the oracle's numbering
+    for R in reversed(Rs):
+        gl = R.T @ gl
+    got = [only.apply_transpose(gL).cpu().numpy() for _ in range(2)]
+    T.status()
+    assert np.array_equal(got[0], got[1])                        # deterministic: no atomics
+    np.testing.assert_allclose(got[0], gl, atol=1e-5 * np.abs(gl).max())
+    np.testing.assert_allclose(got[0], chain.apply_transpose(gL).cpu().numpy(), atol=1e-5 * np.abs(gl).max())
 
 
 def test_matrix_free_applies_on_many_streams():
