@@ -17,8 +17,12 @@
 // (else 0) and g = (1 - w)(1 - 2/n + sum_j 1/(n^2 c_j)) + w (3/4 when k = 2, 1 when k >= 3). Each
 // edge at v is the edge y -> next of exactly one face around v, so nothing is counted twice; a
 // vertex or edge that two faces around v share (a valence-2 vertex) is counted once per face, as
-// its stencil counts it. The per-vertex (a, b, g) depend on the topology only: they are computed
-// once per level when the operator is built.
+// its stencil counts it. The per-vertex (a, b, g), each vertex's designated corner, the ring
+// corners of the valence-4 vertices and each creased edge's min(sigma, 1) depend on the topology
+// only: they are computed once per level when the operator is built.
+// Each level runs in two passes: per coarse face, the terms above that the face contributes at each
+// of its corners (one float4 per corner, the face's own rows read coalesced); then per coarse
+// vertex, its own term plus the contributions at its ring corners.
 #include "common.cuh"
 #include "internal.h"
 
@@ -104,113 +108,107 @@ __global__ void k_adj_sharp(int E, CreaseList cr, float *sh) {
     sh[e] = s < 1.0f ? s : 1.0f;
 }
 
-// The column sum of one coarse vertex (its designated corner x).
-template <bool L0, bool CREASED>
-__device__ __forceinline__ void adj_vertex(const AdjTopo<L0> &A, const AdjArgs &a, int x) {
-    const int v = __ldg(A.fv + x);
+// Levels >= 1 (quads), two passes. k_adj_face: per coarse face r, the whole contribution of r
+// to the vertex at each corner k (the terms of the column sum above that belong to face r at that
+// corner), written to part[4r + k]; its rows are its own (coalesced) and the 17 values it gathers
+// are independent of one another. k_adj_vert: per coarse vertex, its own vertex-point term plus
+// the parts at its ring corners.
+template <bool CREASED>
+__global__ void __launch_bounds__(kBlock) k_adj_face(const int *__restrict__ fv, const int *__restrict__ ce,
+                                                     AdjArgs a, float4 *__restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.F || failed(a.status)) return;
     const int VF = a.V + a.F;
-    float3 acc = __ldg(a.coef + v).z * ldpv(a.G, v, a.G4);
-    int y = x, n = 0;
-    do {
-        const int r = A.face(y), s0 = A.first(r), c = A.order(r), j = y - s0;
-        const float ic = 1.0f / (float)c;
-        acc += ic * ldpv(a.G, a.V + r, a.G4);                          // the face point
-        // the edge y -> next and the vertex at its end
-        const int t = __ldg(A.tw + y);
-        const float ict = L0 ? 1.0f / (float)A.order(A.face(t)) : 0.25f;
-        const int e0 = __ldg(A.ce + y);
+    const int4 vr = ld4(fv + 4 * (size_t)r), er = ld4(ce + 4 * (size_t)r);
+    const int vv[4] = {vr.x, vr.y, vr.z, vr.w}, ee[4] = {er.x, er.y, er.z, er.w};
+    float3 gv[4], ge[4];
+    float4 cf[4];
+    float sk[4];
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        gv[k] = ldpv(a.G, vv[k], a.G4);
+        ge[k] = ldpv(a.G, VF + ee[k], a.G4);
+        cf[k] = __ldg(a.coef + vv[k]);
+        sk[k] = edge_s<CREASED>(a, ee[k]);
+    }
+    const float3 gf = 0.25f * ldpv(a.G, a.V + r, a.G4);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int k1 = (k + 1) & 3, k2 = (k + 2) & 3;
+        float3 p = gf;
+        p += ((1.0f - sk[k]) * 0.375f + 0.5f * sk[k]) * ge[k];                    // ring edge v_k v_k+1
+        p += (1.5f * cf[k1].x + (sk[k] > 0.f ? cf[k1].y : 0.f)) * gv[k1];          // its end vertex
+        p += ((1.0f - sk[k1]) * 0.0625f) * ge[k1];                                  // the far edges
+        p += ((1.0f - sk[k2]) * 0.0625f) * ge[k2];
+        p += (0.25f * cf[k2].x) * gv[k2];                                           // the far vertex
+        part[4 * (size_t)r + k] = make_float4(p.x, p.y, p.z, 0.f);
+    }
+}
+
+// Level 0: the same first pass over polygons (order c, corners s .. s + c - 1; c' of the face
+// across each edge read through the twin).
+template <bool CREASED>
+__global__ void __launch_bounds__(kBlock) k_adj_face0(AdjTopo<true> A, AdjArgs a, float4 *__restrict__ part) {
+    pdl_wait();
+    pdl_trigger();
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= a.F || failed(a.status)) return;
+    const int VF = a.V + a.F;
+    const int s0 = A.first(r), c = A.order(r);
+    const float ic = 1.0f / (float)c;
+    const float3 gf = ic * ldpv(a.G, a.V + r, a.G4);
+    for (int k = 0; k < c; k++) {
+        const int x = s0 + k;
+        const int t = __ldg(A.tw + x);
+        const float ict = 1.0f / (float)A.order(A.face(t));
+        const int e0 = __ldg(A.ce + x);
         const float s0c = edge_s<CREASED>(a, e0);
-        acc += ((1.0f - s0c) * (0.25f + 0.25f * (ic + ict)) + 0.5f * s0c) * ldpv(a.G, VF + e0, a.G4);
-        const int yn = s0 + (j + 1 == c ? 0 : j + 1);
-        const int u = __ldg(A.fv + yn);
+        float3 p = gf;
+        p += ((1.0f - s0c) * (0.25f + 0.25f * (ic + ict)) + 0.5f * s0c) * ldpv(a.G, VF + e0, a.G4);
+        const int u = __ldg(A.fv + s0 + (k + 1 == c ? 0 : k + 1));
         const float4 cu = __ldg(a.coef + u);
-        acc += (cu.x * (1.0f + ic + ict) + (s0c > 0.f ? cu.y : 0.f)) * ldpv(a.G, u, a.G4);
-        // the far edges (from next to prev) and the far vertices (strictly between them)
+        p += (cu.x * (1.0f + ic + ict) + (s0c > 0.f ? cu.y : 0.f)) * ldpv(a.G, u, a.G4);
         for (int q = 1; q + 1 < c; q++) {
-            const int yq = s0 + (j + q) % c;
+            const int yq = s0 + (k + q) % c;
             const int eq = __ldg(A.ce + yq);
-            const float sqc = edge_s<CREASED>(a, eq);
-            acc += ((1.0f - sqc) * 0.25f * ic) * ldpv(a.G, VF + eq, a.G4);
+            p += ((1.0f - edge_s<CREASED>(a, eq)) * 0.25f * ic) * ldpv(a.G, VF + eq, a.G4);
             if (q >= 2) {
                 const int w = __ldg(A.fv + yq);
-                acc += (__ldg(a.coef + w).x * ic) * ldpv(a.G, w, a.G4);
+                p += (__ldg(a.coef + w).x * ic) * ldpv(a.G, w, a.G4);
             }
         }
-        y = A.ring(y);
-        n++;
-    } while (y >= 0 && y != x && n < kMaxValence);
-    stpv(a.g, v, acc, a.g4);
-}
-
-// Levels >= 1 (quads): the ring is taken four faces per round, first the chain of twins (the only
-// dependent loads), then the rows of the four faces, then every gradient and coefficient they
-// name, so a valence-4 vertex waits for six round trips instead of three per face.
-template <bool CREASED>
-__device__ __forceinline__ void adj_vertex_quads(const AdjTopo<false> &A, const AdjArgs &a, int v) {
-    const int VF = a.V + a.F;
-    const int4 rc = __ldg(a.ring + v);               // a valence-4 vertex: its four ring corners
-    const int x = rc.x >= 0 ? rc.x : __ldg(a.corner + v);
-    float3 acc = __ldg(a.coef + v).z * ldpv(a.G, v, a.G4);
-    int y = x, n = 0;
-    bool done = false, first = true;
-    while (!done && n < kMaxValence) {
-        int ys[4];
-        bool use[4];
-        if (first && rc.x >= 0) {
-            ys[0] = rc.x; ys[1] = rc.y; ys[2] = rc.z; ys[3] = rc.w;
-            use[0] = use[1] = use[2] = use[3] = true;
-            y = x;
-            n = 4;
-            done = true;
-        } else {
-#pragma unroll
-            for (int q = 0; q < 4; q++) {
-                use[q] = !done;
-                ys[q] = y;
-                if (!done) {
-                    y = A.ring(y);
-                    n++;
-                    done = y == x || y < 0 || n >= kMaxValence;
-                }
-            }
-        }
-        first = false;
-        int4 fr[4], er[4];
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int r = use[q] ? ys[q] >> 2 : 0;
-            fr[q] = use[q] ? ld4(A.fv + 4 * (size_t)r) : make_int4(0, 0, 0, 0);
-            er[q] = use[q] ? ld4(A.ce + 4 * (size_t)r) : make_int4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            if (!use[q]) continue;
-            const int r = ys[q] >> 2, j = ys[q] & 3, j1 = (j + 1) & 3, j2 = (j + 2) & 3;
-            const int u = comp(fr[q], j1), w = comp(fr[q], j2);
-            const int e0 = comp(er[q], j), e1 = comp(er[q], j1), e2 = comp(er[q], j2);
-            const float s0c = edge_s<CREASED>(a, e0), s1c = edge_s<CREASED>(a, e1), s2c = edge_s<CREASED>(a, e2);
-            const float4 cu = __ldg(a.coef + u), cw = __ldg(a.coef + w);
-            acc += 0.25f * ldpv(a.G, a.V + r, a.G4);
-            acc += ((1.0f - s0c) * 0.375f + 0.5f * s0c) * ldpv(a.G, VF + e0, a.G4);
-            acc += (1.5f * cu.x + (s0c > 0.f ? cu.y : 0.f)) * ldpv(a.G, u, a.G4);
-            acc += ((1.0f - s1c) * 0.0625f) * ldpv(a.G, VF + e1, a.G4);
-            acc += ((1.0f - s2c) * 0.0625f) * ldpv(a.G, VF + e2, a.G4);
-            acc += (0.25f * cw.x) * ldpv(a.G, w, a.G4);
-        }
+        part[x] = make_float4(p.x, p.y, p.z, 0.f);
     }
-    if (y != x) set_status(a.status, ALSUB_ERR_UNSUPPORTED);
-    stpv(a.g, v, acc, a.g4);
 }
 
-// One thread per coarse vertex, from the designated corner the build recorded.
-template <bool L0, bool CREASED>
-__global__ void __launch_bounds__(kBlock) k_adj_gather(AdjTopo<L0> A, AdjArgs a) {
+template <bool L0>
+__global__ void __launch_bounds__(kBlock) k_adj_vert(AdjTopo<L0> A, AdjArgs a, const float4 *__restrict__ part) {
     pdl_wait();
     pdl_trigger();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= a.V || failed(a.status)) return;
-    if constexpr (L0) adj_vertex<true, CREASED>(A, a, __ldg(a.corner + v));
-    else adj_vertex_quads<CREASED>(A, a, v);
+    const int4 rc = L0 ? make_int4(-1, -1, -1, -1) : __ldg(a.ring + v);   // valence 4: its ring corners
+    float3 acc = __ldg(a.coef + v).z * ldpv(a.G, v, a.G4);
+    if (rc.x >= 0) {
+        const float4 p0 = __ldg(part + rc.x), p1 = __ldg(part + rc.y), p2 = __ldg(part + rc.z), p3 = __ldg(part + rc.w);
+        acc += f3(p0.x, p0.y, p0.z);
+        acc += f3(p1.x, p1.y, p1.z);
+        acc += f3(p2.x, p2.y, p2.z);
+        acc += f3(p3.x, p3.y, p3.z);
+    } else {
+        const int x = __ldg(a.corner + v);
+        int y = x, n = 0;
+        do {
+            const float4 p = __ldg(part + y);
+            acc += f3(p.x, p.y, p.z);
+            y = A.ring(y);
+            n++;
+        } while (y >= 0 && y != x && n < kMaxValence);
+        if (y != x) set_status(a.status, ALSUB_ERR_UNSUPPORTED);
+    }
+    stpv(a.g, v, acc, a.g4);
 }
 
 template <bool L0>
@@ -256,7 +254,7 @@ void adjoint_prepare(TopoImpl &T, int l, const AdjLevel &P, cudaStream_t s) {
 }
 
 void adjoint_step(TopoImpl &T, int l, const float *G, bool G4, float *g, bool g4, const AdjLevel &P,
-                  cudaStream_t s) {
+                  float4 *part, cudaStream_t s) {
     AdjArgs a;
     a.nnz = (int)T.L[l].nnz;
     a.V = (int)T.L[l].V;
@@ -269,15 +267,17 @@ void adjoint_step(TopoImpl &T, int l, const float *G, bool G4, float *g, bool g4
     a.sh = P.sh;
     a.status = T.status;
     const bool cr = level_creased(T, l);
-    const unsigned grid = grid_for(a.V);
     if (l == 0) {
-        if (cr) launch_pdl(k_adj_gather<true, true>, grid, kBlock, s, adj_topo<true>(T, l), a);
-        else launch_pdl(k_adj_gather<true, false>, grid, kBlock, s, adj_topo<true>(T, l), a);
+        if (cr) launch_pdl(k_adj_face0<true>, grid_for(a.F), kBlock, s, adj_topo<true>(T, l), a, part);
+        else launch_pdl(k_adj_face0<false>, grid_for(a.F), kBlock, s, adj_topo<true>(T, l), a, part);
+        launch_pdl(k_adj_vert<true>, grid_for(a.V), kBlock, s, adj_topo<true>(T, l), a, (const float4 *)part);
     } else {
-        if (cr) launch_pdl(k_adj_gather<false, true>, grid, kBlock, s, adj_topo<false>(T, l), a);
-        else launch_pdl(k_adj_gather<false, false>, grid, kBlock, s, adj_topo<false>(T, l), a);
+        const LevelBuf &B = T.L[l];
+        if (cr) launch_pdl(k_adj_face<true>, grid_for(a.F), kBlock, s, (const int *)B.fv, (const int *)B.ce, a, part);
+        else launch_pdl(k_adj_face<false>, grid_for(a.F), kBlock, s, (const int *)B.fv, (const int *)B.ce, a, part);
+        launch_pdl(k_adj_vert<false>, grid_for(a.V), kBlock, s, adj_topo<false>(T, l), a, (const float4 *)part);
     }
-    T.launches += 1;
+    T.launches += 2;
 }
 
 }  // namespace alsub

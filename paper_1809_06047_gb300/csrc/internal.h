@@ -302,8 +302,9 @@ alsub_status refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratc
 // Matrix-free adjoint of the Catmull-Clark steps of a closed mesh (g_l = R_l^T g_{l+1} gathered per
 // coarse vertex). Per level, computed once from the topology (which must store the level's edge
 // ids and twins): each vertex's coefficients (float4), designated corner and (levels >= 1) ring
-// corners, and on a level with creases each edge's min(sigma, 1). adjoint_step gathers one level (G: level l + 1, g: level l;
-// float4 rows or packed xyz).
+// corners, and on a level with creases each edge's min(sigma, 1). adjoint_step gathers one level
+// (G: level l + 1, g: level l; float4 rows or packed xyz; part: scratch of one float4 per corner of
+// level l).
 struct AdjLevel {
     float4 *coef = nullptr;   // V_l
     int *corner = nullptr;    // V_l
@@ -314,7 +315,7 @@ bool adjoint_supported(const TopoImpl &T);
 bool adjoint_level_creased(const TopoImpl &T, int l);
 void adjoint_prepare(TopoImpl &T, int l, const AdjLevel &P, cudaStream_t s);
 void adjoint_step(TopoImpl &T, int l, const float *G, bool G4, float *g, bool g4, const AdjLevel &P,
-                  cudaStream_t s);
+                  float4 *part, cudaStream_t s);
 // alsub_mesh_create_ex behind the C ABI. B_stated null: the boundary edges are counted on the
 // device and read back (the call synchronises `stream`); else the caller states their number and
 // the count is checked on the device (mesh_boundary_check), so nothing waits for the device.

@@ -422,6 +422,7 @@ struct alsub_operator_s {
     std::vector<AdjLevel> adj;
     float *adj_buf = nullptr;
     size_t adj_half = 0;           // floats per intermediate level
+    float4 *adj_part = nullptr;    // one per corner of the largest level below the last (any level)
     float *buf = nullptr;          // two intermediate levels of packed xyz for chain applies
     size_t buf_floats = 0;
     int *cnt = nullptr;            // scratch counts
@@ -664,6 +665,9 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
             }
             O->adj_half = 4 * (size_t)vmid;
             if ((st = oalloc(*O, &O->adj_buf, 2 * O->adj_half))) return bail(st);
+            long long nmax = 1;
+            for (int l = 0; l < T.levels; l++) nmax = std::max(nmax, T.L[l].nnz);
+            if ((st = oalloc(*O, (char **)&O->adj_part, sizeof(float4) * (size_t)nmax))) return bail(st);
             O->mf_t = true;
         }
     }
@@ -780,7 +784,7 @@ alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL
         for (int l = L - 1; l >= 0; l--) {
             const float *G = l == L - 1 ? gL : op->adj_buf + op->adj_half * ((l + 1) & 1);
             float *gl = l == 0 ? g0 : op->adj_buf + op->adj_half * (l & 1);
-            adjoint_step(T, l, G, l + 1 < L, gl, l > 0, op->adj[l], s);
+            adjoint_step(T, l, G, l + 1 < L, gl, l > 0, op->adj[l], op->adj_part, s);
         }
         cudaEventRecord(op->mf_done, s);
         cudaError_t e = cudaGetLastError();
