@@ -393,8 +393,10 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
  *          per refined vertex. Its transpose, on a closed Catmull-Clark mesh, is matrix-free too:
  *          g_l = R_l^T g_{l+1} gathered per coarse vertex (its face points, the edge points around
  *          and across its faces, its own and its neighbours' vertex points, with the crease rules),
- *          no atomics, from per-vertex coefficients computed once here (16 bytes per vertex of
- *          every level below the last; the levels' edge ids and twins are stored). With
+ *          no atomics, in two passes per level (per coarse face its contribution at each corner,
+ *          then per coarse vertex the sum of its contributions), from per-vertex coefficients and
+ *          per-corner slots computed once here (about 40 bytes per vertex of every level below the
+ *          last, and the levels' edge ids and twins, which are then stored). With
  *          ALSUB_OP_TRANSPOSE (and no other flag) the transposes of the R_l are stored and applied
  *          instead (any scheme). When combined with CHAIN or COMPOSE, apply takes the matrix-free
  *          form and alsub_operator_info the stored matrices.

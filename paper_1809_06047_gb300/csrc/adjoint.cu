@@ -17,12 +17,13 @@
 // (else 0) and g = (1 - w)(1 - 2/n + sum_j 1/(n^2 c_j)) + w (3/4 when k = 2, 1 when k >= 3). Each
 // edge at v is the edge y -> next of exactly one face around v, so nothing is counted twice; a
 // vertex or edge that two faces around v share (a valence-2 vertex) is counted once per face, as
-// its stencil counts it. The per-vertex (a, b, g), each vertex's designated corner, the ring
-// corners of the valence-4 vertices and each creased edge's min(sigma, 1) depend on the topology
-// only: they are computed once per level when the operator is built.
+// its stencil counts it. The per-vertex (a, b, g), each vertex's designated corner, the slot each
+// corner's contribution goes to and each creased edge's min(sigma, 1) depend on the topology only:
+// they are computed once per level when the operator is built.
 // Each level runs in two passes: per coarse face, the terms above that the face contributes at each
-// of its corners (one float4 per corner, the face's own rows read coalesced); then per coarse
-// vertex, its own term plus the contributions at its ring corners.
+// of its corners (one float4 per corner, the face's own rows read coalesced; on levels >= 1 a
+// valence-4 vertex's four contributions land side by side); then per coarse vertex, its own term
+// plus its contributions.
 #include "common.cuh"
 #include "internal.h"
 
@@ -53,7 +54,8 @@ struct AdjArgs {
     bool G4, g4;              // float4 rows (intermediate levels) or packed xyz
     const float4 *coef;       // (a, b, g, 0) per coarse vertex
     const int *corner;        // each coarse vertex's designated corner
-    const int4 *ring;         // levels >= 1: a valence-4 vertex's ring corners (x = -1: another valence)
+    const int *pidx;          // levels >= 1: where corner x's contribution goes (4 v + i for the i-th
+                              // ring corner of a valence-4 vertex v, else 4 V + x)
     const float *sh;          // min(sigma, 1) per coarse edge (when CREASED)
     int *status;
 };
@@ -71,8 +73,8 @@ __device__ __forceinline__ float edge_s(const AdjArgs &a, int e) {
 // Per-vertex coefficients (a, b, g) of one level and each vertex's designated corner, from one
 // ring walk per designated corner.
 template <bool L0, bool CREASED>
-__global__ void __launch_bounds__(kBlock) k_adj_coef(AdjTopo<L0> A, int nnz, CreaseList cr, float4 *coef,
-                                                     int *corner, int4 *ring, int *status) {
+__global__ void __launch_bounds__(kBlock) k_adj_coef(AdjTopo<L0> A, int nnz, int V, CreaseList cr, float4 *coef,
+                                                     int *corner, int *pidx, int *status) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= nnz || failed(status) || !A.designated(x)) return;
     const int v = __ldg(A.fv + x);
@@ -89,7 +91,15 @@ __global__ void __launch_bounds__(kBlock) k_adj_coef(AdjTopo<L0> A, int nnz, Cre
         n++;
     } while (y >= 0 && y != x && n < kMaxValence);
     if (y != x) { set_status(status, ALSUB_ERR_UNSUPPORTED); return; }   // open or too long
-    if (ring) ring[v] = n == 4 ? make_int4(rc[0], rc[1], rc[2], rc[3]) : make_int4(-1, -1, -1, -1);
+    if (pidx) {
+        // the contributions of a valence-4 vertex's ring faces go to four adjacent slots
+        if (n == 4) {
+            for (int i = 0; i < 4; i++) pidx[rc[i]] = 4 * v + i;
+        } else {
+            int z = x, m = 0;
+            do { pidx[z] = 4 * V + z; z = A.ring(z); m++; } while (z >= 0 && z != x && m < kMaxValence);
+        }
+    }
     const float inv = 1.0f / (float)n;
     float w = 0.f;
     if (k >= 2) { w = S / (float)k; w = w < 1.0f ? w : 1.0f; }
@@ -97,7 +107,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_coef(AdjTopo<L0> A, int nnz, Cre
     const float b = k == 2 ? 0.125f * w : 0.f;
     const float q = k == 2 ? 0.75f : (k >= 3 ? 1.0f : 0.f);
     const float gm = (1.0f - w) * (1.0f - 2.0f * inv + inv * inv * invc) + w * q;
-    coef[v] = make_float4(a, b, gm, 0.f);
+    coef[v] = make_float4(a, b, gm, (float)n);
 }
 
 // min(sigma, 1) of every edge of a creased level (the hash table's lookups, done once).
@@ -110,9 +120,9 @@ __global__ void k_adj_sharp(int E, CreaseList cr, float *sh) {
 
 // Levels >= 1 (quads), two passes. k_adj_face: per coarse face r, the whole contribution of r
 // to the vertex at each corner k (the terms of the column sum above that belong to face r at that
-// corner), written to part[4r + k]; its rows are its own (coalesced) and the 17 values it gathers
-// are independent of one another. k_adj_vert: per coarse vertex, its own vertex-point term plus
-// the parts at its ring corners.
+// corner), written to part[pidx[4r + k]]; its rows are its own (coalesced) and the 17 values it
+// gathers are independent of one another. k_adj_vert: per coarse vertex, its own vertex-point term
+// plus its contributions (a valence-4 vertex reads them as 64 contiguous bytes).
 template <bool CREASED>
 __global__ void __launch_bounds__(kBlock) k_adj_face(const int *__restrict__ fv, const int *__restrict__ ce,
                                                      AdjArgs a, float4 *__restrict__ part) {
@@ -121,7 +131,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_face(const int *__restrict__ fv,
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= a.F || failed(a.status)) return;
     const int VF = a.V + a.F;
-    const int4 vr = ld4(fv + 4 * (size_t)r), er = ld4(ce + 4 * (size_t)r);
+    const int4 vr = ld4(fv + 4 * (size_t)r), er = ld4(ce + 4 * (size_t)r), pr = ld4(a.pidx + 4 * (size_t)r);
     const int vv[4] = {vr.x, vr.y, vr.z, vr.w}, ee[4] = {er.x, er.y, er.z, er.w};
     float3 gv[4], ge[4];
     float4 cf[4];
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(kBlock) k_adj_face(const int *__restrict__ fv,
         p += ((1.0f - sk[k1]) * 0.0625f) * ge[k1];                                  // the far edges
         p += ((1.0f - sk[k2]) * 0.0625f) * ge[k2];
         p += (0.25f * cf[k2].x) * gv[k2];                                           // the far vertex
-        part[4 * (size_t)r + k] = make_float4(p.x, p.y, p.z, 0.f);
+        part[comp(pr, k)] = make_float4(p.x, p.y, p.z, 0.f);
     }
 }
 
@@ -189,19 +199,22 @@ __global__ void __launch_bounds__(kBlock) k_adj_vert(AdjTopo<L0> A, AdjArgs a, c
     pdl_trigger();
     const int v = blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= a.V || failed(a.status)) return;
-    const int4 rc = L0 ? make_int4(-1, -1, -1, -1) : __ldg(a.ring + v);   // valence 4: its ring corners
-    float3 acc = __ldg(a.coef + v).z * ldpv(a.G, v, a.G4);
-    if (rc.x >= 0) {
-        const float4 p0 = __ldg(part + rc.x), p1 = __ldg(part + rc.y), p2 = __ldg(part + rc.z), p3 = __ldg(part + rc.w);
+    const float4 cv = __ldg(a.coef + v);
+    float3 acc = cv.z * ldpv(a.G, v, a.G4);
+    if (!L0 && cv.w == 4.0f) {
+        // a valence-4 vertex: its four contributions side by side
+        const float4 *q = part + 4 * (size_t)v;
+        const float4 p0 = __ldg(q), p1 = __ldg(q + 1), p2 = __ldg(q + 2), p3 = __ldg(q + 3);
         acc += f3(p0.x, p0.y, p0.z);
         acc += f3(p1.x, p1.y, p1.z);
         acc += f3(p2.x, p2.y, p2.z);
         acc += f3(p3.x, p3.y, p3.z);
     } else {
         const int x = __ldg(a.corner + v);
+        const size_t off = L0 ? 0 : 4 * (size_t)a.V;    // levels >= 1: after the valence-4 slots
         int y = x, n = 0;
         do {
-            const float4 p = __ldg(part + y);
+            const float4 p = __ldg(part + off + y);
             acc += f3(p.x, p.y, p.z);
             y = A.ring(y);
             n++;
@@ -234,20 +247,20 @@ bool adjoint_supported(const TopoImpl &T) {
 bool adjoint_level_creased(const TopoImpl &T, int l) { return level_creased(T, l); }
 
 void adjoint_prepare(TopoImpl &T, int l, const AdjLevel &P, cudaStream_t s) {
-    const int nnz = (int)T.L[l].nnz;
+    const int nnz = (int)T.L[l].nnz, V = (int)T.L[l].V;
     const unsigned g = grid_for(nnz);
     const CreaseList &C = T.L[l].cr;
     const bool cr = level_creased(T, l);
     // every vertex of a closed manifold level has exactly one designated corner; the zero fill
     // keeps every entry a valid corner regardless
     cudaMemsetAsync(P.corner, 0, sizeof(int) * (size_t)T.L[l].V, s);
-    if (P.ring) cudaMemsetAsync(P.ring, 0xff, sizeof(int4) * (size_t)T.L[l].V, s);   // -1: walk
+    if (P.pidx) cudaMemsetAsync(P.pidx, 0, sizeof(int) * (size_t)nnz, s);   // every slot in bounds
     if (l == 0) {
-        if (cr) k_adj_coef<true, true><<<g, kBlock, 0, s>>>(adj_topo<true>(T, l), nnz, C, P.coef, P.corner, P.ring, T.status);
-        else k_adj_coef<true, false><<<g, kBlock, 0, s>>>(adj_topo<true>(T, l), nnz, C, P.coef, P.corner, P.ring, T.status);
+        if (cr) k_adj_coef<true, true><<<g, kBlock, 0, s>>>(adj_topo<true>(T, l), nnz, V, C, P.coef, P.corner, P.pidx, T.status);
+        else k_adj_coef<true, false><<<g, kBlock, 0, s>>>(adj_topo<true>(T, l), nnz, V, C, P.coef, P.corner, P.pidx, T.status);
     } else {
-        if (cr) k_adj_coef<false, true><<<g, kBlock, 0, s>>>(adj_topo<false>(T, l), nnz, C, P.coef, P.corner, P.ring, T.status);
-        else k_adj_coef<false, false><<<g, kBlock, 0, s>>>(adj_topo<false>(T, l), nnz, C, P.coef, P.corner, P.ring, T.status);
+        if (cr) k_adj_coef<false, true><<<g, kBlock, 0, s>>>(adj_topo<false>(T, l), nnz, V, C, P.coef, P.corner, P.pidx, T.status);
+        else k_adj_coef<false, false><<<g, kBlock, 0, s>>>(adj_topo<false>(T, l), nnz, V, C, P.coef, P.corner, P.pidx, T.status);
     }
     if (cr) k_adj_sharp<<<grid_for(T.L[l].E), kBlock, 0, s>>>((int)T.L[l].E, C, P.sh);
     T.launches += cr ? 2 : 1;
@@ -263,7 +276,7 @@ void adjoint_step(TopoImpl &T, int l, const float *G, bool G4, float *g, bool g4
     a.g = g; a.g4 = g4;
     a.coef = P.coef;
     a.corner = P.corner;
-    a.ring = P.ring;
+    a.pidx = P.pidx;
     a.sh = P.sh;
     a.status = T.status;
     const bool cr = level_creased(T, l);

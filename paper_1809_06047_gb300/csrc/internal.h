@@ -301,14 +301,14 @@ alsub_status refine_call(TopoImpl &T, const float *P0, float *PL, void *scratch,
 alsub_status refine_direct(TopoImpl &T, const float *P0, float *PL, void *scratch, cudaStream_t s);
 // Matrix-free adjoint of the Catmull-Clark steps of a closed mesh (g_l = R_l^T g_{l+1} gathered per
 // coarse vertex). Per level, computed once from the topology (which must store the level's edge
-// ids and twins): each vertex's coefficients (float4), designated corner and (levels >= 1) ring
-// corners, and on a level with creases each edge's min(sigma, 1). adjoint_step gathers one level
-// (G: level l + 1, g: level l; float4 rows or packed xyz; part: scratch of one float4 per corner of
-// level l).
+// ids and twins): each vertex's coefficients (float4), designated corner and (levels >= 1) the
+// slot of each corner's contribution, and on a level with creases each edge's min(sigma, 1). adjoint_step gathers one level
+// (G: level l + 1, g: level l; float4 rows or packed xyz; part: scratch of 4 V_l + nnz_l float4
+// on levels >= 1, nnz_0 on level 0).
 struct AdjLevel {
     float4 *coef = nullptr;   // V_l
     int *corner = nullptr;    // V_l
-    int4 *ring = nullptr;     // V_l, levels >= 1: a valence-4 vertex's ring corners (else -1)
+    int *pidx = nullptr;      // nnz_l, levels >= 1: the slot of each corner's contribution
     float *sh = nullptr;      // E_l, when adjoint_level_creased
 };
 bool adjoint_supported(const TopoImpl &T);

@@ -658,7 +658,7 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
                 AdjLevel &P = O->adj[l];
                 if ((st = oalloc(*O, (char **)&P.coef, sizeof(float4) * (size_t)T.L[l].V))) return bail(st);
                 if ((st = oalloc(*O, &P.corner, (size_t)T.L[l].V))) return bail(st);
-                if (l >= 1 && (st = oalloc(*O, (char **)&P.ring, sizeof(int4) * (size_t)T.L[l].V))) return bail(st);
+                if (l >= 1 && (st = oalloc(*O, &P.pidx, (size_t)T.L[l].nnz))) return bail(st);
                 if (adjoint_level_creased(T, l) && (st = oalloc(*O, &P.sh, (size_t)T.L[l].E))) return bail(st);
                 adjoint_prepare(T, l, P, s);
                 if (l >= 1) vmid = std::max(vmid, T.L[l].V);
@@ -666,7 +666,8 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
             O->adj_half = 4 * (size_t)vmid;
             if ((st = oalloc(*O, &O->adj_buf, 2 * O->adj_half))) return bail(st);
             long long nmax = 1;
-            for (int l = 0; l < T.levels; l++) nmax = std::max(nmax, T.L[l].nnz);
+            for (int l = 0; l < T.levels; l++)
+                nmax = std::max(nmax, l == 0 ? T.L[0].nnz : 4 * T.L[l].V + T.L[l].nnz);
             if ((st = oalloc(*O, (char **)&O->adj_part, sizeof(float4) * (size_t)nmax))) return bail(st);
             O->mf_t = true;
         }
