@@ -372,7 +372,7 @@ def adjoint_leg(peak):
             "forward_backward_ms": ms_step, "backward_ms": ms_bwd, "backward_bytes_held": S.op.bytes(),
             "stored_transposes": {"backward_ms": ms_stored, "bytes_held": stored_bytes},
             "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                         "kernel": "k_adj_gather (R_l^T gathered per coarse vertex, 4 levels)",
+                         "kernel": "k_adj_face + k_adj_vert (R_l^T gathered per coarse vertex, 4 levels)",
                          "algorithmic_bytes": b}}
 
 
