@@ -727,6 +727,7 @@ alsub_status alsub::create_mesh(alsub_scheme scheme, int32_t V, int32_t F, const
     M.stream = (cudaStream_t)stream;
     cudaStream_t s = M.stream;
     upload_weight_tables();
+    s3f_upload_tables();
     auto cleanup = [&]() {
         if (M.d_block) dev_free(M.alloc, M.d_block, s);
         delete h;

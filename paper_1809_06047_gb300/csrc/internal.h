@@ -246,6 +246,8 @@ void sqrt3_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, flo
 // (topology and/or positions). s3f_export: nothing to do (the steps keep every level's crease list
 // current; returns the launches).
 void s3f_level0(TopoImpl &T, cudaStream_t s);
+// The sqrt(3) feature path's weight table into constant memory (once; before any capture).
+void s3f_upload_tables();
 void s3f_step(TopoImpl &T, int l, bool topo, const float *P, float *Pn, cudaStream_t s);
 int s3f_export(TopoImpl &T, int l, cudaStream_t s);
 

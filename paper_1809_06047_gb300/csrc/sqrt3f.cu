@@ -25,10 +25,29 @@
 // corners, the level's crease list, face points and feature-edge points).
 #include <math.h>
 
+#include <mutex>
+
 #include "common.cuh"
 #include "internal.h"
 
 namespace alsub {
+
+namespace {
+
+// alpha_n of Eq. alpha, (4 - 2 cos(2 pi / n)) / 9, computed on the host in double once
+__constant__ float c_s3f_alpha[kMaxValence + 1];
+
+}  // namespace
+
+void s3f_upload_tables() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        static float al[kMaxValence + 1];
+        al[0] = 0.f;
+        for (int n = 1; n <= kMaxValence; n++) al[n] = (float)((4.0 - 2.0 * cos(2.0 * M_PI / n)) / 9.0);
+        cudaMemcpyToSymbol(c_s3f_alpha, al, sizeof(al));
+    });
+}
 
 namespace {
 
@@ -74,17 +93,39 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a) {
             k++;
         }
     };
+    // the ring four corners per round: the chain of twins first (the only dependent loads), then
+    // the round's neighbours and feature bits, then their positions
     int y = x;
-    bool open = false;
-    do {
-        neighbour(__ldg(a.fv + t_next(y)), feat(a.fm, y));
-        const int t = __ldg(a.tw + t_prev(y));
-        if (t < 0) {
-            open = true;
-            break;
+    bool open = false, done = false;
+    while (!done && n < kMaxValence) {
+        int ys[4];
+        bool use[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            use[q] = !done;
+            ys[q] = y;
+            if (!done) {
+                const int t = __ldg(a.tw + t_prev(y));
+                if (t < 0) {
+                    open = true;             // y stays the corner whose previous edge is open
+                    done = true;
+                } else {
+                    y = t;
+                    done = y == x || n + q + 1 >= kMaxValence;
+                }
+            }
         }
-        y = t;
-    } while (y != x && n < kMaxValence);
+        int w[4];
+        bool f[4];
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            w[q] = use[q] ? __ldg(a.fv + t_next(ys[q])) : 0;
+            f[q] = use[q] && feat(a.fm, ys[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++)
+            if (use[q]) neighbour(w[q], f[q]);
+    }
     if (open) {
         // the fan ends at an incoming boundary edge u -> v; then the corners before x
         neighbour(__ldg(a.fv + t_prev(y)), true);
@@ -109,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a) {
     } else if (k == 2) {
         q = (4.0f / 27.0f) * (ldpv(a.P, n1, a.in4) + ldpv(a.P, n2, a.in4)) + (19.0f / 27.0f) * p;
     } else {
-        const float al = (float)((4.0 - 2.0 * cos(2.0 * M_PI / (double)n)) / 9.0);
+        const float al = c_s3f_alpha[n];
         q = (1.0f - al) * p + (al / (float)n) * sum;
     }
     stpv(a.Pn, v, q, a.out4);
