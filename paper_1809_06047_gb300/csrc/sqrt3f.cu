@@ -191,10 +191,42 @@ __device__ __forceinline__ void push_crease(const S3Args &a, int u, int w) {
     a.csig[i] = INFINITY;
 }
 
+// 9 ints per triangle of the warp's 32 consecutive triangles (first r0, a multiple of 32): staged in
+// shared memory and written as 16-byte stores (the warp's first int is 1152-byte aligned), clipped
+// at n ints.
+__device__ __forceinline__ void warp_rows9(int *dst, int r0, long long n, const int (&v)[9], int *sm) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int i = 0; i < 9; i++) sm[9 * lane + i] = v[i];
+    __syncwarp();
+    const long long g0 = 9LL * r0;
+    int4 *o4 = reinterpret_cast<int4 *>(dst + g0);
+    const int4 *s4 = reinterpret_cast<const int4 *>(sm);
+#pragma unroll
+    for (int k = 0; k < 3; k++) {
+        const int q = 32 * k + lane;
+        if (q < 72) {
+            const long long e = g0 + 4 * q;
+            if (e + 4 <= n) {
+                o4[q] = s4[q];
+            } else {
+                for (int t = 0; t < 4; t++)
+                    if (e + t < n) dst[e + t] = sm[4 * q + t];
+            }
+        }
+    }
+    __syncwarp();
+}
+
 template <bool TOPO, bool EVAL>
 __global__ void __launch_bounds__(kBlock) k_s3f_tri(S3Args a) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= a.F || failed(a.status)) return;
+    // with TOPO every lane of the warp takes part in the staged row stores (a lane past the last
+    // triangle works on triangle 0 and its ints fall past the end); a failed status stops all
+    const int r_in = blockIdx.x * blockDim.x + threadIdx.x;
+    if (failed(a.status)) return;
+    const bool live = r_in < a.F;
+    if (!TOPO && !live) return;
+    const int r = live ? r_in : 0;
     const int c = 3 * r, V = a.V;
     const int mask = __ldg(a.fm + r);
     int vv[3], tt[3];
@@ -205,6 +237,7 @@ __global__ void __launch_bounds__(kBlock) k_s3f_tri(S3Args a) {
     }
     const bool helpers = TOPO && a.twn;        // the child level is not the last one
     const int jf = a.odd ? -1 : (mask & 1 ? 0 : (mask & 2 ? 1 : (mask & 4 ? 2 : -1)));
+    int fo[9], wo[9];
     if (jf < 0) {
         // a face point: every corner's child, its edge flipped unless a feature or (second
         // step) the triangle across has no face point
@@ -216,63 +249,74 @@ __global__ void __launch_bounds__(kBlock) k_s3f_tri(S3Args a) {
             for (int j = 0; j < 3; j++) {
                 const int jn = j == 2 ? 0 : j + 1, jp = j == 0 ? 2 : j - 1, t = tt[j];
                 const bool fj = (mask >> j) & 1;
-                int *o = a.fvn + 3 * (size_t)(c + j);
-                o[0] = vv[j];
-                o[1] = flip[j] ? V + t / 3 : vv[jn];
-                o[2] = V + r;
-                if (fj && t >= 0 && c + j < t) push_crease(a, vv[j], vv[jn]);   // a kept crease edge
+                fo[3 * j + 0] = vv[j];
+                fo[3 * j + 1] = flip[j] ? V + t / 3 : vv[jn];
+                fo[3 * j + 2] = V + r;
+                if (live && fj && t >= 0 && c + j < t) push_crease(a, vv[j], vv[jn]);   // a kept crease edge
                 if (!helpers) continue;
-                int *w = a.twn + 3 * (size_t)(c + j);
-                w[0] = flip[j] ? 3 * t_next(t) + 2 : (t < 0 ? t : carry(a, t));
-                w[1] = flip[j] ? 3 * t + 1 : 3 * (c + jn) + 2;
-                w[2] = flip[jp] ? 3 * tt[jp] : 3 * (c + jp) + 1;
-                a.fmn[c + j] = fj ? 1 : 0;
-                if (__ldg(a.vc + vv[j]) == c + j) a.vcn[vv[j]] = 3 * (c + j);
+                wo[3 * j + 0] = flip[j] ? 3 * t_next(t) + 2 : (t < 0 ? t : carry(a, t));
+                wo[3 * j + 1] = flip[j] ? 3 * t + 1 : 3 * (c + jn) + 2;
+                wo[3 * j + 2] = flip[jp] ? 3 * tt[jp] : 3 * (c + jp) + 1;
+                if (live) {
+                    a.fmn[c + j] = fj ? 1 : 0;
+                    if (__ldg(a.vc + vv[j]) == c + j) a.vcn[vv[j]] = 3 * (c + j);
+                }
             }
-            if (helpers) a.vcn[V + r] = 3 * c + 2;               // the face point: child 0, corner 2
+            if (live && helpers) a.vcn[V + r] = 3 * c + 2;       // the face point: child 0, corner 2
         }
-        if (EVAL) {
+        if (EVAL && live) {
             const float3 p0 = ldpv(a.P, vv[0], a.in4), p1 = ldpv(a.P, vv[1], a.in4), p2 = ldpv(a.P, vv[2], a.in4);
             stpv(a.Pn, V + r, (1.0f / 3.0f) * (p0 + p1 + p2), a.out4);
         }
-        return;
+    } else {
+        // second step, feature edge a -> b at corner jf, third vertex cc: split in three
+        const int jb = jf == 2 ? 0 : jf + 1, jc = jf == 0 ? 2 : jf - 1;
+        const int va = vv[jf], vb = vv[jb], vcc = vv[jc], tf = tt[jf];
+        const int rank = -1 - tf;                              // a boundary edge's rank
+        const int q1 = V + r, q2 = tf >= 0 ? V + tf / 3 : V + a.F + rank;
+        if (TOPO) {
+            fo[0] = va; fo[1] = q1; fo[2] = vcc;
+            fo[3] = q1; fo[4] = q2; fo[5] = vcc;
+            fo[6] = q2; fo[7] = vb; fo[8] = vcc;
+            if (live && tf >= 0 && c + jf < tf) {               // the crease edge's three pieces
+                push_crease(a, va, q1);
+                push_crease(a, q1, q2);
+                push_crease(a, q2, vb);
+            }
+            if (helpers) {
+                const int rf = tf / 3;
+                wo[0] = tf >= 0 ? 3 * (3 * rf + 2) : -1 - 3 * rank;
+                wo[1] = 3 * (c + 1) + 2;
+                wo[2] = carry(a, tt[jc]);
+                wo[3] = tf >= 0 ? 3 * (3 * rf + 1) : -2 - 3 * rank;
+                wo[4] = 3 * (c + 2) + 2;
+                wo[5] = 3 * c + 1;
+                wo[6] = tf >= 0 ? 3 * (3 * rf) : -3 - 3 * rank;
+                wo[7] = carry(a, tt[jb]);
+                wo[8] = 3 * (c + 1) + 1;
+                if (live) {
+                    a.fmn[c] = 1; a.fmn[c + 1] = 1; a.fmn[c + 2] = 1;
+                    // carried corners: a at child 0 corner 0, b at child 2 corner 1, cc at child 0 corner 2
+                    if (__ldg(a.vc + va) == c + jf) a.vcn[va] = 3 * c;
+                    if (__ldg(a.vc + vb) == c + jb) a.vcn[vb] = 3 * (c + 2) + 1;
+                    if (__ldg(a.vc + vcc) == c + jc) a.vcn[vcc] = 3 * c + 2;
+                    a.vcn[q1] = 3 * c + 1;                     // q1: child 0, corner 1
+                    if (tf < 0) a.vcn[q2] = 3 * (c + 1) + 1;   // a boundary q2: child 1, corner 1
+                }
+            }
+        }
+        if (EVAL && live) {
+            const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
+            stpv(a.Pn, q1, third_point(a, va, vb, pa, pb), a.out4);
+            if (tf < 0) stpv(a.Pn, q2, third_point(a, vb, va, pb, pa), a.out4);
+        }
     }
-    // second step, feature edge a -> b at corner jf, third vertex cc: split in three
-    const int jb = jf == 2 ? 0 : jf + 1, jc = jf == 0 ? 2 : jf - 1;
-    const int va = vv[jf], vb = vv[jb], vcc = vv[jc], tf = tt[jf];
-    const int rank = -1 - tf;                                  // a boundary edge's rank
-    const int q1 = V + r, q2 = tf >= 0 ? V + tf / 3 : V + a.F + rank;
     if (TOPO) {
-        const int rows[9] = {va, q1, vcc, q1, q2, vcc, q2, vb, vcc};
-        int *o = a.fvn + 3 * (size_t)c;
-#pragma unroll
-        for (int i = 0; i < 9; i++) o[i] = rows[i];
-        if (tf >= 0 && c + jf < tf) {                          // the crease edge's three pieces
-            push_crease(a, va, q1);
-            push_crease(a, q1, q2);
-            push_crease(a, q2, vb);
-        }
-        if (helpers) {
-            const int rf = tf / 3;
-            const int tw0[3] = {tf >= 0 ? 3 * (3 * rf + 2) : -1 - 3 * rank, tf >= 0 ? 3 * (3 * rf + 1) : -2 - 3 * rank,
-                                tf >= 0 ? 3 * (3 * rf) : -3 - 3 * rank};
-            int *w = a.twn + 3 * (size_t)c;
-            w[0] = tw0[0]; w[1] = 3 * (c + 1) + 2; w[2] = carry(a, tt[jc]);
-            w[3] = tw0[1]; w[4] = 3 * (c + 2) + 2; w[5] = 3 * c + 1;
-            w[6] = tw0[2]; w[7] = carry(a, tt[jb]); w[8] = 3 * (c + 1) + 1;
-            a.fmn[c] = 1; a.fmn[c + 1] = 1; a.fmn[c + 2] = 1;
-            // carried corners: a at child 0 corner 0, b at child 2 corner 1, cc at child 0 corner 2
-            if (__ldg(a.vc + va) == c + jf) a.vcn[va] = 3 * c;
-            if (__ldg(a.vc + vb) == c + jb) a.vcn[vb] = 3 * (c + 2) + 1;
-            if (__ldg(a.vc + vcc) == c + jc) a.vcn[vcc] = 3 * c + 2;
-            a.vcn[q1] = 3 * c + 1;                             // q1: child 0, corner 1
-            if (tf < 0) a.vcn[q2] = 3 * (c + 1) + 1;           // a boundary q2: child 1, corner 1
-        }
-    }
-    if (EVAL) {
-        const float3 pa = ldpv(a.P, va, a.in4), pb = ldpv(a.P, vb, a.in4);
-        stpv(a.Pn, q1, third_point(a, va, vb, pa, pb), a.out4);
-        if (tf < 0) stpv(a.Pn, q2, third_point(a, vb, va, pb, pa), a.out4);
+        // the children's rows (and twins) of the warp's 32 triangles, 1152 contiguous bytes each
+        __shared__ __align__(16) int srow[kBlock / 32][288];
+        const int w = threadIdx.x >> 5, r0 = r_in - (int)(threadIdx.x & 31);
+        warp_rows9(a.fvn, r0, 9LL * a.F, fo, srow[w]);
+        if (helpers) warp_rows9(a.twn, r0, 9LL * a.F, wo, srow[w]);
     }
 }
 
