@@ -93,18 +93,24 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a) {
             k++;
         }
     };
-    // the ring four corners per round: the chain of twins first (the only dependent loads), then
-    // the round's neighbours and feature bits, then their positions
+    // the ring eight corners per round: each corner's neighbour and feature bit are loaded as soon
+    // as the chain of twins (the only dependent loads) reaches it, and the round's positions after
+    // the chain, so a valence-6 vertex waits for the chain plus about two round trips
     int y = x;
     bool open = false, done = false;
     while (!done && n < kMaxValence) {
-        int ys[4];
-        bool use[4];
+        int w[8];
+        unsigned char f[8];
+        bool use[8];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < 8; q++) {
             use[q] = !done;
-            ys[q] = y;
+            w[q] = 0;
+            f[q] = 0;
             if (!done) {
+                w[q] = __ldg(a.fv + t_next(y));
+                const int qq = y / 3;
+                f[q] = (unsigned char)((__ldg(a.fm + qq) >> (y - 3 * qq)) & 1);
                 const int t = __ldg(a.tw + t_prev(y));
                 if (t < 0) {
                     open = true;             // y stays the corner whose previous edge is open
@@ -115,16 +121,9 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a) {
                 }
             }
         }
-        int w[4];
-        bool f[4];
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
-            w[q] = use[q] ? __ldg(a.fv + t_next(ys[q])) : 0;
-            f[q] = use[q] && feat(a.fm, ys[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; q++)
-            if (use[q]) neighbour(w[q], f[q]);
+        for (int q = 0; q < 8; q++)
+            if (use[q]) neighbour(w[q], f[q] != 0);
     }
     if (open) {
         // the fan ends at an incoming boundary edge u -> v; then the corners before x
