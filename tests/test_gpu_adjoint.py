@@ -98,3 +98,33 @@ def test_backward_chain_small_matches_oracle():
     (sub(P) * torch.from_numpy(w.astype(np.float32)).cuda()).sum().backward()
     want = _chain_t(Rs, w[np.argsort(pi)])
     np.testing.assert_allclose(P.grad.double().cpu().numpy(), want, atol=1e-5 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("scheme,fn", [
+    ("cc", lambda: synth.holed_cc_mixed(12, 10, holes=2, seed=73)),
+    ("loop", lambda: synth.torus_tri(8, 7, seed=74)),
+])
+def test_backward_where_no_gather_matches_oracle(scheme, fn):
+    """An open Catmull-Clark mesh and a Loop mesh have no matrix-free transpose: autograd takes
+    their stored transposes, and the gradient is R^T g from the oracle's operator chain."""
+    import scipy.sparse as sp
+    import torch
+    from paper_1809_06047_gb300.autograd import Subdivider
+    from tests import canon
+    m = fn()
+    L = 3
+    ref = oracle.subdivide(m, L, scheme, keep_all=True, operator=True)
+    Rs = [sp.csr_matrix((ref[l]["R_w"], (ref[l]["R_rows"], ref[l]["R_cols"])),
+                        shape=(ref[l + 1]["V"], ref[l]["V"])) for l in range(L)]
+    sub = Subdivider(m, L, scheme)
+    assert sub.op.bytes() > 0
+    counts = [dict(V=r["V"], F=r["F"], E=r["E"]) for r in ref]
+    pi = canon.vertex_maps(scheme, [sub.topo.faces(l) for l in range(L + 1)],
+                           [r["fv"] for r in ref], counts)[L]
+    rng = np.random.default_rng(9)
+    w = rng.standard_normal((ref[L]["V"], 3))
+    P = torch.from_numpy(np.ascontiguousarray(m["P"], np.float32)).cuda().requires_grad_(True)
+    (sub(P) * torch.from_numpy(w.astype(np.float32)).cuda()).sum().backward()
+    sub.topo.status()
+    want = _chain_t(Rs, w[np.argsort(pi)])
+    np.testing.assert_allclose(P.grad.double().cpu().numpy(), want, atol=1e-5 * np.abs(want).max())
