@@ -114,6 +114,9 @@ void free_topo(TopoImpl &T) {
 alsub_status alloc_crease(TopoImpl &T, CreaseList &C, long long cap, bool table, cudaStream_t s) {
     C.cap = cap;
     AL(C.count, 1);
+    // a level without creases keeps count 0 for good (only the inheritance into a level with
+    // capacity writes a count), so it is cleared here once instead of on every call
+    if (cap == 0 && !T.dry) cudaMemsetAsync(C.count, 0, sizeof(int), s);
     if (cap > 0) {
         AL(C.edge, cap);
         AL(C.own, cap);
@@ -559,10 +562,7 @@ void subdivide_body(TopoImpl &T, const float *P0, float *PL, void *scratch, cuda
         level_buffers(T, P0, PL, scratch, l, &in, &out);
         if (l == 2 && z != s) cudaStreamWaitEvent(s, T.ring_ev, 0);
         step(T, l, true, T.L[l + 1].helpers, in, out, s);
-        if (l + 1 < T.levels) {
-            if (crease_alive(T, l + 1)) analyse_beside(l + 1, false);
-            else crease_analyse(T, l + 1, true, s);    // nothing alive: at most a count reset
-        }
+        if (l + 1 < T.levels && crease_alive(T, l + 1)) analyse_beside(l + 1, false);
         if (crease_alive(T, l)) {
             wait_analysis(l);
             crease_fix(T, l, in, out, s);

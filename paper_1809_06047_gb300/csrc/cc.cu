@@ -85,7 +85,8 @@ __device__ __forceinline__ float3 face_point_l0(const Level0 &z, const float *P,
     return (1.0f / (float)c) * acc;
 }
 
-template <bool TOPO, bool HELP, bool EVAL, bool BND>
+// VERTS: the vertex points too (the ragged batch); else k_cc_l0_vert takes them after this kernel.
+template <bool TOPO, bool HELP, bool EVAL, bool BND, bool VERTS = true>
 __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const Level0 &z = a.z;
@@ -119,7 +120,7 @@ __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
                 stpv(a.Pn, VF + __ldg(z.ce + x), ep, a.out4);
             }
         }
-        for (int j = 0; j < c; j++) {
+        for (int j = 0; VERTS && j < c; j++) {
             int x = s + j, v = __ldg(z.fv + x);
             if (__ldg(z.vc + v) != x) continue;
             int y = x, n = 0;
@@ -509,7 +510,60 @@ template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_l0(CCArgs a) {
     pdl_wait();
     pdl_trigger();
-    cc_l0_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    cc_l0_body<TOPO, HELP, EVAL, BND, false>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+// Level 0's vertex points, one thread per control vertex from its designated corner, after
+// k_cc_l0: the ring's face points are read back from the level-1 positions k_cc_l0 stored (the
+// same values the ring would recompute), the ring taken eight corners per round with the chain
+// x <- twin(prev(x)) first. Sums in ring order, as cc_l0_body's.
+template <bool BND>
+__global__ void __launch_bounds__(kBlock) k_cc_l0_vert(CCArgs a) {
+    pdl_wait();
+    pdl_trigger();
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.V || failed(a.status)) return;
+    const Level0 &z = a.z;
+    const float *P = a.P;
+    const int x = __ldg(z.vc + v);
+    float3 sp = f3(0.f, 0.f, 0.f), sf = sp;
+    int y = x, n = 0;
+    bool done = false, open = false;
+    while (!done && n < kMaxValence) {
+        int ys[8];
+        bool use[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            use[q] = !done;
+            ys[q] = y;
+            if (!done) {
+                const int t = __ldg(z.rn + y);
+                if (BND && t < 0) {
+                    open = true;
+                    done = true;
+                } else {
+                    y = t;
+                    done = y == x || n + q + 1 >= kMaxValence;
+                }
+            }
+        }
+        int fq[8], wq[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            fq[q] = use[q] ? __ldg(z.cf + ys[q]) : 0;
+            wq[q] = use[q] ? __ldg(z.fv + __ldg(z.nx + ys[q])) : 0;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (!use[q]) continue;
+            sf += ldpv(a.Pn, a.V + fq[q], a.out4);
+            sp += ldp(P, wq[q]);
+            n++;
+        }
+    }
+    if (BND && open) return;                   // boundary vertex: repaired
+    if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); return; }
+    const float inv = 1.0f / (float)n;
+    stpv(a.Pn, v, (1.0f - 2.0f * inv) * ldp(P, v) + (inv * inv) * (sp + sf), a.out4);
 }
 template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
@@ -669,7 +723,10 @@ __global__ void __launch_bounds__(512, 2) k_cc_batch(const CCArgs *__restrict__ 
 template <bool T, bool H, bool E, bool B>
 void launch_b(const CCArgs &a, int derive, cudaStream_t s) {
     const unsigned g = grid_for(a.F, ALSUB_SIB_BLOCK);
-    if (a.l == 0) launch_pdl(k_cc_l0<T, H, E, B>, grid_for(a.F), kBlock, s, a);
+    if (a.l == 0) {
+        launch_pdl(k_cc_l0<T, H, E, B>, grid_for(a.F), kBlock, s, a);
+        if (E) launch_pdl(k_cc_l0_vert<B>, grid_for(a.V), kBlock, s, a);
+    }
     else if (a.l == 1) launch_pdl(k_cc_quad<T, H, E, B>, grid_for(a.F), kBlock, s, a);
     else if (derive == 2) launch_pdl(k_cc_sib<T, false, E, 2, B>, g, ALSUB_SIB_BLOCK, s, a);
     else if (derive == 1) launch_pdl(k_cc_sib<T, false, E, 1, B>, g, ALSUB_SIB_BLOCK, s, a);
@@ -725,6 +782,7 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     CCArgs a = make_args(T, l, P, Pn, &derive);
     bool ev = P != nullptr;
     if (topo || ev) T.launches += 1;
+    if (ev && l == 0) T.launches += 1;           // k_cc_l0_vert
     // levels >= 2: the vertices born on levels 0 and 1 go to k_cc_ring01, launched first on the
     // handle's ring stream beside the sibling kernel when it has one (forked and joined here, so
     // that its few blocks take SMs before the sibling kernel's grid fills them), else after it

@@ -283,6 +283,26 @@ __device__ __forceinline__ float crease_lookup(const CreaseList &C, int e) {
     }
     return 0.f;
 }
+// A lookup whose first bucket b was loaded already (q): resolved from it, probing on only when the
+// bucket holds two other edges. Lets a thread issue the first probes of many lookups at once.
+__device__ __forceinline__ float crease_resolve(const CreaseList &C, int e, unsigned b, int4 q) {
+    if (q.x == e) return __int_as_float(q.y);
+    if (q.x < 0) return 0.f;
+    if (q.z == e) return __int_as_float(q.w);
+    if (q.z < 0) return 0.f;
+    const int4 *__restrict__ t = reinterpret_cast<const int4 *>(C.tab);
+    const unsigned bmask = (unsigned)C.hmask >> 1;
+    b = (b + 1) & bmask;
+    for (unsigned probe = 0; probe < bmask; probe++) {
+        const int4 r = __ldg(t + b);
+        if (r.x == e) return __int_as_float(r.y);
+        if (r.x < 0) return 0.f;
+        if (r.z == e) return __int_as_float(r.w);
+        if (r.z < 0) return 0.f;
+        b = (b + 1) & bmask;
+    }
+    return 0.f;
+}
 // Returns false when the edge was already in the table.
 __device__ __forceinline__ bool crease_insert(const CreaseList &C, int e, float s) {
     const unsigned bmask = (unsigned)C.hmask >> 1;

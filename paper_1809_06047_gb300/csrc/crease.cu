@@ -84,14 +84,29 @@ __device__ void analyse2(const Acc &A, const CreaseList &C, int sa, int sb, EndI
             if (!da) { ya = A.ring(ya); da = ya == sa; }
             if (!db) { yb = A.ring(yb); db = yb == sb; }
         }
-        float fa[kW], fb[kW];
+        // the round's lookups: every edge id, then every first bucket, then their resolution (a
+        // lookup only probes on past a bucket of two other edges), so they share round trips
+        const int4 *__restrict__ tab = reinterpret_cast<const int4 *>(C.tab);
+        int ea[kW], eb[kW];
         int na[kW], nb[kW];
 #pragma unroll
         for (int q = 0; q < kW; q++) {
-            fa[q] = ua[q] ? crease_lookup(C, A.edge(ca[q])) : 0.f;
-            fb[q] = ub[q] ? crease_lookup(C, A.edge(cb[q])) : 0.f;
+            ea[q] = ua[q] ? A.edge(ca[q]) : 0;
+            eb[q] = ub[q] ? A.edge(cb[q]) : 0;
             na[q] = ua[q] ? A.vtx(A.next(ca[q])) : -1;
             nb[q] = ub[q] ? A.vtx(A.next(cb[q])) : -1;
+        }
+        int4 qa[kW], qb[kW];
+#pragma unroll
+        for (int q = 0; q < kW; q++) {
+            qa[q] = ua[q] ? __ldg(tab + crease_bucket(ea[q], C.hshift)) : make_int4(-1, 0, -1, 0);
+            qb[q] = ub[q] ? __ldg(tab + crease_bucket(eb[q], C.hshift)) : make_int4(-1, 0, -1, 0);
+        }
+        float fa[kW], fb[kW];
+#pragma unroll
+        for (int q = 0; q < kW; q++) {
+            fa[q] = ua[q] ? crease_resolve(C, ea[q], crease_bucket(ea[q], C.hshift), qa[q]) : 0.f;
+            fb[q] = ub[q] ? crease_resolve(C, eb[q], crease_bucket(eb[q], C.hshift), qb[q]) : 0.f;
         }
 #pragma unroll
         for (int q = 0; q < kW; q++) {
@@ -266,10 +281,8 @@ bool crease_alive(const TopoImpl &T, int l) {
 
 void crease_analyse(TopoImpl &T, int l, bool inherit, cudaStream_t s) {
     CreaseList *dst = l + 1 <= T.levels ? &T.L[l + 1].cr : nullptr;
-    if (inherit && dst && dst->cap == 0) {  // all creases have decayed: level l + 1 has none
-        if (dst->count) cudaMemsetAsync(dst->count, 0, sizeof(int), s);
-        inherit = false;
-    }
+    if (inherit && dst && dst->cap == 0) inherit = false;   // all creases have decayed: level l + 1
+                                                              // has none (its count stays 0)
     if (!dst) inherit = false;
     if (!crease_alive(T, l)) return;
     if (inherit) crease_table_clear(*dst, s);
