@@ -69,6 +69,8 @@ struct CCArgs {
     int *status;
     bool bnd;                     // the mesh is open (twins may be -1)
     bool rev;                     // sibling kernel: blocks take the faces from the end backwards
+    int V0 = 0, F0 = 0;           // control-mesh counts and each control edge's owner corner (the
+    const int *eo0 = nullptr;     // designated corners of level 1's vertices)
 };
 
 // Child twins across the halves of a parent edge (corner 0 and corner 3 of the children), or -1
@@ -139,7 +141,8 @@ __device__ __forceinline__ void cc_l0_body(const CCArgs &a, int r) {
     }
 }
 
-template <bool TOPO, bool HELP, bool EVAL, bool BND>
+// VERTS: the vertex points too (the ragged batch); else k_cc_quad_vert takes them after this kernel.
+template <bool TOPO, bool HELP, bool EVAL, bool BND, bool VERTS = true>
 __device__ __forceinline__ void cc_quad_body(const CCArgs &a, int r) {
     if (r >= a.F || failed(a.status)) return;
     const int VF = a.V + a.F, E2 = 2 * a.E, c0 = 4 * r;
@@ -186,7 +189,7 @@ __device__ __forceinline__ void cc_quad_body(const CCArgs &a, int r) {
         }
         // vertex points gathered by designated corners (k = 3 is never designated)
 #pragma unroll 1
-        for (int k = 0; k < 3; k++) {
+        for (int k = 0; VERTS && k < 3; k++) {
             int x = c0 + k;
             if (!cc_vown(a.l, x, a.z)) continue;
             int y = x, n = 0;
@@ -569,7 +572,61 @@ template <bool TOPO, bool HELP, bool EVAL, bool BND>
 __global__ void __launch_bounds__(kBlock) k_cc_quad(CCArgs a) {
     pdl_wait();
     pdl_trigger();
-    cc_quad_body<TOPO, HELP, EVAL, BND>(a, blockIdx.x * blockDim.x + threadIdx.x);
+    cc_quad_body<TOPO, HELP, EVAL, BND, false>(a, blockIdx.x * blockDim.x + threadIdx.x);
+}
+// Level 1's vertex points, one thread per vertex after k_cc_quad, as k_cc_l0_vert does for level
+// 0. The designated corner follows from the vertex's birth: a control vertex's is child 0 of its
+// level-0 corner, a face point's corner 2 of its face's first child, an edge point's corner 1 of
+// its owner corner's child. The ring's face points are read back from the level-2 positions
+// k_cc_quad stored (the values cc_quad_body's ring recomputes, summed in the same order).
+template <bool BND>
+__global__ void __launch_bounds__(kBlock) k_cc_quad_vert(CCArgs a) {
+    pdl_wait();
+    pdl_trigger();
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= a.V || failed(a.status)) return;
+    const Level0 &z = a.z;
+    const float *P = a.P;
+    int x;
+    if (v < a.V0) x = 4 * __ldg(z.vc + v);
+    else if (v < a.V0 + a.F0) x = 4 * __ldg(z.off + (v - a.V0)) + 2;
+    else x = 4 * __ldg(a.eo0 + (v - a.V0 - a.F0)) + 1;
+    float3 sp = f3(0.f, 0.f, 0.f), sf = sp;
+    int y = x, n = 0;
+    bool done = false, open = false;
+    while (!done && n < kMaxValence) {
+        int ys[8];
+        bool use[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            use[q] = !done;
+            ys[q] = y;
+            if (!done) {
+                const int t = __ldg(a.tw + quad_prev(y));
+                if (BND && t < 0) {
+                    open = true;
+                    done = true;
+                } else {
+                    y = t;
+                    done = y == x || n + q + 1 >= kMaxValence;
+                }
+            }
+        }
+        int wq[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) wq[q] = use[q] ? __ldg(a.fv + quad_next(ys[q])) : 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (!use[q]) continue;
+            sf += ldpv(a.Pn, a.V + (ys[q] >> 2), a.out4);
+            sp += ldpv(P, wq[q], a.in4);
+            n++;
+        }
+    }
+    if (BND && open) return;                   // boundary vertex: repaired
+    if (y != x) { set_status(a.status, ALSUB_ERR_UNSUPPORTED); return; }
+    const float inv = 1.0f / (float)n;
+    stpv(a.Pn, v, (1.0f - 2.0f * inv) * ldpv(P, v, a.in4) + (inv * inv) * (sp + sf), a.out4);
 }
 // Vertices born on levels 0 and 1 are left to k_cc_ring01, which runs beside this kernel.
 template <bool TOPO, bool HELP, bool EVAL, int DERIVE, bool BND>
@@ -727,7 +784,10 @@ void launch_b(const CCArgs &a, int derive, cudaStream_t s) {
         launch_pdl(k_cc_l0<T, H, E, B>, grid_for(a.F), kBlock, s, a);
         if (E) launch_pdl(k_cc_l0_vert<B>, grid_for(a.V), kBlock, s, a);
     }
-    else if (a.l == 1) launch_pdl(k_cc_quad<T, H, E, B>, grid_for(a.F), kBlock, s, a);
+    else if (a.l == 1) {
+        launch_pdl(k_cc_quad<T, H, E, B>, grid_for(a.F), kBlock, s, a);
+        if (E) launch_pdl(k_cc_quad_vert<B>, grid_for(a.V), kBlock, s, a);
+    }
     else if (derive == 2) launch_pdl(k_cc_sib<T, false, E, 2, B>, g, ALSUB_SIB_BLOCK, s, a);
     else if (derive == 1) launch_pdl(k_cc_sib<T, false, E, 1, B>, g, ALSUB_SIB_BLOCK, s, a);
     else launch_pdl(k_cc_sib<T, H, E, 0, B>, g, ALSUB_SIB_BLOCK, s, a);
@@ -754,6 +814,9 @@ CCArgs make_args(TopoImpl &T, int l, const float *P, float *Pn, int *derive_out)
     a.fvn = B.fv; a.cen = B.ce; a.twn = B.tw;
     a.status = T.status;
     a.bnd = T.mesh->B > 0;
+    a.V0 = (int)T.L[0].V;
+    a.F0 = (int)T.L[0].F;
+    a.eo0 = T.eo0;
     // consecutive steps take their faces in opposite orders, the last step from the end: a step
     // starts on the rows and positions its predecessor wrote last, which are still in L2
     a.rev = ((T.levels - 1 - l) & 1) == 0;
@@ -782,7 +845,7 @@ void cc_step(TopoImpl &T, int l, bool topo, bool helpers, const float *P, float 
     CCArgs a = make_args(T, l, P, Pn, &derive);
     bool ev = P != nullptr;
     if (topo || ev) T.launches += 1;
-    if (ev && l == 0) T.launches += 1;           // k_cc_l0_vert
+    if (ev && l <= 1) T.launches += 1;           // k_cc_l0_vert, k_cc_quad_vert
     // levels >= 2: the vertices born on levels 0 and 1 go to k_cc_ring01, launched first on the
     // handle's ring stream beside the sibling kernel when it has one (forked and joined here, so
     // that its few blocks take SMs before the sibling kernel's grid fills them), else after it
