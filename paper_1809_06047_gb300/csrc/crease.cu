@@ -160,8 +160,10 @@ __global__ void __launch_bounds__(kBlock) k_crease_analyse(Acc A, CreaseArgs a, 
         return;
     }
     const int t = A.twin(o);
-    const int va = A.vtx(o), vb = A.vtx(t);
-    const int first = a.in.verts[2 * i];    // the list's endpoint order, which the fix reads
+    const int va = A.vtx(o);
+    // the list holds the entry's two endpoints (in either order): the one that is not v_o's
+    const int first = a.in.verts[2 * i], second = a.in.verts[2 * i + 1];
+    const int vb = first == va ? second : first;
     EndInfo ra, rb;
     analyse2(A, a.in, o, t, ra, rb, a.status);
     const int4 ia = make_int4(ra.k | (ra.minc == o ? 1 << 16 : 0), __float_as_int(ra.S), ra.n1, ra.n2);

@@ -289,16 +289,19 @@ __global__ void k_crease0(int K, const int *__restrict__ cv, const float *__rest
     if (i >= K) return;
     out.edge[i] = 0; out.own[i] = 0; out.sig[i] = 0.f; out.verts[2 * i] = 0; out.verts[2 * i + 1] = 0;
     if (failed(status)) return;
-    const int x = dir_find(tab, cv[2 * i], cv[2 * i + 1]);
+    const int va = cv[2 * i], vb = cv[2 * i + 1];
+    const int x = dir_find(tab, va, vb);
     if (x < 0) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
-    const int o = own[x] ? x : tw[x], e = ce[x];
+    // x is the corner va -> vb: it owns the edge, or its twin vb -> va does
+    const bool ox = own[x] != 0;
+    const int o = ox ? x : tw[x], e = ce[x];
     const float s = cs[i];
     if (!crease_insert(out, e, s)) { set_status(status, ALSUB_ERR_INVALID_ARG); return; }
     out.edge[i] = e;
     out.own[i] = o;
     out.sig[i] = s;
-    out.verts[2 * i] = fv[o];
-    out.verts[2 * i + 1] = fv[tw[o]];
+    out.verts[2 * i] = ox ? va : vb;           // the owner corner's start, then its end
+    out.verts[2 * i + 1] = ox ? vb : va;
 }
 
 // sqrt(3) with feature edges, level 0 (the general path of sqrt3f.cu): the boundary corners (twin
