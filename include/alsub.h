@@ -396,7 +396,9 @@ alsub_status alsub_topology_set_edits(alsub_topology_t topo, int32_t level, int3
  *          no atomics, in two passes per level (per coarse face its contribution at each corner,
  *          then per coarse vertex the sum of its contributions), from per-vertex coefficients and
  *          per-corner slots computed once here (about 40 bytes per vertex of every level below the
- *          last, and the levels' edge ids and twins, which are then stored). With
+ *          last, and the levels' edge ids and twins, which are then stored), with a scratch of
+ *          16 bytes per contribution of the largest such level (about 128 bytes per vertex) and
+ *          two levels of gradients. With
  *          ALSUB_OP_TRANSPOSE (and no other flag) the transposes of the R_l are stored and applied
  *          instead (any scheme). When combined with CHAIN or COMPOSE, apply takes the matrix-free
  *          form and alsub_operator_info the stored matrices.

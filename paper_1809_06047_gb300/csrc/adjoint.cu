@@ -47,7 +47,6 @@ struct AdjTopo {
 };
 
 struct AdjArgs {
-    int nnz;                  // corners of the coarse level
     int V, F;                 // coarse counts: level l + 1 numbers [old V | face points F | edge points]
     const float *G;           // gradient of level l + 1
     float *g;                 // gradient of level l
@@ -269,7 +268,6 @@ void adjoint_prepare(TopoImpl &T, int l, const AdjLevel &P, cudaStream_t s) {
 void adjoint_step(TopoImpl &T, int l, const float *G, bool G4, float *g, bool g4, const AdjLevel &P,
                   float4 *part, cudaStream_t s) {
     AdjArgs a;
-    a.nnz = (int)T.L[l].nnz;
     a.V = (int)T.L[l].V;
     a.F = (int)T.L[l].F;
     a.G = G; a.G4 = G4;
