@@ -156,20 +156,19 @@ __global__ void __launch_bounds__(kBlock) k_adj_face(const int *__restrict__ fv,
     }
 }
 
-// Level 0: the same first pass over polygons (order c, corners s .. s + c - 1; c' of the face
-// across each edge read through the twin).
+// Level 0: the same first pass over polygons, one thread per corner x of face r (order c, corners
+// s .. s + c - 1; c' of the face across x's edge read through the twin).
 template <bool CREASED>
-__global__ void __launch_bounds__(kBlock) k_adj_face0(AdjTopo<true> A, AdjArgs a, float4 *__restrict__ part) {
+__global__ void __launch_bounds__(kBlock) k_adj_face0(AdjTopo<true> A, AdjArgs a, int nnz, float4 *__restrict__ part) {
     pdl_wait();
     pdl_trigger();
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= a.F || failed(a.status)) return;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    if (x >= nnz || failed(a.status)) return;
     const int VF = a.V + a.F;
-    const int s0 = A.first(r), c = A.order(r);
+    const int r = A.face(x), s0 = A.first(r), c = A.order(r), k = x - s0;
     const float ic = 1.0f / (float)c;
     const float3 gf = ic * ldpv(a.G, a.V + r, a.G4);
-    for (int k = 0; k < c; k++) {
-        const int x = s0 + k;
+    {
         const int t = __ldg(A.tw + x);
         const float ict = 1.0f / (float)A.order(A.face(t));
         const int e0 = __ldg(A.ce + x);
@@ -279,8 +278,9 @@ void adjoint_step(TopoImpl &T, int l, const float *G, bool G4, float *g, bool g4
     a.status = T.status;
     const bool cr = level_creased(T, l);
     if (l == 0) {
-        if (cr) launch_pdl(k_adj_face0<true>, grid_for(a.F), kBlock, s, adj_topo<true>(T, l), a, part);
-        else launch_pdl(k_adj_face0<false>, grid_for(a.F), kBlock, s, adj_topo<true>(T, l), a, part);
+        const int n0 = (int)T.L[0].nnz;
+        if (cr) launch_pdl(k_adj_face0<true>, grid_for(n0), kBlock, s, adj_topo<true>(T, l), a, n0, part);
+        else launch_pdl(k_adj_face0<false>, grid_for(n0), kBlock, s, adj_topo<true>(T, l), a, n0, part);
         launch_pdl(k_adj_vert<true>, grid_for(a.V), kBlock, s, adj_topo<true>(T, l), a, (const float4 *)part);
     } else {
         const LevelBuf &B = T.L[l];
