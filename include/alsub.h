@@ -416,7 +416,8 @@ typedef enum {
     ALSUB_OP_CHAIN = 1,
     ALSUB_OP_COMPOSE = 2,
     ALSUB_OP_TRANSPOSE = 4,
-    ALSUB_OP_MATRIX_FREE = 8
+    ALSUB_OP_MATRIX_FREE = 8,
+    ALSUB_OP_STACKED = 16          /* alsub_build_adaptive_operator only */
 } alsub_operator_flags;
 
 alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *stream,
@@ -447,6 +448,31 @@ alsub_status alsub_apply_operator(alsub_operator_t op, const float *P0_dev, floa
  * operator has neither. */
 alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL_dev, float *g0_dev,
                                             void *stream);
+
+/*
+ * Feature-adaptive single-SpMV operator (Sec. 3.4, Fig. module_selective, evaluated as Sec. 3.6
+ * "Single SpMV evaluation" and Sec. 5 "Adaptive Subdivision" do): after the build, one SpMV takes
+ * the control points to every refined point of a chain of selective refinement rounds,
+ *   R = R^(n-1) X^(n-1) ... R^(1) X^(1) R^(0),
+ * where R^(k) = R_{L_k - 1} ... R_0 composes the levels of topos[k] (the identity when it has none)
+ * and X^(k) is the extraction matrix of topos[k]'s mesh: row i is e_{vmap[i]} over the vertices of
+ * the level it was extracted from. topos[0] is any built topology of the control mesh; for k >= 1
+ * topos[k] must be built on a mesh that alsub_topology_extract took from the last level of
+ * topos[k - 1] (checked from the handles; INVALID_ARG otherwise). All n topologies are read during
+ * the build only: the operator keeps nothing of them, and they may be destroyed afterwards.
+ *   flags: ALSUB_OP_TRANSPOSE also stores R^T (alsub_apply_operator_transpose);
+ *          ALSUB_OP_STACKED stacks the rounds: rows are the last level of topos[0], then that of
+ *          topos[1], ... (the points every round's patches and faces need), instead of the last
+ *          round's only. Other flags are INVALID_ARG.
+ * alsub_operator_info(op, -1, ...) gives the matrix (rows = the output points, cols = V of topos[0]'s
+ * control mesh); alsub_apply_operator computes P_out = R P_0 with P0_dev float[3 cols] and PL_dev
+ * float[3 rows]. Synchronises `stream` (the non-zero counts size the allocations).
+ * Errors: INVALID_ARG (NULL, n < 1, a topology not built, a chain that is not one), UNSUPPORTED (a
+ * stencil row of more than 192 entries; a sqrt(3) mesh with boundaries or infinitely sharp
+ * creases), OOM, DEVICE.
+ */
+alsub_status alsub_build_adaptive_operator(const alsub_topology_t *topos, int32_t n, uint32_t flags,
+                                           void *stream, alsub_operator_t *out);
 
 alsub_status alsub_operator_destroy(alsub_operator_t op);
 

@@ -225,6 +225,31 @@ def extract(mesh: dict, select=None, rings: int = 1, scheme: str = "cc") -> dict
     return out
 
 
+def adaptive_operator(mesh: dict, rounds: int, rings: int = 2, scheme: str = "cc", stacked: bool = False):
+    """The feature-adaptive subdivision operator as one matrix (Sec. 3.4, Fig. module_selective:
+    the extraction matrices act on the vertex data before each refinement; composed into a single
+    SpMV as Eq. singleSpMV does for uniform refinement and Sec. 5 "Adaptive Subdivision" evaluates
+    it). Each round extracts ``rings`` rings around the selected vertices of the previous round's
+    refined level (``extract`` with its default selection; its vmap gives X, row i = e_vmap[i])
+    and refines them one level (the oracle's R_0 of the extracted mesh), so
+        R = R^(n) X^(n) ... R^(1) X^(1)
+    as scipy sparse products. ``stacked``: the identity of the control mesh, then every round's
+    rows, stacked in round order. Returns a scipy CSR matrix over the control points."""
+    import scipy.sparse as sp
+    cur = dict(mesh, P=np.asarray(mesh["P"], dtype=np.float64))
+    C = sp.identity(int(mesh["V"]), dtype=np.float64, format="csr")
+    blocks = [C]
+    for _ in range(rounds):
+        e = extract(cur, None, rings, scheme=scheme)
+        X = sp.csr_matrix((np.ones(e["V"]), (np.arange(e["V"]), e["vmap"])), shape=(e["V"], int(cur["V"])))
+        lv = subdivide(e, 1, scheme, operator=True)
+        R = sp.csr_matrix((lv[0]["R_w"], (lv[0]["R_rows"], lv[0]["R_cols"])), shape=(lv[1]["V"], e["V"]))
+        C = (R @ (X @ C)).tocsr()
+        cur = lv[1]
+        blocks.append(C)
+    return sp.vstack(blocks).tocsr() if stacked else C
+
+
 def subdivide_edits(mesh: dict, levels: int, scheme: str, edits: dict) -> list[dict]:
     """Refinement with hierarchical edits (Sec. 3.5 "Other effects"): one level at a time, the
     offsets edits[l] = (vertex ids, float[n, 3]) added to level l's positions once it is refined,

@@ -86,6 +86,7 @@ SIGNATURES = {
     "alsub_topology_timings": [H, P(ctypes.c_double), P(c_int32), P(c_int64)],
     "alsub_refine_vertices_static": [H, c_void_p, c_void_p, c_void_p],
     "alsub_build_operator": [H, ctypes.c_uint32, c_void_p, P(H)],
+    "alsub_build_adaptive_operator": [P(H), c_int32, ctypes.c_uint32, c_void_p, P(H)],
     "alsub_operator_info": [H, c_int32, P(c_int64), P(c_int64), P(c_int64), P(c_void_p), P(c_void_p),
                             P(c_void_p)],
     "alsub_apply_operator": [H, c_void_p, c_void_p, c_void_p],

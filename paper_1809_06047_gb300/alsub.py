@@ -394,7 +394,7 @@ class Topology:
 class Operator:
     """alsub_build_operator and friends: R_l per level and/or the composite R = R_{L-1}...R_0."""
 
-    CHAIN, COMPOSE, TRANSPOSE, MATRIX_FREE = 1, 2, 4, 8
+    CHAIN, COMPOSE, TRANSPOSE, MATRIX_FREE, STACKED = 1, 2, 4, 8, 16
 
     def __init__(self, topo: Topology, chain: bool = True, compose: bool = False,
                  transpose: bool = False, matrix_free: bool = False, stream=None):
@@ -415,6 +415,10 @@ class Operator:
             self.close()
         except Exception:  # noqa: BLE001
             pass
+
+    def _sizes(self):
+        """(output points, control points)."""
+        return self.topo.counts[-1]["V"], self.topo.counts[0]["V"]
 
     def bytes(self) -> int:
         """alsub_operator_bytes: device bytes the operator holds."""
@@ -443,7 +447,7 @@ class Operator:
     def apply(self, P0: torch.Tensor, out=None, stream=None) -> torch.Tensor:
         """alsub_apply_operator: P_L = R P_0."""
         assert P0.is_cuda and P0.dtype == torch.float32 and P0.is_contiguous()
-        VL = self.topo.counts[-1]["V"]
+        VL = self._sizes()[0]
         if out is None:
             out = torch.empty((VL, 3), dtype=torch.float32, device=P0.device)
         _check(lib().alsub_apply_operator(self._h, ctypes.c_void_p(P0.data_ptr()),
@@ -453,13 +457,33 @@ class Operator:
     def apply_transpose(self, gL: torch.Tensor, out=None, stream=None) -> torch.Tensor:
         """alsub_apply_operator_transpose: g_0 = R^T g_L."""
         assert gL.is_cuda and gL.dtype == torch.float32 and gL.is_contiguous()
-        V0 = self.topo.counts[0]["V"]
+        V0 = self._sizes()[1]
         if out is None:
             out = torch.empty((V0, 3), dtype=torch.float32, device=gL.device)
         _check(lib().alsub_apply_operator_transpose(self._h, ctypes.c_void_p(gL.data_ptr()),
                                                     ctypes.c_void_p(out.data_ptr()),
                                                     ctypes.c_void_p(_stream(stream))))
         return out
+
+
+class AdaptiveOperator(Operator):
+    """alsub_build_adaptive_operator: one SpMV from the control points to the points of a chain of
+    selective refinement rounds, topos[k] built on a mesh extracted from the last level of
+    topos[k - 1]; ``stacked`` stacks every round's last level. The topologies are read during the
+    build only."""
+
+    def __init__(self, topos, stacked: bool = False, transpose: bool = False, stream=None):
+        self.topo = None
+        hs = (ctypes.c_void_p * len(topos))(*[t.handle.value for t in topos])
+        flags = (self.TRANSPOSE if transpose else 0) | (self.STACKED if stacked else 0)
+        self._h = ctypes.c_void_p()
+        _check(lib().alsub_build_adaptive_operator(hs, len(topos), flags, ctypes.c_void_p(_stream(stream)),
+                                                   ctypes.byref(self._h)))
+        i = self.info(-1)
+        self.rows, self.cols = i["rows"], i["cols"]
+
+    def _sizes(self):
+        return self.rows, self.cols
 
 
 class Batch:

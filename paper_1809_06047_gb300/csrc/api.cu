@@ -895,6 +895,8 @@ alsub_status alsub_topology_extract(alsub_topology_t topo, int32_t level, const 
         return st;
     }
     h->m.B = (int)B;
+    h->m.src_topo = &T;
+    h->m.src_level = level;
     *out = h;
     return ALSUB_OK;
 }

@@ -85,6 +85,8 @@ struct MeshImpl {
     int B = 0;                 // boundary edges (Catmull-Clark open meshes)
     int *d_vmap = nullptr;     // extracted meshes (selective subdivision): kept vertex -> source vertex
     int *d_fmap = nullptr;     //                                           kept face -> source face
+    const void *src_topo = nullptr;   // extracted meshes: the topology and level they were taken
+    int src_level = -1;               // from (identity only: it is never dereferenced)
     void *d_block = nullptr;   // one allocation holding d_off, d_fv, d_cv, d_cs and d_status (or
                                // null: those are allocated one by one)
     int *d_status = nullptr;   // checks of the mesh that run on the device (the boundary edge count

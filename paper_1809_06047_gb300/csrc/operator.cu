@@ -367,6 +367,36 @@ __global__ void k_gemm(long long rows, const long long *__restrict__ ap, const i
     if (!FILL) cnt[i] = m;
 }
 
+// ---------------------------------------------------------------- extraction and stacking
+
+// C = X A for an extraction matrix X (row i = e_{vmap[i]}): row i of C is row vmap[i] of A. With
+// no A (ap null) A is the identity, and with no map X is too (row i = e_i).
+template <bool FILL>
+__global__ void k_take_rows(long long rows, const int *__restrict__ vmap, const long long *__restrict__ ap,
+                            const int *__restrict__ ac, const float *__restrict__ aw, int *cnt,
+                            const long long *__restrict__ cp, int *cc, float *cw) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= rows) return;
+    const int j = vmap ? vmap[i] : (int)i;
+    if (!ap) {
+        if (FILL) { cc[cp[i]] = j; cw[cp[i]] = 1.f; }
+        else cnt[i] = 1;
+        return;
+    }
+    const long long a0 = ap[j], n = ap[j + 1] - a0;
+    if (!FILL) { cnt[i] = (int)n; return; }
+    const long long c0 = cp[i];
+    for (long long q = 0; q < n; q++) { cc[c0 + q] = ac[a0 + q]; cw[c0 + q] = aw[a0 + q]; }
+}
+
+// rowptr of a block of rows placed at row r0 and entry z0 of a stacked matrix (the last block
+// also writes the end)
+__global__ void k_rowptr_shift(long long rows, const long long *__restrict__ ap, long long z0, long long *out,
+                               bool last) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < rows || (last && i == rows)) out[i] = ap[i] + z0;
+}
+
 // ---------------------------------------------------------------- SpMV on packed xyz
 
 // y = A x on xyz rows, S lanes per row: lane k of a row's group takes entries start + k,
@@ -552,6 +582,18 @@ alsub_status build_product(alsub_operator_s &O, const Csr &A, const Csr &B, Csr 
                                                O.cnt, M.rowptr, M.col, M.w, O.status); });
 }
 
+// M = X A: X the extraction map of `rows` rows (the identity when vmap is null); an A without
+// arrays is the identity of A.rows
+alsub_status build_take(alsub_operator_s &O, const Csr &A, const int *vmap, long long rows, Csr &M) {
+    cudaStream_t s = O.stream;
+    unsigned g = grid_for(rows);
+    return two_stage(O, M, rows, A.cols,
+        [&] { k_take_rows<false><<<g, kBlock, 0, s>>>(rows, vmap, A.rowptr, A.col, A.w, O.cnt,
+                                                     nullptr, nullptr, nullptr); },
+        [&] { k_take_rows<true><<<g, kBlock, 0, s>>>(rows, vmap, A.rowptr, A.col, A.w, O.cnt,
+                                                    M.rowptr, M.col, M.w); });
+}
+
 // Lanes per row from the mean row length, about eight entries per lane (measured on the composite
 // operator, 16 per row: 2 lanes; the adjoint's transposed levels, ~38 per row: 4 lanes); a
 // resident grid of 8 blocks per SM.
@@ -569,7 +611,7 @@ void spmv(alsub_operator_s &O, const Csr &M, const float *x, float *y, cudaStrea
     else if (S == 4) k_spmv<4><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
     else if (S == 2) k_spmv<2><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
     else k_spmv<1><<<g, 256, 0, s>>>(M.rows, M.rowptr, M.col, M.w, x, y);
-    O.T->launches += 1;
+    if (O.T) O.T->launches += 1;
 }
 
 void free_op(alsub_operator_s *O) {
@@ -727,6 +769,131 @@ alsub_status alsub_build_operator(alsub_topology_t topo, uint32_t flags, void *s
         }
         if (dst) return bail(report((alsub_status)dst, "operator: the topology reports an error"));
     }
+    *out = O;
+    return ALSUB_OK;
+}
+
+alsub_status alsub_build_adaptive_operator(const alsub_topology_t *topos, int32_t n, uint32_t flags,
+                                           void *stream, alsub_operator_t *out) {
+    if (!topos || !out || n < 1) return report(ALSUB_ERR_INVALID_ARG, "bad adaptive operator arguments");
+    *out = nullptr;
+    if (flags & ~(uint32_t)(ALSUB_OP_TRANSPOSE | ALSUB_OP_STACKED))
+        return report(ALSUB_ERR_INVALID_ARG,
+                      "adaptive operator: flags may only be ALSUB_OP_TRANSPOSE and ALSUB_OP_STACKED");
+    long long vmax = 1;
+    for (int k = 0; k < n; k++) {
+        if (!topos[k]) return report(ALSUB_ERR_INVALID_ARG, "adaptive operator: NULL topology");
+        TopoImpl &T = *topology_impl(topos[k]);
+        if (!T.built) return report(ALSUB_ERR_INVALID_ARG, "adaptive operator: topology not built");
+        if (T.s3f)
+            return report(ALSUB_ERR_UNSUPPORTED, "operator: the rows of sqrt(3) meshes with boundaries or "
+                                                 "infinitely sharp creases are evaluated matrix-free only");
+        if (k > 0) {
+            const TopoImpl &P = *topology_impl(topos[k - 1]);
+            if (T.mesh->src_topo != (const void *)&P || T.mesh->src_level != P.levels)
+                return report(ALSUB_ERR_INVALID_ARG, "adaptive operator: a round's mesh was not extracted from "
+                                                     "the last level of the round before");
+        }
+        for (int l = 0; l <= T.levels; l++) vmax = std::max(vmax, T.L[l].V);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    for (int k = 0; k < n; k++) {
+        TopoImpl &T = *topology_impl(topos[k]);
+        if (T.levels > 0) {
+            alsub_status st = ensure_helpers(T, s);
+            if (st) return st;
+        }
+    }
+    alsub_operator_s *O = new (std::nothrow) alsub_operator_s();
+    if (!O) return report(ALSUB_ERR_OOM, "host allocation failed");
+    O->alloc = topology_impl(topos[0])->alloc;
+    O->stream = s;
+    O->flags = flags;
+    {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&O->sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    auto bail = [&](alsub_status e) { cudaStreamSynchronize(s); free_op(O); delete O; return e; };
+    alsub_status st;
+    if ((st = oalloc(*O, &O->cnt, (size_t)vmax))) return bail(st);
+    if ((st = oalloc(*O, (char **)&O->scan_tmp, scan_tmp_bytes(vmax)))) return bail(st);
+    if ((st = oalloc(*O, &O->status, 1))) return bail(st);
+    cudaMemsetAsync(O->status, 0, sizeof(int), s);
+    const bool stacked = flags & ALSUB_OP_STACKED;
+    // C: the rows so far over the control points (no arrays: the identity); parts: each round's
+    // rows when stacked (kept, so C is not released once it is one)
+    Csr C;
+    C.rows = C.cols = topology_impl(topos[0])->L[0].V;
+    bool c_kept = false;
+    std::vector<Csr> parts;
+    auto replace = [&](Csr next) {
+        if (!c_kept) release(*O, C);
+        C = next;
+        c_kept = false;
+    };
+    for (int k = 0; k < n; k++) {
+        TopoImpl &T = *topology_impl(topos[k]);
+        O->T = &T;
+        if (k > 0) {                            // X^(k): the rows of the kept vertices
+            Csr X;
+            if ((st = build_take(*O, C, T.mesh->d_vmap, T.L[0].V, X))) return bail(st);
+            replace(X);
+        }
+        for (int l = 0; l < T.levels; l++) {    // R^(k), level by level
+            Csr Rl;
+            if ((st = build_level(*O, l, Rl))) return bail(st);
+            if (!C.rowptr) {
+                C = Rl;                         // the identity times R_l
+                continue;
+            }
+            Csr next;
+            if ((st = build_product(*O, Rl, C, next))) return bail(st);
+            release(*O, Rl);
+            replace(next);
+        }
+        if (stacked) {
+            if (!C.rowptr) {                    // a round of no levels on the control mesh
+                Csr I;
+                if ((st = build_take(*O, C, nullptr, C.rows, I))) return bail(st);
+                C = I;
+            }
+            parts.push_back(C);
+            c_kept = true;
+        }
+    }
+    O->T = nullptr;                             // the operator keeps nothing of the topologies
+    if (stacked) {
+        Csr S;
+        S.cols = C.cols;
+        for (const Csr &p : parts) { S.rows += p.rows; S.nnz += p.nnz; }
+        if ((st = oalloc(*O, &S.rowptr, S.rows + 1)) || (st = oalloc(*O, &S.col, S.nnz)) ||
+            (st = oalloc(*O, &S.w, S.nnz)))
+            return bail(st);
+        long long r0 = 0, z0 = 0;
+        for (size_t i = 0; i < parts.size(); i++) {
+            const Csr &p = parts[i];
+            const bool last = i + 1 == parts.size();
+            k_rowptr_shift<<<grid_for(p.rows + 1), kBlock, 0, s>>>(p.rows, p.rowptr, z0, S.rowptr + r0, last);
+            cudaMemcpyAsync(S.col + z0, p.col, sizeof(int) * (size_t)p.nnz, cudaMemcpyDeviceToDevice, s);
+            cudaMemcpyAsync(S.w + z0, p.w, sizeof(float) * (size_t)p.nnz, cudaMemcpyDeviceToDevice, s);
+            r0 += p.rows;
+            z0 += p.nnz;
+        }
+        for (Csr &p : parts) release(*O, p);
+        C = S;
+    } else if (!C.rowptr) {                     // one round of no levels: R is the identity
+        Csr I;
+        if ((st = build_take(*O, C, nullptr, C.rows, I))) return bail(st);
+        C = I;
+    }
+    O->C = C;
+    O->has_comp = true;
+    if (flags & ALSUB_OP_TRANSPOSE) {
+        if ((st = build_transpose(*O, O->C, O->CT))) return bail(st);
+        O->has_t = true;
+    }
+    if ((st = check_status(*O))) return bail(st);
     *out = O;
     return ALSUB_OK;
 }

@@ -676,6 +676,40 @@ def test_loop_adaptive_refinement_tracks_extraordinary_vertices_exactly():
     np.testing.assert_array_equal(cur["P"][ids], uni["P"][evs])
 
 
+@pytest.mark.parametrize("scheme,mesh", [
+    ("cc", synth.torus_cc_mixed(10, 8, merge_frac=0.03, split_frac=0.02, crease_frac=0.0, seed=44)),
+    ("cc", synth.torus_cc_mixed(12, 10, merge_frac=0.03, split_frac=0.02, crease_frac=0.06, seed=45)),
+    ("loop", synth.torus_tri(10, 8, flip_frac=0.03, sharp_frac=0.0, seed=46)),
+])
+def test_adaptive_operator_columns_are_the_chain_of_unit_vectors(scheme, mesh):
+    """Brute force: column j of the stacked adaptive operator is what the chain of (extract two
+    rings, refine one level) makes of the unit vector e_j through the eval rules (the positions of
+    the refined levels, not the operator rows), the control mesh's block first; and every row sums
+    to 1 (each rule is affine, an extraction selects)."""
+    rounds = 2
+    A = oracle.adaptive_operator(mesh, rounds, 2, scheme, stacked=True).toarray()
+    V0 = int(mesh["V"])
+    cols = np.zeros((A.shape[0], V0))
+    for j0 in range(0, V0, 3):                 # three unit vectors at once, one per coordinate
+        P = np.zeros((V0, 3))
+        js = [j for j in range(j0, min(j0 + 3, V0))]
+        for c, j in enumerate(js):
+            P[j, c] = 1.0
+        cur, out = dict(mesh, P=P), [P]
+        for _ in range(rounds):
+            e = oracle.extract(cur, None, 2, scheme=scheme)
+            cur = oracle.subdivide(e, 1, scheme)[1]
+            out.append(cur["P"])
+        S = np.vstack(out)
+        for c, j in enumerate(js):
+            cols[:, j] = S[:, c]
+    assert A.shape == cols.shape
+    np.testing.assert_allclose(A, cols, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(A.sum(axis=1), 1.0, rtol=0, atol=1e-12)
+    last = oracle.adaptive_operator(mesh, rounds, 2, scheme).toarray()
+    np.testing.assert_array_equal(last, A[A.shape[0] - last.shape[0]:])
+
+
 # ---------------------------------------------------------------- hierarchical edits (Sec. 3.5)
 
 @pytest.mark.parametrize("scheme,mesh", [
