@@ -60,6 +60,21 @@ struct TriArgs {
 #define ALSUB_SQRT3_TOPO_SMEM 1
 #endif
 
+// Levels >= 1 of a Loop step: the four children 4R..4R+3 of a parent triangle R sit in four
+// adjacent lanes (F is a multiple of 4 and blocks hold whole groups), and a corner lane k < 3
+// loads R's edge id and twin at corner k once for the group. The others come through width-4
+// shuffles: a derived edge id of corner 2 (R's edge k - 1), and the positions of R's vertex v_k+1
+// and edge point E_k+1, which are corners 0 and 1 of sibling k + 1 (its own row), so the parent's
+// face table and those two ring positions are not read (1); or each lane loads them (0).
+#ifndef ALSUB_LOOP_GROUP
+#define ALSUB_LOOP_GROUP 1
+#endif
+
+__device__ __forceinline__ float3 shfl_g4(float3 v, int src) {
+    return f3(__shfl_sync(0xffffffffu, v.x, src, 4), __shfl_sync(0xffffffffu, v.y, src, 4),
+              __shfl_sync(0xffffffffu, v.z, src, 4));
+}
+
 // BND: an open mesh (Loop boundaries). Every stencil that would read across a corner without twin
 // (-1) reads this triangle instead: the points it gives are the boundary edge points and boundary
 // vertices, which the boundary step (cc.cu, boundary_step) writes afterwards from the level's
@@ -69,16 +84,35 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
     // with staged face rows every lane of the warp takes part in the stores (a lane past the end
     // works on face 0 and writes nothing); otherwise such a lane leaves at once
     constexpr bool STAGE = TOPO && ALSUB_LOOP_TOPO_SMEM;
+    // a sibling group shuffles, so its lanes stay until the shuffles are done (a group is whole:
+    // all four lanes live or none)
+    const bool grp = ALSUB_LOOP_GROUP && a.l >= 1;
     const bool live = r_in < a.F && !failed(a.status);
-    if (!STAGE && !live) return;
+    if (!STAGE && !grp && !live) return;
     const int r = live ? r_in : 0;
     const int c = 3 * r, V = a.V, E2 = 2 * a.E;
+    const int R = r >> 2, k = r & 3;
+    // the group's loads of parent R: edge id and twin at corner k (lane 3 repeats corner 2)
+    const int kk = k < 3 ? k : 2;
+    const int pek = grp ? __ldg(a.pce + 3 * R + kk) : 0;
+    const int km = k == 0 ? 2 : k - 1;
+    const int pem = grp ? __shfl_sync(0xffffffffu, pek, km, 4) : 0;    // R's edge k - 1
     int vv[3], ee[3], tt[3];
     bool ow[3];
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         vv[j] = __ldg(a.fv + c + j);
-        ee[j] = a.t.edge_gi(r, j);
+        if (grp && a.t.derive) {
+            // the child rules of the derived edge ids, with R's edges from the group
+            const bool need = k != 3 && j != 1;
+            const int q = j == 0 ? k : km;
+            const bool own = need && loop_own_gi(a.t.lp, R, q, a.z);
+            const int fromParent = 2 * (j == 0 ? pek : pem) + (j == 0 ? (own ? 0 : 1) : (own ? 1 : 0));
+            const int interior = a.t.E2p + 3 * R + (k == 3 ? (j == 2 ? 0 : j + 1) : k);
+            ee[j] = need ? fromParent : interior;
+        } else {
+            ee[j] = a.t.edge_gi(r, j);
+        }
         // the eval of levels >= 1 reads its neighbours from the parent level: no twins needed
         tt[j] = (HELP || (EVAL && a.l == 0)) ? a.t.twin(c + j) : 0;
         ow[j] = loop_own_gi(a.l, r, j, a.z);
@@ -104,15 +138,15 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
                 const int q = 32 * k + lane;
                 if (base + q / 3 < a.F) o[q] = st[w][q];
             }
-            if (!live) return;
-        } else {
+            if (!live && !grp) return;
+        } else if (live) {
             int4 *o = reinterpret_cast<int4 *>(a.fvn + 12 * (size_t)r);
             o[0] = q0;
             o[1] = q1;
             o[2] = q2;
         }
     }
-    if (HELP) {
+    if (HELP && live) {
         int oe[12], ot[12];
 #pragma unroll
         for (int j = 0; j < 3; j++) {
@@ -139,8 +173,10 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
     if (EVAL) {
         const float *P = a.P;
         float3 p[3];
+        // a group's centre lane gathers nothing
 #pragma unroll
-        for (int j = 0; j < 3; j++) p[j] = ldpv(P, vv[j], a.in4);
+        for (int j = 0; j < 3; j++) p[j] = (grp && k == 3) ? f3(0.f, 0.f, 0.f) : ldpv(P, vv[j], a.in4);
+        const int ptk = grp && a.l > 0 ? __ldg(a.ptw + 3 * R + kk) : 0;
         if (a.l == 0) {
 #pragma unroll
             for (int j = 0; j < 3; j++) {
@@ -174,25 +210,28 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
             // are the edge points of its level-(l-1) edges (a walk of the stored parent ring);
             // those of E_k are v_k, v_k+1, E_k-1, E_k+1 and the two other edge points of the
             // triangle across edge k (valence 6).
-            const int R = r >> 2, k = r & 3;
+            const int k1 = k >= 2 ? 0 : k + 1;
+            // v_k+1 and E_k+1 are corners 0 and 1 of sibling k + 1
+            const float3 gv = grp ? shfl_g4(p[0], k1) : f3(0.f, 0.f, 0.f);
+            const float3 ge = grp ? shfl_g4(p[1], k1) : f3(0.f, 0.f, 0.f);
+            if (!live) return;
             if (k < 3) {
                 // The corner children own their corner-0 edge (the half v_k E_k of R's edge k) and
                 // corner-1 edge (E_k E_k-1, inside R). Far vertices: across the half, E'_k2+1 of
                 // the triangle R2 across edge k (twin 3 R2 + k2); across the inner edge, E_k+1.
-                const int k1 = k == 2 ? 0 : k + 1;
-                const int t0 = __ldg(a.ptw + 3 * R + k);
+                const int t0 = grp ? ptk : __ldg(a.ptw + 3 * R + k);
                 const int t = (BND && t0 < 0) ? 3 * R + k : t0;    // across a boundary: R itself
                 const int R2 = t / 3, k2 = t - 3 * R2;
-                const int en = a.Vp + __ldg(a.pce + 3 * R + k1);
                 const int ea = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 2 ? 0 : k2 + 1));
-                const float3 pen = ldpv(P, en, a.in4), pea = ldpv(P, ea, a.in4);
+                const float3 pen = grp ? ge : ldpv(P, a.Vp + __ldg(a.pce + 3 * R + k1), a.in4);
+                const float3 pea = ldpv(P, ea, a.in4);
                 stpv(a.Pn, V + ee[0], 0.375f * (p[0] + p[1]) + 0.125f * (p[2] + pea), a.out4);
                 stpv(a.Pn, V + ee[1], 0.375f * (p[1] + p[2]) + 0.125f * (p[0] + pen), a.out4);
                 if (loop_own_gi(a.l - 1, R, k, a.z)) {
                     // E_k: v_k, E_k-1 (this triangle), v_k+1, E_k+1, and E'_k2+1, E'_k2-1 across
-                    const int vn = __ldg(a.pfv + 3 * R + k1);
+                    const float3 pvn = grp ? gv : ldpv(P, __ldg(a.pfv + 3 * R + k1), a.in4);
                     const int eb = a.Vp + __ldg(a.pce + 3 * R2 + (k2 == 0 ? 2 : k2 - 1));
-                    const float3 sp = (p[0] + p[2]) + (ldpv(P, vn, a.in4) + pen) + (pea + ldpv(P, eb, a.in4));
+                    const float3 sp = (p[0] + p[2]) + (pvn + pen) + (pea + ldpv(P, eb, a.in4));
                     const float beta = c_loop_beta[6];
                     stpv(a.Pn, vv[1], (1.0f - 6.0f * beta) * p[1] + beta * sp, a.out4);
                 }
