@@ -70,6 +70,11 @@ struct TriArgs {
 #define ALSUB_LOOP_GROUP 1
 #endif
 
+__device__ __forceinline__ float3 shfl_down3(float3 v, int d) {
+    return f3(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d),
+              __shfl_down_sync(0xffffffffu, v.z, d));
+}
+
 __device__ __forceinline__ float3 shfl_g4(float3 v, int src) {
     return f3(__shfl_sync(0xffffffffu, v.x, src, 4), __shfl_sync(0xffffffffu, v.y, src, 4),
               __shfl_sync(0xffffffffu, v.z, src, 4));
@@ -292,11 +297,22 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
     }
 }
 
+// Levels >= 1 of a sqrt(3) step: the children 3T, 3T + 1, 3T + 2 of parent triangle T are
+// adjacent lanes (F is a multiple of 3), and the ring of the face point f_T, designated at child
+// 3T, is T's vertices and the face points across T's edges: corners 0 and 1 of the three
+// children. Child 3T takes those of its siblings by shuffles when they are in its warp (lane <= 29),
+// else it loads them (1); or it always loads them (0).
+#ifndef ALSUB_SQRT3_GROUP
+#define ALSUB_SQRT3_GROUP 1
+#endif
+
 template <bool TOPO, bool HELP, bool EVAL>
 __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r_in) {
     constexpr bool STAGE = TOPO && ALSUB_SQRT3_TOPO_SMEM;   // as in loop_body
+    // lanes stay until the shuffles of the siblings' positions are done
+    const bool grp = ALSUB_SQRT3_GROUP && EVAL && a.l >= 1;
     const bool live = r_in < a.F && !failed(a.status);
-    if (!STAGE && !live) return;
+    if (!STAGE && !grp && !live) return;
     const int r = live ? r_in : 0;
     const int c = 3 * r, V = a.V;
     int vv[3], tt[3];
@@ -335,8 +351,8 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r_in) {
                     }
                 }
             }
-            if (!live) return;
-        } else {
+            if (!live && !grp) return;
+        } else if (live) {
 #pragma unroll
             for (int j = 0; j < 3; j++) {
                 int *o = a.fvn + 3 * (size_t)(c + j);
@@ -344,7 +360,7 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r_in) {
             }
         }
     }
-    if (HELP) {
+    if (HELP && live) {
 #pragma unroll
         for (int j = 0; j < 3; j++) {
             int *o = a.twn + 3 * (size_t)(c + j);
@@ -359,7 +375,7 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r_in) {
         float3 p[3];
 #pragma unroll
         for (int j = 0; j < 3; j++) p[j] = ldpv(P, vv[j], a.in4);
-        stpv(a.Pn, V + r, (1.0f / 3.0f) * (p[0] + p[1] + p[2]), a.out4);
+        if (live) stpv(a.Pn, V + r, (1.0f / 3.0f) * (p[0] + p[1] + p[2]), a.out4);
         if (a.l == 0) {
 #pragma unroll 1
             for (int j = 0; j < 3; j++) {
@@ -391,7 +407,8 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r_in) {
             // ring). One descent serves the designation test and the ring.
             int m = a.l - 1, x = r;
             while (m > 0 && x % 3 == 0) { x /= 3; --m; }
-            const bool des = m > 0 ? (x % 3 == 2 && (x / 3) % 3 == 0) : __ldg(a.z.vc + __ldg(a.z.fv + x)) == x;
+            const bool des = live && (m > 0 ? (x % 3 == 2 && (x / 3) % 3 == 0)
+                                             : __ldg(a.z.vc + __ldg(a.z.fv + x)) == x);
             if (des) {
                 if (m > 0) {
                     // x = corner 2 of triangle g = x / 3 of level m, the child of corner g of
@@ -431,12 +448,25 @@ __device__ __forceinline__ void sqrt3_body(const TriArgs &a, int r_in) {
                     }
                 }
             }
-            if (r % 3 == 0) {
-                // v_r = T's vertex 0 and f_F(r) = the face point across T's edge 0 are p[0], p[1]
-                const int v1 = __ldg(a.pfv + r + 1), v2 = __ldg(a.pfv + r + 2);
-                const int n1 = a.Vp + __ldg(a.ptw + r + 1) / 3, n2 = a.Vp + __ldg(a.ptw + r + 2) / 3;
-                const float3 sp = (p[0] + p[1]) + (ldpv(P, v1, a.in4) + ldpv(P, v2, a.in4)) +
-                                  (ldpv(P, n1, a.in4) + ldpv(P, n2, a.in4));
+            // corners 0 and 1 of the next two lanes (the siblings of a child 3T)
+            const float3 s0a = grp ? shfl_down3(p[0], 1) : f3(0.f, 0.f, 0.f);
+            const float3 s0b = grp ? shfl_down3(p[0], 2) : f3(0.f, 0.f, 0.f);
+            const float3 s1a = grp ? shfl_down3(p[1], 1) : f3(0.f, 0.f, 0.f);
+            const float3 s1b = grp ? shfl_down3(p[1], 2) : f3(0.f, 0.f, 0.f);
+            if (live && r % 3 == 0) {
+                // v_r = T's vertex 0 and f_F(r) = the face point across T's edge 0 are p[0], p[1];
+                // T's vertices 1, 2 and the face points across its edges 1, 2 are corners 0 and 1
+                // of children r + 1, r + 2
+                float3 q1, q2, m1, m2;
+                if (grp && (threadIdx.x & 31) <= 29) {
+                    q1 = s0a; q2 = s0b; m1 = s1a; m2 = s1b;
+                } else {
+                    q1 = ldpv(P, __ldg(a.pfv + r + 1), a.in4);
+                    q2 = ldpv(P, __ldg(a.pfv + r + 2), a.in4);
+                    m1 = ldpv(P, a.Vp + __ldg(a.ptw + r + 1) / 3, a.in4);
+                    m2 = ldpv(P, a.Vp + __ldg(a.ptw + r + 2) / 3, a.in4);
+                }
+                const float3 sp = (p[0] + p[1]) + (q1 + q2) + (m1 + m2);
                 const float al = c_sqrt3_alpha[6];
                 stpv(a.Pn, vv[2], (1.0f - al) * p[2] + (al / 6.0f) * sp, a.out4);
             }
