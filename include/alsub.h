@@ -466,7 +466,8 @@ alsub_status alsub_apply_operator_transpose(alsub_operator_t op, const float *gL
  *          round's only. Other flags are INVALID_ARG.
  * alsub_operator_info(op, -1, ...) gives the matrix (rows = the output points, cols = V of topos[0]'s
  * control mesh); alsub_apply_operator computes P_out = R P_0 with P0_dev float[3 cols] and PL_dev
- * float[3 rows]. Synchronises `stream` (the non-zero counts size the allocations).
+ * float[3 rows]. Synchronises `stream` (the non-zero counts size the allocations) and each
+ * topology's stream (a topology whose device status latched an error fails the build with it).
  * Errors: INVALID_ARG (NULL, n < 1, a topology not built, a chain that is not one), UNSUPPORTED (a
  * stencil row of more than 192 entries; a sqrt(3) mesh with boundaries or infinitely sharp
  * creases), OOM, DEVICE.

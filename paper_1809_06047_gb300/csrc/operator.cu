@@ -799,6 +799,14 @@ alsub_status alsub_build_adaptive_operator(const alsub_topology_t *topos, int32_
     cudaStream_t s = (cudaStream_t)stream;
     for (int k = 0; k < n; k++) {
         TopoImpl &T = *topology_impl(topos[k]);
+        // the topology's build and checks (latched on the device) are done before its rows are read
+        int tst = 0;
+        if (cudaStreamSynchronize(T.stream) != cudaSuccess ||
+            cudaMemcpy(&tst, T.status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return report(ALSUB_ERR_DEVICE, "adaptive operator: reading a topology's status failed");
+        }
+        if (tst) return report((alsub_status)tst, "adaptive operator: a topology reports an error");
         if (T.levels > 0) {
             alsub_status st = ensure_helpers(T, s);
             if (st) return st;

@@ -172,3 +172,42 @@ def test_adaptive_operator_refuses_broken_chains():
     A = _dense(op)
     np.testing.assert_array_equal(A, np.eye(m["V"]))
     op.close()
+
+
+def test_adaptive_autograd_gradient_matches_oracle():
+    """torch.autograd through the adaptive operator: loss = sum |P - target|^2 over the last round's
+    points; the gradient equals 2 R^T (R P0 - target) with the oracle's composed R (rows relabelled
+    through the face tables), and FP64 central differences of the oracle's chain of (extract,
+    refine) eval steps on a few control coordinates."""
+    import torch
+    from paper_1809_06047_gb300.autograd import AdaptiveSubdivider
+    m = synth.torus_cc_mixed(16, 14, merge_frac=0.03, split_frac=0.02, crease_frac=0.04, seed=205)
+    rounds = 2
+    sub = AdaptiveSubdivider(m, rounds)
+    ref = oracle.adaptive_operator(m, rounds, 2, "cc")
+    fv_ref = _oracle_faces(m, "cc", rounds)[-1]
+    perm = _relabel(sub.faces, fv_ref, ref.shape[0])
+    rng = np.random.default_rng(11)
+    target = rng.standard_normal((ref.shape[0], 3))              # oracle vertex order
+    P0 = torch.from_numpy(np.ascontiguousarray(m["P"], dtype=np.float32)).cuda().requires_grad_(True)
+    P = sub(P0)
+    tgt = torch.from_numpy(target[np.argsort(perm)].astype(np.float32)).cuda()   # device order
+    loss = ((P - tgt) ** 2).sum()
+    loss.backward()
+    g = P0.grad.cpu().numpy()
+    P0d = m["P"].astype(np.float64)
+    want = 2.0 * (ref.T @ (ref @ P0d - target))
+    assert float(np.abs(g - want).max()) <= 1e-4 * float(np.abs(want).max())
+
+    def f(Q):                                                # the oracle's chain of eval steps
+        cur = dict(m, P=Q)
+        for _ in range(rounds):
+            cur = oracle.subdivide(oracle.extract(cur, None, 2), 1, "cc")[1]
+        return float(((cur["P"] - target) ** 2).sum())
+    h = 1e-6
+    for (i, c) in [(0, 0), (7, 1), (m["V"] // 2, 2), (m["V"] - 1, 0)]:
+        Qp, Qm = P0d.copy(), P0d.copy()
+        Qp[i, c] += h
+        Qm[i, c] -= h
+        fd = (f(Qp) - f(Qm)) / (2 * h)
+        assert abs(g[i, c] - fd) <= 1e-3 * max(1.0, abs(fd))
