@@ -69,6 +69,11 @@ struct TriArgs {
 #ifndef ALSUB_LOOP_GROUP
 #define ALSUB_LOOP_GROUP 1
 #endif
+// With the group, a level's edge ids come from the parent's by the child rules on every level
+// >= 1, stored or not (1), or are read where the level stores them (0).
+#ifndef ALSUB_LOOP_GROUP_IDS
+#define ALSUB_LOOP_GROUP_IDS 1
+#endif
 
 __device__ __forceinline__ float3 shfl_down3(float3 v, int d) {
     return f3(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d),
@@ -107,7 +112,7 @@ __device__ __forceinline__ void loop_body(const TriArgs &a, int r_in) {
 #pragma unroll
     for (int j = 0; j < 3; j++) {
         vv[j] = __ldg(a.fv + c + j);
-        if (grp && a.t.derive) {
+        if (grp && (a.t.derive || ALSUB_LOOP_GROUP_IDS)) {
             // the child rules of the derived edge ids, with R's edges from the group
             const bool need = k != 3 && j != 1;
             const int q = j == 0 ? k : km;
@@ -548,6 +553,10 @@ TriLevel tri_level(const TopoImpl &T, int l) {
     TriLevel t;
     t.sqrt3 = T.scheme == ALSUB_SQRT3;
     t.z = Level0{T.mesh->d_off, T.mesh->d_fv, T.cf0, T.nx0, T.pv0, T.L[0].tw, T.L[0].ce, T.own0, T.vc0, T.rn0};
+    if (l >= 1) {                 // the parent's counts (the child rules need them either way)
+        t.E2p = (int)(2 * T.L[l - 1].E);
+        t.lp = l - 1;
+    }
     if (A.helpers || l == 0) {
         t.ce = A.ce;
         t.tw = A.tw;
@@ -556,8 +565,6 @@ TriLevel tri_level(const TopoImpl &T, int l) {
         t.derive = true;
         t.pce = Pl.ce;
         t.ptw = Pl.tw;
-        t.E2p = (int)(2 * Pl.E);
-        t.lp = l - 1;
     }
     return t;
 }
