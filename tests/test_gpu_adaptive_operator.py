@@ -55,9 +55,10 @@ def _relabel(dev_fv, ref_fv, V):
 
 
 def _dense(op):
+    info = op.info(-1)
     rp, col, w = op.csr(-1)
-    rows = np.repeat(np.arange(op.rows), np.diff(rp))
-    A = np.zeros((op.rows, op.cols))
+    rows = np.repeat(np.arange(info["rows"]), np.diff(rp))
+    A = np.zeros((info["rows"], info["cols"]))
     A[rows, col] = w
     assert np.all(np.diff(rp) >= 0) and rp[0] == 0 and rp[-1] == col.size
     return A
@@ -211,3 +212,30 @@ def test_adaptive_autograd_gradient_matches_oracle():
         Qm[i, c] -= h
         fd = (f(Qp) - f(Qm)) / (2 * h)
         assert abs(g[i, c] - fd) <= 1e-3 * max(1.0, abs(fd))
+
+
+def test_adaptive_operator_of_one_topology_is_its_composite():
+    """A chain of one topology with levels is R = R_{L-1} ... R_0: the same rows as the composite
+    operator of alsub_build_operator, entry for entry; and a round after it composes with it."""
+    from paper_1809_06047_gb300 import alsub
+    m = synth.torus_cc_mixed(12, 10, merge_frac=0.03, split_frac=0.02, crease_frac=0.05, seed=206)
+    M = alsub.Mesh.from_dict(m, "cc")
+    T = alsub.Topology(M, 2, build=True)
+    T.status()
+    comp = alsub.Operator(T, chain=False, compose=True)
+    ad = alsub.AdaptiveOperator([T])
+    for x, y in zip(comp.csr(-1), ad.csr(-1)):
+        np.testing.assert_array_equal(x, y)
+    # one more round extracted from level 2: rows = R^(1) X^(1) R
+    sub = T.extract(2, None, 2)
+    T1 = alsub.Topology(sub, 1, build=True)
+    T1.status()
+    chain = alsub.AdaptiveOperator([T, T1])
+    A = _dense(chain)
+    R = _dense(ad)
+    op1 = alsub.Operator(T1, chain=False, compose=True)
+    R1 = _dense(op1)
+    vmap, _ = sub.maps()
+    np.testing.assert_allclose(A, R1 @ R[vmap], rtol=0, atol=W_TOL)
+    for o in (comp, ad, chain, op1):
+        o.close()
