@@ -71,6 +71,11 @@ struct S3Args {
     const unsigned char *pfm = nullptr;
     int Vp = 0, Fp = 0;
     bool podd = false;
+    // level l - 2 (l >= 2): twins and feature bits, and whether the step from it was a first step
+    const int *p2tw = nullptr;
+    const unsigned char *p2fm = nullptr;
+    int V2 = 0, F2 = 0;
+    bool p2odd = false;
 };
 
 __device__ __forceinline__ int t_next(int x) { const int q = x / 3; return 3 * q + (x - 3 * q == 2 ? 0 : x - 3 * q + 1); }
@@ -115,6 +120,37 @@ __global__ void __launch_bounds__(kBlock) k_s3f_vert(S3Args a) {
                 sum += ldpv(a.P, vt[j], a.in4);
                 sum += ldpv(a.P, a.Vp + tn[j] / 3, a.in4);
             }
+            const float al = c_s3f_alpha[6];
+            stpv(a.Pn, v, (1.0f - al) * ldpv(a.P, v, a.in4) + (al / 6.0f) * sum, a.out4);
+            return;
+        }
+    }
+    if (a.p2tw && v >= a.V2 && v < a.V2 + a.F2) {
+        // The face point f_T of triangle T of level l - 2, when T's edges all flipped on the step
+        // that made it and the six edges at f_T flipped on the next: its ring on level l is the
+        // face points of its six triangles on level l - 1, the children 3T + j of T's corners and
+        // t_j of the corners across (t_j = T's twins), in the walk's order from its corner: f(t_2),
+        // f(3T), f(t_0), f(3T + 1), f(t_1), f(3T + 2). None of its edges is a feature edge.
+        const int T = v - a.V2;
+        int tn[3];
+#pragma unroll
+        for (int j = 0; j < 3; j++) tn[j] = __ldg(a.p2tw + 3 * T + j);
+        bool flat = (__ldg(a.p2fm + T) & 7) == 0 && tn[0] >= 0 && tn[1] >= 0 && tn[2] >= 0;
+        if (flat) {
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                // a second step flips an edge only between two triangles with face points
+                if (!a.p2odd) flat = flat && (__ldg(a.p2fm + tn[j] / 3) & 7) == 0;
+                if (!a.podd) flat = flat && (__ldg(a.pfm + 3 * T + j) & 7) == 0 && (__ldg(a.pfm + tn[j]) & 7) == 0;
+            }
+        }
+        if (flat) {
+            a.vi[v] = make_int4(0, -1, -1, 0);
+            if (!EVAL) return;
+            const int q[6] = {tn[2], 3 * T, tn[0], 3 * T + 1, tn[1], 3 * T + 2};
+            float3 sum = f3(0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 6; u++) sum += ldpv(a.P, a.Vp + q[u], a.in4);
             const float al = c_s3f_alpha[6];
             stpv(a.Pn, v, (1.0f - al) * ldpv(a.P, v, a.in4) + (al / 6.0f) * sum, a.out4);
             return;
@@ -393,6 +429,12 @@ void s3f_step(TopoImpl &T, int l, bool topo, const float *P, float *Pn, cudaStre
         a.pfv = Pl.fv; a.ptw = Pl.tw; a.pfm = Pl.fm;
         a.Vp = (int)Pl.V; a.Fp = (int)Pl.F;
         a.podd = ((l - 1) & 1) == 0;
+    }
+    if (l >= 2) {
+        const LevelBuf &P2 = T.L[l - 2];
+        a.p2tw = P2.tw; a.p2fm = P2.fm;
+        a.V2 = (int)P2.V; a.F2 = (int)P2.F;
+        a.p2odd = ((l - 2) & 1) == 0;
     }
     if (topo && B.cr.cap > 0) cudaMemsetAsync(B.cr.xcount, 0, sizeof(int), s);
     if (ev) {
