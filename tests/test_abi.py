@@ -170,3 +170,19 @@ def test_allocator_needs_both_callbacks():
                                   ctypes.byref(a), None, ctypes.byref(h))
     assert st == 1 and not h.value
     assert b"alloc and free" in lib.alsub_last_error()
+
+
+def test_adaptive_operator_argument_checks_on_host():
+    """alsub_build_adaptive_operator refuses a NULL chain, an empty one and flags other than
+    TRANSPOSE and STACKED before it reads a handle or calls CUDA."""
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    assert lib.alsub_build_adaptive_operator(None, 1, 0, None, ctypes.byref(out)) == 1
+    arr = (ctypes.c_void_p * 1)(None)
+    assert lib.alsub_build_adaptive_operator(arr, 0, 0, None, ctypes.byref(out)) == 1
+    assert lib.alsub_build_adaptive_operator(arr, 1, alsub.Operator.COMPOSE, None, ctypes.byref(out)) == 1
+    assert lib.alsub_build_adaptive_operator(arr, 1, 0, None, None) == 1
+    # a NULL entry in the chain
+    assert lib.alsub_build_adaptive_operator(arr, 1, alsub.Operator.STACKED, None, ctypes.byref(out)) == 1
+    assert b"NULL topology" in lib.alsub_last_error()
+    assert out.value is None
