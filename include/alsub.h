@@ -12,7 +12,8 @@
  * of Fig. module_core) is integer work that emits each level's face table directly; vertex
  * refinement (the eval step) is FP32. The subdivision operator of Sec. 3.6 "Single SpMV
  * evaluation" (R_i per level, or the composite R = R_{L-1} ... R_0) can be built once and applied
- * as one SpMV per frame, and applied transposed for gradients.
+ * as one SpMV per frame, and applied transposed for gradients; so can the composition of a chain of
+ * selective refinement rounds (feature-adaptive subdivision).
  *
  * Conventions shared by every call:
  *  - Every call returns an alsub_status and never aborts, traps or exits. On failure
